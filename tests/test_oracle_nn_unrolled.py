@@ -1,0 +1,196 @@
+"""Pins for the oracle's convolutions, RBF, MoDL and VarNet blocks (CPU only)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import nn as onn
+from oracle import unrolled as ounr
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def brute_conv(x, w, b):
+    B, Ci, H, W = x.shape
+    Co, _, kh, kw = w.shape
+    out = np.zeros((B, Co, H, W))
+    for bb in range(B):
+        for o in range(Co):
+            for yy in range(H):
+                for xx in range(W):
+                    s = b[o]
+                    for c in range(Ci):
+                        for dy in range(kh):
+                            for dx in range(kw):
+                                sy, sx = yy + dy - kh // 2, xx + dx - kw // 2
+                                if 0 <= sy < H and 0 <= sx < W:
+                                    s += w[o, c, dy, dx] * x[bb, c, sy, sx]
+                    out[bb, o, yy, xx] = s
+    return out
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_conv2d_matches_brute_force(k):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 2, 5, 6))
+    w = rng.standard_normal((3, 2, k, k))
+    b = rng.standard_normal(3)
+    np.testing.assert_allclose(onn.conv2d(x, w, b), brute_conv(x, w, b), atol=1e-12)
+
+
+def test_conv2d_backward_finite_differences_and_adjoint():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((1, 2, 5, 4))
+    w = rng.standard_normal((3, 2, 3, 3))
+    b = rng.standard_normal(3)
+    g = rng.standard_normal((1, 3, 5, 4))
+    gx, gw, gb = onn.conv2d_backward(x, w, g)
+    f = lambda xx, ww, bb: float(np.sum(onn.conv2d(xx, ww, bb) * g))
+    eps = 1e-6
+    for idx in [(0, 0, 1, 1), (0, 1, 4, 3), (0, 1, 0, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += eps
+        xm[idx] -= eps
+        assert abs((f(xp, w, b) - f(xm, w, b)) / (2 * eps) - gx[idx]) < 1e-7
+    for idx in [(0, 0, 0, 0), (2, 1, 2, 1), (1, 1, 1, 2)]:
+        wp, wm = w.copy(), w.copy()
+        wp[idx] += eps
+        wm[idx] -= eps
+        assert abs((f(x, wp, b) - f(x, wm, b)) / (2 * eps) - gw[idx]) < 1e-7
+    np.testing.assert_allclose(gb, g.sum(axis=(0, 2, 3)), atol=1e-13)
+    # K^T is the adjoint of the bias-free K
+    u = rng.standard_normal((1, 3, 5, 4))
+    lhs = np.sum(onn.conv2d(x, w) * u)
+    rhs = np.sum(x * onn.conv2d_transpose(u, w))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_rbf_brute_force_and_derivative():
+    rng = np.random.default_rng(3)
+    z = rng.uniform(-1.2, 1.2, size=(1, 2, 3, 3))
+    wts = rng.standard_normal((2, 31))
+    mu = [-1 + 2 * j / 30 for j in range(31)]
+    s = 2 / 30
+    ref = np.zeros_like(z)
+    for i in range(2):
+        for yy in range(3):
+            for xx in range(3):
+                ref[0, i, yy, xx] = sum(wts[i, j] * np.exp(-(z[0, i, yy, xx] - mu[j]) ** 2 / (2 * s * s))
+                                        for j in range(31))
+    np.testing.assert_allclose(onn.rbf(z, wts), ref, atol=1e-13)
+    eps = 1e-7
+    fd = (onn.rbf(z + eps, wts) - onn.rbf(z - eps, wts)) / (2 * eps)
+    np.testing.assert_allclose(onn.rbf_grad_z(z, wts), fd, rtol=1e-6, atol=1e-6)
+
+
+def test_varnet_parameter_count_matches_paper():
+    vals = {}
+    with open(os.path.join(GOLDEN, "varnet_param_count.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = int(v)
+    assert onn.varnet_param_count(vals["T"], vals["Nk"], vals["k"], vals["Nw"]) == vals["params"]
+    filt, rbf, lam = synth.varnet_weights(0)
+    assert 2 * filt.size + rbf.size + lam.size == vals["params"]
+
+
+def test_modl_cnn_param_count():
+    # 2->64->64->64->64->2 3x3 convolutions with biases, plus one lambda
+    assert onn.modl_param_count() + 1 == 113155
+
+
+def test_modl_cnn_backward_fd():
+    rng = np.random.default_rng(4)
+    ws, bs = synth.modl_cnn_weights(5, chans=(2, 4, 4, 2))
+    bs = [rng.standard_normal(b.shape) * 0.1 for b in bs]
+    x = synth.randn_complex((1, 5, 6), 6)
+    g = synth.randn_complex((1, 5, 6), 7)
+    f = lambda xx, ww: float(np.real(np.vdot(g, onn.modl_cnn_forward(xx, ww, bs)[0])))
+    gx, gws, gbs = onn.modl_cnn_backward(x, ws, bs, g)
+    eps = 1e-6
+    for idx in [(0, 1, 2), (0, 4, 5)]:
+        for unit, part in ((1.0, np.real), (1j, np.imag)):
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += unit * eps
+            xm[idx] -= unit * eps
+            assert abs((f(xp, ws) - f(xm, ws)) / (2 * eps) - part(gx[idx])) < 1e-6
+    for l, idx in [(0, (1, 0, 2, 2)), (1, (3, 2, 0, 1)), (2, (1, 3, 1, 1))]:
+        wp = [w.copy() for w in ws]
+        wm = [w.copy() for w in ws]
+        wp[l][idx] += eps
+        wm[l][idx] -= eps
+        assert abs((f(x, wp) - f(x, wm)) / (2 * eps) - gws[l][idx]) < 1e-6
+
+
+def _small_problem(H=12, W=10, C=2, B=1, seed=11):
+    rng = np.random.default_rng(seed)
+    maps = np.stack([synth.coil_maps(C, H, W, rng) for _ in range(B)])
+    mask = synth.line_mask(W, 2.5, 2, "uniform", rng)
+    AHy = synth.randn_complex((B, H, W), seed + 1) * 0.3
+    gt = synth.randn_complex((B, H, W), seed + 2) * 0.3
+    return maps, mask, AHy, gt
+
+
+def test_modl_train_grads_fd():
+    maps, mask, AHy, gt = _small_problem()
+    ws, bs = synth.modl_cnn_weights(3, chans=(2, 3, 2))
+    ws = [w * 0.5 for w in ws]
+    bs = [np.full(b.shape, 0.05) for b in bs]
+    lam, T, it = 0.1, 2, 80
+
+    def L(ww, bb, ll):
+        return ounr.modl_train_grads(AHy, maps, mask, gt, ww, bb, ll, T, it)[0]
+
+    loss, gws, gbs, glam, _ = ounr.modl_train_grads(AHy, maps, mask, gt, ws, bs, lam, T, it)
+    eps = 1e-6
+    fd = (L(ws, bs, lam + eps) - L(ws, bs, lam - eps)) / (2 * eps)
+    assert abs(fd - glam) <= 1e-5 * max(abs(fd), 1e-3)
+    for l, idx in [(0, (0, 1, 1, 1)), (1, (1, 2, 0, 2))]:
+        wp = [w.copy() for w in ws]
+        wm = [w.copy() for w in ws]
+        wp[l][idx] += eps
+        wm[l][idx] -= eps
+        fd = (L(wp, bs, lam) - L(wm, bs, lam)) / (2 * eps)
+        assert abs(fd - gws[l][idx]) <= 1e-5 * max(abs(fd), 1e-3)
+    bp = [b.copy() for b in bs]
+    bm = [b.copy() for b in bs]
+    bp[0][2] += eps
+    bm[0][2] -= eps
+    fd = (L(ws, bp, lam) - L(ws, bm, lam)) / (2 * eps)
+    assert abs(fd - gbs[0][2]) <= 1e-5 * max(abs(fd), 1e-3)
+
+
+def test_varnet_train_grads_fd():
+    maps, mask, AHy, gt = _small_problem(seed=21)
+    rng = np.random.default_rng(5)
+    T, Nk, k = 2, 3, 3
+    filt = (rng.standard_normal((T, Nk, k, k)) + 1j * rng.standard_normal((T, Nk, k, k))) * 0.2
+    wts = rng.standard_normal((T, Nk, 31)) * 0.1
+    lam = np.array([0.8, 0.6])
+
+    def L(f, w, l):
+        return ounr.varnet_train_grads(AHy, maps, mask, gt, f, w, l)[0]
+
+    loss, gf, gw, gl, _ = ounr.varnet_train_grads(AHy, maps, mask, gt, filt, wts, lam)
+    eps = 1e-6
+    for t in range(T):
+        lp, lm = lam.copy(), lam.copy()
+        lp[t] += eps
+        lm[t] -= eps
+        fd = (L(filt, wts, lp) - L(filt, wts, lm)) / (2 * eps)
+        assert abs(fd - gl[t]) <= 1e-5 * max(abs(fd), 1e-4)
+    for idx in [(0, 1, 2), (1, 2, 17)]:
+        wp, wm = wts.copy(), wts.copy()
+        wp[idx] += eps
+        wm[idx] -= eps
+        fd = (L(filt, wp, lam) - L(filt, wm, lam)) / (2 * eps)
+        assert abs(fd - gw[idx]) <= 1e-5 * max(abs(fd), 1e-4)
+    for idx in [(0, 0, 1, 1), (1, 2, 0, 2)]:
+        for unit, part in ((1.0, np.real), (1j, np.imag)):
+            fp, fm = filt.copy(), filt.copy()
+            fp[idx] += unit * eps
+            fm[idx] -= unit * eps
+            fd = (L(fp, wts, lam) - L(fm, wts, lam)) / (2 * eps)
+            assert abs(fd - part(gf[idx])) <= 1e-5 * max(abs(fd), 1e-4)
