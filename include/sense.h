@@ -1,0 +1,127 @@
+/*
+ * libsense — C ABI of the B300 SENSE / unrolled-reconstruction hot path.
+ *
+ * Operations follow Blumenthal et al., "Deep, Deep Learning with BART":
+ *   Eq. 4 ("inverse_problem", Sec. 2.3): A = P F C — coil-sensitivity multiply
+ *     (C), centred unitary 2-D Fourier transform (F), sampling projection (P).
+ *   Eq. 6 ("update_modl", Sec. 2.3.2): the MoDL data-consistency step applies
+ *     S_lambda^{-1} = (A^H A + lambda I)^{-1} with conjugate gradients; the
+ *     derivatives of S^{-1} are written through S itself (same section).
+ *   Eq. 5 ("update_vn", Sec. 2.3.1): the VarNet step uses A^H A x - A^H y.
+ *
+ * Conventions shared by every call
+ *   - Complex data are complex64: interleaved (re, im) float32, 8 bytes.
+ *   - Layouts are row-major, W fastest:
+ *       image x     [B][H][W]
+ *       maps S      [B][C][H][W]     (one set of maps per slice)
+ *       k-space y   [B][C][H][W]     full Cartesian grid, centred (DC at H/2, W/2)
+ *       mask M      [W] (line mask: constant along H; mask_is_lines = 1)
+ *                   or [H][W] (mask_is_lines = 0), float32, centred order.
+ *     The normal operator uses M^2 (P^H P); for 0/1 masks that is M.
+ *   - Every data pointer is a DEVICE pointer owned by the caller and must be
+ *     16-byte aligned; the library never frees caller memory.  A plan keeps
+ *     the maps and mask pointers it was created with (no copy): the caller
+ *     keeps them alive and unchanged for the plan's lifetime.
+ *   - Calls are asynchronous on the plan's CUDA stream; results are ready
+ *     when that stream reaches them.  A plan is not thread-safe.
+ *   - Return value: SENSE_OK (0) or a negative SENSE_E* code; host-side
+ *     argument checks run before any launch, so an error leaves outputs
+ *     untouched.  Device-side failures (CG breakdown, non-finite scalars) set
+ *     bits of the plan's device status word, read by sense_get_status; the
+ *     kernels never trap.
+ *   - Even H and W are required (the centred transform uses the (-1)^n
+ *     modulation of an even-length DFT).
+ */
+#ifndef SENSE_H
+#define SENSE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SENSE_OK 0
+#define SENSE_EINVAL_SHAPE (-1)   /* non-positive or odd size */
+#define SENSE_EINVAL_PTR (-2)     /* NULL, aliased or misaligned pointer */
+#define SENSE_EINVAL_LAMBDA (-3)  /* lambda not finite or negative */
+#define SENSE_EUNSUPPORTED (-4)   /* shape the kernels do not cover (e.g. prime factor > 31) */
+#define SENSE_ECUDA (-5)          /* a CUDA runtime call failed */
+#define SENSE_EWORKSPACE (-6)     /* workspace missing or too small */
+#define SENSE_EINVAL_ARG (-7)     /* other invalid argument (iteration count, flags) */
+
+/* Device status bits (sense_get_status). */
+#define SENSE_STATUS_CG_BREAKDOWN 1 /* Re<p, S p> <= 0 on a slice with nonzero residual */
+#define SENSE_STATUS_NONFINITE 2    /* a CG scalar became NaN or Inf */
+
+typedef struct sense_plan_s* sense_plan;
+
+/* Create a plan for B slices of C coils on an H x W grid.
+ * maps: device complex64 [B][C][H][W]; mask: device float32 [W] or [H][W];
+ * stream: cudaStream_t (NULL = legacy default stream).
+ * The mask is copied to the host once here (synchronously) to build the
+ * pruned-transform tables; later changes to it are not seen.
+ * Errors: SENSE_EINVAL_SHAPE, SENSE_EINVAL_PTR, SENSE_EUNSUPPORTED, SENSE_ECUDA. */
+int sense_plan_create(sense_plan* plan, int B, int C, int H, int W, const void* maps,
+                      const float* mask, int mask_is_lines, void* stream);
+int sense_plan_destroy(sense_plan plan);
+/* Change the stream later calls launch on. */
+int sense_plan_set_stream(sense_plan plan, void* stream);
+
+/* Scratch memory the plan needs for the calls below (bytes).  The caller
+ * allocates it on the device (256-byte aligned) and hands it over once; the
+ * plan uses it until destroyed or given another one.  Calls that overlap in
+ * time on different streams must not share one plan. */
+int sense_plan_workspace_bytes(sense_plan plan, size_t* bytes);
+int sense_plan_set_workspace(sense_plan plan, void* workspace, size_t bytes);
+
+/* y = P F C x (Eq. 4).  x [B][H][W] -> y [B][C][H][W] (zero where M = 0). */
+int sense_forward(sense_plan plan, const void* x, void* y);
+
+/* x = A^H y = sum_c conj(S_c) F^{-1}(M y_c)  (adjoint of Eq. 4; A^H y is the
+ * initialisation x^0 of both MoDL and VarNet, Sec. 2.3.1-2.3.2).
+ * Needs the workspace. */
+int sense_adjoint(sense_plan plan, const void* y, void* x);
+
+/* out = (A^H A + lambda I) x, the operator S_lambda of Eq. 6 (lambda >= 0,
+ * finite).  x and out must not alias.  Fused per-row kernel for line masks
+ * (no workspace); 2-D masks go through the workspace. */
+int sense_normal(sense_plan plan, const void* x, void* out, float lambda);
+
+/* x = S_lambda^{-1} rhs by exactly `iters` conjugate-gradient iterations
+ * (Sec. 2.3.2), independently per slice.
+ *   rhs    [B][H][W]
+ *   x0     [B][H][W] start value, or NULL for zero
+ *   x      [B][H][W] output (may alias x0, must not alias rhs)
+ *   lambda device float64, lambda_count = 1 (shared) or B (per slice), > 0
+ *          (not checked on the host: lambda <= 0 shows up as a breakdown bit)
+ *   rr_hist NULL or device float64 [iters + 1][B]: ||r_i||^2 per iteration.
+ * Vectors are FP32 complex; inner products, alpha and beta are FP64.
+ * A slice whose residual is exactly zero is frozen.  Needs the workspace. */
+int cg_dc_solve(sense_plan plan, const void* rhs, const void* x0, void* x,
+                const double* lambda, int lambda_count, int iters, double* rr_hist);
+
+/* Reverse mode of the MoDL data-consistency block x = S^{-1}(b + lambda z)
+ * (derivative identities of S^{-1}, Sec. 2.3.2):
+ *   grad_rhs    = v = S^{-1} grad_x            (second CG solve, x0 = 0)
+ *   grad_lambda = Re<v, z - x>  (summed over slices if lambda_count = 1, else per slice)
+ * grad_x, x, z: [B][H][W]; z may be NULL (rhs independent of lambda: -Re<v, x>).
+ * grad_lambda: NULL or device float64 [lambda_count], overwritten.
+ * Complex gradients follow Sec. 2.2.2: real part = d/d(re), imaginary = d/d(im).
+ * Needs the workspace. */
+int cg_dc_solve_backward(sense_plan plan, const void* grad_x, const void* x, const void* z,
+                         const double* lambda, int lambda_count, int iters,
+                         void* grad_rhs, double* grad_lambda);
+
+/* Synchronises the plan's stream, returns the OR of device status bits set
+ * since the last call, and clears them. */
+int sense_get_status(sense_plan plan, int* device_status);
+
+/* Static description of an error code (never NULL). */
+const char* sense_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SENSE_H */

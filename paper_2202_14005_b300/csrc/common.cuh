@@ -1,0 +1,129 @@
+// Shared device helpers of libsense: complex float2 arithmetic, register DFTs of
+// small power-of-two length, status words and fixed-order reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sense.h"
+
+#define SENSE_HD __host__ __device__ __forceinline__
+#define SENSE_D __device__ __forceinline__
+
+// ------------------------------------------------------------------ complex
+SENSE_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+SENSE_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+SENSE_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+SENSE_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+SENSE_HD float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+// acc + a * b
+SENSE_HD float2 cfma(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+  return acc;
+}
+// acc + conj(a) * b
+SENSE_HD float2 cfmac(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+  return acc;
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+SENSE_HD float2 cmul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos(2 pi j / 32), j = 0..8 (the other angles follow by symmetry); literal
+// values of the mathematical constants.
+SENSE_D float cos32(int j) {
+  return j == 0 ? 1.0f
+       : j == 1 ? 0.98078528040323044913f
+       : j == 2 ? 0.92387953251128675613f
+       : j == 3 ? 0.83146961230254523708f
+       : j == 4 ? 0.70710678118654752440f
+       : j == 5 ? 0.55557023301960222474f
+       : j == 6 ? 0.38268343236508977173f
+       : j == 7 ? 0.19509032201612826785f
+       : 0.0f;
+}
+// e^{-2 pi i k / n} (INV: e^{+2 pi i k / n}) for n | 32, 0 <= k < n.
+template <bool INV>
+SENSE_D float2 tw_pow2(int k, int n) {
+  const int j = k * (32 / n);  // angle in units of 2 pi / 32
+  const int q = j >> 3, r = j & 7;
+  float c, s;                  // cos and sin of 2 pi j / 32
+  if (q == 0) { c = cos32(r); s = cos32(8 - r); }
+  else if (q == 1) { c = -cos32(8 - r); s = cos32(r); }
+  else if (q == 2) { c = -cos32(r); s = -cos32(8 - r); }
+  else { c = cos32(8 - r); s = -cos32(r); }
+  return INV ? make_float2(c, s) : make_float2(c, -s);
+}
+// a * e^{-/+ 2 pi i k / n}; trivial angles are folded at compile time.
+template <bool INV>
+SENSE_D float2 cmul_tw(float2 a, int k, int n) {
+  if (k == 0) return a;
+  if (4 * k == n) return cmul_mi<INV>(a);
+  if (2 * k == n) return make_float2(-a.x, -a.y);
+  if (4 * k == 3 * n) return cmul_mi<!INV>(a);
+  return cmul(a, tw_pow2<INV>(k, n));
+}
+
+constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+// Bit reversal of i within `bits` <= 5 bits, loop- and call-free so that it
+// folds to a constant inside unrolled loops.
+SENSE_HD int bitrev5(int i, int bits) {
+  const int r = ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
+  return r >> (5 - bits);
+}
+
+// In-register DFT of length N (power of two <= 32): v[k] <- sum_n v[n] w^{nk},
+// w = e^{-2 pi i / N} (INV: e^{+2 pi i / N}), unnormalised.  Radix-2
+// decimation in time; indices and twiddles resolve at compile time.
+template <int N, bool INV>
+SENSE_D void dft_pow2(float2 (&v)[N]) {
+  constexpr int LB = ilog2c(N);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int j = bitrev5(i, LB);
+    if (i < j) { const float2 t = v[i]; v[i] = v[j]; v[j] = t; }
+  }
+#pragma unroll
+  for (int s = 0; s < LB; ++s) {
+    const int half = 1 << s;
+#pragma unroll
+    for (int bf = 0; bf < N / 2; ++bf) {
+      const int k = bf & (half - 1);
+      const int i = ((bf >> s) << (s + 1)) + k;
+      const float2 a = v[i];
+      const float2 b = cmul_tw<INV>(v[i + half], k, 2 * half);
+      v[i] = cadd(a, b);
+      v[i + half] = csub(a, b);
+    }
+  }
+}
+
+// ------------------------------------------------------------ device status
+#define SENSE_DEVST_CG_BREAKDOWN SENSE_STATUS_CG_BREAKDOWN
+#define SENSE_DEVST_NONFINITE SENSE_STATUS_NONFINITE
+
+SENSE_D void set_status(int* st, int bit) {
+  if (st) atomicOr(st, bit);
+}
+
+// --------------------------------------------------------- fixed-order sums
+// Warp sum in a fixed butterfly order (deterministic).
+SENSE_D double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+SENSE_D float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}

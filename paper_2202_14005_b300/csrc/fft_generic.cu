@@ -1,0 +1,351 @@
+// Mixed-radix Stockham transforms in shared memory for the non-fused parts of
+// the SENSE operator: forward A = P F C, adjoint A^H (Eq. 4) and the normal
+// operator for general 2-D masks.  Each 2-D transform is a row pass (length W)
+// and a column pass (length H) through global memory.
+//
+// Centred unitary DFT along one axis of even length L:
+//   F_c[k, n] = L^{-1/2} e^{-2 pi i (k - L/2)(n - L/2)/L}
+//             = (-1)^{L/2} L^{-1/2} (-1)^k e^{-2 pi i k n / L} (-1)^n,
+// i.e. a plain DFT between two (-1)^n modulations.  For the normal operator the
+// modulations cancel against each other (F^H diag(m) F is circulant), so that
+// path uses a plain DFT pair and the mask shifted to plain frequency order.
+#include <cmath>
+#include <vector>
+
+#include "plan.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRows = 4;   // rows per CTA in row passes
+constexpr int kCols = 8;   // columns per CTA in column passes
+constexpr int kMaxPer = 16;  // accumulator slots per thread: kRows * W <= kThreads * kMaxPer
+
+struct Fft1DDev {
+  int L, nst;
+  int radix[SENSE_MAX_STAGES];
+  const float2* tw;
+};
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_small(float2 (&v)[R], const float2* tw, int L) {
+  if constexpr ((R & (R - 1)) == 0) {
+    dft_pow2<R, INV>(v);
+  } else {
+    float2 X[R];
+    const int step = L / R;
+    float2 s = v[0];
+#pragma unroll
+    for (int t = 1; t < R; ++t) s = cadd(s, v[t]);
+    X[0] = s;
+#pragma unroll
+    for (int k = 1; k < R; ++k) {
+      float2 acc = v[0];
+#pragma unroll
+      for (int t = 1; t < R; ++t) {
+        const float2 w = __ldg(tw + step * ((t * k) % R));
+        acc = INV ? cfmac(w, v[t], acc) : cfma(v[t], w, acc);
+      }
+      X[k] = acc;
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = X[k];
+  }
+}
+
+// One radix-R Stockham butterfly j of a stage whose sub-transforms have length Ns.
+template <int R, bool INV>
+__device__ __forceinline__ void bfly(const float2* in, float2* out, int j, int Ns, int L,
+                                     const float2* tw) {
+  const int stride = L / R;
+  float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
+  const int k = j % Ns;
+  if (Ns > 1) {
+    const int step = k * (L / (Ns * R));
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const float2 w = __ldg(tw + step * r);
+      v[r] = INV ? cmulc(w, v[r]) : cmul(v[r], w);
+    }
+  }
+  dft_small<R, INV>(v, tw, L);
+  const int idxD = (j / Ns) * Ns * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[idxD + r * Ns] = v[r];
+}
+
+// Transform ntr contiguous sequences of length L held in a (ping-pong with b).
+// Returns the buffer holding the result.  All threads of the CTA take part.
+template <bool INV>
+__device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f) {
+  const int L = f.L;
+  int Ns = 1;
+  for (int s = 0; s < f.nst; ++s) {
+    const int R = f.radix[s];
+    const int nb = L / R;
+    for (int w = threadIdx.x; w < ntr * nb; w += blockDim.x) {
+      const int tr = w / nb, j = w - tr * nb;
+      const float2* in = a + tr * L;
+      float2* out = b + tr * L;
+      switch (R) {
+        case 2: bfly<2, INV>(in, out, j, Ns, L, f.tw); break;
+        case 3: bfly<3, INV>(in, out, j, Ns, L, f.tw); break;
+        case 4: bfly<4, INV>(in, out, j, Ns, L, f.tw); break;
+        case 5: bfly<5, INV>(in, out, j, Ns, L, f.tw); break;
+        case 7: bfly<7, INV>(in, out, j, Ns, L, f.tw); break;
+        case 8: bfly<8, INV>(in, out, j, Ns, L, f.tw); break;
+        case 11: bfly<11, INV>(in, out, j, Ns, L, f.tw); break;
+        case 13: bfly<13, INV>(in, out, j, Ns, L, f.tw); break;
+        case 17: bfly<17, INV>(in, out, j, Ns, L, f.tw); break;
+        case 19: bfly<19, INV>(in, out, j, Ns, L, f.tw); break;
+        case 23: bfly<23, INV>(in, out, j, Ns, L, f.tw); break;
+        case 29: bfly<29, INV>(in, out, j, Ns, L, f.tw); break;
+        case 31: bfly<31, INV>(in, out, j, Ns, L, f.tw); break;
+        default: break;
+      }
+    }
+    __syncthreads();
+    float2* t = a; a = b; b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+__device__ __forceinline__ float pm1(int n) { return (n & 1) ? -1.f : 1.f; }
+
+// Row pass, expanding by the coil maps:  T[b,c,h,:] = DFT_W(S_c x) with
+//   mode 0 (forward): input (-1)^{h+w} S x, output (-1)^{kw} (-1)^{W/2} / sqrt(W)
+//   mode 1 (normal):  plain DFT, no modulation, no scale.
+__global__ void __launch_bounds__(kThreads) k_row_expand(int B, int C, int H, const float2* x,
+                                                         const float2* maps, float2* T,
+                                                         Fft1DDev f, int mode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = f.L;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kRows * W;
+  const int bc = blockIdx.y, b = bc / C, c = bc - b * C;
+  const int h0 = blockIdx.x * kRows;
+  const int nr = min(kRows, H - h0);
+  for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
+    const int r = i / W, w = i - r * W, h = h0 + r;
+    float2 v = cmul(maps[(((size_t)b * C + c) * H + h) * W + w], x[((size_t)b * H + h) * W + w]);
+    if (mode == 0) v = cscale(v, pm1(h + w));
+    a[i] = v;
+  }
+  __syncthreads();
+  float2* res = fft_smem<false>(a, bb, nr, f);
+  const float sc = (mode == 0) ? pm1(W / 2) * rsqrtf((float)W) : 1.f;
+  for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
+    const int r = i / W, k = i - r * W;
+    float2 v = res[i];
+    if (mode == 0) v = cscale(v, sc * pm1(k));
+    T[(((size_t)b * C + c) * H + h0 + r) * W + k] = v;
+  }
+}
+
+// Column pass over data [B*C][H][W], kCols columns per CTA (src may equal dst).
+//   mode 0 (forward):  dst = M (-1)^{kh} (-1)^{H/2}/sqrt(H) DFT_H(src)
+//   mode 1 (adjoint):  dst = (-1)^h (-1)^{H/2}/sqrt(H) IDFT_H((-1)^{kh} M src)
+//   mode 2 (normal):   dst = IDFT_H(m2s DFT_H(src))   (m2s: mask^2/(HW), plain order)
+// mask: modes 0/1 the centred mask ([W] if lines else [H][W]); mode 2 shifted mask^2.
+__global__ void __launch_bounds__(kThreads) k_col(int W, const float2* src, float2* dst,
+                                                  Fft1DDev f, const float* mask, int lines,
+                                                  int mode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H = f.L;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kCols * H;
+  const int bc = blockIdx.y;
+  const int w0 = blockIdx.x * kCols;
+  const int nc = min(kCols, W - w0);
+  const size_t base = (size_t)bc * H * W;
+  for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
+    const int h = i / kCols, cc = i - h * kCols;
+    float2 v = make_float2(0.f, 0.f);
+    if (cc < nc) {
+      v = src[base + (size_t)h * W + w0 + cc];
+      if (mode == 1) {
+        const int w = w0 + cc;
+        const float m = lines ? mask[w] : mask[(size_t)h * W + w];
+        v = cscale(v, m * pm1(h));
+      }
+    }
+    a[cc * H + h] = v;
+  }
+  __syncthreads();
+  float2* res;
+  if (mode == 1) {
+    res = fft_smem<true>(a, bb, kCols, f);
+  } else {
+    res = fft_smem<false>(a, bb, kCols, f);
+    if (mode == 2) {
+      float2* other = (res == a) ? bb : a;
+      for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
+        const int cc = i / H, k = i - cc * H;
+        const int w = w0 + cc;
+        float m = 0.f;
+        if (cc < nc) m = lines ? mask[w] : mask[(size_t)k * W + w];
+        res[i] = cscale(res[i], m);
+      }
+      __syncthreads();
+      res = fft_smem<true>(res, other, kCols, f);
+    }
+  }
+  const float sc = pm1(H / 2) * rsqrtf((float)H);
+  for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
+    const int h = i / kCols, cc = i - h * kCols;
+    if (cc >= nc) continue;
+    float2 v = res[cc * H + h];
+    const int w = w0 + cc;
+    if (mode == 0) {
+      const float m = lines ? mask[w] : mask[(size_t)h * W + w];
+      v = cscale(v, sc * pm1(h) * m);
+    } else if (mode == 1) {
+      v = cscale(v, sc * pm1(h));
+    }
+    dst[base + (size_t)h * W + w] = v;
+  }
+}
+
+// Row pass with coil combination:
+//   out[b,h,:] = sum_c conj(S_c) post(IDFT_W(pre(T[b,c,h,:]))) (+ lambda xin)
+//   mode 1 (adjoint): pre (-1)^{kw}, post (-1)^w (-1)^{W/2}/sqrt(W)
+//   mode 2 (normal):  no modulation, no scale (the scale sits in the mask table)
+__global__ void __launch_bounds__(kThreads) k_row_combine(int C, int H, const float2* T,
+                                                          const float2* maps, float2* out,
+                                                          Fft1DDev f, int mode,
+                                                          const float2* xin, float lam_host,
+                                                          const double* lam_dev) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = f.L;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kRows * W;
+  const int b = blockIdx.y;
+  const int h0 = blockIdx.x * kRows;
+  const int nr = min(kRows, H - h0);
+  float2 acc[kMaxPer];
+#pragma unroll
+  for (int e = 0; e < kMaxPer; ++e) acc[e] = make_float2(0.f, 0.f);
+  const float sc = pm1(W / 2) * rsqrtf((float)W);
+  for (int c = 0; c < C; ++c) {
+    for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
+      const int r = i / W, k = i - r * W;
+      float2 v = T[(((size_t)b * C + c) * H + h0 + r) * W + k];
+      if (mode == 1) v = cscale(v, pm1(k));
+      a[i] = v;
+    }
+    __syncthreads();
+    float2* res = fft_smem<true>(a, bb, nr, f);
+#pragma unroll
+    for (int e = 0; e < kMaxPer; ++e) {
+      const int i = threadIdx.x + e * blockDim.x;
+      if (i < nr * W) {
+        const int r = i / W, w = i - r * W;
+        float2 v = res[i];
+        if (mode == 1) v = cscale(v, sc * pm1(w));
+        const float2 s = maps[(((size_t)b * C + c) * H + h0 + r) * W + w];
+        acc[e] = cfmac(s, v, acc[e]);
+      }
+    }
+    __syncthreads();
+  }
+  const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
+#pragma unroll
+  for (int e = 0; e < kMaxPer; ++e) {
+    const int i = threadIdx.x + e * blockDim.x;
+    if (i < nr * W) {
+      const size_t o = ((size_t)b * H + h0) * W + i;
+      float2 v = acc[e];
+      if (xin) {
+        const float2 xv = xin[o];
+        v.x = fmaf(lam, xv.x, v.x);
+        v.y = fmaf(lam, xv.y, v.y);
+      }
+      out[o] = v;
+    }
+  }
+}
+
+Fft1DDev dev(const Fft1D& f) {
+  Fft1DDev d;
+  d.L = f.L;
+  d.nst = f.nst;
+  for (int i = 0; i < SENSE_MAX_STAGES; ++i) d.radix[i] = f.radix[i];
+  d.tw = f.tw;
+  return d;
+}
+
+bool set_smem(const void* k, int bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+
+int smem_rows(int W) { return 2 * kRows * W * (int)sizeof(float2); }
+int smem_cols(int H) { return 2 * kCols * H * (int)sizeof(float2); }
+
+}  // namespace
+
+// Factor L into radices 8, 4, 2 and odd primes <= 31; fill the twiddle table.
+int build_fft1d(Fft1D& f, int L, std::vector<float2>& host_tw) {
+  f.L = L;
+  f.nst = 0;
+  int n = L;
+  while (n % 8 == 0 && f.nst < SENSE_MAX_STAGES) { f.radix[f.nst++] = 8; n /= 8; }
+  while (n % 4 == 0 && f.nst < SENSE_MAX_STAGES) { f.radix[f.nst++] = 4; n /= 4; }
+  while (n % 2 == 0 && f.nst < SENSE_MAX_STAGES) { f.radix[f.nst++] = 2; n /= 2; }
+  const int primes[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+  for (int p : primes)
+    while (n % p == 0 && f.nst < SENSE_MAX_STAGES) { f.radix[f.nst++] = p; n /= p; }
+  if (n != 1) return SENSE_EUNSUPPORTED;
+  host_tw.resize(L);
+  for (int m = 0; m < L; ++m) {
+    const double ang = -2.0 * M_PI * m / L;
+    host_tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+  }
+  return SENSE_OK;
+}
+
+int generic_prepare(sense_plan p) {
+  if (kRows * p->W > kThreads * kMaxPer) return SENSE_EUNSUPPORTED;
+  const int sr = smem_rows(p->W), sc = smem_cols(p->H);
+  if (sr > 200 * 1024 || sc > 200 * 1024) return SENSE_EUNSUPPORTED;
+  if (!set_smem((const void*)k_row_expand, sr) || !set_smem((const void*)k_row_combine, sr) ||
+      !set_smem((const void*)k_col, sc))
+    return SENSE_ECUDA;
+  return SENSE_OK;
+}
+
+int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
+  const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
+  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->C, p->H, x, p->maps, y,
+                                                              dev(p->fW), 0);
+  const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
+  k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, y, dev(p->fH), p->mask,
+                                                      p->mask_is_lines, 0);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
+  const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
+  k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, p->w.T, dev(p->fH), p->mask,
+                                                      p->mask_is_lines, 1);
+  const dim3 gr((p->H + kRows - 1) / kRows, p->B);
+  k_row_combine<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->C, p->H, p->w.T, p->maps, x,
+                                                              dev(p->fW), 1, nullptr, 0.f, nullptr);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
+                          const double* lam_dev) {
+  const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
+  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->C, p->H, x, p->maps,
+                                                              p->w.T, dev(p->fW), 1);
+  const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
+  k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, p->w.T, p->w.T, dev(p->fH),
+                                                      p->mask2s, p->mask_is_lines, 2);
+  const dim3 gr2((p->H + kRows - 1) / kRows, p->B);
+  k_row_combine<<<gr2, kThreads, smem_rows(p->W), p->stream>>>(
+      p->C, p->H, p->w.T, p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}

@@ -1,0 +1,98 @@
+// Internal plan state of libsense and the launcher declarations shared by the
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+#define SENSE_MAX_STAGES 24
+
+// Tables of a 1-D transform of length L (generic mixed-radix path).
+struct Fft1D {
+  int L = 0;
+  int nst = 0;
+  int radix[SENSE_MAX_STAGES] = {0};
+  float2* tw = nullptr;  // device [L], e^{-2 pi i m / L}
+};
+
+// Tables of the fused line-mask normal operator, W = Q * P (Q a power of two).
+struct LinesTables {
+  int ok = 0;
+  int Q = 0, P = 0, J = 0, JMAX = 0;
+  int kstride = 0;         // float4 quads per k1 block of the coefficient table
+  int rows = 0, nwr = 0, threads = 0, smem = 0, grid = 0;
+  float4* coef = nullptr;  // [Q][kstride]
+  float2* tw = nullptr;    // [Q][P] e^{-2 pi i t k1 / W}
+  float* wt = nullptr;     // [Q][J] mask^2 / W per slot (0 = padding)
+  float* sgn = nullptr;    // [Q][J] (-1)^{k2} (even P only)
+};
+
+// Scratch carved from the caller's workspace.
+struct Workspace {
+  float2* T = nullptr;          // [B][C][H][W] coil-image intermediate
+  float2* r = nullptr;          // [B][H][W]
+  float2* p = nullptr;
+  float2* q = nullptr;
+  double* part = nullptr;       // [B][H] per-row partial sums
+  double* rr = nullptr;         // [B]  ||r||^2
+  double* alpha = nullptr;      // [B]
+  double* beta = nullptr;       // [B]
+  double* lam = nullptr;        // [B]  lambda per slice (float64)
+  unsigned* counter = nullptr;  // last-block counter (zero between kernels)
+};
+
+struct sense_plan_s {
+  int B = 0, C = 0, H = 0, W = 0;
+  const float2* maps = nullptr;
+  const float* mask = nullptr;  // device, centred order
+  int mask_is_lines = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 148;
+  std::vector<float> mask_h;    // host copy (centred order)
+  float* mask2s = nullptr;      // device: mask^2/(H W), shifted to plain FFT order
+  LinesTables lines;
+  Fft1D fH, fW;
+  int* status = nullptr;        // device status word (plan-owned)
+  void* own = nullptr;          // plan-owned device allocation (tables + status)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  Workspace w;
+};
+
+// --------------------------------------------------------------- launchers
+// Modes of the fused line-mask normal-operator kernel.
+enum NormalMode { NM_PLAIN = 0, NM_CG = 1, NM_RESID = 2 };
+
+struct NormalLaunch {
+  int mode = NM_PLAIN;
+  const float2* x = nullptr;     // input (NM_CG: r)
+  const float2* pold = nullptr;  // NM_CG: previous direction (NULL on iteration 0)
+  float2* pout = nullptr;        // NM_CG: new direction written here
+  float2* out = nullptr;
+  const float2* rhs = nullptr;   // NM_RESID: out = rhs - S x
+  float lam_host = 0.f;
+  const double* lam_dev = nullptr;  // per-slice lambda [B] if non-NULL
+  const double* beta = nullptr;     // NM_CG: [B]
+  double* part = nullptr;        // [B][H] row partials: Re<x_eff, out> (NM_RESID: ||out||^2)
+  int finalize = 0;              // 1: alpha = rr / pq; 2: rr = sum (+ rr_hist row)
+  double* rr_hist_row = nullptr;
+};
+
+int launch_normal_lines(sense_plan p, const NormalLaunch& L);
+int build_lines_tables(sense_plan p);
+void free_lines_tables(sense_plan p);
+
+int build_fft1d(Fft1D& f, int L, std::vector<float2>& host_tw);
+int generic_prepare(sense_plan p);
+int launch_forward_generic(sense_plan p, const float2* x, float2* y);
+int launch_adjoint_generic(sense_plan p, const float2* y, float2* x);
+int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
+                          const double* lam_dev);
+
+int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const double* lam,
+           int lam_count, int iters, double* rr_hist);
+int launch_dot_rows(sense_plan p, const float2* a, const float2* b, const float2* c,
+                    double* out, int out_count);
