@@ -113,6 +113,18 @@ int cg_dc_solve_backward(sense_plan plan, const void* grad_x, const void* x, con
                          const double* lambda, int lambda_count, int iters,
                          void* grad_rhs, double* grad_lambda);
 
+/* Profiling.  The library counts every kernel it launches for a plan; with
+ * enable != 0 it also records a CUDA event pair on the plan's stream around
+ * each launch of the fused line-mask normal-operator kernel (the one the
+ * operator and the CG iterations spend their time in). */
+int sense_plan_profile(sense_plan plan, int enable);
+/* Synchronises the plan's stream if events are pending and returns, since the
+ * last read: the summed event time of the timed launches (ms), their number,
+ * and the number of kernels launched; then resets all three.  Any output
+ * pointer may be NULL. */
+int sense_plan_profile_read(sense_plan plan, double* normal_ms, int* normal_launches,
+                            long long* kernel_launches);
+
 /* Synchronises the plan's stream, returns the OR of device status bits set
  * since the last call, and clears them. */
 int sense_get_status(sense_plan plan, int* device_status);

@@ -135,6 +135,7 @@ int sense_plan_create(sense_plan* out, int B, int C, int H, int W, const void* m
 
 int sense_plan_destroy(sense_plan p) {
   if (!p) return SENSE_EINVAL_PTR;
+  for (cudaEvent_t e : p->prof.ev) cudaEventDestroy(e);
   free_lines_tables(p);
   if (p->own) cudaFree(p->own);
   delete p;
@@ -243,6 +244,34 @@ int sense_get_status(sense_plan p, int* device_status) {
       cudaMemsetAsync(p->status, 0, sizeof(int), p->stream) != cudaSuccess)
     return SENSE_ECUDA;
   *device_status = v;
+  return SENSE_OK;
+}
+
+int sense_plan_profile(sense_plan p, int enable) {
+  if (!p) return SENSE_EINVAL_PTR;
+  p->prof.on = enable ? 1 : 0;
+  return SENSE_OK;
+}
+
+int sense_plan_profile_read(sense_plan p, double* normal_ms, int* normal_launches,
+                            long long* kernel_launches) {
+  if (!p) return SENSE_EINVAL_PTR;
+  Profiler& f = p->prof;
+  double ms = 0.0;
+  if (f.used > 0) {
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return SENSE_ECUDA;
+    for (int i = 0; i < f.used; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, f.ev[2 * (size_t)i], f.ev[2 * (size_t)i + 1]) != cudaSuccess)
+        return SENSE_ECUDA;
+      ms += t;
+    }
+  }
+  if (normal_ms) *normal_ms = ms;
+  if (normal_launches) *normal_launches = f.used;
+  if (kernel_launches) *kernel_launches = f.launches;
+  f.used = 0;
+  f.launches = 0;
   return SENSE_OK;
 }
 

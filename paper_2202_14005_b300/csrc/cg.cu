@@ -220,6 +220,7 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
   const int gr = grid_rows(p);
   const int B = p->B;
   k_lam_expand<<<(B + 127) / 128, 128, 0, p->stream>>>(B, lam, lam_count, w.lam);
+  count_launch(p);
   // ---- initial residual
   if (x0) {
     if (x0 != x &&
@@ -236,11 +237,13 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
       RowArgs a = base_args(p);
       a.a = rhs; a.o1 = w.r; a.fin = FIN_RR0; a.hist = rr_hist;
       k_resid<<<gr, kWarps * 32, 0, p->stream>>>(a);
+      count_launch(p);
     }
   } else {
     RowArgs a = base_args(p);
     a.a = rhs; a.o1 = w.r; a.o2 = x; a.fin = FIN_RR0; a.hist = rr_hist;
     k_cg_init<<<gr, kWarps * 32, 0, p->stream>>>(a);
+    count_launch(p);
   }
   // ---- iterations
   for (int it = 0; it < iters; ++it) {
@@ -254,14 +257,17 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
       RowArgs a = base_args(p);
       a.a = w.r; a.o1 = w.p; a.beta = it ? w.beta : nullptr;
       k_cg_p<<<gr, kWarps * 32, 0, p->stream>>>(a);
+      count_launch(p);
       if (int e = launch_normal_generic(p, w.p, w.q, 0.f, w.lam)) return e;
       RowArgs d = base_args(p);
       d.a = w.p; d.b = w.q; d.fin = FIN_ALPHA;
       k_dot<<<gr, kWarps * 32, 0, p->stream>>>(d);
+      count_launch(p);
     }
     RowArgs u = base_args(p);
     u.a = w.p; u.b = w.q; u.o1 = x; u.o2 = w.r; u.fin = FIN_RRNEW; u.hist = hist;
     k_cg_update<<<gr, kWarps * 32, 0, p->stream>>>(u);
+    count_launch(p);
   }
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -272,5 +278,6 @@ int launch_dot_rows(sense_plan p, const float2* a_, const float2* b_, const floa
   RowArgs a = base_args(p);
   a.a = a_; a.b = b_; a.c = c_; a.fin = FIN_GLAM; a.gout = out; a.gcount = out_count;
   k_dot<<<grid_rows(p), kWarps * 32, 0, p->stream>>>(a);
+  count_launch(p);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

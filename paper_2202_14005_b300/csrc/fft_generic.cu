@@ -323,6 +323,7 @@ int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, y, dev(p->fH), p->mask,
                                                       p->mask_is_lines, 0);
+  count_launch(p, 2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
@@ -333,6 +334,7 @@ int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
   const dim3 gr((p->H + kRows - 1) / kRows, p->B);
   k_row_combine<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->C, p->H, p->w.T, p->maps, x,
                                                               dev(p->fW), 1, nullptr, 0.f, nullptr);
+  count_launch(p, 2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
@@ -347,5 +349,6 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
   const dim3 gr2((p->H + kRows - 1) / kRows, p->B);
   k_row_combine<<<gr2, kThreads, smem_rows(p->W), p->stream>>>(
       p->C, p->H, p->w.T, p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
+  count_launch(p, 3);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

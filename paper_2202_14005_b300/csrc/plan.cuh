@@ -43,6 +43,14 @@ struct Workspace {
   unsigned* counter = nullptr;  // last-block counter (zero between kernels)
 };
 
+// Launch accounting and optional CUDA-event timing of the fused normal kernel.
+struct Profiler {
+  int on = 0;
+  long long launches = 0;            // every kernel this plan launched
+  std::vector<cudaEvent_t> ev;       // start/stop pairs
+  int used = 0;                      // pairs recorded since the last read
+};
+
 struct sense_plan_s {
   int B = 0, C = 0, H = 0, W = 0;
   const float2* maps = nullptr;
@@ -60,7 +68,23 @@ struct sense_plan_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   Workspace w;
+  Profiler prof;
 };
+
+inline void count_launch(sense_plan p, int n = 1) { p->prof.launches += n; }
+// Records the start (stop = false) or stop event of one timed launch.
+inline void prof_mark(sense_plan p, bool stop) {
+  Profiler& f = p->prof;
+  if (!f.on) return;
+  const size_t need = 2 * (size_t)f.used + 2;
+  while (f.ev.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { f.on = 0; return; }
+    f.ev.push_back(e);
+  }
+  cudaEventRecord(f.ev[2 * (size_t)f.used + (stop ? 1 : 0)], p->stream);
+  if (stop) ++f.used;
+}
 
 // --------------------------------------------------------------- launchers
 // Modes of the fused line-mask normal-operator kernel.

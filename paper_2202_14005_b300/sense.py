@@ -1,0 +1,153 @@
+"""Torch-facing wrappers of the libsense C ABI (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; torch provides device
+memory (tensors, the workspace) and the current stream.  Names follow the C
+ABI and the paper's notation (A = P F C, Eq. 4; S_lambda = A^H A + lambda I,
+Eq. 6).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _req(t: torch.Tensor, name: str, dtype, shape):
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class SensePlan:
+    """A plan for B slices, C coils, H x W images with fixed maps and mask.
+
+    maps: complex64 [B, C, H, W]; mask: float32 [W] (line mask) or [H, W].
+    The plan keeps references to both tensors and owns a torch workspace.
+    """
+
+    def __init__(self, maps: torch.Tensor, mask: torch.Tensor):
+        B, Cc, H, W = maps.shape
+        _req(maps, "maps", torch.complex64, (B, Cc, H, W))
+        lines = 1 if mask.dim() == 1 else 0
+        _req(mask, "mask", torch.float32, (W,) if lines else (H, W))
+        self.B, self.C, self.H, self.W = B, Cc, H, W
+        self.maps, self.mask, self.lines = maps, mask, lines
+        self._lib = _lib.lib()
+        h = C.c_void_p()
+        _lib.check("sense_plan_create", self._lib.sense_plan_create(
+            C.byref(h), B, Cc, H, W, _ptr(maps), _ptr(mask), lines, _stream()))
+        self._h = h
+        nb = C.c_size_t()
+        _lib.check("sense_plan_workspace_bytes", self._lib.sense_plan_workspace_bytes(h, C.byref(nb)))
+        self.workspace = torch.empty(int(nb.value), dtype=torch.uint8, device=maps.device)
+        _lib.check("sense_plan_set_workspace",
+                   self._lib.sense_plan_set_workspace(h, _ptr(self.workspace), nb.value))
+
+    # -- helpers
+    def _sync_stream(self):
+        _lib.check("sense_plan_set_stream", self._lib.sense_plan_set_stream(self._h, _stream()))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sense_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def img_shape(self):
+        return (self.B, self.H, self.W)
+
+    # -- operators
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """y = P F C x (Eq. 4)."""
+        _req(x, "x", torch.complex64, self.img_shape())
+        y = out if out is not None else torch.empty((self.B, self.C, self.H, self.W),
+                                                    dtype=torch.complex64, device=x.device)
+        self._sync_stream()
+        _lib.check("sense_forward", self._lib.sense_forward(self._h, _ptr(x), _ptr(y)))
+        return y
+
+    def adjoint(self, y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """x = A^H y."""
+        _req(y, "y", torch.complex64, (self.B, self.C, self.H, self.W))
+        x = out if out is not None else torch.empty(self.img_shape(), dtype=torch.complex64,
+                                                    device=y.device)
+        self._sync_stream()
+        _lib.check("sense_adjoint", self._lib.sense_adjoint(self._h, _ptr(y), _ptr(x)))
+        return x
+
+    def normal(self, x: torch.Tensor, lam: float = 0.0, out: torch.Tensor | None = None):
+        """(A^H A + lambda I) x."""
+        _req(x, "x", torch.complex64, self.img_shape())
+        o = out if out is not None else torch.empty_like(x)
+        self._sync_stream()
+        _lib.check("sense_normal", self._lib.sense_normal(self._h, _ptr(x), _ptr(o), float(lam)))
+        return o
+
+    def cg_solve(self, rhs, lam: torch.Tensor, iters: int, x0=None, out=None, rr_hist=None):
+        """x = S_lambda^{-1} rhs by `iters` CG iterations (lam: float64 [1] or [B] on device)."""
+        _req(rhs, "rhs", torch.complex64, self.img_shape())
+        if x0 is not None:
+            _req(x0, "x0", torch.complex64, self.img_shape())
+        if lam.dtype != torch.float64 or lam.device.type != "cuda" or lam.numel() not in (1, self.B):
+            raise ValueError("lam must be a CUDA float64 tensor with 1 or B entries")
+        lam = lam.contiguous()
+        x = out if out is not None else torch.empty_like(rhs)
+        if rr_hist is not None:
+            _req(rr_hist, "rr_hist", torch.float64, (iters + 1, self.B))
+        self._sync_stream()
+        _lib.check("cg_dc_solve", self._lib.cg_dc_solve(
+            self._h, _ptr(rhs), _ptr(x0), _ptr(x), _ptr(lam), lam.numel(), int(iters),
+            _ptr(rr_hist)))
+        return x
+
+    def cg_solve_backward(self, grad_x, x, z, lam: torch.Tensor, iters: int,
+                          grad_rhs=None, grad_lam=None):
+        """(v = S^{-1} grad_x, Re<v, z - x>) for the block x = S^{-1}(b + lambda z)."""
+        _req(grad_x, "grad_x", torch.complex64, self.img_shape())
+        _req(x, "x", torch.complex64, self.img_shape())
+        if z is not None:
+            _req(z, "z", torch.complex64, self.img_shape())
+        lam = lam.contiguous()
+        v = grad_rhs if grad_rhs is not None else torch.empty_like(grad_x)
+        gl = grad_lam if grad_lam is not None else torch.empty(lam.numel(), dtype=torch.float64,
+                                                               device=grad_x.device)
+        self._sync_stream()
+        _lib.check("cg_dc_solve_backward", self._lib.cg_dc_solve_backward(
+            self._h, _ptr(grad_x), _ptr(x), _ptr(z), _ptr(lam), lam.numel(), int(iters),
+            _ptr(v), _ptr(gl)))
+        return v, gl
+
+    def profile(self, enable: bool = True) -> None:
+        _lib.check("sense_plan_profile", self._lib.sense_plan_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(ms in timed fused-normal launches, their count, kernels launched) since the last read."""
+        ms, n, k = C.c_double(), C.c_int(), C.c_longlong()
+        _lib.check("sense_plan_profile_read", self._lib.sense_plan_profile_read(
+            self._h, C.byref(ms), C.byref(n), C.byref(k)))
+        return ms.value, n.value, k.value
+
+    def status(self) -> int:
+        v = C.c_int()
+        _lib.check("sense_get_status", self._lib.sense_get_status(self._h, C.byref(v)))
+        return v.value

@@ -1,0 +1,258 @@
+"""GPU parity of the SENSE operators and the CG solve against the FP64 oracle.
+
+Inputs are seeded synthetic data (synth); the GPU receives complex64 values
+and the oracle the same values up-cast to complex128.  Tolerances (relative
+L2, element by element over the whole output): one operator application
+<= 1e-5, a 10-iteration CG solve <= 1e-4, the CG backward <= 1e-4 and its
+lambda gradient <= 1e-4 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cg as ocg
+from oracle import sense as osense
+
+pytestmark = pytest.mark.gpu
+
+TOL_OP = 1e-5
+TOL_CG = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def c64(a):
+    return np.ascontiguousarray(np.asarray(a).astype(np.complex64))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def make_problem(B, Cc, H, W, R=4.0, n_centre=8, density="uniform", seed=0, lines=True):
+    rng = np.random.default_rng(seed)
+    maps = c64(np.stack([synth.coil_maps(Cc, H, W, rng) for _ in range(B)]))
+    if lines:
+        mask = synth.line_mask(W, R, n_centre, density, rng)
+    else:
+        mask = (rng.uniform(size=(H, W)) < 1.0 / R).astype(np.float32)
+        mask[H // 2 - 2:H // 2 + 2, W // 2 - 2:W // 2 + 2] = 1.0
+    x = c64(synth.randn_complex((B, H, W), seed + 100))
+    return maps, mask, x
+
+
+def plan_for(maps, mask):
+    from paper_2202_14005_b300.sense import SensePlan
+    return SensePlan(dev(maps), dev(mask))
+
+
+# shapes of the workloads (full or reduced batch) plus ragged / odd-coil cases
+NORMAL_CASES = [
+    (1, 8, 64, 64, 4.0, 16),       # 64x64, 8 coils
+    (2, 12, 256, 232, 6.0, 24),    # 256x232, 12 coils
+    (1, 15, 320, 368, 4.0, 24),    # 320x368, 15 coils
+    (3, 5, 10, 232, 6.0, 24),      # ragged row tiles, coils not a multiple of 4
+    (2, 3, 6, 64, 2.0, 4),
+    (1, 7, 12, 368, 4.0, 24),
+    (2, 4, 16, 256, 4.0, 8),       # W = 16 * 16
+]
+
+
+@pytest.mark.parametrize("case", NORMAL_CASES)
+def test_normal_lines_parity(case):
+    B, Cc, H, W, R, nc = case
+    maps, mask, x = make_problem(B, Cc, H, W, R, nc, seed=B * 7 + W)
+    plan = plan_for(maps, mask)
+    lam = 0.05
+    out = plan.normal(dev(x), lam)
+    ref = osense.normal(x, maps, mask, lam)
+    assert rel(host(out), ref) <= TOL_OP
+
+
+def test_normal_uses_fused_line_kernel_for_workload_shapes():
+    from paper_2202_14005_b300 import _lib
+    import ctypes as C
+    # the fused kernel needs no workspace; the generic path does
+    for (B, Cc, H, W) in [(1, 8, 64, 64), (1, 12, 256, 232), (1, 15, 320, 368)]:
+        maps, mask, x = make_problem(B, Cc, H, W, 4.0, 8)
+        L = _lib.lib()
+        h = C.c_void_p()
+        m, k = dev(maps), dev(mask)
+        _lib.check("create", L.sense_plan_create(C.byref(h), B, Cc, H, W, C.c_void_p(m.data_ptr()),
+                                                 C.c_void_p(k.data_ptr()), 1, None))
+        xd = dev(x)
+        o = torch.empty_like(xd)
+        rc = L.sense_normal(h, C.c_void_p(xd.data_ptr()), C.c_void_p(o.data_ptr()), C.c_float(0.1))
+        torch.cuda.synchronize()
+        L.sense_plan_destroy(h)
+        assert rc == 0
+        assert rel(o.cpu().numpy(), osense.normal(x, maps, mask, 0.1)) <= TOL_OP
+
+
+def test_normal_full_workload_256x232_b16():
+    cfg = synth.CONFIGS[2]
+    d = synth.make_slices(cfg)
+    maps, mask = c64(d["maps"]), d["mask"]
+    x = c64(d["x_gt"])
+    plan = plan_for(maps, mask)
+    out = plan.normal(dev(x), cfg.lam)
+    assert rel(host(out), osense.normal(x, maps, mask, cfg.lam)) <= TOL_OP
+
+
+@pytest.mark.parametrize("case", [(2, 3, 12, 20), (1, 4, 16, 96), (2, 2, 8, 232)])
+def test_normal_generic_paths(case):
+    """Widths without a fused kernel (20, 96) and a dense line mask go through
+    the shared-memory row/column path."""
+    B, Cc, H, W = case
+    maps, mask, x = make_problem(B, Cc, H, W, 1.2, 4, seed=3)
+    plan = plan_for(maps, mask)
+    out = plan.normal(dev(x), 0.2)
+    assert rel(host(out), osense.normal(x, maps, mask, 0.2)) <= TOL_OP
+
+
+@pytest.mark.parametrize("case", [(1, 4, 16, 20), (2, 3, 64, 64), (1, 5, 24, 232)])
+def test_normal_2d_mask(case):
+    B, Cc, H, W = case
+    maps, mask, x = make_problem(B, Cc, H, W, 3.0, 4, seed=5, lines=False)
+    plan = plan_for(maps, mask)
+    out = plan.normal(dev(x), 0.01)
+    assert rel(host(out), osense.normal(x, maps, mask, 0.01)) <= TOL_OP
+
+
+FA_CASES = [(1, 8, 64, 64, True), (2, 12, 256, 232, True), (1, 15, 320, 368, True),
+            (2, 3, 24, 20, False), (1, 4, 64, 232, False)]
+
+
+@pytest.mark.parametrize("case", FA_CASES)
+def test_forward_adjoint_parity(case):
+    B, Cc, H, W, lines = case
+    maps, mask, x = make_problem(B, Cc, H, W, 4.0, 8, seed=11, lines=lines)
+    plan = plan_for(maps, mask)
+    y = plan.forward(dev(x))
+    yref = osense.forward(x, maps, mask)
+    assert rel(host(y), yref) <= TOL_OP
+    yin = c64(synth.randn_complex((B, Cc, H, W), 12)) * (mask if lines else mask[None, None])
+    yin = c64(yin)
+    xa = plan.adjoint(dev(yin))
+    assert rel(host(xa), osense.adjoint(yin, maps, mask)) <= TOL_OP
+
+
+def _cg_inputs(cfg_index, B=None):
+    cfg = synth.CONFIGS[cfg_index]
+    d = synth.make_slices(cfg, None if B is None else range(B))
+    maps, mask = c64(d["maps"]), d["mask"]
+    y = osense.forward(d["x_gt"], maps, mask) + mask * d["noise"]
+    rhs = c64(osense.adjoint(c64(y), maps, mask))
+    return cfg, maps, mask, rhs, d["x_gt"]
+
+
+@pytest.mark.parametrize("cfg_index,B", [(1, None), (2, 3)])
+def test_cg_solve_parity(cfg_index, B):
+    cfg, maps, mask, rhs, _ = _cg_inputs(cfg_index, B)
+    Bn = rhs.shape[0]
+    plan = plan_for(maps, mask)
+    lam = torch.tensor([cfg.lam], dtype=torch.float64, device="cuda")
+    hist = torch.zeros((cfg.cg_iters + 1, Bn), dtype=torch.float64, device="cuda")
+    x = plan.cg_solve(dev(rhs), lam, cfg.cg_iters, x0=dev(rhs), rr_hist=hist)
+    xref, rr = ocg.cg_solve(maps, mask, cfg.lam, rhs, rhs, cfg.cg_iters)
+    assert rel(host(x), xref) <= TOL_CG
+    np.testing.assert_allclose(hist.cpu().numpy(), rr, rtol=1e-3, atol=1e-12 * rr[0].max())
+    assert plan.status() == 0
+
+
+def test_cg_solve_full_workload_256x232_b16():
+    cfg, maps, mask, rhs, gt = _cg_inputs(2)
+    plan = plan_for(maps, mask)
+    lam = torch.tensor([cfg.lam], dtype=torch.float64, device="cuda")
+    x = plan.cg_solve(dev(rhs), lam, cfg.cg_iters, x0=dev(rhs))
+    xref, _ = ocg.cg_solve(maps, mask, cfg.lam, rhs, rhs, cfg.cg_iters)
+    assert rel(host(x), xref) <= TOL_CG
+
+
+def test_cg_per_slice_lambda_zero_start_and_2d_mask():
+    maps, mask, _ = make_problem(3, 4, 16, 20, 3.0, 4, seed=21, lines=False)
+    rhs = c64(synth.randn_complex((3, 16, 20), 22))
+    lamv = np.array([0.01, 0.1, 1.0])
+    plan = plan_for(maps, mask)
+    x = plan.cg_solve(dev(rhs), torch.tensor(lamv, device="cuda"), 10)
+    xref, _ = ocg.cg_solve(maps, mask, lamv, rhs, None, 10)
+    assert rel(host(x), xref) <= TOL_CG
+
+
+@pytest.mark.parametrize("cfg_index,B", [(1, None), (3, 2)])
+def test_cg_backward_parity(cfg_index, B):
+    cfg, maps, mask, rhs, gt = _cg_inputs(cfg_index, B)
+    Bn = rhs.shape[0]
+    z = c64(synth.randn_complex(rhs.shape, 31) * 0.1)
+    g = c64(synth.randn_complex(rhs.shape, 32) * 0.01)
+    xfw, _ = ocg.cg_solve(maps, mask, cfg.lam, rhs + cfg.lam * z, None, cfg.cg_iters)
+    x = c64(xfw)
+    plan = plan_for(maps, mask)
+    lam = torch.tensor([cfg.lam], dtype=torch.float64, device="cuda")
+    v, gl = plan.cg_solve_backward(dev(g), dev(x), dev(z), lam, cfg.cg_iters)
+    vref, glref = ocg.cg_solve_backward(maps, mask, cfg.lam, g, x, z, cfg.cg_iters)
+    assert rel(host(v), vref) <= TOL_CG
+    assert abs(gl.cpu().item() - glref.sum()) <= TOL_CG * abs(glref).sum()
+    # per-slice lambda gradient
+    lamB = torch.full((Bn,), cfg.lam, dtype=torch.float64, device="cuda")
+    _, glB = plan.cg_solve_backward(dev(g), dev(x), dev(z), lamB, cfg.cg_iters)
+    np.testing.assert_allclose(glB.cpu().numpy(), glref, rtol=TOL_CG, atol=TOL_CG * abs(glref).max())
+
+
+def test_cg_zero_rhs_is_frozen_and_deterministic():
+    maps, mask, _ = make_problem(2, 4, 16, 64, 4.0, 8, seed=41)
+    rhs = c64(synth.randn_complex((2, 16, 64), 42))
+    rhs[1] = 0
+    plan = plan_for(maps, mask)
+    lam = torch.tensor([0.05], dtype=torch.float64, device="cuda")
+    x1 = plan.cg_solve(dev(rhs), lam, 10)
+    x2 = plan.cg_solve(dev(rhs), lam, 10)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)  # bitwise reproducible
+    assert torch.count_nonzero(x1[1]).item() == 0
+    assert plan.status() == 0
+
+
+def test_cg_breakdown_and_nonfinite_status():
+    maps, mask, _ = make_problem(1, 4, 16, 64, 4.0, 8, seed=51)
+    rhs = c64(synth.randn_complex((1, 16, 64), 52))
+    plan = plan_for(maps, mask)
+    x = plan.cg_solve(dev(rhs), torch.tensor([-2.0], dtype=torch.float64, device="cuda"), 3)
+    st = plan.status()
+    assert st & 1
+    assert torch.isfinite(torch.view_as_real(x)).all()
+    bad = rhs.copy()
+    bad[0, 3, 5] = np.nan
+    plan.cg_solve(dev(bad), torch.tensor([0.05], dtype=torch.float64, device="cuda"), 2)
+    assert plan.status() & 2
+    assert plan.status() == 0  # cleared by the read
+
+
+def test_workspace_required_errors():
+    from paper_2202_14005_b300 import _lib
+    import ctypes as C
+    maps, mask, x = make_problem(1, 2, 8, 20, 2.0, 2, seed=61)
+    L = _lib.lib()
+    h = C.c_void_p()
+    m, k = dev(maps), dev(mask)
+    assert L.sense_plan_create(C.byref(h), 1, 2, 8, 20, C.c_void_p(m.data_ptr()),
+                               C.c_void_p(k.data_ptr()), 1, None) == 0
+    xd = dev(x)
+    o = torch.empty_like(xd)
+    lam = torch.tensor([0.1], dtype=torch.float64, device="cuda")
+    assert L.sense_normal(h, C.c_void_p(xd.data_ptr()), C.c_void_p(o.data_ptr()), C.c_float(0.1)) == -6
+    assert L.cg_dc_solve(h, C.c_void_p(xd.data_ptr()), None, C.c_void_p(o.data_ptr()),
+                         C.c_void_p(lam.data_ptr()), 1, 2, None) == -6
+    assert L.sense_normal(h, C.c_void_p(xd.data_ptr()), C.c_void_p(o.data_ptr()), C.c_float(-1.0)) == -3
+    assert L.sense_normal(h, C.c_void_p(xd.data_ptr()), C.c_void_p(xd.data_ptr()), C.c_float(0.1)) == -2
+    L.sense_plan_destroy(h)
