@@ -49,6 +49,7 @@ extern "C" {
 #define SENSE_ECUDA (-5)          /* a CUDA runtime call failed */
 #define SENSE_EWORKSPACE (-6)     /* workspace missing or too small */
 #define SENSE_EINVAL_ARG (-7)     /* other invalid argument (iteration count, flags) */
+#define SENSE_ETOO_LARGE (-8)     /* problem larger than the fixed scratch of sense_dot_re_noalloc */
 
 /* Device status bits (sense_get_status). */
 #define SENSE_STATUS_CG_BREAKDOWN 1 /* Re<p, S p> <= 0 on a slice with nonzero residual */
@@ -128,6 +129,35 @@ int sense_plan_profile_read(sense_plan plan, double* normal_ms, int* normal_laun
 /* Synchronises the plan's stream, returns the OR of device status bits set
  * since the last call, and clears them. */
 int sense_get_status(sense_plan plan, int* device_status);
+
+/* Allocation-free variant of the inner product behind the lambda gradient of
+ * cg_dc_solve_backward.  The paper has no counterpart; it exists for callers
+ * that must not allocate GPU memory once they are running — for example a
+ * reconstruction service that reserves all device memory at start-up and
+ * may not call cudaMalloc while data streams in (an allocation can stall the
+ * device and every other stream on it), or a host program whose own memory
+ * manager owns the device heap.  It needs no plan and no workspace:
+ *
+ *   out[b] = sum over slice b of Re<a, b_ - c>   (out_count = B), or the sum
+ *            over all slices in slice order      (out_count = 1)
+ *
+ * a, b_, c: device complex64 [B][H][W], 16-byte aligned; b_ or c may be NULL
+ * (read as zero).  W must be even.  out: device float64 [out_count].
+ * stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ *
+ * Scratch: a fixed array of SENSE_NOALLOC_SCRATCH_BYTES in the library's own
+ * device memory (every GPU that loads the library holds one copy until the
+ * process exits).  It takes B * H <= SENSE_NOALLOC_MAX_ROWS; larger problems
+ * get SENSE_ETOO_LARGE before anything runs.  The first call on each device
+ * looks up the array's device address (with that device current), so make
+ * that first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * give wrong results — serialise them.  Results equal those of the
+ * workspace path bit for bit (same order of summation). */
+#define SENSE_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define SENSE_NOALLOC_MAX_ROWS ((SENSE_NOALLOC_SCRATCH_BYTES - 256u) / 8u)
+int sense_dot_re_noalloc(int B, int H, int W, const void* a, const void* b_, const void* c,
+                         double* out, int out_count, void* stream);
 
 /* Static description of an error code (never NULL). */
 const char* sense_strerror(int code);

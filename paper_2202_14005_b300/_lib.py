@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libsense.so")
 SENSE_OK = 0
 ERRORS = {
     -1: "EINVAL_SHAPE", -2: "EINVAL_PTR", -3: "EINVAL_LAMBDA", -4: "EUNSUPPORTED",
-    -5: "ECUDA", -6: "EWORKSPACE", -7: "EINVAL_ARG",
+    -5: "ECUDA", -6: "EWORKSPACE", -7: "EINVAL_ARG", -8: "ETOO_LARGE",
 }
 STATUS_CG_BREAKDOWN = 1
 STATUS_NONFINITE = 2
@@ -41,6 +41,7 @@ SIGNATURES = {
     "sense_plan_profile": (_i, [_vp, _i]),
     "sense_plan_profile_read": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i),
                                      C.POINTER(C.c_longlong)]),
+    "sense_dot_re_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _dp, _i, _vp]),
     "sense_strerror": (C.c_char_p, [_i]),
 }
 

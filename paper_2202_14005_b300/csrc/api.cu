@@ -50,6 +50,7 @@ const char* sense_strerror(int code) {
     case SENSE_ECUDA: return "CUDA runtime error";
     case SENSE_EWORKSPACE: return "workspace missing or too small";
     case SENSE_EINVAL_ARG: return "invalid argument";
+    case SENSE_ETOO_LARGE: return "problem exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown error code";
   }
 }

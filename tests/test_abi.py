@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_strerror_covers_codes(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         s = lib.sense_strerror(code).decode()
         assert s and s != "unknown error code"
     assert lib.sense_strerror(-99).decode() == "unknown error code"
