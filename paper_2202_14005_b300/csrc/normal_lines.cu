@@ -113,7 +113,7 @@ __device__ void last_block(const NLArgs& a) {
 }
 
 template <int Q, int P, int JMAX, int MODE>
-__global__ void __launch_bounds__(512) k_normal_lines(const NLArgs a) {
+__global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
   constexpr int GB = 32 / Q;          // coils per warp in phase B
   constexpr int GA = 32 / P;          // coils per pass in phases A/C
   constexpr int HP = (P - 1) / 2;     // conjugate pairs t <-> P - t, t = 1..HP
@@ -183,9 +183,6 @@ __global__ void __launch_bounds__(512) k_normal_lines(const NLArgs a) {
       const float2* xrow = s_x + wrow * W;
       const float2* map0 = a.maps + ((size_t)b * a.C * a.H + h) * W;
       const size_t cstride = (size_t)a.H * W;
-      float2 acc[Q];
-#pragma unroll
-      for (int n1 = 0; n1 < Q; ++n1) acc[n1] = make_float2(0.f, 0.f);
 
       // ---- phase A: expand, Q-point DFT, twiddle
 #pragma unroll
@@ -212,21 +209,16 @@ __global__ void __launch_bounds__(512) k_normal_lines(const NLArgs a) {
       }
       __syncwarp();
 
-      // ---- phase B: pruned P-point DFT at the sampled frequencies and back
+      // ---- phase B: pruned P-point DFT at the sampled frequencies and back.
+      // The conjugate pairs (t, P - t) are streamed from shared memory so that
+      // only the J outputs stay in registers.
       {
         const int gi = lane / Q, k1 = lane - gi * Q;
         float2* col = ybuf + gi * W + k1 * P;
         const float4* crow = s_coef + k1 * a.kstride;
         const float* wrow_ = s_wt + k1 * J;
         const float* srow_ = s_sgn + k1 * J;
-        float2 Sd[HP + 1], Dd[HP + 1];
         const float2 Y0 = col[0];
-#pragma unroll
-        for (int t = 1; t <= HP; ++t) {
-          const float2 u = col[t], w = col[P - t];
-          Sd[t] = cadd(u, w);
-          Dd[t] = csub(u, w);
-        }
         float2 Ym = make_float2(0.f, 0.f);
         if (EVENP) Ym = col[P / 2];
         float2 X[JMAX];
@@ -242,15 +234,23 @@ __global__ void __launch_bounds__(512) k_normal_lines(const NLArgs a) {
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {
           const int t = 2 * q + 1;
+          const float2 u0 = col[t], w0 = col[P - t];
+          const float2 S0 = cadd(u0, w0), D0 = csub(u0, w0);
+          float2 S1 = make_float2(0.f, 0.f), D1 = S1;
+          if (t + 1 <= HP) {
+            const float2 u1 = col[t + 1], w1 = col[P - t - 1];
+            S1 = cadd(u1, w1);
+            D1 = csub(u1, w1);
+          }
 #pragma unroll
           for (int j = 0; j < JMAX; ++j) {
             if (j < J) {
               const float4 cs = crow[j * RQ + q];
-              X[j].x = fmaf(cs.x, Sd[t].x, fmaf(cs.y, Dd[t].y, X[j].x));
-              X[j].y = fmaf(cs.x, Sd[t].y, fmaf(-cs.y, Dd[t].x, X[j].y));
+              X[j].x = fmaf(cs.x, S0.x, fmaf(cs.y, D0.y, X[j].x));
+              X[j].y = fmaf(cs.x, S0.y, fmaf(-cs.y, D0.x, X[j].y));
               if (t + 1 <= HP) {
-                X[j].x = fmaf(cs.z, Sd[t + 1].x, fmaf(cs.w, Dd[t + 1].y, X[j].x));
-                X[j].y = fmaf(cs.z, Sd[t + 1].y, fmaf(-cs.w, Dd[t + 1].x, X[j].y));
+                X[j].x = fmaf(cs.z, S1.x, fmaf(cs.w, D1.y, X[j].x));
+                X[j].y = fmaf(cs.z, S1.y, fmaf(-cs.w, D1.x, X[j].y));
               }
             }
           }
@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(512) k_normal_lines(const NLArgs a) {
             }
           }
         }
+        __syncwarp();  // every lane has read its column before any is overwritten
         col[0] = Z0;
         if (EVENP) col[P / 2] = Zm;
 #pragma unroll
@@ -295,6 +296,9 @@ __global__ void __launch_bounds__(512) k_normal_lines(const NLArgs a) {
       __syncwarp();
 
       // ---- phase C: inverse twiddle, inverse Q-point DFT, conj-map combine
+      float2 acc[Q];
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) acc[n1] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int pass = 0; pass < NPASS; ++pass) {
         const int ga = lane / P, t = lane - ga * P;
@@ -442,9 +446,8 @@ int build_lines_tables(sense_plan pl) {
   // launch geometry: nwr warps per row (GB coils each), several rows per CTA
   const int GB = 32 / Q;
   const int nwr = (pl->C + GB - 1) / GB;
-  if (nwr > 16) return SENSE_OK;
+  if (nwr > 8) return SENSE_OK;
   int rows = std::max(1, 8 / nwr);
-  while (rows > 1 && rows * nwr > 16) --rows;
   const int nwarps = rows * nwr;
   const NLLayout Lo = nl_layout(Q, P, J, kstride, rows, nwarps, GB);
   if (Lo.total > 200 * 1024) return SENSE_OK;
@@ -472,6 +475,8 @@ int build_lines_tables(sense_plan pl) {
     NLKernel k = pick_kernel(Q, P, JMAX, mode);
     int nb = 0;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T.threads, Lo.total) != cudaSuccess)
       return SENSE_ECUDA;
     maxb = (mode == 0) ? nb : std::min(maxb, nb);
