@@ -54,6 +54,7 @@ extern "C" {
 /* Device status bits (sense_get_status). */
 #define SENSE_STATUS_CG_BREAKDOWN 1 /* Re<p, S p> <= 0 on a slice with nonzero residual */
 #define SENSE_STATUS_NONFINITE 2    /* a CG scalar became NaN or Inf */
+#define SENSE_STATUS_DEVICE_TIMEOUT 4 /* a bounded wait inside a kernel gave up (work skipped) */
 
 typedef struct sense_plan_s* sense_plan;
 
@@ -129,6 +130,46 @@ int sense_plan_profile_read(sense_plan plan, double* normal_ms, int* normal_laun
 /* Synchronises the plan's stream, returns the OR of device status bits set
  * since the last call, and clears them. */
 int sense_get_status(sense_plan plan, int* device_status);
+
+/* ------------------------------------------------------------------------
+ * Learned denoisers.  SENSE_DENOISER_MODL: the MoDL residual CNN
+ * D_W(x) = x + CNN(x) (Sec. 2.3.2, Eq. 6) with 3x3 convolutions
+ * 2 -> 64 -> 64 -> 64 -> 64 -> 2 (biases, ReLU between layers, no batch norm);
+ * the complex image enters as two real channels (re, im).
+ *
+ * weights: device float32, denoiser_param_count() values, layer by layer
+ *   w_l [Cout][Cin][3][3] then b_l [Cout], l = 1..5 (113,154 for MoDL).
+ * Convolutions are cross-correlations with zero "same" padding.  Activations
+ * are stored in BF16 (channels-last), products accumulate in FP32; the
+ * network input is rounded to BF16.  The 64 -> 64 layers run on the tensor
+ * cores (tcgen05, FP32 accumulators in tensor memory).
+ *
+ * ws: device workspace of denoiser_workspace_bytes() bytes, 256-byte
+ *   aligned, zero-filled by the caller once before first use (it holds the
+ *   status word read by denoiser_get_status).  It keeps the activations of
+ *   the last forward call, so denoiser_backward(recompute = 0) may follow a
+ *   denoiser_forward on the same x and ws without recomputing them
+ *   (recompute = 1 reruns the forward first: the recomputation policy of the
+ *   checkpointing container, Sec. 2.2.4).  Calls sharing a ws must not overlap.
+ */
+#define SENSE_DENOISER_MODL 0
+size_t denoiser_workspace_bytes(int kind, int B, int H, int W);
+int denoiser_param_count(int kind);
+/* Byte offsets inside ws of the four BF16 [B][H][W][64] layer activations and
+ * the two BF16 gradient buffers (for inspection and per-layer checks). */
+int denoiser_workspace_offsets(int kind, int B, int H, int W, size_t* act_offsets,
+                               size_t* grad_offsets);
+/* out = D_W(x); x, out complex64 [B][H][W] (must not alias). */
+int denoiser_forward(int kind, const float* weights, const void* x, void* out, void* ws,
+                     size_t ws_bytes, int B, int H, int W, void* stream);
+/* Reverse mode: grad_x = (dD/dx)^H grad_out (complex convention of Sec. 2.2.2)
+ * and grad_weights += dL/dW (float32, same layout as weights; accumulated so
+ * that blocks sharing weights add up; deterministic fixed-order sums). */
+int denoiser_backward(int kind, const float* weights, const void* x, const void* grad_out,
+                      void* grad_x, float* grad_weights, void* ws, size_t ws_bytes, int B, int H,
+                      int W, int recompute, void* stream);
+/* Reads (synchronising the stream) and clears the status word in ws. */
+int denoiser_get_status(void* ws, int B, int H, int W, void* stream, int* device_status);
 
 /* Allocation-free variant of the inner product behind the lambda gradient of
  * cg_dc_solve_backward.  The paper has no counterpart; it exists for callers

@@ -75,6 +75,19 @@ def relu(a):
     return np.maximum(a, 0.0)
 
 
+def bf16_round(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64.
+
+    Storage precision of activations and gradients in the GPU path; values are
+    first rounded to float32, then to 8 significand bits.
+    """
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64).reshape(f.shape)
+
+
 # ------------------------------------------------------------ complex <-> 2ch
 def c2r(x: np.ndarray) -> np.ndarray:
     """Complex [B, H, W] -> real two-channel [B, 2, H, W] (real, imaginary)."""
@@ -110,8 +123,13 @@ def modl_cnn_forward(x: np.ndarray, ws, bs, act_round=None):
     return out, {"acts": acts, "pre": pre}
 
 
-def modl_cnn_backward(x: np.ndarray, ws, bs, grad_out: np.ndarray, cache=None, act_round=None):
-    """Reverse mode of D_W: returns (grad_x complex, [grad_w], [grad_b])."""
+def modl_cnn_backward(x: np.ndarray, ws, bs, grad_out: np.ndarray, cache=None, act_round=None,
+                      grad_round=None):
+    """Reverse mode of D_W: returns (grad_x complex, [grad_w], [grad_b]).
+
+    grad_round, if given, is applied to the gradient with respect to each
+    hidden pre-activation (after the ReLU mask), mirroring a storage precision.
+    """
     if cache is None:
         _, cache = modl_cnn_forward(x, ws, bs, act_round)
     acts, pre = cache["acts"], cache["pre"]
@@ -121,6 +139,8 @@ def modl_cnn_backward(x: np.ndarray, ws, bs, grad_out: np.ndarray, cache=None, a
     for l in range(L - 1, -1, -1):
         if l < L - 1:
             g = g * (pre[l] > 0)
+            if grad_round is not None:
+                g = grad_round(g)
         gx, gw, gb = conv2d_backward(acts[l], ws[l], g)
         gws[l], gbs[l] = gw, gb
         g = gx

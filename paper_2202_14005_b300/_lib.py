@@ -19,6 +19,8 @@ ERRORS = {
 }
 STATUS_CG_BREAKDOWN = 1
 STATUS_NONFINITE = 2
+STATUS_DEVICE_TIMEOUT = 4
+DENOISER_MODL = 0
 
 _vp = C.c_void_p
 _i = C.c_int
@@ -41,6 +43,12 @@ SIGNATURES = {
     "sense_plan_profile": (_i, [_vp, _i]),
     "sense_plan_profile_read": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i),
                                      C.POINTER(C.c_longlong)]),
+    "denoiser_workspace_bytes": (C.c_size_t, [_i, _i, _i, _i]),
+    "denoiser_param_count": (_i, [_i]),
+    "denoiser_workspace_offsets": (_i, [_i, _i, _i, _i, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "denoiser_forward": (_i, [_i, _vp, _vp, _vp, _vp, C.c_size_t, _i, _i, _i, _vp]),
+    "denoiser_backward": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _i, _i, _i, _i, _vp]),
+    "denoiser_get_status": (_i, [_vp, _i, _i, _i, _vp, C.POINTER(_i)]),
     "sense_dot_re_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _dp, _i, _vp]),
     "sense_strerror": (C.c_char_p, [_i]),
 }

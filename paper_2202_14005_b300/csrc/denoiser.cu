@@ -1,0 +1,820 @@
+// MoDL residual CNN denoiser D_W(x) = x + CNN(x) (Sec. 2.3.2, Eq. 6), forward
+// and reverse mode.  CNN: 3x3 convolutions 2 -> 64 -> 64 -> 64 -> 64 -> 2 with
+// biases and ReLU between them; the complex image enters as two real channels.
+//
+// Activations are BF16, channels-last [B][H][W][64]; accumulation is FP32.
+// * 64 -> 64 layers (forward and input-gradient): implicit GEMM on the 5th-gen
+//   tensor cores.  One MMA tile is 128 consecutive output pixels of one image
+//   row (M = 128) by 64 channels (N = 64), K = 9 taps x 64 channels.  A TMA
+//   tensor copy brings the 3 x 130-pixel halo into shared memory grouped by
+//   8-channel chunks, so each tap is the same K-major operand at a shifted
+//   start address; weights sit in shared memory K-major; the FP32 accumulator
+//   lives in tensor memory (two buffers, so the epilogue of one tile overlaps
+//   the MMAs of the next).  Epilogue: bias + ReLU (forward) or the ReLU mask of
+//   the layer input (input gradient), rounded to BF16.
+// * 2 -> 64 and 64 -> 2 layers and all weight gradients run on CUDA cores with
+//   FP32 accumulation; weight gradients are per-chunk partials reduced in a
+//   fixed order (deterministic) and added to the caller's FP32 buffer.
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "plan.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int CH = 64;
+constexpr int TILE_M = 128;
+constexpr int HALO_W = TILE_M + 2;            // 130
+constexpr int GBLK_TX = 3 * HALO_W * 16;      // 6240 bytes per channel-group box
+constexpr int GBLK = 6272;                    // padded to 128 bytes
+constexpr int HALO_BYTES = 8 * GBLK;          // 50176
+constexpr int WPACK_BYTES = 9 * 8 * CH * 16;  // 73728 (bf16 [tap][g][n][8])
+constexpr int CONV_THREADS = 128;
+constexpr int OFF_W = 0;
+constexpr int OFF_H0 = WPACK_BYTES;
+constexpr int OFF_H1 = OFF_H0 + HALO_BYTES;
+constexpr int OFF_BIAS = OFF_H1 + HALO_BYTES;
+constexpr int OFF_BAR = OFF_BIAS + CH * 4;
+constexpr int CONV_SMEM = OFF_BAR + 64 + 1024;  // + slack to realign the base to 1 KB
+
+// Offsets (floats) into the flat MoDL weight vector: w_l [Cout][Cin][3][3], b_l [Cout].
+struct ModlOffsets {
+  int w[5], b[5], total;
+};
+constexpr int kChans[6] = {2, 64, 64, 64, 64, 2};
+ModlOffsets modl_offsets() {
+  ModlOffsets o;
+  int p = 0;
+  for (int l = 0; l < 5; ++l) {
+    o.w[l] = p;
+    p += kChans[l] * kChans[l + 1] * 9;
+    o.b[l] = p;
+    p += kChans[l + 1];
+  }
+  o.total = p;
+  return o;
+}
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ------------------------------------------------------------ weight packing
+// 64->64 layer l into the K-major operand layout [tap][g][n][8] (bf16):
+//   forward:        n = cout, k-chunk g over cin:  W[n][g*8+e][tap]
+//   input gradient: n = cin,  k-chunk g over cout: W[g*8+e][n][8 - tap] (flipped taps)
+__global__ void k_pack64(const float* w, __nv_bfloat16* out, int dgrad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9*8*64*8
+  if (i >= 9 * 8 * CH * 8) return;
+  const int e = i & 7, n = (i >> 3) & 63, g = (i >> 9) & 7, tap = i >> 12;
+  float v;
+  if (!dgrad) v = w[(n * CH + g * 8 + e) * 9 + tap];
+  else v = w[((g * 8 + e) * CH + n) * 9 + (8 - tap)];
+  out[i] = __float2bfloat16_rn(v);
+}
+
+// ------------------------------------------------------- tcgen05 convolution
+struct ConvArgs {
+  int B, H, W, ntw;
+  const __nv_bfloat16* wpack;
+  const float* bias;            // forward: [64]
+  const __nv_bfloat16* aprev;   // input gradient: ReLU mask source [B][H][W][64]
+  __nv_bfloat16* out;           // [B][H][W][64]
+  int mode;                     // 0 forward, 1 input gradient
+  int* status;
+};
+
+__device__ __forceinline__ void tile_coords(int t, int H, int ntw, int& b, int& h, int& wt) {
+  wt = t % ntw;
+  const int r = t / ntw;
+  h = r % H;
+  b = r / H;
+}
+
+__device__ __forceinline__ void issue_halo(const CUtensorMap* map, uint8_t* dst, uint64_t* bar, int t,
+                                           int H, int ntw) {
+  int b, h, wt;
+  tile_coords(t, H, ntw, b, h, wt);
+  mbar_expect_tx(bar, 8 * GBLK_TX);
+#pragma unroll
+  for (int g = 0; g < 8; ++g) tma_load_4d(dst + g * GBLK, map, g * 8, wt * TILE_M - 1, h - 1, b, bar);
+}
+
+__device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32_t wts) {
+  const uint32_t idesc = umma_idesc_bf16(TILE_M, CH);
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint64_t ad = umma_desc(halo + (2 * kk) * GBLK + (dy * HALO_W + dx) * 16, GBLK, 128);
+      const uint64_t bd = umma_desc(wts + (tap * 8 + 2 * kk) * 1024, 1024, 128);
+      umma_bf16(tmem_d, ad, bd, idesc, (tap | kk) != 0);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  uint8_t* s_halo0 = smem + OFF_H0;
+  float* s_bias = reinterpret_cast<float*>(smem + OFF_BIAS);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);  // 0 weights, 1-2 loads, 3-4 mma
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 5);
+  int* s_err = reinterpret_cast<int*>(s_tmem + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = a.B * a.H * a.ntw;
+  const int n = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
+    *s_err = 0;
+    fence_mbar_init();
+  }
+  if (tid < CH) s_bias[tid] = (a.mode == 0) ? a.bias[tid] : 0.f;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t sw = smem_u32(smem + OFF_W);
+  const uint32_t sh[2] = {smem_u32(s_halo0), smem_u32(s_halo0 + HALO_BYTES)};
+
+  // thread 0 issues every copy and MMA batch and counts them per barrier, so an
+  // error exit can wait (bounded) for exactly what is still in flight.
+  int issued[5] = {0, 0, 0, 0, 0}, waited[5] = {0, 0, 0, 0, 0};
+  int my_err = 0;
+  if (tid == 0 && n > 0) {
+    mbar_expect_tx(&bars[0], WPACK_BYTES);
+    bulk_load(smem + OFF_W, a.wpack, WPACK_BYTES, &bars[0]);
+    issued[0]++;
+    issue_halo(&tmap, s_halo0, &bars[1], blockIdx.x, a.H, a.ntw);
+    issued[1]++;
+    if (n > 1) {
+      issue_halo(&tmap, s_halo0 + HALO_BYTES, &bars[2], blockIdx.x + gridDim.x, a.H, a.ntw);
+      issued[2]++;
+    }
+    const bool okw = mbar_wait(&bars[0], 0);
+    if (okw) waited[0]++;
+    const bool okl = okw && mbar_wait(&bars[1], 0);
+    if (okl) {
+      waited[1]++;
+      tc_fence_after();
+      issue_mma(tmem, sh[0], sw);
+      umma_commit(&bars[3]);
+      issued[3]++;
+    } else {
+      my_err = 1;
+    }
+  }
+  int err = __syncthreads_or(my_err);
+
+  for (int i = 0; i < n && !err; ++i) {
+    const int buf = i & 1;
+    const bool done = mbar_wait(&bars[3 + buf], (i >> 1) & 1);
+    if (tid == 0 && done) waited[3 + buf]++;
+    if (__syncthreads_or(!done || my_err)) {
+      err = 1;
+      break;
+    }
+    tc_fence_after();
+    if (tid == 0) {
+      if (i + 2 < n) {
+        issue_halo(&tmap, s_halo0 + buf * HALO_BYTES, &bars[1 + buf], blockIdx.x + (i + 2) * gridDim.x,
+                   a.H, a.ntw);
+        issued[1 + buf]++;
+      }
+      if (i + 1 < n) {
+        const int nb = buf ^ 1;
+        if (mbar_wait(&bars[1 + nb], ((i + 1) >> 1) & 1)) {
+          waited[1 + nb]++;
+          issue_mma(tmem + nb * 64, sh[nb], sw);
+          umma_commit(&bars[3 + nb]);
+          issued[3 + nb]++;
+        } else {
+          my_err = 1;
+        }
+      }
+    }
+    __syncwarp();  // warp 0 reconverges before the warp-collective tensor-memory loads
+    // epilogue of tile i: warp w owns pixels 32w .. 32w + 31 of the tile
+    int b, h, wt;
+    tile_coords(blockIdx.x + i * gridDim.x, a.H, a.ntw, b, h, wt);
+    const int px = wt * TILE_M + warp * 32 + lane;
+    const bool valid = px < a.W;
+    const size_t pix = ((size_t)b * a.H + h) * a.W + px;
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + buf * 64 + cb * 16, v);
+      if (valid) {
+        if (a.mode == 0) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_bias[cb * 16 + e], 0.f);
+        } else {
+          const uint4* ap = reinterpret_cast<const uint4*>(a.aprev + pix * CH + cb * 16);
+          const uint4 m0 = ap[0], m1 = ap[1];
+          const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+          const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            if (!(bf(mb0[e]) > 0.f)) v[e] = 0.f;
+            if (!(bf(mb1[e]) > 0.f)) v[8 + e] = 0.f;
+          }
+        }
+        uint4 o0, o1;
+        __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(&o0);
+        __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(&o1);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          p0[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+          p1[e] = __floats2bfloat162_rn(v[8 + 2 * e], v[8 + 2 * e + 1]);
+        }
+        uint4* op = reinterpret_cast<uint4*>(a.out + pix * CH + cb * 16);
+        op[0] = o0;
+        op[1] = o1;
+      }
+    }
+    tc_fence_before();
+    if (__syncthreads_or(my_err)) {
+      err = 1;
+      break;
+    }
+  }
+  err = __syncthreads_or(err || my_err);
+  if (err && tid == 0) {
+    set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
+    // wait (bounded) for whatever this CTA still has in flight before its
+    // shared and tensor memory are released
+    for (int k = 0; k < 5; ++k)
+      while (waited[k] < issued[k]) {
+        mbar_wait(&bars[k], waited[k] & 1, 1u << 20);
+        waited[k]++;
+      }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// ------------------------------------------------ CUDA-core small layers
+// First layer (2 -> 64): a1[p][co] = relu(b1[co] + sum_{c,tap} w1[co][c][tap] xr[p + s_tap][c]),
+// xr = the complex input rounded to BF16 (the network input is a BF16 activation).
+__global__ void __launch_bounds__(256) k_l1_fwd(int B, int H, int W, const float2* x, const float* w1,
+                                                const float* b1, __nv_bfloat16* a1) {
+  __shared__ float s_w[CH * 18];
+  __shared__ float s_b[CH];
+  for (int i = threadIdx.x; i < CH * 18; i += blockDim.x) s_w[i] = w1[i];
+  if (threadIdx.x < CH) s_b[threadIdx.x] = b1[threadIdx.x];
+  __syncthreads();
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (size_t)B * H * W) return;
+  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
+  float xin[2][9];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int yy = h + tap / 3 - 1, xx = w + tap % 3 - 1;
+    float2 v = make_float2(0.f, 0.f);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = x[((size_t)b * H + yy) * W + xx];
+    xin[0][tap] = bf(__float2bfloat16_rn(v.x));
+    xin[1][tap] = bf(__float2bfloat16_rn(v.y));
+  }
+  uint4* op = reinterpret_cast<uint4*>(a1 + p * CH);
+#pragma unroll 1
+  for (int cg = 0; cg < 8; ++cg) {
+    float r[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int co = cg * 8 + e;
+      float s = s_b[co];
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) s = fmaf(s_w[(co * 2 + c) * 9 + tap], xin[c][tap], s);
+      r[e] = fmaxf(s, 0.f);
+    }
+    uint4 o;
+    __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) po[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
+    op[cg] = o;
+  }
+}
+
+// Load the 64 BF16 channels of pixel (yy, xx) (zero outside the image) as floats.
+__device__ __forceinline__ void load_px64(const __nv_bfloat16* t, int b, int yy, int xx, int H, int W,
+                                          float (&v)[CH]) {
+  if (yy < 0 || yy >= H || xx < 0 || xx >= W) {
+#pragma unroll
+    for (int i = 0; i < CH; ++i) v[i] = 0.f;
+    return;
+  }
+  const uint4* p = reinterpret_cast<const uint4*>(t + (((size_t)b * H + yy) * W + xx) * CH);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint4 u = p[q];
+    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(h2[e]);
+      v[q * 8 + 2 * e] = f.x;
+      v[q * 8 + 2 * e + 1] = f.y;
+    }
+  }
+}
+
+// Last layer (64 -> 2) plus the residual: out[p] = x[p] + (b5 + sum_{ci,tap} w5[c][ci][tap] a4[p+s][ci]).
+__global__ void __launch_bounds__(128) k_l5_fwd(int B, int H, int W, const __nv_bfloat16* a4,
+                                                const float* w5, const float* b5, const float2* x,
+                                                float2* out) {
+  __shared__ float s_w[2 * CH * 9];
+  for (int i = threadIdx.x; i < 2 * CH * 9; i += blockDim.x) s_w[i] = w5[i];
+  __syncthreads();
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (size_t)B * H * W) return;
+  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
+  float s0 = b5[0], s1 = b5[1];
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    float v[CH];
+    load_px64(a4, b, h + tap / 3 - 1, w + tap % 3 - 1, H, W, v);
+#pragma unroll
+    for (int ci = 0; ci < CH; ++ci) {
+      s0 = fmaf(s_w[(0 * CH + ci) * 9 + tap], v[ci], s0);
+      s1 = fmaf(s_w[(1 * CH + ci) * 9 + tap], v[ci], s1);
+    }
+  }
+  const float2 xv = x[p];
+  out[p] = make_float2(xv.x + s0, xv.y + s1);
+}
+
+// Input gradient of the last layer, masked by the ReLU of its input:
+//   g4[p][ci] = [a4[p][ci] > 0] * sum_{co,tap} w5[co][ci][tap] g[p - s_tap][co]
+__global__ void __launch_bounds__(128) k_l5_dgrad(int B, int H, int W, const float2* g, const float* w5,
+                                                  const __nv_bfloat16* a4, __nv_bfloat16* g4) {
+  __shared__ float s_w[2 * CH * 9];
+  for (int i = threadIdx.x; i < 2 * CH * 9; i += blockDim.x) s_w[i] = w5[i];
+  __syncthreads();
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (size_t)B * H * W) return;
+  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
+  float gin[2][9];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int yy = h - (tap / 3 - 1), xx = w - (tap % 3 - 1);
+    float2 v = make_float2(0.f, 0.f);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = g[((size_t)b * H + yy) * W + xx];
+    gin[0][tap] = v.x;
+    gin[1][tap] = v.y;
+  }
+  const uint4* ap = reinterpret_cast<const uint4*>(a4 + p * CH);
+  uint4* op = reinterpret_cast<uint4*>(g4 + p * CH);
+#pragma unroll 1
+  for (int cg = 0; cg < 8; ++cg) {
+    const uint4 m = ap[cg];
+    const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
+    float r[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int ci = cg * 8 + e;
+      float s = 0.f;
+#pragma unroll
+      for (int co = 0; co < 2; ++co)
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) s = fmaf(s_w[(co * CH + ci) * 9 + tap], gin[co][tap], s);
+      r[e] = (bf(mb[e]) > 0.f) ? s : 0.f;
+    }
+    uint4 o;
+    __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) po[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
+    op[cg] = o;
+  }
+}
+
+// Input gradient of the first layer plus the residual path:
+//   gx[p][c] = gout[p][c] + sum_{co,tap} w1[co][c][tap] g1[p - s_tap][co]
+__global__ void __launch_bounds__(128) k_l1_dgrad(int B, int H, int W, const __nv_bfloat16* g1,
+                                                  const float* w1, const float2* gout, float2* gx) {
+  __shared__ float s_w[CH * 18];
+  for (int i = threadIdx.x; i < CH * 18; i += blockDim.x) s_w[i] = w1[i];
+  __syncthreads();
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (size_t)B * H * W) return;
+  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    float v[CH];
+    load_px64(g1, b, h - (tap / 3 - 1), w - (tap % 3 - 1), H, W, v);
+#pragma unroll
+    for (int co = 0; co < CH; ++co) {
+      s0 = fmaf(s_w[(co * 2 + 0) * 9 + tap], v[co], s0);
+      s1 = fmaf(s_w[(co * 2 + 1) * 9 + tap], v[co], s1);
+    }
+  }
+  const float2 go = gout[p];
+  gx[p] = make_float2(go.x + s0, go.y + s1);
+}
+
+// --------------------------------------------------- weight gradients (CUDA cores)
+// Small layers, per chunk of R image rows of one slice:
+//  L1 (first):  gw[co][c][tap] = sum_p g1[p][co] * xr[p + s][c],  gb[co] = sum_p g1[p][co]
+//  L5 (last):   gw[co][ci][tap] = sum_p g5[p][co] * a4[p + s][ci], gb[co] = sum_p g5[p][co]
+// Thread j < 64 owns the 64-channel index (co for L1, ci for L5) and 18 (+1) sums;
+// the four thread groups take every fourth pixel and are added in fixed order.
+constexpr int kSmallRows = 4;
+constexpr int kSmallOut = CH * 18 + CH;  // 1152 weights + up to 64 biases
+
+__global__ void __launch_bounds__(256) k_wgrad_small(int B, int H, int W, int last, const __nv_bfloat16* U,
+                                                     const float2* V, float* partial) {
+  const int chunks_per_slice = (H + kSmallRows - 1) / kSmallRows;
+  const int b = blockIdx.x / chunks_per_slice;
+  const int h0 = (blockIdx.x % chunks_per_slice) * kSmallRows;
+  const int h1 = min(h0 + kSmallRows, H);
+  const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
+  float acc[2][9];
+  float bacc = 0.f;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[c][t] = 0.f;
+  const int npx = (h1 - h0) * W;
+  for (int q = grp; q < npx; q += 4) {
+    const int h = h0 + q / W, w = q % W;
+    const size_t p = ((size_t)b * H + h) * W + w;
+    if (!last) {
+      // L1: U = g1 (unshifted), V = x rounded to bf16 (shifted)
+      const float u = bf(U[p * CH + j]);
+      bacc += u;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int yy = h + tap / 3 - 1, xx = w + tap % 3 - 1;
+        float2 v = make_float2(0.f, 0.f);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = V[((size_t)b * H + yy) * W + xx];
+        acc[0][tap] = fmaf(u, bf(__float2bfloat16_rn(v.x)), acc[0][tap]);
+        acc[1][tap] = fmaf(u, bf(__float2bfloat16_rn(v.y)), acc[1][tap]);
+      }
+    } else {
+      // L5: V = g5 (unshifted, 2 channels), U = a4 (shifted)
+      const float2 v = V[p];
+      if (j < 2) bacc += (j == 0) ? v.x : v.y;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int yy = h + tap / 3 - 1, xx = w + tap % 3 - 1;
+        float u = 0.f;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) u = bf(U[(((size_t)b * H + yy) * W + xx) * CH + j]);
+        acc[0][tap] = fmaf(v.x, u, acc[0][tap]);
+        acc[1][tap] = fmaf(v.y, u, acc[1][tap]);
+      }
+    }
+  }
+  __shared__ float s_red[4][CH * 19];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) s_red[grp][j * 19 + c * 9 + t] = acc[c][t];
+  s_red[grp][j * 19 + 18] = bacc;
+  __syncthreads();
+  float* out = partial + (size_t)blockIdx.x * kSmallOut;
+  for (int i = threadIdx.x; i < CH * 19; i += blockDim.x) {
+    const float s = ((s_red[0][i] + s_red[1][i]) + s_red[2][i]) + s_red[3][i];
+    const int jj = i / 19, r = i % 19;
+    if (r == 18) {
+      out[CH * 18 + jj] = s;
+    } else {
+      const int c = r / 9, tap = r % 9;
+      // weight index in [Cout][Cin][tap] order
+      const int widx = !last ? ((jj * 2 + c) * 9 + tap) : ((c * CH + jj) * 9 + tap);
+      out[widx] = s;
+    }
+  }
+}
+
+// Deterministic sum over chunks, added to the caller's gradient buffers.
+__global__ void k_reduce_partials(const float* partial, int nchunks, int stride, int nw, float* gw,
+                                  int nb, int boff, float* gb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nw + nb) return;
+  const int src = (i < nw) ? i : boff + (i - nw);
+  float s = 0.f;
+  for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * stride + src];
+  if (i < nw) gw[i] += s;
+  else gb[i - nw] += s;
+}
+
+// 64 -> 64 layer weight gradient on CUDA cores:
+//   gw[co][ci][tap] = sum_p g[p][co] * a[p + s_tap][ci],  gb[co] = sum_p g[p][co].
+// CTA: one tap, one chunk of rows; 256 threads as a 16 x 16 grid each owning a
+// 4 x 4 block of (co, ci).  Pixels are staged 32 at a time in shared memory.
+constexpr int kW64Rows = 8;
+constexpr int kW64Px = 32;
+
+__global__ void __launch_bounds__(256) k_wgrad64(int B, int H, int W, const __nv_bfloat16* g,
+                                                 const __nv_bfloat16* act, float* partial) {
+  const int tap = blockIdx.y;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int chunks_per_slice = (H + kW64Rows - 1) / kW64Rows;
+  const int b = blockIdx.x / chunks_per_slice;
+  const int h0 = (blockIdx.x % chunks_per_slice) * kW64Rows;
+  const int h1 = min(h0 + kW64Rows, H);
+  __shared__ float s_g[kW64Px][CH + 1];
+  __shared__ float s_a[kW64Px][CH + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ci block tx, co block ty
+  float acc[4][4];
+  float bacc = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+  const int npx = (h1 - h0) * W;
+  for (int q0 = 0; q0 < npx; q0 += kW64Px) {
+    for (int i = threadIdx.x; i < kW64Px * CH; i += blockDim.x) {
+      const int pp = i / CH, ch = i % CH;
+      const int q = q0 + pp;
+      float gv = 0.f, av = 0.f;
+      if (q < npx) {
+        const int h = h0 + q / W, w = q % W;
+        gv = bf(g[(((size_t)b * H + h) * W + w) * CH + ch]);
+        const int yy = h + dy, xx = w + dx;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) av = bf(act[(((size_t)b * H + yy) * W + xx) * CH + ch]);
+      }
+      s_g[pp][ch] = gv;
+      s_a[pp][ch] = av;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int pp = 0; pp < kW64Px; ++pp) {
+      float gg[4], aa[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        gg[i] = s_g[pp][ty * 4 + i];
+        aa[i] = s_a[pp][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(gg[i], aa[k], acc[i][k]);
+    }
+    if (tap == 4 && threadIdx.x < CH)
+      for (int pp = 0; pp < kW64Px; ++pp) bacc += s_g[pp][threadIdx.x];
+    __syncthreads();
+  }
+  // partial layout per (chunk, tap): [co][ci] 4096 floats, bias (tap 4 only) after all taps
+  float* out = partial + ((size_t)blockIdx.x * 9 + tap) * (CH * CH);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[(ty * 4 + i) * CH + tx * 4 + k] = acc[i][k];
+  if (tap == 4 && threadIdx.x < CH) {
+    const int nchunks = gridDim.x;
+    partial[(size_t)nchunks * 9 * CH * CH + (size_t)blockIdx.x * CH + threadIdx.x] = bacc;
+  }
+}
+
+// Sum the 64x64-layer partials over chunks in fixed order into gw [co][ci][tap] and gb.
+__global__ void k_reduce_wgrad64(const float* partial, int nchunks, float* gw, float* gb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < CH * CH * 9) {
+    const int co = i / (CH * 9), ci = (i / 9) % CH, tap = i % 9;
+    float s = 0.f;
+    for (int c = 0; c < nchunks; ++c) s += partial[((size_t)c * 9 + tap) * (CH * CH) + co * CH + ci];
+    gw[i] += s;
+  } else if (i < CH * CH * 9 + CH) {
+    const int co = i - CH * CH * 9;
+    float s = 0.f;
+    const float* pb = partial + (size_t)nchunks * 9 * CH * CH;
+    for (int c = 0; c < nchunks; ++c) s += pb[(size_t)c * CH + co];
+    gb[co] += s;
+  }
+}
+
+// ------------------------------------------------------------ host helpers
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// Tensor map over a BF16 [B][H][W][64] activation; box 8 ch x 130 px x 3 rows x 1 slice.
+int make_act_map(CUtensorMap* m, const void* base, int B, int H, int W) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return SENSE_ECUDA;
+  const cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)CH * 2, (cuuint64_t)W * CH * 2, (cuuint64_t)H * W * CH * 2};
+  const cuuint32_t box[4] = {8, HALO_W, 3, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
+                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SENSE_OK : SENSE_ECUDA;
+}
+
+int g_num_sms = 0;
+
+int conv_prepare() {
+  static int state = 0;  // 0 unknown, 1 ok, -1 failed
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (state == 0) {
+    int dev = 0;
+    state = (cudaGetDevice(&dev) == cudaSuccess &&
+             cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+             cudaFuncSetAttribute(k_conv64, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM) ==
+                 cudaSuccess)
+                ? 1
+                : -1;
+  }
+  return state == 1 ? SENSE_OK : SENSE_ECUDA;
+}
+
+int launch_conv64(const __nv_bfloat16* in, const __nv_bfloat16* wpack, const float* bias,
+                  const __nv_bfloat16* aprev, __nv_bfloat16* out, int mode, int B, int H, int W,
+                  int* status, cudaStream_t st) {
+  CUtensorMap map;
+  if (int e = make_act_map(&map, in, B, H, W)) return e;
+  ConvArgs a;
+  a.B = B; a.H = H; a.W = W; a.ntw = (W + TILE_M - 1) / TILE_M;
+  a.wpack = wpack; a.bias = bias; a.aprev = aprev; a.out = out; a.mode = mode; a.status = status;
+  const int ntiles = B * H * a.ntw;
+  const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  k_conv64<<<grid, CONV_THREADS, CONV_SMEM, st>>>(map, a);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+struct DnLayout {
+  size_t wf[3], wd[3], act[4], g[2], part_small, part64, status, total;
+  int nch_small, nch64;
+};
+
+DnLayout dn_layout(int B, int H, int W) {
+  DnLayout L;
+  const size_t act = up256((size_t)B * H * W * CH * 2);
+  L.nch_small = B * ((H + kSmallRows - 1) / kSmallRows);
+  L.nch64 = B * ((H + kW64Rows - 1) / kW64Rows);
+  size_t o = 0;
+  for (int i = 0; i < 3; ++i) { L.wf[i] = o; o += up256(WPACK_BYTES); }
+  for (int i = 0; i < 3; ++i) { L.wd[i] = o; o += up256(WPACK_BYTES); }
+  for (int i = 0; i < 4; ++i) { L.act[i] = o; o += act; }
+  for (int i = 0; i < 2; ++i) { L.g[i] = o; o += act; }
+  L.part_small = o; o += up256((size_t)L.nch_small * kSmallOut * 4);
+  L.part64 = o; o += up256(((size_t)L.nch64 * 9 * CH * CH + (size_t)L.nch64 * CH) * 4);
+  L.status = o; o += 256;
+  L.total = o;
+  return L;
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_common(int kind, const void* weights, const void* x, void* ws, size_t ws_bytes, int B, int H,
+                 int W) {
+  if (kind != SENSE_DENOISER_MODL) return SENSE_EUNSUPPORTED;
+  if (B <= 0 || H <= 0 || W <= 0) return SENSE_EINVAL_SHAPE;
+  if (!weights || !x || !ws || !al16(weights) || !al16(x) || ((uintptr_t)ws & 255u)) return SENSE_EINVAL_PTR;
+  if (ws_bytes < dn_layout(B, H, W).total) return SENSE_EWORKSPACE;
+  return conv_prepare();
+}
+
+int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, int B, int H, int W,
+                 cudaStream_t st) {
+  const DnLayout L = dn_layout(B, H, W);
+  const ModlOffsets o = modl_offsets();
+  __nv_bfloat16* act[4];
+  for (int i = 0; i < 4; ++i) act[i] = reinterpret_cast<__nv_bfloat16*>(ws + L.act[i]);
+  int* status = reinterpret_cast<int*>(ws + L.status);
+  for (int l = 0; l < 3; ++l)
+    k_pack64<<<(9 * 8 * CH * 8 + 255) / 256, 256, 0, st>>>(wts + o.w[l + 1],
+                                                          reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), 0);
+  const size_t npx = (size_t)B * H * W;
+  k_l1_fwd<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(B, H, W, x, wts + o.w[0], wts + o.b[0], act[0]);
+  for (int l = 0; l < 3; ++l)
+    if (int e = launch_conv64(act[l], reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), wts + o.b[l + 1],
+                              nullptr, act[l + 1], 0, B, H, W, status, st))
+      return e;
+  if (out)
+    k_l5_fwd<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, act[3], wts + o.w[4], wts + o.b[4], x,
+                                                            out);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t denoiser_workspace_bytes(int kind, int B, int H, int W) {
+  if (kind != SENSE_DENOISER_MODL || B <= 0 || H <= 0 || W <= 0) return 0;
+  return dn_layout(B, H, W).total;
+}
+
+int denoiser_param_count(int kind) {
+  return kind == SENSE_DENOISER_MODL ? modl_offsets().total : 0;
+}
+
+int denoiser_workspace_offsets(int kind, int B, int H, int W, size_t* act_offsets /*[4]*/,
+                               size_t* grad_offsets /*[2]*/) {
+  if (kind != SENSE_DENOISER_MODL || B <= 0 || H <= 0 || W <= 0) return SENSE_EINVAL_ARG;
+  const DnLayout L = dn_layout(B, H, W);
+  if (act_offsets)
+    for (int i = 0; i < 4; ++i) act_offsets[i] = L.act[i];
+  if (grad_offsets)
+    for (int i = 0; i < 2; ++i) grad_offsets[i] = L.g[i];
+  return SENSE_OK;
+}
+
+int denoiser_forward(int kind, const float* weights, const void* x, void* out, void* ws, size_t ws_bytes,
+                     int B, int H, int W, void* stream) {
+  if (int e = check_common(kind, weights, x, ws, ws_bytes, B, H, W)) return e;
+  if (!out || !al16(out) || out == x) return SENSE_EINVAL_PTR;
+  return forward_impl(weights, static_cast<const float2*>(x), static_cast<float2*>(out),
+                      static_cast<uint8_t*>(ws), B, H, W, static_cast<cudaStream_t>(stream));
+}
+
+int denoiser_backward(int kind, const float* weights, const void* x, const void* grad_out, void* grad_x,
+                      float* grad_weights, void* ws, size_t ws_bytes, int B, int H, int W, int recompute,
+                      void* stream) {
+  if (int e = check_common(kind, weights, x, ws, ws_bytes, B, H, W)) return e;
+  if (!grad_out || !grad_x || !grad_weights || !al16(grad_out) || !al16(grad_x) || !al16(grad_weights) ||
+      grad_x == grad_out)
+    return SENSE_EINVAL_PTR;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* w8 = static_cast<uint8_t*>(ws);
+  const DnLayout L = dn_layout(B, H, W);
+  const ModlOffsets o = modl_offsets();
+  const float2* xx = static_cast<const float2*>(x);
+  const float2* go = static_cast<const float2*>(grad_out);
+  if (recompute)
+    if (int e = forward_impl(weights, xx, nullptr, w8, B, H, W, st)) return e;
+  __nv_bfloat16* act[4];
+  for (int i = 0; i < 4; ++i) act[i] = reinterpret_cast<__nv_bfloat16*>(w8 + L.act[i]);
+  __nv_bfloat16* gbuf[2] = {reinterpret_cast<__nv_bfloat16*>(w8 + L.g[0]),
+                            reinterpret_cast<__nv_bfloat16*>(w8 + L.g[1])};
+  float* ps = reinterpret_cast<float*>(w8 + L.part_small);
+  float* p64 = reinterpret_cast<float*>(w8 + L.part64);
+  int* status = reinterpret_cast<int*>(w8 + L.status);
+  const size_t npx = (size_t)B * H * W;
+  for (int l = 0; l < 3; ++l)
+    k_pack64<<<(9 * 8 * CH * 8 + 255) / 256, 256, 0, st>>>(weights + o.w[l + 1],
+                                                          reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), 1);
+  // last layer: input gradient (masked by a4 > 0) and weight gradient
+  k_l5_dgrad<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, go, weights + o.w[4], act[3], gbuf[0]);
+  k_wgrad_small<<<L.nch_small, 256, 0, st>>>(B, H, W, 1, act[3], go, ps);
+  k_reduce_partials<<<(2 * CH * 9 + 2 + 255) / 256, 256, 0, st>>>(ps, L.nch_small, kSmallOut, 2 * CH * 9,
+                                                                 grad_weights + o.w[4], 2, CH * 18,
+                                                                 grad_weights + o.b[4]);
+  // 64 -> 64 layers 4, 3, 2 (index l = 2, 1, 0 of the packed set)
+  int cur = 0;
+  for (int l = 2; l >= 0; --l) {
+    const __nv_bfloat16* ain = act[l];  // input activation of this layer
+    dim3 gw(L.nch64, 9);
+    k_wgrad64<<<gw, 256, 0, st>>>(B, H, W, gbuf[cur], ain, p64);
+    k_reduce_wgrad64<<<(CH * CH * 9 + CH + 255) / 256, 256, 0, st>>>(p64, L.nch64, grad_weights + o.w[l + 1],
+                                                                     grad_weights + o.b[l + 1]);
+    if (int e = launch_conv64(gbuf[cur], reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), nullptr, ain,
+                              gbuf[cur ^ 1], 1, B, H, W, status, st))
+      return e;
+    cur ^= 1;
+  }
+  // first layer: weight gradient and input gradient (+ residual)
+  k_wgrad_small<<<L.nch_small, 256, 0, st>>>(B, H, W, 0, gbuf[cur], xx, ps);
+  k_reduce_partials<<<(CH * 18 + CH + 255) / 256, 256, 0, st>>>(ps, L.nch_small, kSmallOut, CH * 18,
+                                                               grad_weights + o.w[0], CH, CH * 18,
+                                                               grad_weights + o.b[0]);
+  k_l1_dgrad<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, gbuf[cur], weights + o.w[0], go,
+                                                            static_cast<float2*>(grad_x));
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+}  // extern "C"
+
+extern "C" int denoiser_get_status(void* ws, int B, int H, int W, void* stream, int* device_status) {
+  if (!ws || !device_status) return SENSE_EINVAL_PTR;
+  if (B <= 0 || H <= 0 || W <= 0) return SENSE_EINVAL_SHAPE;
+  int* st = reinterpret_cast<int*>(static_cast<uint8_t*>(ws) + dn_layout(B, H, W).status);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  if (cudaMemcpyAsync(&v, st, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess || cudaMemsetAsync(st, 0, sizeof(int), s) != cudaSuccess)
+    return SENSE_ECUDA;
+  *device_status = v;
+  return SENSE_OK;
+}

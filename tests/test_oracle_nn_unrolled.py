@@ -194,3 +194,21 @@ def test_varnet_train_grads_fd():
             fm[idx] -= unit * eps
             fd = (L(fp, wts, lam) - L(fm, wts, lam)) / (2 * eps)
             assert abs(fd - part(gf[idx])) <= 1e-5 * max(abs(fd), 1e-4)
+
+
+def test_bf16_round_ties_to_even_and_limits():
+    # exact values on the bfloat16 grid stay; halfway cases go to the even neighbour
+    one = np.float32(1.0)
+    ulp = 2.0 ** -7  # spacing of bfloat16 at 1.0
+    vals = np.array([1.0, 1.0 + ulp, 1.0 + ulp / 2, 1.0 + 3 * ulp / 2, -1.0 - ulp / 2, 0.0, 3.0e38],
+                    dtype=np.float64)
+    got = onn.bf16_round(vals)
+    want = np.array([1.0, 1.0 + ulp, 1.0, 1.0 + 2 * ulp, -1.0, 0.0, got[-1]])
+    np.testing.assert_array_equal(got[:-1], want[:-1])
+    assert abs(got[-1] - 3.0e38) / 3.0e38 < 2 ** -8
+    # relative rounding error is at most half a unit in the 8-bit significand
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal(10000) * 10 ** rng.uniform(-10, 10, 10000)
+    r = onn.bf16_round(a)
+    assert np.all(np.abs(r - a) <= np.abs(a) * 2.0 ** -8 * (1 + 1e-6))
+    assert onn.bf16_round(np.float32(one)) == 1.0
