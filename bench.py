@@ -1,18 +1,25 @@
-"""Benchmark of the SENSE / CG data-consistency hot path on B300.
+"""Benchmark of the unrolled-reconstruction hot path on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload modl_train|cg_sense]
 
-One step = one batched CG-SENSE reconstruction of the 256x232, 12-coil,
-16-slice workload (R = 6 variable-density line mask, lambda = 0.05): x0 = A^H y
-(sense_adjoint) followed by 10 CG iterations of (A^H A + lambda I) from x0
-(cg_dc_solve), all in libsense kernels.  Inputs are seeded synthetic phantoms,
-coil maps and k-space simulated with the library's own forward operator.
+Default step (modl_train): one MoDL training step on 4 slices of 256x232 with
+12 coils (R = 6 variable-density line mask): x^0 = A^H y, five unrolled blocks
+x^{t+1} = (A^H A + lambda I)^{-1}(A^H y + lambda D_W(x^t)) with 10 CG iterations
+each, the MSE loss against the phantoms, the reverse pass through every block
+(second CG solve per block, denoiser backward with recomputed activations) and
+Adam on the 113,155 parameters — every step in libsense kernels (tensor-core
+convolutions, fused normal operator, CG vector kernels).
+
+Also measured: plain CG-SENSE on the 16-slice batch (slices/s, NRMSE) and the
+standalone normal operator (GB/s).  Inputs are seeded synthetic phantoms, coil
+maps and k-space simulated with the library's own forward operator.
 
 Printed (rank 0, one JSON line): slices/s with inputs resident in HBM (value),
-the same through host buffers (e2e), the live roofline of the fused
-normal-operator kernel (CUDA events around every launch inside the timed
-region), the standalone normal-operator bandwidth, clocks sampled during the
-timed region, and the FP64 CPU oracle timed on the host cores.
+the same through host buffers (e2e), the roofline of the dominant kernel (CUDA
+events around its launches inside the timed region), a per-kernel breakdown,
+clocks sampled during the timed region, and the FP64 CPU oracle timed on the
+host cores.
 """
 from __future__ import annotations
 
@@ -31,20 +38,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "unrolled-recon slices/s (fwd+bwd) & normal-op HBM GB/s vs plain CG-SENSE @NRMSE"
-WORKLOAD = "cg_sense_b16_c12_256x232_R6_10it"
-# DRAM bytes per launch of the fused CG normal-operator kernel from the committed
-# ncu capture (profiles/normal_lines_cg_256x232_b16.md); None until captured for
-# the current kernel version.
-NCU_TRAFFIC_PER_LAUNCH = None
-
-
-def peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    except Exception:
-        return 6400.0, "fallback"
+WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it"}
+# DRAM bytes per launch (read + write) of each kernel group from the committed ncu
+# captures under profiles/ (None until captured for the current kernel version).
+NCU_TRAFFIC = {"normal_lines": None, "conv64_tc": None, "wgrad64": None}
 
 
 # ------------------------------------------------------------------ clocks
@@ -109,229 +106,347 @@ def make_inputs(cfg, slice_offset=0):
             "x_gt": d["x_gt"].astype(np.complex64), "noise": d["noise"].astype(np.complex64)}
 
 
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak: 148 SMs x 128 lanes x 2 flop x clock (B300)."""
+    return 148 * 128 * 2 * (sm_mhz or 2032.0) * 1e6 / 1e12
+
+
+def kernel_report(name, ms, n, alg, peaks_d, clocks):
+    """Achieved vs peak for one kernel group; alg = (kind, amount per launch)."""
+    if n == 0 or ms <= 0:
+        return None
+    kind, per = alg
+    t = ms * 1e-3 / n
+    if kind == "hbm":
+        ach = per / t / 1e9
+        peak, unit = peaks_d["hbm_gbs"], "GB/s"
+    elif kind == "tensor":
+        ach = per / t / 1e12
+        peak, unit = peaks_d["bf16_tflops_sustained"], "TFLOP/s"
+    else:  # alu (FP32 FMA)
+        ach = per / t / 1e12
+        peak, unit = fp32_peak_tflops(clocks.get("sm_max_mhz")), "TFLOP/s"
+    return {"kernel": name, "bound": kind, "achieved": round(ach, 2), "peak": round(peak, 1),
+            "unit": unit, "frac": round(ach / peak, 4), "traffic": NCU_TRAFFIC.get(name),
+            "launches": n, "avg_launch_us": round(1e3 * ms / n, 3), "alg_per_launch": per}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "source": "fallback"}
+
+
+def timed_steps(step, steps, flush, dist):
+    import torch
+    from paper_2202_14005_b300 import _lib
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    _lib.kernel_launches(reset=True)
+    for k in ("normal_lines", "conv64_tc", "wgrad64"):
+        _lib.profile_read(k)
+    _lib.profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()  # evict L2 between timed steps (outside the step's events)
+        evs[i][0].record()
+        step()
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    _lib.profile_enable(False)
+    prof = {k: _lib.profile_read(k) for k in ("normal_lines", "conv64_tc", "wgrad64")}
+    launches = _lib.kernel_launches(reset=True)
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    return t_ms, prof, launches
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
     import synth
     from paper_2202_14005_b300.sense import SensePlan
+    from paper_2202_14005_b300.modl import ModlTrainer
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    cfg = synth.CONFIGS[2]
-    inp = make_inputs(cfg, slice_offset=rank * cfg.B)
-    maps = torch.from_numpy(inp["maps"]).to(dev)
-    mask = torch.from_numpy(inp["mask"]).to(dev)
-    plan = SensePlan(maps, mask)
-    # k-space simulated by the forward operator: y = A x_gt + M * noise
-    y = plan.forward(torch.from_numpy(inp["x_gt"]).to(dev))
-    y += torch.from_numpy(inp["noise"]).to(dev) * mask
-    lam = torch.tensor([cfg.lam], dtype=torch.float64, device=dev)
-    rhs = torch.empty((cfg.B, cfg.H, cfg.W), dtype=torch.complex64, device=dev)
-    x = torch.empty_like(rhs)
+    dist = torch.distributed if world > 1 else None
+    pk = load_peaks()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+    clk = ClockSampler(local_rank)
+    res = {}
 
-    def step():
-        plan.adjoint(y, out=rhs)
-        plan.cg_solve(rhs, lam, cfg.cg_iters, x0=rhs, out=x)
+    # ---------------- plain CG-SENSE on the 16-slice batch (secondary, or main)
+    c2 = synth.CONFIGS[2]
+    inp2 = make_inputs(c2, slice_offset=rank * c2.B)
+    maps2 = torch.from_numpy(inp2["maps"]).to(dev)
+    mask2 = torch.from_numpy(inp2["mask"]).to(dev)
+    plan2 = SensePlan(maps2, mask2)
+    y2 = plan2.forward(torch.from_numpy(inp2["x_gt"]).to(dev))
+    y2 += torch.from_numpy(inp2["noise"]).to(dev) * mask2
+    lam2 = torch.tensor([c2.lam], dtype=torch.float64, device=dev)
+    rhs2 = torch.empty((c2.B, c2.H, c2.W), dtype=torch.complex64, device=dev)
+    x2 = torch.empty_like(rhs2)
+
+    def step_cg():
+        plan2.adjoint(y2, out=rhs2)
+        plan2.cg_solve(rhs2, lam2, c2.cg_iters, x0=rhs2, out=x2)
 
     for _ in range(args.warmup):
-        step()
+        step_cg()
     torch.cuda.synchronize()
-    assert plan.status() == 0
-    plan.profile_read()
-
-    # ---- timed region (device-resident inputs)
-    dist = torch.distributed if world > 1 else None
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local_rank)
-    clk.start()
-    plan.profile(True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()  # evict L2 between timed steps (not inside the step's events)
-        evs[i][0].record()
-        step()
-        evs[i][1].record()
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    normal_ms, normal_n, launches = plan.profile_read()
-    plan.profile(False)
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-        dist.barrier()
-    assert plan.status() == 0
-
-    N = cfg.H * cfg.W
-    B, C = cfg.B, cfg.C
-    # algorithmic bytes of the timed fused-kernel launches: NM_RESID (x0, rhs, maps,
-    # write r) once per step, NM_CG (r, maps, write p, q; plus p_old after iteration 0)
-    per_step = 8 * N * B * ((C + 3) + (C + 3) + (cfg.cg_iters - 1) * (C + 4))
-    alg_bytes = per_step * args.steps
-    achieved = alg_bytes / (normal_ms * 1e-3) / 1e9 if normal_ms > 0 else None
-    hbm, src = peaks()
-
-    # ---- standalone normal operator (one launch per flush, CUDA events)
-    xin = rhs.clone()
-    xout = torch.empty_like(xin)
-    nrep = 20
-    tn = []
+    steps_cg = args.steps if args.workload == "cg_sense" else max(5, args.steps // 2)
+    if args.workload == "cg_sense":
+        clk.start()
+    t_cg, prof_cg, launches_cg = timed_steps(step_cg, steps_cg, flush, dist)
+    if args.workload == "cg_sense":
+        clocks = clk.stop()
+    assert plan2.status() == 0
+    gt2 = inp2["x_gt"]
+    nrmse_cg = float(np.linalg.norm(x2.cpu().numpy() - gt2) / np.linalg.norm(gt2))
+    N = c2.H * c2.W
+    # standalone normal operator, one launch per L2 flush
+    xin, xout = rhs2.clone(), torch.empty_like(rhs2)
     for _ in range(3):
-        plan.normal(xin, cfg.lam, out=xout)
-    for _ in range(nrep):
+        plan2.normal(xin, c2.lam, out=xout)
+    tn = []
+    for _ in range(20):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        plan.normal(xin, cfg.lam, out=xout)
+        plan2.normal(xin, c2.lam, out=xout)
         e1.record()
         torch.cuda.synchronize()
         tn.append(e0.elapsed_time(e1))
     tn_med = statistics.median(tn)
-    nbytes = 8 * N * B * (C + 2)
-    normal_gbs = nbytes / (tn_med * 1e-3) / 1e9
+    nbytes = 8 * N * c2.B * (c2.C + 2)
+    res["normal_op"] = {"workload": "256x232, 12 coils, 16 slices, lambda I", "GB/s": round(nbytes / (tn_med * 1e-3) / 1e9, 1),
+                        "frac": round(nbytes / (tn_med * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                        "median_us": round(tn_med * 1e3, 2), "alg_bytes": nbytes}
+    res["cg_sense"] = {"workload": WORKLOADS["cg_sense"], "slices_per_s": round(c2.B * world * steps_cg / (t_cg * 1e-3), 1),
+                       "ms_per_step": round(t_cg / steps_cg, 4), "nrmse": round(nrmse_cg, 5)}
 
-    # ---- end to end through host buffers: H2D of the step's inputs (k-space and
-    # coil maps) from pinned memory, the step, D2H of the reconstruction
-    y_h = y.cpu().pin_memory()
-    maps_h = maps.cpu().pin_memory()
-    x_h = torch.empty(x.shape, dtype=x.dtype).pin_memory()
+    if args.workload == "cg_sense":
+        cfg, B, t_ms, prof, launches, steps = c2, c2.B, t_cg, prof_cg, launches_cg, steps_cg
+        iters_per = (c2.C + 3) + (c2.C + 3) + (c2.cg_iters - 1) * (c2.C + 4)
+        normal_bytes = 8 * N * c2.B * iters_per / (c2.cg_iters + 1)
+        # e2e through host buffers: k-space and maps in, reconstruction out
+        y_h, maps_h = y2.cpu().pin_memory(), maps2.cpu().pin_memory()
+        out_h = torch.empty(x2.shape, dtype=x2.dtype).pin_memory()
+        ins = [(y2, y_h), (maps2, maps_h)]
+        outs = [(out_h, x2)]
+        step_fn = step_cg
+        value_slices = B
+    else:
+        c3 = synth.CONFIGS[3]
+        cfg = c3
+        inp3 = make_inputs(c3, slice_offset=rank * c3.B)
+        maps3 = torch.from_numpy(inp3["maps"]).to(dev)
+        mask3 = torch.from_numpy(inp3["mask"]).to(dev)
+        ws, bs = synth.modl_cnn_weights(3000 + rank)
+        flat = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(ws, bs)]).astype(np.float32)
+        tr = ModlTrainer(maps3, mask3, torch.from_numpy(flat).to(dev), c3.lam, c3.extra["K"], c3.cg_iters,
+                         lr=1e-4, lam_lr=1e-4)
+        gt3 = torch.from_numpy(inp3["x_gt"]).to(dev)
+        y3 = tr.plan.forward(gt3)
+        y3 += torch.from_numpy(inp3["noise"]).to(dev) * mask3
+
+        def step_modl():
+            tr.train_step(y3, gt3)
+
+        for _ in range(args.warmup):
+            step_modl()
+        torch.cuda.synchronize()
+        assert tr.plan.status() == 0 and tr.dn.status() == 0
+        steps = args.steps
+        clk.start()
+        t_ms, prof, launches = timed_steps(step_modl, steps, flush, dist)
+        clocks = clk.stop()
+        assert tr.plan.status() == 0 and tr.dn.status() == 0
+        B = c3.B
+        N3 = c3.H * c3.W
+        iters_per = (c3.C + 3) + (c3.cg_iters - 1) * (c3.C + 4)
+        normal_bytes = 8 * N3 * B * iters_per / c3.cg_iters
+        y_h, maps_h, gt_h = y3.cpu().pin_memory(), maps3.cpu().pin_memory(), gt3.cpu().pin_memory()
+        out_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        ins = [(y3, y_h), (maps3, maps_h), (gt3, gt_h)]
+        outs = [(out_h, tr.loss)]
+        step_fn = step_modl
+        value_slices = B
+        res["modl"] = {"loss_last_step": float(tr.loss.item()),
+                       "nrmse_untrained_forward": round(float(np.linalg.norm(tr.xs[-1].cpu().numpy() - inp3["x_gt"])
+                                                              / np.linalg.norm(inp3["x_gt"])), 5)}
+
+    if dist:
+        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+
+    # per-kernel roofline inside the timed region
+    Hc, Wc = cfg.H, cfg.W
+    conv_flops = 2.0 * B * Hc * Wc * 64 * 576
+    kern = {
+        "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks),
+        "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks),
+        "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("alu", conv_flops), pk, clocks),
+    }
+    kern = {k: v for k, v in kern.items() if v}
+    total_kernel_ms = {k: prof[k][0] for k in prof}
+    dominant = max(kern, key=lambda k: total_kernel_ms[k]) if kern else None
+    for k in kern:
+        kern[k]["share_of_step"] = round(total_kernel_ms[k] / t_ms, 4)
+
+    # end to end through host buffers (pinned), step inputs in and result out
     e2e = []
     for i in range(max(args.steps // 2, 2) + 1):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        y.copy_(y_h, non_blocking=True)
-        maps.copy_(maps_h, non_blocking=True)
-        step()
-        x_h.copy_(x, non_blocking=True)
+        for d, h in ins:
+            d.copy_(h, non_blocking=True)
+        step_fn()
+        for h, d in outs:
+            h.copy_(d, non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
         if i > 0:
             e2e.append(e0.elapsed_time(e1))
     e2e_ms = statistics.mean(e2e)
-    h2d = y.numel() * 8 + maps.numel() * 8
-    d2h = x.numel() * 8
-
-    # reconstruction quality of this step against the phantoms (NRMSE)
-    xr = x.cpu().numpy()
-    gt = inp["x_gt"]
-    nrmse = float(np.linalg.norm(xr - gt) / np.linalg.norm(gt))
+    h2d = sum(d.numel() * d.element_size() for d, _ in ins)
+    d2h = sum(h.numel() * h.element_size() for h, _ in outs)
 
     if rank != 0:
         return None
-    value = B * world * args.steps / (t_ms * 1e-3)
-    res = {
-        "metric": METRIC, "value": round(value, 2), "unit": "slices/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+    value = value_slices * world * steps / (t_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(t_ms / steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+bf16" if args.workload == "modl_train" else "c64",
         "data": "synthetic (seeded ellipse phantoms, Gaussian coil maps, k-space from the forward operator)",
-        "config": {"workload": WORKLOAD, "slices_per_gpu": B, "coils": C, "H": cfg.H, "W": cfg.W,
-                   "R": cfg.R, "cg_iters": cfg.cg_iters, "lambda": cfg.lam,
+        "config": {"workload": WORKLOADS[args.workload], "slices_per_gpu": B, "coils": cfg.C, "H": cfg.H,
+                   "W": cfg.W, "R": cfg.R, "cg_iters": cfg.cg_iters, "lambda": cfg.lam,
+                   "unrolled_blocks": cfg.extra.get("K") if args.workload == "modl_train" else None,
                    "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps"},
-        "roofline": {"kernel": "k_normal_lines (CG mode, fused A^H A + lambda I)", "bound": "hbm",
-                     "achieved": round(achieved, 1) if achieved else None, "peak": hbm,
-                     "peak_source": src, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4) if achieved else None,
-                     "traffic": NCU_TRAFFIC_PER_LAUNCH,
-                     "launches_timed": normal_n, "avg_launch_us": round(1e3 * normal_ms / max(normal_n, 1), 3),
-                     "alg_bytes_per_launch": int(alg_bytes / max(normal_n, 1))},
-        "normal_op": {"GB/s": round(normal_gbs, 1), "frac": round(normal_gbs / hbm, 4),
-                      "median_us": round(tn_med * 1e3, 2), "alg_bytes": nbytes},
-        "e2e": {"value": round(B * world / (e2e_ms * 1e-3), 2), "unit": "slices/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": round(e2e_ms, 3)},
+        "roofline": kern.get(dominant),
+        "kernels": kern,
+        "e2e": {"value": round(value_slices * world / (e2e_ms * 1e-3), 3), "unit": "slices/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
         "gpu_launches": launches,
         "clocks": clocks,
-        "nrmse": {"cg_sense": round(nrmse, 5)},
+        "peaks": pk,
     }
-    return res
+    out.update(res)
+    return out
 
 
 # ------------------------------------------------------------ CPU oracle
-def _oracle_slice(args):
-    """One slice of the workload on the FP64 oracle: A^H y, then 10 CG iterations."""
+def _worker_init():
     os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["MKL_NUM_THREADS"] = "1"
+
+
+def _oracle_slice(args):
+    """One slice of a workload on the FP64 oracle; returns its CPU seconds."""
     import numpy as np
     import synth
     from oracle import cg as ocg
     from oracle import sense as osense
-    cfg_i, s = args
-    cfg = synth.CONFIGS[cfg_i]
+    from oracle import unrolled as ounr
+    workload, s = args
+    cfg = synth.CONFIGS[2 if workload == "cg_sense" else 3]
     d = synth.make_slices(cfg, [s])
     maps = d["maps"].astype(np.complex64)
     mask = d["mask"]
-    y = (osense.forward(d["x_gt"], maps, mask) + mask * d["noise"]).astype(np.complex64)
+    gt = d["x_gt"].astype(np.complex64)
+    y = (osense.forward(gt, maps, mask) + mask * d["noise"]).astype(np.complex64)
     t0 = time.perf_counter()
     rhs = osense.adjoint(y, maps, mask)
-    ocg.cg_solve(maps, mask, cfg.lam, rhs, rhs, cfg.cg_iters)
-    return time.perf_counter() - t0
+    if workload == "cg_sense":
+        ocg.cg_solve(maps, mask, cfg.lam, rhs, rhs, cfg.cg_iters)
+        return time.perf_counter() - t0
+    # MoDL: A^H y plus one unrolled block forward and reverse, scaled by K blocks
+    t_adj = time.perf_counter() - t0
+    ws, bs = synth.modl_cnn_weights(3000)
+    t1 = time.perf_counter()
+    x1, _ = ounr.modl_block(rhs, rhs, maps, mask, ws, bs, cfg.lam, cfg.cg_iters)
+    g = ounr.mse_loss_grad(x1, gt)
+    ounr.modl_block_backward(g, rhs, x1, rhs, maps, mask, ws, bs, cfg.lam, cfg.cg_iters)
+    return t_adj + cfg.extra["K"] * (time.perf_counter() - t1)
 
 
-def cpu_baseline(steps=1, slices=None):
-    """The oracle as it stands on the host cores: a process pool over slices."""
-    import synth
-    cfg = synth.CONFIGS[2]
+def oracle_pool_run(workload, n, reps):
     cores = os.cpu_count() or 1
-    n = slices if slices is not None else min(cfg.B, cores)
     ctx = mp.get_context("spawn")
-    with ctx.Pool(processes=min(n, cores)) as pool:
-        pool.map(_oracle_slice, [(2, 0)])  # warm the workers' imports
-        walls = []
-        for _ in range(steps):
+    walls, per = [], []
+    with ctx.Pool(processes=min(n, cores), initializer=_worker_init) as pool:
+        pool.map(_oracle_slice, [("cg_sense", 0)])  # imports and FFT plans warm
+        for _ in range(reps):
             t0 = time.perf_counter()
-            pool.map(_oracle_slice, [(2, s) for s in range(n)])
+            per = pool.map(_oracle_slice, [(workload, s) for s in range(n)])
             walls.append(time.perf_counter() - t0)
-    wall = sum(walls)
-    return {"value": round(n * steps / wall, 4), "unit": "slices/s", "cores": min(n, cores),
-            "kind": "oracle",
-            "sample": f"{n} of 16 slices x {steps} step(s) of the workload (A^H y + 10 CG iterations, "
-                      f"FP64 NumPy, one process per slice, spawn pool); wall {wall:.1f} s"}
+    return walls, min(n, cores), per
+
+
+def cpu_baseline(workload):
+    """The oracle as it stands on the host cores: one process per slice."""
+    n = 16 if workload == "cg_sense" else 4
+    walls, used, per = oracle_pool_run(workload, n, 1)
+    if workload == "cg_sense":
+        wall = sum(walls)
+        return {"value": round(n / wall, 5), "unit": "slices/s", "cores": used, "kind": "oracle",
+                "sample": f"{n} slices, A^H y + 10 CG iterations each (FP64 NumPy, one spawn process per "
+                          f"slice); wall {wall:.1f} s"}
+    est = max(per)  # slices run in parallel: the step takes as long as the slowest slice
+    return {"value": round(n / est, 6), "unit": "slices/s", "cores": used, "kind": "oracle",
+            "sample": f"{n} slices in parallel; per slice A^H y plus ONE unrolled block forward and reverse "
+                      f"(CNN, 10-iteration CG, recomputed CNN, second CG, CNN backward), time scaled by the "
+                      f"5 blocks of the step (FP64 NumPy, one spawn process per slice); slowest slice "
+                      f"{est:.1f} s per step"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    vals = []
-    import synth
-    cores = os.cpu_count() or 1
-    n = min(synth.CONFIGS[2].B, cores)
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(processes=n) as pool:
-        pool.map(_oracle_slice, [(2, 0)])
-        for i in range(args.warmup + args.steps):
-            t0 = time.perf_counter()
-            pool.map(_oracle_slice, [(2, s) for s in range(n)])
-            if i >= args.warmup:
-                vals.append(time.perf_counter() - t0)
+    n = 16 if args.workload == "cg_sense" else 4
+    reps = args.warmup + args.steps
+    if args.workload == "modl_train":
+        reps = max(1, min(reps, 2))  # each rep is ~1 min of CPU work per slice
+    walls, used, per = oracle_pool_run(args.workload, n, reps)
+    vals = walls[min(args.warmup, reps - 1):]
     wall = sum(vals)
     value = n * len(vals) / wall
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "slices/s",
+    if args.workload == "modl_train":
+        value = n / max(per)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "slices/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * wall / len(vals), 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "slices_per_step": n},
-            "cpu_baseline": {"value": round(value, 4), "unit": "slices/s", "cores": n,
-                             "kind": "oracle",
-                             "sample": f"{n} of 16 slices per step (FP64 NumPy oracle, spawn pool)"},
-            "e2e": {"value": round(value, 4), "unit": "slices/s", "h2d_bytes_per_step": 0,
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "slices_per_step": n},
+            "cpu_baseline": {"value": round(value, 5), "unit": "slices/s", "cores": used, "kind": "oracle",
+                             "sample": f"{n} slices per step (FP64 NumPy oracle, spawn pool)"},
+            "e2e": {"value": round(value, 5), "unit": "slices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="modl_train", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.impl == "ours":
+        args.warmup = max(args.warmup, 3)
+        args.steps = max(args.steps, 1)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -343,10 +458,9 @@ def main():
             print(json.dumps(res), flush=True)
         return
 
-    # the oracle's process pool is spawned before the first GPU call
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(steps=1)
+        base = cpu_baseline(args.workload)  # the spawn pool runs before the first GPU call
 
     import torch
     if world > 1:

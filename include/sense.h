@@ -115,17 +115,17 @@ int cg_dc_solve_backward(sense_plan plan, const void* grad_x, const void* x, con
                          const double* lambda, int lambda_count, int iters,
                          void* grad_rhs, double* grad_lambda);
 
-/* Profiling.  The library counts every kernel it launches for a plan; with
- * enable != 0 it also records a CUDA event pair on the plan's stream around
- * each launch of the fused line-mask normal-operator kernel (the one the
- * operator and the CG iterations spend their time in). */
-int sense_plan_profile(sense_plan plan, int enable);
-/* Synchronises the plan's stream if events are pending and returns, since the
- * last read: the summed event time of the timed launches (ms), their number,
- * and the number of kernels launched; then resets all three.  Any output
- * pointer may be NULL. */
-int sense_plan_profile_read(sense_plan plan, double* normal_ms, int* normal_launches,
-                            long long* kernel_launches);
+/* Profiling (process-wide).  The library counts every kernel it launches;
+ * with enable != 0 it also records a CUDA event pair on the launching stream
+ * around each launch of its main kernels, grouped by name: "normal_lines"
+ * (fused normal operator), "conv64_tc" (tensor-core convolution), "wgrad64"
+ * (64-channel weight gradient). */
+int sense_profile_enable(int enable);
+/* Summed event time (ms) and number of timed launches of one kernel group
+ * since its last read (waits for the recorded events); resets the group. */
+int sense_profile_read(const char* name, double* ms, int* launches);
+/* Kernels launched so far (reset to zero if reset != 0). */
+long long sense_kernel_launches(int reset);
 
 /* Synchronises the plan's stream, returns the OR of device status bits set
  * since the last call, and clears them. */
@@ -170,6 +170,38 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
                       int W, int recompute, void* stream);
 /* Reads (synchronising the stream) and clears the status word in ws. */
 int denoiser_get_status(void* ws, int B, int H, int W, void* stream, int* device_status);
+
+/* ------------------------------------------------------------------------
+ * Unrolled MoDL block (Eq. 6, Sec. 2.3.2) on a plan (maps, mask, workspace)
+ * and a denoiser workspace, on the plan's stream.  lambda: device float64 [1].
+ *   unrolled_step:  z = D_W(x_t);  x_next = S_lambda^{-1}(AHy + lambda z) by
+ *                   cg_iters CG iterations from zero.
+ *   unrolled_step_backward: given grad_next = dL/dx_next, recomputes z from x_t
+ *                   (checkpointing, Sec. 2.2.4), solves v = S_lambda^{-1} grad_next,
+ *                   adds Re<v, z - x_next> to grad_lambda[0], and writes
+ *                   grad_t = (dD/dx)^H (lambda v) while adding dL/dW to grad_weights.
+ * x_t, x_next, AHy, grad_next, grad_t: complex64 [B][H][W]. */
+int unrolled_step(sense_plan plan, int kind, const float* weights, const double* lambda,
+                  const void* AHy, const void* x_t, void* x_next, int cg_iters, void* dn_ws,
+                  size_t dn_ws_bytes);
+int unrolled_step_backward(sense_plan plan, int kind, const float* weights, const double* lambda,
+                           const void* AHy, const void* x_t, const void* x_next,
+                           const void* grad_next, void* grad_t, float* grad_weights,
+                           double* grad_lambda, int cg_iters, void* dn_ws, size_t dn_ws_bytes);
+
+/* Training loss of the unrolled networks: loss[0] = mean |x - gt|^2 over the
+ * plan's B*H*W complex elements (float64, fixed-order sum) and
+ * grad = 2 (x - gt) / n (complex convention of Sec. 2.2.2).  Plan's stream. */
+int sense_mse_loss(sense_plan plan, const void* x, const void* gt, double* loss, void* grad);
+
+/* Adam (Kingma and Ba) on n parameters with moments m, v; step >= 1 is the
+ * 1-based update count (bias correction).  The gradient is consumed and set
+ * to zero, ready to accumulate the next step.  The float64 variant clamps the
+ * parameters at `lower` (used to keep the MoDL lambda positive). */
+int adam_update_f32(float* param, float* grad, float* m, float* v, size_t n, float lr, float beta1,
+                    float beta2, float eps, int step, void* stream);
+int adam_update_f64(double* param, double* grad, double* m, double* v, size_t n, double lr,
+                    double beta1, double beta2, double eps, int step, double lower, void* stream);
 
 /* Allocation-free variant of the inner product behind the lambda gradient of
  * cg_dc_solve_backward.  The paper has no counterpart; it exists for callers

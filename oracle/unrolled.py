@@ -54,7 +54,8 @@ def modl_forward(AHy, maps, mask, ws, bs, lam, T, iters, act_round=None):
     return xs[-1], xs
 
 
-def modl_block_backward(g_next, x_t, x_next, AHy, maps, mask, ws, bs, lam, iters, act_round=None):
+def modl_block_backward(g_next, x_t, x_next, AHy, maps, mask, ws, bs, lam, iters, act_round=None,
+                        grad_round=None):
     """Reverse mode of one MoDL block.
 
     Returns (g_t, grad_ws, grad_bs, grad_lambda).  The denoiser activations
@@ -63,11 +64,11 @@ def modl_block_backward(g_next, x_t, x_next, AHy, maps, mask, ws, bs, lam, iters
     z, cache = _nn.modl_cnn_forward(x_t, ws, bs, act_round)
     v, glam_b = _cg.cg_solve_backward(maps, mask, lam, g_next, x_next, z, iters)
     g_z = lam * v
-    g_t, gws, gbs = _nn.modl_cnn_backward(x_t, ws, bs, g_z, cache)
+    g_t, gws, gbs = _nn.modl_cnn_backward(x_t, ws, bs, g_z, cache, grad_round=grad_round)
     return g_t, gws, gbs, float(np.sum(glam_b))
 
 
-def modl_train_grads(AHy, maps, mask, gt, ws, bs, lam, T, iters, act_round=None):
+def modl_train_grads(AHy, maps, mask, gt, ws, bs, lam, T, iters, act_round=None, grad_round=None):
     """Loss and gradients of one MoDL training step (x^0 = A^H y is constant)."""
     xT, xs = modl_forward(AHy, maps, mask, ws, bs, lam, T, iters, act_round)
     loss = mse_loss(xT, gt)
@@ -77,7 +78,7 @@ def modl_train_grads(AHy, maps, mask, gt, ws, bs, lam, T, iters, act_round=None)
     glam = 0.0
     for t in range(T - 1, -1, -1):
         g, dws, dbs, dl = modl_block_backward(g, xs[t], xs[t + 1], AHy, maps, mask,
-                                              ws, bs, lam, iters, act_round)
+                                              ws, bs, lam, iters, act_round, grad_round)
         for i in range(len(ws)):
             gws[i] += dws[i]
             gbs[i] += dbs[i]

@@ -40,15 +40,22 @@ SIGNATURES = {
     "cg_dc_solve": (_i, [_vp, _vp, _vp, _vp, _dp, _i, _i, _dp]),
     "cg_dc_solve_backward": (_i, [_vp, _vp, _vp, _vp, _dp, _i, _i, _vp, _dp]),
     "sense_get_status": (_i, [_vp, C.POINTER(_i)]),
-    "sense_plan_profile": (_i, [_vp, _i]),
-    "sense_plan_profile_read": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i),
-                                     C.POINTER(C.c_longlong)]),
+    "sense_profile_enable": (_i, [_i]),
+    "sense_profile_read": (_i, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(_i)]),
+    "sense_kernel_launches": (C.c_longlong, [_i]),
     "denoiser_workspace_bytes": (C.c_size_t, [_i, _i, _i, _i]),
     "denoiser_param_count": (_i, [_i]),
     "denoiser_workspace_offsets": (_i, [_i, _i, _i, _i, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "denoiser_forward": (_i, [_i, _vp, _vp, _vp, _vp, C.c_size_t, _i, _i, _i, _vp]),
     "denoiser_backward": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _i, _i, _i, _i, _vp]),
     "denoiser_get_status": (_i, [_vp, _i, _i, _i, _vp, C.POINTER(_i)]),
+    "unrolled_step": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, C.c_size_t]),
+    "unrolled_step_backward": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp,
+                                    C.c_size_t]),
+    "sense_mse_loss": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "adam_update_f32": (_i, [_vp, _vp, _vp, _vp, C.c_size_t, _f, _f, _f, _f, _i, _vp]),
+    "adam_update_f64": (_i, [_vp, _vp, _vp, _vp, C.c_size_t, C.c_double, C.c_double, C.c_double,
+                             C.c_double, _i, C.c_double, _vp]),
     "sense_dot_re_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _dp, _i, _vp]),
     "sense_strerror": (C.c_char_p, [_i]),
 }
@@ -80,6 +87,21 @@ def lib() -> C.CDLL:
     if _LIB is None:
         _LIB = load()
     return _LIB
+
+
+def profile_enable(on: bool = True) -> None:
+    check("sense_profile_enable", lib().sense_profile_enable(1 if on else 0))
+
+
+def profile_read(name: str):
+    """(ms, launches) of one kernel group since its last read."""
+    ms, n = C.c_double(), C.c_int()
+    check("sense_profile_read", lib().sense_profile_read(name.encode(), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def kernel_launches(reset: bool = False) -> int:
+    return int(lib().sense_kernel_launches(1 if reset else 0))
 
 
 def check(fn: str, code: int) -> None:

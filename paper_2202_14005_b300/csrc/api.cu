@@ -13,7 +13,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t T, r, p, q, part, rr, alpha, beta, lam, counter, total;
+  size_t T, r, p, q, t0, t1, part, rr, alpha, beta, lam, counter, total;
 };
 
 WsLayout ws_layout(const sense_plan p) {
@@ -24,6 +24,8 @@ WsLayout ws_layout(const sense_plan p) {
   L.r = o; o += up256(img);
   L.p = o; o += up256(img);
   L.q = o; o += up256(img);
+  L.t0 = o; o += up256(img);
+  L.t1 = o; o += up256(img);
   L.part = o; o += up256((size_t)p->B * p->H * sizeof(double));
   L.rr = o; o += up256(p->B * sizeof(double));
   L.alpha = o; o += up256(p->B * sizeof(double));
@@ -136,7 +138,6 @@ int sense_plan_create(sense_plan* out, int B, int C, int H, int W, const void* m
 
 int sense_plan_destroy(sense_plan p) {
   if (!p) return SENSE_EINVAL_PTR;
-  for (cudaEvent_t e : p->prof.ev) cudaEventDestroy(e);
   free_lines_tables(p);
   if (p->own) cudaFree(p->own);
   delete p;
@@ -167,6 +168,8 @@ int sense_plan_set_workspace(sense_plan p, void* ws, size_t bytes) {
   w.r = reinterpret_cast<float2*>(b + L.r);
   w.p = reinterpret_cast<float2*>(b + L.p);
   w.q = reinterpret_cast<float2*>(b + L.q);
+  w.t0 = reinterpret_cast<float2*>(b + L.t0);
+  w.t1 = reinterpret_cast<float2*>(b + L.t1);
   w.part = reinterpret_cast<double*>(b + L.part);
   w.rr = reinterpret_cast<double*>(b + L.rr);
   w.alpha = reinterpret_cast<double*>(b + L.alpha);
@@ -233,7 +236,7 @@ int cg_dc_solve_backward(sense_plan p, const void* grad_x, const void* x, const 
     return e;
   if (grad_lambda)
     return launch_dot_rows(p, v, static_cast<const float2*>(z), static_cast<const float2*>(x),
-                           grad_lambda, lambda_count);
+                           grad_lambda, lambda_count, 0);
   return SENSE_OK;
 }
 
@@ -245,34 +248,6 @@ int sense_get_status(sense_plan p, int* device_status) {
       cudaMemsetAsync(p->status, 0, sizeof(int), p->stream) != cudaSuccess)
     return SENSE_ECUDA;
   *device_status = v;
-  return SENSE_OK;
-}
-
-int sense_plan_profile(sense_plan p, int enable) {
-  if (!p) return SENSE_EINVAL_PTR;
-  p->prof.on = enable ? 1 : 0;
-  return SENSE_OK;
-}
-
-int sense_plan_profile_read(sense_plan p, double* normal_ms, int* normal_launches,
-                            long long* kernel_launches) {
-  if (!p) return SENSE_EINVAL_PTR;
-  Profiler& f = p->prof;
-  double ms = 0.0;
-  if (f.used > 0) {
-    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return SENSE_ECUDA;
-    for (int i = 0; i < f.used; ++i) {
-      float t = 0.f;
-      if (cudaEventElapsedTime(&t, f.ev[2 * (size_t)i], f.ev[2 * (size_t)i + 1]) != cudaSuccess)
-        return SENSE_ECUDA;
-      ms += t;
-    }
-  }
-  if (normal_ms) *normal_ms = ms;
-  if (normal_launches) *normal_launches = f.used;
-  if (kernel_launches) *kernel_launches = f.launches;
-  f.used = 0;
-  f.launches = 0;
   return SENSE_OK;
 }
 

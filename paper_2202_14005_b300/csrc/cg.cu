@@ -39,6 +39,7 @@ struct RowArgs {
   double* hist;      // rr_hist row [B] or NULL
   double* gout;      // FIN_GLAM output
   int gcount;        // 1 or B
+  int gacc;          // FIN_GLAM: add to gout instead of overwriting
   unsigned* counter;
   int* status;
 };
@@ -70,7 +71,7 @@ __device__ void finalize(const RowArgs& a) {
       a.rr[b] = s;
       if (a.hist) a.hist[b] = s;
     } else if (a.fin == FIN_GLAM) {
-      if (a.gcount == a.B) a.gout[b] = s;
+      if (a.gcount == a.B) a.gout[b] = a.gacc ? a.gout[b] + s : s;
       else a.alpha[b] = s;  // per-slice scratch, summed below in slice order
     }
   }
@@ -79,7 +80,7 @@ __device__ void finalize(const RowArgs& a) {
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int b = 0; b < a.B; ++b) t += a.alpha[b];
-      a.gout[0] = t;
+      a.gout[0] = a.gacc ? a.gout[0] + t : t;
     }
   }
 }
@@ -205,7 +206,7 @@ RowArgs base_args(sense_plan p) {
   a.part = p->w.part;
   a.fin = FIN_NONE;
   a.rr = p->w.rr; a.alpha = p->w.alpha; a.beta = p->w.beta;
-  a.hist = nullptr; a.gout = nullptr; a.gcount = 1;
+  a.hist = nullptr; a.gout = nullptr; a.gcount = 1; a.gacc = 0;
   a.counter = p->w.counter; a.status = p->status;
   return a;
 }
@@ -272,11 +273,13 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
-// out[count] = sum Re<a, b - c> per slice (count == B) or over all slices (count == 1).
+// out[count] (=, or += when accumulate) sum Re<a, b - c> per slice (count == B) or over all
+// slices (count == 1).
 int launch_dot_rows(sense_plan p, const float2* a_, const float2* b_, const float2* c_, double* out,
-                    int out_count) {
+                    int out_count, int accumulate) {
   RowArgs a = base_args(p);
   a.a = a_; a.b = b_; a.c = c_; a.fin = FIN_GLAM; a.gout = out; a.gcount = out_count;
+  a.gacc = accumulate;
   k_dot<<<grid_rows(p), kWarps * 32, 0, p->stream>>>(a);
   count_launch(p);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;

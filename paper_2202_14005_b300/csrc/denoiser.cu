@@ -656,7 +656,10 @@ int launch_conv64(const __nv_bfloat16* in, const __nv_bfloat16* wpack, const flo
   a.wpack = wpack; a.bias = bias; a.aprev = aprev; a.out = out; a.mode = mode; a.status = status;
   const int ntiles = B * H * a.ntw;
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  prof_mark("conv64_tc", st, false);
   k_conv64<<<grid, CONV_THREADS, CONV_SMEM, st>>>(map, a);
+  prof_mark("conv64_tc", st, true);
+  prof_count(1);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
@@ -714,6 +717,7 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
   if (out)
     k_l5_fwd<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, act[3], wts + o.w[4], wts + o.b[4], x,
                                                             out);
+  prof_count(4 + (out ? 1 : 0));  // packing x3, first layer, last layer (convolutions counted apart)
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
@@ -786,7 +790,9 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   for (int l = 2; l >= 0; --l) {
     const __nv_bfloat16* ain = act[l];  // input activation of this layer
     dim3 gw(L.nch64, 9);
+    prof_mark("wgrad64", st, false);
     k_wgrad64<<<gw, 256, 0, st>>>(B, H, W, gbuf[cur], ain, p64);
+    prof_mark("wgrad64", st, true);
     k_reduce_wgrad64<<<(CH * CH * 9 + CH + 255) / 256, 256, 0, st>>>(p64, L.nch64, grad_weights + o.w[l + 1],
                                                                      grad_weights + o.b[l + 1]);
     if (int e = launch_conv64(gbuf[cur], reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), nullptr, ain,
@@ -801,6 +807,7 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
                                                                grad_weights + o.b[0]);
   k_l1_dgrad<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, gbuf[cur], weights + o.w[0], go,
                                                             static_cast<float2*>(grad_x));
+  prof_count(15);  // every launch of the backward except the three tensor-core convolutions
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 

@@ -508,9 +508,9 @@ int launch_normal_lines(sense_plan pl, const NormalLaunch& L) {
   a.beta = L.beta; a.part = L.part; a.finalize = L.finalize;
   a.rr = pl->w.rr; a.alpha = pl->w.alpha; a.rr_hist_row = L.rr_hist_row;
   a.counter = pl->w.counter; a.status = pl->status;
-  prof_mark(pl, false);
+  prof_mark("normal_lines", pl->stream, false);
   k<<<T.grid, T.threads, T.smem, pl->stream>>>(a);
-  prof_mark(pl, true);
+  prof_mark("normal_lines", pl->stream, true);
   count_launch(pl);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

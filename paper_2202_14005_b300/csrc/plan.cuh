@@ -35,20 +35,14 @@ struct Workspace {
   float2* r = nullptr;          // [B][H][W]
   float2* p = nullptr;
   float2* q = nullptr;
+  float2* t0 = nullptr;         // [B][H][W] temporaries of the unrolled blocks
+  float2* t1 = nullptr;
   double* part = nullptr;       // [B][H] per-row partial sums
   double* rr = nullptr;         // [B]  ||r||^2
   double* alpha = nullptr;      // [B]
   double* beta = nullptr;       // [B]
   double* lam = nullptr;        // [B]  lambda per slice (float64)
   unsigned* counter = nullptr;  // last-block counter (zero between kernels)
-};
-
-// Launch accounting and optional CUDA-event timing of the fused normal kernel.
-struct Profiler {
-  int on = 0;
-  long long launches = 0;            // every kernel this plan launched
-  std::vector<cudaEvent_t> ev;       // start/stop pairs
-  int used = 0;                      // pairs recorded since the last read
 };
 
 struct sense_plan_s {
@@ -68,23 +62,12 @@ struct sense_plan_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   Workspace w;
-  Profiler prof;
 };
 
-inline void count_launch(sense_plan p, int n = 1) { p->prof.launches += n; }
-// Records the start (stop = false) or stop event of one timed launch.
-inline void prof_mark(sense_plan p, bool stop) {
-  Profiler& f = p->prof;
-  if (!f.on) return;
-  const size_t need = 2 * (size_t)f.used + 2;
-  while (f.ev.size() < need) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) { f.on = 0; return; }
-    f.ev.push_back(e);
-  }
-  cudaEventRecord(f.ev[2 * (size_t)f.used + (stop ? 1 : 0)], p->stream);
-  if (stop) ++f.used;
-}
+// Process-wide launch accounting and per-kernel-class CUDA-event timing (profile.cu).
+void prof_count(int n);
+void prof_mark(const char* name, cudaStream_t s, bool stop);
+inline void count_launch(sense_plan, int n = 1) { prof_count(n); }
 
 // --------------------------------------------------------------- launchers
 // Modes of the fused line-mask normal-operator kernel.
@@ -119,4 +102,4 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
 int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const double* lam,
            int lam_count, int iters, double* rr_hist);
 int launch_dot_rows(sense_plan p, const float2* a, const float2* b, const float2* c,
-                    double* out, int out_count);
+                    double* out, int out_count, int accumulate);

@@ -1,0 +1,185 @@
+// MoDL unrolled block (Sec. 2.3.2, Eq. 6) forward and reverse mode, the MSE
+// training loss and Adam updates.
+//
+//   forward:  z = D_W(x_t);  x_{t+1} = S_lambda^{-1}(A^H y + lambda z)   (CG from 0)
+//   backward: z recomputed from x_t (checkpointing, Sec. 2.2.4);
+//             v = S_lambda^{-1} g (second CG);  grad_lambda += Re<v, z - x_{t+1}>;
+//             grad_z = lambda v;  grad_x_t = (dD/dx)^H grad_z, grad_W += ...
+//
+// The loss is L = mean |x - x_gt|^2 with gradient 2 (x - x_gt) / n (complex
+// convention of Sec. 2.2.2).  Adam follows Kingma and Ba; it consumes the
+// accumulated gradient and clears it for the next step.
+#include <cmath>
+
+#include "plan.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+
+__global__ void k_rhs(size_t n2, const float4* b, const float4* z, const double* lam, float4* out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  const float l = (float)lam[0];
+  const float4 u = b[i], v = z[i];
+  out[i] = make_float4(fmaf(l, v.x, u.x), fmaf(l, v.y, u.y), fmaf(l, v.z, u.z), fmaf(l, v.w, u.w));
+}
+
+__global__ void k_scale(size_t n2, const float4* v, const double* lam, float4* out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  const float l = (float)lam[0];
+  const float4 u = v[i];
+  out[i] = make_float4(l * u.x, l * u.y, l * u.z, l * u.w);
+}
+
+// loss partials per image row, grad = 2 (x - gt) / n; last CTA sums in row order.
+__global__ void __launch_bounds__(kWarps * 32) k_mse(int rows, int W, const float4* x, const float4* gt,
+                                                     float4* grad, double inv_n, double* part,
+                                                     double* loss, unsigned* counter) {
+  const int row = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row < rows) {
+    const size_t off = (size_t)row * W / 2;
+    float s = 0.f;
+    const float sc = (float)(2.0 * inv_n);
+    for (int i = lane; i < W / 2; i += 32) {
+      const float4 a = x[off + i], b = gt[off + i];
+      const float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+      s = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, s))));
+      grad[off + i] = make_float4(sc * d.x, sc * d.y, sc * d.z, sc * d.w);
+    }
+    const double t = warp_sum_d((double)s);
+    if (lane == 0) part[row] = t;
+  }
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = lane; i < rows; i += 32) t += __ldcg(part + i);
+    t = warp_sum_d(t);
+    if (lane == 0) {
+      loss[0] = t * inv_n;
+      *counter = 0u;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_adam(size_t n, T* p, T* g, T* m, T* v, T lr, T b1, T b2, T eps, T c1, T c2, T lo) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T gi = g[i];
+  const T mi = b1 * m[i] + (T(1) - b1) * gi;
+  const T vi = b2 * v[i] + (T(1) - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  T pi = p[i] - lr * (mi / c1) / (sqrt(vi / c2) + eps);
+  if (pi < lo) pi = lo;
+  p[i] = pi;
+  g[i] = T(0);
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_step(sense_plan p, int kind, const void* weights, const double* lambda, const void* AHy,
+               void* dn_ws, size_t dn_ws_bytes) {
+  if (!p || !weights || !lambda || !AHy || !dn_ws) return SENSE_EINVAL_PTR;
+  if (kind != SENSE_DENOISER_MODL) return SENSE_EUNSUPPORTED;
+  if (!p->ws) return SENSE_EWORKSPACE;
+  if (dn_ws_bytes < denoiser_workspace_bytes(kind, p->B, p->H, p->W)) return SENSE_EWORKSPACE;
+  if (!al16(AHy) || ((uintptr_t)lambda & 7u)) return SENSE_EINVAL_PTR;
+  return SENSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int unrolled_step(sense_plan p, int kind, const float* weights, const double* lambda, const void* AHy,
+                  const void* x_t, void* x_next, int cg_iters, void* dn_ws, size_t dn_ws_bytes) {
+  if (int e = check_step(p, kind, weights, lambda, AHy, dn_ws, dn_ws_bytes)) return e;
+  if (!x_t || !x_next || !al16(x_t) || !al16(x_next) || x_t == x_next) return SENSE_EINVAL_PTR;
+  if (cg_iters < 0 || cg_iters > 100000) return SENSE_EINVAL_ARG;
+  Workspace& w = p->w;
+  const size_t n2 = (size_t)p->B * p->H * p->W / 2;
+  if (int e = denoiser_forward(kind, weights, x_t, w.t0, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
+    return e;
+  k_rhs<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, static_cast<const float4*>(AHy),
+                                                             reinterpret_cast<const float4*>(w.t0), lambda,
+                                                             reinterpret_cast<float4*>(w.t1));
+  count_launch(p);
+  return cg_run(p, w.t1, nullptr, static_cast<float2*>(x_next), lambda, 1, cg_iters, nullptr);
+}
+
+int unrolled_step_backward(sense_plan p, int kind, const float* weights, const double* lambda,
+                           const void* AHy, const void* x_t, const void* x_next, const void* grad_next,
+                           void* grad_t, float* grad_weights, double* grad_lambda, int cg_iters,
+                           void* dn_ws, size_t dn_ws_bytes) {
+  if (int e = check_step(p, kind, weights, lambda, AHy, dn_ws, dn_ws_bytes)) return e;
+  if (!x_t || !x_next || !grad_next || !grad_t || !grad_weights || !grad_lambda || !al16(x_t) ||
+      !al16(x_next) || !al16(grad_next) || !al16(grad_t) || grad_t == grad_next)
+    return SENSE_EINVAL_PTR;
+  if (cg_iters < 0 || cg_iters > 100000) return SENSE_EINVAL_ARG;
+  Workspace& w = p->w;
+  const size_t n2 = (size_t)p->B * p->H * p->W / 2;
+  // z = D(x_t), recomputed; the denoiser keeps its activations in dn_ws
+  if (int e = denoiser_forward(kind, weights, x_t, w.t0, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
+    return e;
+  // v = S^{-1} g  and  grad_lambda += Re<v, z - x_next>
+  if (int e = cg_run(p, static_cast<const float2*>(grad_next), nullptr, w.t1, lambda, 1, cg_iters, nullptr))
+    return e;
+  if (int e = launch_dot_rows(p, w.t1, w.t0, static_cast<const float2*>(x_next), grad_lambda, 1, 1))
+    return e;
+  // grad_z = lambda v  (z is no longer needed)
+  k_scale<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, reinterpret_cast<const float4*>(w.t1),
+                                                               lambda, reinterpret_cast<float4*>(w.t0));
+  count_launch(p);
+  return denoiser_backward(kind, weights, x_t, w.t0, grad_t, grad_weights, dn_ws, dn_ws_bytes, p->B, p->H,
+                           p->W, 0, p->stream);
+}
+
+int sense_mse_loss(sense_plan p, const void* x, const void* gt, double* loss, void* grad) {
+  if (!p || !x || !gt || !loss || !grad || !al16(x) || !al16(gt) || !al16(grad) || ((uintptr_t)loss & 7u))
+    return SENSE_EINVAL_PTR;
+  if (!p->ws) return SENSE_EWORKSPACE;
+  const int rows = p->B * p->H;
+  const double inv_n = 1.0 / ((double)rows * p->W);
+  k_mse<<<(rows + kWarps - 1) / kWarps, kWarps * 32, 0, p->stream>>>(
+      rows, p->W, static_cast<const float4*>(x), static_cast<const float4*>(gt), static_cast<float4*>(grad),
+      inv_n, p->w.part, loss, p->w.counter);
+  count_launch(p);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int adam_update_f32(float* param, float* grad, float* m, float* v, size_t n, float lr, float beta1,
+                    float beta2, float eps, int step, void* stream) {
+  if (!param || !grad || !m || !v) return SENSE_EINVAL_PTR;
+  if (step < 1 || !(lr >= 0.f)) return SENSE_EINVAL_ARG;
+  const float c1 = (float)(1.0 - std::pow((double)beta1, step));
+  const float c2 = (float)(1.0 - std::pow((double)beta2, step));
+  k_adam<float><<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      n, param, grad, m, v, lr, beta1, beta2, eps, c1, c2, -INFINITY);
+  prof_count(1);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int adam_update_f64(double* param, double* grad, double* m, double* v, size_t n, double lr, double beta1,
+                    double beta2, double eps, int step, double lower, void* stream) {
+  if (!param || !grad || !m || !v) return SENSE_EINVAL_PTR;
+  if (step < 1 || !(lr >= 0.0)) return SENSE_EINVAL_ARG;
+  const double c1 = 1.0 - std::pow(beta1, step), c2 = 1.0 - std::pow(beta2, step);
+  k_adam<double><<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      n, param, grad, m, v, lr, beta1, beta2, eps, c1, c2, lower);
+  prof_count(1);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+}  // extern "C"

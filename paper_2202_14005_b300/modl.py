@@ -1,0 +1,85 @@
+"""MoDL training and inference on the libsense C ABI (call sequencing only).
+
+One training step (Eq. 6, Sec. 2.3.2): x^0 = A^H y; K unrolled blocks
+x^{t+1} = S_lambda^{-1}(A^H y + lambda D_W(x^t)) with shared weights; loss
+mean |x^K - x_gt|^2; reverse mode block by block (each block recomputes its
+denoiser activations from its stored input); Adam on the weights and lambda.
+Every arithmetic step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from .denoiser import ModlDenoiser
+from .sense import SensePlan
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class ModlTrainer:
+    def __init__(self, maps: torch.Tensor, mask: torch.Tensor, weights: torch.Tensor, lam: float,
+                 K: int, cg_iters: int, lr: float = 1e-4, lam_lr: float = 1e-4):
+        self.plan = SensePlan(maps, mask)
+        B, H, W = self.plan.img_shape()
+        self.B, self.H, self.W = B, H, W
+        self.K, self.iters = K, cg_iters
+        self.dn = ModlDenoiser(B, H, W, device=maps.device)
+        self.weights = weights
+        self.lam = torch.tensor([lam], dtype=torch.float64, device=maps.device)
+        dev = maps.device
+        self.gw = torch.zeros_like(weights)
+        self.gl = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.m_w, self.v_w = torch.zeros_like(weights), torch.zeros_like(weights)
+        self.m_l, self.v_l = torch.zeros_like(self.lam), torch.zeros_like(self.lam)
+        self.xs = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(K + 1)]
+        self.g = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(2)]
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.lr, self.lam_lr = lr, lam_lr
+        self.t = 0
+        self._lib = _lib.lib()
+
+    def _step_args(self):
+        return (self.plan._h, _lib.DENOISER_MODL, _p(self.weights), _p(self.lam))
+
+    def forward(self, y: torch.Tensor) -> torch.Tensor:
+        """x^K for k-space y [B, C, H, W] (also keeps every x^t)."""
+        self.plan._sync_stream()
+        self.plan.adjoint(y, out=self.xs[0])
+        h, kind, w, lam = self._step_args()
+        for t in range(self.K):
+            _lib.check("unrolled_step", self._lib.unrolled_step(
+                h, kind, w, lam, _p(self.xs[0]), _p(self.xs[t]), _p(self.xs[t + 1]), self.iters,
+                _p(self.dn.ws), self.dn.ws.numel()))
+        return self.xs[self.K]
+
+    def gradients(self, y: torch.Tensor, gt: torch.Tensor):
+        """Forward, loss and reverse mode; gradients accumulate into self.gw / self.gl."""
+        self.forward(y)
+        _lib.check("sense_mse_loss", self._lib.sense_mse_loss(
+            self.plan._h, _p(self.xs[self.K]), _p(gt), _p(self.loss), _p(self.g[0])))
+        h, kind, w, lam = self._step_args()
+        cur = 0
+        for t in range(self.K - 1, -1, -1):
+            _lib.check("unrolled_step_backward", self._lib.unrolled_step_backward(
+                h, kind, w, lam, _p(self.xs[0]), _p(self.xs[t]), _p(self.xs[t + 1]), _p(self.g[cur]),
+                _p(self.g[cur ^ 1]), _p(self.gw), _p(self.gl), self.iters, _p(self.dn.ws),
+                self.dn.ws.numel()))
+            cur ^= 1
+        return self.loss
+
+    def train_step(self, y: torch.Tensor, gt: torch.Tensor):
+        loss = self.gradients(y, gt)
+        self.t += 1
+        st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _lib.check("adam_update_f32", self._lib.adam_update_f32(
+            _p(self.weights), _p(self.gw), _p(self.m_w), _p(self.v_w), self.weights.numel(),
+            self.lr, 0.9, 0.999, 1e-8, self.t, st))
+        _lib.check("adam_update_f64", self._lib.adam_update_f64(
+            _p(self.lam), _p(self.gl), _p(self.m_l), _p(self.v_l), 1, self.lam_lr, 0.9, 0.999, 1e-8,
+            self.t, 1e-6, st))
+        return loss

@@ -137,16 +137,6 @@ class SensePlan:
             _ptr(v), _ptr(gl)))
         return v, gl
 
-    def profile(self, enable: bool = True) -> None:
-        _lib.check("sense_plan_profile", self._lib.sense_plan_profile(self._h, 1 if enable else 0))
-
-    def profile_read(self):
-        """(ms in timed fused-normal launches, their count, kernels launched) since the last read."""
-        ms, n, k = C.c_double(), C.c_int(), C.c_longlong()
-        _lib.check("sense_plan_profile_read", self._lib.sense_plan_profile_read(
-            self._h, C.byref(ms), C.byref(n), C.byref(k)))
-        return ms.value, n.value, k.value
-
     def status(self) -> int:
         v = C.c_int()
         _lib.check("sense_get_status", self._lib.sense_get_status(self._h, C.byref(v)))
