@@ -293,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
     kern = {
         "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks),
         "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks),
-        "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("alu", conv_flops), pk, clocks),
+        "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("tensor", conv_flops), pk, clocks),
     }
     kern = {k: v for k, v in kern.items() if v}
     total_kernel_ms = {k: prof[k][0] for k in prof}

@@ -509,72 +509,134 @@ __global__ void k_reduce_partials(const float* partial, int nchunks, int stride,
   else gb[i - nw] += s;
 }
 
-// 64 -> 64 layer weight gradient on CUDA cores:
+// 64 -> 64 layer weight gradient on the warp-level tensor-core path
+// (mma.sync m16n8k16, BF16 in, FP32 accumulate):
 //   gw[co][ci][tap] = sum_p g[p][co] * a[p + s_tap][ci],  gb[co] = sum_p g[p][co].
-// CTA: one tap, one chunk of rows; 256 threads as a 16 x 16 grid each owning a
-// 4 x 4 block of (co, ci).  Pixels are staged 32 at a time in shared memory.
-constexpr int kW64Rows = 8;
+// CTA = one row of taps (dy) x one chunk of kW64Rows image rows of one slice;
+// its 8 warps tile D = [64 co] x [3 taps x 64 ci]: warp w owns co rows
+// 16*(w%4).. and 96 columns starting at 96*(w/4).  Pixels stream through shared
+// memory 32 at a time (cp.async, double buffered): the output-gradient tile
+// [32 px][64 co] and three shifted activation tiles [32 px][64 ci] (zero
+// outside the image).  Operands reach the MMA through ldmatrix.trans from the
+// channels-last tiles.  Per-chunk partial sums are reduced in fixed order.
+constexpr int kW64Rows = 4;
 constexpr int kW64Px = 32;
+constexpr int kW64Ld = 72;  // padded row (bf16) of the staged tiles: conflict-free ldmatrix
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const uint32_t d = smem_u32(dst);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 
 __global__ void __launch_bounds__(256) k_wgrad64(int B, int H, int W, const __nv_bfloat16* g,
                                                  const __nv_bfloat16* act, float* partial) {
-  const int tap = blockIdx.y;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int dy = blockIdx.y;  // tap row 0..2
   const int chunks_per_slice = (H + kW64Rows - 1) / kW64Rows;
   const int b = blockIdx.x / chunks_per_slice;
   const int h0 = (blockIdx.x % chunks_per_slice) * kW64Rows;
   const int h1 = min(h0 + kW64Rows, H);
-  __shared__ float s_g[kW64Px][CH + 1];
-  __shared__ float s_a[kW64Px][CH + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ci block tx, co block ty
-  float acc[4][4];
-  float bacc = 0.f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
   const int npx = (h1 - h0) * W;
-  for (int q0 = 0; q0 < npx; q0 += kW64Px) {
-    for (int i = threadIdx.x; i < kW64Px * CH; i += blockDim.x) {
-      const int pp = i / CH, ch = i % CH;
-      const int q = q0 + pp;
-      float gv = 0.f, av = 0.f;
-      if (q < npx) {
-        const int h = h0 + q / W, w = q % W;
-        gv = bf(g[(((size_t)b * H + h) * W + w) * CH + ch]);
-        const int yy = h + dy, xx = w + dx;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) av = bf(act[(((size_t)b * H + yy) * W + xx) * CH + ch]);
-      }
-      s_g[pp][ch] = gv;
-      s_a[pp][ch] = av;
+  __shared__ __align__(16) __nv_bfloat16 s_g[2][kW64Px][kW64Ld];
+  __shared__ __align__(16) __nv_bfloat16 s_a[2][3][kW64Px][kW64Ld];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mrow = (warp & 3) * 16;   // co base
+  const int ncol = (warp >> 2) * 96;  // column base in [3 taps x 64 ci]
+
+  // staging: thread tid copies 16-B chunk (tid & 7) of pixel (tid >> 3) of each tile
+  auto stage = [&](int buf, int q0) {
+    const int pp = tid >> 3, ch = (tid & 7) * 8;
+    const int q = q0 + pp;
+    const bool in = q < npx;
+    const int h = h0 + (in ? q / W : 0), w = in ? q % W : 0;
+    const size_t pix = ((size_t)b * H + h) * W + w;
+    cp_async16(&s_g[buf][pp][ch], g + pix * CH + ch, in);
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      const int yy = h + dy - 1, xx = w + dx - 1;
+      const bool ok = in && yy >= 0 && yy < H && xx >= 0 && xx < W;
+      const size_t pa = ok ? (((size_t)b * H + yy) * W + xx) : 0;
+      cp_async16(&s_a[buf][dx][pp][ch], act + pa * CH + ch, ok);
+    }
+    cp_async_commit();
+  };
+
+  float acc[12][4];
+#pragma unroll
+  for (int j = 0; j < 12; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+  float bacc = 0.f;
+
+  const int nsteps = (npx + kW64Px - 1) / kW64Px;
+  if (nsteps > 0) stage(0, 0);
+  for (int it = 0; it < nsteps; ++it) {
+    const int buf = it & 1;
+    if (it + 1 < nsteps) {
+      stage(buf ^ 1, (it + 1) * kW64Px);
+      cp_async_wait1();
+    } else {
+      cp_async_wait0();
     }
     __syncthreads();
-#pragma unroll 4
-    for (int pp = 0; pp < kW64Px; ++pp) {
-      float gg[4], aa[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        gg[i] = s_g[pp][ty * 4 + i];
-        aa[i] = s_a[pp][tx * 4 + i];
+    for (int kk = 0; kk < kW64Px; kk += 16) {
+      // A = g^T (rows co, cols px): matrices (m0,k0), (m8,k0), (m0,k8), (m8,k8)
+      uint32_t af[4];
+      {
+        const int mi = lane >> 3, r = lane & 7;
+        const int m0 = (mi & 1) * 8, k0 = (mi >> 1) * 8;
+        ldsm_x4_t(af, &s_g[buf][kk + k0 + r][mrow + m0]);
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(gg[i], aa[k], acc[i][k]);
+      for (int nb = 0; nb < 6; ++nb) {
+        // 16 columns = two n-tiles; column c -> (tap dx, ci)
+        const int c0 = ncol + nb * 16;
+        const int dx = c0 / 64, ci0 = c0 % 64;
+        uint32_t bfr[4];
+        const int mi = lane >> 3, r = lane & 7;
+        const int k0 = (mi & 1) * 8, n0 = (mi >> 1) * 8;
+        ldsm_x4_t(bfr, &s_a[buf][dx][kk + k0 + r][ci0 + n0]);
+        mma_bf16_16816(acc[2 * nb], af, bfr[0], bfr[1]);
+        mma_bf16_16816(acc[2 * nb + 1], af, bfr[2], bfr[3]);
+      }
     }
-    if (tap == 4 && threadIdx.x < CH)
-      for (int pp = 0; pp < kW64Px; ++pp) bacc += s_g[pp][threadIdx.x];
+    if (dy == 1 && tid < CH)
+      for (int pp = 0; pp < kW64Px; ++pp) bacc += bf(s_g[buf][pp][tid]);
     __syncthreads();
   }
-  // partial layout per (chunk, tap): [co][ci] 4096 floats, bias (tap 4 only) after all taps
-  float* out = partial + ((size_t)blockIdx.x * 9 + tap) * (CH * CH);
+  // D fragment: rows mrow + lane/4 (+8), cols 2*(lane%4) (+1) of each 8-column tile
+  const int gr = lane >> 2, gc = (lane & 3) * 2;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[(ty * 4 + i) * CH + tx * 4 + k] = acc[i][k];
-  if (tap == 4 && threadIdx.x < CH) {
+  for (int j = 0; j < 12; ++j) {
+    const int c = ncol + j * 8 + gc;
+    const int dx = c / 64, ci = c % 64;
+    const int tap = dy * 3 + dx;
+    float* out = partial + ((size_t)blockIdx.x * 9 + tap) * (CH * CH);
+    out[(mrow + gr) * CH + ci] = acc[j][0];
+    out[(mrow + gr) * CH + ci + 1] = acc[j][1];
+    out[(mrow + gr + 8) * CH + ci] = acc[j][2];
+    out[(mrow + gr + 8) * CH + ci + 1] = acc[j][3];
+  }
+  if (dy == 1 && tid < CH) {
     const int nchunks = gridDim.x;
-    partial[(size_t)nchunks * 9 * CH * CH + (size_t)blockIdx.x * CH + threadIdx.x] = bacc;
+    partial[(size_t)nchunks * 9 * CH * CH + (size_t)blockIdx.x * CH + tid] = bacc;
   }
 }
 
@@ -789,7 +851,7 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   int cur = 0;
   for (int l = 2; l >= 0; --l) {
     const __nv_bfloat16* ain = act[l];  // input activation of this layer
-    dim3 gw(L.nch64, 9);
+    dim3 gw(L.nch64, 3);
     prof_mark("wgrad64", st, false);
     k_wgrad64<<<gw, 256, 0, st>>>(B, H, W, gbuf[cur], ain, p64);
     prof_mark("wgrad64", st, true);
