@@ -307,49 +307,66 @@ __global__ void __launch_bounds__(256) k_l1_fwd(int B, int H, int W, const float
   }
 }
 
-// Load the 64 BF16 channels of pixel (yy, xx) (zero outside the image) as floats.
-__device__ __forceinline__ void load_px64(const __nv_bfloat16* t, int b, int yy, int xx, int H, int W,
-                                          float (&v)[CH]) {
-  if (yy < 0 || yy >= H || xx < 0 || xx >= W) {
-#pragma unroll
-    for (int i = 0; i < CH; ++i) v[i] = 0.f;
-    return;
+// Shared-memory halo of a 64-channel BF16 tensor: rows h-1..h+1, pixels
+// w0-1 .. w0+kTw (zero outside the image), rows padded to 144 bytes so that
+// consecutive threads reading consecutive pixels hit distinct banks.
+constexpr int kTw = 128;
+constexpr int kHaloLd = 72;  // bf16 per padded pixel row
+constexpr int kHaloSmem = 3 * (kTw + 2) * kHaloLd * 2;
+
+__device__ __forceinline__ void stage_halo64(__nv_bfloat16* s, const __nv_bfloat16* t, int b, int h, int w0,
+                                             int H, int W) {
+  for (int i = threadIdx.x; i < 3 * (kTw + 2) * 8; i += blockDim.x) {
+    const int q = i & 7, px = (i >> 3) % (kTw + 2), r = (i >> 3) / (kTw + 2);
+    const int yy = h - 1 + r, xx = w0 - 1 + px;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+      v = reinterpret_cast<const uint4*>(t + (((size_t)b * H + yy) * W + xx) * CH)[q];
+    reinterpret_cast<uint4*>(s + (r * (kTw + 2) + px) * kHaloLd)[q] = v;
   }
-  const uint4* p = reinterpret_cast<const uint4*>(t + (((size_t)b * H + yy) * W + xx) * CH);
+}
+
+// 64 -> 2 contraction over the 3x3 neighbourhood from the halo: s[c] +=
+// sum_{tap, ch} wt[(c * 64 + ch) * 9 + tap'] * halo(tap), tap' = flipped taps if flip.
+__device__ __forceinline__ void contract64to2(const __nv_bfloat16* halo, const float* s_w, int t, bool flip,
+                                              float& s0, float& s1) {
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap % 3;
+    const int r = flip ? 2 - dy : dy, c = flip ? t + 2 - dx : t + dx;
+    const uint4* row = reinterpret_cast<const uint4*>(halo + (r * (kTw + 2) + c) * kHaloLd);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const uint4 u = p[q];
-    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+    for (int q = 0; q < 8; ++q) {
+      const uint4 u = row[q];
+      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float2 f = __bfloat1622float2(h2[e]);
-      v[q * 8 + 2 * e] = f.x;
-      v[q * 8 + 2 * e + 1] = f.y;
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(h2[e]);
+        const int ch = q * 8 + 2 * e;
+        s0 = fmaf(s_w[(0 * CH + ch) * 9 + tap], f.x, s0);
+        s0 = fmaf(s_w[(0 * CH + ch + 1) * 9 + tap], f.y, s0);
+        s1 = fmaf(s_w[(1 * CH + ch) * 9 + tap], f.x, s1);
+        s1 = fmaf(s_w[(1 * CH + ch + 1) * 9 + tap], f.y, s1);
+      }
     }
   }
 }
 
 // Last layer (64 -> 2) plus the residual: out[p] = x[p] + (b5 + sum_{ci,tap} w5[c][ci][tap] a4[p+s][ci]).
-__global__ void __launch_bounds__(128) k_l5_fwd(int B, int H, int W, const __nv_bfloat16* a4,
-                                                const float* w5, const float* b5, const float2* x,
-                                                float2* out) {
-  __shared__ float s_w[2 * CH * 9];
+__global__ void __launch_bounds__(kTw) k_l5_fwd(int B, int H, int W, const __nv_bfloat16* a4, const float* w5,
+                                               const float* b5, const float2* x, float2* out) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);
+  float* s_w = reinterpret_cast<float*>(dsm + kHaloSmem);
+  const int bh = blockIdx.y, b = bh / H, h = bh % H, w0 = blockIdx.x * kTw;
   for (int i = threadIdx.x; i < 2 * CH * 9; i += blockDim.x) s_w[i] = w5[i];
+  stage_halo64(halo, a4, b, h, w0, H, W);
   __syncthreads();
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (size_t)B * H * W) return;
-  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
+  const int w = w0 + threadIdx.x;
+  if (w >= W) return;
   float s0 = b5[0], s1 = b5[1];
-#pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    float v[CH];
-    load_px64(a4, b, h + tap / 3 - 1, w + tap % 3 - 1, H, W, v);
-#pragma unroll
-    for (int ci = 0; ci < CH; ++ci) {
-      s0 = fmaf(s_w[(0 * CH + ci) * 9 + tap], v[ci], s0);
-      s1 = fmaf(s_w[(1 * CH + ci) * 9 + tap], v[ci], s1);
-    }
-  }
+  contract64to2(halo, s_w, threadIdx.x, false, s0, s1);
+  const size_t p = ((size_t)b * H + h) * W + w;
   const float2 xv = x[p];
   out[p] = make_float2(xv.x + s0, xv.y + s1);
 }
@@ -400,44 +417,78 @@ __global__ void __launch_bounds__(128) k_l5_dgrad(int B, int H, int W, const flo
 
 // Input gradient of the first layer plus the residual path:
 //   gx[p][c] = gout[p][c] + sum_{co,tap} w1[co][c][tap] g1[p - s_tap][co]
-__global__ void __launch_bounds__(128) k_l1_dgrad(int B, int H, int W, const __nv_bfloat16* g1,
-                                                  const float* w1, const float2* gout, float2* gx) {
-  __shared__ float s_w[CH * 18];
-  for (int i = threadIdx.x; i < CH * 18; i += blockDim.x) s_w[i] = w1[i];
-  __syncthreads();
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (size_t)B * H * W) return;
-  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
-  float s0 = 0.f, s1 = 0.f;
-#pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    float v[CH];
-    load_px64(g1, b, h - (tap / 3 - 1), w - (tap % 3 - 1), H, W, v);
-#pragma unroll
-    for (int co = 0; co < CH; ++co) {
-      s0 = fmaf(s_w[(co * 2 + 0) * 9 + tap], v[co], s0);
-      s1 = fmaf(s_w[(co * 2 + 1) * 9 + tap], v[co], s1);
-    }
+// (w1 is read transposed into the [c][co][tap] order of contract64to2).
+__global__ void __launch_bounds__(kTw) k_l1_dgrad(int B, int H, int W, const __nv_bfloat16* g1,
+                                                 const float* w1, const float2* gout, float2* gx) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);
+  float* s_w = reinterpret_cast<float*>(dsm + kHaloSmem);
+  const int bh = blockIdx.y, b = bh / H, h = bh % H, w0 = blockIdx.x * kTw;
+  for (int i = threadIdx.x; i < 2 * CH * 9; i += blockDim.x) {
+    const int c = i / (CH * 9), co = (i / 9) % CH, tap = i % 9;
+    s_w[i] = w1[(co * 2 + c) * 9 + tap];
   }
+  stage_halo64(halo, g1, b, h, w0, H, W);
+  __syncthreads();
+  const int w = w0 + threadIdx.x;
+  if (w >= W) return;
+  float s0 = 0.f, s1 = 0.f;
+  contract64to2(halo, s_w, threadIdx.x, true, s0, s1);
+  const size_t p = ((size_t)b * H + h) * W + w;
   const float2 go = gout[p];
   gx[p] = make_float2(go.x + s0, go.y + s1);
 }
 
 // --------------------------------------------------- weight gradients (CUDA cores)
-// Small layers, per chunk of R image rows of one slice:
+// Small layers, one image row of one slice per CTA (partials reduced later):
 //  L1 (first):  gw[co][c][tap] = sum_p g1[p][co] * xr[p + s][c],  gb[co] = sum_p g1[p][co]
 //  L5 (last):   gw[co][ci][tap] = sum_p g5[p][co] * a4[p + s][ci], gb[co] = sum_p g5[p][co]
-// Thread j < 64 owns the 64-channel index (co for L1, ci for L5) and 18 (+1) sums;
-// the four thread groups take every fourth pixel and are added in fixed order.
-constexpr int kSmallRows = 4;
+// Thread j < 64 of each of the four groups owns the 64-channel index (co for
+// L1, ci for L5) and 18 (+1) sums over every fourth pixel of the row, all
+// operands in shared memory; the groups are added in fixed order.
 constexpr int kSmallOut = CH * 18 + CH;  // 1152 weights + up to 64 biases
 
-__global__ void __launch_bounds__(256) k_wgrad_small(int B, int H, int W, int last, const __nv_bfloat16* U,
-                                                     const float2* V, float* partial) {
-  const int chunks_per_slice = (H + kSmallRows - 1) / kSmallRows;
-  const int b = blockIdx.x / chunks_per_slice;
-  const int h0 = (blockIdx.x % chunks_per_slice) * kSmallRows;
-  const int h1 = min(h0 + kSmallRows, H);
+__device__ void small_partial_out(float (&acc)[2][9], float bacc, int last, float* out) {
+  __shared__ float s_red[4][CH * 19];
+  const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) s_red[grp][j * 19 + c * 9 + t] = acc[c][t];
+  s_red[grp][j * 19 + 18] = bacc;
+  __syncthreads();
+  for (int i = threadIdx.x; i < CH * 19; i += blockDim.x) {
+    const float v = ((s_red[0][i] + s_red[1][i]) + s_red[2][i]) + s_red[3][i];
+    const int jj = i / 19, r = i % 19;
+    if (r == 18) {
+      out[CH * 18 + jj] = v;
+    } else {
+      const int c = r / 9, tap = r % 9;
+      out[!last ? ((jj * 2 + c) * 9 + tap) : ((c * CH + jj) * 9 + tap)] = v;
+    }
+  }
+}
+
+// L1: U = g1 row h [W][64] (bf16), V = bf16-rounded x on rows h-1..h+1 [3][W+2] (float2).
+__global__ void __launch_bounds__(256) k_wgrad_l1(int B, int H, int W, const __nv_bfloat16* g1,
+                                                  const float2* x, float* partial) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  __nv_bfloat16* su = reinterpret_cast<__nv_bfloat16*>(dsm);
+  float2* sv = reinterpret_cast<float2*>(dsm + (((size_t)W * CH * 2 + 15) & ~(size_t)15));
+  const int b = blockIdx.x / H, h = blockIdx.x % H;
+  const uint4* src = reinterpret_cast<const uint4*>(g1 + ((size_t)b * H + h) * W * CH);
+  for (int i = threadIdx.x; i < W * 8; i += blockDim.x) reinterpret_cast<uint4*>(su)[i] = src[i];
+  for (int i = threadIdx.x; i < 3 * (W + 2); i += blockDim.x) {
+    const int r = i / (W + 2), px = i % (W + 2);
+    const int yy = h - 1 + r, xx = px - 1;
+    float2 v = make_float2(0.f, 0.f);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+      v = x[((size_t)b * H + yy) * W + xx];
+      v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
+    }
+    sv[i] = v;
+  }
+  __syncthreads();
   const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
   float acc[2][9];
   float bacc = 0.f;
@@ -445,56 +496,54 @@ __global__ void __launch_bounds__(256) k_wgrad_small(int B, int H, int W, int la
   for (int c = 0; c < 2; ++c)
 #pragma unroll
     for (int t = 0; t < 9; ++t) acc[c][t] = 0.f;
-  const int npx = (h1 - h0) * W;
-  for (int q = grp; q < npx; q += 4) {
-    const int h = h0 + q / W, w = q % W;
-    const size_t p = ((size_t)b * H + h) * W + w;
-    if (!last) {
-      // L1: U = g1 (unshifted), V = x rounded to bf16 (shifted)
-      const float u = bf(U[p * CH + j]);
-      bacc += u;
+  for (int w = grp; w < W; w += 4) {
+    const float u = bf(su[w * CH + j]);
+    bacc += u;
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int yy = h + tap / 3 - 1, xx = w + tap % 3 - 1;
-        float2 v = make_float2(0.f, 0.f);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = V[((size_t)b * H + yy) * W + xx];
-        acc[0][tap] = fmaf(u, bf(__float2bfloat16_rn(v.x)), acc[0][tap]);
-        acc[1][tap] = fmaf(u, bf(__float2bfloat16_rn(v.y)), acc[1][tap]);
-      }
-    } else {
-      // L5: V = g5 (unshifted, 2 channels), U = a4 (shifted)
-      const float2 v = V[p];
-      if (j < 2) bacc += (j == 0) ? v.x : v.y;
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int yy = h + tap / 3 - 1, xx = w + tap % 3 - 1;
-        float u = 0.f;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) u = bf(U[(((size_t)b * H + yy) * W + xx) * CH + j]);
-        acc[0][tap] = fmaf(v.x, u, acc[0][tap]);
-        acc[1][tap] = fmaf(v.y, u, acc[1][tap]);
-      }
+    for (int tap = 0; tap < 9; ++tap) {
+      const float2 v = sv[(tap / 3) * (W + 2) + w + tap % 3];
+      acc[0][tap] = fmaf(u, v.x, acc[0][tap]);
+      acc[1][tap] = fmaf(u, v.y, acc[1][tap]);
     }
   }
-  __shared__ float s_red[4][CH * 19];
+  small_partial_out(acc, bacc, 0, partial + (size_t)blockIdx.x * kSmallOut);
+}
+
+// L5: U = a4 on rows h-1..h+1 [3][W+2][64] (bf16), V = g5 row h [W] (float2).
+__global__ void __launch_bounds__(256) k_wgrad_l5(int B, int H, int W, const __nv_bfloat16* a4,
+                                                  const float2* g5, float* partial) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  __nv_bfloat16* su = reinterpret_cast<__nv_bfloat16*>(dsm);
+  float2* sv = reinterpret_cast<float2*>(dsm + (size_t)3 * (W + 2) * CH * 2);
+  const int b = blockIdx.x / H, h = blockIdx.x % H;
+  for (int i = threadIdx.x; i < 3 * (W + 2) * 8; i += blockDim.x) {
+    const int q = i & 7, px = (i >> 3) % (W + 2), r = (i >> 3) / (W + 2);
+    const int yy = h - 1 + r, xx = px - 1;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+      v = reinterpret_cast<const uint4*>(a4 + (((size_t)b * H + yy) * W + xx) * CH)[q];
+    reinterpret_cast<uint4*>(su)[(r * (W + 2) + px) * 8 + q] = v;
+  }
+  for (int i = threadIdx.x; i < W; i += blockDim.x) sv[i] = g5[((size_t)b * H + h) * W + i];
+  __syncthreads();
+  const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
+  float acc[2][9];
+  float bacc = 0.f;
 #pragma unroll
   for (int c = 0; c < 2; ++c)
 #pragma unroll
-    for (int t = 0; t < 9; ++t) s_red[grp][j * 19 + c * 9 + t] = acc[c][t];
-  s_red[grp][j * 19 + 18] = bacc;
-  __syncthreads();
-  float* out = partial + (size_t)blockIdx.x * kSmallOut;
-  for (int i = threadIdx.x; i < CH * 19; i += blockDim.x) {
-    const float s = ((s_red[0][i] + s_red[1][i]) + s_red[2][i]) + s_red[3][i];
-    const int jj = i / 19, r = i % 19;
-    if (r == 18) {
-      out[CH * 18 + jj] = s;
-    } else {
-      const int c = r / 9, tap = r % 9;
-      // weight index in [Cout][Cin][tap] order
-      const int widx = !last ? ((jj * 2 + c) * 9 + tap) : ((c * CH + jj) * 9 + tap);
-      out[widx] = s;
+    for (int t = 0; t < 9; ++t) acc[c][t] = 0.f;
+  for (int w = grp; w < W; w += 4) {
+    const float2 v = sv[w];
+    if (j < 2) bacc += (j == 0) ? v.x : v.y;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const float u = bf(su[((tap / 3) * (W + 2) + w + tap % 3) * CH + j]);
+      acc[0][tap] = fmaf(v.x, u, acc[0][tap]);
+      acc[1][tap] = fmaf(v.y, u, acc[1][tap]);
     }
   }
+  small_partial_out(acc, bacc, 1, partial + (size_t)blockIdx.x * kSmallOut);
 }
 
 // Deterministic sum over chunks, added to the caller's gradient buffers.
@@ -642,12 +691,12 @@ __global__ void __launch_bounds__(256) k_wgrad64(int B, int H, int W, const __nv
 
 // Sum the 64x64-layer partials over chunks in fixed order into gw [co][ci][tap] and gb.
 __global__ void k_reduce_wgrad64(const float* partial, int nchunks, float* gw, float* gb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // i = (tap, co, ci), ci fastest: coalesced reads
   if (i < CH * CH * 9) {
-    const int co = i / (CH * 9), ci = (i / 9) % CH, tap = i % 9;
+    const int tap = i / (CH * CH), co = (i / CH) % CH, ci = i % CH;
     float s = 0.f;
     for (int c = 0; c < nchunks; ++c) s += partial[((size_t)c * 9 + tap) * (CH * CH) + co * CH + ci];
-    gw[i] += s;
+    gw[(co * CH + ci) * 9 + tap] += s;
   } else if (i < CH * CH * 9 + CH) {
     const int co = i - CH * CH * 9;
     float s = 0.f;
@@ -691,6 +740,9 @@ int make_act_map(CUtensorMap* m, const void* base, int B, int H, int W) {
 }
 
 int g_num_sms = 0;
+constexpr int kMaxW = 512;  // widest image the denoiser kernels take (shared-memory tiles)
+int wl1_smem(int W) { return (int)((((size_t)W * CH * 2 + 15) & ~(size_t)15) + 3 * (W + 2) * 8); }
+int wl5_smem(int W) { return 3 * (W + 2) * CH * 2 + W * 8; }
 
 int conv_prepare() {
   static int state = 0;  // 0 unknown, 1 ok, -1 failed
@@ -701,6 +753,14 @@ int conv_prepare() {
     state = (cudaGetDevice(&dev) == cudaSuccess &&
              cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
              cudaFuncSetAttribute(k_conv64, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(k_l5_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kHaloSmem + 2 * CH * 9 * 4) == cudaSuccess &&
+             cudaFuncSetAttribute(k_l1_dgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kHaloSmem + 2 * CH * 9 * 4) == cudaSuccess &&
+             cudaFuncSetAttribute(k_wgrad_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, wl1_smem(kMaxW)) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(k_wgrad_l5, cudaFuncAttributeMaxDynamicSharedMemorySize, wl5_smem(kMaxW)) ==
                  cudaSuccess)
                 ? 1
                 : -1;
@@ -735,7 +795,7 @@ struct DnLayout {
 DnLayout dn_layout(int B, int H, int W) {
   DnLayout L;
   const size_t act = up256((size_t)B * H * W * CH * 2);
-  L.nch_small = B * ((H + kSmallRows - 1) / kSmallRows);
+  L.nch_small = B * H;
   L.nch64 = B * ((H + kW64Rows - 1) / kW64Rows);
   size_t o = 0;
   for (int i = 0; i < 3; ++i) { L.wf[i] = o; o += up256(WPACK_BYTES); }
@@ -755,6 +815,7 @@ int check_common(int kind, const void* weights, const void* x, void* ws, size_t 
                  int W) {
   if (kind != SENSE_DENOISER_MODL) return SENSE_EUNSUPPORTED;
   if (B <= 0 || H <= 0 || W <= 0) return SENSE_EINVAL_SHAPE;
+  if (W > kMaxW || (W & 1)) return SENSE_EUNSUPPORTED;
   if (!weights || !x || !ws || !al16(weights) || !al16(x) || ((uintptr_t)ws & 255u)) return SENSE_EINVAL_PTR;
   if (ws_bytes < dn_layout(B, H, W).total) return SENSE_EWORKSPACE;
   return conv_prepare();
@@ -777,8 +838,8 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
                               nullptr, act[l + 1], 0, B, H, W, status, st))
       return e;
   if (out)
-    k_l5_fwd<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, act[3], wts + o.w[4], wts + o.b[4], x,
-                                                            out);
+    k_l5_fwd<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kHaloSmem + 2 * CH * 9 * 4, st>>>(
+        B, H, W, act[3], wts + o.w[4], wts + o.b[4], x, out);
   prof_count(4 + (out ? 1 : 0));  // packing x3, first layer, last layer (convolutions counted apart)
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -837,13 +898,13 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   float* ps = reinterpret_cast<float*>(w8 + L.part_small);
   float* p64 = reinterpret_cast<float*>(w8 + L.part64);
   int* status = reinterpret_cast<int*>(w8 + L.status);
-  const size_t npx = (size_t)B * H * W;
   for (int l = 0; l < 3; ++l)
     k_pack64<<<(9 * 8 * CH * 8 + 255) / 256, 256, 0, st>>>(weights + o.w[l + 1],
                                                           reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), 1);
   // last layer: input gradient (masked by a4 > 0) and weight gradient
+  const size_t npx = (size_t)B * H * W;
   k_l5_dgrad<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, go, weights + o.w[4], act[3], gbuf[0]);
-  k_wgrad_small<<<L.nch_small, 256, 0, st>>>(B, H, W, 1, act[3], go, ps);
+  k_wgrad_l5<<<L.nch_small, 256, wl5_smem(W), st>>>(B, H, W, act[3], go, ps);
   k_reduce_partials<<<(2 * CH * 9 + 2 + 255) / 256, 256, 0, st>>>(ps, L.nch_small, kSmallOut, 2 * CH * 9,
                                                                  grad_weights + o.w[4], 2, CH * 18,
                                                                  grad_weights + o.b[4]);
@@ -863,12 +924,12 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
     cur ^= 1;
   }
   // first layer: weight gradient and input gradient (+ residual)
-  k_wgrad_small<<<L.nch_small, 256, 0, st>>>(B, H, W, 0, gbuf[cur], xx, ps);
+  k_wgrad_l1<<<L.nch_small, 256, wl1_smem(W), st>>>(B, H, W, gbuf[cur], xx, ps);
   k_reduce_partials<<<(CH * 18 + CH + 255) / 256, 256, 0, st>>>(ps, L.nch_small, kSmallOut, CH * 18,
                                                                grad_weights + o.w[0], CH, CH * 18,
                                                                grad_weights + o.b[0]);
-  k_l1_dgrad<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, gbuf[cur], weights + o.w[0], go,
-                                                            static_cast<float2*>(grad_x));
+  k_l1_dgrad<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kHaloSmem + 2 * CH * 9 * 4, st>>>(
+      B, H, W, gbuf[cur], weights + o.w[0], go, static_cast<float2*>(grad_x));
   prof_count(15);  // every launch of the backward except the three tensor-core convolutions
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
