@@ -102,21 +102,34 @@ __device__ void last_block(const RowArgs& a) {
   }
 }
 
-// One warp per image row; elements taken two at a time (float4 = 2 complex).
+// Two warps per image row (four rows per 256-thread CTA); elements are taken
+// two at a time (float4 = 2 complex).  Each warp reduces its FP32 lane sums in
+// FP64; the two warp sums of a row are added in warp order.
+constexpr int kRowsPerCta = kWarps / 2;
+
+__device__ __forceinline__ void row_partial(const RowArgs& a, int row, bool rv, float part) {
+  __shared__ double s_w[kWarps];
+  const double d = warp_sum_d((double)part);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) s_w[warp] = d;
+  __syncthreads();
+  if (rv && a.part && (threadIdx.x & 63) == 0) a.part[row] = s_w[warp] + s_w[warp + 1];
+}
+
 #define ROW_LOOP_BEGIN                                                    \
-  const int row = blockIdx.x * kWarps + (threadIdx.x >> 5);               \
-  const int lane = threadIdx.x & 31;                                      \
-  if (row < a.B * a.H) {                                                  \
+  const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 6);          \
+  const int lt = threadIdx.x & 63;                                        \
+  const bool rv = row < a.B * a.H;                                        \
+  float part = 0.f;                                                       \
+  if (rv) {                                                               \
     const int b = row / a.H;                                              \
     (void)b;                                                              \
     const size_t off = (size_t)row * a.W / 2;                             \
-    float part = 0.f;                                                     \
-    for (int i = lane; i < a.W / 2; i += 32) {
+    for (int i = lt; i < a.W / 2; i += 64) {
 #define ROW_LOOP_END                                                      \
     }                                                                     \
-    const double d = warp_sum_d((double)part);                            \
-    if (lane == 0 && a.part) a.part[row] = d;                             \
-  }
+  }                                                                       \
+  row_partial(a, row, rv, part);
 
 __device__ __forceinline__ float nrm2(float4 v) {
   return fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
@@ -211,7 +224,7 @@ RowArgs base_args(sense_plan p) {
   return a;
 }
 
-int grid_rows(sense_plan p) { return (p->B * p->H + kWarps - 1) / kWarps; }
+int grid_rows(sense_plan p) { return (p->B * p->H + kRowsPerCta - 1) / kRowsPerCta; }
 
 }  // namespace
 
@@ -220,7 +233,9 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
   Workspace& w = p->w;
   const int gr = grid_rows(p);
   const int B = p->B;
+  prof_mark("cg_vec", p->stream, false);
   k_lam_expand<<<(B + 127) / 128, 128, 0, p->stream>>>(B, lam, lam_count, w.lam);
+  prof_mark("cg_vec", p->stream, true);
   count_launch(p);
   // ---- initial residual
   if (x0) {
@@ -237,13 +252,17 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
       if (int e = launch_normal_generic(p, x, w.r, 0.f, w.lam)) return e;
       RowArgs a = base_args(p);
       a.a = rhs; a.o1 = w.r; a.fin = FIN_RR0; a.hist = rr_hist;
+      prof_mark("cg_vec", p->stream, false);
       k_resid<<<gr, kWarps * 32, 0, p->stream>>>(a);
+      prof_mark("cg_vec", p->stream, true);
       count_launch(p);
     }
   } else {
     RowArgs a = base_args(p);
     a.a = rhs; a.o1 = w.r; a.o2 = x; a.fin = FIN_RR0; a.hist = rr_hist;
+    prof_mark("cg_vec", p->stream, false);
     k_cg_init<<<gr, kWarps * 32, 0, p->stream>>>(a);
+    prof_mark("cg_vec", p->stream, true);
     count_launch(p);
   }
   // ---- iterations
@@ -257,17 +276,23 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
     } else {
       RowArgs a = base_args(p);
       a.a = w.r; a.o1 = w.p; a.beta = it ? w.beta : nullptr;
+      prof_mark("cg_vec", p->stream, false);
       k_cg_p<<<gr, kWarps * 32, 0, p->stream>>>(a);
+      prof_mark("cg_vec", p->stream, true);
       count_launch(p);
       if (int e = launch_normal_generic(p, w.p, w.q, 0.f, w.lam)) return e;
       RowArgs d = base_args(p);
       d.a = w.p; d.b = w.q; d.fin = FIN_ALPHA;
+      prof_mark("cg_vec", p->stream, false);
       k_dot<<<gr, kWarps * 32, 0, p->stream>>>(d);
+      prof_mark("cg_vec", p->stream, true);
       count_launch(p);
     }
     RowArgs u = base_args(p);
     u.a = w.p; u.b = w.q; u.o1 = x; u.o2 = w.r; u.fin = FIN_RRNEW; u.hist = hist;
+    prof_mark("cg_vec", p->stream, false);
     k_cg_update<<<gr, kWarps * 32, 0, p->stream>>>(u);
+    prof_mark("cg_vec", p->stream, true);
     count_launch(p);
   }
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
@@ -280,7 +305,9 @@ int launch_dot_rows(sense_plan p, const float2* a_, const float2* b_, const floa
   RowArgs a = base_args(p);
   a.a = a_; a.b = b_; a.c = c_; a.fin = FIN_GLAM; a.gout = out; a.gcount = out_count;
   a.gacc = accumulate;
+  prof_mark("cg_vec", p->stream, false);
   k_dot<<<grid_rows(p), kWarps * 32, 0, p->stream>>>(a);
+  prof_mark("cg_vec", p->stream, true);
   count_launch(p);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

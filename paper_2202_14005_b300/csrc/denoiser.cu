@@ -61,17 +61,23 @@ ModlOffsets modl_offsets() {
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
 // ------------------------------------------------------------ weight packing
-// 64->64 layer l into the K-major operand layout [tap][g][n][8] (bf16):
+// 64->64 layers into the K-major operand layout [tap][g][n][8] (bf16), one
+// launch for all six tables (blockIdx.y = 2 * layer + dgrad):
 //   forward:        n = cout, k-chunk g over cin:  W[n][g*8+e][tap]
 //   input gradient: n = cin,  k-chunk g over cout: W[g*8+e][n][8 - tap] (flipped taps)
-__global__ void k_pack64(const float* w, __nv_bfloat16* out, int dgrad) {
+struct PackArgs {
+  const float* w[3];
+  __nv_bfloat16* fwd[3];
+  __nv_bfloat16* dgr[3];
+};
+__global__ void k_pack64(const PackArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9*8*64*8
   if (i >= 9 * 8 * CH * 8) return;
+  const int l = blockIdx.y >> 1, dgrad = blockIdx.y & 1;
+  const float* w = a.w[l];
   const int e = i & 7, n = (i >> 3) & 63, g = (i >> 9) & 7, tap = i >> 12;
-  float v;
-  if (!dgrad) v = w[(n * CH + g * 8 + e) * 9 + tap];
-  else v = w[((g * 8 + e) * CH + n) * 9 + (8 - tap)];
-  out[i] = __float2bfloat16_rn(v);
+  const float v = !dgrad ? w[(n * CH + g * 8 + e) * 9 + tap] : w[((g * 8 + e) * CH + n) * 9 + (8 - tap)];
+  (dgrad ? a.dgr[l] : a.fwd[l])[i] = __float2bfloat16_rn(v);
 }
 
 // ------------------------------------------------------- tcgen05 convolution
@@ -263,47 +269,87 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
   if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
-// ------------------------------------------------ CUDA-core small layers
-// First layer (2 -> 64): a1[p][co] = relu(b1[co] + sum_{c,tap} w1[co][c][tap] xr[p + s_tap][c]),
-// xr = the complex input rounded to BF16 (the network input is a BF16 activation).
-__global__ void __launch_bounds__(256) k_l1_fwd(int B, int H, int W, const float2* x, const float* w1,
-                                                const float* b1, __nv_bfloat16* a1) {
-  __shared__ float s_w[CH * 18];
+// ------------------------------------------------ 2-channel layers
+// All convolution weights are used in BF16 (rounded when packed); sums are FP32.
+
+// 2 -> 64 on CUDA cores, four consecutive pixels of one row per thread so that
+// each weight read serves four pixels.  n[r][q] = 2-channel source at
+// (h - 1 + r, w0 - 1 + q); output channel j of pixel w0 + i:
+//   mode 0 (first layer):   relu(b[j] + sum_{c,tap} W[j][c][tap] * xr(n[dy][i + dx])), xr = BF16(x)
+//   mode 1 (last layer input gradient): [a4 > 0] * sum_{c,tap} W5[c][j][tap] * g(n[2 - dy][i + 2 - dx])
+constexpr int kQuad = 4;
+
+__global__ void __launch_bounds__(128) k_2to64(int B, int H, int W, int mode, const float2* src,
+                                               const float* wsrc, const float* bias,
+                                               const __nv_bfloat16* mask_src, __nv_bfloat16* out) {
+  __shared__ float s_w[CH * 18];  // [j][c][tap], BF16-rounded
   __shared__ float s_b[CH];
-  for (int i = threadIdx.x; i < CH * 18; i += blockDim.x) s_w[i] = w1[i];
-  if (threadIdx.x < CH) s_b[threadIdx.x] = b1[threadIdx.x];
-  __syncthreads();
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (size_t)B * H * W) return;
-  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
-  float xin[2][9];
-#pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
-    const int yy = h + tap / 3 - 1, xx = w + tap % 3 - 1;
-    float2 v = make_float2(0.f, 0.f);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = x[((size_t)b * H + yy) * W + xx];
-    xin[0][tap] = bf(__float2bfloat16_rn(v.x));
-    xin[1][tap] = bf(__float2bfloat16_rn(v.y));
+  for (int i = threadIdx.x; i < CH * 18; i += blockDim.x) {
+    const int j = i / 18, c = (i / 9) % 2, tap = i % 9;
+    const float v = (mode == 0) ? wsrc[(j * 2 + c) * 9 + tap] : wsrc[(c * CH + j) * 9 + tap];
+    s_w[i] = bf(__float2bfloat16_rn(v));
   }
-  uint4* op = reinterpret_cast<uint4*>(a1 + p * CH);
+  if (threadIdx.x < CH) s_b[threadIdx.x] = (mode == 0) ? bias[threadIdx.x] : 0.f;
+  __syncthreads();
+  const int nq = (W + kQuad - 1) / kQuad;
+  const size_t qi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= (size_t)B * H * nq) return;
+  const int qw = qi % nq, h = (qi / nq) % H, b = qi / ((size_t)nq * H);
+  const int w0 = qw * kQuad;
+  float n[2][3][kQuad + 2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < kQuad + 2; ++q) {
+      const int yy = h - 1 + r, xx = w0 - 1 + q;
+      float2 v = make_float2(0.f, 0.f);
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = src[((size_t)b * H + yy) * W + xx];
+      if (mode == 0) v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
+      n[0][r][q] = v.x;
+      n[1][r][q] = v.y;
+    }
 #pragma unroll 1
   for (int cg = 0; cg < 8; ++cg) {
-    float r[8];
+    float acc[8][kQuad];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int co = cg * 8 + e;
-      float s = s_b[co];
+      const int j = cg * 8 + e;
+#pragma unroll
+      for (int i = 0; i < kQuad; ++i) acc[e][i] = s_b[j];
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) s = fmaf(s_w[(co * 2 + c) * 9 + tap], xin[c][tap], s);
-      r[e] = fmaxf(s, 0.f);
-    }
-    uint4 o;
-    __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
+        for (int tap = 0; tap < 9; ++tap) {
+          const float wv = s_w[j * 18 + c * 9 + tap];
+          const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) po[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
-    op[cg] = o;
+          for (int i = 0; i < kQuad; ++i) {
+            const float x = (mode == 0) ? n[c][dy][i + dx] : n[c][2 - dy][i + 2 - dx];
+            acc[e][i] = fmaf(wv, x, acc[e][i]);
+          }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kQuad; ++i) {
+      const int w = w0 + i;
+      if (w >= W) break;
+      const size_t p = ((size_t)b * H + h) * W + w;
+      float r[8];
+      if (mode == 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[e] = fmaxf(acc[e][i], 0.f);
+      } else {
+        const uint4 m = reinterpret_cast<const uint4*>(mask_src + p * CH)[cg];
+        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[e] = (bf(mb[e]) > 0.f) ? acc[e][i] : 0.f;
+      }
+      uint4 o;
+      __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) po[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
+      reinterpret_cast<uint4*>(out + p * CH)[cg] = o;
+    }
   }
 }
 
@@ -313,6 +359,7 @@ __global__ void __launch_bounds__(256) k_l1_fwd(int B, int H, int W, const float
 constexpr int kTw = 128;
 constexpr int kHaloLd = 72;  // bf16 per padded pixel row
 constexpr int kHaloSmem = 3 * (kTw + 2) * kHaloLd * 2;
+constexpr int kSmem64to2 = kHaloSmem + 9 * 8 * CH * 2;
 
 __device__ __forceinline__ void stage_halo64(__nv_bfloat16* s, const __nv_bfloat16* t, int b, int h, int w0,
                                              int H, int W) {
@@ -326,117 +373,74 @@ __device__ __forceinline__ void stage_halo64(__nv_bfloat16* s, const __nv_bfloat
   }
 }
 
-// 64 -> 2 contraction over the 3x3 neighbourhood from the halo: s[c] +=
-// sum_{tap, ch} wt[(c * 64 + ch) * 9 + tap'] * halo(tap), tap' = flipped taps if flip.
-__device__ __forceinline__ void contract64to2(const __nv_bfloat16* halo, const float* s_w, int t, bool flip,
-                                              float& s0, float& s1) {
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 64 -> 2 on the warp-level tensor cores (mma.sync m16n8k16, N = 8 with 2 used):
+// A = 16 pixels x 16 channels of the halo tile (ldmatrix), B = weights
+// Wt[t][n][ch] for halo offset t = (ry, rx), K = 9 offsets x 64 channels.
+//   mode 0 (last layer):  out = x + b5 + sum_t sum_ch w5[n][ch][t] halo(ry, m + rx)
+//   mode 1 (first layer input gradient): gx = gout + sum w1[ch][n][8 - t] halo(ry, m + rx)
+// (the flipped taps of the input gradient are the offsets t = 8 - tap).
+__global__ void __launch_bounds__(kTw) k_64to2(int B, int H, int W, int mode, const __nv_bfloat16* act,
+                                              const float* wsrc, const float* bias, const float2* res,
+                                              float2* out) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);
+  __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(dsm + kHaloSmem);  // [9][8][64]
+  const int bh = blockIdx.y, b = bh / H, h = bh % H, w0 = blockIdx.x * kTw;
+  for (int i = threadIdx.x; i < 9 * 8 * CH; i += blockDim.x) {
+    const int t = i / (8 * CH), n = (i / CH) % 8, ch = i % CH;
+    float v = 0.f;
+    if (n < 2) v = (mode == 0) ? wsrc[(n * CH + ch) * 9 + t] : wsrc[(ch * 2 + n) * 9 + (8 - t)];
+    wt[i] = __float2bfloat16_rn(v);
+  }
+  stage_halo64(halo, act, b, h, w0, H, W);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int mi = lane >> 3, r = lane & 7;
 #pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap % 3;
-    const int r = flip ? 2 - dy : dy, c = flip ? t + 2 - dx : t + dx;
-    const uint4* row = reinterpret_cast<const uint4*>(halo + (r * (kTw + 2) + c) * kHaloLd);
+  for (int mt = 0; mt < 2; ++mt) {
+    const int mbase = warp * 32 + mt * 16;
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      const int ry = t / 3, rx = t % 3;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint4 u = row[q];
-      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+      for (int kc = 0; kc < 4; ++kc) {
+        const int ch0 = kc * 16;
+        uint32_t af[4];
+        const int m = (mi & 1) * 8 + r, kq = (mi >> 1) * 8;
+        ldsm_x4(af, halo + (ry * (kTw + 2) + mbase + m + rx) * kHaloLd + ch0 + kq);
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wt + (t * 8 + gid) * CH + ch0 + 2 * tig);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wt + (t * 8 + gid) * CH + ch0 + 8 + 2 * tig);
+        mma16816(d, af, b0, b1);
+      }
+    }
+    if (tig == 0) {
+      const float b0v = (mode == 0) ? bias[0] : 0.f, b1v = (mode == 0) ? bias[1] : 0.f;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(h2[e]);
-        const int ch = q * 8 + 2 * e;
-        s0 = fmaf(s_w[(0 * CH + ch) * 9 + tap], f.x, s0);
-        s0 = fmaf(s_w[(0 * CH + ch + 1) * 9 + tap], f.y, s0);
-        s1 = fmaf(s_w[(1 * CH + ch) * 9 + tap], f.x, s1);
-        s1 = fmaf(s_w[(1 * CH + ch + 1) * 9 + tap], f.y, s1);
+      for (int half = 0; half < 2; ++half) {
+        const int w = w0 + mbase + gid + half * 8;
+        if (w < W) {
+          const size_t p = ((size_t)b * H + h) * W + w;
+          const float2 rv = res[p];
+          out[p] = make_float2(rv.x + b0v + d[2 * half], rv.y + b1v + d[2 * half + 1]);
+        }
       }
     }
   }
-}
-
-// Last layer (64 -> 2) plus the residual: out[p] = x[p] + (b5 + sum_{ci,tap} w5[c][ci][tap] a4[p+s][ci]).
-__global__ void __launch_bounds__(kTw) k_l5_fwd(int B, int H, int W, const __nv_bfloat16* a4, const float* w5,
-                                               const float* b5, const float2* x, float2* out) {
-  extern __shared__ __align__(16) uint8_t dsm[];
-  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);
-  float* s_w = reinterpret_cast<float*>(dsm + kHaloSmem);
-  const int bh = blockIdx.y, b = bh / H, h = bh % H, w0 = blockIdx.x * kTw;
-  for (int i = threadIdx.x; i < 2 * CH * 9; i += blockDim.x) s_w[i] = w5[i];
-  stage_halo64(halo, a4, b, h, w0, H, W);
-  __syncthreads();
-  const int w = w0 + threadIdx.x;
-  if (w >= W) return;
-  float s0 = b5[0], s1 = b5[1];
-  contract64to2(halo, s_w, threadIdx.x, false, s0, s1);
-  const size_t p = ((size_t)b * H + h) * W + w;
-  const float2 xv = x[p];
-  out[p] = make_float2(xv.x + s0, xv.y + s1);
-}
-
-// Input gradient of the last layer, masked by the ReLU of its input:
-//   g4[p][ci] = [a4[p][ci] > 0] * sum_{co,tap} w5[co][ci][tap] g[p - s_tap][co]
-__global__ void __launch_bounds__(128) k_l5_dgrad(int B, int H, int W, const float2* g, const float* w5,
-                                                  const __nv_bfloat16* a4, __nv_bfloat16* g4) {
-  __shared__ float s_w[2 * CH * 9];
-  for (int i = threadIdx.x; i < 2 * CH * 9; i += blockDim.x) s_w[i] = w5[i];
-  __syncthreads();
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (size_t)B * H * W) return;
-  const int w = p % W, h = (p / W) % H, b = p / ((size_t)W * H);
-  float gin[2][9];
-#pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
-    const int yy = h - (tap / 3 - 1), xx = w - (tap % 3 - 1);
-    float2 v = make_float2(0.f, 0.f);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = g[((size_t)b * H + yy) * W + xx];
-    gin[0][tap] = v.x;
-    gin[1][tap] = v.y;
-  }
-  const uint4* ap = reinterpret_cast<const uint4*>(a4 + p * CH);
-  uint4* op = reinterpret_cast<uint4*>(g4 + p * CH);
-#pragma unroll 1
-  for (int cg = 0; cg < 8; ++cg) {
-    const uint4 m = ap[cg];
-    const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
-    float r[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int ci = cg * 8 + e;
-      float s = 0.f;
-#pragma unroll
-      for (int co = 0; co < 2; ++co)
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) s = fmaf(s_w[(co * CH + ci) * 9 + tap], gin[co][tap], s);
-      r[e] = (bf(mb[e]) > 0.f) ? s : 0.f;
-    }
-    uint4 o;
-    __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) po[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
-    op[cg] = o;
-  }
-}
-
-// Input gradient of the first layer plus the residual path:
-//   gx[p][c] = gout[p][c] + sum_{co,tap} w1[co][c][tap] g1[p - s_tap][co]
-// (w1 is read transposed into the [c][co][tap] order of contract64to2).
-__global__ void __launch_bounds__(kTw) k_l1_dgrad(int B, int H, int W, const __nv_bfloat16* g1,
-                                                 const float* w1, const float2* gout, float2* gx) {
-  extern __shared__ __align__(16) uint8_t dsm[];
-  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);
-  float* s_w = reinterpret_cast<float*>(dsm + kHaloSmem);
-  const int bh = blockIdx.y, b = bh / H, h = bh % H, w0 = blockIdx.x * kTw;
-  for (int i = threadIdx.x; i < 2 * CH * 9; i += blockDim.x) {
-    const int c = i / (CH * 9), co = (i / 9) % CH, tap = i % 9;
-    s_w[i] = w1[(co * 2 + c) * 9 + tap];
-  }
-  stage_halo64(halo, g1, b, h, w0, H, W);
-  __syncthreads();
-  const int w = w0 + threadIdx.x;
-  if (w >= W) return;
-  float s0 = 0.f, s1 = 0.f;
-  contract64to2(halo, s_w, threadIdx.x, true, s0, s1);
-  const size_t p = ((size_t)b * H + h) * W + w;
-  const float2 go = gout[p];
-  gx[p] = make_float2(go.x + s0, go.y + s1);
 }
 
 // --------------------------------------------------- weight gradients (CUDA cores)
@@ -546,16 +550,34 @@ __global__ void __launch_bounds__(256) k_wgrad_l5(int B, int H, int W, const __n
   small_partial_out(acc, bacc, 1, partial + (size_t)blockIdx.x * kSmallOut);
 }
 
-// Deterministic sum over chunks, added to the caller's gradient buffers.
-__global__ void k_reduce_partials(const float* partial, int nchunks, int stride, int nw, float* gw,
-                                  int nb, int boff, float* gb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nw + nb) return;
-  const int src = (i < nw) ? i : boff + (i - nw);
+// Deterministic sums over chunks, added to the caller's gradient buffers.  A
+// CTA owns 32 consecutive columns; its eight warps each sum every eighth chunk
+// in increasing order, and the eight results are added in warp order.
+__device__ __forceinline__ float colsum8(const float* base, size_t stride, int nchunks, bool valid) {
+  __shared__ float s_part[8][32];
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
   float s = 0.f;
-  for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * stride + src];
-  if (i < nw) gw[i] += s;
-  else gb[i - nw] += s;
+  if (valid)
+    for (int c = wg; c < nchunks; c += 8) s += base[(size_t)c * stride];
+  s_part[wg][lane] = s;
+  __syncthreads();
+  float t = 0.f;
+  if (wg == 0)
+    for (int k = 0; k < 8; ++k) t += s_part[k][lane];
+  return t;
+}
+
+// Small layers: column i < nw is weight i, nw <= i < nw + nb is bias i - nw (at boff).
+__global__ void __launch_bounds__(256) k_reduce_partials(const float* partial, int nchunks, int stride, int nw,
+                                                         float* gw, int nb, int boff, float* gb) {
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const bool valid = i < nw + nb;
+  const int src = valid ? ((i < nw) ? i : boff + (i - nw)) : 0;
+  const float s = colsum8(partial + src, stride, nchunks, valid);
+  if (threadIdx.x < 32 && valid) {
+    if (i < nw) gw[i] += s;
+    else gb[i - nw] += s;
+  }
 }
 
 // 64 -> 64 layer weight gradient on the warp-level tensor-core path
@@ -690,19 +712,25 @@ __global__ void __launch_bounds__(256) k_wgrad64(int B, int H, int W, const __nv
 }
 
 // Sum the 64x64-layer partials over chunks in fixed order into gw [co][ci][tap] and gb.
-__global__ void k_reduce_wgrad64(const float* partial, int nchunks, float* gw, float* gb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // i = (tap, co, ci), ci fastest: coalesced reads
-  if (i < CH * CH * 9) {
-    const int tap = i / (CH * CH), co = (i / CH) % CH, ci = i % CH;
-    float s = 0.f;
-    for (int c = 0; c < nchunks; ++c) s += partial[((size_t)c * 9 + tap) * (CH * CH) + co * CH + ci];
-    gw[(co * CH + ci) * 9 + tap] += s;
-  } else if (i < CH * CH * 9 + CH) {
-    const int co = i - CH * CH * 9;
-    float s = 0.f;
-    const float* pb = partial + (size_t)nchunks * 9 * CH * CH;
-    for (int c = 0; c < nchunks; ++c) s += pb[(size_t)c * CH + co];
-    gb[co] += s;
+// 64x64 layers: columns (tap, co, ci) of the per-chunk [9][64][64] partials, then the biases.
+__global__ void __launch_bounds__(256) k_reduce_wgrad64(const float* partial, int nchunks, float* gw,
+                                                        float* gb) {
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int nw = CH * CH * 9;
+  const bool valid = i < nw + CH;
+  float s;
+  if (i < nw || !valid) {
+    s = colsum8(partial + (valid ? i : 0), (size_t)nw, nchunks, valid);
+  } else {
+    s = colsum8(partial + (size_t)nchunks * nw + (i - nw), CH, nchunks, true);
+  }
+  if (threadIdx.x < 32 && valid) {
+    if (i < nw) {
+      const int tap = i / (CH * CH), co = (i / CH) % CH, ci = i % CH;
+      gw[(co * CH + ci) * 9 + tap] += s;
+    } else {
+      gb[i - nw] += s;
+    }
   }
 }
 
@@ -754,10 +782,8 @@ int conv_prepare() {
              cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
              cudaFuncSetAttribute(k_conv64, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM) ==
                  cudaSuccess &&
-             cudaFuncSetAttribute(k_l5_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kHaloSmem + 2 * CH * 9 * 4) == cudaSuccess &&
-             cudaFuncSetAttribute(k_l1_dgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kHaloSmem + 2 * CH * 9 * 4) == cudaSuccess &&
+             cudaFuncSetAttribute(k_64to2, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem64to2) ==
+                 cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, wl1_smem(kMaxW)) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l5, cudaFuncAttributeMaxDynamicSharedMemorySize, wl5_smem(kMaxW)) ==
@@ -828,19 +854,34 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
   __nv_bfloat16* act[4];
   for (int i = 0; i < 4; ++i) act[i] = reinterpret_cast<__nv_bfloat16*>(ws + L.act[i]);
   int* status = reinterpret_cast<int*>(ws + L.status);
-  for (int l = 0; l < 3; ++l)
-    k_pack64<<<(9 * 8 * CH * 8 + 255) / 256, 256, 0, st>>>(wts + o.w[l + 1],
-                                                          reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), 0);
+  {
+    PackArgs pa;
+    for (int l = 0; l < 3; ++l) {
+      pa.w[l] = wts + o.w[l + 1];
+      pa.fwd[l] = reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]);
+      pa.dgr[l] = reinterpret_cast<__nv_bfloat16*>(ws + L.wd[l]);
+    }
+    prof_mark("dn_pack", st, false);
+    k_pack64<<<dim3((9 * 8 * CH * 8 + 255) / 256, 6), 256, 0, st>>>(pa);
+    prof_mark("dn_pack", st, true);
+  }
   const size_t npx = (size_t)B * H * W;
-  k_l1_fwd<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(B, H, W, x, wts + o.w[0], wts + o.b[0], act[0]);
+  const unsigned nquad = (unsigned)(((size_t)B * H * ((W + kQuad - 1) / kQuad) + 127) / 128);
+  prof_mark("dn_small", st, false);
+  k_2to64<<<nquad, 128, 0, st>>>(B, H, W, 0, x, wts + o.w[0], wts + o.b[0], nullptr, act[0]);
+  prof_mark("dn_small", st, true);
   for (int l = 0; l < 3; ++l)
     if (int e = launch_conv64(act[l], reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), wts + o.b[l + 1],
                               nullptr, act[l + 1], 0, B, H, W, status, st))
       return e;
   if (out)
-    k_l5_fwd<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kHaloSmem + 2 * CH * 9 * 4, st>>>(
-        B, H, W, act[3], wts + o.w[4], wts + o.b[4], x, out);
-  prof_count(4 + (out ? 1 : 0));  // packing x3, first layer, last layer (convolutions counted apart)
+    {
+    prof_mark("dn_small", st, false);
+    k_64to2<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kSmem64to2, st>>>(
+        B, H, W, 0, act[3], wts + o.w[4], wts + o.b[4], x, out);
+    prof_mark("dn_small", st, true);
+    }
+  prof_count(2 + (out ? 1 : 0));  // packing, first layer, last layer (convolutions counted apart)
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
@@ -898,16 +939,21 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   float* ps = reinterpret_cast<float*>(w8 + L.part_small);
   float* p64 = reinterpret_cast<float*>(w8 + L.part64);
   int* status = reinterpret_cast<int*>(w8 + L.status);
-  for (int l = 0; l < 3; ++l)
-    k_pack64<<<(9 * 8 * CH * 8 + 255) / 256, 256, 0, st>>>(weights + o.w[l + 1],
-                                                          reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), 1);
+  // input-gradient weight tables were packed by the forward pass that precedes every backward
   // last layer: input gradient (masked by a4 > 0) and weight gradient
   const size_t npx = (size_t)B * H * W;
-  k_l5_dgrad<<<(unsigned)((npx + 127) / 128), 128, 0, st>>>(B, H, W, go, weights + o.w[4], act[3], gbuf[0]);
+  prof_mark("dn_small", st, false);
+  const unsigned nquad = (unsigned)(((size_t)B * H * ((W + kQuad - 1) / kQuad) + 127) / 128);
+  k_2to64<<<nquad, 128, 0, st>>>(B, H, W, 1, go, weights + o.w[4], nullptr, act[3], gbuf[0]);
+  prof_mark("dn_small", st, true);
+  prof_mark("dn_wgrad_small", st, false);
   k_wgrad_l5<<<L.nch_small, 256, wl5_smem(W), st>>>(B, H, W, act[3], go, ps);
-  k_reduce_partials<<<(2 * CH * 9 + 2 + 255) / 256, 256, 0, st>>>(ps, L.nch_small, kSmallOut, 2 * CH * 9,
+  prof_mark("dn_wgrad_small", st, true);
+  prof_mark("dn_reduce", st, false);
+  k_reduce_partials<<<(2 * CH * 9 + 2 + 31) / 32, 256, 0, st>>>(ps, L.nch_small, kSmallOut, 2 * CH * 9,
                                                                  grad_weights + o.w[4], 2, CH * 18,
                                                                  grad_weights + o.b[4]);
+  prof_mark("dn_reduce", st, true);
   // 64 -> 64 layers 4, 3, 2 (index l = 2, 1, 0 of the packed set)
   int cur = 0;
   for (int l = 2; l >= 0; --l) {
@@ -916,21 +962,29 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
     prof_mark("wgrad64", st, false);
     k_wgrad64<<<gw, 256, 0, st>>>(B, H, W, gbuf[cur], ain, p64);
     prof_mark("wgrad64", st, true);
-    k_reduce_wgrad64<<<(CH * CH * 9 + CH + 255) / 256, 256, 0, st>>>(p64, L.nch64, grad_weights + o.w[l + 1],
+    prof_mark("dn_reduce", st, false);
+    k_reduce_wgrad64<<<(CH * CH * 9 + CH + 31) / 32, 256, 0, st>>>(p64, L.nch64, grad_weights + o.w[l + 1],
                                                                      grad_weights + o.b[l + 1]);
+    prof_mark("dn_reduce", st, true);
     if (int e = launch_conv64(gbuf[cur], reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), nullptr, ain,
                               gbuf[cur ^ 1], 1, B, H, W, status, st))
       return e;
     cur ^= 1;
   }
   // first layer: weight gradient and input gradient (+ residual)
+  prof_mark("dn_wgrad_small", st, false);
   k_wgrad_l1<<<L.nch_small, 256, wl1_smem(W), st>>>(B, H, W, gbuf[cur], xx, ps);
-  k_reduce_partials<<<(CH * 18 + CH + 255) / 256, 256, 0, st>>>(ps, L.nch_small, kSmallOut, CH * 18,
+  prof_mark("dn_wgrad_small", st, true);
+  prof_mark("dn_reduce", st, false);
+  k_reduce_partials<<<(CH * 18 + CH + 31) / 32, 256, 0, st>>>(ps, L.nch_small, kSmallOut, CH * 18,
                                                                grad_weights + o.w[0], CH, CH * 18,
                                                                grad_weights + o.b[0]);
-  k_l1_dgrad<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kHaloSmem + 2 * CH * 9 * 4, st>>>(
-      B, H, W, gbuf[cur], weights + o.w[0], go, static_cast<float2*>(grad_x));
-  prof_count(15);  // every launch of the backward except the three tensor-core convolutions
+  prof_mark("dn_reduce", st, true);
+  prof_mark("dn_small", st, false);
+  k_64to2<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kSmem64to2, st>>>(
+      B, H, W, 1, gbuf[cur], weights + o.w[0], nullptr, go, static_cast<float2*>(grad_x));
+  prof_mark("dn_small", st, true);
+  prof_count(12);  // every launch of the backward except the three tensor-core convolutions
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 

@@ -318,22 +318,30 @@ int generic_prepare(sense_plan p) {
 
 int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
+  prof_mark("fft_generic", p->stream, false);
   k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->C, p->H, x, p->maps, y,
                                                               dev(p->fW), 0);
+  prof_mark("fft_generic", p->stream, true);
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
+  prof_mark("fft_generic", p->stream, false);
   k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, y, dev(p->fH), p->mask,
                                                       p->mask_is_lines, 0);
+  prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
 int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
+  prof_mark("fft_generic", p->stream, false);
   k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, p->w.T, dev(p->fH), p->mask,
                                                       p->mask_is_lines, 1);
+  prof_mark("fft_generic", p->stream, true);
   const dim3 gr((p->H + kRows - 1) / kRows, p->B);
+  prof_mark("fft_generic", p->stream, false);
   k_row_combine<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->C, p->H, p->w.T, p->maps, x,
                                                               dev(p->fW), 1, nullptr, 0.f, nullptr);
+  prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -341,14 +349,20 @@ int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
 int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
                           const double* lam_dev) {
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
+  prof_mark("fft_generic", p->stream, false);
   k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->C, p->H, x, p->maps,
                                                               p->w.T, dev(p->fW), 1);
+  prof_mark("fft_generic", p->stream, true);
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
+  prof_mark("fft_generic", p->stream, false);
   k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, p->w.T, p->w.T, dev(p->fH),
                                                       p->mask2s, p->mask_is_lines, 2);
+  prof_mark("fft_generic", p->stream, true);
   const dim3 gr2((p->H + kRows - 1) / kRows, p->B);
+  prof_mark("fft_generic", p->stream, false);
   k_row_combine<<<gr2, kThreads, smem_rows(p->W), p->stream>>>(
       p->C, p->H, p->w.T, p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
+  prof_mark("fft_generic", p->stream, true);
   count_launch(p, 3);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

@@ -112,9 +112,11 @@ int unrolled_step(sense_plan p, int kind, const float* weights, const double* la
   const size_t n2 = (size_t)p->B * p->H * p->W / 2;
   if (int e = denoiser_forward(kind, weights, x_t, w.t0, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
     return e;
+  prof_mark("unrolled_misc", p->stream, false);
   k_rhs<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, static_cast<const float4*>(AHy),
                                                              reinterpret_cast<const float4*>(w.t0), lambda,
                                                              reinterpret_cast<float4*>(w.t1));
+  prof_mark("unrolled_misc", p->stream, true);
   count_launch(p);
   return cg_run(p, w.t1, nullptr, static_cast<float2*>(x_next), lambda, 1, cg_iters, nullptr);
 }
@@ -139,8 +141,10 @@ int unrolled_step_backward(sense_plan p, int kind, const float* weights, const d
   if (int e = launch_dot_rows(p, w.t1, w.t0, static_cast<const float2*>(x_next), grad_lambda, 1, 1))
     return e;
   // grad_z = lambda v  (z is no longer needed)
+  prof_mark("unrolled_misc", p->stream, false);
   k_scale<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, reinterpret_cast<const float4*>(w.t1),
                                                                lambda, reinterpret_cast<float4*>(w.t0));
+  prof_mark("unrolled_misc", p->stream, true);
   count_launch(p);
   return denoiser_backward(kind, weights, x_t, w.t0, grad_t, grad_weights, dn_ws, dn_ws_bytes, p->B, p->H,
                            p->W, 0, p->stream);
@@ -152,9 +156,11 @@ int sense_mse_loss(sense_plan p, const void* x, const void* gt, double* loss, vo
   if (!p->ws) return SENSE_EWORKSPACE;
   const int rows = p->B * p->H;
   const double inv_n = 1.0 / ((double)rows * p->W);
+  prof_mark("unrolled_misc", p->stream, false);
   k_mse<<<(rows + kWarps - 1) / kWarps, kWarps * 32, 0, p->stream>>>(
       rows, p->W, static_cast<const float4*>(x), static_cast<const float4*>(gt), static_cast<float4*>(grad),
       inv_n, p->w.part, loss, p->w.counter);
+  prof_mark("unrolled_misc", p->stream, true);
   count_launch(p);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -165,8 +171,10 @@ int adam_update_f32(float* param, float* grad, float* m, float* v, size_t n, flo
   if (step < 1 || !(lr >= 0.f)) return SENSE_EINVAL_ARG;
   const float c1 = (float)(1.0 - std::pow((double)beta1, step));
   const float c2 = (float)(1.0 - std::pow((double)beta2, step));
+  prof_mark("unrolled_misc", static_cast<cudaStream_t>(stream), false);
   k_adam<float><<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       n, param, grad, m, v, lr, beta1, beta2, eps, c1, c2, -INFINITY);
+  prof_mark("unrolled_misc", static_cast<cudaStream_t>(stream), true);
   prof_count(1);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -176,8 +184,10 @@ int adam_update_f64(double* param, double* grad, double* m, double* v, size_t n,
   if (!param || !grad || !m || !v) return SENSE_EINVAL_PTR;
   if (step < 1 || !(lr >= 0.0)) return SENSE_EINVAL_ARG;
   const double c1 = 1.0 - std::pow(beta1, step), c2 = 1.0 - std::pow(beta2, step);
+  prof_mark("unrolled_misc", static_cast<cudaStream_t>(stream), false);
   k_adam<double><<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       n, param, grad, m, v, lr, beta1, beta2, eps, c1, c2, lower);
+  prof_mark("unrolled_misc", static_cast<cudaStream_t>(stream), true);
   prof_count(1);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

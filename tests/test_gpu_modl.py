@@ -9,7 +9,9 @@ sides of a BF16 boundary (a jump of 2^-8 relative on that element); from the
 second unrolled block on, such flips in the denoiser input add up to a few
 1e-3, and in the reverse pass they also flip ReLU masks.  Tolerances:
 * one block's reverse mode with both sides given identical inputs (x^t,
-  x^{t+1}, dL/dx^{t+1}): the per-layer convolution bound, 1e-2 relative;
+  x^{t+1}, dL/dx^{t+1}) and the oracle's reverse pass using the denoiser
+  activations the GPU recomputed (so both take the same ReLU masks): the
+  per-layer bound, 1e-2 relative;
 * block outputs and the loss of the two-block chain: 1e-2;
 * gradients of the whole two-block chain (two BF16 reverse chains in series,
   each input differing by the flips above): 5e-2 relative L2.
@@ -19,6 +21,8 @@ import pytest
 import torch
 
 import synth
+from oracle import cg as ocg
+from oracle import nn as onn
 from oracle import sense as osense
 from oracle import unrolled as ounr
 from oracle.nn import bf16_round
@@ -92,8 +96,15 @@ def test_modl_block_reverse_mode_parity():
         p(tr.xs[1]), p(gd), p(gt0), p(tr.gw), p(tr.gl), iters, p(tr.dn.ws), tr.dn.ws.numel()))
     torch.cuda.synchronize()
     wo = oracle_weights(ws)
-    rg, rws, rbs, rgl = ounr.modl_block_backward(g1, x0, x1, x0, maps, mask, wo, bs, lam, iters,
-                                                 act_round=bf16_round, grad_round=bf16_round)
+    # the GPU's recomputed activations of D(x^0) (left in the denoiser workspace)
+    acts, _ = tr.dn.activations()
+    A = [a.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2) for a in acts]
+    xr = bf16_round(onn.c2r(x0))
+    z = x0.astype(np.complex128) + onn.r2c(onn.conv2d(A[3], wo[4], bs[4]))
+    v, glam_b = ocg.cg_solve_backward(maps, mask, lam, g1, x1, z, iters)
+    cache = {"acts": [xr] + A, "pre": A + [None]}  # ReLU masks: pre > 0 <=> stored activation > 0
+    rg, rws, rbs = onn.modl_cnn_backward(x0, wo, bs, lam * v, cache=cache, grad_round=bf16_round)
+    rgl = float(glam_b.sum())
     assert rel(gt0.cpu().numpy(), rg) <= 1e-2
     gws, gbs = unflat(tr.gw.cpu().numpy().astype(np.float64))
     for l in range(5):
