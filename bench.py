@@ -42,6 +42,9 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
 # DRAM bytes per launch (read + write) of each kernel group from the committed ncu
 # captures under profiles/ (None until captured for the current kernel version).
 NCU_TRAFFIC = {"normal_lines": None, "conv64_tc": None, "wgrad64": None}
+# kernel groups the library times with CUDA events when profiling is on
+PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
+                  "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc")
 
 
 # ------------------------------------------------------------------ clocks
@@ -149,7 +152,7 @@ def timed_steps(step, steps, flush, dist):
         dist.barrier()
     torch.cuda.synchronize()
     _lib.kernel_launches(reset=True)
-    for k in ("normal_lines", "conv64_tc", "wgrad64"):
+    for k in PROFILE_GROUPS:
         _lib.profile_read(k)
     _lib.profile_enable(True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -160,7 +163,7 @@ def timed_steps(step, steps, flush, dist):
         evs[i][1].record()
     torch.cuda.synchronize()
     _lib.profile_enable(False)
-    prof = {k: _lib.profile_read(k) for k in ("normal_lines", "conv64_tc", "wgrad64")}
+    prof = {k: _lib.profile_read(k) for k in PROFILE_GROUPS}
     launches = _lib.kernel_launches(reset=True)
     t_ms = sum(a.elapsed_time(b) for a, b in evs)
     return t_ms, prof, launches
@@ -297,6 +300,8 @@ def run_ours(args, rank, world, local_rank):
     }
     kern = {k: v for k, v in kern.items() if v}
     total_kernel_ms = {k: prof[k][0] for k in prof}
+    breakdown = {k: {"ms_per_step": round(prof[k][0] / steps, 4), "launches_per_step": prof[k][1] // max(steps, 1),
+                     "share": round(prof[k][0] / t_ms, 4)} for k in PROFILE_GROUPS if prof[k][1]}
     dominant = max(kern, key=lambda k: total_kernel_ms[k]) if kern else None
     for k in kern:
         kern[k]["share_of_step"] = round(total_kernel_ms[k] / t_ms, 4)
@@ -335,6 +340,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps"},
         "roofline": kern.get(dominant),
         "kernels": kern,
+        "time_breakdown": breakdown,
         "e2e": {"value": round(value_slices * world / (e2e_ms * 1e-3), 3), "unit": "slices/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
         "gpu_launches": launches,

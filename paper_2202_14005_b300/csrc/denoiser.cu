@@ -60,6 +60,16 @@ ModlOffsets modl_offsets() {
 
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const uint32_t d = smem_u32(dst);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+
 // ------------------------------------------------------------ weight packing
 // 64->64 layers into the K-major operand layout [tap][g][n][8] (bf16), one
 // launch for all six tables (blockIdx.y = 2 * layer + dgrad):
@@ -69,9 +79,21 @@ struct PackArgs {
   const float* w[3];
   __nv_bfloat16* fwd[3];
   __nv_bfloat16* dgr[3];
+  const float* w1;       // first layer [64][2][9]
+  const float* w5;       // last layer [2][64][9]
+  __nv_bfloat16* t5;     // [9][8][64]: Wt[t][n][ch] = w5[n][ch][t] (n < 2)
+  __nv_bfloat16* t1;     // [9][8][64]: Wt[t][n][ch] = w1[ch][n][8 - t] (n < 2)
 };
 __global__ void k_pack64(const PackArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9*8*64*8
+  if (blockIdx.y >= 6) {  // 64 -> 2 tables of the first and last layers
+    if (i >= 9 * 8 * CH) return;
+    const int t = i / (8 * CH), n = (i / CH) % 8, ch = i % CH;
+    float v = 0.f;
+    if (n < 2) v = (blockIdx.y == 6) ? a.w5[(n * CH + ch) * 9 + t] : a.w1[(ch * 2 + n) * 9 + (8 - t)];
+    (blockIdx.y == 6 ? a.t5 : a.t1)[i] = __float2bfloat16_rn(v);
+    return;
+  }
   if (i >= 9 * 8 * CH * 8) return;
   const int l = blockIdx.y >> 1, dgrad = blockIdx.y & 1;
   const float* w = a.w[l];
@@ -366,11 +388,11 @@ __device__ __forceinline__ void stage_halo64(__nv_bfloat16* s, const __nv_bfloat
   for (int i = threadIdx.x; i < 3 * (kTw + 2) * 8; i += blockDim.x) {
     const int q = i & 7, px = (i >> 3) % (kTw + 2), r = (i >> 3) / (kTw + 2);
     const int yy = h - 1 + r, xx = w0 - 1 + px;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-      v = reinterpret_cast<const uint4*>(t + (((size_t)b * H + yy) * W + xx) * CH)[q];
-    reinterpret_cast<uint4*>(s + (r * (kTw + 2) + px) * kHaloLd)[q] = v;
+    const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+    const __nv_bfloat16* src = t + (ok ? (((size_t)b * H + yy) * W + xx) * CH + q * 8 : 0);
+    cp_async16(s + (r * (kTw + 2) + px) * kHaloLd + q * 8, src, ok);
   }
+  cp_async_commit();
 }
 
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
@@ -393,19 +415,15 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
 //   mode 1 (first layer input gradient): gx = gout + sum w1[ch][n][8 - t] halo(ry, m + rx)
 // (the flipped taps of the input gradient are the offsets t = 8 - tap).
 __global__ void __launch_bounds__(kTw) k_64to2(int B, int H, int W, int mode, const __nv_bfloat16* act,
-                                              const float* wsrc, const float* bias, const float2* res,
+                                              const __nv_bfloat16* wsrc16, const float* bias, const float2* res,
                                               float2* out) {
   extern __shared__ __align__(16) uint8_t dsm[];
   __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);
   __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(dsm + kHaloSmem);  // [9][8][64]
   const int bh = blockIdx.y, b = bh / H, h = bh % H, w0 = blockIdx.x * kTw;
-  for (int i = threadIdx.x; i < 9 * 8 * CH; i += blockDim.x) {
-    const int t = i / (8 * CH), n = (i / CH) % 8, ch = i % CH;
-    float v = 0.f;
-    if (n < 2) v = (mode == 0) ? wsrc[(n * CH + ch) * 9 + t] : wsrc[(ch * 2 + n) * 9 + (8 - t)];
-    wt[i] = __float2bfloat16_rn(v);
-  }
+  for (int i = threadIdx.x; i < 9 * 8 * CH / 8; i += blockDim.x) cp_async16(wt + i * 8, wsrc16 + i * 8, true);
   stage_halo64(halo, act, b, h, w0, H, W);
+  cp_async_wait0();
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gid = lane >> 2, tig = lane & 3;
@@ -480,8 +498,9 @@ __global__ void __launch_bounds__(256) k_wgrad_l1(int B, int H, int W, const __n
   __nv_bfloat16* su = reinterpret_cast<__nv_bfloat16*>(dsm);
   float2* sv = reinterpret_cast<float2*>(dsm + (((size_t)W * CH * 2 + 15) & ~(size_t)15));
   const int b = blockIdx.x / H, h = blockIdx.x % H;
-  const uint4* src = reinterpret_cast<const uint4*>(g1 + ((size_t)b * H + h) * W * CH);
-  for (int i = threadIdx.x; i < W * 8; i += blockDim.x) reinterpret_cast<uint4*>(su)[i] = src[i];
+  const __nv_bfloat16* src = g1 + ((size_t)b * H + h) * W * CH;
+  for (int i = threadIdx.x; i < W * 8; i += blockDim.x) cp_async16(su + i * 8, src + i * 8, true);
+  cp_async_commit();
   for (int i = threadIdx.x; i < 3 * (W + 2); i += blockDim.x) {
     const int r = i / (W + 2), px = i % (W + 2);
     const int yy = h - 1 + r, xx = px - 1;
@@ -492,6 +511,7 @@ __global__ void __launch_bounds__(256) k_wgrad_l1(int B, int H, int W, const __n
     }
     sv[i] = v;
   }
+  cp_async_wait0();
   __syncthreads();
   const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
   float acc[2][9];
@@ -523,12 +543,13 @@ __global__ void __launch_bounds__(256) k_wgrad_l5(int B, int H, int W, const __n
   for (int i = threadIdx.x; i < 3 * (W + 2) * 8; i += blockDim.x) {
     const int q = i & 7, px = (i >> 3) % (W + 2), r = (i >> 3) / (W + 2);
     const int yy = h - 1 + r, xx = px - 1;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-      v = reinterpret_cast<const uint4*>(a4 + (((size_t)b * H + yy) * W + xx) * CH)[q];
-    reinterpret_cast<uint4*>(su)[(r * (W + 2) + px) * 8 + q] = v;
+    const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+    cp_async16(su + ((r * (W + 2) + px) * 8 + q) * 8,
+               a4 + (ok ? (((size_t)b * H + yy) * W + xx) * CH + q * 8 : 0), ok);
   }
+  cp_async_commit();
   for (int i = threadIdx.x; i < W; i += blockDim.x) sv[i] = g5[((size_t)b * H + h) * W + i];
+  cp_async_wait0();
   __syncthreads();
   const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
   float acc[2][9];
@@ -593,15 +614,6 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const float* partial, i
 constexpr int kW64Rows = 4;
 constexpr int kW64Px = 32;
 constexpr int kW64Ld = 72;  // padded row (bf16) of the staged tiles: conflict-free ldmatrix
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  const uint32_t d = smem_u32(dst);
-  const int sz = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -814,7 +826,7 @@ int launch_conv64(const __nv_bfloat16* in, const __nv_bfloat16* wpack, const flo
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct DnLayout {
-  size_t wf[3], wd[3], act[4], g[2], part_small, part64, status, total;
+  size_t wf[3], wd[3], ts[2], act[4], g[2], part_small, part64, status, total;
   int nch_small, nch64;
 };
 
@@ -826,6 +838,7 @@ DnLayout dn_layout(int B, int H, int W) {
   size_t o = 0;
   for (int i = 0; i < 3; ++i) { L.wf[i] = o; o += up256(WPACK_BYTES); }
   for (int i = 0; i < 3; ++i) { L.wd[i] = o; o += up256(WPACK_BYTES); }
+  for (int i = 0; i < 2; ++i) { L.ts[i] = o; o += up256(9 * 8 * CH * 2); }
   for (int i = 0; i < 4; ++i) { L.act[i] = o; o += act; }
   for (int i = 0; i < 2; ++i) { L.g[i] = o; o += act; }
   L.part_small = o; o += up256((size_t)L.nch_small * kSmallOut * 4);
@@ -862,24 +875,28 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
       pa.dgr[l] = reinterpret_cast<__nv_bfloat16*>(ws + L.wd[l]);
     }
     prof_mark("dn_pack", st, false);
-    k_pack64<<<dim3((9 * 8 * CH * 8 + 255) / 256, 6), 256, 0, st>>>(pa);
+    pa.w1 = wts + o.w[0];
+    pa.w5 = wts + o.w[4];
+    pa.t5 = reinterpret_cast<__nv_bfloat16*>(ws + L.ts[0]);
+    pa.t1 = reinterpret_cast<__nv_bfloat16*>(ws + L.ts[1]);
+    k_pack64<<<dim3((9 * 8 * CH * 8 + 255) / 256, 8), 256, 0, st>>>(pa);
     prof_mark("dn_pack", st, true);
   }
   const size_t npx = (size_t)B * H * W;
   const unsigned nquad = (unsigned)(((size_t)B * H * ((W + kQuad - 1) / kQuad) + 127) / 128);
-  prof_mark("dn_small", st, false);
+  prof_mark("dn_2to64", st, false);
   k_2to64<<<nquad, 128, 0, st>>>(B, H, W, 0, x, wts + o.w[0], wts + o.b[0], nullptr, act[0]);
-  prof_mark("dn_small", st, true);
+  prof_mark("dn_2to64", st, true);
   for (int l = 0; l < 3; ++l)
     if (int e = launch_conv64(act[l], reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), wts + o.b[l + 1],
                               nullptr, act[l + 1], 0, B, H, W, status, st))
       return e;
   if (out)
     {
-    prof_mark("dn_small", st, false);
+    prof_mark("dn_64to2", st, false);
     k_64to2<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kSmem64to2, st>>>(
-        B, H, W, 0, act[3], wts + o.w[4], wts + o.b[4], x, out);
-    prof_mark("dn_small", st, true);
+        B, H, W, 0, act[3], reinterpret_cast<const __nv_bfloat16*>(ws + L.ts[0]), wts + o.b[4], x, out);
+    prof_mark("dn_64to2", st, true);
     }
   prof_count(2 + (out ? 1 : 0));  // packing, first layer, last layer (convolutions counted apart)
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
@@ -942,10 +959,10 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   // input-gradient weight tables were packed by the forward pass that precedes every backward
   // last layer: input gradient (masked by a4 > 0) and weight gradient
   const size_t npx = (size_t)B * H * W;
-  prof_mark("dn_small", st, false);
+  prof_mark("dn_2to64", st, false);
   const unsigned nquad = (unsigned)(((size_t)B * H * ((W + kQuad - 1) / kQuad) + 127) / 128);
   k_2to64<<<nquad, 128, 0, st>>>(B, H, W, 1, go, weights + o.w[4], nullptr, act[3], gbuf[0]);
-  prof_mark("dn_small", st, true);
+  prof_mark("dn_2to64", st, true);
   prof_mark("dn_wgrad_small", st, false);
   k_wgrad_l5<<<L.nch_small, 256, wl5_smem(W), st>>>(B, H, W, act[3], go, ps);
   prof_mark("dn_wgrad_small", st, true);
@@ -980,10 +997,11 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
                                                                grad_weights + o.w[0], CH, CH * 18,
                                                                grad_weights + o.b[0]);
   prof_mark("dn_reduce", st, true);
-  prof_mark("dn_small", st, false);
+  prof_mark("dn_64to2", st, false);
   k_64to2<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kSmem64to2, st>>>(
-      B, H, W, 1, gbuf[cur], weights + o.w[0], nullptr, go, static_cast<float2*>(grad_x));
-  prof_mark("dn_small", st, true);
+      B, H, W, 1, gbuf[cur], reinterpret_cast<const __nv_bfloat16*>(w8 + L.ts[1]), nullptr, go,
+      static_cast<float2*>(grad_x));
+  prof_mark("dn_64to2", st, true);
   prof_count(12);  // every launch of the backward except the three tensor-core convolutions
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
