@@ -1,7 +1,7 @@
 """Benchmark of the unrolled-reconstruction hot path on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload modl_train|cg_sense]
+                    [--workload modl_train|cg_sense|varnet_train]
 
 Default step (modl_train): one MoDL training step on 4 slices of 256x232 with
 12 coils (R = 6 variable-density line mask): x^0 = A^H y, five unrolled blocks
@@ -38,13 +38,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "unrolled-recon slices/s (fwd+bwd) & normal-op HBM GB/s vs plain CG-SENSE @NRMSE"
-WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it"}
+WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it",
+             "varnet_train": "varnet_train_b4_c15_320x368_R4_T10"}
 # DRAM bytes per launch (read + write) of each kernel group from the committed ncu
 # captures under profiles/ (None until captured for the current kernel version).
-NCU_TRAFFIC = {"normal_lines": None, "conv64_tc": None, "wgrad64": None}
+NCU_TRAFFIC = {"normal_lines": None, "conv64_tc": None, "wgrad64": None, "vn_K": None, "vn_Kbwd": None,
+               "vn_KT": None, "vn_wgrad": None}
 # kernel groups the library times with CUDA events when profiling is on
 PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
-                  "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc")
+                  "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc", "vn_K", "vn_Kbwd", "vn_KT",
+                  "vn_wgrad", "vn_rbfgrad", "vn_misc")
 
 
 # ------------------------------------------------------------------ clocks
@@ -245,6 +248,44 @@ def run_ours(args, rank, world, local_rank):
         outs = [(out_h, x2)]
         step_fn = step_cg
         value_slices = B
+    elif args.workload == "varnet_train":
+        from paper_2202_14005_b300.varnet import VarNetTrainer, pack_params
+        c4 = synth.CONFIGS[4]
+        cfg = c4
+        inp4 = make_inputs(c4, slice_offset=rank * c4.B)
+        maps4 = torch.from_numpy(inp4["maps"]).to(dev)
+        mask4 = torch.from_numpy(inp4["mask"]).to(dev)
+        filt, rbfw, lamv = synth.varnet_weights(4000 + rank, c4.extra["T"])
+        vec = torch.from_numpy(pack_params(filt, rbfw, lamv)).to(dev)
+        tr = VarNetTrainer(maps4, mask4, vec, lr=1e-4)
+        gt4 = torch.from_numpy(inp4["x_gt"]).to(dev)
+        y4 = tr.plan.forward(gt4)
+        y4 += torch.from_numpy(inp4["noise"]).to(dev) * mask4
+
+        def step_vn():
+            tr.train_step(y4, gt4)
+
+        for _ in range(args.warmup):
+            step_vn()
+        torch.cuda.synchronize()
+        assert tr.plan.status() == 0
+        steps = args.steps
+        clk.start()
+        t_ms, prof, launches = timed_steps(step_vn, steps, flush, dist)
+        clocks = clk.stop()
+        assert tr.plan.status() == 0
+        B = c4.B
+        N4 = c4.H * c4.W
+        normal_bytes = 8 * N4 * B * (c4.C + 2)
+        y_h, maps_h, gt_h = y4.cpu().pin_memory(), maps4.cpu().pin_memory(), gt4.cpu().pin_memory()
+        out_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        ins = [(y4, y_h), (maps4, maps_h), (gt4, gt_h)]
+        outs = [(out_h, tr.loss)]
+        step_fn = step_vn
+        value_slices = B
+        res["varnet"] = {"loss_last_step": float(tr.loss.item()),
+                         "nrmse_untrained_forward": round(float(np.linalg.norm(tr.xs[-1].cpu().numpy() - inp4["x_gt"])
+                                                                / np.linalg.norm(inp4["x_gt"])), 5)}
     else:
         c3 = synth.CONFIGS[3]
         cfg = c3
@@ -292,11 +333,17 @@ def run_ours(args, rank, world, local_rank):
 
     # per-kernel roofline inside the timed region
     Hc, Wc = cfg.H, cfg.W
-    conv_flops = 2.0 * B * Hc * Wc * 64 * 576
+    px = B * Hc * Wc
+    conv_flops = 2.0 * px * 64 * 576
+    vn_flops = 2.0 * px * 24 * 2 * 121  # one 2<->24 channel 11x11 convolution
     kern = {
         "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks),
         "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks),
         "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("tensor", conv_flops), pk, clocks),
+        "vn_K": kernel_report("vn_K", *prof["vn_K"], ("tensor", vn_flops), pk, clocks),
+        "vn_Kbwd": kernel_report("vn_Kbwd", *prof["vn_Kbwd"], ("tensor", 2 * vn_flops), pk, clocks),
+        "vn_KT": kernel_report("vn_KT", *prof["vn_KT"], ("tensor", vn_flops), pk, clocks),
+        "vn_wgrad": kernel_report("vn_wgrad", *prof["vn_wgrad"], ("tensor", 2 * vn_flops), pk, clocks),
     }
     kern = {k: v for k, v in kern.items() if v}
     total_kernel_ms = {k: prof[k][0] for k in prof}
@@ -332,11 +379,12 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(t_ms / steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64+bf16" if args.workload == "modl_train" else "c64",
+        "dtype": "c64" if args.workload == "cg_sense" else "c64+bf16",
         "data": "synthetic (seeded ellipse phantoms, Gaussian coil maps, k-space from the forward operator)",
         "config": {"workload": WORKLOADS[args.workload], "slices_per_gpu": B, "coils": cfg.C, "H": cfg.H,
                    "W": cfg.W, "R": cfg.R, "cg_iters": cfg.cg_iters, "lambda": cfg.lam,
                    "unrolled_blocks": cfg.extra.get("K") if args.workload == "modl_train" else None,
+                   "stages": cfg.extra.get("T") if args.workload == "varnet_train" else None,
                    "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps"},
         "roofline": kern.get(dominant),
         "kernels": kern,
@@ -366,7 +414,7 @@ def _oracle_slice(args):
     from oracle import sense as osense
     from oracle import unrolled as ounr
     workload, s = args
-    cfg = synth.CONFIGS[2 if workload == "cg_sense" else 3]
+    cfg = synth.CONFIGS[{"cg_sense": 2, "modl_train": 3, "varnet_train": 4}[workload]]
     d = synth.make_slices(cfg, [s])
     maps = d["maps"].astype(np.complex64)
     mask = d["mask"]
@@ -377,8 +425,16 @@ def _oracle_slice(args):
     if workload == "cg_sense":
         ocg.cg_solve(maps, mask, cfg.lam, rhs, rhs, cfg.cg_iters)
         return time.perf_counter() - t0
-    # MoDL: A^H y plus one unrolled block forward and reverse, scaled by K blocks
     t_adj = time.perf_counter() - t0
+    if workload == "varnet_train":
+        # VarNet: A^H y plus one gradient stage forward and reverse, scaled by T stages
+        filt, rbfw, lam = synth.varnet_weights(4000, cfg.extra["T"])
+        t1 = time.perf_counter()
+        x1 = ounr.varnet_stage(rhs, rhs, maps, mask, filt[0], rbfw[0], lam[0])
+        g = ounr.mse_loss_grad(x1, gt)
+        ounr.varnet_stage_backward(g, rhs, rhs, maps, mask, filt[0], rbfw[0], lam[0])
+        return t_adj + cfg.extra["T"] * (time.perf_counter() - t1)
+    # MoDL: A^H y plus one unrolled block forward and reverse, scaled by K blocks
     ws, bs = synth.modl_cnn_weights(3000)
     t1 = time.perf_counter()
     x1, _ = ounr.modl_block(rhs, rhs, maps, mask, ws, bs, cfg.lam, cfg.cg_iters)
@@ -410,6 +466,12 @@ def cpu_baseline(workload):
                 "sample": f"{n} slices, A^H y + 10 CG iterations each (FP64 NumPy, one spawn process per "
                           f"slice); wall {wall:.1f} s"}
     est = max(per)  # slices run in parallel: the step takes as long as the slowest slice
+    if workload == "varnet_train":
+        return {"value": round(n / est, 6), "unit": "slices/s", "cores": used, "kind": "oracle",
+                "sample": f"{n} slices in parallel; per slice A^H y plus ONE gradient stage forward and reverse "
+                          f"(24 11x11 filters, RBF, A^H A x, reverse mode with filter/RBF/lambda gradients), "
+                          f"time scaled by the 10 stages of the step (FP64 NumPy, one spawn process per slice); "
+                          f"slowest slice {est:.1f} s per step"}
     return {"value": round(n / est, 6), "unit": "slices/s", "cores": used, "kind": "oracle",
             "sample": f"{n} slices in parallel; per slice A^H y plus ONE unrolled block forward and reverse "
                       f"(CNN, 10-iteration CG, recomputed CNN, second CG, CNN backward), time scaled by the "
@@ -422,13 +484,13 @@ def run_reference(args, rank, world):
         return None
     n = 16 if args.workload == "cg_sense" else 4
     reps = args.warmup + args.steps
-    if args.workload == "modl_train":
+    if args.workload != "cg_sense":
         reps = max(1, min(reps, 2))  # each rep is ~1 min of CPU work per slice
     walls, used, per = oracle_pool_run(args.workload, n, reps)
     vals = walls[min(args.warmup, reps - 1):]
     wall = sum(vals)
     value = n * len(vals) / wall
-    if args.workload == "modl_train":
+    if args.workload != "cg_sense":
         value = n / max(per)
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "slices/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -189,6 +189,42 @@ int unrolled_step_backward(sense_plan plan, int kind, const float* weights, cons
                            const void* grad_next, void* grad_t, float* grad_weights,
                            double* grad_lambda, int cg_iters, void* dn_ws, size_t dn_ws_bytes);
 
+/* ------------------------------------------------------------------------
+ * VarNet gradient stage (Eq. 5, Sec. 2.3.1) on a plan (maps, mask, workspace):
+ *   x_next = x_t - sum_i K_i^T Phi_i'(K_i x_t) - lambda_t (A^H A x_t - A^H y)
+ * with VARNET_NK complex 11x11 filters k_i, K_i x = Re(k_i * x) (a
+ * cross-correlation with zero "same" padding; the imaginary part is
+ * discarded) and Phi_i'(z) = sum_j r_ij exp(-(z - mu_j)^2 / (2 sigma^2)),
+ * VARNET_NW centres mu_j = -1 + 2 j / (VARNET_NW - 1), sigma = their spacing.
+ *
+ * params: device float32 [varnet_param_count()] = 6,553 values per stage:
+ *   w[i][c][dy][dx]  i < 24, c < 2, 11x11: w[i][0] = Re k_i, w[i][1] = -Im k_i
+ *   r[i][j]          RBF weights, j < 31
+ *   lambda_t         (last value)
+ * AHy, x_t, x_next, grad_next, grad_t: device complex64 [B][H][W], W <= 512.
+ * Arithmetic: convolution inputs and filters rounded to bfloat16, float32
+ * accumulation and RBF evaluation (Phi' sums the 13 centres nearest z; the
+ * rest are below exp(-21) of the largest term); A^H A as sense_normal.
+ *
+ *   varnet_stage:          writes x_next (x_next != x_t).
+ *   varnet_stage_backward: given grad_next = dL/dx_next writes
+ *       grad_t = grad_next - K^T(Phi''(K x_t) K grad_next) - lambda_t A^H A grad_next
+ *     and ADDS dL/dparams to grad_params (filters, RBF weights, lambda_t);
+ *     grad_t != grad_next (grad_t may alias x_t).  Needs the plan workspace.
+ * ws: device workspace of varnet_workspace_bytes(B, H, W) bytes, 256-byte
+ * aligned, used by one call at a time.  Gradient sums use a fixed order:
+ * results are bitwise reproducible.  Plan's stream, asynchronous. */
+#define VARNET_NK 24
+#define VARNET_NW 31
+#define VARNET_KSIZE 11
+size_t varnet_workspace_bytes(int B, int H, int W);
+int varnet_param_count(void);
+int varnet_stage(sense_plan plan, const float* params, const void* AHy, const void* x_t, void* x_next,
+                 void* ws, size_t ws_bytes);
+int varnet_stage_backward(sense_plan plan, const float* params, const void* AHy, const void* x_t,
+                          const void* grad_next, void* grad_t, float* grad_params, void* ws,
+                          size_t ws_bytes);
+
 /* Training loss of the unrolled networks: loss[0] = mean |x - gt|^2 over the
  * plan's B*H*W complex elements (float64, fixed-order sum) and
  * grad = 2 (x - gt) / n (complex convention of Sec. 2.2.2).  Plan's stream. */

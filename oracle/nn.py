@@ -185,11 +185,19 @@ def varnet_filters_real(filt: np.ndarray) -> np.ndarray:
     return np.stack([filt.real, -filt.imag], axis=1)
 
 
-def varnet_regulariser(x: np.ndarray, filt: np.ndarray, wts: np.ndarray):
-    """sum_i K_i^T Phi_i'(K_i x) as a complex image [B, H, W]; returns (value, z)."""
-    wr = varnet_filters_real(filt)
-    z = conv2d(c2r(x), wr)
-    u = rbf(z, wts)
+def _ident(a):
+    return a
+
+
+def varnet_regulariser(x: np.ndarray, filt: np.ndarray, wts: np.ndarray, rnd=None):
+    """sum_i K_i^T Phi_i'(K_i x) as a complex image [B, H, W]; returns (value, z).
+
+    rnd (default: none) is applied to every convolution operand (filters, the
+    image, Phi'(z)) to model an implementation that stores them rounded."""
+    rnd = rnd or _ident
+    wr = rnd(varnet_filters_real(filt))
+    z = conv2d(rnd(c2r(x)), wr)
+    u = rnd(rbf(z, wts))
     return r2c(conv2d_transpose(u, wr)), z
 
 

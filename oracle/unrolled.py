@@ -87,34 +87,39 @@ def modl_train_grads(AHy, maps, mask, gt, ws, bs, lam, T, iters, act_round=None,
 
 
 # ----------------------------------------------------------------- VarNet
-def varnet_stage(x_t, AHy, maps, mask, filt, wts, lam_t):
-    """One VarNet gradient stage (Eq. 5)."""
-    reg, _ = _nn.varnet_regulariser(x_t, filt, wts)
+def varnet_stage(x_t, AHy, maps, mask, filt, wts, lam_t, rnd=None):
+    """One VarNet gradient stage (Eq. 5).  rnd: optional rounding of the
+    convolution operands (see nn.varnet_regulariser)."""
+    reg, _ = _nn.varnet_regulariser(x_t, filt, wts, rnd)
     dc = normal(x_t, maps, mask, 0.0) - AHy
     return np.asarray(x_t, dtype=np.complex128) - reg - lam_t * dc
 
 
-def varnet_forward(AHy, maps, mask, filt, wts, lam):
+def varnet_forward(AHy, maps, mask, filt, wts, lam, rnd=None):
     xs = [np.asarray(AHy, dtype=np.complex128)]
     for t in range(len(lam)):
-        xs.append(varnet_stage(xs[-1], AHy, maps, mask, filt[t], wts[t], lam[t]))
+        xs.append(varnet_stage(xs[-1], AHy, maps, mask, filt[t], wts[t], lam[t], rnd))
     return xs[-1], xs
 
 
-def varnet_stage_backward(g_next, x_t, AHy, maps, mask, filt, wts, lam_t):
+def varnet_stage_backward(g_next, x_t, AHy, maps, mask, filt, wts, lam_t, rnd=None):
     """Reverse mode of one stage: returns (g_t, grad_filt complex, grad_wts, grad_lam).
 
     With u = K x (real), the stage is x - K^T Phi'(u) - lam (N x - b), N = A^H A.
+    rnd: optional rounding of every convolution operand (filters, x, g,
+    Phi'(z) and Phi''(z) K g); the identity by default.
     """
-    wr = _nn.varnet_filters_real(filt)
-    xr = _nn.c2r(x_t)
-    gr = _nn.c2r(g_next)
+    rnd = rnd or _nn._ident
+    wr = rnd(_nn.varnet_filters_real(filt))
+    xr = rnd(_nn.c2r(x_t))
+    gr = rnd(_nn.c2r(g_next))
     z = _nn.conv2d(xr, wr)
-    phi = _nn.rbf(z, wts)
+    phi = rnd(_nn.rbf(z, wts))
     dphi = _nn.rbf_grad_z(z, wts)
     Kg = _nn.conv2d(gr, wr)                       # K g  (real, [B, Nk, H, W])
+    v = rnd(dphi * Kg)
     # d/dx of -K^T Phi'(K x): -K^T diag(Phi''(Kx)) K  (symmetric)
-    reg_back = _nn.conv2d_transpose(dphi * Kg, wr)
+    reg_back = _nn.conv2d_transpose(v, wr)
     Ng = normal(g_next, maps, mask, 0.0)
     g_t = np.asarray(g_next, dtype=np.complex128) - _nn.r2c(reg_back) - lam_t * Ng
     # RBF weights: -sum_pix (K g)_i * phi_j(z_i)
@@ -122,7 +127,7 @@ def varnet_stage_backward(g_next, x_t, AHy, maps, mask, filt, wts, lam_t):
     g_wts = -np.einsum("bkhw,bkhwj->kj", Kg, basis, optimize=True)
     # filters, two paths: through K^T (input g, output-grad phi) and through K
     _, gw1, _ = _nn.conv2d_backward(gr, wr, phi)          # <K g, phi>
-    _, gw2, _ = _nn.conv2d_backward(xr, wr, dphi * Kg)    # <K x, dphi*Kg>
+    _, gw2, _ = _nn.conv2d_backward(xr, wr, v)            # <K x, dphi*Kg>
     gwr = -(gw1 + gw2)                                    # [Nk, 2, k, k]
     g_filt = gwr[:, 0] - 1j * gwr[:, 1]                   # w0 = Re k, w1 = -Im k
     dc = normal(x_t, maps, mask, 0.0) - AHy
@@ -130,8 +135,8 @@ def varnet_stage_backward(g_next, x_t, AHy, maps, mask, filt, wts, lam_t):
     return g_t, g_filt, g_wts, g_lam
 
 
-def varnet_train_grads(AHy, maps, mask, gt, filt, wts, lam):
-    xT, xs = varnet_forward(AHy, maps, mask, filt, wts, lam)
+def varnet_train_grads(AHy, maps, mask, gt, filt, wts, lam, rnd=None):
+    xT, xs = varnet_forward(AHy, maps, mask, filt, wts, lam, rnd)
     loss = mse_loss(xT, gt)
     g = mse_loss_grad(xT, gt)
     T = len(lam)
@@ -139,6 +144,6 @@ def varnet_train_grads(AHy, maps, mask, gt, filt, wts, lam):
     g_wts = np.zeros_like(np.asarray(wts, dtype=np.float64))
     g_lam = np.zeros(T)
     for t in range(T - 1, -1, -1):
-        g, gf, gw, gl = varnet_stage_backward(g, xs[t], AHy, maps, mask, filt[t], wts[t], lam[t])
+        g, gf, gw, gl = varnet_stage_backward(g, xs[t], AHy, maps, mask, filt[t], wts[t], lam[t], rnd)
         g_filt[t], g_wts[t], g_lam[t] = gf, gw, gl
     return loss, g_filt, g_wts, g_lam, xT

@@ -1,0 +1,111 @@
+"""Variational Network training and inference on the libsense C ABI (call
+sequencing only).
+
+One training step (Eq. 5, Sec. 2.3.1): x^0 = A^H y; T gradient stages
+x^{t+1} = x^t - sum_i K_i^T Phi_i'(K_i x^t) - lambda_t (A^H A x^t - A^H y),
+each with its own filters, RBF weights and step size; loss mean |x^T - x_gt|^2;
+reverse mode stage by stage from the stored stage inputs; Adam on all
+parameters.  Every arithmetic step runs in the library's kernels.
+
+Parameter vector of one stage (float32, 6,553 values): real-form filters
+w[24][2][11][11] (w[i][0] = Re k_i, w[i][1] = -Im k_i), RBF weights r[24][31],
+lambda_t.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from .sense import SensePlan
+
+NK, NW, KS = 24, 31, 11
+N_FILT = NK * 2 * KS * KS
+N_PARAM = N_FILT + NK * NW + 1
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def pack_params(filt, rbf_w, lam) -> np.ndarray:
+    """Stage parameters [T, 6553] float32 from complex filters [T, 24, 11, 11],
+    RBF weights [T, 24, 31] and step sizes [T] (layout conversion only)."""
+    filt = np.asarray(filt, dtype=np.complex128)
+    T = filt.shape[0]
+    wr = np.stack([filt.real, -filt.imag], axis=2).reshape(T, -1)
+    return np.concatenate([wr, np.asarray(rbf_w, dtype=np.float64).reshape(T, -1),
+                           np.asarray(lam, dtype=np.float64).reshape(T, 1)], axis=1).astype(np.float32)
+
+
+def unpack_params(vec):
+    """Inverse of pack_params: (complex filters, RBF weights, lambda) per stage."""
+    v = np.asarray(vec, dtype=np.float64).reshape(-1, N_PARAM)
+    wr = v[:, :N_FILT].reshape(-1, NK, 2, KS, KS)
+    return wr[:, :, 0] - 1j * wr[:, :, 1], v[:, N_FILT:N_FILT + NK * NW].reshape(-1, NK, NW), v[:, -1]
+
+
+class VarNetTrainer:
+    def __init__(self, maps: torch.Tensor, mask: torch.Tensor, params: torch.Tensor, lr: float = 1e-4):
+        self.plan = SensePlan(maps, mask)
+        B, H, W = self.plan.img_shape()
+        self.B, self.H, self.W = B, H, W
+        if params.dim() != 2 or params.shape[1] != N_PARAM or params.dtype != torch.float32:
+            raise ValueError(f"params must be float32 [T, {N_PARAM}]")
+        if not params.is_contiguous() or params.device != maps.device:
+            raise ValueError("params must be contiguous and on the maps' device")
+        self._lib = _lib.lib()
+        if self._lib.varnet_param_count() != N_PARAM:
+            raise RuntimeError("libsense VarNet parameter layout mismatch")
+        self.T = params.shape[0]
+        self.params = params
+        dev = maps.device
+        nb = self._lib.varnet_workspace_bytes(B, H, W)
+        self.ws = torch.zeros(int(nb), dtype=torch.uint8, device=dev)
+        self.gp = torch.zeros_like(params)
+        self.m, self.v = torch.zeros_like(params), torch.zeros_like(params)
+        self.xs = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(self.T + 1)]
+        self.g = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(2)]
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.lr = lr
+        self.t = 0
+
+    def stage(self, t: int, x_t: torch.Tensor, x_next: torch.Tensor):
+        _lib.check("varnet_stage", self._lib.varnet_stage(
+            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(x_next), _p(self.ws),
+            self.ws.numel()))
+
+    def stage_backward(self, t: int, x_t, grad_next, grad_t):
+        _lib.check("varnet_stage_backward", self._lib.varnet_stage_backward(
+            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(grad_next), _p(grad_t),
+            _p(self.gp[t]), _p(self.ws), self.ws.numel()))
+
+    def forward(self, y: torch.Tensor) -> torch.Tensor:
+        """x^T for k-space y [B, C, H, W] (also keeps every x^t)."""
+        self.plan._sync_stream()
+        self.plan.adjoint(y, out=self.xs[0])
+        for t in range(self.T):
+            self.stage(t, self.xs[t], self.xs[t + 1])
+        return self.xs[self.T]
+
+    def gradients(self, y: torch.Tensor, gt: torch.Tensor):
+        """Forward, loss and reverse mode; gradients accumulate into self.gp."""
+        self.forward(y)
+        _lib.check("sense_mse_loss", self._lib.sense_mse_loss(
+            self.plan._h, _p(self.xs[self.T]), _p(gt), _p(self.loss), _p(self.g[0])))
+        cur = 0
+        for t in range(self.T - 1, -1, -1):
+            self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1])
+            cur ^= 1
+        return self.loss
+
+    def train_step(self, y: torch.Tensor, gt: torch.Tensor):
+        loss = self.gradients(y, gt)
+        self.t += 1
+        st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _lib.check("adam_update_f32", self._lib.adam_update_f32(
+            _p(self.params), _p(self.gp), _p(self.m), _p(self.v), self.params.numel(), self.lr, 0.9,
+            0.999, 1e-8, self.t, st))
+        return loss

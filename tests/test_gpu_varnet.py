@@ -1,0 +1,242 @@
+"""GPU parity of the VarNet gradient stage (Eq. 5, Sec. 2.3.1) and its reverse
+mode against the oracle.
+
+Precision protocol: the GPU rounds every convolution operand to BF16 (the
+filters, x and the incoming gradient, Phi'(K x) and Phi''(K x) K g) and
+accumulates in FP32 on the tensor cores; the RBF sums run in FP32 over the 13
+centres nearest z.
+* Mirrored oracle (the same operands rounded with bf16_round, FP64 otherwise):
+  what remains is FP32 accumulation of 242 (K) and 2,904 (K^T) products per
+  output.  The filters are zero-mean, so the sum of |products| exceeds the
+  result by 10-30x and the typical relative error is about
+  sqrt(2904) * 2^-24 * 20 ~ 7e-5.  Bounds: 1e-3 relative L2 on the regulariser
+  term, the stage gradient and every parameter gradient; 1e-4 on a whole stage
+  output (x_t dominates it); 1e-4 on the lambda gradient, an FP64 dot with
+  the FP32 residual A^H A x - A^H y, which cancels to a few percent of A^H A x.
+* Exact oracle (no rounding): the BF16 operand error, relative 2^-9 per
+  element, gives ~3e-3; bound 2e-2.
+* A chain of stages: the stage outputs differ at the 1e-4 level, and from the
+  second stage on the BF16 rounding of x flips where the FP32 and FP64 values
+  straddle a boundary: 1e-3 on the stage outputs and the loss, 1e-2 on the
+  gradients.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import nn as onn
+from oracle import sense as osense
+from oracle import unrolled as ounr
+from oracle.nn import bf16_round
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) or np.iscomplexobj(b) else np.float64)
+    b = np.asarray(b, dtype=a.dtype)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def problem(B, Cc, H, W, seed):
+    rng = np.random.default_rng(seed)
+    maps = np.stack([synth.coil_maps(Cc, H, W, rng) for _ in range(B)]).astype(np.complex64)
+    mask = synth.line_mask(W, 4.0, max(4, W // 16), "uniform", rng)
+    gt = np.stack([synth.phantom(H, W, rng, 6) for _ in range(B)]).astype(np.complex64)
+    noise = synth.complex_noise((B, Cc, H, W), 1e-3, rng)
+    y = (osense.forward(gt, maps, mask) + mask * noise).astype(np.complex64)
+    AHy = osense.adjoint(y, maps, mask).astype(np.complex64)
+    return maps, mask, y, gt, AHy
+
+
+def params(T, seed, lam=0.7):
+    """Stage parameters with non-trivial RBF weights, as float32 and as the
+    float64 values the oracle sees (filters complex [T, 24, 11, 11])."""
+    from paper_2202_14005_b300.varnet import pack_params, unpack_params
+    filt, rbfw, _ = synth.varnet_weights(seed, T)
+    rng = np.random.default_rng(seed + 100)
+    rbfw = rbfw + 0.05 * rng.standard_normal(rbfw.shape)
+    vec = pack_params(filt, rbfw, np.full(T, lam))
+    f, r, l = unpack_params(vec)
+    return vec, f, r, l
+
+
+def trainer(maps, mask, vec, AHy):
+    from paper_2202_14005_b300.varnet import VarNetTrainer
+    tr = VarNetTrainer(dev(maps), dev(mask), dev(vec))
+    tr.xs[0].copy_(dev(AHy))
+    return tr
+
+
+SHAPES = [(2, 4, 24, 200), (1, 3, 12, 64), (1, 2, 16, 300)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_stage_forward(shape):
+    B, Cc, H, W = shape
+    maps, mask, y, gt, AHy = problem(B, Cc, H, W, seed=H + W)
+    vec, f, r, lam = params(1, seed=W)
+    x = (AHy + 0.05 * synth.randn_complex(AHy.shape, 3)).astype(np.complex64)
+    tr = trainer(maps, mask, vec, AHy)
+    out = torch.empty_like(tr.xs[0])
+    tr.stage(0, dev(x), out)
+    torch.cuda.synchronize()
+    out = out.cpu().numpy()
+    dc = osense.normal(x, maps, mask, 0.0) - AHy
+    reg_gpu = x.astype(np.complex128) - out - lam[0] * dc
+    reg_m, _ = onn.varnet_regulariser(x, f[0], r[0], bf16_round)
+    reg_e, _ = onn.varnet_regulariser(x, f[0], r[0])
+    assert rel(reg_gpu, reg_m) <= 1e-3, rel(reg_gpu, reg_m)
+    assert rel(reg_gpu, reg_e) <= 2e-2, rel(reg_gpu, reg_e)
+    ref = ounr.varnet_stage(x, AHy, maps, mask, f[0], r[0], lam[0], bf16_round)
+    assert rel(out, ref) <= 1e-4, rel(out, ref)
+    assert tr.plan.status() == 0
+
+
+def _backward(tr, x, g, gp=None):
+    gt_ = torch.empty_like(tr.xs[0])
+    if gp is not None:
+        tr.gp = gp
+    tr.stage_backward(0, dev(x), dev(g), gt_)
+    torch.cuda.synchronize()
+    return gt_
+
+
+def _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, tol_m, tol_e):
+    from paper_2202_14005_b300.varnet import unpack_params
+    gf, gr, gl = unpack_params(tr.gp[0].cpu().numpy())
+    mir = ounr.varnet_stage_backward(g, x, AHy, maps, mask, f[0], r[0], lam[0], bf16_round)
+    ex = ounr.varnet_stage_backward(g, x, AHy, maps, mask, f[0], r[0], lam[0])
+    got = (gt_.cpu().numpy(), gf[0], gr[0])
+    for name, a, m, e in zip(("grad_x", "grad_filters", "grad_rbf"), got, mir[:3], ex[:3]):
+        assert rel(a, m) <= tol_m, f"{name} vs mirrored oracle: {rel(a, m):.3e}"
+        assert rel(a, e) <= tol_e, f"{name} vs exact oracle: {rel(a, e):.3e}"
+    assert abs(gl[0] - mir[3]) <= 1e-4 * abs(mir[3]), (gl[0], mir[3])
+    # the reverse-mode regulariser term alone
+    Ng = osense.normal(g, maps, mask, 0.0)
+    back_gpu = g.astype(np.complex128) - got[0] - lam[0] * Ng
+    back_m = g.astype(np.complex128) - mir[0] - lam[0] * Ng
+    assert rel(back_gpu, back_m) <= tol_m, rel(back_gpu, back_m)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_stage_backward(shape):
+    B, Cc, H, W = shape
+    maps, mask, y, gt, AHy = problem(B, Cc, H, W, seed=H + W + 1)
+    vec, f, r, lam = params(1, seed=W + 1)
+    x = (AHy + 0.05 * synth.randn_complex(AHy.shape, 5)).astype(np.complex64)
+    g = (0.1 * synth.randn_complex(AHy.shape, 6)).astype(np.complex64)
+    tr = trainer(maps, mask, vec, AHy)
+    gt_ = _backward(tr, x, g)
+    _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, 1e-3, 2e-2)
+    assert tr.plan.status() == 0
+
+
+def test_stage_full_size_slice():
+    """One slice of the knee workload (15 coils, 320 x 368: two full 128-pixel
+    tiles and a 112-pixel tail), forward and reverse mode."""
+    cfg = synth.CONFIGS[4]
+    maps, mask, y, gt, AHy = problem(1, cfg.C, cfg.H, cfg.W, seed=41)
+    vec, f, r, lam = params(1, seed=42, lam=1.0)
+    x = AHy
+    g = (1e-3 * synth.randn_complex(AHy.shape, 7)).astype(np.complex64)
+    tr = trainer(maps, mask, vec, AHy)
+    out = torch.empty_like(tr.xs[0])
+    tr.stage(0, dev(x), out)
+    gt_ = _backward(tr, x, g)
+    ref = ounr.varnet_stage(x, AHy, maps, mask, f[0], r[0], lam[0], bf16_round)
+    assert rel(out.cpu().numpy(), ref) <= 1e-4
+    _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, 1e-3, 2e-2)
+    assert tr.plan.status() == 0
+
+
+def test_backward_deterministic_accumulating_and_aliasing():
+    maps, mask, y, gt, AHy = problem(2, 3, 16, 136, seed=8)
+    vec, f, r, lam = params(1, seed=9)
+    x = AHy
+    g = (0.1 * synth.randn_complex(AHy.shape, 10)).astype(np.complex64)
+    tr = trainer(maps, mask, vec, AHy)
+    g1 = _backward(tr, x, g).clone()
+    p1 = tr.gp.clone()
+    g2 = _backward(tr, x, g)
+    assert torch.equal(g1, g2)
+    assert torch.equal(tr.gp, 2 * p1)  # gradients accumulate
+    # grad_t may overwrite x_t
+    xa = dev(x)
+    tr.gp.zero_()
+    tr.stage_backward(0, xa, dev(g), xa)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, g1) and torch.equal(tr.gp, p1)
+
+
+def test_chain_training_gradients():
+    """Three stages, MSE loss, full reverse mode against the mirrored oracle."""
+    maps, mask, y, gt, AHy = problem(2, 4, 20, 136, seed=12)
+    T = 3
+    vec, f, r, lam = params(T, seed=13, lam=0.5)
+    from paper_2202_14005_b300.varnet import VarNetTrainer, unpack_params
+    tr = VarNetTrainer(dev(maps), dev(mask), dev(vec))
+    loss = tr.gradients(dev(y), dev(gt))
+    torch.cuda.synchronize()
+    rloss, rgf, rgw, rgl, rxT = ounr.varnet_train_grads(AHy.astype(np.complex128), maps, mask, gt, f, r, lam,
+                                                        bf16_round)
+    _, rxs = ounr.varnet_forward(AHy.astype(np.complex128), maps, mask, f, r, lam, bf16_round)
+    for t in range(T + 1):
+        assert rel(tr.xs[t].cpu().numpy(), rxs[t]) <= 1e-3, f"x^{t}"
+    assert abs(loss.item() - rloss) <= 1e-3 * rloss
+    gf, gr, gl = unpack_params(tr.gp.cpu().numpy())
+    for t in range(T):
+        assert rel(gf[t], rgf[t]) <= 1e-2, f"grad filters stage {t}"
+        assert rel(gr[t], rgw[t]) <= 1e-2, f"grad rbf stage {t}"
+        assert abs(gl[t] - rgl[t]) <= 1e-2 * abs(rgl[t]), f"grad lambda stage {t}"
+    assert tr.plan.status() == 0
+
+
+def test_train_step_updates_and_clears_gradients():
+    maps, mask, y, gt, AHy = problem(1, 3, 16, 64, seed=2)
+    vec, *_ = params(2, seed=3)
+    from paper_2202_14005_b300.varnet import VarNetTrainer
+    tr = VarNetTrainer(dev(maps), dev(mask), dev(vec), lr=1e-3)
+    p0 = tr.params.clone()
+    losses = [tr.train_step(dev(y), dev(gt)).item() for _ in range(3)]
+    torch.cuda.synchronize()
+    assert not torch.equal(p0, tr.params)
+    assert torch.count_nonzero(tr.gp).item() == 0
+    assert all(np.isfinite(losses))
+
+
+def test_host_argument_errors():
+    from paper_2202_14005_b300 import _lib
+    from paper_2202_14005_b300.sense import SensePlan
+    L = _lib.lib()
+    p = lambda t: C.c_void_p(t.data_ptr())
+    maps, mask, y, gt, AHy = problem(1, 2, 8, 64, seed=1)
+    vec, *_ = params(1, seed=1)
+    tr = trainer(maps, mask, vec, AHy)
+    x = tr.xs[0]
+    out = torch.empty_like(x)
+    pv = dev(vec)
+    h = tr.plan._h
+    ws = tr.ws
+    EWORKSPACE, EINVAL_PTR, EUNSUPPORTED = -6, -2, -4
+    assert L.varnet_stage(h, p(pv), p(x), p(x), p(out), p(ws), 16) == EWORKSPACE
+    assert L.varnet_stage(h, p(pv), p(x), p(x), p(x), p(ws), ws.numel()) == EINVAL_PTR
+    assert L.varnet_stage_backward(h, p(pv), p(x), p(x), p(out), p(out), p(pv), p(ws), ws.numel()) == EINVAL_PTR
+    # rows wider than the filter-gradient kernel covers
+    W = 520
+    maps2 = dev(synth.coil_maps(2, 8, W, np.random.default_rng(0))[None].astype(np.complex64))
+    mask2 = dev(np.ones(W, dtype=np.float32))
+    plan2 = SensePlan(maps2, mask2)
+    x2 = torch.zeros((1, 8, W), dtype=torch.complex64, device="cuda")
+    o2 = torch.empty_like(x2)
+    nb = L.varnet_workspace_bytes(1, 8, W)
+    ws2 = torch.zeros(int(nb), dtype=torch.uint8, device="cuda")
+    assert L.varnet_stage(plan2._h, p(pv), p(x2), p(x2), p(o2), p(ws2), nb) == EUNSUPPORTED
+    torch.cuda.synchronize()
