@@ -201,16 +201,22 @@ int unrolled_step_backward(sense_plan plan, int kind, const float* weights, cons
  *   w[i][c][dy][dx]  i < 24, c < 2, 11x11: w[i][0] = Re k_i, w[i][1] = -Im k_i
  *   r[i][j]          RBF weights, j < 31
  *   lambda_t         (last value)
- * AHy, x_t, x_next, grad_next, grad_t: device complex64 [B][H][W], W <= 512.
- * Arithmetic: convolution inputs and filters rounded to bfloat16, float32
- * accumulation and RBF evaluation (Phi' sums the 13 centres nearest z; the
- * rest are below exp(-21) of the largest term); A^H A as sense_normal.
+ * AHy, x_t, x_next, grad_next, grad_t, nx: device complex64 [B][H][W], W <= 512.
+ * Arithmetic: filters rounded to bfloat16 at use, float32 accumulation on the
+ * tensor cores; K's image operand is split into two bfloat16 terms (hi + lo),
+ * which makes K x as accurate as float32 accumulation (the zero-mean filters
+ * cancel on smooth images, where one bfloat16 rounding of x would cost ~1e-2
+ * relative); Phi'(K x) and Phi''(K x) K g are stored in bfloat16 for K^T and
+ * the filter gradient.  Phi' sums the 13 centres nearest z (the rest are
+ * below exp(-21) of the largest term).  A^H A as sense_normal.
  *
- *   varnet_stage:          writes x_next (x_next != x_t).
+ *   varnet_stage:          writes x_next (x_next != x_t).  nx_out (optional,
+ *       else NULL) receives A^H A x_t for the reverse pass.
  *   varnet_stage_backward: given grad_next = dL/dx_next writes
  *       grad_t = grad_next - K^T(Phi''(K x_t) K grad_next) - lambda_t A^H A grad_next
  *     and ADDS dL/dparams to grad_params (filters, RBF weights, lambda_t);
- *     grad_t != grad_next (grad_t may alias x_t).  Needs the plan workspace.
+ *     grad_t != grad_next (grad_t may alias x_t).  nx_t: A^H A x_t as written
+ *     by varnet_stage, or NULL to recompute it.  Needs the plan workspace.
  * ws: device workspace of varnet_workspace_bytes(B, H, W) bytes, 256-byte
  * aligned, used by one call at a time.  Gradient sums use a fixed order:
  * results are bitwise reproducible.  Plan's stream, asynchronous. */
@@ -220,10 +226,10 @@ int unrolled_step_backward(sense_plan plan, int kind, const float* weights, cons
 size_t varnet_workspace_bytes(int B, int H, int W);
 int varnet_param_count(void);
 int varnet_stage(sense_plan plan, const float* params, const void* AHy, const void* x_t, void* x_next,
-                 void* ws, size_t ws_bytes);
+                 void* nx_out, void* ws, size_t ws_bytes);
 int varnet_stage_backward(sense_plan plan, const float* params, const void* AHy, const void* x_t,
-                          const void* grad_next, void* grad_t, float* grad_params, void* ws,
-                          size_t ws_bytes);
+                          const void* nx_t, const void* grad_next, void* grad_t, float* grad_params,
+                          void* ws, size_t ws_bytes);
 
 /* Training loss of the unrolled networks: loss[0] = mean |x - gt|^2 over the
  * plan's B*H*W complex elements (float64, fixed-order sum) and

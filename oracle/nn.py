@@ -192,11 +192,11 @@ def _ident(a):
 def varnet_regulariser(x: np.ndarray, filt: np.ndarray, wts: np.ndarray, rnd=None):
     """sum_i K_i^T Phi_i'(K_i x) as a complex image [B, H, W]; returns (value, z).
 
-    rnd (default: none) is applied to every convolution operand (filters, the
-    image, Phi'(z)) to model an implementation that stores them rounded."""
+    rnd (default: none) models an implementation that stores the filters and
+    Phi'(z) rounded; K x itself is taken as exact."""
     rnd = rnd or _ident
     wr = rnd(varnet_filters_real(filt))
-    z = conv2d(rnd(c2r(x)), wr)
+    z = conv2d(c2r(x), wr)
     u = rnd(rbf(z, wts))
     return r2c(conv2d_transpose(u, wr)), z
 

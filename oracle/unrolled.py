@@ -106,13 +106,14 @@ def varnet_stage_backward(g_next, x_t, AHy, maps, mask, filt, wts, lam_t, rnd=No
     """Reverse mode of one stage: returns (g_t, grad_filt complex, grad_wts, grad_lam).
 
     With u = K x (real), the stage is x - K^T Phi'(u) - lam (N x - b), N = A^H A.
-    rnd: optional rounding of every convolution operand (filters, x, g,
-    Phi'(z) and Phi''(z) K g); the identity by default.
+    rnd: optional rounding of the operands an implementation stores in reduced
+    precision (the filters, Phi'(z), Phi''(z) K g, and x and g where they enter
+    the filter gradient); K x and K g themselves are exact.  Identity by default.
     """
     rnd = rnd or _nn._ident
     wr = rnd(_nn.varnet_filters_real(filt))
-    xr = rnd(_nn.c2r(x_t))
-    gr = rnd(_nn.c2r(g_next))
+    xr = _nn.c2r(x_t)
+    gr = _nn.c2r(g_next)
     z = _nn.conv2d(xr, wr)
     phi = rnd(_nn.rbf(z, wts))
     dphi = _nn.rbf_grad_z(z, wts)
@@ -126,8 +127,8 @@ def varnet_stage_backward(g_next, x_t, AHy, maps, mask, filt, wts, lam_t, rnd=No
     basis = _nn.rbf_basis(z)
     g_wts = -np.einsum("bkhw,bkhwj->kj", Kg, basis, optimize=True)
     # filters, two paths: through K^T (input g, output-grad phi) and through K
-    _, gw1, _ = _nn.conv2d_backward(gr, wr, phi)          # <K g, phi>
-    _, gw2, _ = _nn.conv2d_backward(xr, wr, v)            # <K x, dphi*Kg>
+    _, gw1, _ = _nn.conv2d_backward(rnd(gr), wr, phi)     # <K g, phi>
+    _, gw2, _ = _nn.conv2d_backward(rnd(xr), wr, v)       # <K x, dphi*Kg>
     gwr = -(gw1 + gw2)                                    # [Nk, 2, k, k]
     g_filt = gwr[:, 0] - 1j * gwr[:, 1]                   # w0 = Re k, w1 = -Im k
     dc = normal(x_t, maps, mask, 0.0) - AHy

@@ -9,17 +9,24 @@
 // real-form filters w[i][c][11][11] (w[i][0] = Re k_i, w[i][1] = -Im k_i),
 // RBF weights r[i][31], step size lambda_t.
 //
-// Arithmetic: convolution inputs and filters in BF16, FP32 accumulation, RBF
-// in FP32.  The sum over the 31 Gaussians keeps the 13 centres within 6.5
-// widths of z (the others are below e^-21 of the largest term).
-//   K       warp-level tensor cores (mma.sync m16n8k16) on an im2col tile built
-//           per filter row in shared memory (K = 2 channels x 11 taps, padded to 32);
-//   K^T     mma.sync straight from a channels-last halo of the 24 (padded 32)
-//           activation channels, 121 taps x 32 channels, N = 8 (2 used);
+// Arithmetic: filters in BF16 (rounded from the float32 parameters at use),
+// warp-level tensor cores (mma.sync m16n8k16, FP32 accumulation):
+//   K       the image operand is split into two BF16 terms (x = x_hi + x_lo,
+//           relative 2^-17), so K x is as accurate as FP32 accumulation: the
+//           zero-mean filters cancel on smooth images, and a single BF16
+//           rounding of x would reach 1e-2 relative in K x.  The im2col tile
+//           of each source row is built once and serves the K_R output rows
+//           it touches (A = pixels x [x_hi taps | x_lo taps], B = filters);
+//   Phi'    FP32 over the 13 centres nearest z (the rest are below e^-21 of
+//           the largest term), fused into the K epilogue;
+//   K^T     from BF16 Phi'(z) (channels-last, 24 of 32 channels): per source
+//           row and tap column dx, A = pixels x channels and B = filters x
+//           (output row, output channel) for a band of 8 output rows, so one
+//           MMA serves 8 rows x 2 channels; the stage combine is its epilogue;
 //   dL/dw   mma.sync per image row: A = u^T (ldmatrix.trans of [w][i]), B = the
 //           Hankel matrix B[w][dx] = row[w + dx] of each shifted source row;
-//   dL/dr   CUDA cores, per-row partials.
-// Every gradient is summed per image row and reduced over rows in a fixed order.
+//   dL/dr   CUDA cores, thread-private shared-memory accumulators per row.
+// Every gradient is summed per image row or CTA and reduced in a fixed order.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -37,19 +44,26 @@ constexpr int NT = KS * KS;     // 121 taps
 constexpr int NPAR = NK * 2 * NT + NK * NW + 1;  // 6553
 constexpr int OFF_RBF = NK * 2 * NT;             // 5808
 constexpr int OFF_LAM = OFF_RBF + NK * NW;       // 6552
-constexpr int CU = 32;          // padded activation channels
+constexpr int CU = 32;          // padded channels of the stored activations u, v
 constexpr int TILE = 128;       // pixels per row tile
 constexpr int HW_ = TILE + 2 * KH;  // 138 halo pixels
-constexpr int LDI = 40;         // padded row (bf16) of im2col / halo tiles: conflict-free ldmatrix
+constexpr int LDI = 40;         // padded row (bf16) of channel tiles: conflict-free ldmatrix
 constexpr float kMu0 = -1.f;
 constexpr float kDelta = 2.f / 30.f;  // centre spacing = width sigma
+constexpr float kEinv = 0.36787944117144233f;  // e^-1
 
-__device__ __forceinline__ float bfv(__nv_bfloat16 v) { return __bfloat162float(v); }
+typedef __nv_bfloat16 bf16;
+
 __device__ __forceinline__ uint32_t smem32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem32(p)));
+}
+__device__ __forceinline__ void ldsm2(uint32_t (&r)[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
                : "r"(smem32(p)));
 }
 __device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void* p) {
@@ -64,9 +78,16 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Index of the centre nearest z, clamped so that the +-6 window stays in int range
 // (NaN maps to 0; far-out z leave an empty window: every term is below e^-21).
@@ -75,182 +96,237 @@ __device__ __forceinline__ int nearest_centre(float z) {
   return __float2int_rn(t);
 }
 
-// Phi'(z) and Phi''(z) for one channel.
+// Phi'(z) = sum_j r_j phi_j(z) and Phi''(z) = -sum_j r_j phi_j(z) (z - mu_j) / sigma^2 with
+// phi_j(z) = exp(-(z - mu_j)^2 / (2 sigma^2)), over the 13 centres nearest z.  With sigma equal
+// to the spacing and d_j = (z - mu_j) / sigma, d_{j+1} = d_j - 1 and
+// phi_{j+1} = phi_j exp(d_j - 1/2): two exponentials start the window, products continue it.
 struct Rbf {
   float d1, d2;
 };
 __device__ __forceinline__ Rbf rbf_eval(float z, const float* r) {
-  const float inv_s2 = 1.f / (kDelta * kDelta);
   const int jc = nearest_centre(z);
   const int j0 = max(jc - 6, 0), j1 = min(jc + 6, NW - 1);
   Rbf o{0.f, 0.f};
+  float d = (z - (kMu0 + kDelta * (float)j0)) * (1.f / kDelta);
+  float phi = expf(-0.5f * d * d);
+  float rho = expf(d - 0.5f);
   for (int j = j0; j <= j1; ++j) {
-    const float d = z - (kMu0 + kDelta * j);
-    const float e = expf(-0.5f * d * d * inv_s2);
-    o.d1 = fmaf(r[j], e, o.d1);
-    o.d2 = fmaf(r[j] * e, -d * inv_s2, o.d2);
+    const float t = r[j] * phi;
+    o.d1 += t;
+    o.d2 = fmaf(t, -d * (1.f / kDelta), o.d2);
+    phi *= rho;
+    rho *= kEinv;
+    d -= 1.f;
   }
   return o;
 }
 
 // ------------------------------------------------------------------ packing
-// Wd[dy][n][k]: K operand per filter row, k = c * 11 + dx (22 of 32 used), n = filter (24 of 32).
-// WT[t][c][k]: K^T operand per halo offset t = (ry, rx), k = filter (24 of 32), flipped taps.
-__global__ void k_vn_pack(const float* prm, __nv_bfloat16* wd, __nv_bfloat16* wt) {
+constexpr int K_R = 4;          // output rows per K CTA
+constexpr int K_KP = 48;        // im2col columns: [x_hi: c0 dx 0..10, c1 dx 0..10, 0, 0 | x_lo: same]
+constexpr int K_LD = 56;        // row pitch (bf16) of the im2col tile and the K table
+constexpr int K_W_ELEMS = KS * NK * K_LD;
+constexpr int KT_W_ELEMS = NT * 2 * CU;
+
+// wk[dy][n][k]: K operand per filter row, the BF16 filter tap w[n][c][dy][dx] at k = part * 24 +
+//   c * 11 + dx for both parts; zero elsewhere.
+// wn[dy][dx][c][i]: K^T operand, the same taps with the filter index i contiguous (zero for i >= 24).
+__global__ void k_vn_pack(const float* prm, bf16* wk, bf16* wn) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < KS * CU * LDI) {
-    const int dy = i / (CU * LDI), n = (i / LDI) % CU, k = i % LDI;
+  if (i < K_W_ELEMS) {
+    const int dy = i / (NK * K_LD), n = (i / K_LD) % NK, k = i % K_LD;
     float v = 0.f;
-    if (n < NK && k < 2 * KS) {
-      const int c = k / KS, dx = k % KS;
+    if (k < K_KP && (k % 24) < 2 * KS) {
+      const int kk = k % 24, c = kk / KS, dx = kk % KS;
       v = prm[(n * 2 + c) * NT + dy * KS + dx];
     }
-    wd[i] = __float2bfloat16_rn(v);
+    wk[i] = __float2bfloat16_rn(v);
   }
-  const int j = i - KS * CU * LDI;
-  if (j >= 0 && j < NT * 2 * CU) {
+  const int j = i - K_W_ELEMS;
+  if (j >= 0 && j < KT_W_ELEMS) {
     const int t = j / (2 * CU), c = (j / CU) % 2, k = j % CU;
-    float v = 0.f;
-    if (k < NK) v = prm[(k * 2 + c) * NT + (NT - 1 - t)];
-    wt[j] = __float2bfloat16_rn(v);
+    wn[j] = __float2bfloat16_rn(k < NK ? prm[(k * 2 + c) * NT + t] : 0.f);
   }
 }
 
 // -------------------------------------------------------------- K (2 -> 24)
-// mode 0 (forward stage):  u = Phi'(K x)                         -> u [px][32] bf16
-// mode 1 (reverse stage):  z = K x, kg = K g;  u = Phi'(z), v = Phi''(z) kg
-//                          -> u, v [px][32] bf16, z, kg [px][24] fp32
+// NSRC = 1 (forward stage):  u = Phi'(K x)                          -> u [px][32] bf16
+// NSRC = 2 (reverse stage):  z = K x, kg = K g;  u = Phi'(z), v = Phi''(z) kg
+//                            -> u, v [px][32] bf16, z, kg [px][24] fp32
+// CTA: 128 pixels x K_R rows, 8 warps x 16 pixels.  Source rows stream through a double-
+// buffered FP32 stage (cp.async) and a double-buffered im2col tile; each source row s feeds
+// every output row h of the CTA with 0 <= s - h + 5 <= 10 (filter row dy = s - h + 5).
 struct KArgs {
-  int B, H, W, mode;
+  int B, H, W;
   const float2* x;
   const float2* g;
-  const __nv_bfloat16* wd;
+  const bf16* wk;
   const float* rbf;  // [24][31]
-  __nv_bfloat16* u;
-  __nv_bfloat16* v;
+  bf16* u;
+  bf16* v;
   float* z;
   float* kg;
 };
 
-constexpr int K_SMEM_HALO = 2 * 2 * KS * HW_ * 2;      // [src][c][row][px] bf16
-constexpr int K_SMEM_COL = 2 * TILE * LDI * 2;         // im2col per source
-constexpr int K_SMEM_W = KS * CU * LDI * 2;
-constexpr int K_SMEM = K_SMEM_HALO + K_SMEM_COL + K_SMEM_W + NK * NW * 4;
+constexpr int K_THREADS = 256;
+constexpr int K_STG = 140;  // staged source row (float2): columns w0 - 6 .. w0 + 133
 
-__global__ void __launch_bounds__(128) k_vn_K(const KArgs a) {
+template <int NSRC>
+struct KSmem {
+  static constexpr int W_BYTES = K_W_ELEMS * 2;
+  static constexpr int COL_BYTES = TILE * K_LD * 2;  // one im2col tile
+  static constexpr int STG_BYTES = K_STG * 8;
+  static constexpr int OFF_COL = W_BYTES;
+  static constexpr int OFF_STG = OFF_COL + 2 * NSRC * COL_BYTES;
+  static constexpr int OFF_R = OFF_STG + 2 * NSRC * STG_BYTES;
+  static constexpr int TOTAL = OFF_R + NK * NW * 4;
+};
+
+template <int NSRC>
+__global__ void __launch_bounds__(K_THREADS, NSRC == 1 ? 3 : 2) k_vn_K(const KArgs a) {
+  using S = KSmem<NSRC>;
   extern __shared__ __align__(16) uint8_t dsm[];
-  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);                       // [2][2][11][138]
-  __nv_bfloat16* col = reinterpret_cast<__nv_bfloat16*>(dsm + K_SMEM_HALO);          // [2][128][40]
-  __nv_bfloat16* wd = reinterpret_cast<__nv_bfloat16*>(dsm + K_SMEM_HALO + K_SMEM_COL);
-  float* s_r = reinterpret_cast<float*>(dsm + K_SMEM_HALO + K_SMEM_COL + K_SMEM_W);
-  const int nsrc = a.mode ? 2 : 1;
-  const int bh = blockIdx.y, b = bh / a.H, h = bh % a.H, w0 = blockIdx.x * TILE;
-  for (int i = threadIdx.x; i < KS * CU * LDI / 8; i += blockDim.x)
-    reinterpret_cast<uint4*>(wd)[i] = reinterpret_cast<const uint4*>(a.wd)[i];
-  for (int i = threadIdx.x; i < NK * NW; i += blockDim.x) s_r[i] = a.rbf[i];
-  for (int s = 0; s < nsrc; ++s) {
-    const float2* src = s ? a.g : a.x;
-    for (int i = threadIdx.x; i < KS * HW_; i += blockDim.x) {
-      const int r = i / HW_, px = i % HW_;
-      const int yy = h - KH + r, xx = w0 - KH + px;
-      float2 v = make_float2(0.f, 0.f);
-      if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) v = src[((size_t)b * a.H + yy) * a.W + xx];
-      halo[((s * 2 + 0) * KS + r) * HW_ + px] = __float2bfloat16_rn(v.x);
-      halo[((s * 2 + 1) * KS + r) * HW_ + px] = __float2bfloat16_rn(v.y);
-    }
-  }
-  // columns 22..39 of the im2col tiles stay zero
-  for (int i = threadIdx.x; i < 2 * TILE * LDI; i += blockDim.x) col[i] = __float2bfloat16_rn(0.f);
-  __syncthreads();
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bf16* wk = reinterpret_cast<const bf16*>(dsm);
+  float* s_r = reinterpret_cast<float*>(dsm + S::OFF_R);
+  const int w0 = blockIdx.x * TILE, h0 = blockIdx.y * K_R, b = blockIdx.z;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gid = lane >> 2, tig = lane & 3, mi = lane >> 3, rr = lane & 7;
-  float acc[2][2][4][4];
+
+  for (int i = tid; i < S::W_BYTES / 16; i += K_THREADS)
+    cp16(dsm + i * 16, reinterpret_cast<const uint8_t*>(a.wk) + i * 16, true);
+  for (int i = tid; i < NK * NW; i += K_THREADS) s_r[i] = a.rbf[i];
+  const int s_lo = max(h0 - KH, 0), s_hi = min(h0 + K_R - 1 + KH, a.H - 1);
+  const int nrows = s_hi - s_lo + 1;
+  auto stage = [&](int k) {
+    const int s = s_lo + k, buf = k & 1;
+    for (int i = tid; i < NSRC * (K_STG / 2); i += K_THREADS) {
+      const int src = i / (K_STG / 2), q = i % (K_STG / 2);
+      const int col = w0 - 6 + 2 * q;  // even; W is even, so col + 1 < W whenever col < W
+      const bool ok = col >= 0 && col < a.W;
+      const float2* base = src ? a.g : a.x;
+      cp16(dsm + S::OFF_STG + (buf * NSRC + src) * S::STG_BYTES + q * 16,
+           base + (ok ? ((size_t)b * a.H + s) * a.W + col : 0), ok);
+    }
+  };
+  stage(0);
+  cp_commit();
+
+  float acc[NSRC][K_R][3][4];
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < NSRC; ++s)
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int r = 0; r < K_R; ++r)
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
+      for (int nt = 0; nt < 3; ++nt)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[s][mt][nt][e] = 0.f;
+        for (int e = 0; e < 4; ++e) acc[s][r][nt][e] = 0.f;
 
 #pragma unroll 1
-  for (int dy = 0; dy < KS; ++dy) {
-    for (int i = threadIdx.x; i < nsrc * TILE * 2 * KS; i += blockDim.x) {
-      const int s = i / (TILE * 2 * KS), rem = i % (TILE * 2 * KS);
-      const int m = rem / (2 * KS), k = rem % (2 * KS);
-      const int c = k / KS, dx = k % KS;
-      col[(s * TILE + m) * LDI + k] = halo[((s * 2 + c) * KS + dy) * HW_ + m + dx];
+  for (int k = 0; k < nrows; ++k) {
+    if (k + 1 < nrows) stage(k + 1);
+    cp_commit();
+    cp_wait<1>();  // everything but the newest group: source row k and the tables have landed
+    __syncthreads();
+    // im2col of source row k: item (src, pixel m, part); halo column of tap dx = stage index m + dx + 1
+    for (int it = tid; it < NSRC * TILE * 2; it += K_THREADS) {
+      const int part = it & 1, m = (it >> 1) % TILE, src = it / (2 * TILE);
+      const float2* stg =
+          reinterpret_cast<const float2*>(dsm + S::OFF_STG + ((k & 1) * NSRC + src) * S::STG_BYTES);
+      bf16 t[24];
+#pragma unroll
+      for (int dx = 0; dx < KS; ++dx) {
+        const float2 v = stg[m + dx + 1];
+        bf16 re = __float2bfloat16_rn(v.x), im = __float2bfloat16_rn(v.y);
+        if (part) {
+          re = __float2bfloat16_rn(v.x - __bfloat162float(re));
+          im = __float2bfloat16_rn(v.y - __bfloat162float(im));
+        }
+        t[dx] = re;
+        t[KS + dx] = im;
+      }
+      t[22] = t[23] = __float2bfloat16_rn(0.f);
+      uint4* dst = reinterpret_cast<uint4*>(dsm + S::OFF_COL + ((k & 1) * NSRC + src) * S::COL_BYTES +
+                                            m * K_LD * 2 + part * 48);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        dst[q] = make_uint4(pack2(t[8 * q], t[8 * q + 1]), pack2(t[8 * q + 2], t[8 * q + 3]),
+                            pack2(t[8 * q + 4], t[8 * q + 5]), pack2(t[8 * q + 6], t[8 * q + 7]));
     }
     __syncthreads();
+    const int s = s_lo + k;
+    const bf16* colb = reinterpret_cast<const bf16*>(dsm + S::OFF_COL + (k & 1) * NSRC * S::COL_BYTES);
 #pragma unroll
-    for (int kk = 0; kk < 32; kk += 16) {
-      uint32_t bfr[2][4];
+    for (int ks = 0; ks < 3; ++ks) {
+      uint32_t af[NSRC][4];
 #pragma unroll
-      for (int np = 0; np < 2; ++np) {  // n-tile pairs (16 filters)
-        const int n = np * 16 + (mi >> 1) * 8 + rr, k = kk + (mi & 1) * 8;
-        ldsm4(bfr[np], wd + (dy * CU + n) * LDI + k);
-      }
+      for (int src = 0; src < NSRC; ++src)
+        ldsm4(af[src], colb + (src * TILE + warp * 16 + (mi & 1) * 8 + rr) * K_LD + ks * 16 + (mi >> 1) * 8);
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        if (s >= nsrc) break;
+      for (int r = 0; r < K_R; ++r) {
+        const int dy = s - (h0 + r) + KH;
+        if (dy < 0 || dy >= KS) continue;
+        const bf16* wrow = wk + dy * NK * K_LD;
+        uint32_t b4[4], b2[2];
+        ldsm4(b4, wrow + ((mi >> 1) * 8 + rr) * K_LD + ks * 16 + (mi & 1) * 8);
+        ldsm2(b2, wrow + (16 + rr) * K_LD + ks * 16 + (mi & 1) * 8);
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          uint32_t af[4];
-          const int m = warp * 32 + mt * 16 + (mi & 1) * 8 + rr, k = kk + (mi >> 1) * 8;
-          ldsm4(af, col + (s * TILE + m) * LDI + k);
-#pragma unroll
-          for (int np = 0; np < 2; ++np) {
-            mma16816(acc[s][mt][2 * np], af, bfr[np][0], bfr[np][1]);
-            mma16816(acc[s][mt][2 * np + 1], af, bfr[np][2], bfr[np][3]);
-          }
+        for (int src = 0; src < NSRC; ++src) {
+          mma16816(acc[src][r][0], af[src], b4[0], b4[1]);
+          mma16816(acc[src][r][1], af[src], b4[2], b4[3]);
+          mma16816(acc[src][r][2], af[src], b2[0], b2[1]);
         }
       }
     }
-    __syncthreads();
   }
-  // epilogue: element (pixel row, filter col) of each fragment
+  // epilogue: fragment element (pixel gid / gid + 8, filter nt * 8 + 2 tig + e)
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  for (int r = 0; r < K_R; ++r) {
+    const int h = h0 + r;
+    if (h >= a.H) continue;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      const int w = w0 + warp * 32 + mt * 16 + gid + half * 8;
+      const int w = w0 + warp * 16 + gid + half * 8;
       if (w >= a.W) continue;
       const size_t p = ((size_t)b * a.H + h) * a.W + w;
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
+      for (int nt = 0; nt < 3; ++nt) {
         const int i0 = nt * 8 + 2 * tig;
-        float uo[2] = {0.f, 0.f}, vo[2] = {0.f, 0.f};
+        float uo[2], vo[2], zo[2], ko[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int i = i0 + e;
-          if (i >= NK) continue;
-          const float z = acc[0][mt][nt][half * 2 + e];
-          const Rbf f = rbf_eval(z, s_r + i * NW);
+          const float z = acc[0][r][nt][half * 2 + e];
+          const Rbf f = rbf_eval(z, s_r + (i0 + e) * NW);
           uo[e] = f.d1;
-          if (a.mode) {
-            const float kgv = acc[1][mt][nt][half * 2 + e];
-            vo[e] = f.d2 * kgv;
-            a.z[p * NK + i] = z;
-            a.kg[p * NK + i] = kgv;
-          }
+          zo[e] = z;
+          ko[e] = NSRC == 2 ? acc[NSRC - 1][r][nt][half * 2 + e] : 0.f;
+          vo[e] = f.d2 * ko[e];
         }
         *reinterpret_cast<uint32_t*>(a.u + p * CU + i0) =
             pack2(__float2bfloat16_rn(uo[0]), __float2bfloat16_rn(uo[1]));
-        if (a.mode)
+        if (NSRC == 2) {
           *reinterpret_cast<uint32_t*>(a.v + p * CU + i0) =
               pack2(__float2bfloat16_rn(vo[0]), __float2bfloat16_rn(vo[1]));
+          *reinterpret_cast<float2*>(a.z + p * NK + i0) = make_float2(zo[0], zo[1]);
+          *reinterpret_cast<float2*>(a.kg + p * NK + i0) = make_float2(ko[0], ko[1]);
+        }
       }
+      // channels 24..31 of the stored activations are zero
+      *reinterpret_cast<uint32_t*>(a.u + p * CU + NK + 2 * tig) = 0u;
+      if (NSRC == 2) *reinterpret_cast<uint32_t*>(a.v + p * CU + NK + 2 * tig) = 0u;
     }
+  }
 }
 
 // ------------------------------------------------------------ K^T (24 -> 2)
 // out = base - K^T(src) - lambda (n - c)   (c may be NULL)
+// CTA: 128 pixels x 8 output rows, 4 warps x 32 pixels.  For source row s and tap column dx:
+//   D[px][(r, c)] += sum_i src[s][px + 5 - dx][i] w[i][c][h0 + r + 5 - s][dx]
+// (A = the staged source row via ldmatrix, B = the filter taps of the two output channels for
+// output rows r = 0..3 and 4..7, zero where the filter row falls outside 0..10).
 struct KTArgs {
   int B, H, W;
-  const __nv_bfloat16* src;  // [px][32]
-  const __nv_bfloat16* wt;   // [121][2][32]
+  const bf16* src;  // [px][32]
+  const bf16* wn;   // [11][11][2][32]
   const float2* base;
   const float2* n;
   const float2* c;
@@ -258,55 +334,89 @@ struct KTArgs {
   float2* out;
 };
 
-constexpr int KT_SMEM_HALO = KS * HW_ * LDI * 2;
-constexpr int KT_SMEM = KT_SMEM_HALO + NT * 2 * CU * 2;
+constexpr int KT_BAND = 8;
+constexpr int KT_NBUF = 3;
+constexpr int KT_ROW = HW_ * LDI;  // bf16 elements of one staged source row
+constexpr int KT_W_BYTES = KT_W_ELEMS * 2;
+constexpr int KT_SMEM = KT_W_BYTES + KT_NBUF * KT_ROW * 2;
 
-__device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem32(dst)), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-
-__global__ void __launch_bounds__(128) k_vn_KT(const KTArgs a) {
+__global__ void __launch_bounds__(128, 4) k_vn_KT(const KTArgs a) {
   extern __shared__ __align__(16) uint8_t dsm[];
-  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);  // [11][138][40]
-  __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(dsm + KT_SMEM_HALO);
-  const int bh = blockIdx.y, b = bh / a.H, h = bh % a.H, w0 = blockIdx.x * TILE;
-  for (int i = threadIdx.x; i < NT * 2 * CU / 8; i += blockDim.x) cp16(wt + i * 8, a.wt + i * 8, true);
-  for (int i = threadIdx.x; i < KS * HW_ * 4; i += blockDim.x) {
-    const int q = i & 3, px = (i >> 2) % HW_, r = (i >> 2) / HW_;
-    const int yy = h - KH + r, xx = w0 - KH + px;
-    const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-    cp16(halo + (r * HW_ + px) * LDI + q * 8,
-         a.src + (ok ? (((size_t)b * a.H + yy) * a.W + xx) * CU + q * 8 : 0), ok);
-  }
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bf16* wn = reinterpret_cast<const bf16*>(dsm);
+  bf16* ub = reinterpret_cast<bf16*>(dsm + KT_W_BYTES);
+  const int w0 = blockIdx.x * TILE, h0 = blockIdx.y * KT_BAND, b = blockIdx.z;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gid = lane >> 2, tig = lane & 3, mi = lane >> 3, rr = lane & 7;
-  float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  for (int i = tid; i < KT_W_BYTES / 16; i += blockDim.x)
+    cp16(dsm + i * 16, reinterpret_cast<const uint8_t*>(a.wn) + i * 16, true);
+  const int s_lo = max(h0 - KH, 0), s_hi = min(h0 + KT_BAND - 1 + KH, a.H - 1);
+  const int nrows = s_hi - s_lo + 1;
+  auto stage = [&](int k) {
+    const int s = s_lo + k;
+    bf16* dst = ub + (k % KT_NBUF) * KT_ROW;
+    for (int i = tid; i < HW_ * 4; i += blockDim.x) {
+      const int px = i >> 2, q = i & 3;
+      const int xx = w0 - KH + px;
+      const bool ok = xx >= 0 && xx < a.W;
+      cp16(dst + px * LDI + q * 8, a.src + (ok ? (((size_t)b * a.H + s) * a.W + xx) * CU + q * 8 : 0), ok);
+    }
+  };
+  stage(0);
+  cp_commit();
+  if (nrows > 1) stage(1);
+  cp_commit();
+  float d[2][2][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[mt][nt][e] = 0.f;
+
 #pragma unroll 1
-  for (int t = 0; t < NT; ++t) {
-    const int ry = t / KS, rx = t % KS;
+  for (int k = 0; k < nrows; ++k) {
+    cp_wait<1>();  // source row k has landed (only row k + 1 may be pending)
+    __syncthreads();  // ... for every thread; and row k - 1's buffer is free for row k + 2
+    if (k + 2 < nrows) stage(k + 2);
+    cp_commit();
+    const int s = s_lo + k;
+    const bf16* u = ub + (k % KT_NBUF) * KT_ROW;
+    const bool v0 = s >= h0 - KH && s <= h0 + 3 + KH;  // some output row 0..3 uses source row s
+    const bool v1 = s >= h0 + 4 - KH && s <= h0 + 7 + KH;
+#pragma unroll 1
+    for (int dx = 0; dx < KS; ++dx) {
 #pragma unroll
-    for (int kk = 0; kk < CU; kk += 16) {
-      uint32_t b0 = 0u, b1 = 0u;
-      if (gid < 2) {
-        b0 = *reinterpret_cast<const uint32_t*>(wt + (t * 2 + gid) * CU + kk + 2 * tig);
-        b1 = *reinterpret_cast<const uint32_t*>(wt + (t * 2 + gid) * CU + kk + 8 + 2 * tig);
-      }
+      for (int ks = 0; ks < 2; ++ks) {
+        uint32_t bq[2][2];
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        uint32_t af[4];
-        const int m = warp * 32 + mt * 16 + (mi & 1) * 8 + rr, k = kk + (mi >> 1) * 8;
-        ldsm4(af, halo + (ry * HW_ + m + rx) * LDI + k);
-        mma16816(d[mt], af, b0, b1);
+        for (int nt = 0; nt < 2; ++nt) {
+          const int r = nt * 4 + (gid >> 1), c = gid & 1, dy = h0 + r + KH - s;
+          bq[nt][0] = bq[nt][1] = 0u;
+          if ((unsigned)dy < (unsigned)KS) {
+            const bf16* wp = wn + ((dy * KS + dx) * 2 + c) * CU + ks * 16 + 2 * tig;
+            bq[nt][0] = *reinterpret_cast<const uint32_t*>(wp);
+            bq[nt][1] = *reinterpret_cast<const uint32_t*>(wp + 8);
+          }
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          uint32_t af[4];
+          const int m = warp * 32 + mt * 16 + (mi & 1) * 8 + rr;
+          ldsm4(af, u + (m + 2 * KH - dx) * LDI + ks * 16 + (mi >> 1) * 8);
+          if (v0) mma16816(d[mt][0], af, bq[0][0], bq[0][1]);
+          if (v1) mma16816(d[mt][1], af, bq[1][0], bq[1][1]);
+        }
       }
     }
   }
-  if (tig == 0) {
-    const float lam = a.lam[0];
+  // epilogue: (c0, c1) = (re, im) of pixel gid, output row nt * 4 + tig; (c2, c3) pixel gid + 8
+  const float lam = a.lam[0];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int h = h0 + nt * 4 + tig;
+      if (h >= a.H) continue;
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int w = w0 + warp * 32 + mt * 16 + gid + half * 8;
@@ -314,10 +424,10 @@ __global__ void __launch_bounds__(128) k_vn_KT(const KTArgs a) {
         const size_t p = ((size_t)b * a.H + h) * a.W + w;
         const float2 bv = a.base[p], nv = a.n[p];
         const float2 cv = a.c ? a.c[p] : make_float2(0.f, 0.f);
-        a.out[p] = make_float2(bv.x - d[mt][2 * half] - lam * (nv.x - cv.x),
-                               bv.y - d[mt][2 * half + 1] - lam * (nv.y - cv.y));
+        a.out[p] = make_float2(bv.x - d[mt][nt][2 * half] - lam * (nv.x - cv.x),
+                               bv.y - d[mt][nt][2 * half + 1] - lam * (nv.y - cv.y));
       }
-  }
+    }
 }
 
 // ------------------------------------------------------- filter gradients
@@ -420,35 +530,43 @@ __global__ void __launch_bounds__(128) k_vn_wgrad(int B, int H, int W, const __n
   }
 }
 
-// RBF weight gradient partial per row: P[i][j] = sum_w kg[w][i] * phi_j(z[w][i]).
-// Thread (i, q): pixels w = q, q + 8, ...; the eight q-partials are added in order.
-__global__ void __launch_bounds__(192) k_vn_rbfgrad(int B, int H, int W, const float* z, const float* kg,
+// RBF weight gradient partial per image row: P[i][j] = sum_w kg[w][i] phi_j(z[w][i]).
+// Thread (i, q), i < 24, q < 10, takes pixels w = q, q + 10, ... and adds into its own
+// shared-memory row of 31 accumulators (Gaussian window by the product recurrence of
+// rbf_eval); the ten rows of each filter are then added in order.
+constexpr int RG_Q = 10;
+constexpr int RG_LD = NW + 2;  // 33: distinct banks for the 32 lanes at equal j
+__global__ void __launch_bounds__(256) k_vn_rbfgrad(int B, int H, int W, const float* z, const float* kg,
                                                     float* partial) {
-  __shared__ float s_p[8][NK * NW];
-  const int i = threadIdx.x % NK, q = threadIdx.x / NK;  // 24 x 8
+  __shared__ float acc[NK * RG_Q * RG_LD];
+  const int t = threadIdx.x;
+  for (int k = t; k < NK * RG_Q * RG_LD; k += blockDim.x) acc[k] = 0.f;
+  __syncthreads();
   const int b = blockIdx.x / H, h = blockIdx.x % H;
-  float acc[NW];
-#pragma unroll
-  for (int j = 0; j < NW; ++j) acc[j] = 0.f;
-  const float inv_s2 = 1.f / (kDelta * kDelta);
-  for (int w = q; w < W; w += 8) {
-    const size_t p = ((size_t)b * H + h) * W + w;
-    const float zz = z[p * NK + i], g = kg[p * NK + i];
-    const int jc = nearest_centre(zz);
-#pragma unroll
-    for (int j = 0; j < NW; ++j) {
-      if (j < jc - 6 || j > jc + 6) continue;
-      const float d = zz - (kMu0 + kDelta * j);
-      acc[j] = fmaf(g, expf(-0.5f * d * d * inv_s2), acc[j]);
+  if (t < NK * RG_Q) {
+    const int i = t % NK, q = t / NK;
+    float* my = acc + t * RG_LD;
+    for (int w = q; w < W; w += RG_Q) {
+      const size_t p = ((size_t)b * H + h) * W + w;
+      const float zz = z[p * NK + i], g = kg[p * NK + i];
+      const int jc = nearest_centre(zz);
+      const int j0 = max(jc - 6, 0), j1 = min(jc + 6, NW - 1);
+      float d = (zz - (kMu0 + kDelta * (float)j0)) * (1.f / kDelta);
+      float phi = g * expf(-0.5f * d * d);
+      float rho = expf(d - 0.5f);
+      for (int j = j0; j <= j1; ++j) {
+        my[j] += phi;
+        phi *= rho;
+        rho *= kEinv;
+      }
     }
   }
-#pragma unroll
-  for (int j = 0; j < NW; ++j) s_p[q][i * NW + j] = acc[j];
   __syncthreads();
   float* out = partial + (size_t)blockIdx.x * (NK * NW);
-  for (int k = threadIdx.x; k < NK * NW; k += blockDim.x) {
+  for (int k = t; k < NK * NW; k += blockDim.x) {
+    const int i = k / NW, j = k % NW;
     float s = 0.f;
-    for (int qq = 0; qq < 8; ++qq) s += s_p[qq][k];
+    for (int q = 0; q < RG_Q; ++q) s += acc[(q * NK + i) * RG_LD + j];
     out[k] = s;
   }
 }
@@ -471,19 +589,17 @@ __global__ void __launch_bounds__(256) k_vn_reduce(const float* partial, int nro
   }
 }
 
-// grad_lambda_t -= Re<g, n - c> is a row-dot via the CG helper (launch_dot_rows).
-
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct VnLayout {
-  size_t wd, wt, u, v, z, kg, n1, n2, part, pdot, total;
+  size_t wk, wn, u, v, z, kg, n1, n2, part, pdot, total;
 };
 VnLayout vn_layout(int B, int H, int W) {
   VnLayout L;
   const size_t px = (size_t)B * H * W;
   size_t o = 0;
-  L.wd = o; o += up256(KS * CU * LDI * 2);
-  L.wt = o; o += up256(NT * 2 * CU * 2);
+  L.wk = o; o += up256(K_W_ELEMS * 2);
+  L.wn = o; o += up256(KT_W_ELEMS * 2);
   L.u = o; o += up256(px * CU * 2);
   L.v = o; o += up256(px * CU * 2);
   L.z = o; o += up256(px * NK * 4);
@@ -501,7 +617,10 @@ int vn_prepare() {
   static std::mutex mu;
   std::lock_guard<std::mutex> l(mu);
   if (state == 0)
-    state = (cudaFuncSetAttribute(k_vn_K, cudaFuncAttributeMaxDynamicSharedMemorySize, K_SMEM) == cudaSuccess &&
+    state = (cudaFuncSetAttribute(k_vn_K<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<1>::TOTAL) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(k_vn_K<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<2>::TOTAL) ==
+                 cudaSuccess &&
              cudaFuncSetAttribute(k_vn_KT, cudaFuncAttributeMaxDynamicSharedMemorySize, KT_SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_vn_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem(WG_MAXW)) ==
                  cudaSuccess)
@@ -512,48 +631,55 @@ int vn_prepare() {
 
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-int vn_check(sense_plan p, const float* prm, const void* AHy, const void* xt, void* ws, size_t ws_bytes) {
-  if (!p || !prm || !AHy || !xt || !ws || !al16(AHy) || !al16(xt) || ((uintptr_t)ws & 255u)) return SENSE_EINVAL_PTR;
-  if (p->W > WG_MAXW || (long long)p->B * p->H > 65535) return SENSE_EUNSUPPORTED;
+int vn_check(sense_plan p, const float* prm, const void* AHy, const void* xt, const void* nx, void* ws,
+             size_t ws_bytes) {
+  if (!p || !prm || !AHy || !xt || !ws || !al16(AHy) || !al16(xt) || (nx && !al16(nx)) || ((uintptr_t)ws & 255u))
+    return SENSE_EINVAL_PTR;
+  if (p->W > WG_MAXW || p->B > 65535 || (p->H + K_R - 1) / K_R > 65535) return SENSE_EUNSUPPORTED;
   if (ws_bytes < vn_layout(p->B, p->H, p->W).total) return SENSE_EWORKSPACE;
   return vn_prepare();
 }
 
 void vn_pack(const float* prm, uint8_t* ws, const VnLayout& L, cudaStream_t st) {
-  const int n = KS * CU * LDI + NT * 2 * CU;
+  const int n = K_W_ELEMS + KT_W_ELEMS;
   prof_mark("vn_misc", st, false);
-  k_vn_pack<<<(n + 255) / 256, 256, 0, st>>>(prm, reinterpret_cast<__nv_bfloat16*>(ws + L.wd),
-                                             reinterpret_cast<__nv_bfloat16*>(ws + L.wt));
+  k_vn_pack<<<(n + 255) / 256, 256, 0, st>>>(prm, reinterpret_cast<bf16*>(ws + L.wk),
+                                             reinterpret_cast<bf16*>(ws + L.wn));
   prof_mark("vn_misc", st, true);
 }
 
-int launch_K(sense_plan p, int mode, const float* prm, const float2* x, const float2* g, uint8_t* ws,
+int launch_K(sense_plan p, int nsrc, const float* prm, const float2* x, const float2* g, uint8_t* ws,
              const VnLayout& L) {
   KArgs a;
-  a.B = p->B; a.H = p->H; a.W = p->W; a.mode = mode;
+  a.B = p->B; a.H = p->H; a.W = p->W;
   a.x = x; a.g = g;
-  a.wd = reinterpret_cast<const __nv_bfloat16*>(ws + L.wd);
+  a.wk = reinterpret_cast<const bf16*>(ws + L.wk);
   a.rbf = prm + OFF_RBF;
-  a.u = reinterpret_cast<__nv_bfloat16*>(ws + L.u);
-  a.v = reinterpret_cast<__nv_bfloat16*>(ws + L.v);
+  a.u = reinterpret_cast<bf16*>(ws + L.u);
+  a.v = reinterpret_cast<bf16*>(ws + L.v);
   a.z = reinterpret_cast<float*>(ws + L.z);
   a.kg = reinterpret_cast<float*>(ws + L.kg);
-  const char* grp = mode ? "vn_Kbwd" : "vn_K";
+  const dim3 grid((p->W + TILE - 1) / TILE, (p->H + K_R - 1) / K_R, p->B);
+  const char* grp = nsrc == 2 ? "vn_Kbwd" : "vn_K";
   prof_mark(grp, p->stream, false);
-  k_vn_K<<<dim3((p->W + TILE - 1) / TILE, p->B * p->H), 128, K_SMEM, p->stream>>>(a);
+  if (nsrc == 2)
+    k_vn_K<2><<<grid, K_THREADS, KSmem<2>::TOTAL, p->stream>>>(a);
+  else
+    k_vn_K<1><<<grid, K_THREADS, KSmem<1>::TOTAL, p->stream>>>(a);
   prof_mark(grp, p->stream, true);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
-int launch_KT(sense_plan p, const __nv_bfloat16* src, const float* prm, const float2* base, const float2* n,
+int launch_KT(sense_plan p, const bf16* src, const float* prm, const float2* base, const float2* n,
               const float2* c, float2* out, uint8_t* ws, const VnLayout& L) {
   KTArgs a;
   a.B = p->B; a.H = p->H; a.W = p->W;
   a.src = src;
-  a.wt = reinterpret_cast<const __nv_bfloat16*>(ws + L.wt);
+  a.wn = reinterpret_cast<const bf16*>(ws + L.wn);
   a.base = base; a.n = n; a.c = c; a.lam = prm + OFF_LAM; a.out = out;
+  const dim3 grid((p->W + TILE - 1) / TILE, (p->H + KT_BAND - 1) / KT_BAND, p->B);
   prof_mark("vn_KT", p->stream, false);
-  k_vn_KT<<<dim3((p->W + TILE - 1) / TILE, p->B * p->H), 128, KT_SMEM, p->stream>>>(a);
+  k_vn_KT<<<grid, 128, KT_SMEM, p->stream>>>(a);
   prof_mark("vn_KT", p->stream, true);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -575,64 +701,68 @@ size_t varnet_workspace_bytes(int B, int H, int W) {
 
 int varnet_param_count(void) { return NPAR; }
 
-int varnet_stage(sense_plan p, const float* prm, const void* AHy, const void* x_t, void* x_next, void* ws,
-                 size_t ws_bytes) {
-  if (int e = vn_check(p, prm, AHy, x_t, ws, ws_bytes)) return e;
-  if (!x_next || !al16(x_next) || x_next == x_t) return SENSE_EINVAL_PTR;
+int varnet_stage(sense_plan p, const float* prm, const void* AHy, const void* x_t, void* x_next, void* nx_out,
+                 void* ws, size_t ws_bytes) {
+  if (int e = vn_check(p, prm, AHy, x_t, nx_out, ws, ws_bytes)) return e;
+  if (!x_next || !al16(x_next) || x_next == x_t || nx_out == x_t || nx_out == x_next) return SENSE_EINVAL_PTR;
   uint8_t* w8 = static_cast<uint8_t*>(ws);
   const VnLayout L = vn_layout(p->B, p->H, p->W);
   const float2* x = static_cast<const float2*>(x_t);
-  float2* n1 = reinterpret_cast<float2*>(w8 + L.n1);
+  float2* n1 = nx_out ? static_cast<float2*>(nx_out) : reinterpret_cast<float2*>(w8 + L.n1);
   vn_pack(prm, w8, L, p->stream);
   if (int e = normal0(p, x, n1)) return e;
-  if (int e = launch_K(p, 0, prm, x, nullptr, w8, L)) return e;
-  if (int e = launch_KT(p, reinterpret_cast<const __nv_bfloat16*>(w8 + L.u), prm, x, n1,
-                        static_cast<const float2*>(AHy), static_cast<float2*>(x_next), w8, L))
+  if (int e = launch_K(p, 1, prm, x, nullptr, w8, L)) return e;
+  if (int e = launch_KT(p, reinterpret_cast<const bf16*>(w8 + L.u), prm, x, n1, static_cast<const float2*>(AHy),
+                        static_cast<float2*>(x_next), w8, L))
     return e;
   prof_count(3);
   return SENSE_OK;
 }
 
-int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const void* x_t,
+int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const void* x_t, const void* nx_t,
                           const void* grad_next, void* grad_t, float* grad_prm, void* ws, size_t ws_bytes) {
-  if (int e = vn_check(p, prm, AHy, x_t, ws, ws_bytes)) return e;
-  if (!grad_next || !grad_t || !grad_prm || !al16(grad_next) || !al16(grad_t) || grad_t == grad_next)
+  if (int e = vn_check(p, prm, AHy, x_t, nx_t, ws, ws_bytes)) return e;
+  if (!grad_next || !grad_t || !grad_prm || !al16(grad_next) || !al16(grad_t) || grad_t == grad_next ||
+      grad_t == nx_t)
     return SENSE_EINVAL_PTR;
   if (!p->ws) return SENSE_EWORKSPACE;  // the lambda-gradient dot uses the plan's workspace
   uint8_t* w8 = static_cast<uint8_t*>(ws);
   const VnLayout L = vn_layout(p->B, p->H, p->W);
   const float2* x = static_cast<const float2*>(x_t);
   const float2* g = static_cast<const float2*>(grad_next);
-  float2* n1 = reinterpret_cast<float2*>(w8 + L.n1);
   float2* n2 = reinterpret_cast<float2*>(w8 + L.n2);
   double* pdot = reinterpret_cast<double*>(w8 + L.pdot);
   float* part = reinterpret_cast<float*>(w8 + L.part);
   const int rows = p->B * p->H;
   vn_pack(prm, w8, L, p->stream);
-  // grad lambda_t = -Re<g, A^H A x - A^H y>
-  if (int e = normal0(p, x, n1)) return e;
+  // grad lambda_t = -Re<g, A^H A x - A^H y>  (A^H A x from the forward when given)
+  const float2* n1 = static_cast<const float2*>(nx_t);
+  if (!n1) {
+    float2* t = reinterpret_cast<float2*>(w8 + L.n1);
+    if (int e = normal0(p, x, t)) return e;
+    n1 = t;
+  }
   if (int e = launch_dot_rows(p, g, n1, static_cast<const float2*>(AHy), pdot, 1, 0)) return e;
   prof_mark("vn_misc", p->stream, false);
   k_vn_addlam<<<1, 1, 0, p->stream>>>(pdot, grad_prm);
   prof_mark("vn_misc", p->stream, true);
   // z = K x, kg = K g, u = Phi'(z), v = Phi''(z) kg
-  if (int e = launch_K(p, 1, prm, x, g, w8, L)) return e;
+  if (int e = launch_K(p, 2, prm, x, g, w8, L)) return e;
   // filter gradient: -(sum u (x) g_shift + v (x) x_shift); reads g and x before grad_t is written
   prof_mark("vn_wgrad", p->stream, false);
-  k_vn_wgrad<<<rows, 128, wg_smem(p->W), p->stream>>>(
-      p->B, p->H, p->W, reinterpret_cast<const __nv_bfloat16*>(w8 + L.u),
-      reinterpret_cast<const __nv_bfloat16*>(w8 + L.v), g, x, part);
+  k_vn_wgrad<<<rows, 128, wg_smem(p->W), p->stream>>>(p->B, p->H, p->W, reinterpret_cast<const bf16*>(w8 + L.u),
+                                                        reinterpret_cast<const bf16*>(w8 + L.v), g, x, part);
   k_vn_reduce<<<(NK * 2 * NT + 31) / 32, 256, 0, p->stream>>>(part, rows, NK * 2 * NT, -1.f, grad_prm);
   prof_mark("vn_wgrad", p->stream, true);
   // RBF weight gradient: -sum kg phi_j(z)
   prof_mark("vn_rbfgrad", p->stream, false);
-  k_vn_rbfgrad<<<rows, 192, 0, p->stream>>>(p->B, p->H, p->W, reinterpret_cast<const float*>(w8 + L.z),
+  k_vn_rbfgrad<<<rows, 256, 0, p->stream>>>(p->B, p->H, p->W, reinterpret_cast<const float*>(w8 + L.z),
                                             reinterpret_cast<const float*>(w8 + L.kg), part);
   k_vn_reduce<<<(NK * NW + 31) / 32, 256, 0, p->stream>>>(part, rows, NK * NW, -1.f, grad_prm + OFF_RBF);
   prof_mark("vn_rbfgrad", p->stream, true);
   // grad_t = g - K^T v - lambda A^H A g
   if (int e = normal0(p, g, n2)) return e;
-  if (int e = launch_KT(p, reinterpret_cast<const __nv_bfloat16*>(w8 + L.v), prm, g, n2, nullptr,
+  if (int e = launch_KT(p, reinterpret_cast<const bf16*>(w8 + L.v), prm, g, n2, nullptr,
                         static_cast<float2*>(grad_t), w8, L))
     return e;
   prof_count(8);

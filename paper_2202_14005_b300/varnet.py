@@ -67,19 +67,21 @@ class VarNetTrainer:
         self.gp = torch.zeros_like(params)
         self.m, self.v = torch.zeros_like(params), torch.zeros_like(params)
         self.xs = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(self.T + 1)]
+        # A^H A x^t of every stage, written by the forward pass for the reverse pass
+        self.nx = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(self.T)]
         self.g = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(2)]
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
         self.lr = lr
         self.t = 0
 
-    def stage(self, t: int, x_t: torch.Tensor, x_next: torch.Tensor):
+    def stage(self, t: int, x_t: torch.Tensor, x_next: torch.Tensor, nx_out: torch.Tensor | None = None):
         _lib.check("varnet_stage", self._lib.varnet_stage(
-            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(x_next), _p(self.ws),
+            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(x_next), _p(nx_out), _p(self.ws),
             self.ws.numel()))
 
-    def stage_backward(self, t: int, x_t, grad_next, grad_t):
+    def stage_backward(self, t: int, x_t, grad_next, grad_t, nx_t: torch.Tensor | None = None):
         _lib.check("varnet_stage_backward", self._lib.varnet_stage_backward(
-            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(grad_next), _p(grad_t),
+            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(nx_t), _p(grad_next), _p(grad_t),
             _p(self.gp[t]), _p(self.ws), self.ws.numel()))
 
     def forward(self, y: torch.Tensor) -> torch.Tensor:
@@ -87,7 +89,7 @@ class VarNetTrainer:
         self.plan._sync_stream()
         self.plan.adjoint(y, out=self.xs[0])
         for t in range(self.T):
-            self.stage(t, self.xs[t], self.xs[t + 1])
+            self.stage(t, self.xs[t], self.xs[t + 1], self.nx[t])
         return self.xs[self.T]
 
     def gradients(self, y: torch.Tensor, gt: torch.Tensor):
@@ -97,7 +99,7 @@ class VarNetTrainer:
             self.plan._h, _p(self.xs[self.T]), _p(gt), _p(self.loss), _p(self.g[0])))
         cur = 0
         for t in range(self.T - 1, -1, -1):
-            self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1])
+            self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1], self.nx[t])
             cur ^= 1
         return self.loss
 
