@@ -225,6 +225,12 @@ int unrolled_step_backward(sense_plan plan, int kind, const float* weights, cons
 #define VARNET_KSIZE 11
 size_t varnet_workspace_bytes(int B, int H, int W);
 int varnet_param_count(void);
+/* Byte offsets in ws of the activations the last call left there (for tests and
+ * inspection): offsets[0] u = Phi'(K x_t) and offsets[1] v = Phi''(K x_t) K grad_next,
+ * bfloat16 [B][H][W][32] (channels 24..31 zero); offsets[2] z = K x_t and
+ * offsets[3] K grad_next, float32 [B][H][W][24] (v, z and K grad_next from
+ * varnet_stage_backward only). */
+int varnet_workspace_offsets(int B, int H, int W, size_t* offsets);
 int varnet_stage(sense_plan plan, const float* params, const void* AHy, const void* x_t, void* x_next,
                  void* nx_out, void* ws, size_t ws_bytes);
 int varnet_stage_backward(sense_plan plan, const float* params, const void* AHy, const void* x_t,

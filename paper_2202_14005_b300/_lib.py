@@ -54,6 +54,7 @@ SIGNATURES = {
                                     C.c_size_t]),
     "varnet_workspace_bytes": (C.c_size_t, [_i, _i, _i]),
     "varnet_param_count": (_i, []),
+    "varnet_workspace_offsets": (_i, [_i, _i, _i, C.POINTER(C.c_size_t)]),
     "varnet_stage": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
     "varnet_stage_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
     "sense_mse_loss": (_i, [_vp, _vp, _vp, _vp, _vp]),

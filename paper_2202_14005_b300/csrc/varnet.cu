@@ -11,12 +11,13 @@
 //
 // Arithmetic: filters in BF16 (rounded from the float32 parameters at use),
 // warp-level tensor cores (mma.sync m16n8k16, FP32 accumulation):
-//   K       the image operand is split into two BF16 terms (x = x_hi + x_lo,
-//           relative 2^-17), so K x is as accurate as FP32 accumulation: the
-//           zero-mean filters cancel on smooth images, and a single BF16
-//           rounding of x would reach 1e-2 relative in K x.  The im2col tile
-//           of each source row is built once and serves the K_R output rows
-//           it touches (A = pixels x [x_hi taps | x_lo taps], B = filters);
+//   K       the image operand is split into three BF16 terms (x = x1 + x2 + x3,
+//           the full 24-bit significand), so K x is as accurate as FP32
+//           accumulation: the zero-mean filters cancel on smooth images (one
+//           BF16 rounding of x costs ~1e-2 relative in K x, two terms ~1e-4,
+//           and the RBF tails amplify errors of z by up to (z - mu)/sigma^2).
+//           The im2col tile of each source row is built once and serves the
+//           output rows it touches (A = pixels x [x1 | x2 | x3 taps], B = filters);
 //   Phi'    FP32 over the 13 centres nearest z (the rest are below e^-21 of
 //           the largest term), fused into the K epilogue;
 //   K^T     from BF16 Phi'(z) (channels-last, 24 of 32 channels): per source
@@ -89,48 +90,71 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Index of the centre nearest z, clamped so that the +-6 window stays in int range
-// (NaN maps to 0; far-out z leave an empty window: every term is below e^-21).
-__device__ __forceinline__ int nearest_centre(float z) {
-  const float t = fminf(fmaxf((z - kMu0) * (1.f / kDelta), -64.f), 64.f);
-  return __float2int_rn(t);
+// Phi'(z) = sum_j r_j phi_j(z) and Phi''(z) = -sum_j r_j phi_j(z) (z - mu_j) / sigma^2 with
+// phi_j(z) = exp(-(z - mu_j)^2 / (2 sigma^2)), over the 13 centres j0 .. j0 + 12, j0 = jc - 6, around
+// the centre jc nearest z; every centre left out is more than 6.5 widths from z, below e^-21 of the
+// largest term.  Centres outside 0 .. 30 carry weight zero (the weight rows are padded by RBF_PAD
+// on both sides), so the window never shifts and its first term exp(-d_j0^2 / 2), d_j0 in
+// [5.5, 6.5], stays a normal float.  With sigma equal to the spacing and d_j = (z - mu_j) / sigma:
+// d_{j+1} = d_j - 1 and phi_{j+1} = phi_j exp(d_j - 1/2), so two exponentials start the window and
+// products continue it.  Then Phi' = S0 = sum_k t_k and Phi'' = (S1 - (d_j0 - 6) S0) / sigma with
+// t_k = r_{j0+k} phi_{j0+k} and S1 = sum_k (k - 6) t_k (|d_j0 - 6| <= 1/2: no cancellation between
+// the two parts).  jc is clamped to -6 .. 36 (z beyond: every term below e^-18 r).  The two filters
+// of a pair run side by side in packed FP32x2 arithmetic.
+constexpr int RBF_WIN = 13;
+constexpr int RBF_PAD = 12;                  // zero weights below centre 0 and above centre 30
+constexpr int RBF_LD = NW + 2 * RBF_PAD;     // 55: padded weight row
+__device__ __forceinline__ int window_start(float z, float& d) {
+  const float zc = fminf(fmaxf(z, kMu0 - 8.f * kDelta), -kMu0 + 8.f * kDelta);
+  const int jc = min(max(__float2int_rn((zc - kMu0) * (1.f / kDelta)), -6), NW - 1 + 6);
+  const int j0 = jc - 6;
+  d = (zc - (kMu0 + kDelta * (float)j0)) * (1.f / kDelta);
+  return j0;  // -12 .. 30
 }
 
-// Phi'(z) = sum_j r_j phi_j(z) and Phi''(z) = -sum_j r_j phi_j(z) (z - mu_j) / sigma^2 with
-// phi_j(z) = exp(-(z - mu_j)^2 / (2 sigma^2)), over the 13 centres nearest z.  With sigma equal
-// to the spacing and d_j = (z - mu_j) / sigma, d_{j+1} = d_j - 1 and
-// phi_{j+1} = phi_j exp(d_j - 1/2): two exponentials start the window, products continue it.
-struct Rbf {
-  float d1, d2;
+struct Rbf2 {
+  float2 d1, d2;
 };
-__device__ __forceinline__ Rbf rbf_eval(float z, const float* r) {
-  const int jc = nearest_centre(z);
-  const int j0 = max(jc - 6, 0), j1 = min(jc + 6, NW - 1);
-  Rbf o{0.f, 0.f};
-  float d = (z - (kMu0 + kDelta * (float)j0)) * (1.f / kDelta);
-  float phi = expf(-0.5f * d * d);
-  float rho = expf(d - 0.5f);
-  for (int j = j0; j <= j1; ++j) {
-    const float t = r[j] * phi;
-    o.d1 += t;
-    o.d2 = fmaf(t, -d * (1.f / kDelta), o.d2);
-    phi *= rho;
-    rho *= kEinv;
-    d -= 1.f;
+// Filters a and b (padded RBF weight rows ra, rb: centre j at ra[j + RBF_PAD]) at z.x and z.y.
+__device__ __forceinline__ Rbf2 rbf_eval2(float2 z, const float* ra, const float* rb) {
+  float2 d;
+  const int ja = window_start(z.x, d.x), jb = window_start(z.y, d.y);
+  ra += ja + RBF_PAD;
+  rb += jb + RBF_PAD;
+  float2 phi = make_float2(expf(-0.5f * d.x * d.x), expf(-0.5f * d.y * d.y));
+  float2 rho = make_float2(expf(d.x - 0.5f), expf(d.y - 0.5f));
+  const float2 q = make_float2(kEinv, kEinv);
+  float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < RBF_WIN; ++k) {
+    const float2 t = __fmul2_rn(make_float2(ra[k], rb[k]), phi);
+    s0 = __fadd2_rn(s0, t);
+    s1 = __ffma2_rn(make_float2((float)(k - 6), (float)(k - 6)), t, s1);
+    phi = __fmul2_rn(phi, rho);
+    rho = __fmul2_rn(rho, q);
   }
+  Rbf2 o;
+  o.d1 = s0;
+  o.d2 = make_float2((s1.x - (d.x - 6.f) * s0.x) * (1.f / kDelta), (s1.y - (d.y - 6.f) * s0.y) * (1.f / kDelta));
+  if (z.x != z.x) o.d1.x = o.d2.x = z.x;  // NaN propagates
+  if (z.y != z.y) o.d1.y = o.d2.y = z.y;
   return o;
 }
 
 // ------------------------------------------------------------------ packing
-constexpr int K_R = 4;          // output rows per K CTA
-constexpr int K_KP = 48;        // im2col columns: [x_hi: c0 dx 0..10, c1 dx 0..10, 0, 0 | x_lo: same]
-constexpr int K_LD = 56;        // row pitch (bf16) of the im2col tile and the K table
+constexpr int K_RMAX = 8;       // output rows per K CTA: 8 (one source), 4 (two sources)
+constexpr int K_PARTS = 3;      // BF16 terms of the image operand: x = x1 + x2 + x3 (24 bits)
+constexpr int K_KP = 24 * K_PARTS;  // im2col columns: per part c0 dx 0..10, c1 dx 0..10, 0, 0
+constexpr int K_KSTEPS = (K_KP + 15) / 16;  // 5 MMA k-steps (columns 72..79 zero)
+constexpr int K_LD = 88;        // row pitch (bf16) of the im2col tile and the K table (conflict-free)
 constexpr int K_W_ELEMS = KS * NK * K_LD;
-constexpr int KT_W_ELEMS = NT * 2 * CU;
+constexpr int KT_LDW = 40;      // row pitch (bf16) of the K^T table: conflict-free across filter rows
+constexpr int KT_W_ELEMS = NT * 2 * KT_LDW;
 
 // wk[dy][n][k]: K operand per filter row, the BF16 filter tap w[n][c][dy][dx] at k = part * 24 +
-//   c * 11 + dx for both parts; zero elsewhere.
-// wn[dy][dx][c][i]: K^T operand, the same taps with the filter index i contiguous (zero for i >= 24).
+//   c * 11 + dx for every part; zero elsewhere.
+// wn[dy][dx][c][i]: K^T operand, the same taps with the filter index i contiguous (zero for i >= 24;
+//   pitch KT_LDW).
 __global__ void k_vn_pack(const float* prm, bf16* wk, bf16* wn) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < K_W_ELEMS) {
@@ -144,7 +168,7 @@ __global__ void k_vn_pack(const float* prm, bf16* wk, bf16* wn) {
   }
   const int j = i - K_W_ELEMS;
   if (j >= 0 && j < KT_W_ELEMS) {
-    const int t = j / (2 * CU), c = (j / CU) % 2, k = j % CU;
+    const int t = j / (2 * KT_LDW), c = (j / KT_LDW) % 2, k = j % KT_LDW;
     wn[j] = __float2bfloat16_rn(k < NK ? prm[(k * 2 + c) * NT + t] : 0.f);
   }
 }
@@ -153,9 +177,11 @@ __global__ void k_vn_pack(const float* prm, bf16* wk, bf16* wn) {
 // NSRC = 1 (forward stage):  u = Phi'(K x)                          -> u [px][32] bf16
 // NSRC = 2 (reverse stage):  z = K x, kg = K g;  u = Phi'(z), v = Phi''(z) kg
 //                            -> u, v [px][32] bf16, z, kg [px][24] fp32
-// CTA: 128 pixels x K_R rows, 8 warps x 16 pixels.  Source rows stream through a double-
-// buffered FP32 stage (cp.async) and a double-buffered im2col tile; each source row s feeds
-// every output row h of the CTA with 0 <= s - h + 5 <= 10 (filter row dy = s - h + 5).
+// CTA: 128 pixels x R rows (R = 8 / NSRC), 8 warps x 16 pixels.  Source rows stream through a double-
+// buffered FP32 stage (cp.async) into one im2col tile per source; each source row s feeds every
+// output row h of the CTA with 0 <= s - h + 5 <= 10 (filter row dy = s - h + 5).  The image
+// operand enters as three BF16 terms x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2), so
+// K x carries the 24-bit significand of x into the FP32 accumulation.
 struct KArgs {
   int B, H, W;
   const float2* x;
@@ -170,6 +196,7 @@ struct KArgs {
 
 constexpr int K_THREADS = 256;
 constexpr int K_STG = 140;  // staged source row (float2): columns w0 - 6 .. w0 + 133
+constexpr int K_PR_LD = 144;  // BF16 part row: the K_STG columns of one part and channel
 
 template <int NSRC>
 struct KSmem {
@@ -177,14 +204,17 @@ struct KSmem {
   static constexpr int COL_BYTES = TILE * K_LD * 2;  // one im2col tile
   static constexpr int STG_BYTES = K_STG * 8;
   static constexpr int OFF_COL = W_BYTES;
-  static constexpr int OFF_STG = OFF_COL + 2 * NSRC * COL_BYTES;
-  static constexpr int OFF_R = OFF_STG + 2 * NSRC * STG_BYTES;
-  static constexpr int TOTAL = OFF_R + NK * NW * 4;
+  static constexpr int OFF_STG = OFF_COL + NSRC * COL_BYTES;
+  static constexpr int PR_BYTES = K_PARTS * 2 * K_PR_LD * 2;  // BF16 part rows of one source row
+  static constexpr int OFF_PR = OFF_STG + 2 * NSRC * STG_BYTES;
+  static constexpr int OFF_R = OFF_PR + NSRC * PR_BYTES;
+  static constexpr int TOTAL = OFF_R + NK * RBF_LD * 4;
 };
 
 template <int NSRC>
-__global__ void __launch_bounds__(K_THREADS, NSRC == 1 ? 3 : 2) k_vn_K(const KArgs a) {
+__global__ void __launch_bounds__(K_THREADS, 2) k_vn_K(const KArgs a) {
   using S = KSmem<NSRC>;
+  constexpr int K_R = K_RMAX / NSRC;
   extern __shared__ __align__(16) uint8_t dsm[];
   const bf16* wk = reinterpret_cast<const bf16*>(dsm);
   float* s_r = reinterpret_cast<float*>(dsm + S::OFF_R);
@@ -194,7 +224,10 @@ __global__ void __launch_bounds__(K_THREADS, NSRC == 1 ? 3 : 2) k_vn_K(const KAr
 
   for (int i = tid; i < S::W_BYTES / 16; i += K_THREADS)
     cp16(dsm + i * 16, reinterpret_cast<const uint8_t*>(a.wk) + i * 16, true);
-  for (int i = tid; i < NK * NW; i += K_THREADS) s_r[i] = a.rbf[i];
+  for (int i = tid; i < NK * RBF_LD; i += K_THREADS) {
+    const int j = i % RBF_LD - RBF_PAD;
+    s_r[i] = (unsigned)j < (unsigned)NW ? a.rbf[(i / RBF_LD) * NW + j] : 0.f;
+  }
   const int s_lo = max(h0 - KH, 0), s_hi = min(h0 + K_R - 1 + KH, a.H - 1);
   const int nrows = s_hi - s_lo + 1;
   auto stage = [&](int k) {
@@ -210,6 +243,9 @@ __global__ void __launch_bounds__(K_THREADS, NSRC == 1 ? 3 : 2) k_vn_K(const KAr
   };
   stage(0);
   cp_commit();
+  // im2col columns K_KP .. K_LD - 1 are read by the last k-step (against zero taps) but never built
+  for (int i = tid; i < NSRC * TILE; i += K_THREADS)
+    reinterpret_cast<uint4*>(dsm + S::OFF_COL + (size_t)i * K_LD * 2 + K_KP * 2)[0] = make_uint4(0u, 0u, 0u, 0u);
 
   float acc[NSRC][K_R][3][4];
 #pragma unroll
@@ -227,36 +263,58 @@ __global__ void __launch_bounds__(K_THREADS, NSRC == 1 ? 3 : 2) k_vn_K(const KAr
     cp_commit();
     cp_wait<1>();  // everything but the newest group: source row k and the tables have landed
     __syncthreads();
-    // im2col of source row k: item (src, pixel m, part); halo column of tap dx = stage index m + dx + 1
-    for (int it = tid; it < NSRC * TILE * 2; it += K_THREADS) {
-      const int part = it & 1, m = (it >> 1) % TILE, src = it / (2 * TILE);
-      const float2* stg =
-          reinterpret_cast<const float2*>(dsm + S::OFF_STG + ((k & 1) * NSRC + src) * S::STG_BYTES);
-      bf16 t[24];
+    // BF16 terms of source row k, once per column: part rows pr[src][part][c][column]
+    for (int it = tid; it < NSRC * K_STG; it += K_THREADS) {
+      const int src = it / K_STG, j = it % K_STG;
+      float2 v = reinterpret_cast<const float2*>(dsm + S::OFF_STG + ((k & 1) * NSRC + src) * S::STG_BYTES)[j];
+      bf16* pr = reinterpret_cast<bf16*>(dsm + S::OFF_PR + src * S::PR_BYTES);
 #pragma unroll
-      for (int dx = 0; dx < KS; ++dx) {
-        const float2 v = stg[m + dx + 1];
-        bf16 re = __float2bfloat16_rn(v.x), im = __float2bfloat16_rn(v.y);
-        if (part) {
-          re = __float2bfloat16_rn(v.x - __bfloat162float(re));
-          im = __float2bfloat16_rn(v.y - __bfloat162float(im));
-        }
-        t[dx] = re;
-        t[KS + dx] = im;
+      for (int part = 0; part < K_PARTS; ++part) {  // x1 = bf16(x), x2 = bf16(x - x1), ... (exact residuals)
+        const bf16 re = __float2bfloat16_rn(v.x), im = __float2bfloat16_rn(v.y);
+        pr[(part * 2) * K_PR_LD + j] = re;
+        pr[(part * 2 + 1) * K_PR_LD + j] = im;
+        v.x -= __bfloat162float(re);
+        v.y -= __bfloat162float(im);
       }
-      t[22] = t[23] = __float2bfloat16_rn(0.f);
-      uint4* dst = reinterpret_cast<uint4*>(dsm + S::OFF_COL + ((k & 1) * NSRC + src) * S::COL_BYTES +
-                                            m * K_LD * 2 + part * 48);
+    }
+    __syncthreads();
+    // im2col of source row k: item (src, part, pixel m) = taps dx 0..10 of both channels, part-row
+    // columns m + 1 .. m + 11 (stage column of tap dx: m + dx + 1).  Consecutive lanes take
+    // consecutive pixels of one part (row pitch 176 B: eight lanes store to eight bank groups).
+    for (int it = tid; it < NSRC * K_PARTS * TILE; it += K_THREADS) {
+      const int src = it / (K_PARTS * TILE), part = (it / TILE) % K_PARTS, m = it % TILE;
+      const uint32_t* r0 =
+          reinterpret_cast<const uint32_t*>(dsm + S::OFF_PR + src * S::PR_BYTES + (part * 2) * K_PR_LD * 2);
+      const uint32_t* r1 = r0 + K_PR_LD / 2;
+      const int e0 = m + 1, w0i = e0 >> 1;
+      const bool odd = e0 & 1;
+      uint32_t A[6], Bw[6];
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
-        dst[q] = make_uint4(pack2(t[8 * q], t[8 * q + 1]), pack2(t[8 * q + 2], t[8 * q + 3]),
-                            pack2(t[8 * q + 4], t[8 * q + 5]), pack2(t[8 * q + 6], t[8 * q + 7]));
+      for (int q = 0; q < 6; ++q) {
+        A[q] = r0[w0i + q];
+        Bw[q] = r1[w0i + q];
+      }
+      // align: pair q holds columns e0 + 2q, e0 + 2q + 1 (low half first); element 10 in the low half of [5]
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        A[q] = odd ? __byte_perm(A[q], A[q + 1], 0x5432) : A[q];
+        Bw[q] = odd ? __byte_perm(Bw[q], Bw[q + 1], 0x5432) : Bw[q];
+      }
+      A[5] = odd ? (A[5] >> 16) : (A[5] & 0xffffu);
+      Bw[5] = odd ? (Bw[5] >> 16) : (Bw[5] & 0xffffu);
+      // row: [c0 taps 0..10 | c1 taps 0..10 | 0 0]
+      uint4* dst = reinterpret_cast<uint4*>(dsm + S::OFF_COL + src * S::COL_BYTES + m * K_LD * 2 + part * 48);
+      dst[0] = make_uint4(A[0], A[1], A[2], A[3]);
+      dst[1] = make_uint4(A[4], A[5] | (Bw[0] << 16), __byte_perm(Bw[0], Bw[1], 0x5432),
+                          __byte_perm(Bw[1], Bw[2], 0x5432));
+      dst[2] = make_uint4(__byte_perm(Bw[2], Bw[3], 0x5432), __byte_perm(Bw[3], Bw[4], 0x5432),
+                          __byte_perm(Bw[4], Bw[5], 0x5432), 0u);
     }
     __syncthreads();
     const int s = s_lo + k;
-    const bf16* colb = reinterpret_cast<const bf16*>(dsm + S::OFF_COL + (k & 1) * NSRC * S::COL_BYTES);
-#pragma unroll
-    for (int ks = 0; ks < 3; ++ks) {
+    const bf16* colb = reinterpret_cast<const bf16*>(dsm + S::OFF_COL);
+#pragma unroll 1
+    for (int ks = 0; ks < K_KSTEPS; ++ks) {
       uint32_t af[NSRC][4];
 #pragma unroll
       for (int src = 0; src < NSRC; ++src)
@@ -291,23 +349,16 @@ __global__ void __launch_bounds__(K_THREADS, NSRC == 1 ? 3 : 2) k_vn_K(const KAr
 #pragma unroll
       for (int nt = 0; nt < 3; ++nt) {
         const int i0 = nt * 8 + 2 * tig;
-        float uo[2], vo[2], zo[2], ko[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const float z = acc[0][r][nt][half * 2 + e];
-          const Rbf f = rbf_eval(z, s_r + (i0 + e) * NW);
-          uo[e] = f.d1;
-          zo[e] = z;
-          ko[e] = NSRC == 2 ? acc[NSRC - 1][r][nt][half * 2 + e] : 0.f;
-          vo[e] = f.d2 * ko[e];
-        }
+        const float2 z = make_float2(acc[0][r][nt][half * 2], acc[0][r][nt][half * 2 + 1]);
+        const Rbf2 f = rbf_eval2(z, s_r + i0 * RBF_LD, s_r + (i0 + 1) * RBF_LD);
         *reinterpret_cast<uint32_t*>(a.u + p * CU + i0) =
-            pack2(__float2bfloat16_rn(uo[0]), __float2bfloat16_rn(uo[1]));
+            pack2(__float2bfloat16_rn(f.d1.x), __float2bfloat16_rn(f.d1.y));
         if (NSRC == 2) {
+          const float2 kg = make_float2(acc[NSRC - 1][r][nt][half * 2], acc[NSRC - 1][r][nt][half * 2 + 1]);
           *reinterpret_cast<uint32_t*>(a.v + p * CU + i0) =
-              pack2(__float2bfloat16_rn(vo[0]), __float2bfloat16_rn(vo[1]));
-          *reinterpret_cast<float2*>(a.z + p * NK + i0) = make_float2(zo[0], zo[1]);
-          *reinterpret_cast<float2*>(a.kg + p * NK + i0) = make_float2(ko[0], ko[1]);
+              pack2(__float2bfloat16_rn(f.d2.x * kg.x), __float2bfloat16_rn(f.d2.y * kg.y));
+          *reinterpret_cast<float2*>(a.z + p * NK + i0) = z;
+          *reinterpret_cast<float2*>(a.kg + p * NK + i0) = kg;
         }
       }
       // channels 24..31 of the stored activations are zero
@@ -326,7 +377,7 @@ __global__ void __launch_bounds__(K_THREADS, NSRC == 1 ? 3 : 2) k_vn_K(const KAr
 struct KTArgs {
   int B, H, W;
   const bf16* src;  // [px][32]
-  const bf16* wn;   // [11][11][2][32]
+  const bf16* wn;   // [11][11][2][KT_LDW]
   const float2* base;
   const float2* n;
   const float2* c;
@@ -393,7 +444,7 @@ __global__ void __launch_bounds__(128, 4) k_vn_KT(const KTArgs a) {
           const int r = nt * 4 + (gid >> 1), c = gid & 1, dy = h0 + r + KH - s;
           bq[nt][0] = bq[nt][1] = 0u;
           if ((unsigned)dy < (unsigned)KS) {
-            const bf16* wp = wn + ((dy * KS + dx) * 2 + c) * CU + ks * 16 + 2 * tig;
+            const bf16* wp = wn + ((dy * KS + dx) * 2 + c) * KT_LDW + ks * 16 + 2 * tig;
             bq[nt][0] = *reinterpret_cast<const uint32_t*>(wp);
             bq[nt][1] = *reinterpret_cast<const uint32_t*>(wp + 8);
           }
@@ -532,8 +583,8 @@ __global__ void __launch_bounds__(128) k_vn_wgrad(int B, int H, int W, const __n
 
 // RBF weight gradient partial per image row: P[i][j] = sum_w kg[w][i] phi_j(z[w][i]).
 // Thread (i, q), i < 24, q < 10, takes pixels w = q, q + 10, ... and adds into its own
-// shared-memory row of 31 accumulators (Gaussian window by the product recurrence of
-// rbf_eval); the ten rows of each filter are then added in order.
+// shared-memory row of 31 accumulators (13-centre window by the product recurrence of
+// rbf_eval2); the ten rows of each filter are then added in order.
 constexpr int RG_Q = 10;
 constexpr int RG_LD = NW + 2;  // 33: distinct banks for the 32 lanes at equal j
 __global__ void __launch_bounds__(256) k_vn_rbfgrad(int B, int H, int W, const float* z, const float* kg,
@@ -549,13 +600,13 @@ __global__ void __launch_bounds__(256) k_vn_rbfgrad(int B, int H, int W, const f
     for (int w = q; w < W; w += RG_Q) {
       const size_t p = ((size_t)b * H + h) * W + w;
       const float zz = z[p * NK + i], g = kg[p * NK + i];
-      const int jc = nearest_centre(zz);
-      const int j0 = max(jc - 6, 0), j1 = min(jc + 6, NW - 1);
-      float d = (zz - (kMu0 + kDelta * (float)j0)) * (1.f / kDelta);
-      float phi = g * expf(-0.5f * d * d);
+      float d;
+      const int j0 = window_start(zz, d);
+      float phi = zz == zz ? g * expf(-0.5f * d * d) : zz;  // NaN propagates
       float rho = expf(d - 0.5f);
-      for (int j = j0; j <= j1; ++j) {
-        my[j] += phi;
+#pragma unroll
+      for (int k = 0; k < RBF_WIN; ++k) {
+        if ((unsigned)(j0 + k) < (unsigned)NW) my[j0 + k] += phi;
         phi *= rho;
         rho *= kEinv;
       }
@@ -635,7 +686,7 @@ int vn_check(sense_plan p, const float* prm, const void* AHy, const void* xt, co
              size_t ws_bytes) {
   if (!p || !prm || !AHy || !xt || !ws || !al16(AHy) || !al16(xt) || (nx && !al16(nx)) || ((uintptr_t)ws & 255u))
     return SENSE_EINVAL_PTR;
-  if (p->W > WG_MAXW || p->B > 65535 || (p->H + K_R - 1) / K_R > 65535) return SENSE_EUNSUPPORTED;
+  if (p->W > WG_MAXW || p->B > 65535 || (p->H + 3) / 4 > 65535) return SENSE_EUNSUPPORTED;
   if (ws_bytes < vn_layout(p->B, p->H, p->W).total) return SENSE_EWORKSPACE;
   return vn_prepare();
 }
@@ -659,7 +710,8 @@ int launch_K(sense_plan p, int nsrc, const float* prm, const float2* x, const fl
   a.v = reinterpret_cast<bf16*>(ws + L.v);
   a.z = reinterpret_cast<float*>(ws + L.z);
   a.kg = reinterpret_cast<float*>(ws + L.kg);
-  const dim3 grid((p->W + TILE - 1) / TILE, (p->H + K_R - 1) / K_R, p->B);
+  const int R = K_RMAX / nsrc;
+  const dim3 grid((p->W + TILE - 1) / TILE, (p->H + R - 1) / R, p->B);
   const char* grp = nsrc == 2 ? "vn_Kbwd" : "vn_K";
   prof_mark(grp, p->stream, false);
   if (nsrc == 2)
@@ -700,6 +752,17 @@ size_t varnet_workspace_bytes(int B, int H, int W) {
 }
 
 int varnet_param_count(void) { return NPAR; }
+
+int varnet_workspace_offsets(int B, int H, int W, size_t* offsets) {
+  if (B <= 0 || H <= 0 || W <= 0) return SENSE_EINVAL_SHAPE;
+  if (!offsets) return SENSE_EINVAL_PTR;
+  const VnLayout L = vn_layout(B, H, W);
+  offsets[0] = L.u;
+  offsets[1] = L.v;
+  offsets[2] = L.z;
+  offsets[3] = L.kg;
+  return SENSE_OK;
+}
 
 int varnet_stage(sense_plan p, const float* prm, const void* AHy, const void* x_t, void* x_next, void* nx_out,
                  void* ws, size_t ws_bytes) {

@@ -84,6 +84,18 @@ class VarNetTrainer:
             self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(nx_t), _p(grad_next), _p(grad_t),
             _p(self.gp[t]), _p(self.ws), self.ws.numel()))
 
+    def activations(self):
+        """Views of the workspace activations of the last stage call:
+        u, v (bfloat16 [B, H, W, 32]) and z = K x, K g (float32 [B, H, W, 24])."""
+        off = (C.c_size_t * 4)()
+        _lib.check("varnet_workspace_offsets", self._lib.varnet_workspace_offsets(self.B, self.H, self.W, off))
+        n = self.B * self.H * self.W
+        u = self.ws[off[0]:off[0] + n * 64].view(torch.bfloat16).view(self.B, self.H, self.W, 32)
+        v = self.ws[off[1]:off[1] + n * 64].view(torch.bfloat16).view(self.B, self.H, self.W, 32)
+        z = self.ws[off[2]:off[2] + n * 96].view(torch.float32).view(self.B, self.H, self.W, NK)
+        kg = self.ws[off[3]:off[3] + n * 96].view(torch.float32).view(self.B, self.H, self.W, NK)
+        return u, v, z, kg
+
     def forward(self, y: torch.Tensor) -> torch.Tensor:
         """x^T for k-space y [B, C, H, W] (also keeps every x^t)."""
         self.plan._sync_stream()

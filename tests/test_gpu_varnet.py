@@ -7,24 +7,21 @@ BF16 split of the image (hi + lo) and are as accurate as FP32 accumulation;
 Phi'(K x), Phi''(K x) K g, and x and g as operands of the filter gradient
 are stored in BF16; the RBF sums run in FP32 over the 13 centres nearest z.
 * Mirrored oracle (those stored operands rounded with bf16_round, FP64
-  otherwise): what remains is FP32 accumulation of 242 (K) and 2,904 (K^T)
-  products per output.  The filters are zero-mean, so the sum of |products|
-  exceeds the result by 10-30x and the typical relative error is about
-  sqrt(2904) * 2^-24 * 20 ~ 7e-5, plus one-ulp BF16 rounding flips of
-  Phi'(z) where the FP32 and FP64 values of z straddle a boundary.  Bounds:
-  1e-3 relative L2 on the regulariser term, a whole stage output (x_t, the
-  regulariser and the data term are of comparable size on smooth images),
-  the stage gradient and every parameter gradient; 1e-4 on the lambda
-  gradient, an FP64 dot with the FP32 residual A^H A x - A^H y, which cancels
-  to a few percent of A^H A x.
-* Exact oracle (no rounding): the BF16 storage of Phi' and Phi'' K g (relative
-  2^-9 per element) gives a few 1e-3 (measured on the oracle: 6e-3 on the
-  regulariser, 3e-3 on the filter gradient at 320 x 368); bound 2e-2.
-* A chain of stages (initial, monotone RBF weights): the stage outputs differ
-  at the 1e-4 level and each stage passes the difference on through its
-  Jacobian; bounds 1e-3 on the stage outputs and the loss, 1e-2 on the
-  gradients.  (With sign-changing Phi'' the random untrained stages amplify
-  differences by ~2x per stage.)
+  otherwise).  What remains is FP32 arithmetic: K x accumulates 726 products
+  of zero-mean filters whose |products| exceed |z| 10-30x (z to ~1e-6, checked
+  per layer below); Gaussian terms change by (|z - mu| / sigma^2) dz, so BF16
+  storage of Phi'(z) occasionally rounds the other way; K^T and the filter
+  gradient sum 2,904 such products again.  Observed (B300): 6e-5 to 5e-4
+  relative L2 on the regulariser, stage gradient and parameter gradients.
+  Bounds: 2e-3 on those and on whole stage outputs; 1e-4 on the lambda
+  gradient, an FP64 dot with the FP32 residual A^H A x - A^H y.
+* Exact oracle (no rounding): the BF16 storage of Phi' and Phi'' K g adds
+  relative 2^-9 per element: observed 1e-3 to 3e-3; bound 2e-2.
+* A chain of three stages (initial, monotone RBF weights), forward, MSE loss
+  and the reverse pass through all stages: every stage passes the differences
+  above on through its Jacobian, and the stage-0 gradients sit at the end of
+  three reverse stages.  Observed 2e-5 to 1e-3; bounds 1e-2 on the stage
+  outputs, the loss and the gradients.
 """
 import ctypes as C
 
@@ -102,10 +99,11 @@ def test_stage_forward(shape):
     reg_gpu = x.astype(np.complex128) - out - lam[0] * dc
     reg_m, _ = onn.varnet_regulariser(x, f[0], r[0], bf16_round)
     reg_e, _ = onn.varnet_regulariser(x, f[0], r[0])
-    assert rel(reg_gpu, reg_m) <= 1e-3, rel(reg_gpu, reg_m)
+    print(f"varnet regulariser: mirrored {rel(reg_gpu, reg_m):.2e} exact {rel(reg_gpu, reg_e):.2e}")
+    assert rel(reg_gpu, reg_m) <= 2e-3, rel(reg_gpu, reg_m)
     assert rel(reg_gpu, reg_e) <= 2e-2, rel(reg_gpu, reg_e)
     ref = ounr.varnet_stage(x, AHy, maps, mask, f[0], r[0], lam[0], bf16_round)
-    assert rel(out, ref) <= 1e-3, rel(out, ref)
+    assert rel(out, ref) <= 2e-3, rel(out, ref)
     assert tr.plan.status() == 0
 
 
@@ -123,6 +121,7 @@ def _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, tol_m, tol_e):
     ex = ounr.varnet_stage_backward(g, x, AHy, maps, mask, f[0], r[0], lam[0])
     got = (gt_.cpu().numpy(), gf[0], gr[0])
     for name, a, m, e in zip(("grad_x", "grad_filters", "grad_rbf"), got, mir[:3], ex[:3]):
+        print(f"varnet {name}: mirrored {rel(a, m):.2e} exact {rel(a, e):.2e}")
         assert rel(a, m) <= tol_m, f"{name} vs mirrored oracle: {rel(a, m):.3e}"
         assert rel(a, e) <= tol_e, f"{name} vs exact oracle: {rel(a, e):.3e}"
     assert abs(gl[0] - mir[3]) <= 1e-4 * abs(mir[3]), (gl[0], mir[3])
@@ -134,6 +133,35 @@ def _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, tol_m, tol_e):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
+def test_layer_outputs_from_workspace(shape):
+    """Each layer of the reverse-mode recomputation against the oracle, fed the
+    GPU's own inputs: z = K x and K g (FP32 accumulation of the three-term
+    image split; observed 1e-6, bound 1e-4), u = Phi'(z) and v = Phi''(z) K g
+    from the GPU's z and K g (FP32 sums of 13 Gaussians, then one BF16
+    rounding: observed 1.7e-3, bound 4e-3 = 2^-8)."""
+    B, Cc, H, W = shape
+    maps, mask, y, gt, AHy = problem(B, Cc, H, W, seed=H + W + 1)
+    vec, f, r, lam = params(1, seed=W + 1)
+    x = (AHy + 0.05 * synth.randn_complex(AHy.shape, 5)).astype(np.complex64)
+    g = (0.1 * synth.randn_complex(AHy.shape, 6)).astype(np.complex64)
+    tr = trainer(maps, mask, vec, AHy)
+    _backward(tr, x, g)
+    u, v, z, kg = [t.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2) for t in tr.activations()]
+    wr = onn.varnet_filters_real(f[0])
+    rz = onn.conv2d(onn.c2r(x), wr)
+    rkg = onn.conv2d(onn.c2r(g), wr)
+    print(f"varnet layers: z {rel(z, rz):.2e} Kg {rel(kg, rkg):.2e}")
+    assert rel(z, rz) <= 1e-4
+    assert rel(kg, rkg) <= 1e-4
+    ru = onn.rbf(z, r[0])
+    rv = onn.rbf_grad_z(z, r[0]) * kg
+    print(f"varnet layers: u {rel(u[:, :24], ru):.2e} v {rel(v[:, :24], rv):.2e}")
+    assert rel(u[:, :24], ru) <= 4e-3
+    assert rel(v[:, :24], rv) <= 4e-3
+    assert not u[:, 24:].any() and not v[:, 24:].any()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 def test_stage_backward(shape):
     B, Cc, H, W = shape
     maps, mask, y, gt, AHy = problem(B, Cc, H, W, seed=H + W + 1)
@@ -142,7 +170,7 @@ def test_stage_backward(shape):
     g = (0.1 * synth.randn_complex(AHy.shape, 6)).astype(np.complex64)
     tr = trainer(maps, mask, vec, AHy)
     gt_ = _backward(tr, x, g)
-    _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, 1e-3, 2e-2)
+    _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, 2e-3, 2e-2)
     assert tr.plan.status() == 0
 
 
@@ -160,14 +188,15 @@ def test_stage_full_size_slice():
     gt_ = _backward(tr, x, g)
     out = out.cpu().numpy()
     ref = ounr.varnet_stage(x, AHy, maps, mask, f[0], r[0], lam[0], bf16_round)
-    assert rel(out, ref) <= 1e-3, rel(out, ref)
+    assert rel(out, ref) <= 2e-3, rel(out, ref)
     dc = osense.normal(x, maps, mask, 0.0) - AHy
     reg_gpu = x.astype(np.complex128) - out - lam[0] * dc
     reg_m, _ = onn.varnet_regulariser(x, f[0], r[0], bf16_round)
     reg_e, _ = onn.varnet_regulariser(x, f[0], r[0])
-    assert rel(reg_gpu, reg_m) <= 1e-3, rel(reg_gpu, reg_m)
+    print(f"varnet regulariser: mirrored {rel(reg_gpu, reg_m):.2e} exact {rel(reg_gpu, reg_e):.2e}")
+    assert rel(reg_gpu, reg_m) <= 2e-3, rel(reg_gpu, reg_m)
     assert rel(reg_gpu, reg_e) <= 2e-2, rel(reg_gpu, reg_e)
-    _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, 1e-3, 2e-2)
+    _check_backward(tr, gt_, x, g, AHy, maps, mask, f, r, lam, 2e-3, 2e-2)
     assert tr.plan.status() == 0
 
 
@@ -209,9 +238,12 @@ def test_chain_training_gradients():
                                                         bf16_round)
     _, rxs = ounr.varnet_forward(AHy.astype(np.complex128), maps, mask, f, r, lam, bf16_round)
     for t in range(T + 1):
-        assert rel(tr.xs[t].cpu().numpy(), rxs[t]) <= 1e-3, f"x^{t}"
-    assert abs(loss.item() - rloss) <= 1e-3 * rloss
+        assert rel(tr.xs[t].cpu().numpy(), rxs[t]) <= 1e-2, f"x^{t}"
+    assert abs(loss.item() - rloss) <= 1e-2 * rloss
     gf, gr, gl = unpack_params(tr.gp.cpu().numpy())
+    for t in range(T):
+        print(f"varnet chain stage {t}: x {rel(tr.xs[t + 1].cpu().numpy(), rxs[t + 1]):.2e} filters "
+              f"{rel(gf[t], rgf[t]):.2e} rbf {rel(gr[t], rgw[t]):.2e} lambda {abs(gl[t] / rgl[t] - 1):.2e}")
     for t in range(T):
         assert rel(gf[t], rgf[t]) <= 1e-2, f"grad filters stage {t}"
         assert rel(gr[t], rgw[t]) <= 1e-2, f"grad rbf stage {t}"
