@@ -136,6 +136,10 @@ int sense_get_status(sense_plan plan, int* device_status);
  * D_W(x) = x + CNN(x) (Sec. 2.3.2, Eq. 6) with 3x3 convolutions
  * 2 -> 64 -> 64 -> 64 -> 64 -> 2 (biases, ReLU between layers, no batch norm);
  * the complex image enters as two real channels (re, im).
+ * SENSE_DENOISER_VARNET: the VarNet regulariser term of Eq. 5 (Sec. 2.3.1),
+ * R(x) = sum_i K_i^T Phi_i'(K_i x), with the filters and RBF weights of one
+ * stage in the layout of varnet_stage below (6,553 values; lambda_t unused);
+ * its workspace is varnet's (no status word; backward always recomputes K x).
  *
  * weights: device float32, denoiser_param_count() values, layer by layer
  *   w_l [Cout][Cin][3][3] then b_l [Cout], l = 1..5 (113,154 for MoDL).
@@ -153,13 +157,14 @@ int sense_get_status(sense_plan plan, int* device_status);
  *   checkpointing container, Sec. 2.2.4).  Calls sharing a ws must not overlap.
  */
 #define SENSE_DENOISER_MODL 0
+#define SENSE_DENOISER_VARNET 1
 size_t denoiser_workspace_bytes(int kind, int B, int H, int W);
 int denoiser_param_count(int kind);
-/* Byte offsets inside ws of the four BF16 [B][H][W][64] layer activations and
- * the two BF16 gradient buffers (for inspection and per-layer checks). */
+/* MoDL: byte offsets inside ws of the four BF16 [B][H][W][64] layer activations
+ * and the two BF16 gradient buffers (for inspection and per-layer checks). */
 int denoiser_workspace_offsets(int kind, int B, int H, int W, size_t* act_offsets,
                                size_t* grad_offsets);
-/* out = D_W(x); x, out complex64 [B][H][W] (must not alias). */
+/* out = D_W(x) (MoDL) or R(x) (VarNet); x, out complex64 [B][H][W] (must not alias). */
 int denoiser_forward(int kind, const float* weights, const void* x, void* out, void* ws,
                      size_t ws_bytes, int B, int H, int W, void* stream);
 /* Reverse mode: grad_x = (dD/dx)^H grad_out (complex convention of Sec. 2.2.2)
@@ -168,19 +173,23 @@ int denoiser_forward(int kind, const float* weights, const void* x, void* out, v
 int denoiser_backward(int kind, const float* weights, const void* x, const void* grad_out,
                       void* grad_x, float* grad_weights, void* ws, size_t ws_bytes, int B, int H,
                       int W, int recompute, void* stream);
-/* Reads (synchronising the stream) and clears the status word in ws. */
+/* MoDL workspaces: reads (synchronising the stream) and clears the status word in ws. */
 int denoiser_get_status(void* ws, int B, int H, int W, void* stream, int* device_status);
 
 /* ------------------------------------------------------------------------
- * Unrolled MoDL block (Eq. 6, Sec. 2.3.2) on a plan (maps, mask, workspace)
- * and a denoiser workspace, on the plan's stream.  lambda: device float64 [1].
+ * Unrolled block on a plan (maps, mask, workspace) and a denoiser workspace,
+ * on the plan's stream.  x_t, x_next, AHy, grad_next, grad_t: complex64 [B][H][W].
+ * kind SENSE_DENOISER_MODL (Eq. 6, Sec. 2.3.2); lambda: device float64 [1]:
  *   unrolled_step:  z = D_W(x_t);  x_next = S_lambda^{-1}(AHy + lambda z) by
  *                   cg_iters CG iterations from zero.
  *   unrolled_step_backward: given grad_next = dL/dx_next, recomputes z from x_t
  *                   (checkpointing, Sec. 2.2.4), solves v = S_lambda^{-1} grad_next,
  *                   adds Re<v, z - x_next> to grad_lambda[0], and writes
  *                   grad_t = (dD/dx)^H (lambda v) while adding dL/dW to grad_weights.
- * x_t, x_next, AHy, grad_next, grad_t: complex64 [B][H][W]. */
+ * kind SENSE_DENOISER_VARNET (Eq. 5, Sec. 2.3.1): the calls are varnet_stage and
+ *   varnet_stage_backward (lambda_t and its gradient live in the stage
+ *   parameters; lambda, grad_lambda, x_next of the backward and cg_iters are
+ *   not used; dn_ws is a varnet workspace). */
 int unrolled_step(sense_plan plan, int kind, const float* weights, const double* lambda,
                   const void* AHy, const void* x_t, void* x_next, int cg_iters, void* dn_ws,
                   size_t dn_ws_bytes);

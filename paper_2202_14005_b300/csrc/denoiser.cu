@@ -907,11 +907,13 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
 extern "C" {
 
 size_t denoiser_workspace_bytes(int kind, int B, int H, int W) {
+  if (kind == SENSE_DENOISER_VARNET) return vn_denoiser_bytes(B, H, W);
   if (kind != SENSE_DENOISER_MODL || B <= 0 || H <= 0 || W <= 0) return 0;
   return dn_layout(B, H, W).total;
 }
 
 int denoiser_param_count(int kind) {
+  if (kind == SENSE_DENOISER_VARNET) return varnet_param_count();
   return kind == SENSE_DENOISER_MODL ? modl_offsets().total : 0;
 }
 
@@ -928,6 +930,8 @@ int denoiser_workspace_offsets(int kind, int B, int H, int W, size_t* act_offset
 
 int denoiser_forward(int kind, const float* weights, const void* x, void* out, void* ws, size_t ws_bytes,
                      int B, int H, int W, void* stream) {
+  if (kind == SENSE_DENOISER_VARNET)
+    return vn_denoiser_forward(weights, x, out, ws, ws_bytes, B, H, W, static_cast<cudaStream_t>(stream));
   if (int e = check_common(kind, weights, x, ws, ws_bytes, B, H, W)) return e;
   if (!out || !al16(out) || out == x) return SENSE_EINVAL_PTR;
   return forward_impl(weights, static_cast<const float2*>(x), static_cast<float2*>(out),
@@ -937,6 +941,9 @@ int denoiser_forward(int kind, const float* weights, const void* x, void* out, v
 int denoiser_backward(int kind, const float* weights, const void* x, const void* grad_out, void* grad_x,
                       float* grad_weights, void* ws, size_t ws_bytes, int B, int H, int W, int recompute,
                       void* stream) {
+  if (kind == SENSE_DENOISER_VARNET)  // always recomputes K x (the workspace keeps no forward state)
+    return vn_denoiser_backward(weights, x, grad_out, grad_x, grad_weights, ws, ws_bytes, B, H, W,
+                                static_cast<cudaStream_t>(stream));
   if (int e = check_common(kind, weights, x, ws, ws_bytes, B, H, W)) return e;
   if (!grad_out || !grad_x || !grad_weights || !al16(grad_out) || !al16(grad_x) || !al16(grad_weights) ||
       grad_x == grad_out)

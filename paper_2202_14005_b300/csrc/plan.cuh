@@ -103,3 +103,11 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
            int lam_count, int iters, double* rr_hist);
 int launch_dot_rows(sense_plan p, const float2* a, const float2* b, const float2* c,
                     double* out, int out_count, int accumulate);
+
+// VarNet regulariser R(x) = sum_i K_i^T Phi_i'(K_i x) alone (varnet.cu): the VarNet kind of the
+// denoiser calls.  Parameters in the 6,553-value stage layout (lambda unused).
+size_t vn_denoiser_bytes(int B, int H, int W);
+int vn_denoiser_forward(const float* prm, const void* x, void* out, void* ws, size_t ws_bytes, int B, int H,
+                        int W, cudaStream_t st);
+int vn_denoiser_backward(const float* prm, const void* x, const void* grad_out, void* grad_x, float* grad_prm,
+                         void* ws, size_t ws_bytes, int B, int H, int W, cudaStream_t st);

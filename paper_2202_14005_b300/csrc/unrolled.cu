@@ -92,7 +92,7 @@ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 int check_step(sense_plan p, int kind, const void* weights, const double* lambda, const void* AHy,
                void* dn_ws, size_t dn_ws_bytes) {
   if (!p || !weights || !lambda || !AHy || !dn_ws) return SENSE_EINVAL_PTR;
-  if (kind != SENSE_DENOISER_MODL) return SENSE_EUNSUPPORTED;
+  if (kind != SENSE_DENOISER_MODL) return SENSE_EUNSUPPORTED;  // VarNet stages return earlier
   if (!p->ws) return SENSE_EWORKSPACE;
   if (dn_ws_bytes < denoiser_workspace_bytes(kind, p->B, p->H, p->W)) return SENSE_EWORKSPACE;
   if (!al16(AHy) || ((uintptr_t)lambda & 7u)) return SENSE_EINVAL_PTR;
@@ -105,6 +105,8 @@ extern "C" {
 
 int unrolled_step(sense_plan p, int kind, const float* weights, const double* lambda, const void* AHy,
                   const void* x_t, void* x_next, int cg_iters, void* dn_ws, size_t dn_ws_bytes) {
+  if (kind == SENSE_DENOISER_VARNET)  // Eq. 5: lambda_t is part of the stage parameters, no CG
+    return varnet_stage(p, weights, AHy, x_t, x_next, nullptr, dn_ws, dn_ws_bytes);
   if (int e = check_step(p, kind, weights, lambda, AHy, dn_ws, dn_ws_bytes)) return e;
   if (!x_t || !x_next || !al16(x_t) || !al16(x_next) || x_t == x_next) return SENSE_EINVAL_PTR;
   if (cg_iters < 0 || cg_iters > 100000) return SENSE_EINVAL_ARG;
@@ -125,6 +127,9 @@ int unrolled_step_backward(sense_plan p, int kind, const float* weights, const d
                            const void* AHy, const void* x_t, const void* x_next, const void* grad_next,
                            void* grad_t, float* grad_weights, double* grad_lambda, int cg_iters,
                            void* dn_ws, size_t dn_ws_bytes) {
+  if (kind == SENSE_DENOISER_VARNET)  // d/d lambda_t lands in grad_weights (stage layout)
+    return varnet_stage_backward(p, weights, AHy, x_t, nullptr, grad_next, grad_t, grad_weights, dn_ws,
+                                 dn_ws_bytes);
   if (int e = check_step(p, kind, weights, lambda, AHy, dn_ws, dn_ws_bytes)) return e;
   if (!x_t || !x_next || !grad_next || !grad_t || !grad_weights || !grad_lambda || !al16(x_t) ||
       !al16(x_next) || !al16(grad_next) || !al16(grad_t) || grad_t == grad_next)

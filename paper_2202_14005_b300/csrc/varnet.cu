@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(K_THREADS, 2) k_vn_K(const KArgs a) {
 }
 
 // ------------------------------------------------------------ K^T (24 -> 2)
-// out = base - K^T(src) - lambda (n - c)   (c may be NULL)
+// out = base + sgn K^T(src) - lambda (n - c): base, n and c may be NULL (zero; no data term
+// without n)
 // CTA: 128 pixels x 8 output rows, 4 warps x 32 pixels.  For source row s and tap column dx:
 //   D[px][(r, c)] += sum_i src[s][px + 5 - dx][i] w[i][c][h0 + r + 5 - s][dx]
 // (A = the staged source row via ldmatrix, B = the filter taps of the two output channels for
@@ -382,6 +383,7 @@ struct KTArgs {
   const float2* n;
   const float2* c;
   const float* lam;
+  float sgn;
   float2* out;
 };
 
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(128, 4) k_vn_KT(const KTArgs a) {
     }
   }
   // epilogue: (c0, c1) = (re, im) of pixel gid, output row nt * 4 + tig; (c2, c3) pixel gid + 8
-  const float lam = a.lam[0];
+  const float lam = a.n ? a.lam[0] : 0.f;
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -473,10 +475,19 @@ __global__ void __launch_bounds__(128, 4) k_vn_KT(const KTArgs a) {
         const int w = w0 + warp * 32 + mt * 16 + gid + half * 8;
         if (w >= a.W) continue;
         const size_t p = ((size_t)b * a.H + h) * a.W + w;
-        const float2 bv = a.base[p], nv = a.n[p];
-        const float2 cv = a.c ? a.c[p] : make_float2(0.f, 0.f);
-        a.out[p] = make_float2(bv.x - d[mt][nt][2 * half] - lam * (nv.x - cv.x),
-                               bv.y - d[mt][nt][2 * half + 1] - lam * (nv.y - cv.y));
+        float2 o = make_float2(a.sgn * d[mt][nt][2 * half], a.sgn * d[mt][nt][2 * half + 1]);
+        if (a.base) {
+          const float2 bv = a.base[p];
+          o.x += bv.x;
+          o.y += bv.y;
+        }
+        if (a.n) {
+          const float2 nv = a.n[p];
+          const float2 cv = a.c ? a.c[p] : make_float2(0.f, 0.f);
+          o.x -= lam * (nv.x - cv.x);
+          o.y -= lam * (nv.y - cv.y);
+        }
+        a.out[p] = o;
       }
     }
 }
@@ -682,14 +693,25 @@ int vn_prepare() {
 
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+int vn_shape_check(int B, int H, int W) {
+  if (B <= 0 || H <= 0 || W <= 0 || (W & 1)) return SENSE_EINVAL_SHAPE;
+  if (W > WG_MAXW || B > 65535 || (H + 3) / 4 > 65535) return SENSE_EUNSUPPORTED;
+  return SENSE_OK;
+}
+
 int vn_check(sense_plan p, const float* prm, const void* AHy, const void* xt, const void* nx, void* ws,
              size_t ws_bytes) {
   if (!p || !prm || !AHy || !xt || !ws || !al16(AHy) || !al16(xt) || (nx && !al16(nx)) || ((uintptr_t)ws & 255u))
     return SENSE_EINVAL_PTR;
-  if (p->W > WG_MAXW || p->B > 65535 || (p->H + 3) / 4 > 65535) return SENSE_EUNSUPPORTED;
+  if (int e = vn_shape_check(p->B, p->H, p->W)) return e;
   if (ws_bytes < vn_layout(p->B, p->H, p->W).total) return SENSE_EWORKSPACE;
   return vn_prepare();
 }
+
+struct Shape {
+  int B, H, W;
+  cudaStream_t st;
+};
 
 void vn_pack(const float* prm, uint8_t* ws, const VnLayout& L, cudaStream_t st) {
   const int n = K_W_ELEMS + KT_W_ELEMS;
@@ -699,10 +721,10 @@ void vn_pack(const float* prm, uint8_t* ws, const VnLayout& L, cudaStream_t st) 
   prof_mark("vn_misc", st, true);
 }
 
-int launch_K(sense_plan p, int nsrc, const float* prm, const float2* x, const float2* g, uint8_t* ws,
+int launch_K(const Shape& sh, int nsrc, const float* prm, const float2* x, const float2* g, uint8_t* ws,
              const VnLayout& L) {
   KArgs a;
-  a.B = p->B; a.H = p->H; a.W = p->W;
+  a.B = sh.B; a.H = sh.H; a.W = sh.W;
   a.x = x; a.g = g;
   a.wk = reinterpret_cast<const bf16*>(ws + L.wk);
   a.rbf = prm + OFF_RBF;
@@ -711,29 +733,48 @@ int launch_K(sense_plan p, int nsrc, const float* prm, const float2* x, const fl
   a.z = reinterpret_cast<float*>(ws + L.z);
   a.kg = reinterpret_cast<float*>(ws + L.kg);
   const int R = K_RMAX / nsrc;
-  const dim3 grid((p->W + TILE - 1) / TILE, (p->H + R - 1) / R, p->B);
+  const dim3 grid((sh.W + TILE - 1) / TILE, (sh.H + R - 1) / R, sh.B);
   const char* grp = nsrc == 2 ? "vn_Kbwd" : "vn_K";
-  prof_mark(grp, p->stream, false);
+  prof_mark(grp, sh.st, false);
   if (nsrc == 2)
-    k_vn_K<2><<<grid, K_THREADS, KSmem<2>::TOTAL, p->stream>>>(a);
+    k_vn_K<2><<<grid, K_THREADS, KSmem<2>::TOTAL, sh.st>>>(a);
   else
-    k_vn_K<1><<<grid, K_THREADS, KSmem<1>::TOTAL, p->stream>>>(a);
-  prof_mark(grp, p->stream, true);
+    k_vn_K<1><<<grid, K_THREADS, KSmem<1>::TOTAL, sh.st>>>(a);
+  prof_mark(grp, sh.st, true);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
-int launch_KT(sense_plan p, const bf16* src, const float* prm, const float2* base, const float2* n,
-              const float2* c, float2* out, uint8_t* ws, const VnLayout& L) {
+int launch_KT(const Shape& sh, const bf16* src, const float* prm, float sgn, const float2* base,
+              const float2* n, const float2* c, float2* out, uint8_t* ws, const VnLayout& L) {
   KTArgs a;
-  a.B = p->B; a.H = p->H; a.W = p->W;
+  a.B = sh.B; a.H = sh.H; a.W = sh.W;
   a.src = src;
   a.wn = reinterpret_cast<const bf16*>(ws + L.wn);
-  a.base = base; a.n = n; a.c = c; a.lam = prm + OFF_LAM; a.out = out;
-  const dim3 grid((p->W + TILE - 1) / TILE, (p->H + KT_BAND - 1) / KT_BAND, p->B);
-  prof_mark("vn_KT", p->stream, false);
-  k_vn_KT<<<grid, 128, KT_SMEM, p->stream>>>(a);
-  prof_mark("vn_KT", p->stream, true);
+  a.base = base; a.n = n; a.c = c; a.lam = prm + OFF_LAM; a.sgn = sgn; a.out = out;
+  const dim3 grid((sh.W + TILE - 1) / TILE, (sh.H + KT_BAND - 1) / KT_BAND, sh.B);
+  prof_mark("vn_KT", sh.st, false);
+  k_vn_KT<<<grid, 128, KT_SMEM, sh.st>>>(a);
+  prof_mark("vn_KT", sh.st, true);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+// Parameter gradients of the regulariser sum_i K_i^T Phi_i'(K_i x), scaled by `scale` and added to
+// grad_prm: filters  scale * sum (u (x) g_shift + v (x) x_shift),  RBF weights  scale * sum kg phi_j(z).
+// Needs u, v, z, kg of a two-source K launch in the workspace.
+void launch_param_grads(const Shape& sh, const float2* x, const float2* g, float scale, float* grad_prm,
+                        uint8_t* ws, const VnLayout& L) {
+  const int rows = sh.B * sh.H;
+  float* part = reinterpret_cast<float*>(ws + L.part);
+  prof_mark("vn_wgrad", sh.st, false);
+  k_vn_wgrad<<<rows, 128, wg_smem(sh.W), sh.st>>>(sh.B, sh.H, sh.W, reinterpret_cast<const bf16*>(ws + L.u),
+                                                   reinterpret_cast<const bf16*>(ws + L.v), g, x, part);
+  k_vn_reduce<<<(NK * 2 * NT + 31) / 32, 256, 0, sh.st>>>(part, rows, NK * 2 * NT, scale, grad_prm);
+  prof_mark("vn_wgrad", sh.st, true);
+  prof_mark("vn_rbfgrad", sh.st, false);
+  k_vn_rbfgrad<<<rows, 256, 0, sh.st>>>(sh.B, sh.H, sh.W, reinterpret_cast<const float*>(ws + L.z),
+                                         reinterpret_cast<const float*>(ws + L.kg), part);
+  k_vn_reduce<<<(NK * NW + 31) / 32, 256, 0, sh.st>>>(part, rows, NK * NW, scale, grad_prm + OFF_RBF);
+  prof_mark("vn_rbfgrad", sh.st, true);
 }
 
 // Normal operator without lambda (A^H A x) through the plan's own path.
@@ -770,13 +811,14 @@ int varnet_stage(sense_plan p, const float* prm, const void* AHy, const void* x_
   if (!x_next || !al16(x_next) || x_next == x_t || nx_out == x_t || nx_out == x_next) return SENSE_EINVAL_PTR;
   uint8_t* w8 = static_cast<uint8_t*>(ws);
   const VnLayout L = vn_layout(p->B, p->H, p->W);
+  const Shape sh{p->B, p->H, p->W, p->stream};
   const float2* x = static_cast<const float2*>(x_t);
   float2* n1 = nx_out ? static_cast<float2*>(nx_out) : reinterpret_cast<float2*>(w8 + L.n1);
   vn_pack(prm, w8, L, p->stream);
   if (int e = normal0(p, x, n1)) return e;
-  if (int e = launch_K(p, 1, prm, x, nullptr, w8, L)) return e;
-  if (int e = launch_KT(p, reinterpret_cast<const bf16*>(w8 + L.u), prm, x, n1, static_cast<const float2*>(AHy),
-                        static_cast<float2*>(x_next), w8, L))
+  if (int e = launch_K(sh, 1, prm, x, nullptr, w8, L)) return e;
+  if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.u), prm, -1.f, x, n1,
+                        static_cast<const float2*>(AHy), static_cast<float2*>(x_next), w8, L))
     return e;
   prof_count(3);
   return SENSE_OK;
@@ -791,12 +833,11 @@ int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const
   if (!p->ws) return SENSE_EWORKSPACE;  // the lambda-gradient dot uses the plan's workspace
   uint8_t* w8 = static_cast<uint8_t*>(ws);
   const VnLayout L = vn_layout(p->B, p->H, p->W);
+  const Shape sh{p->B, p->H, p->W, p->stream};
   const float2* x = static_cast<const float2*>(x_t);
   const float2* g = static_cast<const float2*>(grad_next);
   float2* n2 = reinterpret_cast<float2*>(w8 + L.n2);
   double* pdot = reinterpret_cast<double*>(w8 + L.pdot);
-  float* part = reinterpret_cast<float*>(w8 + L.part);
-  const int rows = p->B * p->H;
   vn_pack(prm, w8, L, p->stream);
   // grad lambda_t = -Re<g, A^H A x - A^H y>  (A^H A x from the forward when given)
   const float2* n1 = static_cast<const float2*>(nx_t);
@@ -809,23 +850,13 @@ int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const
   prof_mark("vn_misc", p->stream, false);
   k_vn_addlam<<<1, 1, 0, p->stream>>>(pdot, grad_prm);
   prof_mark("vn_misc", p->stream, true);
-  // z = K x, kg = K g, u = Phi'(z), v = Phi''(z) kg
-  if (int e = launch_K(p, 2, prm, x, g, w8, L)) return e;
-  // filter gradient: -(sum u (x) g_shift + v (x) x_shift); reads g and x before grad_t is written
-  prof_mark("vn_wgrad", p->stream, false);
-  k_vn_wgrad<<<rows, 128, wg_smem(p->W), p->stream>>>(p->B, p->H, p->W, reinterpret_cast<const bf16*>(w8 + L.u),
-                                                        reinterpret_cast<const bf16*>(w8 + L.v), g, x, part);
-  k_vn_reduce<<<(NK * 2 * NT + 31) / 32, 256, 0, p->stream>>>(part, rows, NK * 2 * NT, -1.f, grad_prm);
-  prof_mark("vn_wgrad", p->stream, true);
-  // RBF weight gradient: -sum kg phi_j(z)
-  prof_mark("vn_rbfgrad", p->stream, false);
-  k_vn_rbfgrad<<<rows, 256, 0, p->stream>>>(p->B, p->H, p->W, reinterpret_cast<const float*>(w8 + L.z),
-                                            reinterpret_cast<const float*>(w8 + L.kg), part);
-  k_vn_reduce<<<(NK * NW + 31) / 32, 256, 0, p->stream>>>(part, rows, NK * NW, -1.f, grad_prm + OFF_RBF);
-  prof_mark("vn_rbfgrad", p->stream, true);
+  // z = K x, kg = K g, u = Phi'(z), v = Phi''(z) kg; parameter gradients of -R (read g and x before
+  // grad_t is written)
+  if (int e = launch_K(sh, 2, prm, x, g, w8, L)) return e;
+  launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L);
   // grad_t = g - K^T v - lambda A^H A g
   if (int e = normal0(p, g, n2)) return e;
-  if (int e = launch_KT(p, reinterpret_cast<const bf16*>(w8 + L.v), prm, g, n2, nullptr,
+  if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.v), prm, -1.f, g, n2, nullptr,
                         static_cast<float2*>(grad_t), w8, L))
     return e;
   prof_count(8);
@@ -833,3 +864,52 @@ int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const
 }
 
 }  // extern "C"
+
+// The regulariser R(x) = sum_i K_i^T Phi_i'(K_i x) alone, as the VarNet kind of the denoiser calls.
+size_t vn_denoiser_bytes(int B, int H, int W) {
+  if (vn_shape_check(B, H, W)) return 0;
+  return vn_layout(B, H, W).total;
+}
+
+int vn_denoiser_forward(const float* prm, const void* x, void* out, void* ws, size_t ws_bytes, int B, int H, int W,
+                        cudaStream_t st) {
+  if (int e = vn_shape_check(B, H, W)) return e;
+  if (!prm || !x || !out || !ws || !al16(x) || !al16(out) || x == out || ((uintptr_t)ws & 255u))
+    return SENSE_EINVAL_PTR;
+  const VnLayout L = vn_layout(B, H, W);
+  if (ws_bytes < L.total) return SENSE_EWORKSPACE;
+  if (int e = vn_prepare()) return e;
+  uint8_t* w8 = static_cast<uint8_t*>(ws);
+  const Shape sh{B, H, W, st};
+  vn_pack(prm, w8, L, st);
+  if (int e = launch_K(sh, 1, prm, static_cast<const float2*>(x), nullptr, w8, L)) return e;
+  if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.u), prm, 1.f, nullptr, nullptr, nullptr,
+                        static_cast<float2*>(out), w8, L))
+    return e;
+  prof_count(3);
+  return SENSE_OK;
+}
+
+int vn_denoiser_backward(const float* prm, const void* x, const void* grad_out, void* grad_x, float* grad_prm,
+                         void* ws, size_t ws_bytes, int B, int H, int W, cudaStream_t st) {
+  if (int e = vn_shape_check(B, H, W)) return e;
+  if (!prm || !x || !grad_out || !grad_x || !grad_prm || !ws || !al16(x) || !al16(grad_out) || !al16(grad_x) ||
+      grad_x == grad_out || ((uintptr_t)ws & 255u))
+    return SENSE_EINVAL_PTR;
+  const VnLayout L = vn_layout(B, H, W);
+  if (ws_bytes < L.total) return SENSE_EWORKSPACE;
+  if (int e = vn_prepare()) return e;
+  uint8_t* w8 = static_cast<uint8_t*>(ws);
+  const Shape sh{B, H, W, st};
+  const float2* xx = static_cast<const float2*>(x);
+  const float2* g = static_cast<const float2*>(grad_out);
+  vn_pack(prm, w8, L, st);
+  if (int e = launch_K(sh, 2, prm, xx, g, w8, L)) return e;
+  launch_param_grads(sh, xx, g, 1.f, grad_prm, w8, L);
+  // dR/dx^H g = K^T (Phi''(K x) K g)  (the Jacobian of R is symmetric)
+  if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.v), prm, 1.f, nullptr, nullptr, nullptr,
+                        static_cast<float2*>(grad_x), w8, L))
+    return e;
+  prof_count(6);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}

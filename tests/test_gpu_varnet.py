@@ -296,3 +296,58 @@ def test_host_argument_errors():
     ws2 = torch.zeros(int(nb), dtype=torch.uint8, device="cuda")
     assert L.varnet_stage(plan2._h, p(pv), p(x2), p(x2), p(o2), None, p(ws2), nb) == EUNSUPPORTED
     torch.cuda.synchronize()
+
+
+def test_denoiser_and_unrolled_step_kind_varnet():
+    """The VarNet kind of the generic calls: denoiser_forward/backward give the
+    regulariser R(x) = sum_i K_i^T Phi_i'(K_i x) and its reverse mode (checked
+    against the oracle stage with lambda = 0, whose regulariser terms carry the
+    opposite sign); unrolled_step(_backward) equal varnet_stage(_backward) bit
+    for bit."""
+    from paper_2202_14005_b300 import _lib
+    from paper_2202_14005_b300.varnet import unpack_params
+    L = _lib.lib()
+    p = lambda t: C.c_void_p(t.data_ptr())
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    VN = 1
+    B, Cc, H, W = 2, 3, 16, 200
+    maps, mask, y, gt, AHy = problem(B, Cc, H, W, seed=77)
+    vec, f, r, lam = params(1, seed=78)
+    x = (AHy + 0.05 * synth.randn_complex(AHy.shape, 9)).astype(np.complex64)
+    g = (0.1 * synth.randn_complex(AHy.shape, 10)).astype(np.complex64)
+    assert L.denoiser_param_count(VN) == vec.shape[1]
+    nb = L.denoiser_workspace_bytes(VN, B, H, W)
+    ws = torch.zeros(int(nb), dtype=torch.uint8, device="cuda")
+    pv = dev(vec[0])
+    xd, gd = dev(x), dev(g)
+    out = torch.empty_like(xd)
+    _lib.check("denoiser_forward", L.denoiser_forward(VN, p(pv), p(xd), p(out), p(ws), nb, B, H, W, st))
+    gx = torch.empty_like(xd)
+    gw = torch.zeros_like(pv)
+    _lib.check("denoiser_backward", L.denoiser_backward(VN, p(pv), p(xd), p(gd), p(gx), p(gw), p(ws), nb,
+                                                         B, H, W, 1, st))
+    torch.cuda.synchronize()
+    reg_m, _ = onn.varnet_regulariser(x, f[0], r[0], bf16_round)
+    assert rel(out.cpu().numpy(), reg_m) <= 2e-3
+    g_t, g_f, g_w, _ = ounr.varnet_stage_backward(g, x, AHy, maps, mask, f[0], r[0], 0.0, bf16_round)
+    assert rel(gx.cpu().numpy(), g.astype(np.complex128) - g_t) <= 2e-3
+    gf, gr, gl = unpack_params(gw.cpu().numpy())
+    assert rel(gf[0], -g_f) <= 2e-3 and rel(gr[0], -g_w) <= 2e-3
+    assert gl[0] == 0.0  # lambda_t is not a parameter of the regulariser
+    # unrolled_step with the VarNet kind is the VarNet stage
+    tr = trainer(maps, mask, vec, AHy)
+    a1, a2 = torch.empty_like(xd), torch.empty_like(xd)
+    tr.stage(0, xd, a1)
+    lam_unused = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _lib.check("unrolled_step", L.unrolled_step(tr.plan._h, VN, p(tr.params[0]), p(lam_unused), p(tr.xs[0]),
+                                                p(xd), p(a2), 0, p(tr.ws), tr.ws.numel()))
+    b1 = _backward(tr, x, g)
+    p1 = tr.gp.clone()
+    tr.gp.zero_()
+    b2 = torch.empty_like(xd)
+    _lib.check("unrolled_step_backward", L.unrolled_step_backward(
+        tr.plan._h, VN, p(tr.params[0]), p(lam_unused), p(tr.xs[0]), p(xd), p(a2), p(gd), p(b2), p(tr.gp[0]),
+        p(lam_unused), 0, p(tr.ws), tr.ws.numel()))
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2) and torch.equal(b1, b2) and torch.equal(p1, tr.gp)
+    assert lam_unused.item() == 0.0
