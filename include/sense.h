@@ -251,6 +251,14 @@ int varnet_stage_backward(sense_plan plan, const float* params, const void* AHy,
  * grad = 2 (x - gt) / n (complex convention of Sec. 2.2.2).  Plan's stream. */
 int sense_mse_loss(sense_plan plan, const void* x, const void* gt, double* loss, void* grad);
 
+/* Per-slice data scaling of the VarNet workload (Sec. 2.3.1: the data are
+ * scaled so that max |x^0| = 1): with m_b = max over slice b of |x_b|,
+ * x_b /= m_b and, when other != NULL, other_b /= m_b (e.g. the ground truth of
+ * the loss); scale (NULL or device float32 [B]) receives 1 / m_b.  An all-zero
+ * slice is left as it is (scale 1).  x, other: complex64 [B][H][W].  Uses the
+ * plan's workspace; plan's stream. */
+int sense_normalize_max(sense_plan plan, void* x, void* other, float* scale);
+
 /* Adam (Kingma and Ba) on n parameters with moments m, v; step >= 1 is the
  * 1-based update count (bias correction).  The gradient is consumed and set
  * to zero, ready to accumulate the next step.  The float64 variant clamps the

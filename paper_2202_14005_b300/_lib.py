@@ -58,6 +58,7 @@ SIGNATURES = {
     "varnet_stage": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
     "varnet_stage_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
     "sense_mse_loss": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "sense_normalize_max": (_i, [_vp, _vp, _vp, _vp]),
     "adam_update_f32": (_i, [_vp, _vp, _vp, _vp, C.c_size_t, _f, _f, _f, _f, _i, _vp]),
     "adam_update_f64": (_i, [_vp, _vp, _vp, _vp, C.c_size_t, C.c_double, C.c_double, C.c_double,
                              C.c_double, _i, C.c_double, _vp]),

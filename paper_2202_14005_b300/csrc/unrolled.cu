@@ -72,6 +72,50 @@ __global__ void __launch_bounds__(kWarps * 32) k_mse(int rows, int W, const floa
   }
 }
 
+// Per-slice normalisation (the VarNet data scaling, Sec. 2.3.1): m_b = max |x_b| from per-row
+// maxima (order-independent, so exact and reproducible); then x_b /= m_b and, if given,
+// other_b /= m_b; scale[b] = 1 / m_b (1 for an all-zero slice).
+__global__ void __launch_bounds__(kWarps * 32) k_row_absmax(int rows, int W, const float2* x, float* rmax) {
+  const int row = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  float m = 0.f;
+  for (int i = lane; i < W; i += 32) {
+    const float2 v = x[(size_t)row * W + i];
+    m = fmaxf(m, v.x * v.x + v.y * v.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) rmax[row] = m;
+}
+
+__global__ void k_scale_slices(int B, int H, int W, const float* rmax, float2* x, float2* other, float* scale) {
+  __shared__ float s_inv;
+  const int b = blockIdx.y;
+  if (threadIdx.x < 32) {
+    float m = 0.f;
+    for (int h = threadIdx.x; h < H; h += 32) m = fmaxf(m, rmax[(size_t)b * H + h]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      const float inv = m > 0.f ? 1.f / sqrtf(m) : 1.f;
+      s_inv = inv;
+      if (blockIdx.x == 0 && scale) scale[b] = inv;
+    }
+  }
+  __syncthreads();
+  const float inv = s_inv;
+  const size_t n = (size_t)H * W;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float2 v = x[(size_t)b * n + i];
+    x[(size_t)b * n + i] = make_float2(v.x * inv, v.y * inv);
+    if (other) {
+      v = other[(size_t)b * n + i];
+      other[(size_t)b * n + i] = make_float2(v.x * inv, v.y * inv);
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_adam(size_t n, T* p, T* g, T* m, T* v, T lr, T b1, T b2, T eps, T c1, T c2, T lo) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -167,6 +211,23 @@ int sense_mse_loss(sense_plan p, const void* x, const void* gt, double* loss, vo
       inv_n, p->w.part, loss, p->w.counter);
   prof_mark("unrolled_misc", p->stream, true);
   count_launch(p);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int sense_normalize_max(sense_plan p, void* x, void* other, float* scale) {
+  if (!p || !x || !al16(x) || (other && (!al16(other) || other == x)) || (scale && ((uintptr_t)scale & 3u)))
+    return SENSE_EINVAL_PTR;
+  if (!p->ws) return SENSE_EWORKSPACE;
+  const int rows = p->B * p->H;
+  float* rmax = reinterpret_cast<float*>(p->w.part);  // [B][H] scratch (the row-partial buffer)
+  prof_mark("unrolled_misc", p->stream, false);
+  k_row_absmax<<<(rows + kWarps - 1) / kWarps, kWarps * 32, 0, p->stream>>>(rows, p->W,
+                                                                           static_cast<const float2*>(x), rmax);
+  const int per = (int)(((size_t)p->H * p->W + 255) / 256);
+  k_scale_slices<<<dim3(min(per, 64), p->B), 256, 0, p->stream>>>(p->B, p->H, p->W, rmax, static_cast<float2*>(x),
+                                                                  static_cast<float2*>(other), scale);
+  prof_mark("unrolled_misc", p->stream, true);
+  prof_count(2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 

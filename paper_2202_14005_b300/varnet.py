@@ -1,7 +1,8 @@
 """Variational Network training and inference on the libsense C ABI (call
 sequencing only).
 
-One training step (Eq. 5, Sec. 2.3.1): x^0 = A^H y; T gradient stages
+One training step (Eq. 5, Sec. 2.3.1): x^0 = A^H y (optionally scaled to max|x^0| = 1 per
+slice, the paper's VarNet data scaling, with the target scaled alike); T gradient stages
 x^{t+1} = x^t - sum_i K_i^T Phi_i'(K_i x^t) - lambda_t (A^H A x^t - A^H y),
 each with its own filters, RBF weights and step size; loss mean |x^T - x_gt|^2;
 reverse mode stage by stage from the stored stage inputs; Adam on all
@@ -48,7 +49,8 @@ def unpack_params(vec):
 
 
 class VarNetTrainer:
-    def __init__(self, maps: torch.Tensor, mask: torch.Tensor, params: torch.Tensor, lr: float = 1e-4):
+    def __init__(self, maps: torch.Tensor, mask: torch.Tensor, params: torch.Tensor, lr: float = 1e-4,
+                 normalize: bool = False):
         self.plan = SensePlan(maps, mask)
         B, H, W = self.plan.img_shape()
         self.B, self.H, self.W = B, H, W
@@ -71,6 +73,10 @@ class VarNetTrainer:
         self.nx = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(self.T)]
         self.g = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(2)]
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        # data scaling max|x^0| = 1 per slice (Sec. 2.3.1); gtn holds the equally scaled target
+        self.normalize = normalize
+        self.scale = torch.ones(B, dtype=torch.float32, device=dev)
+        self.gtn = torch.empty((B, H, W), dtype=torch.complex64, device=dev)
         self.lr = lr
         self.t = 0
 
@@ -96,19 +102,25 @@ class VarNetTrainer:
         kg = self.ws[off[3]:off[3] + n * 96].view(torch.float32).view(self.B, self.H, self.W, NK)
         return u, v, z, kg
 
-    def forward(self, y: torch.Tensor) -> torch.Tensor:
-        """x^T for k-space y [B, C, H, W] (also keeps every x^t)."""
+    def forward(self, y: torch.Tensor, gt: torch.Tensor | None = None) -> torch.Tensor:
+        """x^T for k-space y [B, C, H, W] (also keeps every x^t).  With normalize, x^0 = A^H y is
+        scaled to max|x^0| = 1 per slice (self.scale) and gt, if given, is scaled alike into self.gtn."""
         self.plan._sync_stream()
         self.plan.adjoint(y, out=self.xs[0])
+        if gt is not None:
+            self.gtn.copy_(gt)
+        if self.normalize:
+            _lib.check("sense_normalize_max", self._lib.sense_normalize_max(
+                self.plan._h, _p(self.xs[0]), _p(self.gtn) if gt is not None else None, _p(self.scale)))
         for t in range(self.T):
             self.stage(t, self.xs[t], self.xs[t + 1], self.nx[t])
         return self.xs[self.T]
 
     def gradients(self, y: torch.Tensor, gt: torch.Tensor):
         """Forward, loss and reverse mode; gradients accumulate into self.gp."""
-        self.forward(y)
+        self.forward(y, gt)
         _lib.check("sense_mse_loss", self._lib.sense_mse_loss(
-            self.plan._h, _p(self.xs[self.T]), _p(gt), _p(self.loss), _p(self.g[0])))
+            self.plan._h, _p(self.xs[self.T]), _p(self.gtn), _p(self.loss), _p(self.g[0])))
         cur = 0
         for t in range(self.T - 1, -1, -1):
             self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1], self.nx[t])

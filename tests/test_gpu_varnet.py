@@ -351,3 +351,26 @@ def test_denoiser_and_unrolled_step_kind_varnet():
     torch.cuda.synchronize()
     assert torch.equal(a1, a2) and torch.equal(b1, b2) and torch.equal(p1, tr.gp)
     assert lam_unused.item() == 0.0
+
+
+def test_normalize_max_scales_each_slice():
+    """sense_normalize_max: max |x_b| = 1 per slice afterwards, the second
+    tensor scaled by the same factor, an all-zero slice untouched."""
+    from paper_2202_14005_b300.varnet import VarNetTrainer
+    maps, mask, y, gt, AHy = problem(3, 2, 16, 64, seed=4)
+    vec, *_ = params(1, seed=5)
+    tr = VarNetTrainer(dev(maps), dev(mask), dev(vec), normalize=True)
+    yd = dev(y)
+    yd[2].zero_()
+    gtd = dev(gt)
+    tr.forward(yd, gtd)
+    torch.cuda.synchronize()
+    a = AHy.astype(np.complex128)
+    a[2] = 0
+    m = np.abs(a).reshape(3, -1).max(axis=1)
+    sc = tr.scale.cpu().numpy()
+    assert np.allclose(sc[:2], 1 / m[:2], rtol=1e-5) and sc[2] == 1.0
+    x0 = tr.xs[0].cpu().numpy()
+    assert np.allclose(np.abs(x0[:2]).reshape(2, -1).max(axis=1), 1.0, rtol=1e-5)
+    assert not x0[2].any()
+    assert rel(tr.gtn.cpu().numpy()[:2], gt[:2] * sc[:2, None, None]) <= 1e-6
