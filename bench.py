@@ -29,7 +29,6 @@ import math
 import multiprocessing as mp
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -52,56 +51,90 @@ PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic
 
 
 # ------------------------------------------------------------------ clocks
+class _Nvml:
+    """Read-only NVML queries through ctypes on the driver's libnvidia-ml (no Python binding
+    needed): SM clock, its maximum and the clock-event reason bits of one device."""
+    SM = 1  # NVML_CLOCK_SM
+    REASONS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+               ("hw_thermal_slowdown", 0x40))
+
+    def __init__(self, pci: str | None, index: int):
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = C.c_void_p()
+        rc = (self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), C.byref(self.h)) if pci
+              else self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h)))
+        if rc != 0:
+            raise RuntimeError(f"no NVML device handle ({rc})")
+
+    def _uint(self, fn, *args):
+        v = self.C.c_uint()
+        if fn(self.h, *args, self.C.byref(v)) != 0:
+            raise RuntimeError("NVML query failed")
+        return v.value
+
+    def sm_mhz(self):
+        return self._uint(self.lib.nvmlDeviceGetClockInfo, self.C.c_int(self.SM))
+
+    def sm_max_mhz(self):
+        return self._uint(self.lib.nvmlDeviceGetMaxClockInfo, self.C.c_int(self.SM))
+
+    def reasons(self):
+        v = self.C.c_ulonglong()
+        if self.lib.nvmlDeviceGetCurrentClocksEventReasons(self.h, self.C.byref(v)) != 0:
+            raise RuntimeError("NVML query failed")
+        return [name for name, bit in self.REASONS if v.value & bit]
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons of one GPU, polled through NVML (read-only queries)
+    every 5 ms from a background thread while the timed region runs."""
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.lines = []
+        self.index = index  # CUDA device index; matched to the NVML device by PCI address
+        self.pci = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(index)
+            self.pci = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        except Exception:
+            pass
+        self.sm, self.reasons, self.smax = [], set(), None
+        self.stop_evt = threading.Event()
+        self.err = None
+
+    def _poll(self):
+        try:
+            nv = _Nvml(self.pci, self.index)
+            self.smax = nv.sm_max_mhz()
+            while not self.stop_evt.is_set():
+                self.sm.append(nv.sm_mhz())
+                self.reasons.update(nv.reasons())
+                time.sleep(0.005)
+            nv.close()
+        except Exception as e:  # NVML unavailable: no samples
+            self.err = str(e)
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+        self.stop_evt.clear()
+        self.t = threading.Thread(target=self._poll, daemon=True)
+        self.t.start()
+        time.sleep(0.02)
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        self.stop_evt.set()
+        self.t.join(timeout=5)
+        if not self.sm:
+            return {"sm_mhz": None, "sm_max_mhz": self.smax, "reasons": [f"no samples: {self.err}"],
+                    "samples": 0}
+        return {"sm_mhz": statistics.median(self.sm), "sm_max_mhz": self.smax,
+                "reasons": sorted(self.reasons), "samples": len(self.sm), "source": "nvml"}
 
 
 # ------------------------------------------------------------- workload

@@ -1,391 +1,22 @@
-// Fused SENSE normal operator for Cartesian line masks (hot path).
-//
-//   out = sum_c conj(S_c) * F^{-1} M^2 F (S_c * x) + lambda * x      (Eq. 4, Eq. 6)
-//
-// With a mask constant along H (phase-encode lines along W), the 2-D transform
-// reduces row by row: F^{-1} diag(m) F = I_H (x) (F_W^{-1} diag(m) F_W), since the
-// H-direction transform meets its own inverse.  The centring of the unitary DFT
-// cancels as well (F_W^{-1} diag(m) F_W is circulant), leaving a plain DFT pair
-// with the mask shifted to plain frequency order and a 1/W scale.
-//
-// Each row-coil pair is transformed with W = Q * P (Q a power of two):
-//   phase A  lane t < P holds u[t + P n1], n1 < Q: Q-point DFT in registers,
-//            twiddle by e^{-2 pi i t k1 / W}, store to shared memory as [k1][t];
-//   phase B  lane (coil gi, residue k1): the P-point DFT over t is evaluated only
-//            at the sampled frequencies k = k1 + Q k2 (pruned, using the pairing
-//            t <-> P - t), weighted by mask^2 / W, and transformed back (again
-//            only from the sampled frequencies) — no coil image or k-space ever
-//            leaves the SM;
-//   phase C  inverse twiddle, inverse Q-point DFT in registers, accumulate
-//            conj(S_c) * v over the coils of the warp.
-// Warps of one row sum their coil groups through shared memory in a fixed
-// order; per-row FP64 partials of the CG inner products are written, and the
-// last CTA to finish reduces them per slice (fixed order, deterministic).
+// Fused SENSE normal operator for Cartesian line masks: plan tables and launcher (the kernel
+// template is in normal_lines.cuh).
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
-#include "plan.cuh"
+#include "normal_lines.cuh"
+
+using namespace nl;
 
 namespace {
-
-struct NLArgs {
-  int B, C, H, J, kstride, rows, nwr, tiles_per_slice, ntiles;
-  const float2* maps;
-  const float4* coef;
-  const float2* tw;
-  const float* wt;
-  const float* sgn;
-  const float2* x;
-  const float2* pold;
-  float2* pout;
-  float2* out;
-  const float2* rhs;
-  float lam_host;
-  const double* lam_dev;
-  const double* beta;
-  double* part;
-  int finalize;
-  double* rr;
-  double* alpha;
-  double* rr_hist_row;
-  unsigned* counter;
-  int* status;
-};
-
-// Shared-memory layout (bytes), identical on host and device.
-struct NLLayout {
-  int coef, tw, wt, sgn, x, y, total;
-};
-SENSE_HD NLLayout nl_layout(int Q, int P, int J, int kstride, int rows, int nwarps, int GB) {
-  NLLayout L;
-  const int W = Q * P;
-  L.coef = 0;
-  L.tw = L.coef + Q * kstride * 16;
-  L.wt = L.tw + Q * P * 8;
-  L.sgn = L.wt + Q * J * 4;
-  L.x = (L.sgn + Q * J * 4 + 15) & ~15;
-  L.y = L.x + rows * W * 8;
-  L.total = L.y + nwarps * GB * W * 8;
-  return L;
-}
-
-// Fixed-order per-slice reductions done by the last CTA of a launch.
-__device__ void nl_finalize(const NLArgs& a) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int b = warp; b < a.B; b += nwarps) {
-    double s = 0.0;
-    for (int i = lane; i < a.H; i += 32) s += __ldcg(a.part + (size_t)b * a.H + i);
-    s = warp_sum_d(s);
-    if (lane != 0) continue;
-    if (a.finalize == 1) {  // alpha = ||r||^2 / Re<p, S p>
-      const double rr = __ldcg(a.rr + b);
-      double al = 0.0;
-      if (!isfinite(s) || !isfinite(rr)) set_status(a.status, SENSE_DEVST_NONFINITE);
-      else if (rr > 0.0) {
-        if (s > 0.0) al = rr / s;
-        else set_status(a.status, SENSE_DEVST_CG_BREAKDOWN);
-      }
-      a.alpha[b] = al;
-    } else {  // initial residual norm
-      if (!isfinite(s)) set_status(a.status, SENSE_DEVST_NONFINITE);
-      a.rr[b] = s;
-      if (a.rr_hist_row) a.rr_hist_row[b] = s;
-    }
-  }
-}
-
-__device__ void last_block(const NLArgs& a) {
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(a.counter, 1u);
-    s_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    nl_finalize(a);
-    __syncthreads();
-    if (threadIdx.x == 0) *a.counter = 0u;
-  }
-}
-
-template <int Q, int P, int JMAX, int MODE>
-__global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
-  constexpr int GB = 32 / Q;          // coils per warp in phase B
-  constexpr int GA = 32 / P;          // coils per pass in phases A/C
-  constexpr int HP = (P - 1) / 2;     // conjugate pairs t <-> P - t, t = 1..HP
-  constexpr bool EVENP = (P % 2) == 0;
-  constexpr int RQ = (HP + 1) / 2;    // float4 quads per slot row
-  constexpr int W = Q * P;
-  constexpr int NPASS = (GB + GA - 1) / GA;
-  static_assert(GB * Q == 32, "Q must divide 32");
-  static_assert(P <= 32 && P >= Q, "phase A needs Q <= P <= 32");
-
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int nthreads = blockDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = nthreads >> 5;
-  const NLLayout Lo = nl_layout(Q, P, a.J, a.kstride, a.rows, nwarps, GB);
-  float4* s_coef = reinterpret_cast<float4*>(smem + Lo.coef);
-  float2* s_tw = reinterpret_cast<float2*>(smem + Lo.tw);
-  float* s_wt = reinterpret_cast<float*>(smem + Lo.wt);
-  float* s_sgn = reinterpret_cast<float*>(smem + Lo.sgn);
-  float2* s_x = reinterpret_cast<float2*>(smem + Lo.x);
-  float2* s_y = reinterpret_cast<float2*>(smem + Lo.y);
-
-  for (int i = threadIdx.x; i < Q * a.kstride; i += nthreads) s_coef[i] = a.coef[i];
-  for (int i = threadIdx.x; i < Q * P; i += nthreads) s_tw[i] = a.tw[i];
-  for (int i = threadIdx.x; i < Q * a.J; i += nthreads) {
-    s_wt[i] = a.wt[i];
-    s_sgn[i] = EVENP ? a.sgn[i] : 0.f;
-  }
-
-  const int J = a.J;
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int b = tile / a.tiles_per_slice;
-    const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
-    const int nrows = min(a.rows, a.H - h0);
-    const size_t img0 = ((size_t)b * a.H + h0) * W;
-    const float lam = a.lam_dev ? (float)a.lam_dev[b] : a.lam_host;
-
-    // ---- stage the input rows (CG: p = r + beta p_old, written back)
-    {
-      const int n4 = nrows * W / 2;
-      const float4* src = reinterpret_cast<const float4*>(a.x + img0);
-      float4* sx4 = reinterpret_cast<float4*>(s_x);
-      if (MODE == NM_CG) {
-        const float be = a.pold ? (float)a.beta[b] : 0.f;
-        const float4* po = a.pold ? reinterpret_cast<const float4*>(a.pold + img0) : nullptr;
-        float4* pn = reinterpret_cast<float4*>(a.pout + img0);
-        for (int i = threadIdx.x; i < n4; i += nthreads) {
-          float4 v = src[i];
-          if (po) {
-            const float4 o = po[i];
-            v.x = fmaf(be, o.x, v.x); v.y = fmaf(be, o.y, v.y);
-            v.z = fmaf(be, o.z, v.z); v.w = fmaf(be, o.w, v.w);
-          }
-          pn[i] = v;
-          sx4[i] = v;
-        }
-      } else {
-        for (int i = threadIdx.x; i < n4; i += nthreads) sx4[i] = src[i];
-      }
-    }
-    __syncthreads();
-
-    const int wrow = warp / a.nwr, cgp = warp - wrow * a.nwr;
-    float2* ybuf = s_y + warp * (GB * W);
-    if (wrow < nrows) {
-      const int h = h0 + wrow;
-      const float2* xrow = s_x + wrow * W;
-      const float2* map0 = a.maps + ((size_t)b * a.C * a.H + h) * W;
-      const size_t cstride = (size_t)a.H * W;
-
-      // ---- phase A: expand, Q-point DFT, twiddle
-#pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
-        const int ga = lane / P, t = lane - ga * P;
-        const int gi = pass * GA + ga;
-        const int c = cgp * GB + gi;
-        if (ga < GA && gi < GB) {
-          float2 v[Q];
-          if (c < a.C) {
-            const float2* srow = map0 + c * cstride;
-#pragma unroll
-            for (int n1 = 0; n1 < Q; ++n1) v[n1] = cmul(__ldg(srow + t + P * n1), xrow[t + P * n1]);
-          } else {
-#pragma unroll
-            for (int n1 = 0; n1 < Q; ++n1) v[n1] = make_float2(0.f, 0.f);
-          }
-          dft_pow2<Q, false>(v);
-          float2* yc = ybuf + gi * W;
-          yc[t] = v[0];
-#pragma unroll
-          for (int k1 = 1; k1 < Q; ++k1) yc[k1 * P + t] = cmul(v[k1], s_tw[k1 * P + t]);
-        }
-      }
-      __syncwarp();
-
-      // ---- phase B: pruned P-point DFT at the sampled frequencies and back.
-      // The conjugate pairs (t, P - t) are streamed from shared memory so that
-      // only the J outputs stay in registers.
-      {
-        const int gi = lane / Q, k1 = lane - gi * Q;
-        float2* col = ybuf + gi * W + k1 * P;
-        const float4* crow = s_coef + k1 * a.kstride;
-        const float* wrow_ = s_wt + k1 * J;
-        const float* srow_ = s_sgn + k1 * J;
-        const float2 Y0 = col[0];
-        float2 Ym = make_float2(0.f, 0.f);
-        if (EVENP) Ym = col[P / 2];
-        float2 X[JMAX];
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-          X[j] = Y0;
-          if (EVENP && j < J) {
-            const float sg = srow_[j];
-            X[j].x = fmaf(sg, Ym.x, X[j].x);
-            X[j].y = fmaf(sg, Ym.y, X[j].y);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-          const int t = 2 * q + 1;
-          const float2 u0 = col[t], w0 = col[P - t];
-          const float2 S0 = cadd(u0, w0), D0 = csub(u0, w0);
-          float2 S1 = make_float2(0.f, 0.f), D1 = S1;
-          if (t + 1 <= HP) {
-            const float2 u1 = col[t + 1], w1 = col[P - t - 1];
-            S1 = cadd(u1, w1);
-            D1 = csub(u1, w1);
-          }
-#pragma unroll
-          for (int j = 0; j < JMAX; ++j) {
-            if (j < J) {
-              const float4 cs = crow[j * RQ + q];
-              X[j].x = fmaf(cs.x, S0.x, fmaf(cs.y, D0.y, X[j].x));
-              X[j].y = fmaf(cs.x, S0.y, fmaf(-cs.y, D0.x, X[j].y));
-              if (t + 1 <= HP) {
-                X[j].x = fmaf(cs.z, S1.x, fmaf(cs.w, D1.y, X[j].x));
-                X[j].y = fmaf(cs.z, S1.y, fmaf(-cs.w, D1.x, X[j].y));
-              }
-            }
-          }
-        }
-        float2 Z0 = make_float2(0.f, 0.f), Zm = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-          if (j < J) {
-            X[j] = cscale(X[j], wrow_[j]);
-            Z0 = cadd(Z0, X[j]);
-            if (EVENP) {
-              const float sg = srow_[j];
-              Zm.x = fmaf(sg, X[j].x, Zm.x);
-              Zm.y = fmaf(sg, X[j].y, Zm.y);
-            }
-          }
-        }
-        __syncwarp();  // every lane has read its column before any is overwritten
-        col[0] = Z0;
-        if (EVENP) col[P / 2] = Zm;
-#pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-          const int t = 2 * q + 1;
-          float2 A0 = make_float2(0.f, 0.f), B0 = A0, A1 = A0, B1 = A0;
-#pragma unroll
-          for (int j = 0; j < JMAX; ++j) {
-            if (j < J) {
-              const float4 cs = crow[j * RQ + q];
-              A0.x = fmaf(cs.x, X[j].x, A0.x); A0.y = fmaf(cs.x, X[j].y, A0.y);
-              B0.x = fmaf(cs.y, X[j].x, B0.x); B0.y = fmaf(cs.y, X[j].y, B0.y);
-              A1.x = fmaf(cs.z, X[j].x, A1.x); A1.y = fmaf(cs.z, X[j].y, A1.y);
-              B1.x = fmaf(cs.w, X[j].x, B1.x); B1.y = fmaf(cs.w, X[j].y, B1.y);
-            }
-          }
-          col[t] = make_float2(A0.x - B0.y, A0.y + B0.x);
-          col[P - t] = make_float2(A0.x + B0.y, A0.y - B0.x);
-          if (t + 1 <= HP) {
-            col[t + 1] = make_float2(A1.x - B1.y, A1.y + B1.x);
-            col[P - t - 1] = make_float2(A1.x + B1.y, A1.y - B1.x);
-          }
-        }
-      }
-      __syncwarp();
-
-      // ---- phase C: inverse twiddle, inverse Q-point DFT, conj-map combine
-      float2 acc[Q];
-#pragma unroll
-      for (int n1 = 0; n1 < Q; ++n1) acc[n1] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
-        const int ga = lane / P, t = lane - ga * P;
-        const int gi = pass * GA + ga;
-        const int c = cgp * GB + gi;
-        if (ga < GA && gi < GB && c < a.C) {
-          const float2* yc = ybuf + gi * W;
-          float2 z[Q];
-          z[0] = yc[t];
-#pragma unroll
-          for (int k1 = 1; k1 < Q; ++k1) z[k1] = cmulc(s_tw[k1 * P + t], yc[k1 * P + t]);
-          dft_pow2<Q, true>(z);
-          const float2* srow = map0 + c * cstride;
-#pragma unroll
-          for (int n1 = 0; n1 < Q; ++n1) acc[n1] = cfmac(__ldg(srow + t + P * n1), z[n1], acc[n1]);
-        }
-      }
-      __syncwarp();
-      if (lane < GA * P) {
-        const int ga = lane / P, t = lane - ga * P;
-#pragma unroll
-        for (int n1 = 0; n1 < Q; ++n1) ybuf[ga * W + t + P * n1] = acc[n1];
-      }
-    }
-    __syncthreads();
-
-    // ---- epilogue: sum coil groups in fixed order, + lambda x, row partial
-    for (int rr = warp; rr < nrows; rr += nwarps) {
-      const int h = h0 + rr;
-      float part = 0.f;
-      const float2* xr = s_x + rr * W;
-      const float2* rh = (MODE == NM_RESID) ? a.rhs + img0 + (size_t)rr * W : nullptr;
-      float2* orow = a.out + img0 + (size_t)rr * W;
-      for (int n = lane; n < W; n += 32) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int g = 0; g < a.nwr; ++g) {
-          const float2* yb = s_y + (rr * a.nwr + g) * (GB * W);
-#pragma unroll
-          for (int ga = 0; ga < GA; ++ga) s = cadd(s, yb[ga * W + n]);
-        }
-        const float2 xv = xr[n];
-        float2 o = make_float2(fmaf(lam, xv.x, s.x), fmaf(lam, xv.y, s.y));
-        if (MODE == NM_RESID) {
-          o = csub(rh[n], o);
-          part = fmaf(o.x, o.x, fmaf(o.y, o.y, part));
-        } else {
-          part = fmaf(xv.x, o.x, fmaf(xv.y, o.y, part));
-        }
-        orow[n] = o;
-      }
-      if (a.part) {
-        const double d = warp_sum_d((double)part);
-        if (lane == 0) a.part[(size_t)b * a.H + h] = d;
-      }
-    }
-    __syncthreads();
-  }
-  if (a.finalize) last_block(a);
-}
-
-typedef void (*NLKernel)(const NLArgs);
-
-template <int Q, int P, int JMAX>
-NLKernel pick_mode(int mode) {
-  switch (mode) {
-    case NM_PLAIN: return k_normal_lines<Q, P, JMAX, NM_PLAIN>;
-    case NM_CG: return k_normal_lines<Q, P, JMAX, NM_CG>;
-    default: return k_normal_lines<Q, P, JMAX, NM_RESID>;
-  }
-}
-template <int Q, int P>
-NLKernel pick_j(int jmax, int mode) {
-  switch (jmax) {
-    case 4: return pick_mode<Q, P, 4>(mode);
-    case 8: return pick_mode<Q, P, 8>(mode);
-    default: return pick_mode<Q, P, 16>(mode);
-  }
-}
 
 // (Q, P) factorisations with a compiled kernel: W = 64, 128, 232, 256, 320, 368.
 struct QP { int Q, P; };
 const QP kSupported[] = {{8, 8}, {8, 16}, {8, 29}, {16, 16}, {16, 20}, {16, 23}};
 
 NLKernel pick_kernel(int Q, int P, int jmax, int mode) {
-#define SENSE_QP(q, p) if (Q == q && P == p) return pick_j<q, p>(jmax, mode);
-  SENSE_QP(8, 8) SENSE_QP(8, 16) SENSE_QP(8, 29) SENSE_QP(16, 16) SENSE_QP(16, 20) SENSE_QP(16, 23)
-#undef SENSE_QP
+  if (Q == 8) return pick_q8(P, jmax, mode);
+  if (Q == 16) return pick_q16(P, jmax, mode);
   return nullptr;
 }
 
@@ -410,7 +41,9 @@ int build_lines_tables(sense_plan pl) {
       if (mplain[k1 + Q * k2] != 0.f) slots[k1].push_back(k2);
   int J = 1;
   for (auto& s : slots) J = std::max<int>(J, (int)s.size());
-  const int JMAX = J <= 4 ? 4 : (J <= 8 ? 8 : (J <= 16 ? 16 : 0));
+  int JMAX = 0;
+  for (int c : kJmax)
+    if (!JMAX && J <= c) JMAX = c;
   if (!JMAX) return SENSE_OK;  // too dense for the pruned kernel: generic path
   int kstride = J * RQ;
   if (kstride % 2 == 0) kstride += 1;  // odd quad stride spreads k1 rows over banks
