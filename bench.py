@@ -41,9 +41,10 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
              "varnet_train": "varnet_train_b4_c15_320x368_R4_T10"}
 # DRAM bytes per launch (read + write) of each kernel group from the committed ncu
 # captures under profiles/ (None until captured for the current kernel version).
-# normal_lines: 113.6 MB on a 16-slice launch, scaled to the 4-slice MoDL launch; conv64_tc: a dgrad launch.
-NCU_TRAFFIC = {"normal_lines": 28.4e6, "conv64_tc": 65.0e6, "wgrad64": None, "vn_K": None, "vn_Kbwd": None,
-               "vn_KT": None, "vn_wgrad": None}
+# normal_lines: 113.6 MB on a 16-slice launch, scaled to the 4-slice MoDL launch; conv64_tc: a dgrad
+# launch; vn_*: one launch each of the 4-slice 320x368 VarNet step (profiles/varnet_train_*.md).
+NCU_TRAFFIC = {"normal_lines": 28.4e6, "conv64_tc": 65.0e6, "wgrad64": None, "vn_K": 3.9e6, "vn_Kbwd": 103.4e6,
+               "vn_KT": 41.5e6, "vn_wgrad": 70.9e6}
 # kernel groups the library times with CUDA events when profiling is on
 PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
                   "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc", "vn_K", "vn_Kbwd", "vn_KT",
