@@ -41,10 +41,15 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
              "varnet_train": "varnet_train_b4_c15_320x368_R4_T10"}
 # DRAM bytes per launch (read + write) of each kernel group from the committed ncu
 # captures under profiles/ (None until captured for the current kernel version).
-# normal_lines: 113.6 MB on a 16-slice launch, scaled to the 4-slice MoDL launch; conv64_tc: a dgrad
-# launch; vn_*: one launch each of the 4-slice 320x368 VarNet step (profiles/varnet_train_*.md).
-NCU_TRAFFIC = {"normal_lines": 28.4e6, "conv64_tc": 65.0e6, "wgrad64": None, "vn_K": 3.9e6, "vn_Kbwd": 103.4e6,
-               "vn_KT": 41.5e6, "vn_wgrad": 70.9e6}
+# DRAM bytes (read + write) per launch from the committed ncu captures under profiles/, per workload
+# (None where no capture of the current kernel version exists for that workload):
+# normal_lines 113.6 MB on a 16-slice CG launch (cg_sense), scaled to the 4-slice MoDL launch by slices;
+# conv64_tc a dgrad launch; vn_* one launch each of the 4-slice 320x368 VarNet step.
+NCU_TRAFFIC = {
+    "cg_sense": {"normal_lines": 113.6e6},
+    "modl_train": {"normal_lines": 28.4e6, "conv64_tc": 65.0e6},
+    "varnet_train": {"vn_K": 3.9e6, "vn_Kbwd": 103.4e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
+}
 # kernel groups the library times with CUDA events when profiling is on
 PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
                   "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc", "vn_K", "vn_Kbwd", "vn_KT",
@@ -152,7 +157,7 @@ def fp32_peak_tflops(sm_mhz):
     return 148 * 128 * 2 * (sm_mhz or 2032.0) * 1e6 / 1e12
 
 
-def kernel_report(name, ms, n, alg, peaks_d, clocks):
+def kernel_report(name, ms, n, alg, peaks_d, clocks, workload):
     """Achieved vs peak for one kernel group; alg = (kind, amount per launch)."""
     if n == 0 or ms <= 0:
         return None
@@ -168,7 +173,7 @@ def kernel_report(name, ms, n, alg, peaks_d, clocks):
         ach = per / t / 1e12
         peak, unit = fp32_peak_tflops(clocks.get("sm_max_mhz")), "TFLOP/s"
     return {"kernel": name, "bound": kind, "achieved": round(ach, 2), "peak": round(peak, 1),
-            "unit": unit, "frac": round(ach / peak, 4), "traffic": NCU_TRAFFIC.get(name),
+            "unit": unit, "frac": round(ach / peak, 4), "traffic": NCU_TRAFFIC.get(workload, {}).get(name),
             "launches": n, "avg_launch_us": round(1e3 * ms / n, 3), "alg_per_launch": per}
 
 
@@ -373,13 +378,13 @@ def run_ours(args, rank, world, local_rank):
     conv_flops = 2.0 * px * 64 * 576
     vn_flops = 2.0 * px * 24 * 2 * 121  # one 2<->24 channel 11x11 convolution
     kern = {
-        "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks),
-        "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks),
-        "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("tensor", conv_flops), pk, clocks),
-        "vn_K": kernel_report("vn_K", *prof["vn_K"], ("tensor", vn_flops), pk, clocks),
-        "vn_Kbwd": kernel_report("vn_Kbwd", *prof["vn_Kbwd"], ("tensor", 2 * vn_flops), pk, clocks),
-        "vn_KT": kernel_report("vn_KT", *prof["vn_KT"], ("tensor", vn_flops), pk, clocks),
-        "vn_wgrad": kernel_report("vn_wgrad", *prof["vn_wgrad"], ("tensor", 2 * vn_flops), pk, clocks),
+        "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks, args.workload),
+        "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks, args.workload),
+        "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("tensor", conv_flops), pk, clocks, args.workload),
+        "vn_K": kernel_report("vn_K", *prof["vn_K"], ("tensor", vn_flops), pk, clocks, args.workload),
+        "vn_Kbwd": kernel_report("vn_Kbwd", *prof["vn_Kbwd"], ("tensor", 2 * vn_flops), pk, clocks, args.workload),
+        "vn_KT": kernel_report("vn_KT", *prof["vn_KT"], ("tensor", vn_flops), pk, clocks, args.workload),
+        "vn_wgrad": kernel_report("vn_wgrad", *prof["vn_wgrad"], ("tensor", 2 * vn_flops), pk, clocks, args.workload),
     }
     kern = {k: v for k, v in kern.items() if v}
     total_kernel_ms = {k: prof[k][0] for k in prof}
