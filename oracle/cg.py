@@ -26,7 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .sense import normal, dot, _lam
+from .sense import normal, normal_sets, dot, _lam
 
 
 class CGBreakdown(RuntimeError):
@@ -69,6 +69,12 @@ def cg_solve(maps, mask, lam, rhs, x0, iters: int):
     """x = (A^H A + lambda I)^{-1} rhs by ``iters`` CG iterations from x0 (None -> 0)."""
     lam_b = _lam(lam, np.asarray(rhs).shape[0])
     return cg(lambda p: normal(p, maps, mask, lam_b), rhs, x0, iters)
+
+
+def cg_solve_sets(maps, mask, lam, rhs, x0, iters: int):
+    """Soft-SENSE data consistency (Sec. 2.3.3): x [B, NS, H, W] = (A^H A + lambda I)^{-1} rhs."""
+    lam_b = _lam(lam, np.asarray(rhs).shape[0])
+    return cg(lambda p: normal_sets(p, maps, mask, lam_b), rhs, x0, iters)
 
 
 def cg_solve_backward(maps, mask, lam, grad_x, x, z, iters: int):

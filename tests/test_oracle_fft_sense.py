@@ -146,3 +146,60 @@ def test_forward_matches_matrix_form():
     for c in range(2):
         ref = (FH @ (maps[0, c] * x[0]) @ FW.T) * mask[None, :]
         np.testing.assert_allclose(y[0, c], ref, atol=1e-12)
+
+
+# ------------------------------------------------------------ soft-SENSE (Sec. 2.3.3)
+def _sets_problem(H=6, W=10, C=3, B=2, NS=2, seed=21, line=True):
+    rng = np.random.default_rng(seed)
+    maps = np.stack([np.stack([synth.coil_maps(C, H, W, rng) * (0.6 if s else 1.0) for s in range(NS)])
+                     for _ in range(B)])  # [B, NS, C, H, W]
+    mask = synth.line_mask(W, 2.5, 2, "uniform", rng) if line else \
+        (rng.uniform(size=(H, W)) < 0.4).astype(np.float32)
+    return maps, mask
+
+
+def test_soft_sense_one_set_is_sense():
+    maps, mask = _sets_problem(NS=1)
+    x = synth.randn_complex((2, 6, 10), 31)
+    y = synth.randn_complex((2, 3, 6, 10), 32)
+    np.testing.assert_allclose(osense.forward_sets(x[:, None], maps, mask), osense.forward(x, maps[:, 0], mask),
+                               atol=1e-14)
+    np.testing.assert_allclose(osense.adjoint_sets(y, maps, mask)[:, 0], osense.adjoint(y, maps[:, 0], mask),
+                               atol=1e-14)
+
+
+@pytest.mark.parametrize("line", [True, False])
+def test_soft_sense_adjoint_identity(line):
+    maps, mask = _sets_problem(line=line)
+    x = synth.randn_complex((2, 2, 6, 10), 33)
+    y = synth.randn_complex((2, 3, 6, 10), 34)
+    lhs = np.vdot(osense.forward_sets(x, maps, mask), y)
+    rhs = np.vdot(x, osense.adjoint_sets(y, maps, mask))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_soft_sense_full_mask_is_pointwise_gram():
+    """Full sampling: F^H F = I, so (A^H A x)_s' = sum_s (sum_c conj(S_{s',c}) S_{s,c}) x_s pixel by pixel."""
+    maps, _ = _sets_problem(H=8, W=12, C=4)
+    x = synth.randn_complex((2, 2, 8, 12), 35)
+    lam = 0.2
+    G = np.einsum("bpchw,bschw->bpshw", np.conj(maps), maps)
+    ref = np.einsum("bpshw,bshw->bphw", G, x) + lam * x
+    np.testing.assert_allclose(osense.normal_sets(x, maps, np.ones(12, dtype=np.float32), lam), ref, atol=1e-12)
+
+
+def test_soft_sense_normal_hermitian_psd_and_cg_matches_solve():
+    from oracle import cg as ocg
+    maps, mask = _sets_problem(H=4, W=6, C=3, B=1)
+    n = 2 * 4 * 6
+    lam = 0.05
+    M = np.zeros((n, n), dtype=np.complex128)
+    for j in range(n):
+        e = np.zeros((1, 2, 4, 6), dtype=np.complex128)
+        e.flat[j] = 1
+        M[:, j] = osense.normal_sets(e, maps, mask, lam).reshape(-1)
+    assert np.abs(M - M.conj().T).max() < 1e-13
+    assert np.linalg.eigvalsh(M).min() >= lam - 1e-12
+    b = synth.randn_complex((1, 2, 4, 6), 36)
+    x, _ = ocg.cg_solve_sets(maps, mask, lam, b, None, n)
+    np.testing.assert_allclose(x.reshape(-1), np.linalg.solve(M, b.reshape(-1)), atol=1e-9)
