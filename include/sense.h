@@ -66,6 +66,17 @@ typedef struct sense_plan_s* sense_plan;
  * Errors: SENSE_EINVAL_SHAPE, SENSE_EINVAL_PTR, SENSE_EUNSUPPORTED, SENSE_ECUDA. */
 int sense_plan_create(sense_plan* plan, int B, int C, int H, int W, const void* maps,
                       const float* mask, int mask_is_lines, void* stream);
+/* Soft-SENSE (Sec. 2.3.3, "Extensions to the SENSE model"): S >= 1 sets of maps,
+ * maps [B][S][C][H][W].  Every image of such a plan (x, x0, rhs, out, AHy, CG
+ * vectors) is [B][S][H][W], one component per map set:
+ *   A x = { M F sum_s S_{s,c} x_s }_c,   (A^H y)_s = sum_c conj(S_{s,c}) F^{-1}(M y_c).
+ * S = 1 is sense_plan_create.  S = 2 with a line mask uses the fused
+ * normal-operator kernel where one is compiled (W = 128, 232, 320, 368); other
+ * cases (S <= 8) run the generic row/column transforms.  The learned-regulariser
+ * calls (unrolled_step, varnet_stage, ...) take S = 1 plans only
+ * (SENSE_EUNSUPPORTED). */
+int sense_plan_create_sets(sense_plan* plan, int B, int S, int C, int H, int W, const void* maps,
+                           const float* mask, int mask_is_lines, void* stream);
 int sense_plan_destroy(sense_plan plan);
 /* Change the stream later calls launch on. */
 int sense_plan_set_stream(sense_plan plan, void* stream);
@@ -247,7 +258,7 @@ int varnet_stage_backward(sense_plan plan, const float* params, const void* AHy,
                           void* ws, size_t ws_bytes);
 
 /* Training loss of the unrolled networks: loss[0] = mean |x - gt|^2 over the
- * plan's B*H*W complex elements (float64, fixed-order sum) and
+ * plan's B*S*H*W complex elements (float64, fixed-order sum) and
  * grad = 2 (x - gt) / n (complex convention of Sec. 2.2.2).  Plan's stream. */
 int sense_mse_loss(sense_plan plan, const void* x, const void* gt, double* loss, void* grad);
 

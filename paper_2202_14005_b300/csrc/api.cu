@@ -18,15 +18,16 @@ struct WsLayout {
 
 WsLayout ws_layout(const sense_plan p) {
   WsLayout L;
-  const size_t img = (size_t)p->B * p->H * p->W * sizeof(float2);
+  const size_t plane = (size_t)p->B * p->H * p->W * sizeof(float2);
+  const size_t img = plane * p->S;  // images [B][S][H][W]
   size_t o = 0;
-  L.T = o; o += up256(img * p->C);
+  L.T = o; o += up256(plane * p->C);
   L.r = o; o += up256(img);
   L.p = o; o += up256(img);
   L.q = o; o += up256(img);
   L.t0 = o; o += up256(img);
   L.t1 = o; o += up256(img);
-  L.part = o; o += up256((size_t)p->B * p->H * sizeof(double));
+  L.part = o; o += up256((size_t)p->B * p->S * p->H * sizeof(double));
   L.rr = o; o += up256(p->B * sizeof(double));
   L.alpha = o; o += up256(p->B * sizeof(double));
   L.beta = o; o += up256(p->B * sizeof(double));
@@ -59,10 +60,16 @@ const char* sense_strerror(int code) {
 
 int sense_plan_create(sense_plan* out, int B, int C, int H, int W, const void* maps,
                       const float* mask, int mask_is_lines, void* stream) {
+  return sense_plan_create_sets(out, B, 1, C, H, W, maps, mask, mask_is_lines, stream);
+}
+
+int sense_plan_create_sets(sense_plan* out, int B, int S, int C, int H, int W, const void* maps,
+                           const float* mask, int mask_is_lines, void* stream) {
   if (!out) return SENSE_EINVAL_PTR;
   *out = nullptr;
-  if (B <= 0 || C <= 0 || H <= 0 || W <= 0 || (H & 1) || (W & 1)) return SENSE_EINVAL_SHAPE;
-  if ((long long)B * C * H * W > (1ll << 34)) return SENSE_EUNSUPPORTED;
+  if (B <= 0 || S <= 0 || C <= 0 || H <= 0 || W <= 0 || (H & 1) || (W & 1)) return SENSE_EINVAL_SHAPE;
+  if (S > 8) return SENSE_EUNSUPPORTED;
+  if ((long long)B * S * C * H * W > (1ll << 34)) return SENSE_EUNSUPPORTED;
   if (!maps || !mask || !aligned16(maps) || !aligned16(mask)) return SENSE_EINVAL_PTR;
   if (mask_is_lines != 0 && mask_is_lines != 1) return SENSE_EINVAL_ARG;
   std::vector<float2> twH, twW;
@@ -71,7 +78,7 @@ int sense_plan_create(sense_plan* out, int B, int C, int H, int W, const void* m
   if (int e = build_fft1d(fW, W, twW)) return e;
   sense_plan p = new (std::nothrow) sense_plan_s();
   if (!p) return SENSE_ECUDA;
-  p->B = B; p->C = C; p->H = H; p->W = W;
+  p->B = B; p->C = C; p->H = H; p->W = W; p->S = S;
   p->maps = static_cast<const float2*>(maps);
   p->mask = mask;
   p->mask_is_lines = mask_is_lines;
@@ -127,7 +134,7 @@ int sense_plan_create(sense_plan* out, int B, int C, int H, int W, const void* m
     return SENSE_ECUDA;
   }
   int err = generic_prepare(p);
-  if (!err) err = build_lines_tables(p);
+  if (!err) err = build_lines_tables(p);  // fused line-mask kernel where one is compiled
   if (err) {
     sense_plan_destroy(p);
     return err;

@@ -213,7 +213,7 @@ __global__ void k_lam_expand(int B, const double* lam, int count, double* out) {
 
 RowArgs base_args(sense_plan p) {
   RowArgs a;
-  a.B = p->B; a.H = p->H; a.W = p->W;
+  a.B = p->B; a.H = p->S * p->H; a.W = p->W;  // [B][S][H][W] = [B][S*H][W] rows
   a.a = a.b = a.c = nullptr;
   a.o1 = a.o2 = nullptr;
   a.part = p->w.part;
@@ -224,7 +224,7 @@ RowArgs base_args(sense_plan p) {
   return a;
 }
 
-int grid_rows(sense_plan p) { return (p->B * p->H + kRowsPerCta - 1) / kRowsPerCta; }
+int grid_rows(sense_plan p) { return (p->B * p->S * p->H + kRowsPerCta - 1) / kRowsPerCta; }
 
 }  // namespace
 
@@ -240,7 +240,7 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
   // ---- initial residual
   if (x0) {
     if (x0 != x &&
-        cudaMemcpyAsync(x, x0, (size_t)B * p->H * p->W * sizeof(float2), cudaMemcpyDeviceToDevice,
+        cudaMemcpyAsync(x, x0, (size_t)B * p->S * p->H * p->W * sizeof(float2), cudaMemcpyDeviceToDevice,
                         p->stream) != cudaSuccess)
       return SENSE_ECUDA;
     if (p->lines.ok) {

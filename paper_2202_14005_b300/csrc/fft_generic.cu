@@ -118,7 +118,7 @@ __device__ __forceinline__ float pm1(int n) { return (n & 1) ? -1.f : 1.f; }
 // Row pass, expanding by the coil maps:  T[b,c,h,:] = DFT_W(S_c x) with
 //   mode 0 (forward): input (-1)^{h+w} S x, output (-1)^{kw} (-1)^{W/2} / sqrt(W)
 //   mode 1 (normal):  plain DFT, no modulation, no scale.
-__global__ void __launch_bounds__(kThreads) k_row_expand(int B, int C, int H, const float2* x,
+__global__ void __launch_bounds__(kThreads) k_row_expand(int B, int S, int C, int H, const float2* x,
                                                          const float2* maps, float2* T,
                                                          Fft1DDev f, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -130,7 +130,10 @@ __global__ void __launch_bounds__(kThreads) k_row_expand(int B, int C, int H, co
   const int nr = min(kRows, H - h0);
   for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
     const int r = i / W, w = i - r * W, h = h0 + r;
-    float2 v = cmul(maps[(((size_t)b * C + c) * H + h) * W + w], x[((size_t)b * H + h) * W + w]);
+    // coil image: sum over the map sets of S_{s,c} x_s (maps [B][S][C][H][W], x [B][S][H][W])
+    float2 v = make_float2(0.f, 0.f);
+    for (int s = 0; s < S; ++s)
+      v = cfma(maps[((((size_t)b * S + s) * C + c) * H + h) * W + w], x[(((size_t)b * S + s) * H + h) * W + w], v);
     if (mode == 0) v = cscale(v, pm1(h + w));
     a[i] = v;
   }
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_col(int W, const float2* src, floa
 //   out[b,h,:] = sum_c conj(S_c) post(IDFT_W(pre(T[b,c,h,:]))) (+ lambda xin)
 //   mode 1 (adjoint): pre (-1)^{kw}, post (-1)^w (-1)^{W/2}/sqrt(W)
 //   mode 2 (normal):  no modulation, no scale (the scale sits in the mask table)
-__global__ void __launch_bounds__(kThreads) k_row_combine(int C, int H, const float2* T,
+__global__ void __launch_bounds__(kThreads) k_row_combine(int S, int C, int H, const float2* T,
                                                           const float2* maps, float2* out,
                                                           Fft1DDev f, int mode,
                                                           const float2* xin, float lam_host,
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_row_combine(int C, int H, const fl
   const int W = f.L;
   float2* a = reinterpret_cast<float2*>(smem);
   float2* bb = a + kRows * W;
-  const int b = blockIdx.y;
+  const int b = blockIdx.y / S, s = blockIdx.y - b * S;  // output set s of slice b
   const int h0 = blockIdx.x * kRows;
   const int nr = min(kRows, H - h0);
   float2 acc[kMaxPer];
@@ -245,8 +248,8 @@ __global__ void __launch_bounds__(kThreads) k_row_combine(int C, int H, const fl
         const int r = i / W, w = i - r * W;
         float2 v = res[i];
         if (mode == 1) v = cscale(v, sc * pm1(w));
-        const float2 s = maps[(((size_t)b * C + c) * H + h0 + r) * W + w];
-        acc[e] = cfmac(s, v, acc[e]);
+        const float2 sm = maps[((((size_t)b * S + s) * C + c) * H + h0 + r) * W + w];
+        acc[e] = cfmac(sm, v, acc[e]);
       }
     }
     __syncthreads();
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_row_combine(int C, int H, const fl
   for (int e = 0; e < kMaxPer; ++e) {
     const int i = threadIdx.x + e * blockDim.x;
     if (i < nr * W) {
-      const size_t o = ((size_t)b * H + h0) * W + i;
+      const size_t o = (((size_t)b * S + s) * H + h0) * W + i;
       float2 v = acc[e];
       if (xin) {
         const float2 xv = xin[o];
@@ -319,7 +322,7 @@ int generic_prepare(sense_plan p) {
 int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->C, p->H, x, p->maps, y,
+  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->S, p->C, p->H, x, p->maps, y,
                                                               dev(p->fW), 0);
   prof_mark("fft_generic", p->stream, true);
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
@@ -337,9 +340,9 @@ int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
   k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, p->w.T, dev(p->fH), p->mask,
                                                       p->mask_is_lines, 1);
   prof_mark("fft_generic", p->stream, true);
-  const dim3 gr((p->H + kRows - 1) / kRows, p->B);
+  const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->S);
   prof_mark("fft_generic", p->stream, false);
-  k_row_combine<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->C, p->H, p->w.T, p->maps, x,
+  k_row_combine<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->S, p->C, p->H, p->w.T, p->maps, x,
                                                               dev(p->fW), 1, nullptr, 0.f, nullptr);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
@@ -350,7 +353,7 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
                           const double* lam_dev) {
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->C, p->H, x, p->maps,
+  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->S, p->C, p->H, x, p->maps,
                                                               p->w.T, dev(p->fW), 1);
   prof_mark("fft_generic", p->stream, true);
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
@@ -358,10 +361,10 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
   k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, p->w.T, p->w.T, dev(p->fH),
                                                       p->mask2s, p->mask_is_lines, 2);
   prof_mark("fft_generic", p->stream, true);
-  const dim3 gr2((p->H + kRows - 1) / kRows, p->B);
+  const dim3 gr2((p->H + kRows - 1) / kRows, p->B * p->S);
   prof_mark("fft_generic", p->stream, false);
   k_row_combine<<<gr2, kThreads, smem_rows(p->W), p->stream>>>(
-      p->C, p->H, p->w.T, p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
+      p->S, p->C, p->H, p->w.T, p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 3);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;

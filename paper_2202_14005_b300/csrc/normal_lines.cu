@@ -14,9 +14,9 @@ namespace {
 struct QP { int Q, P; };
 const QP kSupported[] = {{8, 8}, {8, 16}, {8, 29}, {16, 16}, {16, 20}, {16, 23}};
 
-NLKernel pick_kernel(int Q, int P, int jmax, int mode) {
-  if (Q == 8) return pick_q8(P, jmax, mode);
-  if (Q == 16) return pick_q16(P, jmax, mode);
+NLKernel pick_kernel(int Q, int P, int jmax, int mode, int ns) {
+  if (Q == 8) return pick_q8(P, jmax, mode, ns);
+  if (Q == 16) return pick_q16(P, jmax, mode, ns);
   return nullptr;
 }
 
@@ -82,7 +82,7 @@ int build_lines_tables(sense_plan pl) {
   if (nwr > 8) return SENSE_OK;
   int rows = std::max(1, 8 / nwr);
   const int nwarps = rows * nwr;
-  const NLLayout Lo = nl_layout(Q, P, J, kstride, rows, nwarps, GB);
+  const NLLayout Lo = nl_layout(Q, P, J, kstride, rows, nwarps, GB, pl->S);
   if (Lo.total > 200 * 1024) return SENSE_OK;
 
   const size_t bc = coef.size() * sizeof(float4), bt = tw.size() * sizeof(float2);
@@ -105,7 +105,8 @@ int build_lines_tables(sense_plan pl) {
   T.rows = rows; T.nwr = nwr; T.threads = nwarps * 32; T.smem = Lo.total;
   int maxb = 0;
   for (int mode = 0; mode < 3; ++mode) {
-    NLKernel k = pick_kernel(Q, P, JMAX, mode);
+    NLKernel k = pick_kernel(Q, P, JMAX, mode, pl->S);
+    if (!k) return SENSE_OK;  // no fused kernel for this (Q, P, sets): generic path
     int nb = 0;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total) != cudaSuccess ||
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -128,10 +129,10 @@ void free_lines_tables(sense_plan pl) {
 
 int launch_normal_lines(sense_plan pl, const NormalLaunch& L) {
   const LinesTables& T = pl->lines;
-  NLKernel k = pick_kernel(T.Q, T.P, T.JMAX, L.mode);
+  NLKernel k = pick_kernel(T.Q, T.P, T.JMAX, L.mode, pl->S);
   if (!k) return SENSE_EUNSUPPORTED;
   NLArgs a;
-  a.B = pl->B; a.C = pl->C; a.H = pl->H; a.J = T.J; a.kstride = T.kstride;
+  a.B = pl->B; a.C = pl->C; a.H = pl->H; a.HS = pl->S * pl->H; a.J = T.J; a.kstride = T.kstride;
   a.rows = T.rows; a.nwr = T.nwr;
   a.tiles_per_slice = (pl->H + T.rows - 1) / T.rows;
   a.ntiles = pl->B * a.tiles_per_slice;

@@ -32,7 +32,7 @@
 namespace nl {
 
 struct NLArgs {
-  int B, C, H, J, kstride, rows, nwr, tiles_per_slice, ntiles;
+  int B, C, H, HS, J, kstride, rows, nwr, tiles_per_slice, ntiles;  // HS = sets * H (CG rows per slice)
   const float2* maps;
   const float4* coef;
   const float2* tw;
@@ -59,7 +59,7 @@ struct NLArgs {
 struct NLLayout {
   int coef, tw, wt, sgn, x, y, total;
 };
-SENSE_HD NLLayout nl_layout(int Q, int P, int J, int kstride, int rows, int nwarps, int GB) {
+SENSE_HD NLLayout nl_layout(int Q, int P, int J, int kstride, int rows, int nwarps, int GB, int NS) {
   NLLayout L;
   const int W = Q * P;
   L.coef = 0;
@@ -67,7 +67,7 @@ SENSE_HD NLLayout nl_layout(int Q, int P, int J, int kstride, int rows, int nwar
   L.wt = L.tw + Q * P * 8;
   L.sgn = L.wt + Q * J * 4;
   L.x = (L.sgn + Q * J * 4 + 15) & ~15;
-  L.y = L.x + rows * W * 8;
+  L.y = L.x + NS * rows * W * 8;
   L.total = L.y + nwarps * GB * W * 8;
   return L;
 }
@@ -77,7 +77,7 @@ __device__ inline void nl_finalize(const NLArgs& a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int b = warp; b < a.B; b += nwarps) {
     double s = 0.0;
-    for (int i = lane; i < a.H; i += 32) s += __ldcg(a.part + (size_t)b * a.H + i);
+    for (int i = lane; i < a.HS; i += 32) s += __ldcg(a.part + (size_t)b * a.HS + i);
     s = warp_sum_d(s);
     if (lane != 0) continue;
     if (a.finalize == 1) {  // alpha = ||r||^2 / Re<p, S p>
@@ -114,8 +114,10 @@ __device__ inline void last_block(const NLArgs& a) {
   }
 }
 
-template <int Q, int P, int JMAX, int MODE>
-__global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
+// NS = map sets (soft-SENSE): x, out [B][NS][H][W], maps [B][NS][C][H][W]; coil image
+// sum_s S_{s,c} x_s in phase A, one conj(S_{s,c}) accumulation per set in phase C.
+template <int Q, int P, int JMAX, int MODE, int NS>
+__global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLArgs a) {
   constexpr int GB = 32 / Q;          // coils per warp in phase B
   constexpr int GA = 32 / P;          // coils per pass in phases A/C
   constexpr int HP = (P - 1) / 2;     // conjugate pairs t <-> P - t, t = 1..HP
@@ -125,12 +127,13 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
   constexpr int NPASS = (GB + GA - 1) / GA;
   static_assert(GB * Q == 32, "Q must divide 32");
   static_assert(P <= 32 && P >= Q, "phase A needs Q <= P <= 32");
+  static_assert(NS * GA <= GB, "phase C stores NS x GA rows in a warp's GB-row buffer");
 
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthreads = blockDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = nthreads >> 5;
-  const NLLayout Lo = nl_layout(Q, P, a.J, a.kstride, a.rows, nwarps, GB);
+  const NLLayout Lo = nl_layout(Q, P, a.J, a.kstride, a.rows, nwarps, GB, NS);
   float4* s_coef = reinterpret_cast<float4*>(smem + Lo.coef);
   float2* s_tw = reinterpret_cast<float2*>(smem + Lo.tw);
   float* s_wt = reinterpret_cast<float*>(smem + Lo.wt);
@@ -150,14 +153,15 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
     const int b = tile / a.tiles_per_slice;
     const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
     const int nrows = min(a.rows, a.H - h0);
-    const size_t img0 = ((size_t)b * a.H + h0) * W;
     const float lam = a.lam_dev ? (float)a.lam_dev[b] : a.lam_host;
 
-    // ---- stage the input rows (CG: p = r + beta p_old, written back)
-    {
+    // ---- stage the input rows of every set (CG: p = r + beta p_old, written back)
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+      const size_t img0 = (((size_t)b * NS + st) * a.H + h0) * W;
       const int n4 = nrows * W / 2;
       const float4* src = reinterpret_cast<const float4*>(a.x + img0);
-      float4* sx4 = reinterpret_cast<float4*>(s_x);
+      float4* sx4 = reinterpret_cast<float4*>(s_x + st * a.rows * W);
       if (MODE == NM_CG) {
         const float be = a.pold ? (float)a.beta[b] : 0.f;
         const float4* po = a.pold ? reinterpret_cast<const float4*>(a.pold + img0) : nullptr;
@@ -182,9 +186,9 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
     float2* ybuf = s_y + warp * (GB * W);
     if (wrow < nrows) {
       const int h = h0 + wrow;
-      const float2* xrow = s_x + wrow * W;
-      const float2* map0 = a.maps + ((size_t)b * a.C * a.H + h) * W;
-      const size_t cstride = (size_t)a.H * W;
+      const float2* xrow = s_x + wrow * W;  // set st: + st * rows * W
+      const float2* map0 = a.maps + ((size_t)b * NS * a.C * a.H + h) * W;
+      const size_t cstride = (size_t)a.H * W, sstride = (size_t)a.C * a.H * W;
 
       // ---- phase A: expand, Q-point DFT, twiddle
 #pragma unroll
@@ -198,6 +202,11 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
             const float2* srow = map0 + c * cstride;
 #pragma unroll
             for (int n1 = 0; n1 < Q; ++n1) v[n1] = cmul(__ldg(srow + t + P * n1), xrow[t + P * n1]);
+#pragma unroll
+            for (int st = 1; st < NS; ++st)
+#pragma unroll
+              for (int n1 = 0; n1 < Q; ++n1)
+                v[n1] = cfma(__ldg(srow + st * sstride + t + P * n1), xrow[st * a.rows * W + t + P * n1], v[n1]);
           } else {
 #pragma unroll
             for (int n1 = 0; n1 < Q; ++n1) v[n1] = make_float2(0.f, 0.f);
@@ -297,10 +306,12 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
       }
       __syncwarp();
 
-      // ---- phase C: inverse twiddle, inverse Q-point DFT, conj-map combine
-      float2 acc[Q];
+      // ---- phase C: inverse twiddle, inverse Q-point DFT, conj-map combine (one sum per set)
+      float2 acc[NS][Q];
 #pragma unroll
-      for (int n1 = 0; n1 < Q; ++n1) acc[n1] = make_float2(0.f, 0.f);
+      for (int st = 0; st < NS; ++st)
+#pragma unroll
+        for (int n1 = 0; n1 < Q; ++n1) acc[st][n1] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int pass = 0; pass < NPASS; ++pass) {
         const int ga = lane / P, t = lane - ga * P;
@@ -315,29 +326,36 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
           dft_pow2<Q, true>(z);
           const float2* srow = map0 + c * cstride;
 #pragma unroll
-          for (int n1 = 0; n1 < Q; ++n1) acc[n1] = cfmac(__ldg(srow + t + P * n1), z[n1], acc[n1]);
+          for (int st = 0; st < NS; ++st)
+#pragma unroll
+            for (int n1 = 0; n1 < Q; ++n1)
+              acc[st][n1] = cfmac(__ldg(srow + st * sstride + t + P * n1), z[n1], acc[st][n1]);
         }
       }
       __syncwarp();
       if (lane < GA * P) {
         const int ga = lane / P, t = lane - ga * P;
 #pragma unroll
-        for (int n1 = 0; n1 < Q; ++n1) ybuf[ga * W + t + P * n1] = acc[n1];
+        for (int st = 0; st < NS; ++st)
+#pragma unroll
+          for (int n1 = 0; n1 < Q; ++n1) ybuf[(st * GA + ga) * W + t + P * n1] = acc[st][n1];
       }
     }
     __syncthreads();
 
-    // ---- epilogue: sum coil groups in fixed order, + lambda x, row partial
-    for (int rr = warp; rr < nrows; rr += nwarps) {
+    // ---- epilogue: sum coil groups in fixed order, + lambda x, row partial (per set and row)
+    for (int it = warp; it < NS * nrows; it += nwarps) {
+      const int st = it / nrows, rr = it - st * nrows;
       const int h = h0 + rr;
+      const size_t orow0 = (((size_t)b * NS + st) * a.H + h) * W;
       float part = 0.f;
-      const float2* xr = s_x + rr * W;
-      const float2* rh = (MODE == NM_RESID) ? a.rhs + img0 + (size_t)rr * W : nullptr;
-      float2* orow = a.out + img0 + (size_t)rr * W;
+      const float2* xr = s_x + (st * a.rows + rr) * W;
+      const float2* rh = (MODE == NM_RESID) ? a.rhs + orow0 : nullptr;
+      float2* orow = a.out + orow0;
       for (int n = lane; n < W; n += 32) {
         float2 s = make_float2(0.f, 0.f);
         for (int g = 0; g < a.nwr; ++g) {
-          const float2* yb = s_y + (rr * a.nwr + g) * (GB * W);
+          const float2* yb = s_y + (rr * a.nwr + g) * (GB * W) + st * GA * W;
 #pragma unroll
           for (int ga = 0; ga < GA; ++ga) s = cadd(s, yb[ga * W + n]);
         }
@@ -353,7 +371,7 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
       }
       if (a.part) {
         const double d = warp_sum_d((double)part);
-        if (lane == 0) a.part[(size_t)b * a.H + h] = d;
+        if (lane == 0) a.part[(size_t)b * a.HS + st * a.H + h] = d;
       }
     }
     __syncthreads();
@@ -363,31 +381,33 @@ __global__ void __launch_bounds__(256, 3) k_normal_lines(const NLArgs a) {
 
 typedef void (*NLKernel)(const NLArgs);
 
-template <int Q, int P, int JMAX>
+template <int Q, int P, int JMAX, int NS>
 NLKernel pick_mode(int mode) {
   switch (mode) {
-    case NM_PLAIN: return k_normal_lines<Q, P, JMAX, NM_PLAIN>;
-    case NM_CG: return k_normal_lines<Q, P, JMAX, NM_CG>;
-    default: return k_normal_lines<Q, P, JMAX, NM_RESID>;
+    case NM_PLAIN: return k_normal_lines<Q, P, JMAX, NM_PLAIN, NS>;
+    case NM_CG: return k_normal_lines<Q, P, JMAX, NM_CG, NS>;
+    default: return k_normal_lines<Q, P, JMAX, NM_RESID, NS>;
   }
 }
+
 // Slot capacities with a compiled kernel: the smallest one >= J is used.
 constexpr int kJmax[] = {4, 6, 8, 10, 12, 16};
 
-template <int Q, int P>
+template <int Q, int P, int NS>
 NLKernel pick_j(int jmax, int mode) {
   switch (jmax) {
-    case 4: return pick_mode<Q, P, 4>(mode);
-    case 6: return pick_mode<Q, P, 6>(mode);
-    case 8: return pick_mode<Q, P, 8>(mode);
-    case 10: return pick_mode<Q, P, 10>(mode);
-    case 12: return pick_mode<Q, P, 12>(mode);
-    default: return pick_mode<Q, P, 16>(mode);
+    case 4: return pick_mode<Q, P, 4, NS>(mode);
+    case 6: return pick_mode<Q, P, 6, NS>(mode);
+    case 8: return pick_mode<Q, P, 8, NS>(mode);
+    case 10: return pick_mode<Q, P, 10, NS>(mode);
+    case 12: return pick_mode<Q, P, 12, NS>(mode);
+    default: return pick_mode<Q, P, 16, NS>(mode);
   }
 }
 
-// Defined in normal_lines_q8.cu (Q = 8) and normal_lines_q16.cu (Q = 16); NULL if not compiled.
-NLKernel pick_q8(int P, int jmax, int mode);
-NLKernel pick_q16(int P, int jmax, int mode);
+// Defined in normal_lines_q8.cu (Q = 8) and normal_lines_q16.cu (Q = 16); NULL if not compiled
+// (ns = 2 map sets only where two sets fit a warp's phase-C buffer: P >= 16 for Q = 8, P > 16 for Q = 16).
+NLKernel pick_q8(int P, int jmax, int mode, int ns);
+NLKernel pick_q16(int P, int jmax, int mode, int ns);
 
 }  // namespace nl

@@ -3,10 +3,15 @@
 
 namespace nl {
 
-NLKernel pick_q16(int P, int jmax, int mode) {
-  if (P == 16) return pick_j<16, 16>(jmax, mode);
-  if (P == 20) return pick_j<16, 20>(jmax, mode);
-  if (P == 23) return pick_j<16, 23>(jmax, mode);
+NLKernel pick_q16(int P, int jmax, int mode, int ns) {
+  if (ns == 1) {
+    if (P == 16) return pick_j<16, 16, 1>(jmax, mode);
+    if (P == 20) return pick_j<16, 20, 1>(jmax, mode);
+    if (P == 23) return pick_j<16, 23, 1>(jmax, mode);
+  } else if (ns == 2) {
+    if (P == 20) return pick_j<16, 20, 2>(jmax, mode);
+    if (P == 23) return pick_j<16, 23, 2>(jmax, mode);
+  }
   return nullptr;
 }
 

@@ -3,10 +3,15 @@
 
 namespace nl {
 
-NLKernel pick_q8(int P, int jmax, int mode) {
-  if (P == 8) return pick_j<8, 8>(jmax, mode);
-  if (P == 16) return pick_j<8, 16>(jmax, mode);
-  if (P == 29) return pick_j<8, 29>(jmax, mode);
+NLKernel pick_q8(int P, int jmax, int mode, int ns) {
+  if (ns == 1) {
+    if (P == 8) return pick_j<8, 8, 1>(jmax, mode);
+    if (P == 16) return pick_j<8, 16, 1>(jmax, mode);
+    if (P == 29) return pick_j<8, 29, 1>(jmax, mode);
+  } else if (ns == 2) {
+    if (P == 16) return pick_j<8, 16, 2>(jmax, mode);
+    if (P == 29) return pick_j<8, 29, 2>(jmax, mode);
+  }
   return nullptr;
 }
 

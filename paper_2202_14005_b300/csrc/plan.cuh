@@ -47,6 +47,7 @@ struct Workspace {
 
 struct sense_plan_s {
   int B = 0, C = 0, H = 0, W = 0;
+  int S = 1;                    // sets of maps (soft-SENSE); images are [B][S][H][W]
   const float2* maps = nullptr;
   const float* mask = nullptr;  // device, centred order
   int mask_is_lines = 0;

@@ -137,6 +137,7 @@ int check_step(sense_plan p, int kind, const void* weights, const double* lambda
                void* dn_ws, size_t dn_ws_bytes) {
   if (!p || !weights || !lambda || !AHy || !dn_ws) return SENSE_EINVAL_PTR;
   if (kind != SENSE_DENOISER_MODL) return SENSE_EUNSUPPORTED;  // VarNet stages return earlier
+  if (p->S != 1) return SENSE_EUNSUPPORTED;                    // one image per slice
   if (!p->ws) return SENSE_EWORKSPACE;
   if (dn_ws_bytes < denoiser_workspace_bytes(kind, p->B, p->H, p->W)) return SENSE_EWORKSPACE;
   if (!al16(AHy) || ((uintptr_t)lambda & 7u)) return SENSE_EINVAL_PTR;
@@ -203,7 +204,7 @@ int sense_mse_loss(sense_plan p, const void* x, const void* gt, double* loss, vo
   if (!p || !x || !gt || !loss || !grad || !al16(x) || !al16(gt) || !al16(grad) || ((uintptr_t)loss & 7u))
     return SENSE_EINVAL_PTR;
   if (!p->ws) return SENSE_EWORKSPACE;
-  const int rows = p->B * p->H;
+  const int rows = p->B * p->S * p->H;  // every map-set image of every slice
   const double inv_n = 1.0 / ((double)rows * p->W);
   prof_mark("unrolled_misc", p->stream, false);
   k_mse<<<(rows + kWarps - 1) / kWarps, kWarps * 32, 0, p->stream>>>(
@@ -218,13 +219,14 @@ int sense_normalize_max(sense_plan p, void* x, void* other, float* scale) {
   if (!p || !x || !al16(x) || (other && (!al16(other) || other == x)) || (scale && ((uintptr_t)scale & 3u)))
     return SENSE_EINVAL_PTR;
   if (!p->ws) return SENSE_EWORKSPACE;
-  const int rows = p->B * p->H;
-  float* rmax = reinterpret_cast<float*>(p->w.part);  // [B][H] scratch (the row-partial buffer)
+  const int HS = p->S * p->H;  // a slice holds S map-set images
+  const int rows = p->B * HS;
+  float* rmax = reinterpret_cast<float*>(p->w.part);  // [B][S*H] scratch (the row-partial buffer)
   prof_mark("unrolled_misc", p->stream, false);
   k_row_absmax<<<(rows + kWarps - 1) / kWarps, kWarps * 32, 0, p->stream>>>(rows, p->W,
                                                                            static_cast<const float2*>(x), rmax);
-  const int per = (int)(((size_t)p->H * p->W + 255) / 256);
-  k_scale_slices<<<dim3(min(per, 64), p->B), 256, 0, p->stream>>>(p->B, p->H, p->W, rmax, static_cast<float2*>(x),
+  const int per = (int)(((size_t)HS * p->W + 255) / 256);
+  k_scale_slices<<<dim3(min(per, 64), p->B), 256, 0, p->stream>>>(p->B, HS, p->W, rmax, static_cast<float2*>(x),
                                                                   static_cast<float2*>(other), scale);
   prof_mark("unrolled_misc", p->stream, true);
   prof_count(2);

@@ -704,6 +704,7 @@ int vn_check(sense_plan p, const float* prm, const void* AHy, const void* xt, co
   if (!p || !prm || !AHy || !xt || !ws || !al16(AHy) || !al16(xt) || (nx && !al16(nx)) || ((uintptr_t)ws & 255u))
     return SENSE_EINVAL_PTR;
   if (int e = vn_shape_check(p->B, p->H, p->W)) return e;
+  if (p->S != 1) return SENSE_EUNSUPPORTED;  // one image per slice
   if (ws_bytes < vn_layout(p->B, p->H, p->W).total) return SENSE_EWORKSPACE;
   return vn_prepare();
 }

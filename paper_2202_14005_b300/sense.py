@@ -36,21 +36,27 @@ def _req(t: torch.Tensor, name: str, dtype, shape):
 class SensePlan:
     """A plan for B slices, C coils, H x W images with fixed maps and mask.
 
-    maps: complex64 [B, C, H, W]; mask: float32 [W] (line mask) or [H, W].
+    maps: complex64 [B, C, H, W], or [B, S, C, H, W] for S sets of maps
+    (soft-SENSE, Sec. 2.3.3: images are then [B, S, H, W]);
+    mask: float32 [W] (line mask) or [H, W].
     The plan keeps references to both tensors and owns a torch workspace.
     """
 
     def __init__(self, maps: torch.Tensor, mask: torch.Tensor):
-        B, Cc, H, W = maps.shape
-        _req(maps, "maps", torch.complex64, (B, Cc, H, W))
+        if maps.dim() == 5:
+            B, NS, Cc, H, W = maps.shape
+        else:
+            B, Cc, H, W = maps.shape
+            NS = 0
+        _req(maps, "maps", torch.complex64, tuple(maps.shape))
         lines = 1 if mask.dim() == 1 else 0
         _req(mask, "mask", torch.float32, (W,) if lines else (H, W))
-        self.B, self.C, self.H, self.W = B, Cc, H, W
+        self.B, self.C, self.H, self.W, self.S = B, Cc, H, W, NS
         self.maps, self.mask, self.lines = maps, mask, lines
         self._lib = _lib.lib()
         h = C.c_void_p()
-        _lib.check("sense_plan_create", self._lib.sense_plan_create(
-            C.byref(h), B, Cc, H, W, _ptr(maps), _ptr(mask), lines, _stream()))
+        _lib.check("sense_plan_create", self._lib.sense_plan_create_sets(
+            C.byref(h), B, max(NS, 1), Cc, H, W, _ptr(maps), _ptr(mask), lines, _stream()))
         self._h = h
         nb = C.c_size_t()
         _lib.check("sense_plan_workspace_bytes", self._lib.sense_plan_workspace_bytes(h, C.byref(nb)))
@@ -74,7 +80,7 @@ class SensePlan:
             pass
 
     def img_shape(self):
-        return (self.B, self.H, self.W)
+        return (self.B, self.S, self.H, self.W) if self.S else (self.B, self.H, self.W)
 
     # -- operators
     def forward(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -256,3 +256,83 @@ def test_workspace_required_errors():
     assert L.sense_normal(h, C.c_void_p(xd.data_ptr()), C.c_void_p(o.data_ptr()), C.c_float(-1.0)) == -3
     assert L.sense_normal(h, C.c_void_p(xd.data_ptr()), C.c_void_p(xd.data_ptr()), C.c_float(0.1)) == -2
     L.sense_plan_destroy(h)
+
+
+# ------------------------------------------------------------ soft-SENSE (Sec. 2.3.3)
+def _sets_problem(B, NS, C, H, W, seed, line=True):
+    rng = np.random.default_rng(seed)
+    maps = np.stack([np.stack([synth.coil_maps(C, H, W, rng) * (0.6 if s else 1.0) for s in range(NS)])
+                     for _ in range(B)]).astype(np.complex64)
+    if line:
+        mask = synth.line_mask(W, 4.0, max(4, W // 16), "uniform", rng)
+    else:
+        mask = (rng.uniform(size=(H, W)) < 0.3).astype(np.float32)
+    return maps, mask
+
+
+@pytest.mark.parametrize("shape,line", [((2, 2, 4, 24, 40), True), ((1, 2, 3, 32, 64), False),
+                                        ((3, 3, 2, 16, 30), True)])
+def test_soft_sense_operators(shape, line):
+    """Forward, adjoint and normal operator with several map sets against the oracle."""
+    from paper_2202_14005_b300.sense import SensePlan
+    B, NS, C, H, W = shape
+    maps, mask = _sets_problem(B, NS, C, H, W, seed=H + W, line=line)
+    x = synth.randn_complex((B, NS, H, W), 1).astype(np.complex64)
+    y = (synth.randn_complex((B, C, H, W), 2) * osense.mask2d(mask, H, W)).astype(np.complex64)
+    plan = SensePlan(dev(maps), dev(mask))
+    assert plan.img_shape() == (B, NS, H, W)
+    yg = plan.forward(dev(x)).cpu().numpy()
+    xg = plan.adjoint(dev(y)).cpu().numpy()
+    ng = plan.normal(dev(x), 0.3).cpu().numpy()
+    torch.cuda.synchronize()
+    assert rel(yg, osense.forward_sets(x, maps, mask)) <= 1e-5
+    assert rel(xg, osense.adjoint_sets(y, maps, mask)) <= 1e-5
+    assert rel(ng, osense.normal_sets(x, maps, mask, 0.3)) <= 1e-5
+
+
+def test_soft_sense_cg_and_backward():
+    from paper_2202_14005_b300.sense import SensePlan
+    B, NS, C, H, W = 2, 2, 4, 32, 64
+    maps, mask = _sets_problem(B, NS, C, H, W, seed=5)
+    rhs = synth.randn_complex((B, NS, H, W), 3).astype(np.complex64)
+    plan = SensePlan(dev(maps), dev(mask))
+    lam = torch.tensor([0.05], dtype=torch.float64, device="cuda")
+    x = plan.cg_solve(dev(rhs), lam, 10).cpu().numpy()
+    ref, _ = ocg.cg_solve_sets(maps, mask, 0.05, rhs, None, 10)
+    assert rel(x, ref) <= 1e-4
+    g = synth.randn_complex((B, NS, H, W), 4).astype(np.complex64)
+    v, gl = plan.cg_solve_backward(dev(g), dev(x), dev(rhs), lam, 10)
+    rv, _ = ocg.cg_solve_sets(maps, mask, 0.05, g, None, 10)
+    assert rel(v.cpu().numpy(), rv) <= 1e-4
+    rgl = float(np.sum(np.real(osense.dot(rv, rhs.astype(np.complex128) - x))))
+    assert abs(gl.item() - rgl) <= 1e-4 * abs(rgl)
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 4, 16, 232), (1, 2, 6, 8, 368), (1, 2, 3, 12, 128), (2, 2, 5, 10, 320)])
+def test_soft_sense_fused_line_kernel(shape):
+    """Two map sets with a line mask run the fused normal-operator kernel (checked through the
+    library's per-kernel-class profile counters); normal operator and 10-iteration CG against
+    the oracle."""
+    from paper_2202_14005_b300 import _lib
+    from paper_2202_14005_b300.sense import SensePlan
+    B, NS, C, H, W = shape
+    maps, mask = _sets_problem(B, NS, C, H, W, seed=W + 1)
+    x = synth.randn_complex((B, NS, H, W), 7).astype(np.complex64)
+    plan = SensePlan(dev(maps), dev(mask))
+    torch.cuda.synchronize()
+    _lib.profile_read("normal_lines")
+    _lib.profile_read("fft_generic")
+    _lib.profile_enable(True)
+    ng = plan.normal(dev(x), 0.1)
+    lam = torch.tensor([0.05], dtype=torch.float64, device="cuda")
+    xs = plan.cg_solve(dev(x), lam, 10)
+    torch.cuda.synchronize()
+    _lib.profile_enable(False)
+    n_fused = _lib.profile_read("normal_lines")[1]
+    n_generic = _lib.profile_read("fft_generic")[1]
+    assert n_fused == 11 and n_generic == 0, (n_fused, n_generic)
+    assert rel(ng.cpu().numpy(), osense.normal_sets(x, maps, mask, 0.1)) <= 1e-5
+    ref, _ = ocg.cg_solve_sets(maps, mask, 0.05, x, None, 10)
+    assert rel(xs.cpu().numpy(), ref) <= 1e-4
+    assert plan.status() == 0
