@@ -1,7 +1,7 @@
 """Benchmark of the unrolled-reconstruction hot path on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload modl_train|cg_sense|varnet_train]
+                    [--workload modl_train|cg_sense|varnet_train|noncart_modl_infer]
 
 Default step (modl_train): one MoDL training step on 4 slices of 256x232 with
 12 coils (R = 6 variable-density line mask): x^0 = A^H y, five unrolled blocks
@@ -38,7 +38,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "unrolled-recon slices/s (fwd+bwd) & normal-op HBM GB/s vs plain CG-SENSE @NRMSE"
 WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it",
-             "varnet_train": "varnet_train_b4_c15_320x368_R4_T10"}
+             "varnet_train": "varnet_train_b4_c15_320x368_R4_T10",
+             "noncart_modl_infer": "modl_infer_radial_b32_c12_256x256_96x512_K10_cg10"}
 # DRAM bytes per launch (read + write) of each kernel group from the committed ncu
 # captures under profiles/ (None until captured for the current kernel version).
 # DRAM bytes (read + write) per launch from the committed ncu captures under profiles/, per workload
@@ -53,7 +54,7 @@ NCU_TRAFFIC = {
 # kernel groups the library times with CUDA events when profiling is on
 PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
                   "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc", "vn_K", "vn_Kbwd", "vn_KT",
-                  "vn_wgrad", "vn_rbfgrad", "vn_misc")
+                  "vn_wgrad", "vn_rbfgrad", "vn_misc", "toeplitz")
 
 
 # ------------------------------------------------------------------ clocks
@@ -311,6 +312,83 @@ def run_ours(args, rank, world, local_rank):
         outs = [(out_h, x2)]
         step_fn = step_cg
         value_slices = B
+    elif args.workload == "noncart_modl_infer":
+        # Sec. 2.3.3: radial sampling, A^H A through the Toeplitz embedding (PSF on the 2x grid,
+        # computed on the GPU from the trajectory); x^0 = A^H y precomputed (noiseless here:
+        # A^H A x_gt, since the non-uniform adjoint of measured samples is gridding, not built);
+        # MoDL inference with K = 10 blocks of the config-3 CNN (He-initialised weights) and 10 CG
+        # iterations each; plain 30-iteration CG-SENSE measured beside it.
+        from paper_2202_14005_b300.sense import toeplitz_psf
+        c5 = synth.CONFIGS[5]
+        cfg = c5
+        inp5 = make_inputs(c5, slice_offset=rank * c5.B)
+        maps5 = torch.from_numpy(inp5["maps"]).to(dev)
+        traj = synth.radial_trajectory(c5.extra["spokes"], c5.extra["samples"], c5.H).reshape(-1, 2)
+        psf = toeplitz_psf(torch.from_numpy(traj.astype(np.float32)).to(dev), c5.H, c5.W)
+        plan5 = SensePlan.toeplitz(maps5, psf)
+        gt5 = torch.from_numpy(inp5["x_gt"]).to(dev)
+        AHy5 = plan5.normal(gt5, 0.0)
+        ws, bs = synth.modl_cnn_weights(5000 + rank)
+        flat = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(ws, bs)]).astype(np.float32)
+        tr = ModlTrainer(maps5, None, torch.from_numpy(flat).to(dev), c5.lam, c5.extra["K"], c5.cg_iters,
+                         plan=plan5)
+
+        def step_nc():
+            tr.forward_from_adjoint(AHy5)
+
+        for _ in range(args.warmup):
+            step_nc()
+        torch.cuda.synchronize()
+        assert plan5.status() == 0 and tr.dn.status() == 0
+        steps = args.steps
+        clk.start()
+        t_ms, prof, launches = timed_steps(step_nc, steps, flush, dist)
+        clocks = clk.stop()
+        assert plan5.status() == 0 and tr.dn.status() == 0
+        B = c5.B
+        N5 = c5.H * c5.W
+        normal_bytes = 8 * N5 * B * (c5.C + 2)
+        gt_np = inp5["x_gt"]
+        nrmse_modl = float(np.linalg.norm(tr.xs[-1].cpu().numpy() - gt_np) / np.linalg.norm(gt_np))
+        # plain CG-SENSE, 30 iterations from x^0 = A^H y
+        lam5 = torch.tensor([c5.lam], dtype=torch.float64, device=dev)
+        xcg = torch.empty_like(AHy5)
+        plan5.cg_solve(AHy5, lam5, 30, x0=AHy5, out=xcg)
+        torch.cuda.synchronize()
+        tc = []
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan5.cg_solve(AHy5, lam5, 30, x0=AHy5, out=xcg)
+            e1.record()
+            torch.cuda.synchronize()
+            tc.append(e0.elapsed_time(e1))
+        nrmse_cg = float(np.linalg.norm(xcg.cpu().numpy() - gt_np) / np.linalg.norm(gt_np))
+        # standalone Toeplitz normal operator
+        tn5 = []
+        xo5 = torch.empty_like(AHy5)
+        for _ in range(10):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan5.normal(AHy5, c5.lam, out=xo5)
+            e1.record()
+            torch.cuda.synchronize()
+            tn5.append(e0.elapsed_time(e1))
+        tn5m = statistics.median(tn5)
+        res["noncart"] = {"toeplitz_normal_op": {"GB/s": round(normal_bytes / (tn5m * 1e-3) / 1e9, 1),
+                                                 "median_us": round(tn5m * 1e3, 1), "alg_bytes": normal_bytes},
+                          "cg_sense_30it": {"slices_per_s": round(B * world / (statistics.median(tc) * 1e-3), 1),
+                                            "nrmse": round(nrmse_cg, 5)},
+                          "modl_untrained_nrmse": round(nrmse_modl, 5),
+                          "data": "x^0 = A^H A x_gt (noiseless; the adjoint of measured radial samples is not built)"}
+        y_h, maps_h = AHy5.cpu().pin_memory(), maps5.cpu().pin_memory()
+        out_h = torch.empty(tr.xs[-1].shape, dtype=tr.xs[-1].dtype).pin_memory()
+        ins = [(AHy5, y_h), (maps5, maps_h)]
+        outs = [(out_h, tr.xs[-1])]
+        step_fn = step_nc
+        value_slices = B
     elif args.workload == "varnet_train":
         from paper_2202_14005_b300.varnet import VarNetTrainer, pack_params
         c4 = synth.CONFIGS[4]
@@ -408,6 +486,7 @@ def run_ours(args, rank, world, local_rank):
         "vn_Kbwd": kernel_report("vn_Kbwd", *prof["vn_Kbwd"], ("tensor", 2 * vn_flops), pk, clocks, args.workload),
         "vn_KT": kernel_report("vn_KT", *prof["vn_KT"], ("tensor", vn_flops), pk, clocks, args.workload),
         "vn_wgrad": kernel_report("vn_wgrad", *prof["vn_wgrad"], ("tensor", 2 * vn_flops), pk, clocks, args.workload),
+        "toeplitz": kernel_report("toeplitz", *prof["toeplitz"], ("hbm", normal_bytes), pk, clocks, args.workload),
     }
     kern = {k: v for k, v in kern.items() if v}
     total_kernel_ms = {k: prof[k][0] for k in prof}
@@ -447,7 +526,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded ellipse phantoms, Gaussian coil maps, k-space from the forward operator)",
         "config": {"workload": WORKLOADS[args.workload], "slices_per_gpu": B, "coils": cfg.C, "H": cfg.H,
                    "W": cfg.W, "R": cfg.R, "cg_iters": cfg.cg_iters, "lambda": cfg.lam,
-                   "unrolled_blocks": cfg.extra.get("K") if args.workload == "modl_train" else None,
+                   "unrolled_blocks": cfg.extra.get("K") if args.workload in ("modl_train", "noncart_modl_infer") else None,
                    "stages": cfg.extra.get("T") if args.workload == "varnet_train" else None,
                    "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps"},
         "roofline": kern.get(dominant),
@@ -478,11 +557,24 @@ def _oracle_slice(args):
     from oracle import sense as osense
     from oracle import unrolled as ounr
     workload, s = args
-    cfg = synth.CONFIGS[{"cg_sense": 2, "modl_train": 3, "varnet_train": 4}[workload]]
+    cfg = synth.CONFIGS[{"cg_sense": 2, "modl_train": 3, "varnet_train": 4, "noncart_modl_infer": 5}[workload]]
     d = synth.make_slices(cfg, [s])
     maps = d["maps"].astype(np.complex64)
     mask = d["mask"]
     gt = d["x_gt"].astype(np.complex64)
+    if workload == "noncart_modl_infer":
+        # one MoDL block (CNN forward + 10 CG iterations with the Toeplitz normal operator), scaled by
+        # the K blocks; the PSF and x^0 = A^H A x_gt are setup, not timed
+        from oracle import nn as onn
+        from oracle import noncart as onc
+        traj = synth.radial_trajectory(cfg.extra["spokes"], cfg.extra["samples"], cfg.H).reshape(-1, 2)
+        psf = onc.toeplitz_psf(traj, cfg.H, cfg.W)
+        x0 = onc.toeplitz_normal(gt, maps, psf, 0.0)
+        ws, bs = synth.modl_cnn_weights(5000)
+        t1 = time.perf_counter()
+        z, _ = onn.modl_cnn_forward(x0, ws, bs)
+        ocg.cg(lambda p: onc.toeplitz_normal(p, maps, psf, cfg.lam), x0 + cfg.lam * z, None, cfg.cg_iters)
+        return cfg.extra["K"] * (time.perf_counter() - t1)
     y = (osense.forward(gt, maps, mask) + mask * d["noise"]).astype(np.complex64)
     t0 = time.perf_counter()
     rhs = osense.adjoint(y, maps, mask)
@@ -530,6 +622,12 @@ def cpu_baseline(workload):
                 "sample": f"{n} slices, A^H y + 10 CG iterations each (FP64 NumPy, one spawn process per "
                           f"slice); wall {wall:.1f} s"}
     est = max(per)  # slices run in parallel: the step takes as long as the slowest slice
+    if workload == "noncart_modl_infer":
+        return {"value": round(n / est, 6), "unit": "slices/s", "cores": used, "kind": "oracle",
+                "sample": f"{n} slices in parallel; per slice ONE MoDL block (CNN forward, 10 CG iterations with "
+                          f"the Toeplitz normal operator, 12 coils, 512x512 embedding) timed and scaled by the "
+                          f"10 blocks (FP64 NumPy, one spawn process per slice; PSF and x^0 precomputed); "
+                          f"slowest slice {est:.1f} s per step"}
     if workload == "varnet_train":
         return {"value": round(n / est, 6), "unit": "slices/s", "cores": used, "kind": "oracle",
                 "sample": f"{n} slices in parallel; per slice A^H y plus ONE gradient stage forward and reverse "

@@ -77,6 +77,26 @@ int sense_plan_create(sense_plan* plan, int B, int C, int H, int W, const void* 
  * (SENSE_EUNSUPPORTED). */
 int sense_plan_create_sets(sense_plan* plan, int B, int S, int C, int H, int W, const void* maps,
                            const float* mask, int mask_is_lines, void* stream);
+/* Non-Cartesian SENSE (Sec. 2.3.3): the normal operator A^H A is applied as a
+ * convolution with the point spread function of the sampling pattern (the
+ * Toeplitz embedding on the 2H x 2W grid); A^H y is precomputed by the caller,
+ * as in the paper.  psf: device complex64 [2H][2W] as sense_toeplitz_psf
+ * writes it; the plan transforms it once at creation (asynchronously on
+ * stream) and keeps its own copy.  Such a plan supports sense_normal,
+ * cg_dc_solve(_backward), the unrolled blocks and varnet_stage (images
+ * [B][H][W]); sense_forward and sense_adjoint return SENSE_EUNSUPPORTED.
+ * The workspace holds [B][C][H][2W] coil rows. */
+int sense_plan_create_toeplitz(sense_plan* plan, int B, int C, int H, int W, const void* maps,
+                               const void* psf, void* stream);
+/* PSF of a non-Cartesian trajectory on the 2H x 2W embedding grid (direct sum
+ * over the M samples: FP32 phasors, FP64 accumulation):
+ *   psf[iy][ix] = (H W)^{-1} sum_m exp(2 pi i (ky_m dy / H + kx_m dx / W)),
+ *   dy = iy (iy < H) or iy - 2H, dx likewise; zero on row H and column W.
+ * traj: device float32 [M][2] = (ky, kx) in grid units (the Cartesian grid is
+ * the integer lattice, k in [-H/2, H/2) x [-W/2, W/2)); image coordinates are
+ * centred (index - H/2, index - W/2), so on-grid samples give the centred
+ * unitary DFT of sense_forward.  psf: device complex64 [2H][2W]. */
+int sense_toeplitz_psf(const float* traj, int M, int H, int W, void* psf, void* stream);
 int sense_plan_destroy(sense_plan plan);
 /* Change the stream later calls launch on. */
 int sense_plan_set_stream(sense_plan plan, void* stream);

@@ -31,6 +31,8 @@ _dp = C.c_void_p  # device double* passed as an address
 SIGNATURES = {
     "sense_plan_create": (_i, [C.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _i, _vp]),
     "sense_plan_create_sets": (_i, [C.POINTER(_vp), _i, _i, _i, _i, _i, _vp, _vp, _i, _vp]),
+    "sense_plan_create_toeplitz": (_i, [C.POINTER(_vp), _i, _i, _i, _i, _vp, _vp, _vp]),
+    "sense_toeplitz_psf": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "sense_plan_destroy": (_i, [_vp]),
     "sense_plan_set_stream": (_i, [_vp, _vp]),
     "sense_plan_workspace_bytes": (_i, [_vp, C.POINTER(C.c_size_t)]),

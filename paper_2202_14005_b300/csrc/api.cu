@@ -21,7 +21,7 @@ WsLayout ws_layout(const sense_plan p) {
   const size_t plane = (size_t)p->B * p->H * p->W * sizeof(float2);
   const size_t img = plane * p->S;  // images [B][S][H][W]
   size_t o = 0;
-  L.T = o; o += up256(plane * p->C);
+  L.T = o; o += up256(plane * p->C * (p->toep ? 2 : 1));  // Toeplitz plans: rows of length 2W
   L.r = o; o += up256(img);
   L.p = o; o += up256(img);
   L.q = o; o += up256(img);
@@ -143,6 +143,58 @@ int sense_plan_create_sets(sense_plan* out, int B, int S, int C, int H, int W, c
   return SENSE_OK;
 }
 
+int sense_plan_create_toeplitz(sense_plan* out, int B, int C, int H, int W, const void* maps, const void* psf,
+                               void* stream) {
+  if (!out) return SENSE_EINVAL_PTR;
+  *out = nullptr;
+  if (B <= 0 || C <= 0 || H <= 0 || W <= 0 || (H & 1) || (W & 1)) return SENSE_EINVAL_SHAPE;
+  if ((long long)B * C * H * W > (1ll << 33)) return SENSE_EUNSUPPORTED;
+  if (!maps || !psf || !aligned16(maps) || !aligned16(psf)) return SENSE_EINVAL_PTR;
+  std::vector<float2> twH, twW, twH2, twW2;
+  Fft1D fH, fW, fH2, fW2;
+  if (int e = build_fft1d(fH, H, twH)) return e;
+  if (int e = build_fft1d(fW, W, twW)) return e;
+  if (int e = build_fft1d(fH2, 2 * H, twH2)) return e;
+  if (int e = build_fft1d(fW2, 2 * W, twW2)) return e;
+  sense_plan p = new (std::nothrow) sense_plan_s();
+  if (!p) return SENSE_ECUDA;
+  p->B = B; p->C = C; p->H = H; p->W = W; p->S = 1;
+  p->toep = 1;
+  p->maps = static_cast<const float2*>(maps);
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->fH = fH; p->fW = fW; p->fH2 = fH2; p->fW2 = fW2;
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    delete p;
+    return SENSE_ECUDA;
+  }
+  // plan-owned device block: status word | twH2 | twW2 | psf_hat [2H][2W]
+  const size_t o_tH = 256, o_tW = o_tH + up256(2 * H * sizeof(float2)),
+               o_p = o_tW + up256(2 * W * sizeof(float2)), tot = o_p + up256((size_t)4 * H * W * sizeof(float2));
+  char* d = nullptr;
+  if (cudaMalloc(&d, tot) != cudaSuccess) {
+    delete p;
+    return SENSE_ECUDA;
+  }
+  p->own = d;
+  p->status = reinterpret_cast<int*>(d);
+  p->fH2.tw = reinterpret_cast<float2*>(d + o_tH);
+  p->fW2.tw = reinterpret_cast<float2*>(d + o_tW);
+  p->psf_hat = reinterpret_cast<float2*>(d + o_p);
+  if (cudaMemset(d, 0, 256) != cudaSuccess ||
+      cudaMemcpy(p->fH2.tw, twH2.data(), 2 * H * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->fW2.tw, twW2.data(), 2 * W * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    sense_plan_destroy(p);
+    return SENSE_ECUDA;
+  }
+  if (int e = toeplitz_prepare(p, static_cast<const float2*>(psf))) {
+    sense_plan_destroy(p);
+    return e;
+  }
+  *out = p;
+  return SENSE_OK;
+}
+
 int sense_plan_destroy(sense_plan p) {
   if (!p) return SENSE_EINVAL_PTR;
   free_lines_tables(p);
@@ -188,11 +240,13 @@ int sense_plan_set_workspace(sense_plan p, void* ws, size_t bytes) {
 
 int sense_forward(sense_plan p, const void* x, void* y) {
   if (!p || !x || !y || !aligned16(x) || !aligned16(y) || x == y) return SENSE_EINVAL_PTR;
+  if (p->toep) return SENSE_EUNSUPPORTED;  // non-Cartesian plans hold the normal operator only
   return launch_forward_generic(p, static_cast<const float2*>(x), static_cast<float2*>(y));
 }
 
 int sense_adjoint(sense_plan p, const void* y, void* x) {
   if (!p || !x || !y || !aligned16(x) || !aligned16(y) || x == y) return SENSE_EINVAL_PTR;
+  if (p->toep) return SENSE_EUNSUPPORTED;
   if (int e = need_ws(p)) return e;
   return launch_adjoint_generic(p, static_cast<const float2*>(y), static_cast<float2*>(x));
 }

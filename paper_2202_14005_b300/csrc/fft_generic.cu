@@ -10,6 +10,7 @@
 // modulations cancel against each other (F^H diag(m) F is circulant), so that
 // path uses a plain DFT pair and the mask shifted to plain frequency order.
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "plan.cuh"
@@ -76,10 +77,15 @@ __device__ __forceinline__ void bfly(const float2* in, float2* out, int j, int N
   for (int r = 0; r < R; ++r) out[idxD + r * Ns] = v[r];
 }
 
-// Transform ntr contiguous sequences of length L held in a (ping-pong with b).
-// Returns the buffer holding the result.  All threads of the CTA take part.
-template <bool INV>
-__device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f) {
+// Transform ntr sequences of length L held in a at stride ld (>= L; ping-pong with b).  Column
+// passes use ld = L + 1: the transposing loads and stores of neighbouring columns then fall into
+// different shared-memory banks.  Returns the buffer holding the result.  All threads take part.
+// CLS selects the radices compiled into the stage loop: 0 = {2, 4, 8}, 1 = also {3, 5, 7},
+// 2 = every supported radix.  Large-prime butterflies hold R complex values in registers;
+// leaving them out of the smaller classes keeps power-of-two transforms at low register counts
+// (and several CTAs per SM).
+template <bool INV, int CLS>
+__device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, int ld) {
   const int L = f.L;
   int Ns = 1;
   for (int s = 0; s < f.nst; ++s) {
@@ -87,23 +93,33 @@ __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f) {
     const int nb = L / R;
     for (int w = threadIdx.x; w < ntr * nb; w += blockDim.x) {
       const int tr = w / nb, j = w - tr * nb;
-      const float2* in = a + tr * L;
-      float2* out = b + tr * L;
+      const float2* in = a + tr * ld;
+      float2* out = b + tr * ld;
       switch (R) {
         case 2: bfly<2, INV>(in, out, j, Ns, L, f.tw); break;
-        case 3: bfly<3, INV>(in, out, j, Ns, L, f.tw); break;
         case 4: bfly<4, INV>(in, out, j, Ns, L, f.tw); break;
-        case 5: bfly<5, INV>(in, out, j, Ns, L, f.tw); break;
-        case 7: bfly<7, INV>(in, out, j, Ns, L, f.tw); break;
         case 8: bfly<8, INV>(in, out, j, Ns, L, f.tw); break;
-        case 11: bfly<11, INV>(in, out, j, Ns, L, f.tw); break;
-        case 13: bfly<13, INV>(in, out, j, Ns, L, f.tw); break;
-        case 17: bfly<17, INV>(in, out, j, Ns, L, f.tw); break;
-        case 19: bfly<19, INV>(in, out, j, Ns, L, f.tw); break;
-        case 23: bfly<23, INV>(in, out, j, Ns, L, f.tw); break;
-        case 29: bfly<29, INV>(in, out, j, Ns, L, f.tw); break;
-        case 31: bfly<31, INV>(in, out, j, Ns, L, f.tw); break;
-        default: break;
+        default:
+          if constexpr (CLS >= 1) {
+            switch (R) {
+              case 3: bfly<3, INV>(in, out, j, Ns, L, f.tw); break;
+              case 5: bfly<5, INV>(in, out, j, Ns, L, f.tw); break;
+              case 7: bfly<7, INV>(in, out, j, Ns, L, f.tw); break;
+              default:
+                if constexpr (CLS >= 2) {
+                  switch (R) {
+                    case 11: bfly<11, INV>(in, out, j, Ns, L, f.tw); break;
+                    case 13: bfly<13, INV>(in, out, j, Ns, L, f.tw); break;
+                    case 17: bfly<17, INV>(in, out, j, Ns, L, f.tw); break;
+                    case 19: bfly<19, INV>(in, out, j, Ns, L, f.tw); break;
+                    case 23: bfly<23, INV>(in, out, j, Ns, L, f.tw); break;
+                    case 29: bfly<29, INV>(in, out, j, Ns, L, f.tw); break;
+                    case 31: bfly<31, INV>(in, out, j, Ns, L, f.tw); break;
+                    default: break;
+                  }
+                }
+            }
+          }
       }
     }
     __syncthreads();
@@ -118,7 +134,8 @@ __device__ __forceinline__ float pm1(int n) { return (n & 1) ? -1.f : 1.f; }
 // Row pass, expanding by the coil maps:  T[b,c,h,:] = DFT_W(S_c x) with
 //   mode 0 (forward): input (-1)^{h+w} S x, output (-1)^{kw} (-1)^{W/2} / sqrt(W)
 //   mode 1 (normal):  plain DFT, no modulation, no scale.
-__global__ void __launch_bounds__(kThreads) k_row_expand(int B, int S, int C, int H, const float2* x,
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_expand(int B, int S, int C, int H, const float2* x,
                                                          const float2* maps, float2* T,
                                                          Fft1DDev f, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -138,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_row_expand(int B, int S, int C, in
     a[i] = v;
   }
   __syncthreads();
-  float2* res = fft_smem<false>(a, bb, nr, f);
+  float2* res = fft_smem<false, CLS>(a, bb, nr, f, W);
   const float sc = (mode == 0) ? pm1(W / 2) * rsqrtf((float)W) : 1.f;
   for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
     const int r = i / W, k = i - r * W;
@@ -153,13 +170,14 @@ __global__ void __launch_bounds__(kThreads) k_row_expand(int B, int S, int C, in
 //   mode 1 (adjoint):  dst = (-1)^h (-1)^{H/2}/sqrt(H) IDFT_H((-1)^{kh} M src)
 //   mode 2 (normal):   dst = IDFT_H(m2s DFT_H(src))   (m2s: mask^2/(HW), plain order)
 // mask: modes 0/1 the centred mask ([W] if lines else [H][W]); mode 2 shifted mask^2.
-__global__ void __launch_bounds__(kThreads) k_col(int W, const float2* src, float2* dst,
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_col(int W, const float2* src, float2* dst,
                                                   Fft1DDev f, const float* mask, int lines,
                                                   int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int H = f.L;
+  const int H = f.L, ld = H + 1;
   float2* a = reinterpret_cast<float2*>(smem);
-  float2* bb = a + kCols * H;
+  float2* bb = a + kCols * ld;
   const int bc = blockIdx.y;
   const int w0 = blockIdx.x * kCols;
   const int nc = min(kCols, W - w0);
@@ -175,14 +193,14 @@ __global__ void __launch_bounds__(kThreads) k_col(int W, const float2* src, floa
         v = cscale(v, m * pm1(h));
       }
     }
-    a[cc * H + h] = v;
+    a[cc * ld + h] = v;
   }
   __syncthreads();
   float2* res;
   if (mode == 1) {
-    res = fft_smem<true>(a, bb, kCols, f);
+    res = fft_smem<true, CLS>(a, bb, kCols, f, ld);
   } else {
-    res = fft_smem<false>(a, bb, kCols, f);
+    res = fft_smem<false, CLS>(a, bb, kCols, f, ld);
     if (mode == 2) {
       float2* other = (res == a) ? bb : a;
       for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
@@ -190,17 +208,17 @@ __global__ void __launch_bounds__(kThreads) k_col(int W, const float2* src, floa
         const int w = w0 + cc;
         float m = 0.f;
         if (cc < nc) m = lines ? mask[w] : mask[(size_t)k * W + w];
-        res[i] = cscale(res[i], m);
+        res[cc * ld + k] = cscale(res[cc * ld + k], m);
       }
       __syncthreads();
-      res = fft_smem<true>(res, other, kCols, f);
+      res = fft_smem<true, CLS>(res, other, kCols, f, ld);
     }
   }
   const float sc = pm1(H / 2) * rsqrtf((float)H);
   for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
     const int h = i / kCols, cc = i - h * kCols;
     if (cc >= nc) continue;
-    float2 v = res[cc * H + h];
+    float2 v = res[cc * ld + h];
     const int w = w0 + cc;
     if (mode == 0) {
       const float m = lines ? mask[w] : mask[(size_t)h * W + w];
@@ -216,7 +234,8 @@ __global__ void __launch_bounds__(kThreads) k_col(int W, const float2* src, floa
 //   out[b,h,:] = sum_c conj(S_c) post(IDFT_W(pre(T[b,c,h,:]))) (+ lambda xin)
 //   mode 1 (adjoint): pre (-1)^{kw}, post (-1)^w (-1)^{W/2}/sqrt(W)
 //   mode 2 (normal):  no modulation, no scale (the scale sits in the mask table)
-__global__ void __launch_bounds__(kThreads) k_row_combine(int S, int C, int H, const float2* T,
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_combine(int S, int C, int H, const float2* T,
                                                           const float2* maps, float2* out,
                                                           Fft1DDev f, int mode,
                                                           const float2* xin, float lam_host,
@@ -240,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_row_combine(int S, int C, int H, c
       a[i] = v;
     }
     __syncthreads();
-    float2* res = fft_smem<true>(a, bb, nr, f);
+    float2* res = fft_smem<true, CLS>(a, bb, nr, f, W);
 #pragma unroll
     for (int e = 0; e < kMaxPer; ++e) {
       const int i = threadIdx.x + e * blockDim.x;
@@ -271,6 +290,219 @@ __global__ void __launch_bounds__(kThreads) k_row_combine(int S, int C, int H, c
   }
 }
 
+// ------------------------------------------------ Toeplitz embedding (non-Cartesian)
+// F^H P^H P F u = crop(IFFT2(psf_hat * FFT2(pad(u)))) on the 2H x 2W grid, with psf_hat holding
+// the 1 / (4 H W) of the inverse.  Rows H .. 2H - 1 of pad(u) are zero, so only H rows are
+// transformed along W, and the column pass keeps only rows 0 .. H - 1 of its result.
+//   k_tp_rows_fwd:  T[b,c,h,:] = FFT_2W(S_c x [b,h,0..W-1], zero-padded)          h < H
+//   k_tp_cols:      T[:,kw] (rows < H) = rows < H of IFFT_2H(psf_hat[:,kw] FFT_2H(T[:,kw] padded))
+//   k_tp_rows_inv:  out[b,h,:] = sum_c conj(S_c) IFFT_2W(T[b,c,h,:])[0..W-1] + lambda x
+// T is [B][C][H][2W].
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_rows_fwd(int C, int H, int W, const float2* x,
+                                                          const float2* maps, float2* T, Fft1DDev f) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W2 = f.L;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kRows * W2;
+  const int bc = blockIdx.y, b = bc / C;
+  const int h0 = blockIdx.x * kRows;
+  const int nr = min(kRows, H - h0);
+  for (int i = threadIdx.x; i < nr * W2; i += blockDim.x) {
+    const int r = i / W2, w = i - r * W2, h = h0 + r;
+    float2 v = make_float2(0.f, 0.f);
+    if (w < W) v = cmul(maps[((size_t)bc * H + h) * W + w], x[((size_t)b * H + h) * W + w]);
+    a[i] = v;
+  }
+  __syncthreads();
+  float2* res = fft_smem<false, CLS>(a, bb, nr, f, W2);
+  for (int i = threadIdx.x; i < nr * W2; i += blockDim.x)
+    T[((size_t)bc * H + h0) * W2 + i] = res[i];
+}
+
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_cols(int H, int W2, float2* T, Fft1DDev f,
+                                                      const float2* psf_hat) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H2 = f.L, ld = H2 + 1;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kCols * ld;
+  const int bc = blockIdx.y;
+  const int w0 = blockIdx.x * kCols;
+  const int nc = min(kCols, W2 - w0);
+  const size_t base = (size_t)bc * H * W2;
+  for (int i = threadIdx.x; i < H2 * kCols; i += blockDim.x) {
+    const int h = i / kCols, cc = i - h * kCols;
+    float2 v = make_float2(0.f, 0.f);
+    if (cc < nc && h < H) v = T[base + (size_t)h * W2 + w0 + cc];
+    a[cc * ld + h] = v;
+  }
+  __syncthreads();
+  float2* res = fft_smem<false, CLS>(a, bb, kCols, f, ld);
+  float2* other = (res == a) ? bb : a;
+  for (int i = threadIdx.x; i < H2 * kCols; i += blockDim.x) {
+    const int h = i / kCols, cc = i - h * kCols;  // psf_hat read along its rows
+    const float2 ph = cc < nc ? psf_hat[(size_t)h * W2 + w0 + cc] : make_float2(0.f, 0.f);
+    res[cc * ld + h] = cmul(res[cc * ld + h], ph);
+  }
+  __syncthreads();
+  res = fft_smem<true, CLS>(res, other, kCols, f, ld);
+  for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
+    const int h = i / kCols, cc = i - h * kCols;
+    if (cc < nc) T[base + (size_t)h * W2 + w0 + cc] = res[cc * ld + h];
+  }
+}
+
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_rows_inv(int C, int H, int W, const float2* T,
+                                                          const float2* maps, float2* out, Fft1DDev f,
+                                                          const float2* xin, float lam_host,
+                                                          const double* lam_dev) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W2 = f.L;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kRows * W2;
+  const int b = blockIdx.y;
+  const int h0 = blockIdx.x * kRows;
+  const int nr = min(kRows, H - h0);
+  float2 acc[kMaxPer];
+#pragma unroll
+  for (int e = 0; e < kMaxPer; ++e) acc[e] = make_float2(0.f, 0.f);
+  for (int c = 0; c < C; ++c) {
+    for (int i = threadIdx.x; i < nr * W2; i += blockDim.x)
+      a[i] = T[(((size_t)b * C + c) * H + h0) * W2 + i];
+    __syncthreads();
+    float2* res = fft_smem<true, CLS>(a, bb, nr, f, W2);
+#pragma unroll
+    for (int e = 0; e < kMaxPer; ++e) {
+      const int i = threadIdx.x + e * blockDim.x;  // output element (row r, column w < W)
+      if (i < nr * W) {
+        const int r = i / W, w = i - r * W;
+        const float2 sm = maps[(((size_t)b * C + c) * H + h0 + r) * W + w];
+        acc[e] = cfmac(sm, res[r * W2 + w], acc[e]);
+      }
+    }
+    __syncthreads();
+  }
+  const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
+#pragma unroll
+  for (int e = 0; e < kMaxPer; ++e) {
+    const int i = threadIdx.x + e * blockDim.x;
+    if (i < nr * W) {
+      const size_t o = ((size_t)b * H + h0) * W + i;
+      const float2 xv = xin[o];
+      out[o] = make_float2(fmaf(lam, xv.x, acc[e].x), fmaf(lam, xv.y, acc[e].y));
+    }
+  }
+}
+
+// psf_hat = FFT2(psf) / (4 H W): rows along 2W, then columns along 2H (in place, one array).
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_psf_rows(int H2, const float2* psf, float2* out, Fft1DDev f) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W2 = f.L;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kRows * W2;
+  const int h0 = blockIdx.x * kRows;
+  const int nr = min(kRows, H2 - h0);
+  for (int i = threadIdx.x; i < nr * W2; i += blockDim.x) a[i] = psf[(size_t)h0 * W2 + i];
+  __syncthreads();
+  float2* res = fft_smem<false, CLS>(a, bb, nr, f, W2);
+  for (int i = threadIdx.x; i < nr * W2; i += blockDim.x) out[(size_t)h0 * W2 + i] = res[i];
+}
+
+template <int CLS>
+__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_psf_cols(int W2, float2* io, Fft1DDev f, float scale) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int H2 = f.L, ld = H2 + 1;
+  float2* a = reinterpret_cast<float2*>(smem);
+  float2* bb = a + kCols * ld;
+  const int w0 = blockIdx.x * kCols;
+  const int nc = min(kCols, W2 - w0);
+  for (int i = threadIdx.x; i < H2 * kCols; i += blockDim.x) {
+    const int h = i / kCols, cc = i - h * kCols;
+    a[cc * ld + h] = cc < nc ? io[(size_t)h * W2 + w0 + cc] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2* res = fft_smem<false, CLS>(a, bb, kCols, f, ld);
+  for (int i = threadIdx.x; i < H2 * kCols; i += blockDim.x) {
+    const int h = i / kCols, cc = i - h * kCols;
+    if (cc < nc) io[(size_t)h * W2 + w0 + cc] = cscale(res[cc * ld + h], scale);
+  }
+}
+
+// PSF of a non-Cartesian trajectory on the 2H x 2W grid (direct sum; products of FP32 phasors,
+// FP64 accumulation):  psf[iy][ix] = (H W)^{-1} sum_m exp(2 pi i (ky_m dy / H + kx_m dx / W)),
+// dy = iy (iy < H) or iy - 2H, likewise dx; zero on row H and column W.  One thread per grid point;
+// the CTA's 16 x 16 block stages chunks of the trajectory and their phasors in shared memory.
+constexpr int kPsfTile = 16, kPsfChunk = 64;
+__global__ void __launch_bounds__(256) k_tp_psf(int M, int H, int W, const float* traj, float2* psf) {
+  __shared__ float2 ey[kPsfChunk][kPsfTile], ex[kPsfChunk][kPsfTile];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int iy = blockIdx.y * kPsfTile + ty, ix = blockIdx.x * kPsfTile + tx;
+  const int iy0 = blockIdx.y * kPsfTile, ix0 = blockIdx.x * kPsfTile;
+  double re = 0.0, im = 0.0;
+  for (int m0 = 0; m0 < M; m0 += kPsfChunk) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPsfChunk * kPsfTile; i += blockDim.x) {
+      const int mm = i / kPsfTile, j = i - mm * kPsfTile, m = m0 + mm;
+      float2 vy = make_float2(0.f, 0.f), vx = vy;
+      if (m < M) {
+        const int gy = iy0 + j, gx = ix0 + j;
+        const double dy = gy < H ? gy : gy - 2 * H, dx = gx < W ? gx : gx - 2 * W;
+        // phase in turns, reduced to [0, 1) in FP64 before the FP32 sin/cos
+        double ty_ = (double)traj[2 * m] * dy / H, tx_ = (double)traj[2 * m + 1] * dx / W;
+        ty_ -= floor(ty_);
+        tx_ -= floor(tx_);
+        float sy, cy, sx, cx;
+        sincospif(2.f * (float)ty_, &sy, &cy);
+        sincospif(2.f * (float)tx_, &sx, &cx);
+        vy = make_float2(cy, sy);
+        vx = make_float2(cx, sx);
+      }
+      ey[mm][j] = vy;
+      ex[mm][j] = vx;
+    }
+    __syncthreads();
+    const int mmax = min(kPsfChunk, M - m0);
+    for (int mm = 0; mm < mmax; ++mm) {
+      const float2 p = cmul(ey[mm][ty], ex[mm][tx]);
+      re += (double)p.x;
+      im += (double)p.y;
+    }
+  }
+  if (iy < 2 * H && ix < 2 * W) {
+    const double sc = (iy == H || ix == W) ? 0.0 : 1.0 / ((double)H * W);
+    psf[(size_t)iy * 2 * W + ix] = make_float2((float)(re * sc), (float)(im * sc));
+  }
+}
+
+// Radix class of a 1-D plan (see fft_smem).
+int fft_class(const Fft1D& f) {
+  int cls = 0;
+  for (int i = 0; i < f.nst; ++i) {
+    const int r = f.radix[i];
+    if (r == 3 || r == 5 || r == 7) cls = cls < 1 ? 1 : cls;
+    else if (r != 2 && r != 4 && r != 8) cls = 2;
+  }
+  return cls;
+}
+
+#define SENSE_LAUNCH_CLS(cls, kernel, grid, smem_bytes, stream, ...)                       \
+  do {                                                                                      \
+    if ((cls) == 0) kernel<0><<<(grid), kThreads, (smem_bytes), (stream)>>>(__VA_ARGS__);   \
+    else if ((cls) == 1) kernel<1><<<(grid), kThreads, (smem_bytes), (stream)>>>(__VA_ARGS__); \
+    else kernel<2><<<(grid), kThreads, (smem_bytes), (stream)>>>(__VA_ARGS__);             \
+  } while (0)
+
+template <typename K>
+bool set_smem3(K k0, K k1, K k2, int bytes) {
+  return cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+#define SENSE_SET_SMEM(kernel, bytes) set_smem3(kernel<0>, kernel<1>, kernel<2>, (bytes))
+
 Fft1DDev dev(const Fft1D& f) {
   Fft1DDev d;
   d.L = f.L;
@@ -285,7 +517,7 @@ bool set_smem(const void* k, int bytes) {
 }
 
 int smem_rows(int W) { return 2 * kRows * W * (int)sizeof(float2); }
-int smem_cols(int H) { return 2 * kCols * H * (int)sizeof(float2); }
+int smem_cols(int H) { return 2 * kCols * (H + 1) * (int)sizeof(float2); }
 
 }  // namespace
 
@@ -313,8 +545,7 @@ int generic_prepare(sense_plan p) {
   if (kRows * p->W > kThreads * kMaxPer) return SENSE_EUNSUPPORTED;
   const int sr = smem_rows(p->W), sc = smem_cols(p->H);
   if (sr > 200 * 1024 || sc > 200 * 1024) return SENSE_EUNSUPPORTED;
-  if (!set_smem((const void*)k_row_expand, sr) || !set_smem((const void*)k_row_combine, sr) ||
-      !set_smem((const void*)k_col, sc))
+  if (!SENSE_SET_SMEM(k_row_expand, sr) || !SENSE_SET_SMEM(k_row_combine, sr) || !SENSE_SET_SMEM(k_col, sc))
     return SENSE_ECUDA;
   return SENSE_OK;
 }
@@ -322,13 +553,13 @@ int generic_prepare(sense_plan p) {
 int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->S, p->C, p->H, x, p->maps, y,
-                                                              dev(p->fW), 0);
+  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_expand, gr, smem_rows(p->W), p->stream, p->B, p->S, p->C, p->H, x,
+                   p->maps, y, dev(p->fW), 0);
   prof_mark("fft_generic", p->stream, true);
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, y, dev(p->fH), p->mask,
-                                                      p->mask_is_lines, 0);
+  SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, y, y, dev(p->fH), p->mask,
+                   p->mask_is_lines, 0);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
@@ -337,13 +568,13 @@ int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
 int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, y, p->w.T, dev(p->fH), p->mask,
-                                                      p->mask_is_lines, 1);
+  SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, y, p->w.T, dev(p->fH),
+                   p->mask, p->mask_is_lines, 1);
   prof_mark("fft_generic", p->stream, true);
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->S);
   prof_mark("fft_generic", p->stream, false);
-  k_row_combine<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->S, p->C, p->H, p->w.T, p->maps, x,
-                                                              dev(p->fW), 1, nullptr, 0.f, nullptr);
+  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_combine, gr, smem_rows(p->W), p->stream, p->S, p->C, p->H, p->w.T,
+                   p->maps, x, dev(p->fW), 1, nullptr, 0.f, nullptr);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
@@ -351,21 +582,64 @@ int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
 
 int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
                           const double* lam_dev) {
+  if (p->toep) return launch_normal_toeplitz(p, x, out, lam_host, lam_dev);
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  k_row_expand<<<gr, kThreads, smem_rows(p->W), p->stream>>>(p->B, p->S, p->C, p->H, x, p->maps,
-                                                              p->w.T, dev(p->fW), 1);
+  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_expand, gr, smem_rows(p->W), p->stream, p->B, p->S, p->C, p->H, x,
+                   p->maps, p->w.T, dev(p->fW), 1);
   prof_mark("fft_generic", p->stream, true);
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  k_col<<<gc, kThreads, smem_cols(p->H), p->stream>>>(p->W, p->w.T, p->w.T, dev(p->fH),
-                                                      p->mask2s, p->mask_is_lines, 2);
+  SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, p->w.T, p->w.T, dev(p->fH),
+                   p->mask2s, p->mask_is_lines, 2);
   prof_mark("fft_generic", p->stream, true);
   const dim3 gr2((p->H + kRows - 1) / kRows, p->B * p->S);
   prof_mark("fft_generic", p->stream, false);
-  k_row_combine<<<gr2, kThreads, smem_rows(p->W), p->stream>>>(
-      p->S, p->C, p->H, p->w.T, p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
+  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_combine, gr2, smem_rows(p->W), p->stream, p->S, p->C, p->H, p->w.T,
+                   p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 3);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int toeplitz_prepare(sense_plan p, const float2* psf) {
+  const int H2 = 2 * p->H, W2 = 2 * p->W;
+  if (kRows * W2 > kThreads * kMaxPer || kRows * p->W > kThreads * kMaxPer) return SENSE_EUNSUPPORTED;
+  const int sr = smem_rows(W2), sc = smem_cols(H2);
+  if (sr > 200 * 1024 || sc > 200 * 1024) return SENSE_EUNSUPPORTED;
+  if (!SENSE_SET_SMEM(k_tp_rows_fwd, sr) || !SENSE_SET_SMEM(k_tp_rows_inv, sr) ||
+      !SENSE_SET_SMEM(k_tp_psf_rows, sr) || !SENSE_SET_SMEM(k_tp_cols, sc) || !SENSE_SET_SMEM(k_tp_psf_cols, sc))
+    return SENSE_ECUDA;
+  SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_psf_rows, (H2 + kRows - 1) / kRows, sr, p->stream, H2, psf,
+                   p->psf_hat, dev(p->fW2));
+  SENSE_LAUNCH_CLS(fft_class(p->fH2), k_tp_psf_cols, (W2 + kCols - 1) / kCols, sc, p->stream, W2, p->psf_hat,
+                   dev(p->fH2), (float)(1.0 / ((double)H2 * W2)));
+  count_launch(p, 2);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam_host, const double* lam_dev) {
+  const int W2 = 2 * p->W;
+  const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
+  prof_mark("toeplitz", p->stream, false);
+  SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_fwd, gr, smem_rows(W2), p->stream, p->C, p->H, p->W, x, p->maps,
+                   p->w.T, dev(p->fW2));
+  const dim3 gc((W2 + kCols - 1) / kCols, p->B * p->C);
+  SENSE_LAUNCH_CLS(fft_class(p->fH2), k_tp_cols, gc, smem_cols(2 * p->H), p->stream, p->H, W2, p->w.T,
+                   dev(p->fH2), p->psf_hat);
+  const dim3 gr2((p->H + kRows - 1) / kRows, p->B);
+  SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows(W2), p->stream, p->C, p->H, p->W, p->w.T,
+                   p->maps, out, dev(p->fW2), x, lam_host, lam_dev);
+  prof_mark("toeplitz", p->stream, true);
+  count_launch(p, 3);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+extern "C" int sense_toeplitz_psf(const float* traj, int M, int H, int W, void* psf, void* stream) {
+  if (M <= 0 || H <= 0 || W <= 0 || (H & 1) || (W & 1)) return SENSE_EINVAL_SHAPE;
+  if (!traj || !psf || ((uintptr_t)traj & 7u) || ((uintptr_t)psf & 15u)) return SENSE_EINVAL_PTR;
+  const dim3 g((2 * W + kPsfTile - 1) / kPsfTile, (2 * H + kPsfTile - 1) / kPsfTile);
+  k_tp_psf<<<g, 256, 0, static_cast<cudaStream_t>(stream)>>>(M, H, W, traj, static_cast<float2*>(psf));
+  prof_count(1);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

@@ -58,6 +58,11 @@ struct sense_plan_s {
   float* mask2s = nullptr;      // device: mask^2/(H W), shifted to plain FFT order
   LinesTables lines;
   Fft1D fH, fW;
+  // non-Cartesian plans (Toeplitz embedding, Sec. 2.3.3): FFTs on the 2H x 2W grid and the
+  // transformed PSF, psf_hat = FFT2(PSF) / (4 H W), complex64 [2H][2W] (plan-owned)
+  int toep = 0;
+  Fft1D fH2, fW2;
+  float2* psf_hat = nullptr;
   int* status = nullptr;        // device status word (plan-owned)
   void* own = nullptr;          // plan-owned device allocation (tables + status)
   void* ws = nullptr;
@@ -99,6 +104,9 @@ int launch_forward_generic(sense_plan p, const float2* x, float2* y);
 int launch_adjoint_generic(sense_plan p, const float2* y, float2* x);
 int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
                           const double* lam_dev);
+int toeplitz_prepare(sense_plan p, const float2* psf);  // psf_hat from the PSF, kernel attributes
+int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam_host,
+                           const double* lam_dev);
 
 int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const double* lam,
            int lam_count, int iters, double* rr_hist);

@@ -23,8 +23,9 @@ def _p(t):
 
 class ModlTrainer:
     def __init__(self, maps: torch.Tensor, mask: torch.Tensor, weights: torch.Tensor, lam: float,
-                 K: int, cg_iters: int, lr: float = 1e-4, lam_lr: float = 1e-4):
-        self.plan = SensePlan(maps, mask)
+                 K: int, cg_iters: int, lr: float = 1e-4, lam_lr: float = 1e-4, plan: SensePlan | None = None):
+        # plan: an existing plan (e.g. a non-Cartesian Toeplitz plan, Sec. 2.3.3) instead of maps/mask
+        self.plan = plan if plan is not None else SensePlan(maps, mask)
         B, H, W = self.plan.img_shape()
         self.B, self.H, self.W = B, H, W
         self.K, self.iters = K, cg_iters
@@ -50,6 +51,14 @@ class ModlTrainer:
         """x^K for k-space y [B, C, H, W] (also keeps every x^t)."""
         self.plan._sync_stream()
         self.plan.adjoint(y, out=self.xs[0])
+        return self.forward_from_adjoint(None)
+
+    def forward_from_adjoint(self, AHy: torch.Tensor | None) -> torch.Tensor:
+        """x^K from a given x^0 = A^H y (the non-Cartesian case precomputes it, Sec. 2.3.3);
+        None: x^0 already in self.xs[0]."""
+        self.plan._sync_stream()
+        if AHy is not None:
+            self.xs[0].copy_(AHy)
         h, kind, w, lam = self._step_args()
         for t in range(self.K):
             _lib.check("unrolled_step", self._lib.unrolled_step(

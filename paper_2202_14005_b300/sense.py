@@ -64,6 +64,28 @@ class SensePlan:
         _lib.check("sense_plan_set_workspace",
                    self._lib.sense_plan_set_workspace(h, _ptr(self.workspace), nb.value))
 
+    @classmethod
+    def toeplitz(cls, maps: torch.Tensor, psf: torch.Tensor) -> "SensePlan":
+        """Non-Cartesian plan (Sec. 2.3.3): A^H A applied as the convolution with the PSF on the
+        2H x 2W grid (psf: complex64 [2H, 2W], e.g. from toeplitz_psf).  Normal operator and CG only."""
+        B, Cc, H, W = maps.shape
+        _req(maps, "maps", torch.complex64, (B, Cc, H, W))
+        _req(psf, "psf", torch.complex64, (2 * H, 2 * W))
+        self = cls.__new__(cls)
+        self.B, self.C, self.H, self.W, self.S = B, Cc, H, W, 0
+        self.maps, self.mask, self.lines, self.psf = maps, None, 0, psf
+        self._lib = _lib.lib()
+        h = C.c_void_p()
+        _lib.check("sense_plan_create_toeplitz", self._lib.sense_plan_create_toeplitz(
+            C.byref(h), B, Cc, H, W, _ptr(maps), _ptr(psf), _stream()))
+        self._h = h
+        nb = C.c_size_t()
+        _lib.check("sense_plan_workspace_bytes", self._lib.sense_plan_workspace_bytes(h, C.byref(nb)))
+        self.workspace = torch.empty(int(nb.value), dtype=torch.uint8, device=maps.device)
+        _lib.check("sense_plan_set_workspace",
+                   self._lib.sense_plan_set_workspace(h, _ptr(self.workspace), nb.value))
+        return self
+
     # -- helpers
     def _sync_stream(self):
         _lib.check("sense_plan_set_stream", self._lib.sense_plan_set_stream(self._h, _stream()))
@@ -147,3 +169,15 @@ class SensePlan:
         v = C.c_int()
         _lib.check("sense_get_status", self._lib.sense_get_status(self._h, C.byref(v)))
         return v.value
+
+
+def toeplitz_psf(traj: torch.Tensor, H: int, W: int) -> torch.Tensor:
+    """PSF of a non-Cartesian trajectory (float32 [M, 2] = (ky, kx) in grid units, on the GPU)
+    on the 2H x 2W embedding grid, complex64 [2H, 2W] (Sec. 2.3.3)."""
+    if traj.device.type != "cuda" or traj.dtype != torch.float32 or traj.dim() != 2 or traj.shape[1] != 2:
+        raise ValueError("traj must be a CUDA float32 [M, 2] tensor")
+    traj = traj.contiguous()
+    psf = torch.empty((2 * H, 2 * W), dtype=torch.complex64, device=traj.device)
+    _lib.check("sense_toeplitz_psf", _lib.lib().sense_toeplitz_psf(_ptr(traj), traj.shape[0], H, W, _ptr(psf),
+                                                                  _stream()))
+    return psf
