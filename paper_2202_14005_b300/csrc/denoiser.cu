@@ -204,6 +204,21 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
 
   for (int i = 0; i < n && !err; ++i) {
     const int buf = i & 1;
+    // queue the MMAs of tile i + 1 behind those of tile i as soon as its halo has landed (its
+    // tensor-memory half was freed by the epilogue of tile i - 1), so the tensor pipe never waits
+    // for an epilogue; then wait for tile i and refill its halo buffer with tile i + 2
+    if (tid == 0 && i + 1 < n) {
+      const int nb = buf ^ 1;
+      if (mbar_wait(&bars[1 + nb], ((i + 1) >> 1) & 1)) {
+        waited[1 + nb]++;
+        tc_fence_after();
+        issue_mma(tmem + nb * 64, sh[nb], sw);
+        umma_commit(&bars[3 + nb]);
+        issued[3 + nb]++;
+      } else {
+        my_err = 1;
+      }
+    }
     const bool done = mbar_wait(&bars[3 + buf], (i >> 1) & 1);
     if (tid == 0 && done) waited[3 + buf]++;
     if (__syncthreads_or(!done || my_err)) {
@@ -211,23 +226,10 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
       break;
     }
     tc_fence_after();
-    if (tid == 0) {
-      if (i + 2 < n) {
-        issue_halo(&tmap, s_halo0 + buf * HALO_BYTES, &bars[1 + buf], blockIdx.x + (i + 2) * gridDim.x,
-                   a.H, a.ntw);
-        issued[1 + buf]++;
-      }
-      if (i + 1 < n) {
-        const int nb = buf ^ 1;
-        if (mbar_wait(&bars[1 + nb], ((i + 1) >> 1) & 1)) {
-          waited[1 + nb]++;
-          issue_mma(tmem + nb * 64, sh[nb], sw);
-          umma_commit(&bars[3 + nb]);
-          issued[3 + nb]++;
-        } else {
-          my_err = 1;
-        }
-      }
+    if (tid == 0 && i + 2 < n) {
+      issue_halo(&tmap, s_halo0 + buf * HALO_BYTES, &bars[1 + buf], blockIdx.x + (i + 2) * gridDim.x,
+                 a.H, a.ntw);
+      issued[1 + buf]++;
     }
     __syncwarp();  // warp 0 reconverges before the warp-collective tensor-memory loads
     // epilogue of tile i: warp w owns pixels 32w .. 32w + 31 of the tile
@@ -236,6 +238,13 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
     const int px = wt * TILE_M + warp * 32 + lane;
     const bool valid = px < a.W;
     const size_t pix = ((size_t)b * a.H + h) * a.W + px;
+    // input-gradient mode: the whole 128-byte ReLU-mask row of this pixel in one batch of loads
+    uint4 mrow[8];
+    if (a.mode == 1 && valid) {
+      const uint4* ap = reinterpret_cast<const uint4*>(a.aprev + pix * CH);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) mrow[q] = ap[q];
+    }
 #pragma unroll
     for (int cb = 0; cb < 4; ++cb) {
       float v[16];
@@ -245,8 +254,7 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_bias[cb * 16 + e], 0.f);
         } else {
-          const uint4* ap = reinterpret_cast<const uint4*>(a.aprev + pix * CH + cb * 16);
-          const uint4 m0 = ap[0], m1 = ap[1];
+          const uint4 m0 = mrow[2 * cb], m1 = mrow[2 * cb + 1];
           const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
           const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
 #pragma unroll
