@@ -28,9 +28,9 @@ namespace {
 constexpr int CH = 64;
 constexpr int TILE_M = 128;
 constexpr int HALO_W = TILE_M + 2;            // 130
-constexpr int GBLK_TX = 3 * HALO_W * 16;      // 6240 bytes per channel-group box
-constexpr int GBLK = 6272;                    // padded to 128 bytes
-constexpr int HALO_BYTES = 8 * GBLK;          // 50176
+constexpr int HALO_ROWB = HALO_W * CH * 2;    // 16640 bytes: one halo row, 128 bytes per pixel
+constexpr int HALO_TX = 3 * HALO_ROWB;        // 49920 bytes per tile (one TMA box)
+constexpr int HALO_BYTES = 50176;             // padded to whole 1024-byte swizzle atoms
 constexpr int WPACK_BYTES = 9 * 8 * CH * 16;  // 73728 (bf16 [tap][g][n][8])
 constexpr int CONV_THREADS = 128;
 constexpr int OFF_W = 0;
@@ -124,9 +124,9 @@ __device__ __forceinline__ void issue_halo(const CUtensorMap* map, uint8_t* dst,
                                            int H, int ntw) {
   int b, h, wt;
   tile_coords(t, H, ntw, b, h, wt);
-  mbar_expect_tx(bar, 8 * GBLK_TX);
-#pragma unroll
-  for (int g = 0; g < 8; ++g) tma_load_4d(dst + g * GBLK, map, g * 8, wt * TILE_M - 1, h - 1, b, bar);
+  mbar_expect_tx(bar, HALO_TX);
+  // one box {64 channels, 130 pixels, 3 rows}: [row][pixel][128 bytes], 128-byte swizzled
+  tma_load_4d(dst, map, 0, wt * TILE_M - 1, h - 1, b, bar);
 }
 
 __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32_t wts) {
@@ -136,7 +136,8 @@ __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32
     const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-      const uint64_t ad = umma_desc(halo + (2 * kk) * GBLK + (dy * HALO_W + dx) * 16, GBLK, 128);
+      // A: 128 pixels starting at halo pixel (dy, dx), channels 16 kk .. 16 kk + 15
+      const uint64_t ad = umma_desc_sw128(halo + (dy * HALO_W + dx) * 128 + kk * 32);
       const uint64_t bd = umma_desc(wts + (tap * 8 + 2 * kk) * 1024, 1024, 128);
       umma_bf16(tmem_d, ad, bd, idesc, (tap | kk) != 0);
     }
@@ -779,10 +780,10 @@ int make_act_map(CUtensorMap* m, const void* base, int B, int H, int W) {
   if (!enc) return SENSE_ECUDA;
   const cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
   const cuuint64_t strides[3] = {(cuuint64_t)CH * 2, (cuuint64_t)W * CH * 2, (cuuint64_t)H * W * CH * 2};
-  const cuuint32_t box[4] = {8, HALO_W, 3, 1};
+  const cuuint32_t box[4] = {CH, HALO_W, 3, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
-                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SENSE_OK : SENSE_ECUDA;
 }

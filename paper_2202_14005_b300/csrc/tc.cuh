@@ -82,6 +82,20 @@ SENSE_D uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   d |= (uint64_t)1 << 46;
   return d;
 }
+// Shared-memory matrix descriptor for a K-major operand stored with the 128-byte swizzle (rows of
+// 128 bytes, 16-byte chunks XOR-permuted by the row index within each 1024-byte atom, as a TMA
+// copy with CU_TENSOR_MAP_SWIZZLE_128B writes them): stride byte offset 1024 between 8-row groups,
+// leading byte offset unused (16), layout type 2 (128-byte swizzle).  The swizzle phase follows the
+// address bits of each row, so a start address inside an atom (a pixel offset) needs no base offset.
+SENSE_D uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
 // Instruction descriptor of kind::f16 with BF16 A/B, FP32 D, both K-major.
 SENSE_HD uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
