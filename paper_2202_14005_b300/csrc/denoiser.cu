@@ -246,10 +246,11 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) mrow[q] = ap[q];
     }
+    float acc[64];
+    tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + buf * 64, acc);
 #pragma unroll
     for (int cb = 0; cb < 4; ++cb) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + buf * 64 + cb * 16, v);
+      float* v = acc + cb * 16;
       if (valid) {
         if (a.mode == 0) {
 #pragma unroll
