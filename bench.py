@@ -48,7 +48,7 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
 # conv64_tc a dgrad launch; vn_* one launch each of the 4-slice 320x368 VarNet step.
 NCU_TRAFFIC = {
     "cg_sense": {"normal_lines": 113.6e6},
-    "modl_train": {"normal_lines": 28.4e6, "conv64_tc": 65.0e6},
+    "modl_train": {"normal_lines": 28.4e6},
     "varnet_train": {"vn_K": 3.9e6, "vn_Kbwd": 103.4e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
 }
 # kernel groups the library times with CUDA events when profiling is on

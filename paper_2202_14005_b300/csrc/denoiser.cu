@@ -32,13 +32,14 @@ constexpr int HALO_ROWB = HALO_W * CH * 2;    // 16640 bytes: one halo row, 128 
 constexpr int HALO_TX = 3 * HALO_ROWB;        // 49920 bytes per tile (one TMA box)
 constexpr int HALO_BYTES = 50176;             // padded to whole 1024-byte swizzle atoms
 constexpr int WPACK_BYTES = 9 * 8 * CH * 16;  // 73728 (bf16 [tap][g][n][8])
-constexpr int CONV_THREADS = 128;
+constexpr int CONV_THREADS = 160;             // warps 0-3 epilogue (one TMEM lane quadrant each), warp 4 producer
+constexpr int NHALO = 3;                      // halo slots (TMA runs two tiles ahead of the MMAs)
 constexpr int OFF_W = 0;
 constexpr int OFF_H0 = WPACK_BYTES;
-constexpr int OFF_H1 = OFF_H0 + HALO_BYTES;
-constexpr int OFF_BIAS = OFF_H1 + HALO_BYTES;
+constexpr int OFF_BIAS = OFF_H0 + NHALO * HALO_BYTES;
 constexpr int OFF_BAR = OFF_BIAS + CH * 4;
-constexpr int CONV_SMEM = OFF_BAR + 64 + 1024;  // + slack to realign the base to 1 KB
+constexpr int NBARS = 1 + 2 * NHALO + 2 + 2;  // weights, halo full/empty, TMEM full/empty
+constexpr int CONV_SMEM = OFF_BAR + NBARS * 8 + 16 + 1024;  // + slack to realign the base to 1 KB
 
 // Offsets (floats) into the flat MoDL weight vector: w_l [Cout][Cin][3][3], b_l [Cout].
 struct ModlOffsets {
@@ -144,21 +145,47 @@ __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32
   }
 }
 
+// Warp-specialised persistent kernel.  Warp 4 (one lane) is the producer: it streams tile halos
+// into NHALO shared slots with TMA and issues each tile's 36 MMAs into one of two TMEM halves as
+// soon as the halo has landed and the epilogue has drained that half.  Warps 0-3 run the epilogue
+// of every tile (warp w reads TMEM lanes 32w..32w+31: pixels 32w..32w+31).  Hand-offs go through
+// mbarriers only:
+//   halo_full[s]  TMA of slot s landed            (expect-tx, producer waits)
+//   halo_empty[s] MMAs reading slot s finished    (tcgen05.commit, producer waits before reuse)
+//   tm_full[t]    MMAs into TMEM half t finished  (tcgen05.commit, epilogue waits)
+//   tm_empty[t]   four epilogue warps drained t   (count 4, producer waits before reuse)
+// Tile j uses slot j % NHALO (use index j / NHALO) and TMEM half j % 2 (use index j / 2); the
+// parity waited for is that use index's low bit.  Every wait is bounded: a role that gives up
+// records an error, and the CTA waits (bounded) for whatever it still has in flight, frees its
+// tensor memory and returns with SENSE_STATUS_DEVICE_TIMEOUT set.
 __global__ void __launch_bounds__(CONV_THREADS, 1)
 k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  uint8_t* s_halo0 = smem + OFF_H0;
+  uint8_t* s_halo = smem + OFF_H0;
   float* s_bias = reinterpret_cast<float*>(smem + OFF_BIAS);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);  // 0 weights, 1-2 loads, 3-4 mma
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 5);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+  uint64_t* w_full = bars;
+  uint64_t* halo_full = bars + 1;
+  uint64_t* halo_empty = bars + 1 + NHALO;
+  uint64_t* tm_full = bars + 1 + 2 * NHALO;
+  uint64_t* tm_empty = bars + 3 + 2 * NHALO;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + NBARS);
   int* s_err = reinterpret_cast<int*>(s_tmem + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = a.B * a.H * a.ntw;
   const int n = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
+    mbar_init(w_full, 1);
+    for (int k = 0; k < NHALO; ++k) {
+      mbar_init(&halo_full[k], 1);
+      mbar_init(&halo_empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&tm_full[k], 1);
+      mbar_init(&tm_empty[k], 4);
+    }
     *s_err = 0;
     fence_mbar_init();
   }
@@ -171,129 +198,114 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const uint32_t sw = smem_u32(smem + OFF_W);
-  const uint32_t sh[2] = {smem_u32(s_halo0), smem_u32(s_halo0 + HALO_BYTES)};
 
-  // thread 0 issues every copy and MMA batch and counts them per barrier, so an
-  // error exit can wait (bounded) for exactly what is still in flight.
-  int issued[5] = {0, 0, 0, 0, 0}, waited[5] = {0, 0, 0, 0, 0};
-  int my_err = 0;
-  if (tid == 0 && n > 0) {
-    mbar_expect_tx(&bars[0], WPACK_BYTES);
-    bulk_load(smem + OFF_W, a.wpack, WPACK_BYTES, &bars[0]);
-    issued[0]++;
-    issue_halo(&tmap, s_halo0, &bars[1], blockIdx.x, a.H, a.ntw);
-    issued[1]++;
-    if (n > 1) {
-      issue_halo(&tmap, s_halo0 + HALO_BYTES, &bars[2], blockIdx.x + gridDim.x, a.H, a.ntw);
-      issued[2]++;
-    }
-    const bool okw = mbar_wait(&bars[0], 0);
-    if (okw) waited[0]++;
-    const bool okl = okw && mbar_wait(&bars[1], 0);
-    if (okl) {
-      waited[1]++;
-      tc_fence_after();
-      issue_mma(tmem, sh[0], sw);
-      umma_commit(&bars[3]);
-      issued[3]++;
-    } else {
-      my_err = 1;
-    }
-  }
-  int err = __syncthreads_or(my_err);
-
-  for (int i = 0; i < n && !err; ++i) {
-    const int buf = i & 1;
-    // queue the MMAs of tile i + 1 behind those of tile i as soon as its halo has landed (its
-    // tensor-memory half was freed by the epilogue of tile i - 1), so the tensor pipe never waits
-    // for an epilogue; then wait for tile i and refill its halo buffer with tile i + 2
-    if (tid == 0 && i + 1 < n) {
-      const int nb = buf ^ 1;
-      if (mbar_wait(&bars[1 + nb], ((i + 1) >> 1) & 1)) {
-        waited[1 + nb]++;
+  // producer bookkeeping (lane 0 of warp 4): what it issued and what it has seen complete
+  int tma_issued = 0, mma_issued = 0;
+  if (warp == 4) {
+    if (lane == 0 && n > 0) {
+      const uint32_t sw = smem_u32(smem + OFF_W);
+      bool ok = true;
+      mbar_expect_tx(w_full, WPACK_BYTES);
+      bulk_load(smem + OFF_W, a.wpack, WPACK_BYTES, w_full);
+      const int pre = n < 2 ? n : 2;
+      for (int j = 0; j < pre; ++j) {
+        issue_halo(&tmap, s_halo + j * HALO_BYTES, &halo_full[j], blockIdx.x + j * gridDim.x, a.H, a.ntw);
+        ++tma_issued;
+      }
+      ok = mbar_wait(w_full, 0);
+      for (int i = 0; i < n && ok; ++i) {
+        const int s = i % NHALO, t = i & 1;
+        ok = mbar_wait(&halo_full[s], (i / NHALO) & 1);
+        if (ok && i >= 2) ok = mbar_wait(&tm_empty[t], ((i - 2) >> 1) & 1);
+        if (!ok) break;
         tc_fence_after();
-        issue_mma(tmem + nb * 64, sh[nb], sw);
-        umma_commit(&bars[3 + nb]);
-        issued[3 + nb]++;
-      } else {
-        my_err = 1;
+        issue_mma(tmem + t * 64, smem_u32(s_halo + s * HALO_BYTES), sw);
+        umma_commit(&tm_full[t]);
+        umma_commit(&halo_empty[s]);
+        ++mma_issued;
+        // refill the slot of tile i - 1 with tile i + 2 once the MMAs of tile i - 1 are done
+        if (i + 2 < n) {
+          const int s2 = (i + 2) % NHALO;
+          if (i >= 1) ok = mbar_wait(&halo_empty[s2], ((i - 1) / NHALO) & 1);
+          if (!ok) break;
+          issue_halo(&tmap, s_halo + s2 * HALO_BYTES, &halo_full[s2], blockIdx.x + (i + 2) * gridDim.x, a.H,
+                     a.ntw);
+          ++tma_issued;
+        }
       }
+      if (!ok) atomicExch(s_err, 1);
     }
-    const bool done = mbar_wait(&bars[3 + buf], (i >> 1) & 1);
-    if (tid == 0 && done) waited[3 + buf]++;
-    if (__syncthreads_or(!done || my_err)) {
-      err = 1;
-      break;
-    }
-    tc_fence_after();
-    if (tid == 0 && i + 2 < n) {
-      issue_halo(&tmap, s_halo0 + buf * HALO_BYTES, &bars[1 + buf], blockIdx.x + (i + 2) * gridDim.x,
-                 a.H, a.ntw);
-      issued[1 + buf]++;
-    }
-    __syncwarp();  // warp 0 reconverges before the warp-collective tensor-memory loads
-    // epilogue of tile i: warp w owns pixels 32w .. 32w + 31 of the tile
-    int b, h, wt;
-    tile_coords(blockIdx.x + i * gridDim.x, a.H, a.ntw, b, h, wt);
-    const int px = wt * TILE_M + warp * 32 + lane;
-    const bool valid = px < a.W;
-    const size_t pix = ((size_t)b * a.H + h) * a.W + px;
-    // input-gradient mode: the whole 128-byte ReLU-mask row of this pixel in one batch of loads
-    uint4 mrow[8];
-    if (a.mode == 1 && valid) {
-      const uint4* ap = reinterpret_cast<const uint4*>(a.aprev + pix * CH);
+  } else {
+    // epilogue: warp w owns pixels 32w .. 32w + 31 of each tile
+    for (int i = 0; i < n; ++i) {
+      const int t = i & 1;
+      if (!mbar_wait(&tm_full[t], (i >> 1) & 1)) {
+        atomicExch(s_err, 1);
+        break;
+      }
+      tc_fence_after();
+      int b, h, wt;
+      tile_coords(blockIdx.x + i * gridDim.x, a.H, a.ntw, b, h, wt);
+      const int px = wt * TILE_M + warp * 32 + lane;
+      const bool valid = px < a.W;
+      const size_t pix = ((size_t)b * a.H + h) * a.W + px;
+      // input-gradient mode: the whole 128-byte ReLU-mask row of this pixel in one batch of loads
+      uint4 mrow[8];
+      if (a.mode == 1 && valid) {
+        const uint4* ap = reinterpret_cast<const uint4*>(a.aprev + pix * CH);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) mrow[q] = ap[q];
-    }
-    float acc[64];
-    tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + buf * 64, acc);
-#pragma unroll
-    for (int cb = 0; cb < 4; ++cb) {
-      float* v = acc + cb * 16;
+        for (int q = 0; q < 8; ++q) mrow[q] = ap[q];
+      }
+      float acc[64];
+      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + t * 64, acc);
+      // the accumulators are in registers: hand the TMEM half back to the producer
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tm_empty[t]);
       if (valid) {
-        if (a.mode == 0) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_bias[cb * 16 + e], 0.f);
-        } else {
-          const uint4 m0 = mrow[2 * cb], m1 = mrow[2 * cb + 1];
-          const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
-          const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+        for (int cb = 0; cb < 4; ++cb) {
+          float* v = acc + cb * 16;
+          if (a.mode == 0) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            if (!(bf(mb0[e]) > 0.f)) v[e] = 0.f;
-            if (!(bf(mb1[e]) > 0.f)) v[8 + e] = 0.f;
+            for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_bias[cb * 16 + e], 0.f);
+          } else {
+            const uint4 m0 = mrow[2 * cb], m1 = mrow[2 * cb + 1];
+            const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+            const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              if (!(bf(mb0[e]) > 0.f)) v[e] = 0.f;
+              if (!(bf(mb1[e]) > 0.f)) v[8 + e] = 0.f;
+            }
           }
-        }
-        uint4 o0, o1;
-        __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(&o0);
-        __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(&o1);
+          uint4 o0, o1;
+          __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(&o0);
+          __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(&o1);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          p0[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-          p1[e] = __floats2bfloat162_rn(v[8 + 2 * e], v[8 + 2 * e + 1]);
+          for (int e = 0; e < 4; ++e) {
+            p0[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+            p1[e] = __floats2bfloat162_rn(v[8 + 2 * e], v[8 + 2 * e + 1]);
+          }
+          uint4* op = reinterpret_cast<uint4*>(a.out + pix * CH + cb * 16);
+          op[0] = o0;
+          op[1] = o1;
         }
-        uint4* op = reinterpret_cast<uint4*>(a.out + pix * CH + cb * 16);
-        op[0] = o0;
-        op[1] = o1;
       }
-    }
-    tc_fence_before();
-    if (__syncthreads_or(my_err)) {
-      err = 1;
-      break;
     }
   }
-  err = __syncthreads_or(err || my_err);
-  if (err && tid == 0) {
+  tc_fence_before();
+  __syncthreads();
+  if (*s_err && tid == 4 * 32) {
     set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
-    // wait (bounded) for whatever this CTA still has in flight before its
-    // shared and tensor memory are released
-    for (int k = 0; k < 5; ++k)
-      while (waited[k] < issued[k]) {
-        mbar_wait(&bars[k], waited[k] & 1, 1u << 20);
-        waited[k]++;
-      }
+    // bounded drain of everything still in flight before shared and tensor memory are released:
+    // every issued halo copy, and the last committed MMA batch (commits cover all earlier MMAs)
+    for (int j = tma_issued > NHALO ? tma_issued - NHALO : 0; j < tma_issued; ++j)  // latest use of each slot
+      mbar_wait(&halo_full[j % NHALO], (j / NHALO) & 1, 1u << 20);
+    if (mma_issued > 0) {
+      const int j = mma_issued - 1;
+      mbar_wait(&halo_empty[j % NHALO], (j / NHALO) & 1, 1u << 20);
+    }
   }
   tc_fence_before();
   __syncthreads();
