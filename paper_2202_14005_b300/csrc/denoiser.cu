@@ -34,12 +34,21 @@ constexpr int HALO_BYTES = 50176;             // padded to whole 1024-byte swizz
 constexpr int WPACK_BYTES = 9 * 8 * CH * 16;  // 73728 (bf16 [tap][g][n][8])
 constexpr int CONV_THREADS = 160;             // warps 0-3 epilogue (one TMEM lane quadrant each), warp 4 producer
 constexpr int NHALO = 3;                      // halo slots (TMA runs two tiles ahead of the MMAs)
-constexpr int OFF_W = 0;
-constexpr int OFF_H0 = WPACK_BYTES;
-constexpr int OFF_BIAS = OFF_H0 + NHALO * HALO_BYTES;
-constexpr int OFF_BAR = OFF_BIAS + CH * 4;
 constexpr int NBARS = 1 + 2 * NHALO + 2 + 2;  // weights, halo full/empty, TMEM full/empty
-constexpr int CONV_SMEM = OFF_BAR + NBARS * 8 + 16 + 1024;  // + slack to realign the base to 1 KB
+// Shared-memory layout of the convolution kernel for NOUT output channels (64: the 64 -> 64
+// layers; 16: the 64 -> 2 layers with 14 zero rows): packed weights [tap][g][n][8], NHALO halo
+// slots (1 KB aligned), bias, barriers.
+template <int NOUT>
+struct ConvLayout {
+  static constexpr int WP = 9 * 8 * NOUT * 16;
+  static constexpr int OFF_W = 0;
+  static constexpr int OFF_H0 = (WP + 1023) & ~1023;
+  static constexpr int OFF_BIAS = OFF_H0 + NHALO * HALO_BYTES;
+  static constexpr int OFF_BAR = OFF_BIAS + CH * 4;
+  static constexpr int SMEM = OFF_BAR + NBARS * 8 + 16 + 1024;  // + slack to realign the base to 1 KB
+  static constexpr int TMEM_COLS = 2 * NOUT < 32 ? 32 : 2 * NOUT;
+};
+constexpr int WP16_BYTES = ConvLayout<16>::WP;  // 18432 (64 -> 2 tables, N padded to 16)
 
 // Offsets (floats) into the flat MoDL weight vector: w_l [Cout][Cin][3][3], b_l [Cout].
 struct ModlOffsets {
@@ -82,16 +91,17 @@ struct PackArgs {
   __nv_bfloat16* dgr[3];
   const float* w1;       // first layer [64][2][9]
   const float* w5;       // last layer [2][64][9]
-  __nv_bfloat16* t5;     // [9][8][64]: Wt[t][n][ch] = w5[n][ch][t] (n < 2)
-  __nv_bfloat16* t1;     // [9][8][64]: Wt[t][n][ch] = w1[ch][n][8 - t] (n < 2)
+  __nv_bfloat16* t5;     // last layer forward, [tap][g][n16][8]: w5[n][g*8+e][tap] (n < 2)
+  __nv_bfloat16* t1;     // first layer input gradient, [tap][g][n16][8]: w1[g*8+e][n][8 - tap] (n < 2)
 };
 __global__ void k_pack64(const PackArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9*8*64*8
-  if (blockIdx.y >= 6) {  // 64 -> 2 tables of the first and last layers
-    if (i >= 9 * 8 * CH) return;
-    const int t = i / (8 * CH), n = (i / CH) % 8, ch = i % CH;
+  if (blockIdx.y >= 6) {  // 64 -> 2 tables of the first and last layers (N padded to 16)
+    if (i >= 9 * 8 * 16 * 8) return;
+    const int e = i & 7, n = (i >> 3) & 15, g = (i >> 7) & 7, tap = i >> 10;
     float v = 0.f;
-    if (n < 2) v = (blockIdx.y == 6) ? a.w5[(n * CH + ch) * 9 + t] : a.w1[(ch * 2 + n) * 9 + (8 - t)];
+    if (n < 2)
+      v = (blockIdx.y == 6) ? a.w5[(n * CH + g * 8 + e) * 9 + tap] : a.w1[((g * 8 + e) * 2 + n) * 9 + (8 - tap)];
     (blockIdx.y == 6 ? a.t5 : a.t1)[i] = __float2bfloat16_rn(v);
     return;
   }
@@ -110,7 +120,9 @@ struct ConvArgs {
   const float* bias;            // forward: [64]
   const __nv_bfloat16* aprev;   // input gradient: ReLU mask source [B][H][W][64]
   __nv_bfloat16* out;           // [B][H][W][64]
-  int mode;                     // 0 forward, 1 input gradient
+  int mode;                     // 0 forward, 1 input gradient (64 -> 64); 2 last layer, 3 first-layer input gradient (64 -> 2)
+  const float2* res;            // modes 2/3: residual added to the two output channels
+  float2* out2;                 // modes 2/3: complex output [B][H][W]
   int* status;
 };
 
@@ -130,8 +142,9 @@ __device__ __forceinline__ void issue_halo(const CUtensorMap* map, uint8_t* dst,
   tma_load_4d(dst, map, 0, wt * TILE_M - 1, h - 1, b, bar);
 }
 
+template <int NOUT>
 __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32_t wts) {
-  const uint32_t idesc = umma_idesc_bf16(TILE_M, CH);
+  const uint32_t idesc = umma_idesc_bf16(TILE_M, NOUT);
 #pragma unroll
   for (int tap = 0; tap < 9; ++tap) {
     const int dy = tap / 3, dx = tap - dy * 3;
@@ -139,13 +152,17 @@ __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32
     for (int kk = 0; kk < 4; ++kk) {
       // A: 128 pixels starting at halo pixel (dy, dx), channels 16 kk .. 16 kk + 15
       const uint64_t ad = umma_desc_sw128(halo + (dy * HALO_W + dx) * 128 + kk * 32);
-      const uint64_t bd = umma_desc(wts + (tap * 8 + 2 * kk) * 1024, 1024, 128);
+      const uint64_t bd = umma_desc(wts + (tap * 8 + 2 * kk) * (NOUT * 16), NOUT * 16, 128);
       umma_bf16(tmem_d, ad, bd, idesc, (tap | kk) != 0);
     }
   }
 }
 
-// Warp-specialised persistent kernel.  Warp 4 (one lane) is the producer: it streams tile halos
+// Warp-specialised persistent kernel, one 128-pixel row segment per tile, 3x3 taps as 36 MMAs of
+// K = 16 over the halo (M = 128 pixels, N = NOUT).  NOUT = 64: the 64 -> 64 layers (epilogue
+// bias + ReLU, or the input gradient masked by the previous activation).  NOUT = 16: the 64 -> 2
+// layers with two live columns (mode 2, last layer: out = x + b5 + acc; mode 3, first-layer
+// input gradient with flipped taps: gx = gout + acc).  Warp 4 (one lane) is the producer: it streams tile halos
 // into NHALO shared slots with TMA and issues each tile's 36 MMAs into one of two TMEM halves as
 // soon as the halo has landed and the epilogue has drained that half.  Warps 0-3 run the epilogue
 // of every tile (warp w reads TMEM lanes 32w..32w+31: pixels 32w..32w+31).  Hand-offs go through
@@ -158,13 +175,15 @@ __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32
 // parity waited for is that use index's low bit.  Every wait is bounded: a role that gives up
 // records an error, and the CTA waits (bounded) for whatever it still has in flight, frees its
 // tensor memory and returns with SENSE_STATUS_DEVICE_TIMEOUT set.
+template <int NOUT>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
 k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
+  using CL = ConvLayout<NOUT>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  uint8_t* s_halo = smem + OFF_H0;
-  float* s_bias = reinterpret_cast<float*>(smem + OFF_BIAS);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+  uint8_t* s_halo = smem + CL::OFF_H0;
+  float* s_bias = reinterpret_cast<float*>(smem + CL::OFF_BIAS);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CL::OFF_BAR);
   uint64_t* w_full = bars;
   uint64_t* halo_full = bars + 1;
   uint64_t* halo_empty = bars + 1 + NHALO;
@@ -189,9 +208,9 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
     *s_err = 0;
     fence_mbar_init();
   }
-  if (tid < CH) s_bias[tid] = (a.mode == 0) ? a.bias[tid] : 0.f;
+  if (tid < CH) s_bias[tid] = (a.mode == 0 || (a.mode == 2 && tid < 2)) ? a.bias[tid] : 0.f;
   if (warp == 0) {
-    tmem_alloc(s_tmem, 128);
+    tmem_alloc(s_tmem, CL::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -203,10 +222,10 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
   int tma_issued = 0, mma_issued = 0;
   if (warp == 4) {
     if (lane == 0 && n > 0) {
-      const uint32_t sw = smem_u32(smem + OFF_W);
+      const uint32_t sw = smem_u32(smem + CL::OFF_W);
       bool ok = true;
-      mbar_expect_tx(w_full, WPACK_BYTES);
-      bulk_load(smem + OFF_W, a.wpack, WPACK_BYTES, w_full);
+      mbar_expect_tx(w_full, CL::WP);
+      bulk_load(smem + CL::OFF_W, a.wpack, CL::WP, w_full);
       const int pre = n < 2 ? n : 2;
       for (int j = 0; j < pre; ++j) {
         issue_halo(&tmap, s_halo + j * HALO_BYTES, &halo_full[j], blockIdx.x + j * gridDim.x, a.H, a.ntw);
@@ -219,7 +238,7 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
         if (ok && i >= 2) ok = mbar_wait(&tm_empty[t], ((i - 2) >> 1) & 1);
         if (!ok) break;
         tc_fence_after();
-        issue_mma(tmem + t * 64, smem_u32(s_halo + s * HALO_BYTES), sw);
+        issue_mma<NOUT>(tmem + t * NOUT, smem_u32(s_halo + s * HALO_BYTES), sw);
         umma_commit(&tm_full[t]);
         umma_commit(&halo_empty[s]);
         ++mma_issued;
@@ -249,6 +268,18 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
       const int px = wt * TILE_M + warp * 32 + lane;
       const bool valid = px < a.W;
       const size_t pix = ((size_t)b * a.H + h) * a.W + px;
+      if constexpr (NOUT == 16) {  // 64 -> 2: two accumulator columns, residual, complex output
+        float2 acc2;
+        tmem_ld2(tmem + ((uint32_t)(warp * 32) << 16) + t * NOUT, acc2);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tm_empty[t]);
+        if (valid) {
+          const float2 rv = a.res[pix];
+          a.out2[pix] = make_float2(rv.x + s_bias[0] + acc2.x, rv.y + s_bias[1] + acc2.y);
+        }
+        continue;
+      }
       // input-gradient mode: the whole 128-byte ReLU-mask row of this pixel in one batch of loads
       uint4 mrow[8];
       if (a.mode == 1 && valid) {
@@ -257,7 +288,7 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
         for (int q = 0; q < 8; ++q) mrow[q] = ap[q];
       }
       float acc[64];
-      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + t * 64, acc);
+      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + t * NOUT, acc);
       // the accumulators are in registers: hand the TMEM half back to the producer
       tc_fence_before();
       __syncwarp();
@@ -310,7 +341,7 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 128);
+  if (warp == 0) tmem_dealloc(tmem, CL::TMEM_COLS);
 }
 
 // ------------------------------------------------ 2-channel layers
@@ -393,92 +424,6 @@ __global__ void __launch_bounds__(128) k_2to64(int B, int H, int W, int mode, co
 #pragma unroll
       for (int e = 0; e < 4; ++e) po[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
       reinterpret_cast<uint4*>(out + p * CH)[cg] = o;
-    }
-  }
-}
-
-// Shared-memory halo of a 64-channel BF16 tensor: rows h-1..h+1, pixels
-// w0-1 .. w0+kTw (zero outside the image), rows padded to 144 bytes so that
-// consecutive threads reading consecutive pixels hit distinct banks.
-constexpr int kTw = 128;
-constexpr int kHaloLd = 72;  // bf16 per padded pixel row
-constexpr int kHaloSmem = 3 * (kTw + 2) * kHaloLd * 2;
-constexpr int kSmem64to2 = kHaloSmem + 9 * 8 * CH * 2;
-
-__device__ __forceinline__ void stage_halo64(__nv_bfloat16* s, const __nv_bfloat16* t, int b, int h, int w0,
-                                             int H, int W) {
-  for (int i = threadIdx.x; i < 3 * (kTw + 2) * 8; i += blockDim.x) {
-    const int q = i & 7, px = (i >> 3) % (kTw + 2), r = (i >> 3) / (kTw + 2);
-    const int yy = h - 1 + r, xx = w0 - 1 + px;
-    const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
-    const __nv_bfloat16* src = t + (ok ? (((size_t)b * H + yy) * W + xx) * CH + q * 8 : 0);
-    cp_async16(s + (r * (kTw + 2) + px) * kHaloLd + q * 8, src, ok);
-  }
-  cp_async_commit();
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"((uint32_t)__cvta_generic_to_shared(p)));
-}
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// 64 -> 2 on the warp-level tensor cores (mma.sync m16n8k16, N = 8 with 2 used):
-// A = 16 pixels x 16 channels of the halo tile (ldmatrix), B = weights
-// Wt[t][n][ch] for halo offset t = (ry, rx), K = 9 offsets x 64 channels.
-//   mode 0 (last layer):  out = x + b5 + sum_t sum_ch w5[n][ch][t] halo(ry, m + rx)
-//   mode 1 (first layer input gradient): gx = gout + sum w1[ch][n][8 - t] halo(ry, m + rx)
-// (the flipped taps of the input gradient are the offsets t = 8 - tap).
-__global__ void __launch_bounds__(kTw) k_64to2(int B, int H, int W, int mode, const __nv_bfloat16* act,
-                                              const __nv_bfloat16* wsrc16, const float* bias, const float2* res,
-                                              float2* out) {
-  extern __shared__ __align__(16) uint8_t dsm[];
-  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(dsm);
-  __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(dsm + kHaloSmem);  // [9][8][64]
-  const int bh = blockIdx.y, b = bh / H, h = bh % H, w0 = blockIdx.x * kTw;
-  for (int i = threadIdx.x; i < 9 * 8 * CH / 8; i += blockDim.x) cp_async16(wt + i * 8, wsrc16 + i * 8, true);
-  stage_halo64(halo, act, b, h, w0, H, W);
-  cp_async_wait0();
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gid = lane >> 2, tig = lane & 3;
-  const int mi = lane >> 3, r = lane & 7;
-#pragma unroll 1
-  for (int mt = 0; mt < 2; ++mt) {
-    const int mbase = warp * 32 + mt * 16;
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-    for (int t = 0; t < 9; ++t) {
-      const int ry = t / 3, rx = t % 3;
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-        const int ch0 = kc * 16;
-        uint32_t af[4];
-        const int m = (mi & 1) * 8 + r, kq = (mi >> 1) * 8;
-        ldsm_x4(af, halo + (ry * (kTw + 2) + mbase + m + rx) * kHaloLd + ch0 + kq);
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wt + (t * 8 + gid) * CH + ch0 + 2 * tig);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wt + (t * 8 + gid) * CH + ch0 + 8 + 2 * tig);
-        mma16816(d, af, b0, b1);
-      }
-    }
-    if (tig == 0) {
-      const float b0v = (mode == 0) ? bias[0] : 0.f, b1v = (mode == 0) ? bias[1] : 0.f;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int w = w0 + mbase + gid + half * 8;
-        if (w < W) {
-          const size_t p = ((size_t)b * H + h) * W + w;
-          const float2 rv = res[p];
-          out[p] = make_float2(rv.x + b0v + d[2 * half], rv.y + b1v + d[2 * half + 1]);
-        }
-      }
     }
   }
 }
@@ -814,10 +759,10 @@ int conv_prepare() {
     int dev = 0;
     state = (cudaGetDevice(&dev) == cudaSuccess &&
              cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-             cudaFuncSetAttribute(k_conv64, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM) ==
-                 cudaSuccess &&
-             cudaFuncSetAttribute(k_64to2, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem64to2) ==
-                 cudaSuccess &&
+             cudaFuncSetAttribute(k_conv64<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ConvLayout<64>::SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_conv64<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ConvLayout<16>::SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, wl1_smem(kMaxW)) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l5, cudaFuncAttributeMaxDynamicSharedMemorySize, wl5_smem(kMaxW)) ==
@@ -830,17 +775,24 @@ int conv_prepare() {
 
 int launch_conv64(const __nv_bfloat16* in, const __nv_bfloat16* wpack, const float* bias,
                   const __nv_bfloat16* aprev, __nv_bfloat16* out, int mode, int B, int H, int W,
-                  int* status, cudaStream_t st) {
+                  int* status, cudaStream_t st, const float2* res = nullptr, float2* out2 = nullptr) {
   CUtensorMap map;
   if (int e = make_act_map(&map, in, B, H, W)) return e;
   ConvArgs a;
   a.B = B; a.H = H; a.W = W; a.ntw = (W + TILE_M - 1) / TILE_M;
   a.wpack = wpack; a.bias = bias; a.aprev = aprev; a.out = out; a.mode = mode; a.status = status;
+  a.res = res; a.out2 = out2;
   const int ntiles = B * H * a.ntw;
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-  prof_mark("conv64_tc", st, false);
-  k_conv64<<<grid, CONV_THREADS, CONV_SMEM, st>>>(map, a);
-  prof_mark("conv64_tc", st, true);
+  if (mode >= 2) {  // 64 -> 2 layers
+    prof_mark("dn_64to2", st, false);
+    k_conv64<16><<<grid, CONV_THREADS, ConvLayout<16>::SMEM, st>>>(map, a);
+    prof_mark("dn_64to2", st, true);
+  } else {
+    prof_mark("conv64_tc", st, false);
+    k_conv64<64><<<grid, CONV_THREADS, ConvLayout<64>::SMEM, st>>>(map, a);
+    prof_mark("conv64_tc", st, true);
+  }
   prof_count(1);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -860,7 +812,7 @@ DnLayout dn_layout(int B, int H, int W) {
   size_t o = 0;
   for (int i = 0; i < 3; ++i) { L.wf[i] = o; o += up256(WPACK_BYTES); }
   for (int i = 0; i < 3; ++i) { L.wd[i] = o; o += up256(WPACK_BYTES); }
-  for (int i = 0; i < 2; ++i) { L.ts[i] = o; o += up256(9 * 8 * CH * 2); }
+  for (int i = 0; i < 2; ++i) { L.ts[i] = o; o += up256(WP16_BYTES); }
   for (int i = 0; i < 4; ++i) { L.act[i] = o; o += act; }
   for (int i = 0; i < 2; ++i) { L.g[i] = o; o += act; }
   L.part_small = o; o += up256((size_t)L.nch_small * kSmallOut * 4);
@@ -913,14 +865,11 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
     if (int e = launch_conv64(act[l], reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), wts + o.b[l + 1],
                               nullptr, act[l + 1], 0, B, H, W, status, st))
       return e;
-  if (out)
-    {
-    prof_mark("dn_64to2", st, false);
-    k_64to2<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kSmem64to2, st>>>(
-        B, H, W, 0, act[3], reinterpret_cast<const __nv_bfloat16*>(ws + L.ts[0]), wts + o.b[4], x, out);
-    prof_mark("dn_64to2", st, true);
-    }
-  prof_count(2 + (out ? 1 : 0));  // packing, first layer, last layer (convolutions counted apart)
+  if (out)  // last layer on the tensor cores: out = x + b5 + conv(a4) (two of 16 MMA columns used)
+    if (int e = launch_conv64(act[3], reinterpret_cast<const __nv_bfloat16*>(ws + L.ts[0]), wts + o.b[4],
+                              nullptr, nullptr, 2, B, H, W, status, st, x, out))
+      return e;
+  prof_count(2);  // packing, first layer (convolutions counted apart)
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
@@ -1026,12 +975,11 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
                                                                grad_weights + o.w[0], CH, CH * 18,
                                                                grad_weights + o.b[0]);
   prof_mark("dn_reduce", st, true);
-  prof_mark("dn_64to2", st, false);
-  k_64to2<<<dim3((W + kTw - 1) / kTw, B * H), kTw, kSmem64to2, st>>>(
-      B, H, W, 1, gbuf[cur], reinterpret_cast<const __nv_bfloat16*>(w8 + L.ts[1]), nullptr, go,
-      static_cast<float2*>(grad_x));
-  prof_mark("dn_64to2", st, true);
-  prof_count(12);  // every launch of the backward except the three tensor-core convolutions
+  // first layer input gradient on the tensor cores: gx = gout + conv^T(g1) (flipped taps)
+  if (int e = launch_conv64(gbuf[cur], reinterpret_cast<const __nv_bfloat16*>(w8 + L.ts[1]), nullptr, nullptr,
+                            nullptr, 3, B, H, W, status, st, go, static_cast<float2*>(grad_x)))
+    return e;
+  prof_count(11);  // every launch of the backward except the tensor-core convolutions
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 

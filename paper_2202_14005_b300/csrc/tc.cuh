@@ -117,6 +117,17 @@ SENSE_D void umma_commit(uint64_t* bar) {
                    smem_u32(bar))
                : "memory");
 }
+// 32 lanes x 32 bit, 2 consecutive columns.
+SENSE_D void tmem_ld2(uint32_t taddr, float2& v) {
+  uint32_t r0, r1;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r0), "=r"(r1)
+      : "r"(taddr));
+  v = make_float2(__uint_as_float(r0), __uint_as_float(r1));
+}
+
 // 32 lanes x 32 bit, 64 consecutive columns in one load and one completion wait (a single
 // round trip to tensor memory for a whole 64-channel accumulator row).
 SENSE_D void tmem_ld64(uint32_t taddr, float (&v)[64]) {
