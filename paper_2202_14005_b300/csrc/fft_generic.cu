@@ -9,6 +9,7 @@
 // i.e. a plain DFT between two (-1)^n modulations.  For the normal operator the
 // modulations cancel against each other (F^H diag(m) F is circulant), so that
 // path uses a plain DFT pair and the mask shifted to plain frequency order.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -77,13 +78,37 @@ __device__ __forceinline__ void bfly(const float2* in, float2* out, int j, int N
   for (int r = 0; r < R; ++r) out[idxD + r * Ns] = v[r];
 }
 
+// Radix-R stage for the larger primes (R >= 11), one output per work item: item (j, kout) of a
+// stage whose sub-transforms have length Ns evaluates
+//   X_kout = sum_r in[j + r L/R] w^{r D},  D = (j mod Ns) L/(Ns R) + kout L/R,  w = e^{-2 pi i / L},
+// which is the stage twiddle w^{(j mod Ns) r L/(Ns R)} times the R-point kernel w^{(r kout mod R) L/R}
+// folded into one table index (r D mod L).  R times as many work items as butterflies keep all
+// threads busy on short rows, and no R-element register arrays are needed.
+template <bool INV>
+__device__ __forceinline__ void bfly_out(const float2* in, float2* out, int j, int kout, int R, int Ns, int L,
+                                         const float2* tw) {
+  const int stride = L / R;
+  const int jm = j % Ns;
+  const int D = jm * (L / (Ns * R)) + kout * stride;  // < L
+  float2 acc = in[j];
+  int idx = 0;
+  for (int r = 1; r < R; ++r) {
+    idx += D;
+    if (idx >= L) idx -= L;
+    const float2 w = __ldg(tw + idx);
+    const float2 v = in[j + r * stride];
+    acc = INV ? cfmac(w, v, acc) : cfma(v, w, acc);
+  }
+  out[(j / Ns) * Ns * R + jm + kout * Ns] = acc;
+}
+
 // Transform ntr sequences of length L held in a at stride ld (>= L; ping-pong with b).  Column
 // passes use ld = L + 1: the transposing loads and stores of neighbouring columns then fall into
 // different shared-memory banks.  Returns the buffer holding the result.  All threads take part.
 // CLS selects the radices compiled into the stage loop: 0 = {2, 4, 8}, 1 = also {3, 5, 7},
-// 2 = every supported radix.  Large-prime butterflies hold R complex values in registers;
-// leaving them out of the smaller classes keeps power-of-two transforms at low register counts
-// (and several CTAs per SM).
+// 2 = also the primes 11 .. 31 (one output per work item, bfly_out).  The radix 3 - 7 butterflies
+// hold R complex values in registers; leaving them out of class 0 keeps power-of-two transforms
+// at the lowest register counts.
 template <bool INV, int CLS>
 __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, int ld) {
   const int L = f.L;
@@ -91,6 +116,17 @@ __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, in
   for (int s = 0; s < f.nst; ++s) {
     const int R = f.radix[s];
     const int nb = L / R;
+    if (CLS >= 2 && R >= 11) {
+      for (int w = threadIdx.x; w < ntr * L; w += blockDim.x) {
+        const int tr = w / L, rem = w - tr * L;
+        const int kout = rem / nb, j = rem - kout * nb;
+        bfly_out<INV>(a + tr * ld, b + tr * ld, j, kout, R, Ns, L, f.tw);
+      }
+      __syncthreads();
+      float2* t = a; a = b; b = t;
+      Ns *= R;
+      continue;
+    }
     for (int w = threadIdx.x; w < ntr * nb; w += blockDim.x) {
       const int tr = w / nb, j = w - tr * nb;
       const float2* in = a + tr * ld;
@@ -105,19 +141,7 @@ __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, in
               case 3: bfly<3, INV>(in, out, j, Ns, L, f.tw); break;
               case 5: bfly<5, INV>(in, out, j, Ns, L, f.tw); break;
               case 7: bfly<7, INV>(in, out, j, Ns, L, f.tw); break;
-              default:
-                if constexpr (CLS >= 2) {
-                  switch (R) {
-                    case 11: bfly<11, INV>(in, out, j, Ns, L, f.tw); break;
-                    case 13: bfly<13, INV>(in, out, j, Ns, L, f.tw); break;
-                    case 17: bfly<17, INV>(in, out, j, Ns, L, f.tw); break;
-                    case 19: bfly<19, INV>(in, out, j, Ns, L, f.tw); break;
-                    case 23: bfly<23, INV>(in, out, j, Ns, L, f.tw); break;
-                    case 29: bfly<29, INV>(in, out, j, Ns, L, f.tw); break;
-                    case 31: bfly<31, INV>(in, out, j, Ns, L, f.tw); break;
-                    default: break;
-                  }
-                }
+              default: break;
             }
           }
       }
@@ -135,7 +159,7 @@ __device__ __forceinline__ float pm1(int n) { return (n & 1) ? -1.f : 1.f; }
 //   mode 0 (forward): input (-1)^{h+w} S x, output (-1)^{kw} (-1)^{W/2} / sqrt(W)
 //   mode 1 (normal):  plain DFT, no modulation, no scale.
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_expand(int B, int S, int C, int H, const float2* x,
+__global__ void __launch_bounds__(kThreads, 2) k_row_expand(int B, int S, int C, int H, const float2* x,
                                                          const float2* maps, float2* T,
                                                          Fft1DDev f, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -171,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_expand(int B
 //   mode 2 (normal):   dst = IDFT_H(m2s DFT_H(src))   (m2s: mask^2/(HW), plain order)
 // mask: modes 0/1 the centred mask ([W] if lines else [H][W]); mode 2 shifted mask^2.
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_col(int W, const float2* src, float2* dst,
+__global__ void __launch_bounds__(kThreads, 2) k_col(int W, const float2* src, float2* dst,
                                                   Fft1DDev f, const float* mask, int lines,
                                                   int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -234,12 +258,15 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_col(int W, const
 //   out[b,h,:] = sum_c conj(S_c) post(IDFT_W(pre(T[b,c,h,:]))) (+ lambda xin)
 //   mode 1 (adjoint): pre (-1)^{kw}, post (-1)^w (-1)^{W/2}/sqrt(W)
 //   mode 2 (normal):  no modulation, no scale (the scale sits in the mask table)
+// With cpg < C (one map set only), CTA z sums coils z cpg .. z cpg + cpg - 1 and writes that
+// partial sum over the rows of coil z cpg it has just read (no other CTA reads them);
+// k_coil_groups_sum then adds the groups in fixed order.
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_combine(int S, int C, int H, const float2* T,
+__global__ void __launch_bounds__(kThreads, 2) k_row_combine(int S, int C, int H, float2* T,
                                                           const float2* maps, float2* out,
                                                           Fft1DDev f, int mode,
                                                           const float2* xin, float lam_host,
-                                                          const double* lam_dev) {
+                                                          const double* lam_dev, int cpg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = f.L;
   float2* a = reinterpret_cast<float2*>(smem);
@@ -247,11 +274,12 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_combine(int 
   const int b = blockIdx.y / S, s = blockIdx.y - b * S;  // output set s of slice b
   const int h0 = blockIdx.x * kRows;
   const int nr = min(kRows, H - h0);
+  const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
   float2 acc[kMaxPer];
 #pragma unroll
   for (int e = 0; e < kMaxPer; ++e) acc[e] = make_float2(0.f, 0.f);
   const float sc = pm1(W / 2) * rsqrtf((float)W);
-  for (int c = 0; c < C; ++c) {
+  for (int c = c0; c < c1; ++c) {
     for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
       const int r = i / W, k = i - r * W;
       float2 v = T[(((size_t)b * C + c) * H + h0 + r) * W + k];
@@ -273,6 +301,15 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_combine(int 
     }
     __syncthreads();
   }
+  if (cpg < C) {  // partial sum of this coil group
+    float2* dst = T + (((size_t)b * C + c0) * H + h0) * W;
+#pragma unroll
+    for (int e = 0; e < kMaxPer; ++e) {
+      const int i = threadIdx.x + e * blockDim.x;
+      if (i < nr * W) dst[i] = acc[e];
+    }
+    return;
+  }
   const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
 #pragma unroll
   for (int e = 0; e < kMaxPer; ++e) {
@@ -290,6 +327,29 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_combine(int 
   }
 }
 
+// out[b] = sum over coil groups g (in order) of T[b, g cpg] (+ lambda xin[b]); one map set.
+__global__ void k_coil_groups_sum(int B, int C, int HW, int cpg, const float2* T, const float2* xin,
+                                  float lam_host, const double* lam_dev, float2* out) {
+  const size_t n = (size_t)B * HW;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / HW);
+    const size_t q = i - (size_t)b * HW;
+    float2 v = make_float2(0.f, 0.f);
+    for (int c = 0; c < C; c += cpg) {
+      const float2 t = T[((size_t)b * C + c) * HW + q];
+      v.x += t.x;
+      v.y += t.y;
+    }
+    if (xin) {
+      const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
+      const float2 xv = xin[i];
+      v.x = fmaf(lam, xv.x, v.x);
+      v.y = fmaf(lam, xv.y, v.y);
+    }
+    out[i] = v;
+  }
+}
+
 // ------------------------------------------------ Toeplitz embedding (non-Cartesian)
 // F^H P^H P F u = crop(IFFT2(psf_hat * FFT2(pad(u)))) on the 2H x 2W grid, with psf_hat holding
 // the 1 / (4 H W) of the inverse.  Rows H .. 2H - 1 of pad(u) are zero, so only H rows are
@@ -299,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_row_combine(int 
 //   k_tp_rows_inv:  out[b,h,:] = sum_c conj(S_c) IFFT_2W(T[b,c,h,:])[0..W-1] + lambda x
 // T is [B][C][H][2W].
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_rows_fwd(int C, int H, int W, const float2* x,
+__global__ void __launch_bounds__(kThreads, 2) k_tp_rows_fwd(int C, int H, int W, const float2* x,
                                                           const float2* maps, float2* T, Fft1DDev f) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W2 = f.L;
@@ -321,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_rows_fwd(int 
 }
 
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_cols(int H, int W2, float2* T, Fft1DDev f,
+__global__ void __launch_bounds__(kThreads, 2) k_tp_cols(int H, int W2, float2* T, Fft1DDev f,
                                                       const float2* psf_hat) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int H2 = f.L, ld = H2 + 1;
@@ -354,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_cols(int H, i
 }
 
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_rows_inv(int C, int H, int W, const float2* T,
+__global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W, const float2* T,
                                                           const float2* maps, float2* out, Fft1DDev f,
                                                           const float2* xin, float lam_host,
                                                           const double* lam_dev) {
@@ -398,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_rows_inv(int 
 
 // psf_hat = FFT2(psf) / (4 H W): rows along 2W, then columns along 2H (in place, one array).
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_psf_rows(int H2, const float2* psf, float2* out, Fft1DDev f) {
+__global__ void __launch_bounds__(kThreads, 2) k_tp_psf_rows(int H2, const float2* psf, float2* out, Fft1DDev f) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W2 = f.L;
   float2* a = reinterpret_cast<float2*>(smem);
@@ -412,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_psf_rows(int 
 }
 
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, CLS == 2 ? 1 : 2) k_tp_psf_cols(int W2, float2* io, Fft1DDev f, float scale) {
+__global__ void __launch_bounds__(kThreads, 2) k_tp_psf_cols(int W2, float2* io, Fft1DDev f, float scale) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int H2 = f.L, ld = H2 + 1;
   float2* a = reinterpret_cast<float2*>(smem);
@@ -550,6 +610,35 @@ int generic_prepare(sense_plan p) {
   return SENSE_OK;
 }
 
+// Row pass with coil combination over p->w.T.  Few row tiles (small batches) leave most SMs idle
+// while each CTA walks all coils, so with one map set the coils are split into groups across
+// grid.z (about 1024 CTAs in all) and the group sums are added by a second, streaming kernel.
+int launch_row_combine(sense_plan p, float2* out, int mode, const float2* xin, float lam_host,
+                       const double* lam_dev) {
+  const int nrb = (p->H + kRows - 1) / kRows;
+  int groups = 1;
+  if (p->S == 1) {
+    groups = (1024 + nrb * p->B - 1) / (nrb * p->B);
+    groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
+  }
+  const int cpg = (p->C + groups - 1) / groups;
+  groups = (p->C + cpg - 1) / cpg;
+  const dim3 gr(nrb, p->B * p->S, groups);
+  prof_mark("fft_generic", p->stream, false);
+  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_combine, gr, smem_rows(p->W), p->stream, p->S, p->C, p->H, p->w.T,
+                   p->maps, out, dev(p->fW), mode, xin, lam_host, lam_dev, groups > 1 ? cpg : p->C);
+  if (groups > 1) {
+    const int HW = p->H * p->W;
+    const long long n = (long long)p->B * HW;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 2048LL);
+    k_coil_groups_sum<<<grid, 256, 0, p->stream>>>(p->B, p->C, HW, cpg, p->w.T, xin, lam_host, lam_dev, out);
+    count_launch(p, 1);
+  }
+  prof_mark("fft_generic", p->stream, true);
+  count_launch(p, 1);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
 int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
@@ -571,13 +660,8 @@ int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
   SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, y, p->w.T, dev(p->fH),
                    p->mask, p->mask_is_lines, 1);
   prof_mark("fft_generic", p->stream, true);
-  const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->S);
-  prof_mark("fft_generic", p->stream, false);
-  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_combine, gr, smem_rows(p->W), p->stream, p->S, p->C, p->H, p->w.T,
-                   p->maps, x, dev(p->fW), 1, nullptr, 0.f, nullptr);
-  prof_mark("fft_generic", p->stream, true);
-  count_launch(p, 2);
-  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+  count_launch(p, 1);
+  return launch_row_combine(p, x, 1, nullptr, 0.f, nullptr);
 }
 
 int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
@@ -593,13 +677,8 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
   SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, p->w.T, p->w.T, dev(p->fH),
                    p->mask2s, p->mask_is_lines, 2);
   prof_mark("fft_generic", p->stream, true);
-  const dim3 gr2((p->H + kRows - 1) / kRows, p->B * p->S);
-  prof_mark("fft_generic", p->stream, false);
-  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_combine, gr2, smem_rows(p->W), p->stream, p->S, p->C, p->H, p->w.T,
-                   p->maps, out, dev(p->fW), 2, x, lam_host, lam_dev);
-  prof_mark("fft_generic", p->stream, true);
-  count_launch(p, 3);
-  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+  count_launch(p, 2);
+  return launch_row_combine(p, out, 2, x, lam_host, lam_dev);
 }
 
 int toeplitz_prepare(sense_plan p, const float2* psf) {

@@ -130,7 +130,9 @@ def test_normal_2d_mask(case):
 
 
 FA_CASES = [(1, 8, 64, 64, True), (2, 12, 256, 232, True), (1, 15, 320, 368, True),
-            (2, 3, 24, 20, False), (1, 4, 64, 232, False)]
+            (2, 3, 24, 20, False), (1, 4, 64, 232, False),
+            # every large-prime radix (11 .. 31), two of them in one length (286 = 2 * 11 * 13)
+            (1, 3, 22, 26, False), (1, 2, 34, 38, False), (1, 2, 46, 58, False), (1, 2, 62, 286, False)]
 
 
 @pytest.mark.parametrize("case", FA_CASES)
