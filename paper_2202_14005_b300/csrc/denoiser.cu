@@ -17,6 +17,7 @@
 //   fixed order (deterministic) and added to the caller's FP32 buffer.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -568,126 +569,189 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const float* partial, i
   }
 }
 
-// 64 -> 64 layer weight gradient on the warp-level tensor-core path
-// (mma.sync m16n8k16, BF16 in, FP32 accumulate):
-//   gw[co][ci][tap] = sum_p g[p][co] * a[p + s_tap][ci],  gb[co] = sum_p g[p][co].
-// CTA = one row of taps (dy) x one chunk of kW64Rows image rows of one slice;
-// its 8 warps tile D = [64 co] x [3 taps x 64 ci]: warp w owns co rows
-// 16*(w%4).. and 96 columns starting at 96*(w/4).  Pixels stream through shared
-// memory 32 at a time (cp.async, double buffered): the output-gradient tile
-// [32 px][64 co] and three shifted activation tiles [32 px][64 ci] (zero
-// outside the image).  Operands reach the MMA through ldmatrix.trans from the
-// channels-last tiles.  Per-chunk partial sums are reduced in fixed order.
-constexpr int kW64Rows = 4;
-constexpr int kW64Px = 32;
-constexpr int kW64Ld = 72;  // padded row (bf16) of the staged tiles: conflict-free ldmatrix
+// 64 -> 64 layer weight gradient on tcgen05 (BF16 operands, FP32 accumulation in TMEM):
+//   gw[co][ci][tap] = sum_p g[p][co] * a[p + s_tap][ci],  gb[co] = sum_p g[p][co],
+// a contraction over pixels.  Work items are row segments (slice b, row h, pixels
+// w0 .. w0 + 127); each CTA takes a contiguous range of them and keeps its sums in TMEM until the
+// end.  Per item a TMA box brings activation rows h-1, h, h+1 (pixels w0-1 .. w0+134, zero
+// outside the image) and one box the gradient row h; both are channels-last with 128-byte rows,
+// i.e. MN-major operands with K = pixels.  For each 16-pixel step and horizontal tap dx:
+//   MMA a: A = [row h-1 | row h] (two 64-channel blocks one row apart, M = 128), B = g row h
+//          -> TMEM lanes 0-63 accumulate tap (0, dx), lanes 64-127 tap (1, dx);
+//   MMA b: A = [row h+1 | ones] -> lanes 0-63 tap (2, dx), lanes 64-127 the bias sums.
+// The pixel offset dx is a start-address offset of 128 bytes (the swizzle follows the address
+// bits).  Warp 4 (one lane) issues TMA and MMAs through a three-slot pipeline; warps 0-3 read the
+// accumulators once at the end and write the CTA's partial sums [tap][co][ci] and bias [co],
+// which k_reduce_wgrad64 adds over CTAs in fixed order.
+constexpr int WG_SEG = 128;
+constexpr int WG_ROWPX = 136;                 // staged pixels per activation row (130 used)
+constexpr int WG_ROWB = WG_ROWPX * 128;       // 17408
+constexpr int WG_ACT = 3 * WG_ROWB;
+constexpr int WG_GB = WG_SEG * 128;
+constexpr int WG_STAGE = WG_ACT + WG_GB;      // 68608 (1 KB multiple)
+constexpr int WG_NST = 3;
+constexpr int WG_ONES = WG_NST * WG_STAGE;
+constexpr int WG_ONES_BYTES = 130 * 128;      // covers the offsets (16 kk + dx) + 15 rows
+constexpr int WG_BAR = WG_ONES + WG_ONES_BYTES;
+constexpr int WG_NBARS = 2 * WG_NST + 1;
+constexpr int WG_SMEM = WG_BAR + WG_NBARS * 8 + 16 + 1024;
+constexpr int WG_THREADS = 160;
+constexpr int kWgMaxParts = 256;              // partial-sum slots (one per CTA, CTAs <= SM count)
 
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+struct WgArgs {
+  int B, H, W, nseg, items;
+  float* partial;
+  int* status;
+};
+
+__device__ __forceinline__ void wg_item(int it, int H, int nseg, int& b, int& h, int& seg) {
+  h = it % H;
+  const int t = it / H;
+  seg = t % nseg;
+  b = t / nseg;
 }
 
-__global__ void __launch_bounds__(256) k_wgrad64(int B, int H, int W, const __nv_bfloat16* g,
-                                                 const __nv_bfloat16* act, float* partial) {
-  const int dy = blockIdx.y;  // tap row 0..2
-  const int chunks_per_slice = (H + kW64Rows - 1) / kW64Rows;
-  const int b = blockIdx.x / chunks_per_slice;
-  const int h0 = (blockIdx.x % chunks_per_slice) * kW64Rows;
-  const int h1 = min(h0 + kW64Rows, H);
-  const int npx = (h1 - h0) * W;
-  __shared__ __align__(16) __nv_bfloat16 s_g[2][kW64Px][kW64Ld];
-  __shared__ __align__(16) __nv_bfloat16 s_a[2][3][kW64Px][kW64Ld];
+__global__ void __launch_bounds__(WG_THREADS, 1)
+k_wgrad64(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap gmap, const WgArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + WG_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + WG_NST;
+  uint64_t* done = bars + 2 * WG_NST;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + WG_NBARS);
+  int* s_err = reinterpret_cast<int*>(s_tmem + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mrow = (warp & 3) * 16;   // co base
-  const int ncol = (warp >> 2) * 96;  // column base in [3 taps x 64 ci]
+  const int i0 = (int)(((long long)blockIdx.x * a.items) / gridDim.x);
+  const int i1 = (int)(((long long)(blockIdx.x + 1) * a.items) / gridDim.x);
+  const int n = i1 - i0;
 
-  // staging: thread tid copies 16-B chunk (tid & 7) of pixel (tid >> 3) of each tile
-  auto stage = [&](int buf, int q0) {
-    const int pp = tid >> 3, ch = (tid & 7) * 8;
-    const int q = q0 + pp;
-    const bool in = q < npx;
-    const int h = h0 + (in ? q / W : 0), w = in ? q % W : 0;
-    const size_t pix = ((size_t)b * H + h) * W + w;
-    cp_async16(&s_g[buf][pp][ch], g + pix * CH + ch, in);
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-      const int yy = h + dy - 1, xx = w + dx - 1;
-      const bool ok = in && yy >= 0 && yy < H && xx >= 0 && xx < W;
-      const size_t pa = ok ? (((size_t)b * H + yy) * W + xx) : 0;
-      cp_async16(&s_a[buf][dx][pp][ch], act + pa * CH + ch, ok);
+  if (tid == 0) {
+    for (int k = 0; k < WG_NST; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
     }
-    cp_async_commit();
-  };
+    mbar_init(done, 1);
+    *s_err = 0;
+    fence_mbar_init();
+  }
+  {  // the ones block (BF16 1.0), read by the tensor cores through the async proxy
+    uint4* o = reinterpret_cast<uint4*>(smem + WG_ONES);
+    for (int i = tid; i < WG_ONES_BYTES / 16; i += blockDim.x) o[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    fence_proxy_async();
+  }
+  if (warp == 0) {
+    tmem_alloc(s_tmem, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
 
-  float acc[12][4];
-#pragma unroll
-  for (int j = 0; j < 12; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
-  float bacc = 0.f;
-
-  const int nsteps = (npx + kW64Px - 1) / kW64Px;
-  if (nsteps > 0) stage(0, 0);
-  for (int it = 0; it < nsteps; ++it) {
-    const int buf = it & 1;
-    if (it + 1 < nsteps) {
-      stage(buf ^ 1, (it + 1) * kW64Px);
-      cp_async_wait1();
-    } else {
-      cp_async_wait0();
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kW64Px; kk += 16) {
-      // A = g^T (rows co, cols px): matrices (m0,k0), (m8,k0), (m0,k8), (m8,k8)
-      uint32_t af[4];
-      {
-        const int mi = lane >> 3, r = lane & 7;
-        const int m0 = (mi & 1) * 8, k0 = (mi >> 1) * 8;
-        ldsm_x4_t(af, &s_g[buf][kk + k0 + r][mrow + m0]);
+  int tma_issued = 0, mma_issued = 0;
+  if (warp == 4) {
+    if (lane == 0 && n > 0) {
+      const uint32_t idesc = umma_idesc_bf16_mn(128, CH);
+      const uint32_t ones = smem_u32(smem + WG_ONES);
+      auto load = [&](int it, int s) {
+        int b, h, seg;
+        wg_item(it, a.H, a.nseg, b, h, seg);
+        uint8_t* st = smem + s * WG_STAGE;
+        mbar_expect_tx(&full[s], WG_STAGE);
+        tma_load_4d(st, &amap, 0, seg * WG_SEG - 1, h - 1, b, &full[s]);
+        tma_load_4d(st + WG_ACT, &gmap, 0, seg * WG_SEG, h, b, &full[s]);
+      };
+      bool ok = true;
+      const int pre = n < 2 ? n : 2;
+      for (int j = 0; j < pre; ++j) {
+        load(i0 + j, j);
+        ++tma_issued;
       }
+      for (int i = 0; i < n && ok; ++i) {
+        const int s = i % WG_NST;
+        ok = mbar_wait(&full[s], (i / WG_NST) & 1);
+        if (!ok) break;
+        tc_fence_after();
+        int b, h, seg;
+        wg_item(i0 + i, a.H, a.nseg, b, h, seg);
+        const int rem = a.W - seg * WG_SEG;
+        const int nk = rem >= WG_SEG ? WG_SEG / 16 : (rem + 15) / 16;
+        const uint32_t act = smem_u32(smem + s * WG_STAGE);
+        const uint32_t gro = act + WG_ACT;
+        const uint32_t lbo_b = ones - (act + 2 * WG_ROWB);
+        for (int kk = 0; kk < nk; ++kk) {
+          const uint64_t bd = umma_desc_mn_sw128(gro + kk * 2048, 1024);
 #pragma unroll
-      for (int nb = 0; nb < 6; ++nb) {
-        // 16 columns = two n-tiles; column c -> (tap dx, ci)
-        const int c0 = ncol + nb * 16;
-        const int dx = c0 / 64, ci0 = c0 % 64;
-        uint32_t bfr[4];
-        const int mi = lane >> 3, r = lane & 7;
-        const int k0 = (mi & 1) * 8, n0 = (mi >> 1) * 8;
-        ldsm_x4_t(bfr, &s_a[buf][dx][kk + k0 + r][ci0 + n0]);
-        mma_bf16_16816(acc[2 * nb], af, bfr[0], bfr[1]);
-        mma_bf16_16816(acc[2 * nb + 1], af, bfr[2], bfr[3]);
+          for (int dx = 0; dx < 3; ++dx) {
+            const uint32_t off = (uint32_t)(kk * 16 + dx) * 128;
+            const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+            umma_bf16(tmem + dx * 128, umma_desc_mn_sw128(act + off, WG_ROWB), bd, idesc, acc);
+            umma_bf16(tmem + dx * 128 + 64, umma_desc_mn_sw128(act + 2 * WG_ROWB + off, lbo_b), bd, idesc, acc);
+          }
+        }
+        umma_commit(&empty[s]);
+        ++mma_issued;
+        if (i + 2 < n) {  // refill the slot of item i - 1 with item i + 2
+          const int s2 = (i + 2) % WG_NST;
+          if (i >= 1) ok = mbar_wait(&empty[s2], ((i - 1) / WG_NST) & 1);
+          if (!ok) break;
+          load(i0 + i + 2, s2);
+          ++tma_issued;
+        }
+      }
+      if (ok) {
+        umma_commit(done);
+      } else {
+        atomicExch(s_err, 1);
+        mbar_arrive(done);
       }
     }
-    if (dy == 1 && tid < CH)
-      for (int pp = 0; pp < kW64Px; ++pp) bacc += bf(s_g[buf][pp][tid]);
-    __syncthreads();
-  }
-  // D fragment: rows mrow + lane/4 (+8), cols 2*(lane%4) (+1) of each 8-column tile
-  const int gr = lane >> 2, gc = (lane & 3) * 2;
+  } else if (n > 0) {
+    // epilogue: TMEM lane m = 32 warp + lane
+    const bool ok = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ok) atomicExch(s_err, 1);
+    const bool write = ok && *reinterpret_cast<volatile int*>(s_err) == 0;
+    const int m = warp * 32 + lane;
+    float* out = a.partial + (size_t)blockIdx.x * 9 * CH * CH;
+#pragma unroll 1
+    for (int q = 0; q < 6; ++q) {
+      const int dx = q >> 1, half = q & 1;
+      float v[64];
+      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + dx * 128 + half * 64, v);
+      if (!write) continue;
+      if (half == 1 && m >= 64) {  // bias sums (identical in every lane of this block)
+        if (dx == 0 && m == 64) {
+          float* ob = a.partial + (size_t)gridDim.x * 9 * CH * CH + (size_t)blockIdx.x * CH;
 #pragma unroll
-  for (int j = 0; j < 12; ++j) {
-    const int c = ncol + j * 8 + gc;
-    const int dx = c / 64, ci = c % 64;
-    const int tap = dy * 3 + dx;
-    float* out = partial + ((size_t)blockIdx.x * 9 + tap) * (CH * CH);
-    out[(mrow + gr) * CH + ci] = acc[j][0];
-    out[(mrow + gr) * CH + ci + 1] = acc[j][1];
-    out[(mrow + gr + 8) * CH + ci] = acc[j][2];
-    out[(mrow + gr + 8) * CH + ci + 1] = acc[j][3];
+          for (int co = 0; co < CH; ++co) ob[co] = v[co];
+        }
+        continue;
+      }
+      const int dy = half == 0 ? (m >> 6) : 2;
+      const int ci = m & 63;
+      float* o = out + (size_t)(dy * 3 + dx) * CH * CH + ci;
+#pragma unroll
+      for (int co = 0; co < CH; ++co) o[co * CH] = v[co];
+    }
   }
-  if (dy == 1 && tid < CH) {
-    const int nchunks = gridDim.x;
-    partial[(size_t)nchunks * 9 * CH * CH + (size_t)blockIdx.x * CH + tid] = bacc;
+  tc_fence_before();
+  __syncthreads();
+  if (*s_err && tid == 4 * 32) {
+    set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
+    // bounded drain of the copies and MMAs still in flight before the memory is released
+    for (int j = tma_issued > WG_NST ? tma_issued - WG_NST : 0; j < tma_issued; ++j)
+      mbar_wait(&full[j % WG_NST], (j / WG_NST) & 1, 1u << 20);
+    if (mma_issued > 0) {
+      const int j = mma_issued - 1;
+      mbar_wait(&empty[j % WG_NST], (j / WG_NST) & 1, 1u << 20);
+    }
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // Sum the 64x64-layer partials over chunks in fixed order into gw [co][ci][tap] and gb.
@@ -733,12 +797,14 @@ EncodeTiledFn get_encode() {
 }
 
 // Tensor map over a BF16 [B][H][W][64] activation; box 8 ch x 130 px x 3 rows x 1 slice.
-int make_act_map(CUtensorMap* m, const void* base, int B, int H, int W) {
+// 4-D map {channel, pixel, row, slice} of a channels-last BF16 tensor, 128-byte swizzle; boxes of
+// box_px pixels x box_rows rows (the convolution halo by default).
+int make_act_map(CUtensorMap* m, const void* base, int B, int H, int W, int box_px = HALO_W, int box_rows = 3) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return SENSE_ECUDA;
   const cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
   const cuuint64_t strides[3] = {(cuuint64_t)CH * 2, (cuuint64_t)W * CH * 2, (cuuint64_t)H * W * CH * 2};
-  const cuuint32_t box[4] = {CH, HALO_W, 3, 1};
+  const cuuint32_t box[4] = {CH, (cuuint32_t)box_px, (cuuint32_t)box_rows, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
                          es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -763,6 +829,8 @@ int conv_prepare() {
                                   ConvLayout<64>::SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_conv64<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   ConvLayout<16>::SMEM) == cudaSuccess &&
+             cudaFuncSetAttribute(k_wgrad64, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM) ==
+                 cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, wl1_smem(kMaxW)) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l5, cudaFuncAttributeMaxDynamicSharedMemorySize, wl5_smem(kMaxW)) ==
@@ -799,6 +867,26 @@ int launch_conv64(const __nv_bfloat16* in, const __nv_bfloat16* wpack, const flo
 
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
+// Weight gradient of a 64 -> 64 layer into per-CTA partial sums (at most max_parts CTAs).
+int launch_wgrad64(const __nv_bfloat16* g, const __nv_bfloat16* act, float* partial, int max_parts, int B, int H,
+                   int W, int* status, cudaStream_t st, int* nparts) {
+  CUtensorMap amap, gmap;
+  if (int e = make_act_map(&amap, act, B, H, W, WG_ROWPX, 3)) return e;
+  if (int e = make_act_map(&gmap, g, B, H, W, WG_SEG, 1)) return e;
+  WgArgs a;
+  a.B = B; a.H = H; a.W = W; a.nseg = (W + WG_SEG - 1) / WG_SEG;
+  a.items = B * H * a.nseg;
+  a.partial = partial; a.status = status;
+  int grid = a.items < g_num_sms ? a.items : g_num_sms;
+  if (grid > max_parts) grid = max_parts;
+  *nparts = grid;
+  prof_mark("wgrad64", st, false);
+  k_wgrad64<<<grid, WG_THREADS, WG_SMEM, st>>>(amap, gmap, a);
+  prof_mark("wgrad64", st, true);
+  prof_count(1);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
 struct DnLayout {
   size_t wf[3], wd[3], ts[2], act[4], g[2], part_small, part64, status, total;
   int nch_small, nch64;
@@ -808,7 +896,7 @@ DnLayout dn_layout(int B, int H, int W) {
   DnLayout L;
   const size_t act = up256((size_t)B * H * W * CH * 2);
   L.nch_small = B * H;
-  L.nch64 = B * ((H + kW64Rows - 1) / kW64Rows);
+  L.nch64 = std::min(B * H * ((W + WG_SEG - 1) / WG_SEG), kWgMaxParts);
   size_t o = 0;
   for (int i = 0; i < 3; ++i) { L.wf[i] = o; o += up256(WPACK_BYTES); }
   for (int i = 0; i < 3; ++i) { L.wd[i] = o; o += up256(WPACK_BYTES); }
@@ -953,12 +1041,10 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   int cur = 0;
   for (int l = 2; l >= 0; --l) {
     const __nv_bfloat16* ain = act[l];  // input activation of this layer
-    dim3 gw(L.nch64, 3);
-    prof_mark("wgrad64", st, false);
-    k_wgrad64<<<gw, 256, 0, st>>>(B, H, W, gbuf[cur], ain, p64);
-    prof_mark("wgrad64", st, true);
+    int nparts = 0;
+    if (int e = launch_wgrad64(gbuf[cur], ain, p64, L.nch64, B, H, W, status, st, &nparts)) return e;
     prof_mark("dn_reduce", st, false);
-    k_reduce_wgrad64<<<(CH * CH * 9 + CH + 31) / 32, 256, 0, st>>>(p64, L.nch64, grad_weights + o.w[l + 1],
+    k_reduce_wgrad64<<<(CH * CH * 9 + CH + 31) / 32, 256, 0, st>>>(p64, nparts, grad_weights + o.w[l + 1],
                                                                      grad_weights + o.b[l + 1]);
     prof_mark("dn_reduce", st, true);
     if (int e = launch_conv64(gbuf[cur], reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), nullptr, ain,
@@ -979,7 +1065,7 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   if (int e = launch_conv64(gbuf[cur], reinterpret_cast<const __nv_bfloat16*>(w8 + L.ts[1]), nullptr, nullptr,
                             nullptr, 3, B, H, W, status, st, go, static_cast<float2*>(grad_x)))
     return e;
-  prof_count(11);  // every launch of the backward except the tensor-core convolutions
+  prof_count(8);  // every launch of the backward except the tensor-core kernels
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 

@@ -99,10 +99,24 @@ SENSE_D uint64_t umma_desc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
+// Descriptor for an MN-major operand with the 128-byte swizzle: each 128-byte row holds 64
+// consecutive M (or N) elements of one K index, rows of consecutive K at 128 bytes, 8-row groups
+// at the stride byte offset (1024), 64-element M/N blocks at the leading byte offset (lbo).
+SENSE_D uint64_t umma_desc_mn_sw128(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
 // Instruction descriptor of kind::f16 with BF16 A/B, FP32 D, both K-major.
 SENSE_HD uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// The same with both A and B MN-major (transpose bits 15 and 16).
+SENSE_HD uint32_t umma_idesc_bf16_mn(int M, int N) { return umma_idesc_bf16(M, N) | (1u << 15) | (1u << 16); }
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
 SENSE_D void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
   asm volatile(

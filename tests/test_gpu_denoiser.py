@@ -141,7 +141,7 @@ def test_backward_deterministic_accumulating_and_reusing_forward():
     assert dn.status() == 0
 
 
-@pytest.mark.parametrize("shape", [(2, 12, 150), (2, 20, 232), (1, 8, 136)])
+@pytest.mark.parametrize("shape", [(2, 12, 150), (2, 20, 232), (1, 8, 136), (1, 5, 300)])
 def test_backward_per_layer_from_gpu_buffers(shape):
     """Each reverse-mode stage against the oracle fed the GPU's own stored
     activations and gradient buffers: only FP32-vs-FP64 summation differs
