@@ -54,7 +54,7 @@ NCU_TRAFFIC = {
 # kernel groups the library times with CUDA events when profiling is on
 PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
                   "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc", "vn_K", "vn_Kbwd", "vn_KT",
-                  "vn_wgrad", "vn_rbfgrad", "vn_misc", "toeplitz")
+                  "vn_wgrad", "vn_rbfgrad", "vn_misc", "toeplitz", "adjoint_lines")
 
 
 # ------------------------------------------------------------------ clocks

@@ -47,8 +47,7 @@ struct RowArgs {
 __device__ void finalize(const RowArgs& a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int b = warp; b < a.B; b += nwarps) {
-    double s = 0.0;
-    for (int i = lane; i < a.H; i += 32) s += __ldcg(a.part + (size_t)b * a.H + i);
+    double s = lane_strided_sum(a.part + (size_t)b * a.H, a.H, lane);
     s = warp_sum_d(s);
     if (lane != 0) continue;
     if (a.fin == FIN_RR0) {

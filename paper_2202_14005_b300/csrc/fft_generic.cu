@@ -194,25 +194,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_expand(int B, int S, int C,
 //   mode 1 (adjoint):  dst = (-1)^h (-1)^{H/2}/sqrt(H) IDFT_H((-1)^{kh} M src)
 //   mode 2 (normal):   dst = IDFT_H(m2s DFT_H(src))   (m2s: mask^2/(HW), plain order)
 // mask: modes 0/1 the centred mask ([W] if lines else [H][W]); mode 2 shifted mask^2.
+// cols (optional): transform only the ncols listed columns (mode 1 with a line mask: the sampled
+// ones; the other columns of dst are left untouched).
 template <int CLS>
 __global__ void __launch_bounds__(kThreads, 2) k_col(int W, const float2* src, float2* dst,
                                                   Fft1DDev f, const float* mask, int lines,
-                                                  int mode) {
+                                                  int mode, const int* cols, int ncols) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = f.L, ld = H + 1;
   float2* a = reinterpret_cast<float2*>(smem);
   float2* bb = a + kCols * ld;
   const int bc = blockIdx.y;
   const int w0 = blockIdx.x * kCols;
-  const int nc = min(kCols, W - w0);
+  const int nc = min(kCols, (cols ? ncols : W) - w0);
   const size_t base = (size_t)bc * H * W;
+  auto colw = [&](int cc) { return cols ? cols[w0 + cc] : w0 + cc; };
   for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
     const int h = i / kCols, cc = i - h * kCols;
     float2 v = make_float2(0.f, 0.f);
     if (cc < nc) {
-      v = src[base + (size_t)h * W + w0 + cc];
+      v = src[base + (size_t)h * W + colw(cc)];
       if (mode == 1) {
-        const int w = w0 + cc;
+        const int w = colw(cc);
         const float m = lines ? mask[w] : mask[(size_t)h * W + w];
         v = cscale(v, m * pm1(h));
       }
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_col(int W, const float2* src, f
       float2* other = (res == a) ? bb : a;
       for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
         const int cc = i / H, k = i - cc * H;
-        const int w = w0 + cc;
+        const int w = colw(cc < nc ? cc : 0);
         float m = 0.f;
         if (cc < nc) m = lines ? mask[w] : mask[(size_t)k * W + w];
         res[cc * ld + k] = cscale(res[cc * ld + k], m);
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_col(int W, const float2* src, f
     const int h = i / kCols, cc = i - h * kCols;
     if (cc >= nc) continue;
     float2 v = res[cc * ld + h];
-    const int w = w0 + cc;
+    const int w = colw(cc);
     if (mode == 0) {
       const float m = lines ? mask[w] : mask[(size_t)h * W + w];
       v = cscale(v, sc * pm1(h) * m);
@@ -648,17 +651,29 @@ int launch_forward_generic(sense_plan p, const float2* x, float2* y) {
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
   SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, y, y, dev(p->fH), p->mask,
-                   p->mask_is_lines, 0);
+                   p->mask_is_lines, 0, nullptr, 0);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
 int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
+  if (p->lines.ok && p->lines.ncols > 0) {
+    // line mask: column transforms of the sampled columns only, then the fused pruned row pass
+    const dim3 gc((p->lines.ncols + kCols - 1) / kCols, p->B * p->C);
+    prof_mark("adjoint_lines", p->stream, false);
+    SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, y, p->w.T, dev(p->fH),
+                     p->mask, p->mask_is_lines, 1, p->lines.cols, p->lines.ncols);
+    prof_mark("adjoint_lines", p->stream, true);
+    count_launch(p, 1);
+    NormalLaunch L;
+    L.mode = NM_ADJ; L.x = p->w.T; L.out = x;
+    return launch_normal_lines(p, L);
+  }
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
   SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, y, p->w.T, dev(p->fH),
-                   p->mask, p->mask_is_lines, 1);
+                   p->mask, p->mask_is_lines, 1, nullptr, 0);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 1);
   return launch_row_combine(p, x, 1, nullptr, 0.f, nullptr);
@@ -675,7 +690,7 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
   const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
   SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, p->w.T, p->w.T, dev(p->fH),
-                   p->mask2s, p->mask_is_lines, 2);
+                   p->mask2s, p->mask_is_lines, 2, nullptr, 0);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
   return launch_row_combine(p, out, 2, x, lam_host, lam_dev);

@@ -49,7 +49,10 @@ int build_lines_tables(sense_plan pl) {
   if (kstride % 2 == 0) kstride += 1;  // odd quad stride spreads k1 rows over banks
   std::vector<float4> coef((size_t)Q * kstride, make_float4(0, 0, 0, 0));
   std::vector<float2> tw((size_t)Q * P);
-  std::vector<float> wt((size_t)Q * J, 0.f), sgn((size_t)Q * J, 0.f);
+  std::vector<float> wt((size_t)Q * J, 0.f), sgn((size_t)Q * J, 0.f), af((size_t)Q * J, 0.f);
+  std::vector<int> akx((size_t)Q * J, 0), cols;
+  for (int kx = 0; kx < W; ++kx)
+    if (pl->mask_h[kx] != 0.f) cols.push_back(kx);
   const double twopi = 2.0 * M_PI;
   for (int k1 = 0; k1 < Q; ++k1) {
     for (int t = 0; t < P; ++t) {
@@ -61,6 +64,9 @@ int build_lines_tables(sense_plan pl) {
       const double m = mplain[k1 + Q * k2];
       wt[(size_t)k1 * J + j] = (float)(m * m / W);
       sgn[(size_t)k1 * J + j] = (k2 & 1) ? -1.f : 1.f;
+      const int k = k1 + Q * k2;  // plain frequency; its centred column is (k + W/2) mod W
+      akx[(size_t)k1 * J + j] = (k + W / 2) % W;
+      af[(size_t)k1 * J + j] = (float)(((k & 1) ? -1.0 : 1.0) / std::sqrt((double)W));
       for (int q = 0; q < RQ; ++q) {
         const int t = 2 * q + 1;
         float4 v = make_float4(0, 0, 0, 0);
@@ -87,16 +93,26 @@ int build_lines_tables(sense_plan pl) {
 
   const size_t bc = coef.size() * sizeof(float4), bt = tw.size() * sizeof(float2);
   const size_t bw = wt.size() * sizeof(float), bs = sgn.size() * sizeof(float);
+  const size_t bk = akx.size() * sizeof(int), bf = af.size() * sizeof(float);
+  const size_t bl = std::max<size_t>(cols.size(), 1) * sizeof(int);
   char* d = nullptr;
-  if (cudaMalloc(&d, bc + bt + bw + bs + 64) != cudaSuccess) return SENSE_ECUDA;
+  if (cudaMalloc(&d, bc + bt + bw + bs + bk + bf + bl + 64) != cudaSuccess) return SENSE_ECUDA;
   T.coef = reinterpret_cast<float4*>(d);
   T.tw = reinterpret_cast<float2*>(d + bc);
   T.wt = reinterpret_cast<float*>(d + bc + bt);
   T.sgn = reinterpret_cast<float*>(d + bc + bt + bw);
+  T.akx = reinterpret_cast<int*>(d + bc + bt + bw + bs);
+  T.af = reinterpret_cast<float*>(d + bc + bt + bw + bs + bk);
+  T.cols = reinterpret_cast<int*>(d + bc + bt + bw + bs + bk + bf);
+  T.ncols = (int)cols.size();
   if (cudaMemcpy(T.coef, coef.data(), bc, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(T.tw, tw.data(), bt, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(T.wt, wt.data(), bw, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(T.sgn, sgn.data(), bs, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(T.sgn, sgn.data(), bs, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(T.akx, akx.data(), bk, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(T.af, af.data(), bf, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (T.ncols > 0 && cudaMemcpy(T.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                          cudaSuccess)) {
     cudaFree(d);
     T = LinesTables();
     return SENSE_ECUDA;
@@ -104,7 +120,7 @@ int build_lines_tables(sense_plan pl) {
   T.Q = Q; T.P = P; T.J = J; T.JMAX = JMAX; T.kstride = kstride;
   T.rows = rows; T.nwr = nwr; T.threads = nwarps * 32; T.smem = Lo.total;
   int maxb = 0;
-  for (int mode = 0; mode < 3; ++mode) {
+  for (int mode = 0; mode < 4; ++mode) {
     NLKernel k = pick_kernel(Q, P, JMAX, mode, pl->S);
     if (!k) return SENSE_OK;  // no fused kernel for this (Q, P, sets): generic path
     int nb = 0;
@@ -136,15 +152,16 @@ int launch_normal_lines(sense_plan pl, const NormalLaunch& L) {
   a.rows = T.rows; a.nwr = T.nwr;
   a.tiles_per_slice = (pl->H + T.rows - 1) / T.rows;
   a.ntiles = pl->B * a.tiles_per_slice;
-  a.maps = pl->maps; a.coef = T.coef; a.tw = T.tw; a.wt = T.wt; a.sgn = T.sgn;
+  a.maps = pl->maps; a.coef = T.coef; a.tw = T.tw; a.wt = T.wt; a.sgn = T.sgn; a.akx = T.akx; a.af = T.af;
   a.x = L.x; a.pold = L.pold; a.pout = L.pout; a.out = L.out; a.rhs = L.rhs;
   a.lam_host = L.lam_host; a.lam_dev = L.lam_dev;
   a.beta = L.beta; a.part = L.part; a.finalize = L.finalize;
   a.rr = pl->w.rr; a.alpha = pl->w.alpha; a.rr_hist_row = L.rr_hist_row;
   a.counter = pl->w.counter; a.status = pl->status;
-  prof_mark("normal_lines", pl->stream, false);
+  const char* group = L.mode == NM_ADJ ? "adjoint_lines" : "normal_lines";
+  prof_mark(group, pl->stream, false);
   k<<<T.grid, T.threads, T.smem, pl->stream>>>(a);
-  prof_mark("normal_lines", pl->stream, true);
+  prof_mark(group, pl->stream, true);
   count_launch(pl);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

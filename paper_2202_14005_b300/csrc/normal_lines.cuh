@@ -38,7 +38,9 @@ struct NLArgs {
   const float2* tw;
   const float* wt;
   const float* sgn;
-  const float2* x;
+  const int* akx;   // NM_ADJ: centred column of slot (k1, j)
+  const float* af;  // NM_ADJ: slot factor (-1)^k / sqrt(W)
+  const float2* x;  // NM_ADJ: column-transformed k-space T [B][C][H][W]
   const float2* pold;
   float2* pout;
   float2* out;
@@ -76,8 +78,7 @@ SENSE_HD NLLayout nl_layout(int Q, int P, int J, int kstride, int rows, int nwar
 __device__ inline void nl_finalize(const NLArgs& a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int b = warp; b < a.B; b += nwarps) {
-    double s = 0.0;
-    for (int i = lane; i < a.HS; i += 32) s += __ldcg(a.part + (size_t)b * a.HS + i);
+    double s = lane_strided_sum(a.part + (size_t)b * a.HS, a.HS, lane);
     s = warp_sum_d(s);
     if (lane != 0) continue;
     if (a.finalize == 1) {  // alpha = ||r||^2 / Re<p, S p>
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
 
     // ---- stage the input rows of every set (CG: p = r + beta p_old, written back)
 #pragma unroll
-    for (int st = 0; st < NS; ++st) {
+    for (int st = 0; st < (MODE == NM_ADJ ? 0 : NS); ++st) {
       const size_t img0 = (((size_t)b * NS + st) * a.H + h0) * W;
       const int n4 = nrows * W / 2;
       const float4* src = reinterpret_cast<const float4*>(a.x + img0);
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
 
       // ---- phase A: expand, Q-point DFT, twiddle
 #pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
+      for (int pass = 0; pass < (MODE == NM_ADJ ? 0 : NPASS); ++pass) {
         const int ga = lane / P, t = lane - ga * P;
         const int gi = pass * GA + ga;
         const int c = cgp * GB + gi;
@@ -229,10 +230,22 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
         const float4* crow = s_coef + k1 * a.kstride;
         const float* wrow_ = s_wt + k1 * J;
         const float* srow_ = s_sgn + k1 * J;
+        float2 X[JMAX];
+        if constexpr (MODE == NM_ADJ) {
+          // the sampled frequencies k = k1 + Q k2 of this lane's coil row, (-1)^k / sqrt(W) applied
+          const int c = cgp * GB + gi;
+          const float2* trow = a.x + (((size_t)b * a.C + (c < a.C ? c : 0)) * a.H + h) * W;
+          const int* kx = a.akx + k1 * J;
+          const float* fk = a.af + k1 * J;
+#pragma unroll
+          for (int j = 0; j < JMAX; ++j) {
+            X[j] = make_float2(0.f, 0.f);
+            if (j < J && c < a.C) X[j] = cscale(__ldg(trow + kx[j]), fk[j]);
+          }
+        } else {
         const float2 Y0 = col[0];
         float2 Ym = make_float2(0.f, 0.f);
         if (EVENP) Ym = col[P / 2];
-        float2 X[JMAX];
 #pragma unroll
         for (int j = 0; j < JMAX; ++j) {
           X[j] = Y0;
@@ -266,11 +279,12 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
             }
           }
         }
+        }
         float2 Z0 = make_float2(0.f, 0.f), Zm = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < JMAX; ++j) {
           if (j < J) {
-            X[j] = cscale(X[j], wrow_[j]);
+            if (MODE != NM_ADJ) X[j] = cscale(X[j], wrow_[j]);
             Z0 = cadd(Z0, X[j]);
             if (EVENP) {
               const float sg = srow_[j];
@@ -359,6 +373,10 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
 #pragma unroll
           for (int ga = 0; ga < GA; ++ga) s = cadd(s, yb[ga * W + n]);
         }
+        if (MODE == NM_ADJ) {
+          orow[n] = s;
+          continue;
+        }
         const float2 xv = xr[n];
         float2 o = make_float2(fmaf(lam, xv.x, s.x), fmaf(lam, xv.y, s.y));
         if (MODE == NM_RESID) {
@@ -369,7 +387,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
         }
         orow[n] = o;
       }
-      if (a.part) {
+      if (MODE != NM_ADJ && a.part) {
         const double d = warp_sum_d((double)part);
         if (lane == 0) a.part[(size_t)b * a.HS + st * a.H + h] = d;
       }
@@ -386,7 +404,8 @@ NLKernel pick_mode(int mode) {
   switch (mode) {
     case NM_PLAIN: return k_normal_lines<Q, P, JMAX, NM_PLAIN, NS>;
     case NM_CG: return k_normal_lines<Q, P, JMAX, NM_CG, NS>;
-    default: return k_normal_lines<Q, P, JMAX, NM_RESID, NS>;
+    case NM_RESID: return k_normal_lines<Q, P, JMAX, NM_RESID, NS>;
+    default: return k_normal_lines<Q, P, JMAX, NM_ADJ, NS>;
   }
 }
 

@@ -27,6 +27,10 @@ struct LinesTables {
   float2* tw = nullptr;    // [Q][P] e^{-2 pi i t k1 / W}
   float* wt = nullptr;     // [Q][J] mask^2 / W per slot (0 = padding)
   float* sgn = nullptr;    // [Q][J] (-1)^{k2} (even P only)
+  int* akx = nullptr;      // [Q][J] adjoint: centred column index (k + W/2) mod W of slot (k1, j)
+  float* af = nullptr;     // [Q][J] adjoint: (-1)^k / sqrt(W) per slot (0 = padding)
+  int* cols = nullptr;     // sampled columns (centred index), ncols of them
+  int ncols = 0;
 };
 
 // Scratch carved from the caller's workspace.
@@ -77,7 +81,9 @@ inline void count_launch(sense_plan, int n = 1) { prof_count(n); }
 
 // --------------------------------------------------------------- launchers
 // Modes of the fused line-mask normal-operator kernel.
-enum NormalMode { NM_PLAIN = 0, NM_CG = 1, NM_RESID = 2 };
+// NM_ADJ is the adjoint's row pass: x = sum_c conj(S_c) IDFT_W(T_c) from the sampled columns of
+// the column-transformed k-space T (no phase A, no forward half of phase B).
+enum NormalMode { NM_PLAIN = 0, NM_CG = 1, NM_RESID = 2, NM_ADJ = 3 };
 
 struct NormalLaunch {
   int mode = NM_PLAIN;

@@ -62,8 +62,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_mse(int rows, int W, const floa
   if (!s_last) return;
   __threadfence();
   if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int i = lane; i < rows; i += 32) t += __ldcg(part + i);
+    double t = lane_strided_sum(part, rows, lane);
     t = warp_sum_d(t);
     if (lane == 0) {
       loss[0] = t * inv_n;
