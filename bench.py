@@ -54,7 +54,7 @@ NCU_TRAFFIC = {
 # kernel groups the library times with CUDA events when profiling is on
 PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
                   "dn_wgrad_small", "dn_reduce", "dn_pack", "unrolled_misc", "vn_K", "vn_Kbwd", "vn_KT",
-                  "vn_wgrad", "vn_rbfgrad", "vn_misc", "toeplitz", "adjoint_lines")
+                  "vn_wgrad", "vn_rbfgrad", "vn_misc", "toeplitz", "adjoint_lines", "cg_lines")
 
 
 # ------------------------------------------------------------------ clocks
@@ -301,10 +301,13 @@ def run_ours(args, rank, world, local_rank):
     res["cg_sense"] = {"workload": WORKLOADS["cg_sense"], "slices_per_s": round(c2.B * world * steps_cg / (t_cg * 1e-3), 1),
                        "ms_per_step": round(t_cg / steps_cg, 4), "nrmse": round(nrmse_cg, 5)}
 
+    cg_bytes = None  # algorithmic bytes of one whole-solve CG launch (line-mask workloads)
     if args.workload == "cg_sense":
         cfg, B, t_ms, prof, launches, steps = c2, c2.B, t_cg, prof_cg, launches_cg, steps_cg
-        iters_per = (c2.C + 3) + (c2.C + 3) + (c2.cg_iters - 1) * (c2.C + 4)
-        normal_bytes = 8 * N * c2.B * iters_per / (c2.cg_iters + 1)
+        # initial residual (normal operator, maps + x + rhs + out) and the one-launch CG solve:
+        # per iteration the normal operator (maps, r, p_old, p, q) and the update (p, q, x, r; x, r)
+        normal_bytes = 8 * N * c2.B * (c2.C + 3)
+        cg_bytes = 8 * N * c2.B * ((c2.C + 3) + (c2.cg_iters - 1) * (c2.C + 4) + 6 * c2.cg_iters)
         # e2e through host buffers: k-space and maps in, reconstruction out
         y_h, maps_h = y2.cpu().pin_memory(), maps2.cpu().pin_memory()
         out_h = torch.empty(x2.shape, dtype=x2.dtype).pin_memory()
@@ -456,8 +459,8 @@ def run_ours(args, rank, world, local_rank):
         assert tr.plan.status() == 0 and tr.dn.status() == 0
         B = c3.B
         N3 = c3.H * c3.W
-        iters_per = (c3.C + 3) + (c3.cg_iters - 1) * (c3.C + 4)
-        normal_bytes = 8 * N3 * B * iters_per / c3.cg_iters
+        normal_bytes = 8 * N3 * B * (c3.C + 3)
+        cg_bytes = 8 * N3 * B * ((c3.C + 3) + (c3.cg_iters - 1) * (c3.C + 4) + 6 * c3.cg_iters)
         y_h, maps_h, gt_h = y3.cpu().pin_memory(), maps3.cpu().pin_memory(), gt3.cpu().pin_memory()
         out_h = torch.empty(1, dtype=torch.float64).pin_memory()
         ins = [(y3, y_h), (maps3, maps_h), (gt3, gt_h)]
@@ -480,6 +483,8 @@ def run_ours(args, rank, world, local_rank):
     vn_flops = 2.0 * px * 24 * 2 * 121  # one 2<->24 channel 11x11 convolution
     kern = {
         "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks, args.workload),
+        "cg_lines": kernel_report("cg_lines", *prof["cg_lines"], ("hbm", cg_bytes), pk, clocks, args.workload)
+        if cg_bytes else None,
         "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks, args.workload),
         "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("tensor", conv_flops), pk, clocks, args.workload),
         "vn_K": kernel_report("vn_K", *prof["vn_K"], ("tensor", vn_flops), pk, clocks, args.workload),

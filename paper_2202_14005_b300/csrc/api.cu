@@ -13,7 +13,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct WsLayout {
-  size_t T, r, p, q, t0, t1, part, rr, alpha, beta, lam, counter, total;
+  size_t T, r, p, q, t0, t1, wv, sv, part, part2, rr, alpha, beta, lam, counter, total;
 };
 
 WsLayout ws_layout(const sense_plan p) {
@@ -27,7 +27,10 @@ WsLayout ws_layout(const sense_plan p) {
   L.q = o; o += up256(img);
   L.t0 = o; o += up256(img);
   L.t1 = o; o += up256(img);
+  L.wv = o; o += up256(img);
+  L.sv = o; o += up256(img);
   L.part = o; o += up256((size_t)p->B * p->S * p->H * sizeof(double));
+  L.part2 = o; o += up256(4 * (size_t)p->B * p->S * p->H * sizeof(double));  // one-launch CG: 4 sets
   L.rr = o; o += up256(p->B * sizeof(double));
   L.alpha = o; o += up256(p->B * sizeof(double));
   L.beta = o; o += up256(p->B * sizeof(double));
@@ -229,7 +232,10 @@ int sense_plan_set_workspace(sense_plan p, void* ws, size_t bytes) {
   w.q = reinterpret_cast<float2*>(b + L.q);
   w.t0 = reinterpret_cast<float2*>(b + L.t0);
   w.t1 = reinterpret_cast<float2*>(b + L.t1);
+  w.wv = reinterpret_cast<float2*>(b + L.wv);
+  w.sv = reinterpret_cast<float2*>(b + L.sv);
   w.part = reinterpret_cast<double*>(b + L.part);
+  w.part2 = reinterpret_cast<double*>(b + L.part2);
   w.rr = reinterpret_cast<double*>(b + L.rr);
   w.alpha = reinterpret_cast<double*>(b + L.alpha);
   w.beta = reinterpret_cast<double*>(b + L.beta);

@@ -264,7 +264,8 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
     prof_mark("cg_vec", p->stream, true);
     count_launch(p);
   }
-  // ---- iterations
+  // ---- iterations: all of them in one cooperative launch where the fused kernel applies
+  if (p->lines.ok && p->lines.coop && iters > 0) return launch_cg_lines(p, x, iters, rr_hist);
   for (int it = 0; it < iters; ++it) {
     double* hist = rr_hist ? rr_hist + (size_t)(it + 1) * B : nullptr;
     if (p->lines.ok) {

@@ -135,12 +135,65 @@ int build_lines_tables(sense_plan pl) {
   const int tiles = pl->B * ((pl->H + rows - 1) / rows);
   T.grid = std::min(tiles, maxb * pl->num_sms);
   T.ok = 1;
+  // the whole-solve CG kernel: all of its CTAs must be resident at once (cooperative launch).
+  // It pays off while each CTA holds at most two tiles (the tile's update traffic then sits on
+  // the CTA's own latency chain; with more tiles per CTA separate streaming launches are faster:
+  // measured on B300, 256x232, 12 coils: 4 slices 29.6 vs 36 us, 16 slices 114 vs 98 us per iteration).
+  if (pl->B <= kCoopMaxB) {
+    CgKernel ck = Q == 8 ? pick_cg_q8(P, JMAX, pl->S) : pick_cg_q16(P, JMAX, pl->S);
+    int nb = 0, coop = 0, dev = 0;
+    if (ck && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+        cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, Lo.total) == cudaSuccess &&
+        cudaFuncSetAttribute(ck, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ck, T.threads, Lo.total) == cudaSuccess && nb >= 1) {
+      const int cgrid = std::min(tiles, nb * pl->num_sms);
+      if (tiles <= 2 * cgrid) {
+        T.coop = reinterpret_cast<const void*>(ck);
+        T.coop_grid = cgrid;
+      }
+    }
+  }
   return SENSE_OK;
 }
 
 void free_lines_tables(sense_plan pl) {
   if (pl->lines.coef) cudaFree(pl->lines.coef);
   pl->lines = LinesTables();
+}
+
+int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist) {
+  const LinesTables& T = pl->lines;
+  if (!T.coop) return SENSE_EUNSUPPORTED;
+  Workspace& w = pl->w;
+  NLArgs a;
+  a.B = pl->B; a.C = pl->C; a.H = pl->H; a.HS = pl->S * pl->H; a.J = T.J; a.kstride = T.kstride;
+  a.rows = T.rows; a.nwr = T.nwr;
+  a.tiles_per_slice = (pl->H + T.rows - 1) / T.rows;
+  a.ntiles = pl->B * a.tiles_per_slice;
+  a.maps = pl->maps; a.coef = T.coef; a.tw = T.tw; a.wt = T.wt; a.sgn = T.sgn; a.akx = T.akx; a.af = T.af;
+  a.x = w.r; a.pold = nullptr; a.pout = w.p; a.out = w.q; a.rhs = nullptr;
+  a.lam_host = 0.f; a.lam_dev = w.lam;
+  a.beta = nullptr; a.part = w.part; a.finalize = 0;
+  a.rr = w.rr; a.alpha = w.alpha; a.rr_hist_row = nullptr;
+  a.counter = w.counter; a.status = pl->status;
+  CgCoop c;
+  c.iters = iters; c.x = x; c.r = w.r; c.p = w.p; c.s = w.sv; c.w = w.wv; c.hist = rr_hist;
+  const size_t np = (size_t)pl->B * pl->S * pl->H;
+  for (int i = 0; i < 2; ++i) {
+    c.pd[i] = w.part2 + i * np;
+    c.pg[i] = w.part2 + (2 + i) * np;
+  }
+  c.bar = w.counter + 16;  // two words of the zeroed counter block, apart from the last-block counter
+  if (cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), pl->stream) != cudaSuccess) return SENSE_ECUDA;
+  void* args[] = {&a, &c};
+  prof_mark("cg_lines", pl->stream, false);
+  const cudaError_t e = cudaLaunchCooperativeKernel(T.coop, dim3(T.coop_grid), dim3(T.threads), args,
+                                                    (size_t)T.smem, pl->stream);
+  prof_mark("cg_lines", pl->stream, true);
+  count_launch(pl);
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
 int launch_normal_lines(sense_plan pl, const NormalLaunch& L) {

@@ -40,7 +40,15 @@ struct NLArgs {
   const float* sgn;
   const int* akx;   // NM_ADJ: centred column of slot (k1, j)
   const float* af;  // NM_ADJ: slot factor (-1)^k / sqrt(W)
-  const float2* x;  // NM_ADJ: column-transformed k-space T [B][C][H][W]
+  const float2* x;  // NM_ADJ: column-transformed k-space T [B][C][H][W]; NM_CG2: r
+  // NM_CG2 (one pass of the single-reduction CG): with upd, first p = r + beta p, s = w + beta s
+  // (p = r, s = w when first), x += alpha p, r -= alpha s; then w = S r; rows of Re<r, w> to part
+  // and of ||r||^2 to part2.  alpha, beta per slice (shared memory of the solve kernel).
+  float2* sv = nullptr;
+  float2* xs = nullptr;
+  double* part2 = nullptr;
+  const double* al_s = nullptr;
+  int upd = 0, first = 0;
   const float2* pold;
   float2* pout;
   float2* out;
@@ -115,287 +123,524 @@ __device__ inline void last_block(const NLArgs& a) {
   }
 }
 
+#define NL_CONSTS                                                                          \
+  constexpr int GB = 32 / Q;          /* coils per warp in phase B */                         \
+  constexpr int GA = 32 / P;          /* coils per pass in phases A/C */                      \
+  constexpr int HP = (P - 1) / 2;     /* conjugate pairs t <-> P - t, t = 1..HP */            \
+  constexpr bool EVENP = (P % 2) == 0;                                                         \
+  constexpr int RQ = (HP + 1) / 2;    /* float4 quads per slot row */                         \
+  constexpr int W = Q * P;                                                                     \
+  constexpr int NPASS = (GB + GA - 1) / GA;                                                    \
+  static_assert(GB * Q == 32, "Q must divide 32");                                             \
+  static_assert(P <= 32 && P >= Q, "phase A needs Q <= P <= 32");                              \
+  static_assert(NS * GA <= GB, "phase C stores NS x GA rows in a warp's GB-row buffer");
+
+// Shared-memory tables and row buffers of one CTA (dynamic shared memory, nl_layout).
+struct NLSmem {
+  float4* coef;
+  float2* tw;
+  float* wt;
+  float* sgn;
+  float2* x;
+  float2* y;
+};
+
+// Carve the CTA's shared memory and load the tables (the first tile's barrier publishes them).
+template <int Q, int P, int NS>
+__device__ __forceinline__ NLSmem nl_smem_setup(const NLArgs& a) {
+  NL_CONSTS
+  (void)NPASS;
+  (void)RQ;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nthreads = blockDim.x;
+  const NLLayout Lo = nl_layout(Q, P, a.J, a.kstride, a.rows, nthreads >> 5, GB, NS);
+  NLSmem S;
+  S.coef = reinterpret_cast<float4*>(smem + Lo.coef);
+  S.tw = reinterpret_cast<float2*>(smem + Lo.tw);
+  S.wt = reinterpret_cast<float*>(smem + Lo.wt);
+  S.sgn = reinterpret_cast<float*>(smem + Lo.sgn);
+  S.x = reinterpret_cast<float2*>(smem + Lo.x);
+  S.y = reinterpret_cast<float2*>(smem + Lo.y);
+  for (int i = threadIdx.x; i < Q * a.kstride; i += nthreads) S.coef[i] = a.coef[i];
+  for (int i = threadIdx.x; i < Q * P; i += nthreads) S.tw[i] = a.tw[i];
+  for (int i = threadIdx.x; i < Q * a.J; i += nthreads) {
+    S.wt[i] = a.wt[i];
+    S.sgn[i] = EVENP ? a.sgn[i] : 0.f;
+  }
+  return S;
+}
+
+// One tile (a.rows image rows of one slice, every coil and set) of the fused operator.
+template <int Q, int P, int JMAX, int MODE, int NS>
+__device__ __forceinline__ void nl_tile(const NLArgs& a, const NLSmem& S, int tile) {
+  NL_CONSTS
+  const int nthreads = blockDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = nthreads >> 5;
+  float4* s_coef = S.coef;
+  float2* s_tw = S.tw;
+  float* s_wt = S.wt;
+  float* s_sgn = S.sgn;
+  float2* s_x = S.x;
+  float2* s_y = S.y;
+  const int J = a.J;
+  const int b = tile / a.tiles_per_slice;
+  const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
+  const int nrows = min(a.rows, a.H - h0);
+  const float lam = a.lam_dev ? (float)a.lam_dev[b] : a.lam_host;
+
+  // ---- stage the input rows of every set (CG: p = r + beta p_old, written back)
+#pragma unroll
+  for (int st = 0; st < (MODE == NM_ADJ ? 0 : NS); ++st) {
+    const size_t img0 = (((size_t)b * NS + st) * a.H + h0) * W;
+    const int n4 = nrows * W / 2;
+    const float4* src = reinterpret_cast<const float4*>(a.x + img0);
+    float4* sx4 = reinterpret_cast<float4*>(s_x + st * a.rows * W);
+    if (MODE == NM_CG2) {
+      float4* rv = reinterpret_cast<float4*>(const_cast<float2*>(a.x) + img0);
+      if (a.upd) {
+        const float be = a.first ? 0.f : (float)a.beta[b];
+        const float al = (float)a.al_s[b];
+        float4* pv = reinterpret_cast<float4*>(a.pout + img0);
+        float4* sv = reinterpret_cast<float4*>(a.sv + img0);
+        float4* xv = reinterpret_cast<float4*>(a.xs + img0);
+        const float4* wv = reinterpret_cast<const float4*>(a.out + img0);
+        for (int i = threadIdx.x; i < n4; i += nthreads) {
+          float4 r = rv[i], w = wv[i], x = xv[i];
+          float4 pp = r, ss = w;
+          if (!a.first) {
+            const float4 po = pv[i], so = sv[i];
+            pp.x = fmaf(be, po.x, r.x); pp.y = fmaf(be, po.y, r.y); pp.z = fmaf(be, po.z, r.z); pp.w = fmaf(be, po.w, r.w);
+            ss.x = fmaf(be, so.x, w.x); ss.y = fmaf(be, so.y, w.y); ss.z = fmaf(be, so.z, w.z); ss.w = fmaf(be, so.w, w.w);
+          }
+          x.x = fmaf(al, pp.x, x.x); x.y = fmaf(al, pp.y, x.y); x.z = fmaf(al, pp.z, x.z); x.w = fmaf(al, pp.w, x.w);
+          r.x = fmaf(-al, ss.x, r.x); r.y = fmaf(-al, ss.y, r.y); r.z = fmaf(-al, ss.z, r.z); r.w = fmaf(-al, ss.w, r.w);
+          pv[i] = pp;
+          sv[i] = ss;
+          xv[i] = x;
+          rv[i] = r;
+          sx4[i] = r;
+        }
+      } else {
+        for (int i = threadIdx.x; i < n4; i += nthreads) sx4[i] = rv[i];
+      }
+    } else if (MODE == NM_CG) {
+      const float be = a.pold ? (float)a.beta[b] : 0.f;
+      const float4* po = a.pold ? reinterpret_cast<const float4*>(a.pold + img0) : nullptr;
+      float4* pn = reinterpret_cast<float4*>(a.pout + img0);
+      for (int i = threadIdx.x; i < n4; i += nthreads) {
+        float4 v = src[i];
+        if (po) {
+          const float4 o = po[i];
+          v.x = fmaf(be, o.x, v.x); v.y = fmaf(be, o.y, v.y);
+          v.z = fmaf(be, o.z, v.z); v.w = fmaf(be, o.w, v.w);
+        }
+        pn[i] = v;
+        sx4[i] = v;
+      }
+    } else {
+      for (int i = threadIdx.x; i < n4; i += nthreads) sx4[i] = src[i];
+    }
+  }
+  __syncthreads();
+
+  const int wrow = warp / a.nwr, cgp = warp - wrow * a.nwr;
+  float2* ybuf = s_y + warp * (GB * W);
+  if (wrow < nrows) {
+    const int h = h0 + wrow;
+    const float2* xrow = s_x + wrow * W;  // set st: + st * rows * W
+    const float2* map0 = a.maps + ((size_t)b * NS * a.C * a.H + h) * W;
+    const size_t cstride = (size_t)a.H * W, sstride = (size_t)a.C * a.H * W;
+
+    // ---- phase A: expand, Q-point DFT, twiddle
+#pragma unroll
+    for (int pass = 0; pass < (MODE == NM_ADJ ? 0 : NPASS); ++pass) {
+      const int ga = lane / P, t = lane - ga * P;
+      const int gi = pass * GA + ga;
+      const int c = cgp * GB + gi;
+      if (ga < GA && gi < GB) {
+        float2 v[Q];
+        if (c < a.C) {
+          const float2* srow = map0 + c * cstride;
+#pragma unroll
+          for (int n1 = 0; n1 < Q; ++n1) v[n1] = cmul(__ldg(srow + t + P * n1), xrow[t + P * n1]);
+#pragma unroll
+          for (int st = 1; st < NS; ++st)
+#pragma unroll
+            for (int n1 = 0; n1 < Q; ++n1)
+              v[n1] = cfma(__ldg(srow + st * sstride + t + P * n1), xrow[st * a.rows * W + t + P * n1], v[n1]);
+        } else {
+#pragma unroll
+          for (int n1 = 0; n1 < Q; ++n1) v[n1] = make_float2(0.f, 0.f);
+        }
+        dft_pow2<Q, false>(v);
+        float2* yc = ybuf + gi * W;
+        yc[t] = v[0];
+#pragma unroll
+        for (int k1 = 1; k1 < Q; ++k1) yc[k1 * P + t] = cmul(v[k1], s_tw[k1 * P + t]);
+      }
+    }
+    __syncwarp();
+
+    // ---- phase B: pruned P-point DFT at the sampled frequencies and back.
+    // The conjugate pairs (t, P - t) are streamed from shared memory so that
+    // only the J outputs stay in registers.
+    {
+      const int gi = lane / Q, k1 = lane - gi * Q;
+      float2* col = ybuf + gi * W + k1 * P;
+      const float4* crow = s_coef + k1 * a.kstride;
+      const float* wrow_ = s_wt + k1 * J;
+      const float* srow_ = s_sgn + k1 * J;
+      float2 X[JMAX];
+      if constexpr (MODE == NM_ADJ) {
+        // the sampled frequencies k = k1 + Q k2 of this lane's coil row, (-1)^k / sqrt(W) applied
+        const int c = cgp * GB + gi;
+        const float2* trow = a.x + (((size_t)b * a.C + (c < a.C ? c : 0)) * a.H + h) * W;
+        const int* kx = a.akx + k1 * J;
+        const float* fk = a.af + k1 * J;
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+          X[j] = make_float2(0.f, 0.f);
+          if (j < J && c < a.C) X[j] = cscale(__ldg(trow + kx[j]), fk[j]);
+        }
+      } else {
+      const float2 Y0 = col[0];
+      float2 Ym = make_float2(0.f, 0.f);
+      if (EVENP) Ym = col[P / 2];
+#pragma unroll
+      for (int j = 0; j < JMAX; ++j) {
+        X[j] = Y0;
+        if (EVENP && j < J) {
+          const float sg = srow_[j];
+          X[j].x = fmaf(sg, Ym.x, X[j].x);
+          X[j].y = fmaf(sg, Ym.y, X[j].y);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const int t = 2 * q + 1;
+        const float2 u0 = col[t], w0 = col[P - t];
+        const float2 S0 = cadd(u0, w0), D0 = csub(u0, w0);
+        float2 S1 = make_float2(0.f, 0.f), D1 = S1;
+        if (t + 1 <= HP) {
+          const float2 u1 = col[t + 1], w1 = col[P - t - 1];
+          S1 = cadd(u1, w1);
+          D1 = csub(u1, w1);
+        }
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+          if (j < J) {
+            const float4 cs = crow[j * RQ + q];
+            X[j].x = fmaf(cs.x, S0.x, fmaf(cs.y, D0.y, X[j].x));
+            X[j].y = fmaf(cs.x, S0.y, fmaf(-cs.y, D0.x, X[j].y));
+            if (t + 1 <= HP) {
+              X[j].x = fmaf(cs.z, S1.x, fmaf(cs.w, D1.y, X[j].x));
+              X[j].y = fmaf(cs.z, S1.y, fmaf(-cs.w, D1.x, X[j].y));
+            }
+          }
+        }
+      }
+      }
+      float2 Z0 = make_float2(0.f, 0.f), Zm = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < JMAX; ++j) {
+        if (j < J) {
+          if (MODE != NM_ADJ) X[j] = cscale(X[j], wrow_[j]);
+          Z0 = cadd(Z0, X[j]);
+          if (EVENP) {
+            const float sg = srow_[j];
+            Zm.x = fmaf(sg, X[j].x, Zm.x);
+            Zm.y = fmaf(sg, X[j].y, Zm.y);
+          }
+        }
+      }
+      __syncwarp();  // every lane has read its column before any is overwritten
+      col[0] = Z0;
+      if (EVENP) col[P / 2] = Zm;
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const int t = 2 * q + 1;
+        float2 A0 = make_float2(0.f, 0.f), B0 = A0, A1 = A0, B1 = A0;
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j) {
+          if (j < J) {
+            const float4 cs = crow[j * RQ + q];
+            A0.x = fmaf(cs.x, X[j].x, A0.x); A0.y = fmaf(cs.x, X[j].y, A0.y);
+            B0.x = fmaf(cs.y, X[j].x, B0.x); B0.y = fmaf(cs.y, X[j].y, B0.y);
+            A1.x = fmaf(cs.z, X[j].x, A1.x); A1.y = fmaf(cs.z, X[j].y, A1.y);
+            B1.x = fmaf(cs.w, X[j].x, B1.x); B1.y = fmaf(cs.w, X[j].y, B1.y);
+          }
+        }
+        col[t] = make_float2(A0.x - B0.y, A0.y + B0.x);
+        col[P - t] = make_float2(A0.x + B0.y, A0.y - B0.x);
+        if (t + 1 <= HP) {
+          col[t + 1] = make_float2(A1.x - B1.y, A1.y + B1.x);
+          col[P - t - 1] = make_float2(A1.x + B1.y, A1.y - B1.x);
+        }
+      }
+    }
+    __syncwarp();
+
+    // ---- phase C: inverse twiddle, inverse Q-point DFT, conj-map combine (one sum per set)
+    float2 acc[NS][Q];
+#pragma unroll
+    for (int st = 0; st < NS; ++st)
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) acc[st][n1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int pass = 0; pass < NPASS; ++pass) {
+      const int ga = lane / P, t = lane - ga * P;
+      const int gi = pass * GA + ga;
+      const int c = cgp * GB + gi;
+      if (ga < GA && gi < GB && c < a.C) {
+        const float2* yc = ybuf + gi * W;
+        float2 z[Q];
+        z[0] = yc[t];
+#pragma unroll
+        for (int k1 = 1; k1 < Q; ++k1) z[k1] = cmulc(s_tw[k1 * P + t], yc[k1 * P + t]);
+        dft_pow2<Q, true>(z);
+        const float2* srow = map0 + c * cstride;
+#pragma unroll
+        for (int st = 0; st < NS; ++st)
+#pragma unroll
+          for (int n1 = 0; n1 < Q; ++n1)
+            acc[st][n1] = cfmac(__ldg(srow + st * sstride + t + P * n1), z[n1], acc[st][n1]);
+      }
+    }
+    __syncwarp();
+    if (lane < GA * P) {
+      const int ga = lane / P, t = lane - ga * P;
+#pragma unroll
+      for (int st = 0; st < NS; ++st)
+#pragma unroll
+        for (int n1 = 0; n1 < Q; ++n1) ybuf[(st * GA + ga) * W + t + P * n1] = acc[st][n1];
+    }
+  }
+  __syncthreads();
+
+  // ---- epilogue: sum coil groups in fixed order, + lambda x, row partial (per set and row)
+  for (int it = warp; it < NS * nrows; it += nwarps) {
+    const int st = it / nrows, rr = it - st * nrows;
+    const int h = h0 + rr;
+    const size_t orow0 = (((size_t)b * NS + st) * a.H + h) * W;
+    float part = 0.f, part_rr = 0.f;
+    const float2* xr = s_x + (st * a.rows + rr) * W;
+    const float2* rh = (MODE == NM_RESID) ? a.rhs + orow0 : nullptr;
+    float2* orow = a.out + orow0;
+    for (int n = lane; n < W; n += 32) {
+      float2 s = make_float2(0.f, 0.f);
+      for (int g = 0; g < a.nwr; ++g) {
+        const float2* yb = s_y + (rr * a.nwr + g) * (GB * W) + st * GA * W;
+#pragma unroll
+        for (int ga = 0; ga < GA; ++ga) s = cadd(s, yb[ga * W + n]);
+      }
+      if (MODE == NM_ADJ) {
+        orow[n] = s;
+        continue;
+      }
+      const float2 xv = xr[n];
+      float2 o = make_float2(fmaf(lam, xv.x, s.x), fmaf(lam, xv.y, s.y));
+      if (MODE == NM_RESID) {
+        o = csub(rh[n], o);
+        part = fmaf(o.x, o.x, fmaf(o.y, o.y, part));
+      } else {
+        part = fmaf(xv.x, o.x, fmaf(xv.y, o.y, part));
+        if (MODE == NM_CG2) part_rr = fmaf(xv.x, xv.x, fmaf(xv.y, xv.y, part_rr));
+      }
+      orow[n] = o;
+    }
+    if (MODE != NM_ADJ && a.part) {
+      const double d = warp_sum_d((double)part);
+      if (lane == 0) a.part[(size_t)b * a.HS + st * a.H + h] = d;
+    }
+    if (MODE == NM_CG2) {
+      const double d = warp_sum_d((double)part_rr);
+      if (lane == 0) a.part2[(size_t)b * a.HS + st * a.H + h] = d;
+    }
+  }
+  __syncthreads();
+}
+
 // NS = map sets (soft-SENSE): x, out [B][NS][H][W], maps [B][NS][C][H][W]; coil image
 // sum_s S_{s,c} x_s in phase A, one conj(S_{s,c}) accumulation per set in phase C.
 template <int Q, int P, int JMAX, int MODE, int NS>
 __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLArgs a) {
-  constexpr int GB = 32 / Q;          // coils per warp in phase B
-  constexpr int GA = 32 / P;          // coils per pass in phases A/C
-  constexpr int HP = (P - 1) / 2;     // conjugate pairs t <-> P - t, t = 1..HP
-  constexpr bool EVENP = (P % 2) == 0;
-  constexpr int RQ = (HP + 1) / 2;    // float4 quads per slot row
-  constexpr int W = Q * P;
-  constexpr int NPASS = (GB + GA - 1) / GA;
-  static_assert(GB * Q == 32, "Q must divide 32");
-  static_assert(P <= 32 && P >= Q, "phase A needs Q <= P <= 32");
-  static_assert(NS * GA <= GB, "phase C stores NS x GA rows in a warp's GB-row buffer");
+  const NLSmem S = nl_smem_setup<Q, P, NS>(a);
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) nl_tile<Q, P, JMAX, MODE, NS>(a, S, tile);
+  if (a.finalize) last_block(a);
+}
 
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int nthreads = blockDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = nthreads >> 5;
-  const NLLayout Lo = nl_layout(Q, P, a.J, a.kstride, a.rows, nwarps, GB, NS);
-  float4* s_coef = reinterpret_cast<float4*>(smem + Lo.coef);
-  float2* s_tw = reinterpret_cast<float2*>(smem + Lo.tw);
-  float* s_wt = reinterpret_cast<float*>(smem + Lo.wt);
-  float* s_sgn = reinterpret_cast<float*>(smem + Lo.sgn);
-  float2* s_x = reinterpret_cast<float2*>(smem + Lo.x);
-  float2* s_y = reinterpret_cast<float2*>(smem + Lo.y);
+// ------------------------------------------------------- whole CG solve in one launch
+// Cooperative persistent kernel running every iteration of CG on S = A^H A + lambda I with one
+// global reduction per iteration: the Chronopoulos-Gear form of the recurrence, which produces
+// the iterates of the textbook (Hestenes-Stiefel) CG in exact arithmetic.  It keeps w = S r and
+// s = S p (s_k = w_k + beta_{k-1} s_{k-1}) and obtains Re<p_k, S p_k> from the two inner
+// products of one pass, gamma_k = ||r_k||^2 and delta_k = Re<r_k, w_k>:
+//   beta_{k-1} = gamma_k / gamma_{k-1},  alpha_k = gamma_k / (delta_k - beta_{k-1} gamma_k / alpha_{k-1})
+// (alpha_0 = gamma_0 / delta_0), using the orthogonality of the residuals.  Pass k (k < iters):
+// staging p, s, x, r of iteration k - 1 (k >= 1), w = S r through the fused operator, row
+// partials of delta and gamma; barrier; every CTA forms beta and alpha per slice from all row
+// partials in fixed order (identical in every CTA).  A last pass makes the update of iteration
+// iters - 1 and gamma for the residual history.  Each CTA keeps the same row tiles throughout,
+// so only the row partials cross CTAs.  The grid barrier is a counter and a generation word in
+// global memory; the launch is cooperative (all CTAs resident), and every wait is bounded: a CTA
+// that gives up sets SENSE_STATUS_DEVICE_TIMEOUT and returns.
+constexpr int kCoopMaxB = 16;  // slices per solve on this path (3 x 16 FP64 scalars in static shared
+                               // memory: small enough to keep the CTAs per SM of the operator kernel)
 
-  for (int i = threadIdx.x; i < Q * a.kstride; i += nthreads) s_coef[i] = a.coef[i];
-  for (int i = threadIdx.x; i < Q * P; i += nthreads) s_tw[i] = a.tw[i];
-  for (int i = threadIdx.x; i < Q * a.J; i += nthreads) {
-    s_wt[i] = a.wt[i];
-    s_sgn[i] = EVENP ? a.sgn[i] : 0.f;
+struct CgCoop {
+  int iters;
+  float2* x;        // solution, updated in place
+  float2* r;        // residual (initial residual on entry)
+  float2* p;
+  float2* s;        // S p
+  float2* w;        // S r
+  double* hist;     // [iters + 1][B] squared residual norms (row 0 by the caller) or NULL
+  unsigned* bar;    // {arrival count, generation}, count zero between barriers
+  // row partials of delta and gamma, two buffers each used by alternate passes: a CTA may start
+  // writing pass k + 1 while others still read pass k (it cannot get further ahead than that)
+  double* pd[2];
+  double* pg[2];
+};
+
+__device__ __forceinline__ bool coop_barrier(unsigned* bar) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    int ok = 1;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned n = 0;
+      while (*gen == g0) {
+        if (++n > (1u << 22)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
   }
+  __syncthreads();
+  return s_ok != 0;
+}
 
-  const int J = a.J;
+// Scalars of pass k from the row partials (delta in part, gamma in part2).  g_prev / a_prev hold
+// gamma_{k-1} / alpha_{k-1} and take gamma_k / alpha_k; beta receives beta_{k-1}.  A slice whose
+// gamma is zero (or whose previous alpha is zero) is frozen: alpha = beta = 0.  With
+// only_gamma the pass made the last update: gamma is recorded, no new alpha.  Block 0 alone
+// records status bits, the history row and the global ||r||^2.
+__device__ __forceinline__ void coop_scalars(const NLArgs& a, int k, bool only_gamma, double* g_prev,
+                                             double* a_prev, double* beta, double* hist) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const bool rec = blockIdx.x == 0;
+  for (int b = warp; b < a.B; b += nwarps) {
+    double g = lane_strided_sum(a.part2 + (size_t)b * a.HS, a.HS, lane);
+    g = warp_sum_d(g);
+    double d = 0.0;
+    if (!only_gamma) {
+      d = lane_strided_sum(a.part + (size_t)b * a.HS, a.HS, lane);
+      d = warp_sum_d(d);
+    }
+    if (lane != 0) continue;
+    const bool fin = isfinite(g) && isfinite(d);
+    if (!fin && rec) set_status(a.status, SENSE_DEVST_NONFINITE);
+    const double gp = g_prev[b], ap = a_prev[b];
+    double be = 0.0, al = 0.0;
+    if (fin && g > 0.0 && (k == 0 || (gp > 0.0 && ap != 0.0))) {
+      be = k == 0 ? 0.0 : g / gp;
+      if (!only_gamma) {
+        const double den = k == 0 ? d : d - be * g / ap;
+        if (den > 0.0) al = g / den;
+        else if (rec) set_status(a.status, SENSE_DEVST_CG_BREAKDOWN);
+      }
+    }
+    beta[b] = be;
+    a_prev[b] = al;
+    g_prev[b] = g;
+    if (rec) {
+      a.rr[b] = g;
+      a.alpha[b] = al;
+      if (hist && k > 0) hist[b] = g;
+    }
+  }
+}
+
+template <int Q, int P, int JMAX, int NS>
+__global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs a0, const CgCoop c) {
+  constexpr int W = Q * P;
+  __shared__ double s_g[kCoopMaxB], s_alpha[kCoopMaxB], s_beta[kCoopMaxB];
+  const NLSmem S = nl_smem_setup<Q, P, NS>(a0);
+  const int nthreads = blockDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = nthreads >> 5;
+  for (int b = threadIdx.x; b < a0.B; b += nthreads) s_g[b] = s_alpha[b] = s_beta[b] = 0.0;
+  __syncthreads();
+  NLArgs a = a0;
+  a.x = c.r; a.out = c.w; a.pout = c.p; a.sv = c.s; a.xs = c.x; a.beta = s_beta; a.al_s = s_alpha;
+  a.finalize = 0;
+  for (int k = 0; k < c.iters; ++k) {
+    a.upd = k > 0;
+    a.first = k == 1;
+    a.part = c.pd[k & 1];
+    a.part2 = c.pg[k & 1];
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);
+    if (!coop_barrier(c.bar)) {
+      if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
+      return;
+    }
+    coop_scalars(a, k, false, s_g, s_alpha, s_beta, c.hist ? c.hist + (size_t)k * a.B : nullptr);
+    __syncthreads();
+  }
+  // last update (iteration iters - 1) and gamma of the final residual; one warp per row
+  const bool first = c.iters == 1;
+  a.part2 = c.pg[c.iters & 1];
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int b = tile / a.tiles_per_slice;
     const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
     const int nrows = min(a.rows, a.H - h0);
-    const float lam = a.lam_dev ? (float)a.lam_dev[b] : a.lam_host;
-
-    // ---- stage the input rows of every set (CG: p = r + beta p_old, written back)
-#pragma unroll
-    for (int st = 0; st < (MODE == NM_ADJ ? 0 : NS); ++st) {
-      const size_t img0 = (((size_t)b * NS + st) * a.H + h0) * W;
-      const int n4 = nrows * W / 2;
-      const float4* src = reinterpret_cast<const float4*>(a.x + img0);
-      float4* sx4 = reinterpret_cast<float4*>(s_x + st * a.rows * W);
-      if (MODE == NM_CG) {
-        const float be = a.pold ? (float)a.beta[b] : 0.f;
-        const float4* po = a.pold ? reinterpret_cast<const float4*>(a.pold + img0) : nullptr;
-        float4* pn = reinterpret_cast<float4*>(a.pout + img0);
-        for (int i = threadIdx.x; i < n4; i += nthreads) {
-          float4 v = src[i];
-          if (po) {
-            const float4 o = po[i];
-            v.x = fmaf(be, o.x, v.x); v.y = fmaf(be, o.y, v.y);
-            v.z = fmaf(be, o.z, v.z); v.w = fmaf(be, o.w, v.w);
-          }
-          pn[i] = v;
-          sx4[i] = v;
-        }
-      } else {
-        for (int i = threadIdx.x; i < n4; i += nthreads) sx4[i] = src[i];
-      }
-    }
-    __syncthreads();
-
-    const int wrow = warp / a.nwr, cgp = warp - wrow * a.nwr;
-    float2* ybuf = s_y + warp * (GB * W);
-    if (wrow < nrows) {
-      const int h = h0 + wrow;
-      const float2* xrow = s_x + wrow * W;  // set st: + st * rows * W
-      const float2* map0 = a.maps + ((size_t)b * NS * a.C * a.H + h) * W;
-      const size_t cstride = (size_t)a.H * W, sstride = (size_t)a.C * a.H * W;
-
-      // ---- phase A: expand, Q-point DFT, twiddle
-#pragma unroll
-      for (int pass = 0; pass < (MODE == NM_ADJ ? 0 : NPASS); ++pass) {
-        const int ga = lane / P, t = lane - ga * P;
-        const int gi = pass * GA + ga;
-        const int c = cgp * GB + gi;
-        if (ga < GA && gi < GB) {
-          float2 v[Q];
-          if (c < a.C) {
-            const float2* srow = map0 + c * cstride;
-#pragma unroll
-            for (int n1 = 0; n1 < Q; ++n1) v[n1] = cmul(__ldg(srow + t + P * n1), xrow[t + P * n1]);
-#pragma unroll
-            for (int st = 1; st < NS; ++st)
-#pragma unroll
-              for (int n1 = 0; n1 < Q; ++n1)
-                v[n1] = cfma(__ldg(srow + st * sstride + t + P * n1), xrow[st * a.rows * W + t + P * n1], v[n1]);
-          } else {
-#pragma unroll
-            for (int n1 = 0; n1 < Q; ++n1) v[n1] = make_float2(0.f, 0.f);
-          }
-          dft_pow2<Q, false>(v);
-          float2* yc = ybuf + gi * W;
-          yc[t] = v[0];
-#pragma unroll
-          for (int k1 = 1; k1 < Q; ++k1) yc[k1 * P + t] = cmul(v[k1], s_tw[k1 * P + t]);
-        }
-      }
-      __syncwarp();
-
-      // ---- phase B: pruned P-point DFT at the sampled frequencies and back.
-      // The conjugate pairs (t, P - t) are streamed from shared memory so that
-      // only the J outputs stay in registers.
-      {
-        const int gi = lane / Q, k1 = lane - gi * Q;
-        float2* col = ybuf + gi * W + k1 * P;
-        const float4* crow = s_coef + k1 * a.kstride;
-        const float* wrow_ = s_wt + k1 * J;
-        const float* srow_ = s_sgn + k1 * J;
-        float2 X[JMAX];
-        if constexpr (MODE == NM_ADJ) {
-          // the sampled frequencies k = k1 + Q k2 of this lane's coil row, (-1)^k / sqrt(W) applied
-          const int c = cgp * GB + gi;
-          const float2* trow = a.x + (((size_t)b * a.C + (c < a.C ? c : 0)) * a.H + h) * W;
-          const int* kx = a.akx + k1 * J;
-          const float* fk = a.af + k1 * J;
-#pragma unroll
-          for (int j = 0; j < JMAX; ++j) {
-            X[j] = make_float2(0.f, 0.f);
-            if (j < J && c < a.C) X[j] = cscale(__ldg(trow + kx[j]), fk[j]);
-          }
-        } else {
-        const float2 Y0 = col[0];
-        float2 Ym = make_float2(0.f, 0.f);
-        if (EVENP) Ym = col[P / 2];
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-          X[j] = Y0;
-          if (EVENP && j < J) {
-            const float sg = srow_[j];
-            X[j].x = fmaf(sg, Ym.x, X[j].x);
-            X[j].y = fmaf(sg, Ym.y, X[j].y);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-          const int t = 2 * q + 1;
-          const float2 u0 = col[t], w0 = col[P - t];
-          const float2 S0 = cadd(u0, w0), D0 = csub(u0, w0);
-          float2 S1 = make_float2(0.f, 0.f), D1 = S1;
-          if (t + 1 <= HP) {
-            const float2 u1 = col[t + 1], w1 = col[P - t - 1];
-            S1 = cadd(u1, w1);
-            D1 = csub(u1, w1);
-          }
-#pragma unroll
-          for (int j = 0; j < JMAX; ++j) {
-            if (j < J) {
-              const float4 cs = crow[j * RQ + q];
-              X[j].x = fmaf(cs.x, S0.x, fmaf(cs.y, D0.y, X[j].x));
-              X[j].y = fmaf(cs.x, S0.y, fmaf(-cs.y, D0.x, X[j].y));
-              if (t + 1 <= HP) {
-                X[j].x = fmaf(cs.z, S1.x, fmaf(cs.w, D1.y, X[j].x));
-                X[j].y = fmaf(cs.z, S1.y, fmaf(-cs.w, D1.x, X[j].y));
-              }
-            }
-          }
-        }
-        }
-        float2 Z0 = make_float2(0.f, 0.f), Zm = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j) {
-          if (j < J) {
-            if (MODE != NM_ADJ) X[j] = cscale(X[j], wrow_[j]);
-            Z0 = cadd(Z0, X[j]);
-            if (EVENP) {
-              const float sg = srow_[j];
-              Zm.x = fmaf(sg, X[j].x, Zm.x);
-              Zm.y = fmaf(sg, X[j].y, Zm.y);
-            }
-          }
-        }
-        __syncwarp();  // every lane has read its column before any is overwritten
-        col[0] = Z0;
-        if (EVENP) col[P / 2] = Zm;
-#pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-          const int t = 2 * q + 1;
-          float2 A0 = make_float2(0.f, 0.f), B0 = A0, A1 = A0, B1 = A0;
-#pragma unroll
-          for (int j = 0; j < JMAX; ++j) {
-            if (j < J) {
-              const float4 cs = crow[j * RQ + q];
-              A0.x = fmaf(cs.x, X[j].x, A0.x); A0.y = fmaf(cs.x, X[j].y, A0.y);
-              B0.x = fmaf(cs.y, X[j].x, B0.x); B0.y = fmaf(cs.y, X[j].y, B0.y);
-              A1.x = fmaf(cs.z, X[j].x, A1.x); A1.y = fmaf(cs.z, X[j].y, A1.y);
-              B1.x = fmaf(cs.w, X[j].x, B1.x); B1.y = fmaf(cs.w, X[j].y, B1.y);
-            }
-          }
-          col[t] = make_float2(A0.x - B0.y, A0.y + B0.x);
-          col[P - t] = make_float2(A0.x + B0.y, A0.y - B0.x);
-          if (t + 1 <= HP) {
-            col[t + 1] = make_float2(A1.x - B1.y, A1.y + B1.x);
-            col[P - t - 1] = make_float2(A1.x + B1.y, A1.y - B1.x);
-          }
-        }
-      }
-      __syncwarp();
-
-      // ---- phase C: inverse twiddle, inverse Q-point DFT, conj-map combine (one sum per set)
-      float2 acc[NS][Q];
-#pragma unroll
-      for (int st = 0; st < NS; ++st)
-#pragma unroll
-        for (int n1 = 0; n1 < Q; ++n1) acc[st][n1] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
-        const int ga = lane / P, t = lane - ga * P;
-        const int gi = pass * GA + ga;
-        const int c = cgp * GB + gi;
-        if (ga < GA && gi < GB && c < a.C) {
-          const float2* yc = ybuf + gi * W;
-          float2 z[Q];
-          z[0] = yc[t];
-#pragma unroll
-          for (int k1 = 1; k1 < Q; ++k1) z[k1] = cmulc(s_tw[k1 * P + t], yc[k1 * P + t]);
-          dft_pow2<Q, true>(z);
-          const float2* srow = map0 + c * cstride;
-#pragma unroll
-          for (int st = 0; st < NS; ++st)
-#pragma unroll
-            for (int n1 = 0; n1 < Q; ++n1)
-              acc[st][n1] = cfmac(__ldg(srow + st * sstride + t + P * n1), z[n1], acc[st][n1]);
-        }
-      }
-      __syncwarp();
-      if (lane < GA * P) {
-        const int ga = lane / P, t = lane - ga * P;
-#pragma unroll
-        for (int st = 0; st < NS; ++st)
-#pragma unroll
-          for (int n1 = 0; n1 < Q; ++n1) ybuf[(st * GA + ga) * W + t + P * n1] = acc[st][n1];
-      }
-    }
-    __syncthreads();
-
-    // ---- epilogue: sum coil groups in fixed order, + lambda x, row partial (per set and row)
-    for (int it = warp; it < NS * nrows; it += nwarps) {
-      const int st = it / nrows, rr = it - st * nrows;
-      const int h = h0 + rr;
-      const size_t orow0 = (((size_t)b * NS + st) * a.H + h) * W;
+    const float al = (float)s_alpha[b], be = first ? 0.f : (float)s_beta[b];
+    for (int rw = warp; rw < NS * nrows; rw += nwarps) {
+      const int st = rw / nrows, h = h0 + (rw - st * nrows);
+      const size_t off = ((((size_t)b * NS + st) * a.H + h) * W) / 2;
+      const float4* pv = reinterpret_cast<const float4*>(c.p) + off;
+      const float4* sv = reinterpret_cast<const float4*>(c.s) + off;
+      const float4* wv = reinterpret_cast<const float4*>(c.w) + off;
+      float4* xv = reinterpret_cast<float4*>(c.x) + off;
+      float4* rv = reinterpret_cast<float4*>(c.r) + off;
       float part = 0.f;
-      const float2* xr = s_x + (st * a.rows + rr) * W;
-      const float2* rh = (MODE == NM_RESID) ? a.rhs + orow0 : nullptr;
-      float2* orow = a.out + orow0;
-      for (int n = lane; n < W; n += 32) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int g = 0; g < a.nwr; ++g) {
-          const float2* yb = s_y + (rr * a.nwr + g) * (GB * W) + st * GA * W;
-#pragma unroll
-          for (int ga = 0; ga < GA; ++ga) s = cadd(s, yb[ga * W + n]);
+      for (int i = lane; i < W / 2; i += 32) {
+        float4 r = rv[i], x = xv[i];
+        const float4 w = wv[i];
+        float4 pp = r, ss = w;
+        if (!first) {
+          const float4 po = pv[i], so = sv[i];
+          pp.x = fmaf(be, po.x, r.x); pp.y = fmaf(be, po.y, r.y); pp.z = fmaf(be, po.z, r.z); pp.w = fmaf(be, po.w, r.w);
+          ss.x = fmaf(be, so.x, w.x); ss.y = fmaf(be, so.y, w.y); ss.z = fmaf(be, so.z, w.z); ss.w = fmaf(be, so.w, w.w);
         }
-        if (MODE == NM_ADJ) {
-          orow[n] = s;
-          continue;
-        }
-        const float2 xv = xr[n];
-        float2 o = make_float2(fmaf(lam, xv.x, s.x), fmaf(lam, xv.y, s.y));
-        if (MODE == NM_RESID) {
-          o = csub(rh[n], o);
-          part = fmaf(o.x, o.x, fmaf(o.y, o.y, part));
-        } else {
-          part = fmaf(xv.x, o.x, fmaf(xv.y, o.y, part));
-        }
-        orow[n] = o;
+        x.x = fmaf(al, pp.x, x.x); x.y = fmaf(al, pp.y, x.y); x.z = fmaf(al, pp.z, x.z); x.w = fmaf(al, pp.w, x.w);
+        r.x = fmaf(-al, ss.x, r.x); r.y = fmaf(-al, ss.y, r.y); r.z = fmaf(-al, ss.z, r.z); r.w = fmaf(-al, ss.w, r.w);
+        xv[i] = x;
+        rv[i] = r;
+        part = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, part))));
       }
-      if (MODE != NM_ADJ && a.part) {
-        const double d = warp_sum_d((double)part);
-        if (lane == 0) a.part[(size_t)b * a.HS + st * a.H + h] = d;
-      }
+      const double d = warp_sum_d((double)part);
+      if (lane == 0) a.part2[(size_t)b * a.HS + st * a.H + h] = d;
     }
-    __syncthreads();
   }
-  if (a.finalize) last_block(a);
+  if (!coop_barrier(c.bar)) {
+    if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
+    return;
+  }
+  coop_scalars(a, c.iters, true, s_g, s_alpha, s_beta, c.hist ? c.hist + (size_t)c.iters * a.B : nullptr);
 }
+
+typedef void (*CgKernel)(const NLArgs, const CgCoop);
 
 typedef void (*NLKernel)(const NLArgs);
 
@@ -413,6 +658,18 @@ NLKernel pick_mode(int mode) {
 constexpr int kJmax[] = {4, 6, 8, 10, 12, 16};
 
 template <int Q, int P, int NS>
+CgKernel pick_cg_j(int jmax) {
+  switch (jmax) {
+    case 4: return k_cg_lines<Q, P, 4, NS>;
+    case 6: return k_cg_lines<Q, P, 6, NS>;
+    case 8: return k_cg_lines<Q, P, 8, NS>;
+    case 10: return k_cg_lines<Q, P, 10, NS>;
+    case 12: return k_cg_lines<Q, P, 12, NS>;
+    default: return k_cg_lines<Q, P, 16, NS>;
+  }
+}
+
+template <int Q, int P, int NS>
 NLKernel pick_j(int jmax, int mode) {
   switch (jmax) {
     case 4: return pick_mode<Q, P, 4, NS>(mode);
@@ -428,5 +685,7 @@ NLKernel pick_j(int jmax, int mode) {
 // (ns = 2 map sets only where two sets fit a warp's phase-C buffer: P >= 16 for Q = 8, P > 16 for Q = 16).
 NLKernel pick_q8(int P, int jmax, int mode, int ns);
 NLKernel pick_q16(int P, int jmax, int mode, int ns);
+CgKernel pick_cg_q8(int P, int jmax, int ns);
+CgKernel pick_cg_q16(int P, int jmax, int ns);
 
 }  // namespace nl

@@ -15,4 +15,16 @@ NLKernel pick_q8(int P, int jmax, int mode, int ns) {
   return nullptr;
 }
 
+CgKernel pick_cg_q8(int P, int jmax, int ns) {
+  if (ns == 1) {
+    if (P == 8) return pick_cg_j<8, 8, 1>(jmax);
+    if (P == 16) return pick_cg_j<8, 16, 1>(jmax);
+    if (P == 29) return pick_cg_j<8, 29, 1>(jmax);
+  } else if (ns == 2) {
+    if (P == 16) return pick_cg_j<8, 16, 2>(jmax);
+    if (P == 29) return pick_cg_j<8, 29, 2>(jmax);
+  }
+  return nullptr;
+}
+
 }  // namespace nl

@@ -31,6 +31,8 @@ struct LinesTables {
   float* af = nullptr;     // [Q][J] adjoint: (-1)^k / sqrt(W) per slot (0 = padding)
   int* cols = nullptr;     // sampled columns (centred index), ncols of them
   int ncols = 0;
+  const void* coop = nullptr;  // whole-solve cooperative CG kernel (NULL: one launch per step)
+  int coop_grid = 0;
 };
 
 // Scratch carved from the caller's workspace.
@@ -42,6 +44,9 @@ struct Workspace {
   float2* t0 = nullptr;         // [B][H][W] temporaries of the unrolled blocks
   float2* t1 = nullptr;
   double* part = nullptr;       // [B][H] per-row partial sums
+  double* part2 = nullptr;      // [4][B][H] row partials of the one-launch CG (two double buffers)
+  float2* wv = nullptr;         // [B][S][H][W] S r of the one-launch CG
+  float2* sv = nullptr;         // [B][S][H][W] S p of the one-launch CG
   double* rr = nullptr;         // [B]  ||r||^2
   double* alpha = nullptr;      // [B]
   double* beta = nullptr;       // [B]
@@ -83,7 +88,8 @@ inline void count_launch(sense_plan, int n = 1) { prof_count(n); }
 // Modes of the fused line-mask normal-operator kernel.
 // NM_ADJ is the adjoint's row pass: x = sum_c conj(S_c) IDFT_W(T_c) from the sampled columns of
 // the column-transformed k-space T (no phase A, no forward half of phase B).
-enum NormalMode { NM_PLAIN = 0, NM_CG = 1, NM_RESID = 2, NM_ADJ = 3 };
+// NM_CG2 is one pass of the single-reduction CG of the one-launch solve (see k_cg_lines).
+enum NormalMode { NM_PLAIN = 0, NM_CG = 1, NM_RESID = 2, NM_ADJ = 3, NM_CG2 = 4 };
 
 struct NormalLaunch {
   int mode = NM_PLAIN;
@@ -101,6 +107,9 @@ struct NormalLaunch {
 };
 
 int launch_normal_lines(sense_plan p, const NormalLaunch& L);
+// Every CG iteration in one cooperative launch (p->lines.coop): x, w.r, w.p, w.q, w.rr as left by
+// the initial residual; rr_hist rows 1..iters written when non-NULL.
+int launch_cg_lines(sense_plan p, float2* x, int iters, double* rr_hist);
 int build_lines_tables(sense_plan p);
 void free_lines_tables(sense_plan p);
 

@@ -197,6 +197,56 @@ def test_cg_solve_parity(cfg_index, B):
     assert plan.status() == 0
 
 
+def _cg_path_counts(fn):
+    from paper_2202_14005_b300 import _lib
+    torch.cuda.synchronize()
+    for g in ("normal_lines", "cg_lines", "cg_vec"):
+        _lib.profile_read(g)
+    _lib.profile_enable(True)
+    out = fn()
+    torch.cuda.synchronize()
+    _lib.profile_enable(False)
+    return out, {g: _lib.profile_read(g)[1] for g in ("normal_lines", "cg_lines", "cg_vec")}
+
+
+@pytest.mark.parametrize("B,one_launch", [(4, True), (16, False)])
+def test_cg_paths_by_batch(B, one_launch):
+    """256x232 line-mask solves: a small batch runs every iteration in one cooperative launch
+    (single-reduction recurrence), a large one per-iteration launches (textbook recurrence);
+    both against the oracle, residual histories included."""
+    cfg, maps, mask, rhs, _ = _cg_inputs(2, B)
+    plan = plan_for(maps, mask)
+    lam = torch.tensor([cfg.lam], dtype=torch.float64, device="cuda")
+    hist = torch.zeros((cfg.cg_iters + 1, B), dtype=torch.float64, device="cuda")
+    x, n = _cg_path_counts(lambda: plan.cg_solve(dev(rhs), lam, cfg.cg_iters, x0=dev(rhs), rr_hist=hist))
+    if one_launch:
+        assert n["cg_lines"] == 1 and n["normal_lines"] == 1, n
+    else:
+        assert n["cg_lines"] == 0 and n["normal_lines"] == 1 + cfg.cg_iters, n
+    xref, rr = ocg.cg_solve(maps, mask, cfg.lam, rhs, rhs, cfg.cg_iters)
+    assert rel(host(x), xref) <= TOL_CG
+    np.testing.assert_allclose(hist.cpu().numpy(), rr, rtol=1e-3, atol=1e-12 * rr[0].max())
+    assert plan.status() == 0
+
+
+def test_cg_one_launch_long_solve_and_frozen_slice():
+    """40 iterations of the one-launch solve against the oracle (the single-reduction recurrence
+    over many steps), with one slice whose right-hand side is zero (frozen: stays zero, no
+    breakdown flag)."""
+    cfg, maps, mask, rhs, _ = _cg_inputs(2, 3)
+    rhs = rhs.copy()
+    rhs[1] = 0
+    plan = plan_for(maps, mask)
+    lam = torch.tensor([cfg.lam], dtype=torch.float64, device="cuda")
+    x, n = _cg_path_counts(lambda: plan.cg_solve(dev(rhs), lam, 40))
+    assert n["cg_lines"] == 1, n
+    xref, _ = ocg.cg_solve(maps, mask, cfg.lam, rhs, None, 40)
+    xh = host(x)
+    assert np.all(xh[1] == 0)
+    assert rel(xh[[0, 2]], xref[[0, 2]]) <= TOL_CG
+    assert plan.status() == 0
+
+
 def test_cg_solve_full_workload_256x232_b16():
     cfg, maps, mask, rhs, gt = _cg_inputs(2)
     plan = plan_for(maps, mask)
@@ -348,8 +398,8 @@ def test_soft_sense_fused_line_kernel(shape):
     x = synth.randn_complex((B, NS, H, W), 7).astype(np.complex64)
     plan = SensePlan(dev(maps), dev(mask))
     torch.cuda.synchronize()
-    _lib.profile_read("normal_lines")
-    _lib.profile_read("fft_generic")
+    for g in ("normal_lines", "cg_lines", "fft_generic"):
+        _lib.profile_read(g)
     _lib.profile_enable(True)
     ng = plan.normal(dev(x), 0.1)
     lam = torch.tensor([0.05], dtype=torch.float64, device="cuda")
@@ -357,8 +407,10 @@ def test_soft_sense_fused_line_kernel(shape):
     torch.cuda.synchronize()
     _lib.profile_enable(False)
     n_fused = _lib.profile_read("normal_lines")[1]
+    n_cg = _lib.profile_read("cg_lines")[1]
     n_generic = _lib.profile_read("fft_generic")[1]
-    assert n_fused == 11 and n_generic == 0, (n_fused, n_generic)
+    # the normal operator, then the whole 10-iteration solve in one cooperative launch
+    assert n_fused == 1 and n_cg == 1 and n_generic == 0, (n_fused, n_cg, n_generic)
     assert rel(ng.cpu().numpy(), osense.normal_sets(x, maps, mask, 0.1)) <= 1e-5
     ref, _ = ocg.cg_solve_sets(maps, mask, 0.05, x, None, 10)
     assert rel(xs.cpu().numpy(), ref) <= 1e-4
