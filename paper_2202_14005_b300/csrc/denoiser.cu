@@ -348,93 +348,103 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
 // ------------------------------------------------ 2-channel layers
 // All convolution weights are used in BF16 (rounded when packed); sums are FP32.
 
-// 2 -> 64 on CUDA cores, four consecutive pixels of one row per thread so that
-// each weight read serves four pixels.  n[r][q] = 2-channel source at
-// (h - 1 + r, w0 - 1 + q); output channel j of pixel w0 + i:
-//   mode 0 (first layer):   relu(b[j] + sum_{c,tap} W[j][c][tap] * xr(n[dy][i + dx])), xr = BF16(x)
-//   mode 1 (last layer input gradient): [a4 > 0] * sum_{c,tap} W5[c][j][tap] * g(n[2 - dy][i + 2 - dx])
-constexpr int kQuad = 4;
+// 2 -> 64 on CUDA cores.  A CTA takes k2Rows full image rows of one slice; their 2-channel
+// (k2Rows + 2) x (W + 2) neighbourhood and the 64 x 18 BF16-rounded weights are staged in shared
+// memory.  Thread t owns output channels 4 (t mod 16) .. + 3 (72 weights in registers) for the
+// pixels t / 16, t / 16 + 16, ... of each row, so that 16 threads write one pixel's 128 bytes.
+// n[r][q] = 2-channel source at (h - 1 + r, q - 1); output channel j of pixel (h, w):
+//   mode 0 (first layer):   relu(b[j] + sum_{c,tap} W[j][c][tap] * xr(n[dy][w + dx])), xr = BF16(x)
+//   mode 1 (last layer input gradient): [a4 > 0] * sum_{c,tap} W5[c][j][tap] * g(n[2 - dy][w + 2 - dx])
+constexpr int k2Rows = 2;
+constexpr int k2Threads = 256;
+int k2_smem(int W) { return ((k2Rows + 2) * (W + 2) * 2 + CH * 18) * (int)sizeof(float); }
 
-__global__ void __launch_bounds__(128) k_2to64(int B, int H, int W, int mode, const float2* src,
-                                               const float* wsrc, const float* bias,
-                                               const __nv_bfloat16* mask_src, __nv_bfloat16* out) {
-  __shared__ float s_w[CH * 18];  // [j][c][tap], BF16-rounded
-  __shared__ float s_b[CH];
+__global__ void __launch_bounds__(k2Threads) k_2to64(int B, int H, int W, int mode, const float2* src,
+                                                     const float* wsrc, const float* bias,
+                                                     const __nv_bfloat16* mask_src, __nv_bfloat16* out) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  float2* s_n = reinterpret_cast<float2*>(dsm);                        // [k2Rows + 2][W + 2]
+  float* s_w = reinterpret_cast<float*>(s_n + (k2Rows + 2) * (W + 2));  // [j][c][tap]
+  const int nrb = (H + k2Rows - 1) / k2Rows;
+  const int b = blockIdx.x / nrb, h0 = (blockIdx.x % nrb) * k2Rows;
+  const int nrows = min(k2Rows, H - h0);
+  const int ld = W + 2;
+  for (int i = threadIdx.x; i < (nrows + 2) * ld; i += blockDim.x) {
+    const int r = i / ld, q = i - r * ld;
+    const int yy = h0 - 1 + r, xx = q - 1;
+    float2 v = make_float2(0.f, 0.f);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = src[((size_t)b * H + yy) * W + xx];
+    if (mode == 0) v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
+    s_n[i] = v;
+  }
   for (int i = threadIdx.x; i < CH * 18; i += blockDim.x) {
     const int j = i / 18, c = (i / 9) % 2, tap = i % 9;
     const float v = (mode == 0) ? wsrc[(j * 2 + c) * 9 + tap] : wsrc[(c * CH + j) * 9 + tap];
     s_w[i] = bf(__float2bfloat16_rn(v));
   }
-  if (threadIdx.x < CH) s_b[threadIdx.x] = (mode == 0) ? bias[threadIdx.x] : 0.f;
   __syncthreads();
-  const int nq = (W + kQuad - 1) / kQuad;
-  const size_t qi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (qi >= (size_t)B * H * nq) return;
-  const int qw = qi % nq, h = (qi / nq) % H, b = qi / ((size_t)nq * H);
-  const int w0 = qw * kQuad;
-  float n[2][3][kQuad + 2];
+  const int cq = threadIdx.x & 15, pl = threadIdx.x >> 4;
+  // weights of the channel pairs (4cq, 4cq + 1) and (4cq + 2, 4cq + 3): packed FP32x2 FMAs
+  float2 wr[2][18];
+  float2 bj[2];
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
+  for (int e = 0; e < 2; ++e) {
+    const int j0 = cq * 4 + 2 * e;
+    bj[e] = (mode == 0) ? make_float2(bias[j0], bias[j0 + 1]) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < kQuad + 2; ++q) {
-      const int yy = h - 1 + r, xx = w0 - 1 + q;
-      float2 v = make_float2(0.f, 0.f);
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = src[((size_t)b * H + yy) * W + xx];
-      if (mode == 0) v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
-      n[0][r][q] = v.x;
-      n[1][r][q] = v.y;
-    }
-#pragma unroll 1
-  for (int cg = 0; cg < 8; ++cg) {
-    float acc[8][kQuad];
+    for (int k = 0; k < 18; ++k) wr[e][k] = make_float2(s_w[j0 * 18 + k], s_w[(j0 + 1) * 18 + k]);
+  }
+  constexpr int kStep = k2Threads / 16;  // pixels between a thread's consecutive pixels
+  const uint2* mrow =
+      mode == 1 ? reinterpret_cast<const uint2*>(mask_src + ((size_t)b * H + h0) * W * CH) + cq : nullptr;
+  for (int r = 0; r < nrows; ++r) {
+    const int h = h0 + r;
+    // input-gradient mode: the mask of the thread's next pixel is loaded one pixel ahead
+    uint2 mnext = make_uint2(0u, 0u);
+    if (mode == 1 && pl < W) mnext = mrow[((size_t)r * W + pl) * (CH / 4)];
+    for (int w = pl; w < W; w += kStep) {
+      const uint2 m = mnext;
+      if (mode == 1 && w + kStep < W) mnext = mrow[((size_t)r * W + w + kStep) * (CH / 4)];
+      float2 acc[2] = {bj[0], bj[1]};
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int j = cg * 8 + e;
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        const float2 v = (mode == 0) ? s_n[(r + dy) * ld + w + dx] : s_n[(r + 2 - dy) * ld + w + 2 - dx];
+        const float2 vx = make_float2(v.x, v.x), vy = make_float2(v.y, v.y);
 #pragma unroll
-      for (int i = 0; i < kQuad; ++i) acc[e][i] = s_b[j];
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-          const float wv = s_w[j * 18 + c * 9 + tap];
-          const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-          for (int i = 0; i < kQuad; ++i) {
-            const float x = (mode == 0) ? n[c][dy][i + dx] : n[c][2 - dy][i + 2 - dx];
-            acc[e][i] = fmaf(wv, x, acc[e][i]);
-          }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < kQuad; ++i) {
-      const int w = w0 + i;
-      if (w >= W) break;
+        for (int e = 0; e < 2; ++e) acc[e] = __ffma2_rn(wr[e][9 + tap], vy, __ffma2_rn(wr[e][tap], vx, acc[e]));
+      }
       const size_t p = ((size_t)b * H + h) * W + w;
-      float r[8];
+      float o4[4];
       if (mode == 0) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = fmaxf(acc[e][i], 0.f);
+        for (int e = 0; e < 2; ++e) {
+          o4[2 * e] = fmaxf(acc[e].x, 0.f);
+          o4[2 * e + 1] = fmaxf(acc[e].y, 0.f);
+        }
       } else {
-        const uint4 m = reinterpret_cast<const uint4*>(mask_src + p * CH)[cg];
         const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = (bf(mb[e]) > 0.f) ? acc[e][i] : 0.f;
+        for (int e = 0; e < 2; ++e) {
+          o4[2 * e] = (bf(mb[2 * e]) > 0.f) ? acc[e].x : 0.f;
+          o4[2 * e + 1] = (bf(mb[2 * e + 1]) > 0.f) ? acc[e].y : 0.f;
+        }
       }
-      uint4 o;
+      uint2 o;
       __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) po[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
-      reinterpret_cast<uint4*>(out + p * CH)[cg] = o;
+      po[0] = __floats2bfloat162_rn(o4[0], o4[1]);
+      po[1] = __floats2bfloat162_rn(o4[2], o4[3]);
+      reinterpret_cast<uint2*>(out + p * CH)[cq] = o;
     }
   }
 }
 
 // --------------------------------------------------- weight gradients (CUDA cores)
-// Small layers, one image row of one slice per CTA (partials reduced later):
+// Small layers (partials per CTA, reduced later):
 //  L1 (first):  gw[co][c][tap] = sum_p g1[p][co] * xr[p + s][c],  gb[co] = sum_p g1[p][co]
 //  L5 (last):   gw[co][ci][tap] = sum_p g5[p][co] * a4[p + s][ci], gb[co] = sum_p g5[p][co]
 // Thread j < 64 of each of the four groups owns the 64-channel index (co for
-// L1, ci for L5) and 18 (+1) sums over every fourth pixel of the row, all
+// L1, ci for L5) and 18 (+1) sums over a quarter of each row's pixels, all
 // operands in shared memory; the groups are added in fixed order.
 constexpr int kSmallOut = CH * 18 + CH;  // 1152 weights + up to 64 biases
 
@@ -459,82 +469,151 @@ __device__ void small_partial_out(float (&acc)[2][9], float bacc, int last, floa
   }
 }
 
-// L1: U = g1 row h [W][64] (bf16), V = bf16-rounded x on rows h-1..h+1 [3][W+2] (float2).
+// A CTA takes kSmallRows consecutive rows of one slice; the sums of all its rows accumulate in
+// registers (one partial per CTA).  Thread j < 64 of group g (of four) owns channel j and the
+// pixel range [g W4, (g + 1) W4) of every row, walked with a 3 x 3 window kept in registers (one
+// new window column per pixel).  The 3-row halo source sits in a ring of three row slots
+// (row yy in slot (yy + 3) mod 3, one new row staged per output row), zero outside the image.
+constexpr int kSmallRows = 4;
+
+__device__ __forceinline__ int ring_slot(int yy) { return (yy + 3) % 3; }
+
+// L1: U = g1 row h [W][64] (bf16), V = bf16-rounded x, ring of rows [3][W+2] (float2).
 __global__ void __launch_bounds__(256) k_wgrad_l1(int B, int H, int W, const __nv_bfloat16* g1,
                                                   const float2* x, float* partial) {
   extern __shared__ __align__(16) uint8_t dsm[];
   __nv_bfloat16* su = reinterpret_cast<__nv_bfloat16*>(dsm);
   float2* sv = reinterpret_cast<float2*>(dsm + (((size_t)W * CH * 2 + 15) & ~(size_t)15));
-  const int b = blockIdx.x / H, h = blockIdx.x % H;
-  const __nv_bfloat16* src = g1 + ((size_t)b * H + h) * W * CH;
-  for (int i = threadIdx.x; i < W * 8; i += blockDim.x) cp_async16(su + i * 8, src + i * 8, true);
-  cp_async_commit();
-  for (int i = threadIdx.x; i < 3 * (W + 2); i += blockDim.x) {
-    const int r = i / (W + 2), px = i % (W + 2);
-    const int yy = h - 1 + r, xx = px - 1;
-    float2 v = make_float2(0.f, 0.f);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-      v = x[((size_t)b * H + yy) * W + xx];
-      v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
+  const int nrb = (H + kSmallRows - 1) / kSmallRows;
+  const int b = blockIdx.x / nrb, h0 = (blockIdx.x % nrb) * kSmallRows, h1 = min(h0 + kSmallRows, H);
+  auto stage_x = [&](int yy) {  // x row yy (zero outside) into its ring slot, columns -1 .. W
+    float2* d = sv + ring_slot(yy) * (W + 2);
+    for (int i = threadIdx.x; i < W + 2; i += blockDim.x) {
+      const int xx = i - 1;
+      float2 v = make_float2(0.f, 0.f);
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+        v = x[((size_t)b * H + yy) * W + xx];
+        v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
+      }
+      d[i] = v;
     }
-    sv[i] = v;
-  }
-  cp_async_wait0();
-  __syncthreads();
+  };
+  stage_x(h0 - 1);
+  stage_x(h0);
   const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
-  float acc[2][9];
+  const int W4 = (W + 3) / 4, wa = min(W, grp * W4), wb = min(W, wa + W4);
+  float2 acc2[9];  // (input channel 0, 1) of each tap
   float bacc = 0.f;
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+  for (int t = 0; t < 9; ++t) acc2[t] = make_float2(0.f, 0.f);
+  for (int h = h0; h < h1; ++h) {
+    __syncthreads();  // the slots and the g1 row of the previous row are no longer read
+    const __nv_bfloat16* src = g1 + ((size_t)b * H + h) * W * CH;
+    for (int i = threadIdx.x; i < W * 8; i += blockDim.x) cp_async16(su + i * 8, src + i * 8, true);
+    cp_async_commit();
+    stage_x(h + 1);
+    cp_async_wait0();
+    __syncthreads();
+    const float2* r0 = sv + ring_slot(h - 1) * (W + 2);
+    const float2* r1 = sv + ring_slot(h) * (W + 2);
+    const float2* r2 = sv + ring_slot(h + 1) * (W + 2);
+    if (wa < wb) {
+      // window columns w - 1, w, w + 1 (image) = slot columns w, w + 1, w + 2; the two input
+      // channels of a tap as one packed FP32x2 FMA
+      float2 c0[3] = {r0[wa], r1[wa], r2[wa]};
+      float2 c1[3] = {r0[wa + 1], r1[wa + 1], r2[wa + 1]};
+#pragma unroll 3
+      for (int w = wa; w < wb; ++w) {
+        const float2 c2[3] = {r0[w + 2], r1[w + 2], r2[w + 2]};
+        const float u = bf(su[w * CH + j]);
+        const float2 uu = make_float2(u, u);
+        bacc += u;
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc[c][t] = 0.f;
-  for (int w = grp; w < W; w += 4) {
-    const float u = bf(su[w * CH + j]);
-    bacc += u;
+        for (int dy = 0; dy < 3; ++dy) {
+          acc2[dy * 3 + 0] = __ffma2_rn(uu, c0[dy], acc2[dy * 3 + 0]);
+          acc2[dy * 3 + 1] = __ffma2_rn(uu, c1[dy], acc2[dy * 3 + 1]);
+          acc2[dy * 3 + 2] = __ffma2_rn(uu, c2[dy], acc2[dy * 3 + 2]);
+        }
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const float2 v = sv[(tap / 3) * (W + 2) + w + tap % 3];
-      acc[0][tap] = fmaf(u, v.x, acc[0][tap]);
-      acc[1][tap] = fmaf(u, v.y, acc[1][tap]);
+        for (int dy = 0; dy < 3; ++dy) {
+          c0[dy] = c1[dy];
+          c1[dy] = c2[dy];
+        }
+      }
     }
+  }
+  __syncthreads();
+  float acc[2][9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    acc[0][t] = acc2[t].x;
+    acc[1][t] = acc2[t].y;
   }
   small_partial_out(acc, bacc, 0, partial + (size_t)blockIdx.x * kSmallOut);
 }
 
-// L5: U = a4 on rows h-1..h+1 [3][W+2][64] (bf16), V = g5 row h [W] (float2).
+// L5: U = a4, ring of rows [3][W+2][64] (bf16), V = g5 row h [W] (float2).
 __global__ void __launch_bounds__(256) k_wgrad_l5(int B, int H, int W, const __nv_bfloat16* a4,
                                                   const float2* g5, float* partial) {
   extern __shared__ __align__(16) uint8_t dsm[];
   __nv_bfloat16* su = reinterpret_cast<__nv_bfloat16*>(dsm);
   float2* sv = reinterpret_cast<float2*>(dsm + (size_t)3 * (W + 2) * CH * 2);
-  const int b = blockIdx.x / H, h = blockIdx.x % H;
-  for (int i = threadIdx.x; i < 3 * (W + 2) * 8; i += blockDim.x) {
-    const int q = i & 7, px = (i >> 3) % (W + 2), r = (i >> 3) / (W + 2);
-    const int yy = h - 1 + r, xx = px - 1;
-    const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
-    cp_async16(su + ((r * (W + 2) + px) * 8 + q) * 8,
-               a4 + (ok ? (((size_t)b * H + yy) * W + xx) * CH + q * 8 : 0), ok);
-  }
-  cp_async_commit();
-  for (int i = threadIdx.x; i < W; i += blockDim.x) sv[i] = g5[((size_t)b * H + h) * W + i];
-  cp_async_wait0();
-  __syncthreads();
+  const int nrb = (H + kSmallRows - 1) / kSmallRows;
+  const int b = blockIdx.x / nrb, h0 = (blockIdx.x % nrb) * kSmallRows, h1 = min(h0 + kSmallRows, H);
+  auto stage_a = [&](int yy) {  // a4 row yy (zero outside) into its ring slot, columns -1 .. W
+    __nv_bfloat16* d = su + (size_t)ring_slot(yy) * (W + 2) * CH;
+    for (int i = threadIdx.x; i < (W + 2) * 8; i += blockDim.x) {
+      const int q = i & 7, px = i >> 3, xx = px - 1;
+      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+      cp_async16(d + (px * 8 + q) * 8, a4 + (ok ? (((size_t)b * H + yy) * W + xx) * CH + q * 8 : 0), ok);
+    }
+  };
+  stage_a(h0 - 1);
+  stage_a(h0);
   const int j = threadIdx.x & 63, grp = threadIdx.x >> 6;
-  float acc[2][9];
+  const int W4 = (W + 3) / 4, wa = min(W, grp * W4), wb = min(W, wa + W4);
+  float2 acc2[9];  // (output channel 0, 1) of each tap
   float bacc = 0.f;
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+  for (int t = 0; t < 9; ++t) acc2[t] = make_float2(0.f, 0.f);
+  for (int h = h0; h < h1; ++h) {
+    __syncthreads();  // the slot of row h - 2 and the g5 row of the previous row are no longer read
+    stage_a(h + 1);
+    cp_async_commit();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) sv[i] = g5[((size_t)b * H + h) * W + i];
+    cp_async_wait0();
+    __syncthreads();
+    const __nv_bfloat16* r0 = su + (size_t)ring_slot(h - 1) * (W + 2) * CH + j;
+    const __nv_bfloat16* r1 = su + (size_t)ring_slot(h) * (W + 2) * CH + j;
+    const __nv_bfloat16* r2 = su + (size_t)ring_slot(h + 1) * (W + 2) * CH + j;
+    if (wa < wb) {
+      float c0[3] = {bf(r0[wa * CH]), bf(r1[wa * CH]), bf(r2[wa * CH])};
+      float c1[3] = {bf(r0[(wa + 1) * CH]), bf(r1[(wa + 1) * CH]), bf(r2[(wa + 1) * CH])};
+#pragma unroll 3
+      for (int w = wa; w < wb; ++w) {
+        const float c2[3] = {bf(r0[(w + 2) * CH]), bf(r1[(w + 2) * CH]), bf(r2[(w + 2) * CH])};
+        const float2 v = sv[w];
+        if (j < 2) bacc += (j == 0) ? v.x : v.y;
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc[c][t] = 0.f;
-  for (int w = grp; w < W; w += 4) {
-    const float2 v = sv[w];
-    if (j < 2) bacc += (j == 0) ? v.x : v.y;
+        for (int dy = 0; dy < 3; ++dy) {
+          acc2[dy * 3 + 0] = __ffma2_rn(v, make_float2(c0[dy], c0[dy]), acc2[dy * 3 + 0]);
+          acc2[dy * 3 + 1] = __ffma2_rn(v, make_float2(c1[dy], c1[dy]), acc2[dy * 3 + 1]);
+          acc2[dy * 3 + 2] = __ffma2_rn(v, make_float2(c2[dy], c2[dy]), acc2[dy * 3 + 2]);
+        }
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const float u = bf(su[((tap / 3) * (W + 2) + w + tap % 3) * CH + j]);
-      acc[0][tap] = fmaf(v.x, u, acc[0][tap]);
-      acc[1][tap] = fmaf(v.y, u, acc[1][tap]);
+        for (int dy = 0; dy < 3; ++dy) {
+          c0[dy] = c1[dy];
+          c1[dy] = c2[dy];
+        }
+      }
     }
+  }
+  __syncthreads();
+  float acc[2][9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    acc[0][t] = acc2[t].x;
+    acc[1][t] = acc2[t].y;
   }
   small_partial_out(acc, bacc, 1, partial + (size_t)blockIdx.x * kSmallOut);
 }
@@ -546,8 +625,17 @@ __device__ __forceinline__ float colsum8(const float* base, size_t stride, int n
   __shared__ float s_part[8][32];
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
   float s = 0.f;
-  if (valid)
-    for (int c = wg; c < nchunks; c += 8) s += base[(size_t)c * stride];
+  if (valid) {
+    int c = wg;
+    for (; c + 7 * 8 < nchunks; c += 8 * 8) {  // eight loads in flight, added in chunk order
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldcg(base + (size_t)(c + 8 * k) * stride);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s += v[k];
+    }
+    for (; c < nchunks; c += 8) s += __ldcg(base + (size_t)c * stride);
+  }
   s_part[wg][lane] = s;
   __syncthreads();
   float t = 0.f;
@@ -831,6 +919,8 @@ int conv_prepare() {
                                   ConvLayout<16>::SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad64, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM) ==
                  cudaSuccess &&
+             cudaFuncSetAttribute(k_2to64, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(kMaxW)) ==
+                 cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, wl1_smem(kMaxW)) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l5, cudaFuncAttributeMaxDynamicSharedMemorySize, wl5_smem(kMaxW)) ==
@@ -895,7 +985,7 @@ struct DnLayout {
 DnLayout dn_layout(int B, int H, int W) {
   DnLayout L;
   const size_t act = up256((size_t)B * H * W * CH * 2);
-  L.nch_small = B * H;
+  L.nch_small = B * ((H + kSmallRows - 1) / kSmallRows);
   L.nch64 = std::min(B * H * ((W + WG_SEG - 1) / WG_SEG), kWgMaxParts);
   size_t o = 0;
   for (int i = 0; i < 3; ++i) { L.wf[i] = o; o += up256(WPACK_BYTES); }
@@ -945,9 +1035,9 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
     prof_mark("dn_pack", st, true);
   }
   const size_t npx = (size_t)B * H * W;
-  const unsigned nquad = (unsigned)(((size_t)B * H * ((W + kQuad - 1) / kQuad) + 127) / 128);
   prof_mark("dn_2to64", st, false);
-  k_2to64<<<nquad, 128, 0, st>>>(B, H, W, 0, x, wts + o.w[0], wts + o.b[0], nullptr, act[0]);
+  k_2to64<<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(B, H, W, 0, x, wts + o.w[0],
+                                                                                      wts + o.b[0], nullptr, act[0]);
   prof_mark("dn_2to64", st, true);
   for (int l = 0; l < 3; ++l)
     if (int e = launch_conv64(act[l], reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), wts + o.b[l + 1],
@@ -1026,8 +1116,8 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   // last layer: input gradient (masked by a4 > 0) and weight gradient
   const size_t npx = (size_t)B * H * W;
   prof_mark("dn_2to64", st, false);
-  const unsigned nquad = (unsigned)(((size_t)B * H * ((W + kQuad - 1) / kQuad) + 127) / 128);
-  k_2to64<<<nquad, 128, 0, st>>>(B, H, W, 1, go, weights + o.w[4], nullptr, act[3], gbuf[0]);
+  k_2to64<<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(B, H, W, 1, go, weights + o.w[4],
+                                                                                      nullptr, act[3], gbuf[0]);
   prof_mark("dn_2to64", st, true);
   prof_mark("dn_wgrad_small", st, false);
   k_wgrad_l5<<<L.nch_small, 256, wl5_smem(W), st>>>(B, H, W, act[3], go, ps);
