@@ -40,15 +40,14 @@ METRIC = "unrolled-recon slices/s (fwd+bwd) & normal-op HBM GB/s vs plain CG-SEN
 WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it",
              "varnet_train": "varnet_train_b4_c15_320x368_R4_T10",
              "noncart_modl_infer": "modl_infer_radial_b32_c12_256x256_96x512_K10_cg10"}
-# DRAM bytes per launch (read + write) of each kernel group from the committed ncu
-# captures under profiles/ (None until captured for the current kernel version).
 # DRAM bytes (read + write) per launch from the committed ncu captures under profiles/, per workload
 # (None where no capture of the current kernel version exists for that workload):
-# normal_lines 113.6 MB on a 16-slice CG launch (cg_sense), scaled to the 4-slice MoDL launch by slices;
-# conv64_tc a dgrad launch; vn_* one launch each of the 4-slice 320x368 VarNet step.
+# normal_lines a 16-slice residual-mode launch (cg_sense); cg_lines one 10-iteration solve, conv64_tc
+# a forward launch and wgrad64 one launch of the 4-slice MoDL step; vn_* one launch each of the
+# 4-slice 320x368 VarNet step.
 NCU_TRAFFIC = {
-    "cg_sense": {"normal_lines": 113.6e6},
-    "modl_train": {"normal_lines": 28.4e6},
+    "cg_sense": {"normal_lines": 110.3e6},
+    "modl_train": {"cg_lines": 26.7e6, "conv64_tc": 30.55e6, "wgrad64": 62.9e6},
     "varnet_train": {"vn_K": 3.9e6, "vn_Kbwd": 103.4e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
 }
 # kernel groups the library times with CUDA events when profiling is on
