@@ -27,29 +27,43 @@
 namespace {
 
 constexpr int CH = 64;
-constexpr int TILE_M = 128;
-constexpr int HALO_W = TILE_M + 2;            // 130
-constexpr int HALO_ROWB = HALO_W * CH * 2;    // 16640 bytes: one halo row, 128 bytes per pixel
-constexpr int HALO_TX = 3 * HALO_ROWB;        // 49920 bytes per tile (one TMA box)
-constexpr int HALO_BYTES = 50176;             // padded to whole 1024-byte swizzle atoms
-constexpr int WPACK_BYTES = 9 * 8 * CH * 16;  // 73728 (bf16 [tap][g][n][8])
+// Convolutions with a 64-channel input run as implicit GEMMs on tcgen05 (M = 128 halo pixels of
+// one image row, K = 16 channels per MMA), in one of two forms:
+//  * NOUT = 64 (the 64 -> 64 layers): 36 MMAs per tile, one per (tap, 16-channel step), the tap's
+//    pixel offset dx applied as a 128-byte start offset of the A operand; N = 64; 128 outputs
+//    per tile from a 130-pixel halo.
+//  * NOUT = 16 (the 64 -> 2 layers): the horizontal tap moved to the output side: 12 MMAs, one per
+//    (dy, 16-channel step), with the three taps' weights stacked along N (column 2 dx + c), and the
+//    epilogue adds D_0[q] + D_1[q + 1] + D_2[q + 2] across lanes; 126 outputs per tile from a
+//    128-pixel halo.  (For N = 64 the cross-lane epilogue costs more than the MMAs it saves.)
+constexpr int TILE_M = 128;                   // MMA M
 constexpr int CONV_THREADS = 160;             // warps 0-3 epilogue (one TMEM lane quadrant each), warp 4 producer
 constexpr int NHALO = 3;                      // halo slots (TMA runs two tiles ahead of the MMAs)
 constexpr int NBARS = 1 + 2 * NHALO + 2 + 2;  // weights, halo full/empty, TMEM full/empty
-// Shared-memory layout of the convolution kernel for NOUT output channels (64: the 64 -> 64
-// layers; 16: the 64 -> 2 layers with 14 zero rows): packed weights [tap][g][n][8], NHALO halo
-// slots (1 KB aligned), bias, barriers.
+// Shared-memory layout and tile geometry per NOUT: packed weights, NHALO halo slots (1 KB
+// aligned), bias, the epilogue warps' boundary exchange (NOUT = 16), barriers.
 template <int NOUT>
 struct ConvLayout {
-  static constexpr int WP = 9 * 8 * NOUT * 16;
+  static constexpr bool SHIFT = NOUT == 16;             // output-side horizontal tap
+  static constexpr int CO = NOUT == 64 ? 64 : 2;        // output channels
+  static constexpr int NCOL = NOUT;                     // MMA N
+  static constexpr int HALO_PX = SHIFT ? TILE_M : TILE_M + 2;
+  static constexpr int TILE_OUT = SHIFT ? TILE_M - 2 : TILE_M;
+  static constexpr int HALO_ROWB = HALO_PX * 64 * 2;
+  static constexpr int HALO_TX = 3 * HALO_ROWB;
+  static constexpr int HALO_SLOT = (HALO_TX + 1023) & ~1023;
+  static constexpr int WP = (SHIFT ? 3 : 9) * 8 * NCOL * 16;  // [dy][g][n][8] or [tap][g][n][8]
   static constexpr int OFF_W = 0;
   static constexpr int OFF_H0 = (WP + 1023) & ~1023;
-  static constexpr int OFF_BIAS = OFF_H0 + NHALO * HALO_BYTES;
-  static constexpr int OFF_BAR = OFF_BIAS + CH * 4;
+  static constexpr int OFF_BIAS = OFF_H0 + NHALO * HALO_SLOT;
+  static constexpr int OFF_XCH = OFF_BIAS + 64 * 4;     // [2 tiles][4 warps][4 rows][CO] floats
+  static constexpr int OFF_BAR = OFF_XCH + (SHIFT ? 2 * 4 * 4 * CO * 4 : 0);
   static constexpr int SMEM = OFF_BAR + NBARS * 8 + 16 + 1024;  // + slack to realign the base to 1 KB
+  static constexpr int TCOL = NOUT;                     // TMEM columns between the two accumulators
   static constexpr int TMEM_COLS = 2 * NOUT < 32 ? 32 : 2 * NOUT;
 };
-constexpr int WP16_BYTES = ConvLayout<16>::WP;  // 18432 (64 -> 2 tables, N padded to 16)
+constexpr int WPACK_BYTES = ConvLayout<64>::WP;  // 73728 (bf16 [tap][g][64][8])
+constexpr int WP16_BYTES = ConvLayout<16>::WP;   // 6144 (64 -> 2 tables [dy][g][16][8])
 
 // Offsets (floats) into the flat MoDL weight vector: w_l [Cout][Cin][3][3], b_l [Cout].
 struct ModlOffsets {
@@ -82,27 +96,31 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 
 
 // ------------------------------------------------------------ weight packing
-// 64->64 layers into the K-major operand layout [tap][g][n][8] (bf16), one
-// launch for all six tables (blockIdx.y = 2 * layer + dgrad):
+// Convolution weights into K-major operand layouts (bf16), one launch for all eight tables:
+//  blockIdx.y = 2 * layer + dgrad, the 64 -> 64 layers, [tap][g][n][8]:
 //   forward:        n = cout, k-chunk g over cin:  W[n][g*8+e][tap]
 //   input gradient: n = cin,  k-chunk g over cout: W[g*8+e][n][8 - tap] (flipped taps)
+//  blockIdx.y = 6 (last layer forward) and 7 (first-layer input gradient), [dy][g][16][8] with
+//  row n = 2 dx + c (c < 2) holding tap (dy, dx), output channel c; rows 6..15 zero.
 struct PackArgs {
   const float* w[3];
   __nv_bfloat16* fwd[3];
   __nv_bfloat16* dgr[3];
   const float* w1;       // first layer [64][2][9]
   const float* w5;       // last layer [2][64][9]
-  __nv_bfloat16* t5;     // last layer forward, [tap][g][n16][8]: w5[n][g*8+e][tap] (n < 2)
-  __nv_bfloat16* t1;     // first layer input gradient, [tap][g][n16][8]: w1[g*8+e][n][8 - tap] (n < 2)
+  __nv_bfloat16* t5;     // last layer forward: w5[c][g*8+e][3 dy + dx] at n = 2 dx + c
+  __nv_bfloat16* t1;     // first layer input gradient: w1[g*8+e][c][8 - (3 dy + dx)] at n = 2 dx + c
 };
 __global__ void k_pack64(const PackArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9*8*64*8
-  if (blockIdx.y >= 6) {  // 64 -> 2 tables of the first and last layers (N padded to 16)
-    if (i >= 9 * 8 * 16 * 8) return;
-    const int e = i & 7, n = (i >> 3) & 15, g = (i >> 7) & 7, tap = i >> 10;
+  if (blockIdx.y >= 6) {  // 64 -> 2 tables of the first and last layers (N = 16, 6 live rows)
+    if (i >= 3 * 8 * 16 * 8) return;
+    const int e = i & 7, n = (i >> 3) & 15, g = (i >> 7) & 7, dy = i >> 10;
     float v = 0.f;
-    if (n < 2)
-      v = (blockIdx.y == 6) ? a.w5[(n * CH + g * 8 + e) * 9 + tap] : a.w1[((g * 8 + e) * 2 + n) * 9 + (8 - tap)];
+    if (n < 6) {
+      const int dx = n >> 1, c = n & 1, tap = dy * 3 + dx;
+      v = (blockIdx.y == 6) ? a.w5[(c * CH + g * 8 + e) * 9 + tap] : a.w1[((g * 8 + e) * 2 + c) * 9 + (8 - tap)];
+    }
     (blockIdx.y == 6 ? a.t5 : a.t1)[i] = __float2bfloat16_rn(v);
     return;
   }
@@ -134,30 +152,82 @@ __device__ __forceinline__ void tile_coords(int t, int H, int ntw, int& b, int& 
   b = r / H;
 }
 
+template <int NOUT>
 __device__ __forceinline__ void issue_halo(const CUtensorMap* map, uint8_t* dst, uint64_t* bar, int t,
                                            int H, int ntw) {
+  using CL = ConvLayout<NOUT>;
   int b, h, wt;
   tile_coords(t, H, ntw, b, h, wt);
-  mbar_expect_tx(bar, HALO_TX);
-  // one box {64 channels, 130 pixels, 3 rows}: [row][pixel][128 bytes], 128-byte swizzled
-  tma_load_4d(dst, map, 0, wt * TILE_M - 1, h - 1, b, bar);
+  mbar_expect_tx(bar, CL::HALO_TX);
+  // one box {64 channels, HALO_PX pixels, 3 rows}: [row][pixel][128 bytes], 128-byte swizzled;
+  // halo pixel p is image pixel wt * TILE_OUT - 1 + p
+  tma_load_4d(dst, map, 0, wt * CL::TILE_OUT - 1, h - 1, b, bar);
 }
 
 template <int NOUT>
 __device__ __forceinline__ void issue_mma(uint32_t tmem_d, uint32_t halo, uint32_t wts) {
-  const uint32_t idesc = umma_idesc_bf16(TILE_M, NOUT);
+  using CL = ConvLayout<NOUT>;
+  constexpr int NCOL = CL::NCOL;
+  const uint32_t idesc = umma_idesc_bf16(TILE_M, NCOL);
+  if constexpr (CL::SHIFT) {
 #pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap - dy * 3;
+    for (int dy = 0; dy < 3; ++dy) {
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      // A: 128 pixels starting at halo pixel (dy, dx), channels 16 kk .. 16 kk + 15
-      const uint64_t ad = umma_desc_sw128(halo + (dy * HALO_W + dx) * 128 + kk * 32);
-      const uint64_t bd = umma_desc(wts + (tap * 8 + 2 * kk) * (NOUT * 16), NOUT * 16, 128);
-      umma_bf16(tmem_d, ad, bd, idesc, (tap | kk) != 0);
+      for (int kk = 0; kk < 4; ++kk) {
+        // A: the 128 halo pixels of row dy, channels 16 kk .. 16 kk + 15; B: taps (dy, 0..2)
+        const uint64_t ad = umma_desc_sw128(halo + dy * CL::HALO_ROWB + kk * 32);
+        const uint64_t bd = umma_desc(wts + (dy * 8 + 2 * kk) * (NCOL * 16), NCOL * 16, 128);
+        umma_bf16(tmem_d, ad, bd, idesc, (dy | kk) != 0);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        // A: 128 pixels starting at halo pixel (dy, dx), channels 16 kk .. 16 kk + 15
+        const uint64_t ad = umma_desc_sw128(halo + (dy * CL::HALO_PX + dx) * 128 + kk * 32);
+        const uint64_t bd = umma_desc(wts + (tap * 8 + 2 * kk) * (NCOL * 16), NCOL * 16, 128);
+        umma_bf16(tmem_d, ad, bd, idesc, (tap | kk) != 0);
+      }
     }
   }
 }
+
+// Epilogue helpers: 16 output channels of one pixel, bias + ReLU (forward) or the ReLU mask of
+// the previous activation (input gradient), stored as BF16.
+__device__ __forceinline__ void conv_store16(const float (&o)[16], int cb, int mode, const float* s_bias,
+                                             const uint4 (&mrow)[8], __nv_bfloat16* dst) {
+  float v[16];
+  if (mode == 0) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = fmaxf(o[e] + s_bias[cb * 16 + e], 0.f);
+  } else {
+    const uint4 m0 = mrow[2 * cb], m1 = mrow[2 * cb + 1];
+    const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+    const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[e] = (bf(mb0[e]) > 0.f) ? o[e] : 0.f;
+      v[8 + e] = (bf(mb1[e]) > 0.f) ? o[8 + e] : 0.f;
+    }
+  }
+  uint4 o0, o1;
+  __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(&o0);
+  __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(&o1);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    p0[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+    p1[e] = __floats2bfloat162_rn(v[8 + 2 * e], v[8 + 2 * e + 1]);
+  }
+  uint4* op = reinterpret_cast<uint4*>(dst + cb * 16);
+  op[0] = o0;
+  op[1] = o1;
+}
+
+// Named barrier of the four epilogue warps (the producer warp does not take part).
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Warp-specialised persistent kernel, one 128-pixel row segment per tile, 3x3 taps as 36 MMAs of
 // K = 16 over the halo (M = 128 pixels, N = NOUT).  NOUT = 64: the 64 -> 64 layers (epilogue
@@ -229,7 +299,7 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
       bulk_load(smem + CL::OFF_W, a.wpack, CL::WP, w_full);
       const int pre = n < 2 ? n : 2;
       for (int j = 0; j < pre; ++j) {
-        issue_halo(&tmap, s_halo + j * HALO_BYTES, &halo_full[j], blockIdx.x + j * gridDim.x, a.H, a.ntw);
+        issue_halo<NOUT>(&tmap, s_halo + j * CL::HALO_SLOT, &halo_full[j], blockIdx.x + j * gridDim.x, a.H, a.ntw);
         ++tma_issued;
       }
       ok = mbar_wait(w_full, 0);
@@ -239,7 +309,7 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
         if (ok && i >= 2) ok = mbar_wait(&tm_empty[t], ((i - 2) >> 1) & 1);
         if (!ok) break;
         tc_fence_after();
-        issue_mma<NOUT>(tmem + t * NOUT, smem_u32(s_halo + s * HALO_BYTES), sw);
+        issue_mma<NOUT>(tmem + t * CL::TCOL, smem_u32(s_halo + s * CL::HALO_SLOT), sw);
         umma_commit(&tm_full[t]);
         umma_commit(&halo_empty[s]);
         ++mma_issued;
@@ -248,15 +318,15 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
           const int s2 = (i + 2) % NHALO;
           if (i >= 1) ok = mbar_wait(&halo_empty[s2], ((i - 1) / NHALO) & 1);
           if (!ok) break;
-          issue_halo(&tmap, s_halo + s2 * HALO_BYTES, &halo_full[s2], blockIdx.x + (i + 2) * gridDim.x, a.H,
-                     a.ntw);
+          issue_halo<NOUT>(&tmap, s_halo + s2 * CL::HALO_SLOT, &halo_full[s2], blockIdx.x + (i + 2) * gridDim.x,
+                           a.H, a.ntw);
           ++tma_issued;
         }
       }
       if (!ok) atomicExch(s_err, 1);
     }
-  } else {
-    // epilogue: warp w owns pixels 32w .. 32w + 31 of each tile
+  } else if constexpr (!CL::SHIFT) {
+    // epilogue (NOUT = 64): warp w owns pixels 32w .. 32w + 31 of each tile
     for (int i = 0; i < n; ++i) {
       const int t = i & 1;
       if (!mbar_wait(&tm_full[t], (i >> 1) & 1)) {
@@ -266,21 +336,9 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
       tc_fence_after();
       int b, h, wt;
       tile_coords(blockIdx.x + i * gridDim.x, a.H, a.ntw, b, h, wt);
-      const int px = wt * TILE_M + warp * 32 + lane;
+      const int px = wt * CL::TILE_OUT + warp * 32 + lane;
       const bool valid = px < a.W;
       const size_t pix = ((size_t)b * a.H + h) * a.W + px;
-      if constexpr (NOUT == 16) {  // 64 -> 2: two accumulator columns, residual, complex output
-        float2 acc2;
-        tmem_ld2(tmem + ((uint32_t)(warp * 32) << 16) + t * NOUT, acc2);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tm_empty[t]);
-        if (valid) {
-          const float2 rv = a.res[pix];
-          a.out2[pix] = make_float2(rv.x + s_bias[0] + acc2.x, rv.y + s_bias[1] + acc2.y);
-        }
-        continue;
-      }
       // input-gradient mode: the whole 128-byte ReLU-mask row of this pixel in one batch of loads
       uint4 mrow[8];
       if (a.mode == 1 && valid) {
@@ -289,7 +347,7 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
         for (int q = 0; q < 8; ++q) mrow[q] = ap[q];
       }
       float acc[64];
-      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + t * NOUT, acc);
+      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + t * CL::TCOL, acc);
       // the accumulators are in registers: hand the TMEM half back to the producer
       tc_fence_before();
       __syncwarp();
@@ -297,32 +355,69 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
       if (valid) {
 #pragma unroll
         for (int cb = 0; cb < 4; ++cb) {
-          float* v = acc + cb * 16;
-          if (a.mode == 0) {
+          float o[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_bias[cb * 16 + e], 0.f);
-          } else {
-            const uint4 m0 = mrow[2 * cb], m1 = mrow[2 * cb + 1];
-            const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
-            const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              if (!(bf(mb0[e]) > 0.f)) v[e] = 0.f;
-              if (!(bf(mb1[e]) > 0.f)) v[8 + e] = 0.f;
-            }
-          }
-          uint4 o0, o1;
-          __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(&o0);
-          __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(&o1);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            p0[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-            p1[e] = __floats2bfloat162_rn(v[8 + 2 * e], v[8 + 2 * e + 1]);
-          }
-          uint4* op = reinterpret_cast<uint4*>(a.out + pix * CH + cb * 16);
-          op[0] = o0;
-          op[1] = o1;
+          for (int e = 0; e < 16; ++e) o[e] = acc[cb * 16 + e];
+          conv_store16(o, cb, a.mode, s_bias, mrow, a.out + pix * CH);
         }
+      }
+    }
+  } else {
+    // epilogue (NOUT = 16, 64 -> 2): warp w owns halo pixels 32w .. 32w + 31 of each tile (TMEM
+    // lanes).  Lane l forms the output at halo pixel p = 32w + l from D_0[p] + D_1[p + 1] +
+    // D_2[p + 2]: neighbours in the warp by shuffles; lanes 30 and 31 need lanes 0 and 1 of the
+    // next warp, which publish D_1[p0] + D_2[p0 + 1] (for lane 31) and D_2[p0] (for lane 30) in the
+    // exchange buffer while lanes 30 and 31 park their partial sums there; after one named barrier
+    // of the epilogue warps they finish.  After a timed-out wait a warp stops waiting and reading
+    // TMEM but keeps taking part in the barriers (one per tile).
+    constexpr int CO = CL::CO;
+    float* xch_base = reinterpret_cast<float*>(smem + CL::OFF_XCH);
+    bool fail = false;
+    for (int i = 0; i < n; ++i) {
+      const int t = i & 1;
+      if (!fail) {
+        const bool ok_wait = mbar_wait(&tm_full[t], (i >> 1) & 1);
+        if (!ok_wait && lane == 0) atomicExch(s_err, 1);
+        fail = __any_sync(0xffffffffu, !ok_wait);
+      }
+      tc_fence_after();
+      int b, h, wt;
+      tile_coords(blockIdx.x + i * gridDim.x, a.H, a.ntw, b, h, wt);
+      const int p = warp * 32 + lane;
+      const int px = wt * CL::TILE_OUT + p;
+      const bool valid = p < CL::TILE_OUT && px < a.W;
+      const size_t pix = ((size_t)b * a.H + h) * a.W + px;
+      float* xw = xch_base + (size_t)(t * 4 + warp) * 4 * CO;             // this warp's rows
+      const float* xn = xch_base + (size_t)(t * 4 + warp + 1) * 4 * CO;   // the next warp's rows
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + t * CL::TCOL;
+      float d[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (!fail) tmem_ld8(trow, d);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tm_empty[t]);
+      float o[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float s1 = __shfl_down_sync(0xffffffffu, d[2 + c], 1);
+        const float s2 = __shfl_down_sync(0xffffffffu, d[4 + c], 2);
+        const float s21 = __shfl_down_sync(0xffffffffu, d[4 + c], 1);
+        o[c] = d[c] + (lane < 31 ? s1 : 0.f) + (lane < 30 ? s2 : 0.f);
+        if (lane == 0) {
+          xw[0 * CO + c] = d[2 + c] + s21;  // D_1[p0] + D_2[p0 + 1]
+          xw[1 * CO + c] = d[4 + c];        // D_2[p0]
+        }
+        if (lane >= 30) xw[(2 + lane - 30) * CO + c] = o[c];
+      }
+      if (lane < 30 && valid) {
+        const float2 rv = a.res[pix];
+        a.out2[pix] = make_float2(rv.x + s_bias[0] + o[0], rv.y + s_bias[1] + o[1]);
+      }
+      epi_bar();
+      if (lane >= 30 && warp < 3 && valid) {
+        const float* part = xw + (2 + lane - 30) * CO;
+        const float* add = xn + (lane == 31 ? 0 : 1) * CO;
+        const float2 rv = a.res[pix];
+        a.out2[pix] = make_float2(rv.x + s_bias[0] + (part[0] + add[0]), rv.y + s_bias[1] + (part[1] + add[1]));
       }
     }
   }
@@ -887,7 +982,7 @@ EncodeTiledFn get_encode() {
 // Tensor map over a BF16 [B][H][W][64] activation; box 8 ch x 130 px x 3 rows x 1 slice.
 // 4-D map {channel, pixel, row, slice} of a channels-last BF16 tensor, 128-byte swizzle; boxes of
 // box_px pixels x box_rows rows (the convolution halo by default).
-int make_act_map(CUtensorMap* m, const void* base, int B, int H, int W, int box_px = HALO_W, int box_rows = 3) {
+int make_act_map(CUtensorMap* m, const void* base, int B, int H, int W, int box_px = TILE_M, int box_rows = 3) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return SENSE_ECUDA;
   const cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
@@ -934,10 +1029,13 @@ int conv_prepare() {
 int launch_conv64(const __nv_bfloat16* in, const __nv_bfloat16* wpack, const float* bias,
                   const __nv_bfloat16* aprev, __nv_bfloat16* out, int mode, int B, int H, int W,
                   int* status, cudaStream_t st, const float2* res = nullptr, float2* out2 = nullptr) {
+  const bool two = mode >= 2;  // 64 -> 2 layers (NOUT = 16)
+  const int halo_px = two ? ConvLayout<16>::HALO_PX : ConvLayout<64>::HALO_PX;
+  const int tile_out = two ? ConvLayout<16>::TILE_OUT : ConvLayout<64>::TILE_OUT;
   CUtensorMap map;
-  if (int e = make_act_map(&map, in, B, H, W)) return e;
+  if (int e = make_act_map(&map, in, B, H, W, halo_px, 3)) return e;
   ConvArgs a;
-  a.B = B; a.H = H; a.W = W; a.ntw = (W + TILE_M - 1) / TILE_M;
+  a.B = B; a.H = H; a.W = W; a.ntw = (W + tile_out - 1) / tile_out;
   a.wpack = wpack; a.bias = bias; a.aprev = aprev; a.out = out; a.mode = mode; a.status = status;
   a.res = res; a.out2 = out2;
   const int ntiles = B * H * a.ntw;

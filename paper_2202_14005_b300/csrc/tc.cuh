@@ -142,6 +142,18 @@ SENSE_D void tmem_ld2(uint32_t taddr, float2& v) {
   v = make_float2(__uint_as_float(r0), __uint_as_float(r1));
 }
 
+// 32 lanes x 32 bit, 8 consecutive columns.
+SENSE_D void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 32 lanes x 32 bit, 64 consecutive columns in one load and one completion wait (a single
 // round trip to tensor memory for a whole 64-channel accumulator row).
 SENSE_D void tmem_ld64(uint32_t taddr, float (&v)[64]) {

@@ -73,7 +73,7 @@ def run_forward(B, H, W, seed=0):
     return dn, ws, bs, flat, x, out.cpu().numpy(), acts
 
 
-@pytest.mark.parametrize("shape", [(2, 12, 150), (1, 9, 64), (2, 40, 232)])
+@pytest.mark.parametrize("shape", [(2, 12, 150), (1, 9, 64), (2, 40, 232), (1, 5, 126), (1, 4, 130), (1, 3, 128), (1, 3, 254)])
 def test_forward_per_layer(shape):
     B, H, W = shape
     dn, ws, bs, flat, x, out, acts = run_forward(B, H, W, seed=B + H)
