@@ -102,6 +102,47 @@ __device__ __forceinline__ void bfly_out(const float2* in, float2* out, int j, i
   out[(j / Ns) * Ns * R + jm + kout * Ns] = acc;
 }
 
+// Power-of-two lengths with the stage structure fixed at compile time: the same radix order as
+// the generic plan (radix 8 while it divides, then one radix 4 or 2 stage), the same twiddles
+// and butterflies, with every stride, mask and shift a constant (no per-butterfly divisions or
+// radix dispatch).
+template <int R, bool INV, int NS, int L>
+__device__ __forceinline__ void bfly_p2(const float2* in, float2* out, int j, const float2* tw) {
+  constexpr int stride = L / R;
+  float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
+  const int k = j & (NS - 1);
+  if constexpr (NS > 1) {
+    const int step = k * (L / (NS * R));
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const float2 w = __ldg(tw + step * r);
+      v[r] = INV ? cmulc(w, v[r]) : cmul(v[r], w);
+    }
+  }
+  dft_pow2<R, INV>(v);
+  const int idxD = (j / NS) * NS * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[idxD + r * NS] = v[r];
+}
+
+template <bool INV, int L, int NS>
+__device__ __forceinline__ float2* fft_p2(float2* a, float2* b, int ntr, const float2* tw, int ld) {
+  if constexpr (NS >= L) {
+    return a;
+  } else {
+    constexpr int R = (L / NS >= 8) ? 8 : L / NS;
+    constexpr int NB = L / R;
+    for (int w = threadIdx.x; w < ntr * NB; w += blockDim.x) {
+      const int tr = w / NB, j = w - tr * NB;
+      bfly_p2<R, INV, NS, L>(a + tr * ld, b + tr * ld, j, tw);
+    }
+    __syncthreads();
+    return fft_p2<INV, L, NS * R>(b, a, ntr, tw, ld);
+  }
+}
+
 // Transform ntr sequences of length L held in a at stride ld (>= L; ping-pong with b).  Column
 // passes use ld = L + 1: the transposing loads and stores of neighbouring columns then fall into
 // different shared-memory banks.  Returns the buffer holding the result.  All threads take part.
@@ -112,6 +153,16 @@ __device__ __forceinline__ void bfly_out(const float2* in, float2* out, int j, i
 template <bool INV, int CLS>
 __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, int ld) {
   const int L = f.L;
+  if constexpr (CLS == 0) {  // compile-time plans for the common power-of-two lengths
+    switch (L) {
+      case 64: return fft_p2<INV, 64, 1>(a, b, ntr, f.tw, ld);
+      case 128: return fft_p2<INV, 128, 1>(a, b, ntr, f.tw, ld);
+      case 256: return fft_p2<INV, 256, 1>(a, b, ntr, f.tw, ld);
+      case 512: return fft_p2<INV, 512, 1>(a, b, ntr, f.tw, ld);
+      case 1024: return fft_p2<INV, 1024, 1>(a, b, ntr, f.tw, ld);
+      default: break;
+    }
+  }
   int Ns = 1;
   for (int s = 0; s < f.nst; ++s) {
     const int R = f.radix[s];
@@ -330,16 +381,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_combine(int S, int C, int H
   }
 }
 
-// out[b] = sum over coil groups g (in order) of T[b, g cpg] (+ lambda xin[b]); one map set.
-__global__ void k_coil_groups_sum(int B, int C, int HW, int cpg, const float2* T, const float2* xin,
+// out[b] = sum over coil groups g (in order) of T[b, g cpg] (+ lambda xin[b]); one map set.  T
+// holds H rows of ldT entries per coil, of which the first W are used.
+__global__ void k_coil_groups_sum(int B, int C, int H, int W, int ldT, int cpg, const float2* T, const float2* xin,
                                   float lam_host, const double* lam_dev, float2* out) {
+  const int HW = H * W;
   const size_t n = (size_t)B * HW;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(i / HW);
-    const size_t q = i - (size_t)b * HW;
+    const int q = (int)(i - (size_t)b * HW);
+    const int h = q / W, w = q - h * W;
     float2 v = make_float2(0.f, 0.f);
     for (int c = 0; c < C; c += cpg) {
-      const float2 t = T[((size_t)b * C + c) * HW + q];
+      const float2 t = T[(((size_t)b * C + c) * H + h) * ldT + w];
       v.x += t.x;
       v.y += t.y;
     }
@@ -384,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_fwd(int C, int H, int W
 }
 
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, 2) k_tp_cols(int H, int W2, float2* T, Fft1DDev f,
+__global__ void __launch_bounds__(kThreads, 3) k_tp_cols(int H, int W2, float2* T, Fft1DDev f,
                                                       const float2* psf_hat) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int H2 = f.L, ld = H2 + 1;
@@ -416,11 +470,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_cols(int H, int W2, float2* 
   }
 }
 
+// With cpg < C, CTA z sums coils z cpg .. z cpg + cpg - 1 and writes that partial sum over the
+// first W entries of the rows of coil z cpg it has just read; k_coil_groups_sum (row stride 2W)
+// adds the groups in fixed order and + lambda x.
 template <int CLS>
-__global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W, const float2* T,
+__global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W, float2* T,
                                                           const float2* maps, float2* out, Fft1DDev f,
                                                           const float2* xin, float lam_host,
-                                                          const double* lam_dev) {
+                                                          const double* lam_dev, int cpg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W2 = f.L;
   float2* a = reinterpret_cast<float2*>(smem);
@@ -428,10 +485,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
   const int b = blockIdx.y;
   const int h0 = blockIdx.x * kRows;
   const int nr = min(kRows, H - h0);
+  const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
   float2 acc[kMaxPer];
 #pragma unroll
   for (int e = 0; e < kMaxPer; ++e) acc[e] = make_float2(0.f, 0.f);
-  for (int c = 0; c < C; ++c) {
+  for (int c = c0; c < c1; ++c) {
     for (int i = threadIdx.x; i < nr * W2; i += blockDim.x)
       a[i] = T[(((size_t)b * C + c) * H + h0) * W2 + i];
     __syncthreads();
@@ -446,6 +504,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
       }
     }
     __syncthreads();
+  }
+  if (cpg < C) {  // partial sum of this coil group over the rows of coil c0 (already read)
+#pragma unroll
+    for (int e = 0; e < kMaxPer; ++e) {
+      const int i = threadIdx.x + e * blockDim.x;
+      if (i < nr * W) {
+        const int r = i / W, w = i - r * W;
+        T[(((size_t)b * C + c0) * H + h0 + r) * W2 + w] = acc[e];
+      }
+    }
+    return;
   }
   const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
 #pragma unroll
@@ -634,7 +703,8 @@ int launch_row_combine(sense_plan p, float2* out, int mode, const float2* xin, f
     const int HW = p->H * p->W;
     const long long n = (long long)p->B * HW;
     const int grid = (int)std::min<long long>((n + 255) / 256, 2048LL);
-    k_coil_groups_sum<<<grid, 256, 0, p->stream>>>(p->B, p->C, HW, cpg, p->w.T, xin, lam_host, lam_dev, out);
+    k_coil_groups_sum<<<grid, 256, 0, p->stream>>>(p->B, p->C, p->H, p->W, p->W, cpg, p->w.T, xin, lam_host,
+                                                    lam_dev, out);
     count_launch(p, 1);
   }
   prof_mark("fft_generic", p->stream, true);
@@ -721,9 +791,22 @@ int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam
   const dim3 gc((W2 + kCols - 1) / kCols, p->B * p->C);
   SENSE_LAUNCH_CLS(fft_class(p->fH2), k_tp_cols, gc, smem_cols(2 * p->H), p->stream, p->H, W2, p->w.T,
                    dev(p->fH2), p->psf_hat);
-  const dim3 gr2((p->H + kRows - 1) / kRows, p->B);
+  // inverse rows and coil combine, the coils split into groups across grid.z (about 2048 CTAs)
+  const int nrb = (p->H + kRows - 1) / kRows;
+  int groups = (2048 + nrb * p->B - 1) / (nrb * p->B);
+  groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
+  const int cpg = (p->C + groups - 1) / groups;
+  groups = (p->C + cpg - 1) / cpg;
+  const dim3 gr2(nrb, p->B, groups);
   SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows(W2), p->stream, p->C, p->H, p->W, p->w.T,
-                   p->maps, out, dev(p->fW2), x, lam_host, lam_dev);
+                   p->maps, out, dev(p->fW2), x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
+  if (groups > 1) {
+    const long long n = (long long)p->B * p->H * p->W;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 2048LL);
+    k_coil_groups_sum<<<grid, 256, 0, p->stream>>>(p->B, p->C, p->H, p->W, W2, cpg, p->w.T, x, lam_host, lam_dev,
+                                                    out);
+    count_launch(p, 1);
+  }
   prof_mark("toeplitz", p->stream, true);
   count_launch(p, 3);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
