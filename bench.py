@@ -143,6 +143,29 @@ class ClockSampler:
                 "reasons": sorted(self.reasons), "samples": len(self.sm), "source": "nvml"}
 
 
+# ------------------------------------------------------------- replicas
+# Slices are independent (one CG per slice, per-slice scalars), so N GPUs run N replicas on
+# disjoint slice ranges; the only exchange is the max of the timed region over ranks.
+def replica_slice_offset(rank, slices_per_rank):
+    """First seeded slice of this rank: rank r takes slices r*B .. r*B + B - 1."""
+    return rank * slices_per_rank
+
+
+def max_over_ranks(t_ms, dist, device):
+    """The job's time is the slowest rank's (all-reduce MAX of one double)."""
+    if not dist:
+        return t_ms
+    import torch
+    t = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(slices_per_rank, world, steps, t_ms):
+    """Aggregate slices/s over all ranks for `steps` steps that took t_ms (max over ranks)."""
+    return slices_per_rank * world * steps / (t_ms * 1e-3)
+
+
 # ------------------------------------------------------------- workload
 def make_inputs(cfg, slice_offset=0):
     import numpy as np
@@ -229,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---------------- plain CG-SENSE on the 16-slice batch (secondary, or main)
     c2 = synth.CONFIGS[2]
-    inp2 = make_inputs(c2, slice_offset=rank * c2.B)
+    inp2 = make_inputs(c2, slice_offset=replica_slice_offset(rank, c2.B))
     maps2 = torch.from_numpy(inp2["maps"]).to(dev)
     mask2 = torch.from_numpy(inp2["mask"]).to(dev)
     plan2 = SensePlan(maps2, mask2)
@@ -353,7 +376,7 @@ def run_ours(args, rank, world, local_rank):
         from paper_2202_14005_b300.sense import toeplitz_psf
         c5 = synth.CONFIGS[5]
         cfg = c5
-        inp5 = make_inputs(c5, slice_offset=rank * c5.B)
+        inp5 = make_inputs(c5, slice_offset=replica_slice_offset(rank, c5.B))
         maps5 = torch.from_numpy(inp5["maps"]).to(dev)
         traj = synth.radial_trajectory(c5.extra["spokes"], c5.extra["samples"], c5.H).reshape(-1, 2)
         psf = toeplitz_psf(torch.from_numpy(traj.astype(np.float32)).to(dev), c5.H, c5.W)
@@ -425,7 +448,7 @@ def run_ours(args, rank, world, local_rank):
         from paper_2202_14005_b300.varnet import VarNetTrainer, pack_params
         c4 = synth.CONFIGS[4]
         cfg = c4
-        inp4 = make_inputs(c4, slice_offset=rank * c4.B)
+        inp4 = make_inputs(c4, slice_offset=replica_slice_offset(rank, c4.B))
         maps4 = torch.from_numpy(inp4["maps"]).to(dev)
         mask4 = torch.from_numpy(inp4["mask"]).to(dev)
         filt, rbfw, lamv = synth.varnet_weights(4000 + rank, c4.extra["T"])
@@ -463,7 +486,7 @@ def run_ours(args, rank, world, local_rank):
     else:
         c3 = synth.CONFIGS[3]
         cfg = c3
-        inp3 = make_inputs(c3, slice_offset=rank * c3.B)
+        inp3 = make_inputs(c3, slice_offset=replica_slice_offset(rank, c3.B))
         maps3 = torch.from_numpy(inp3["maps"]).to(dev)
         mask3 = torch.from_numpy(inp3["mask"]).to(dev)
         ws, bs = synth.modl_cnn_weights(3000 + rank)
@@ -500,10 +523,7 @@ def run_ours(args, rank, world, local_rank):
                        "nrmse_untrained_forward": round(float(np.linalg.norm(tr.xs[-1].cpu().numpy() - inp3["x_gt"])
                                                               / np.linalg.norm(inp3["x_gt"])), 5)}
 
-    if dist:
-        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(t_ms, dist, dev)
 
     # per-kernel roofline inside the timed region
     Hc, Wc = cfg.H, cfg.W
@@ -551,7 +571,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return None
-    value = value_slices * world * steps / (t_ms * 1e-3)
+    value = whole_job_value(value_slices, world, steps, t_ms)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "slices/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(t_ms / steps, 4),
