@@ -110,9 +110,30 @@ struct PackArgs {
   const float* w5;       // last layer [2][64][9]
   __nv_bfloat16* t5;     // last layer forward: w5[c][g*8+e][3 dy + dx] at n = 2 dx + c
   __nv_bfloat16* t1;     // first layer input gradient: w1[g*8+e][c][8 - (3 dy + dx)] at n = 2 dx + c
+  uint32_t* f1;          // first layer forward, mma.sync B fragments [2 ks][8 nt][32 lanes][2]
+  uint32_t* f5;          // last layer input gradient, B fragments [4 ks][8 nt][32 lanes][2]
 };
+// mma.sync m16n8k16 B fragment element pair (k, k + 1) of column j for the 2 -> 64 layers:
+//   first layer forward: k = 9 c + tap < 18, W = w1[j][c][tap]
+//   last layer input gradient: k = 18 part + 9 c + tap < 54, W = w5[c][j][tap] (each BF16 term)
+__device__ __forceinline__ float w2to64(const float* w, int mode, int k, int j) {
+  if (k >= (mode == 0 ? 18 : 54)) return 0.f;
+  const int kk = k % 18, c = kk / 9, tap = kk % 9;
+  return mode == 0 ? w[(j * 2 + c) * 9 + tap] : w[(c * CH + j) * 9 + tap];
+}
 __global__ void k_pack64(const PackArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9*8*64*8
+  if (blockIdx.y >= 8) {  // B fragments of the 2 -> 64 layers, in the order a lane loads them
+    const int mode = blockIdx.y - 8, ks_n = mode == 0 ? 2 : 4;
+    if (i >= ks_n * 8 * 32 * 2) return;
+    const int hf = i & 1, lane = (i >> 1) & 31, nt = (i >> 6) & 7, ks = i >> 9;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int k = 16 * ks + 2 * tig + 8 * hf, j = 8 * nt + gid;
+    const float* w = mode == 0 ? a.w1 : a.w5;
+    __nv_bfloat162 v = __floats2bfloat162_rn(w2to64(w, mode, k, j), w2to64(w, mode, k + 1, j));
+    (mode == 0 ? a.f1 : a.f5)[i] = *reinterpret_cast<uint32_t*>(&v);
+    return;
+  }
   if (blockIdx.y >= 6) {  // 64 -> 2 tables of the first and last layers (N = 16, 6 live rows)
     if (i >= 3 * 8 * 16 * 8) return;
     const int e = i & 7, n = (i >> 3) & 15, g = (i >> 7) & 7, dy = i >> 10;
@@ -443,94 +464,169 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
 // ------------------------------------------------ 2-channel layers
 // All convolution weights are used in BF16 (rounded when packed); sums are FP32.
 
-// 2 -> 64 on CUDA cores.  A CTA takes k2Rows full image rows of one slice; their 2-channel
-// (k2Rows + 2) x (W + 2) neighbourhood and the 64 x 18 BF16-rounded weights are staged in shared
-// memory.  Thread t owns output channels 4 (t mod 16) .. + 3 (72 weights in registers) for the
-// pixels t / 16, t / 16 + 16, ... of each row, so that 16 threads write one pixel's 128 bytes.
-// n[r][q] = 2-channel source at (h - 1 + r, q - 1); output channel j of pixel (h, w):
-//   mode 0 (first layer):   relu(b[j] + sum_{c,tap} W[j][c][tap] * xr(n[dy][w + dx])), xr = BF16(x)
-//   mode 1 (last layer input gradient): [a4 > 0] * sum_{c,tap} W5[c][j][tap] * g(n[2 - dy][w + 2 - dx])
+// 2 -> 64 on the warp-level tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation).
+// A CTA takes k2Rows image rows of one slice and stages their 2-channel (k2Rows + 2) x (W + 2)
+// neighbourhood (zero outside the image); each warp takes 16-pixel groups of a row:
+//   out[p][j] = sum_k A[p][k] W[k][j],  A = im2col of the neighbourhood, W in BF16,
+//   mode 0 (first layer):   k = 9 c + tap (18, padded to 32), A = BF16(x) at (dy, dx); the
+//                           products are exact, so only the summation order differs from a
+//                           sequential FP32 sum; out = relu(b + sum)
+//   mode 1 (last layer input gradient): k = 18 part + 9 c + tap (54, padded to 64), A = the FP32
+//                           gradient at (2 - dy, 2 - dx) as three BF16 terms g1 + g2 + g3 (24
+//                           significant bits); out = [a4 > 0] * sum, W = w5[c][j][tap]
+// The 16 x 64 result of a group goes through shared memory (rows padded to 144 bytes) so that
+// pixels are written as whole 128-byte rows, the ReLU mask of mode 1 read the same way.
 constexpr int k2Rows = 2;
 constexpr int k2Threads = 256;
-int k2_smem(int W) { return ((k2Rows + 2) * (W + 2) * 2 + CH * 18) * (int)sizeof(float); }
+constexpr int k2Ld = 72;  // bf16 per staged output row (144 bytes: conflict-free fragment stores)
+int k2_smem(int W) {
+  return (k2Rows + 2) * (W + 2) * (int)sizeof(float2) + (k2Threads / 32) * 16 * k2Ld * 2 + 4 * 8 * 32 * 2 * 4;
+}
 
-__global__ void __launch_bounds__(k2Threads) k_2to64(int B, int H, int W, int mode, const float2* src,
-                                                     const float* wsrc, const float* bias,
-                                                     const __nv_bfloat16* mask_src, __nv_bfloat16* out) {
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(k2Threads) k_2to64(int B, int H, int W, const float2* src, const uint32_t* frag,
+                                                     const float* bias, const __nv_bfloat16* mask_src,
+                                                     __nv_bfloat16* out) {
+  constexpr int KS = MODE == 0 ? 2 : 4;  // k-steps of 16
+  constexpr int KV = MODE == 0 ? 18 : 54;
   extern __shared__ __align__(16) uint8_t dsm[];
-  float2* s_n = reinterpret_cast<float2*>(dsm);                        // [k2Rows + 2][W + 2]
-  float* s_w = reinterpret_cast<float*>(s_n + (k2Rows + 2) * (W + 2));  // [j][c][tap]
+  float2* s_n = reinterpret_cast<float2*>(dsm);  // [k2Rows + 2][W + 2]
+  const int ld = W + 2;
+  __nv_bfloat16* s_o = reinterpret_cast<__nv_bfloat16*>(dsm + (size_t)(k2Rows + 2) * ld * sizeof(float2));
+  uint2* s_f = reinterpret_cast<uint2*>(s_o + (k2Threads / 32) * 16 * k2Ld);  // [KS][8][32] fragment pairs
+  for (int i = threadIdx.x; i < KS * 8 * 32; i += blockDim.x) s_f[i] = reinterpret_cast<const uint2*>(frag)[i];
   const int nrb = (H + k2Rows - 1) / k2Rows;
   const int b = blockIdx.x / nrb, h0 = (blockIdx.x % nrb) * k2Rows;
   const int nrows = min(k2Rows, H - h0);
-  const int ld = W + 2;
   for (int i = threadIdx.x; i < (nrows + 2) * ld; i += blockDim.x) {
     const int r = i / ld, q = i - r * ld;
     const int yy = h0 - 1 + r, xx = q - 1;
     float2 v = make_float2(0.f, 0.f);
     if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = src[((size_t)b * H + yy) * W + xx];
-    if (mode == 0) v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
+    if (MODE == 0) v = make_float2(bf(__float2bfloat16_rn(v.x)), bf(__float2bfloat16_rn(v.y)));
     s_n[i] = v;
   }
-  for (int i = threadIdx.x; i < CH * 18; i += blockDim.x) {
-    const int j = i / 18, c = (i / 9) % 2, tap = i % 9;
-    const float v = (mode == 0) ? wsrc[(j * 2 + c) * 9 + tap] : wsrc[(c * CH + j) * 9 + tap];
-    s_w[i] = bf(__float2bfloat16_rn(v));
-  }
-  __syncthreads();
-  const int cq = threadIdx.x & 15, pl = threadIdx.x >> 4;
-  // weights of the channel pairs (4cq, 4cq + 1) and (4cq + 2, 4cq + 3): packed FP32x2 FMAs
-  float2 wr[2][18];
-  float2 bj[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gid = lane >> 2, tig = lane & 3;
+  // B fragments (k-step ks, n-tile nt: b0 = W[16 ks + 2 tig (+1)][8 nt + gid], b1 = rows + 8) come
+  // from the table packed with the weights, one shared-memory pair per (ks, nt) and lane
+  // this lane's A columns: for k-step ks and slot sl (k = 16 ks + 2 tig + (sl & 1) + 8 (sl >> 1)),
+  // the neighbourhood offset, channel and BF16 term (or -1 for padding)
+  int aoff[KS][4], acomp[KS][4];
 #pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int j0 = cq * 4 + 2 * e;
-    bj[e] = (mode == 0) ? make_float2(bias[j0], bias[j0 + 1]) : make_float2(0.f, 0.f);
+  for (int ks = 0; ks < KS; ++ks)
 #pragma unroll
-    for (int k = 0; k < 18; ++k) wr[e][k] = make_float2(s_w[j0 * 18 + k], s_w[(j0 + 1) * 18 + k]);
-  }
-  constexpr int kStep = k2Threads / 16;  // pixels between a thread's consecutive pixels
-  const uint2* mrow =
-      mode == 1 ? reinterpret_cast<const uint2*>(mask_src + ((size_t)b * H + h0) * W * CH) + cq : nullptr;
-  for (int r = 0; r < nrows; ++r) {
-    const int h = h0 + r;
-    // input-gradient mode: the mask of the thread's next pixel is loaded one pixel ahead
-    uint2 mnext = make_uint2(0u, 0u);
-    if (mode == 1 && pl < W) mnext = mrow[((size_t)r * W + pl) * (CH / 4)];
-    for (int w = pl; w < W; w += kStep) {
-      const uint2 m = mnext;
-      if (mode == 1 && w + kStep < W) mnext = mrow[((size_t)r * W + w + kStep) * (CH / 4)];
-      float2 acc[2] = {bj[0], bj[1]};
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-        const float2 v = (mode == 0) ? s_n[(r + dy) * ld + w + dx] : s_n[(r + 2 - dy) * ld + w + 2 - dx];
-        const float2 vx = make_float2(v.x, v.x), vy = make_float2(v.y, v.y);
-#pragma unroll
-        for (int e = 0; e < 2; ++e) acc[e] = __ffma2_rn(wr[e][9 + tap], vy, __ffma2_rn(wr[e][tap], vx, acc[e]));
-      }
-      const size_t p = ((size_t)b * H + h) * W + w;
-      float o4[4];
-      if (mode == 0) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          o4[2 * e] = fmaxf(acc[e].x, 0.f);
-          o4[2 * e + 1] = fmaxf(acc[e].y, 0.f);
-        }
+    for (int sl = 0; sl < 4; ++sl) {
+      const int k = 16 * ks + 2 * tig + (sl & 1) + 8 * (sl >> 1);
+      if (k >= KV) {
+        aoff[ks][sl] = 0;
+        acomp[ks][sl] = -1;
       } else {
-        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m);
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          o4[2 * e] = (bf(mb[2 * e]) > 0.f) ? acc[e].x : 0.f;
-          o4[2 * e + 1] = (bf(mb[2 * e + 1]) > 0.f) ? acc[e].y : 0.f;
-        }
+        const int part = k / 18, kk = k % 18, c = kk / 9, tap = kk % 9, dy = tap / 3, dx = tap % 3;
+        aoff[ks][sl] = (MODE == 0) ? dy * ld + dx : (2 - dy) * ld + (2 - dx);
+        acomp[ks][sl] = part * 2 + c;
       }
-      uint2 o;
-      __nv_bfloat162* po = reinterpret_cast<__nv_bfloat162*>(&o);
-      po[0] = __floats2bfloat162_rn(o4[0], o4[1]);
-      po[1] = __floats2bfloat162_rn(o4[2], o4[3]);
-      reinterpret_cast<uint2*>(out + p * CH)[cq] = o;
     }
+  float bj[8][2];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) bj[nt][e] = (MODE == 0) ? bias[8 * nt + 2 * tig + e] : 0.f;
+  __syncthreads();
+  __nv_bfloat16* so = s_o + warp * 16 * k2Ld;
+  const int ngw = (W + 15) / 16;  // groups per row
+  for (int gi = warp; gi < nrows * ngw; gi += k2Threads / 32) {
+    const int r = gi / ngw, w0 = (gi - r * ngw) * 16;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][2] = bj[nt][0];
+      acc[nt][1] = acc[nt][3] = bj[nt][1];
+    }
+    const int pa = w0 + gid, pb = pa + 8;  // this lane's two pixels
+    const float2* base_a = s_n + r * ld + pa;
+    const float2* base_b = s_n + r * ld + pb;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      float va[4], vb[4];
+#pragma unroll
+      for (int sl = 0; sl < 4; ++sl) {
+        const int cp = acomp[ks][sl];
+        float xa = 0.f, xb = 0.f;
+        if (cp >= 0) {
+          const float2 fa = pa < W ? base_a[aoff[ks][sl]] : make_float2(0.f, 0.f);
+          const float2 fb = pb < W ? base_b[aoff[ks][sl]] : make_float2(0.f, 0.f);
+          xa = (cp & 1) ? fa.y : fa.x;
+          xb = (cp & 1) ? fb.y : fb.x;
+          if (MODE == 1) {  // BF16 term part = cp >> 1 of the FP32 value
+            const int part = cp >> 1;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              if (part > q) {
+                xa -= bf(__float2bfloat16_rn(xa));
+                xb -= bf(__float2bfloat16_rn(xb));
+              }
+            }
+          }
+        }
+        va[sl] = xa;
+        vb[sl] = xb;
+      }
+      uint32_t afr[4];
+      afr[0] = pack_bf2(va[0], va[1]);  // row gid, k 2tig, 2tig+1
+      afr[1] = pack_bf2(vb[0], vb[1]);  // row gid+8
+      afr[2] = pack_bf2(va[2], va[3]);  // row gid, k 2tig+8, +9
+      afr[3] = pack_bf2(vb[2], vb[3]);  // row gid+8
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const uint2 bb = s_f[(ks * 8 + nt) * 32 + lane];
+        mma_bf16_16816(acc[nt], afr, bb.x, bb.y);
+      }
+    }
+    // stage the 16 x 64 result (mode 0: ReLU) as BF16
+    __syncwarp();
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float v0 = acc[nt][0], v1 = acc[nt][1], v2 = acc[nt][2], v3 = acc[nt][3];
+      if (MODE == 0) {
+        v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); v2 = fmaxf(v2, 0.f); v3 = fmaxf(v3, 0.f);
+      }
+      *reinterpret_cast<uint32_t*>(so + gid * k2Ld + 8 * nt + 2 * tig) = pack_bf2(v0, v1);
+      *reinterpret_cast<uint32_t*>(so + (gid + 8) * k2Ld + 8 * nt + 2 * tig) = pack_bf2(v2, v3);
+    }
+    __syncwarp();
+    // 16 pixels x 8 chunks of 16 bytes: four chunks per lane, whole 128-byte pixel rows per 8 lanes
+    const size_t prow = ((size_t)b * H + h0 + r) * W;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = q * 32 + lane, m = idx >> 3, ch = idx & 7;
+      const int px = w0 + m;
+      if (px < W) {
+        uint4 v = *reinterpret_cast<const uint4*>(so + m * k2Ld + ch * 8);
+        if (MODE == 1) {
+          const uint4 mk = reinterpret_cast<const uint4*>(mask_src + (prow + px) * CH)[ch];
+          const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+          __nv_bfloat16* vb = reinterpret_cast<__nv_bfloat16*>(&v);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (!(bf(mb[e]) > 0.f)) vb[e] = __float2bfloat16_rn(0.f);
+        }
+        reinterpret_cast<uint4*>(out + (prow + px) * CH)[ch] = v;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1014,7 +1110,9 @@ int conv_prepare() {
                                   ConvLayout<16>::SMEM) == cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad64, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM) ==
                  cudaSuccess &&
-             cudaFuncSetAttribute(k_2to64, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(kMaxW)) ==
+             cudaFuncSetAttribute(k_2to64<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(kMaxW)) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(k_2to64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(kMaxW)) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(k_wgrad_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, wl1_smem(kMaxW)) ==
                  cudaSuccess &&
@@ -1076,7 +1174,7 @@ int launch_wgrad64(const __nv_bfloat16* g, const __nv_bfloat16* act, float* part
 }
 
 struct DnLayout {
-  size_t wf[3], wd[3], ts[2], act[4], g[2], part_small, part64, status, total;
+  size_t wf[3], wd[3], ts[2], tf[2], act[4], g[2], part_small, part64, status, total;
   int nch_small, nch64;
 };
 
@@ -1089,6 +1187,7 @@ DnLayout dn_layout(int B, int H, int W) {
   for (int i = 0; i < 3; ++i) { L.wf[i] = o; o += up256(WPACK_BYTES); }
   for (int i = 0; i < 3; ++i) { L.wd[i] = o; o += up256(WPACK_BYTES); }
   for (int i = 0; i < 2; ++i) { L.ts[i] = o; o += up256(WP16_BYTES); }
+  for (int i = 0; i < 2; ++i) { L.tf[i] = o; o += up256((size_t)(i == 0 ? 2 : 4) * 8 * 32 * 2 * 4); }
   for (int i = 0; i < 4; ++i) { L.act[i] = o; o += act; }
   for (int i = 0; i < 2; ++i) { L.g[i] = o; o += act; }
   L.part_small = o; o += up256((size_t)L.nch_small * kSmallOut * 4);
@@ -1129,13 +1228,15 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
     pa.w5 = wts + o.w[4];
     pa.t5 = reinterpret_cast<__nv_bfloat16*>(ws + L.ts[0]);
     pa.t1 = reinterpret_cast<__nv_bfloat16*>(ws + L.ts[1]);
-    k_pack64<<<dim3((9 * 8 * CH * 8 + 255) / 256, 8), 256, 0, st>>>(pa);
+    pa.f1 = reinterpret_cast<uint32_t*>(ws + L.tf[0]);
+    pa.f5 = reinterpret_cast<uint32_t*>(ws + L.tf[1]);
+    k_pack64<<<dim3((9 * 8 * CH * 8 + 255) / 256, 10), 256, 0, st>>>(pa);
     prof_mark("dn_pack", st, true);
   }
   const size_t npx = (size_t)B * H * W;
   prof_mark("dn_2to64", st, false);
-  k_2to64<<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(B, H, W, 0, x, wts + o.w[0],
-                                                                                      wts + o.b[0], nullptr, act[0]);
+  k_2to64<0><<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(
+      B, H, W, x, reinterpret_cast<const uint32_t*>(ws + L.tf[0]), wts + o.b[0], nullptr, act[0]);
   prof_mark("dn_2to64", st, true);
   for (int l = 0; l < 3; ++l)
     if (int e = launch_conv64(act[l], reinterpret_cast<__nv_bfloat16*>(ws + L.wf[l]), wts + o.b[l + 1],
@@ -1214,8 +1315,8 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   // last layer: input gradient (masked by a4 > 0) and weight gradient
   const size_t npx = (size_t)B * H * W;
   prof_mark("dn_2to64", st, false);
-  k_2to64<<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(B, H, W, 1, go, weights + o.w[4],
-                                                                                      nullptr, act[3], gbuf[0]);
+  k_2to64<1><<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(
+      B, H, W, go, reinterpret_cast<const uint32_t*>(w8 + L.tf[1]), nullptr, act[3], gbuf[0]);
   prof_mark("dn_2to64", st, true);
   prof_mark("dn_wgrad_small", st, false);
   k_wgrad_l5<<<L.nch_small, 256, wl5_smem(W), st>>>(B, H, W, act[3], go, ps);
