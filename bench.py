@@ -386,7 +386,7 @@ def run_ours(args, rank, world, local_rank):
         ws, bs = synth.modl_cnn_weights(5000 + rank)
         flat = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(ws, bs)]).astype(np.float32)
         tr = ModlTrainer(maps5, None, torch.from_numpy(flat).to(dev), c5.lam, c5.extra["K"], c5.cg_iters,
-                         plan=plan5)
+                         plan=plan5, store_activations=False)  # inference: no reverse pass
 
         def step_nc():
             tr.forward_from_adjoint(AHy5)
@@ -394,12 +394,12 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.warmup):
             step_nc()
         torch.cuda.synchronize()
-        assert plan5.status() == 0 and tr.dn.status() == 0
+        assert plan5.status() == 0 and tr.denoiser_status() == 0
         steps = args.steps
         clk.start()
         t_ms, prof, launches = timed_steps(step_nc, steps, flush, dist)
         clocks = clk.stop()
-        assert plan5.status() == 0 and tr.dn.status() == 0
+        assert plan5.status() == 0 and tr.denoiser_status() == 0
         B = c5.B
         N5 = c5.H * c5.W
         normal_bytes = 8 * N5 * B * (c5.C + 2)
@@ -503,12 +503,12 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.warmup):
             step_modl()
         torch.cuda.synchronize()
-        assert tr.plan.status() == 0 and tr.dn.status() == 0
+        assert tr.plan.status() == 0 and tr.denoiser_status() == 0
         steps = args.steps
         clk.start()
         t_ms, prof, launches = timed_steps(step_modl, steps, flush, dist)
         clocks = clk.stop()
-        assert tr.plan.status() == 0 and tr.dn.status() == 0
+        assert tr.plan.status() == 0 and tr.denoiser_status() == 0
         B = c3.B
         N3 = c3.H * c3.W
         normal_bytes = 8 * N3 * B * (c3.C + 3)
@@ -582,7 +582,9 @@ def run_ours(args, rank, world, local_rank):
                    "W": cfg.W, "R": cfg.R, "cg_iters": cfg.cg_iters, "lambda": cfg.lam,
                    "unrolled_blocks": cfg.extra.get("K") if args.workload in ("modl_train", "noncart_modl_infer") else None,
                    "stages": cfg.extra.get("T") if args.workload == "varnet_train" else None,
-                   "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps"},
+                   "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps",
+                   "reverse_pass": ("each block's denoiser activations kept from the forward pass (no recompute)"
+                                    if args.workload == "modl_train" else None)},
         "roofline": kern.get(dominant),
         "kernels": kern,
         "time_breakdown": breakdown,

@@ -212,7 +212,8 @@ int denoiser_get_status(void* ws, int B, int H, int W, void* stream, int* device
  * on the plan's stream.  x_t, x_next, AHy, grad_next, grad_t: complex64 [B][H][W].
  * kind SENSE_DENOISER_MODL (Eq. 6, Sec. 2.3.2); lambda: device float64 [1]:
  *   unrolled_step:  z = D_W(x_t);  x_next = S_lambda^{-1}(AHy + lambda z) by
- *                   cg_iters CG iterations from zero.
+ *                   cg_iters CG iterations from zero; z and the denoiser activations
+ *                   stay in dn_ws.
  *   unrolled_step_backward: given grad_next = dL/dx_next, recomputes z from x_t
  *                   (checkpointing, Sec. 2.2.4), solves v = S_lambda^{-1} grad_next,
  *                   adds Re<v, z - x_next> to grad_lambda[0], and writes
@@ -228,6 +229,15 @@ int unrolled_step_backward(sense_plan plan, int kind, const float* weights, cons
                            const void* AHy, const void* x_t, const void* x_next,
                            const void* grad_next, void* grad_t, float* grad_weights,
                            double* grad_lambda, int cg_iters, void* dn_ws, size_t dn_ws_bytes);
+/* The same with a choice (MoDL): recompute != 0 is unrolled_step_backward; recompute == 0 takes z
+ * and the denoiser activations from dn_ws as the unrolled_step of this block left them (the
+ * caller keeps one denoiser workspace per block between the forward and reverse passes, and
+ * the weights unchanged) instead of recomputing them.  Results are identical either way. */
+int unrolled_step_backward_ex(sense_plan plan, int kind, const float* weights, const double* lambda,
+                              const void* AHy, const void* x_t, const void* x_next,
+                              const void* grad_next, void* grad_t, float* grad_weights,
+                              double* grad_lambda, int cg_iters, void* dn_ws, size_t dn_ws_bytes,
+                              int recompute);
 
 /* ------------------------------------------------------------------------
  * VarNet gradient stage (Eq. 5, Sec. 2.3.1) on a plan (maps, mask, workspace):

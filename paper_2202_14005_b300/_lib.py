@@ -55,6 +55,8 @@ SIGNATURES = {
     "unrolled_step": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, C.c_size_t]),
     "unrolled_step_backward": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp,
                                     C.c_size_t]),
+    "unrolled_step_backward_ex": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp,
+                                       C.c_size_t, _i]),
     "varnet_workspace_bytes": (C.c_size_t, [_i, _i, _i]),
     "varnet_param_count": (_i, []),
     "varnet_workspace_offsets": (_i, [_i, _i, _i, C.POINTER(C.c_size_t)]),

@@ -1174,7 +1174,7 @@ int launch_wgrad64(const __nv_bfloat16* g, const __nv_bfloat16* act, float* part
 }
 
 struct DnLayout {
-  size_t wf[3], wd[3], ts[2], tf[2], act[4], g[2], part_small, part64, status, total;
+  size_t wf[3], wd[3], ts[2], tf[2], act[4], g[2], zout, part_small, part64, status, total;
   int nch_small, nch64;
 };
 
@@ -1190,6 +1190,7 @@ DnLayout dn_layout(int B, int H, int W) {
   for (int i = 0; i < 2; ++i) { L.tf[i] = o; o += up256((size_t)(i == 0 ? 2 : 4) * 8 * 32 * 2 * 4); }
   for (int i = 0; i < 4; ++i) { L.act[i] = o; o += act; }
   for (int i = 0; i < 2; ++i) { L.g[i] = o; o += act; }
+  L.zout = o; o += up256((size_t)B * H * W * 8);  // the block output z of an unrolled step
   L.part_small = o; o += up256((size_t)L.nch_small * kSmallOut * 4);
   L.part64 = o; o += up256(((size_t)L.nch64 * 9 * CH * CH + (size_t)L.nch64 * CH) * 4);
   L.status = o; o += 256;
@@ -1251,6 +1252,11 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
 }
 
 }  // namespace
+
+// z = D(x_t) of an unrolled MoDL step, kept in its denoiser workspace beside the activations.
+float2* modl_zout(void* ws, int B, int H, int W) {
+  return reinterpret_cast<float2*>(static_cast<uint8_t*>(ws) + dn_layout(B, H, W).zout);
+}
 
 extern "C" {
 

@@ -107,6 +107,8 @@ struct NormalLaunch {
 };
 
 int launch_normal_lines(sense_plan p, const NormalLaunch& L);
+// The region of a MoDL denoiser workspace that keeps an unrolled step's z = D(x_t).
+float2* modl_zout(void* ws, int B, int H, int W);
 // Every CG iteration in one cooperative launch (p->lines.coop): x, w.r, w.p, w.q, w.rr as left by
 // the initial residual; rr_hist rows 1..iters written when non-NULL.
 int launch_cg_lines(sense_plan p, float2* x, int iters, double* rr_hist);

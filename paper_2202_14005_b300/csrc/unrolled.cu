@@ -156,21 +156,23 @@ int unrolled_step(sense_plan p, int kind, const float* weights, const double* la
   if (cg_iters < 0 || cg_iters > 100000) return SENSE_EINVAL_ARG;
   Workspace& w = p->w;
   const size_t n2 = (size_t)p->B * p->H * p->W / 2;
-  if (int e = denoiser_forward(kind, weights, x_t, w.t0, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
+  // z lands in the denoiser workspace, next to the activations, for a backward that reuses them
+  float2* z = modl_zout(dn_ws, p->B, p->H, p->W);
+  if (int e = denoiser_forward(kind, weights, x_t, z, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
     return e;
   prof_mark("unrolled_misc", p->stream, false);
   k_rhs<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, static_cast<const float4*>(AHy),
-                                                             reinterpret_cast<const float4*>(w.t0), lambda,
+                                                             reinterpret_cast<const float4*>(z), lambda,
                                                              reinterpret_cast<float4*>(w.t1));
   prof_mark("unrolled_misc", p->stream, true);
   count_launch(p);
   return cg_run(p, w.t1, nullptr, static_cast<float2*>(x_next), lambda, 1, cg_iters, nullptr);
 }
 
-int unrolled_step_backward(sense_plan p, int kind, const float* weights, const double* lambda,
-                           const void* AHy, const void* x_t, const void* x_next, const void* grad_next,
-                           void* grad_t, float* grad_weights, double* grad_lambda, int cg_iters,
-                           void* dn_ws, size_t dn_ws_bytes) {
+int unrolled_step_backward_ex(sense_plan p, int kind, const float* weights, const double* lambda,
+                              const void* AHy, const void* x_t, const void* x_next, const void* grad_next,
+                              void* grad_t, float* grad_weights, double* grad_lambda, int cg_iters,
+                              void* dn_ws, size_t dn_ws_bytes, int recompute) {
   if (kind == SENSE_DENOISER_VARNET)  // d/d lambda_t lands in grad_weights (stage layout)
     return varnet_stage_backward(p, weights, AHy, x_t, nullptr, grad_next, grad_t, grad_weights, dn_ws,
                                  dn_ws_bytes);
@@ -181,13 +183,16 @@ int unrolled_step_backward(sense_plan p, int kind, const float* weights, const d
   if (cg_iters < 0 || cg_iters > 100000) return SENSE_EINVAL_ARG;
   Workspace& w = p->w;
   const size_t n2 = (size_t)p->B * p->H * p->W / 2;
-  // z = D(x_t), recomputed; the denoiser keeps its activations in dn_ws
-  if (int e = denoiser_forward(kind, weights, x_t, w.t0, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
-    return e;
+  // z = D(x_t): recomputed (checkpointing), or as the forward step left it in dn_ws together with
+  // the activations
+  float2* z = modl_zout(dn_ws, p->B, p->H, p->W);
+  if (recompute)
+    if (int e = denoiser_forward(kind, weights, x_t, z, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
+      return e;
   // v = S^{-1} g  and  grad_lambda += Re<v, z - x_next>
   if (int e = cg_run(p, static_cast<const float2*>(grad_next), nullptr, w.t1, lambda, 1, cg_iters, nullptr))
     return e;
-  if (int e = launch_dot_rows(p, w.t1, w.t0, static_cast<const float2*>(x_next), grad_lambda, 1, 1))
+  if (int e = launch_dot_rows(p, w.t1, z, static_cast<const float2*>(x_next), grad_lambda, 1, 1))
     return e;
   // grad_z = lambda v  (z is no longer needed)
   prof_mark("unrolled_misc", p->stream, false);
@@ -197,6 +202,14 @@ int unrolled_step_backward(sense_plan p, int kind, const float* weights, const d
   count_launch(p);
   return denoiser_backward(kind, weights, x_t, w.t0, grad_t, grad_weights, dn_ws, dn_ws_bytes, p->B, p->H,
                            p->W, 0, p->stream);
+}
+
+int unrolled_step_backward(sense_plan p, int kind, const float* weights, const double* lambda,
+                           const void* AHy, const void* x_t, const void* x_next, const void* grad_next,
+                           void* grad_t, float* grad_weights, double* grad_lambda, int cg_iters,
+                           void* dn_ws, size_t dn_ws_bytes) {
+  return unrolled_step_backward_ex(p, kind, weights, lambda, AHy, x_t, x_next, grad_next, grad_t, grad_weights,
+                                   grad_lambda, cg_iters, dn_ws, dn_ws_bytes, 1);
 }
 
 int sense_mse_loss(sense_plan p, const void* x, const void* gt, double* loss, void* grad) {

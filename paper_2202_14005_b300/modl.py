@@ -2,9 +2,14 @@
 
 One training step (Eq. 6, Sec. 2.3.2): x^0 = A^H y; K unrolled blocks
 x^{t+1} = S_lambda^{-1}(A^H y + lambda D_W(x^t)) with shared weights; loss
-mean |x^K - x_gt|^2; reverse mode block by block (each block recomputes its
-denoiser activations from its stored input); Adam on the weights and lambda.
+mean |x^K - x_gt|^2; reverse mode block by block; Adam on the weights and lambda.
 Every arithmetic step runs in the library's kernels.
+
+Each block keeps its denoiser activations and output in a workspace of its own (about 0.6 GB
+for the 4-slice 256 x 232 workload), and its reverse pass reuses them.  With
+store_activations=False one workspace serves all blocks and each reverse pass recomputes the
+activations from the block input instead (the checkpointing of Sec. 2.2.4); the results are the
+same.
 """
 from __future__ import annotations
 
@@ -23,13 +28,16 @@ def _p(t):
 
 class ModlTrainer:
     def __init__(self, maps: torch.Tensor, mask: torch.Tensor, weights: torch.Tensor, lam: float,
-                 K: int, cg_iters: int, lr: float = 1e-4, lam_lr: float = 1e-4, plan: SensePlan | None = None):
+                 K: int, cg_iters: int, lr: float = 1e-4, lam_lr: float = 1e-4, plan: SensePlan | None = None,
+                 store_activations: bool = True):
         # plan: an existing plan (e.g. a non-Cartesian Toeplitz plan, Sec. 2.3.3) instead of maps/mask
         self.plan = plan if plan is not None else SensePlan(maps, mask)
         B, H, W = self.plan.img_shape()
         self.B, self.H, self.W = B, H, W
         self.K, self.iters = K, cg_iters
-        self.dn = ModlDenoiser(B, H, W, device=maps.device)
+        self.store = store_activations
+        self.dns = [ModlDenoiser(B, H, W, device=maps.device) for _ in range(K if store_activations else 1)]
+        self.dn = self.dns[0]
         self.weights = weights
         self.lam = torch.tensor([lam], dtype=torch.float64, device=maps.device)
         dev = maps.device
@@ -61,10 +69,21 @@ class ModlTrainer:
             self.xs[0].copy_(AHy)
         h, kind, w, lam = self._step_args()
         for t in range(self.K):
+            ws = self._ws(t)
             _lib.check("unrolled_step", self._lib.unrolled_step(
                 h, kind, w, lam, _p(self.xs[0]), _p(self.xs[t]), _p(self.xs[t + 1]), self.iters,
-                _p(self.dn.ws), self.dn.ws.numel()))
+                _p(ws), ws.numel()))
         return self.xs[self.K]
+
+    def _ws(self, t: int) -> torch.Tensor:
+        return self.dns[t if self.store else 0].ws
+
+    def denoiser_status(self) -> int:
+        """OR of the device status words of the denoiser workspaces (0 = no error)."""
+        st = 0
+        for d in self.dns:
+            st |= d.status()
+        return st
 
     def gradients(self, y: torch.Tensor, gt: torch.Tensor):
         """Forward, loss and reverse mode; gradients accumulate into self.gw / self.gl."""
@@ -74,10 +93,11 @@ class ModlTrainer:
         h, kind, w, lam = self._step_args()
         cur = 0
         for t in range(self.K - 1, -1, -1):
-            _lib.check("unrolled_step_backward", self._lib.unrolled_step_backward(
+            ws = self._ws(t)
+            _lib.check("unrolled_step_backward_ex", self._lib.unrolled_step_backward_ex(
                 h, kind, w, lam, _p(self.xs[0]), _p(self.xs[t]), _p(self.xs[t + 1]), _p(self.g[cur]),
-                _p(self.g[cur ^ 1]), _p(self.gw), _p(self.gl), self.iters, _p(self.dn.ws),
-                self.dn.ws.numel()))
+                _p(self.g[cur ^ 1]), _p(self.gw), _p(self.gl), self.iters, _p(ws), ws.numel(),
+                0 if self.store else 1))
             cur ^= 1
         return self.loss
 

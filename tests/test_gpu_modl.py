@@ -70,7 +70,26 @@ def test_modl_forward_blocks_and_training_gradients():
         assert rel(gws[l], rgws[l]) <= 5e-2, f"grad w{l + 1}"
         assert rel(gbs[l], rgbs[l]) <= 5e-2, f"grad b{l + 1}"
     assert abs(tr.gl.item() - rglam) <= 5e-2 * abs(rglam)
-    assert tr.plan.status() == 0 and tr.dn.status() == 0
+    assert tr.plan.status() == 0 and tr.denoiser_status() == 0
+
+
+def test_modl_stored_activations_match_recompute():
+    """The reverse pass reusing each block's stored activations and output (one denoiser workspace
+    per block) gives bitwise the same loss and gradients as recomputing them from the block input."""
+    from paper_2202_14005_b300.modl import ModlTrainer
+    maps, mask, y, gt = problem(B=2, C=4, H=24, W=232, seed=13)
+    ws, bs, flat = make_weights(17)
+    res = []
+    for store in (True, False):
+        tr = ModlTrainer(dev(maps), dev(mask), dev(flat), 0.05, 3, 6, store_activations=store)
+        loss = tr.gradients(dev(y), dev(gt))
+        torch.cuda.synchronize()
+        assert len(tr.dns) == (3 if store else 1)
+        res.append((loss.item(), tr.gw.cpu().numpy().copy(), tr.gl.item(), tr.xs[-1].cpu().numpy()))
+        assert tr.plan.status() == 0 and tr.denoiser_status() == 0
+    (l0, g0, gl0, x0), (l1, g1, gl1, x1) = res
+    assert l0 == l1 and gl0 == gl1
+    assert np.array_equal(g0, g1) and np.array_equal(x0, x1)
 
 
 def test_modl_block_reverse_mode_parity():
@@ -111,7 +130,7 @@ def test_modl_block_reverse_mode_parity():
         assert rel(gws[l], rws[l]) <= 1e-2, f"grad w{l + 1}"
         assert rel(gbs[l], rbs[l]) <= 1e-2, f"grad b{l + 1}"
     assert abs(tr.gl.item() - rgl) <= 1e-2 * abs(rgl)
-    assert tr.plan.status() == 0 and tr.dn.status() == 0
+    assert tr.plan.status() == 0 and tr.denoiser_status() == 0
 
 
 def test_modl_train_step_updates_and_clears_gradients():
