@@ -278,14 +278,21 @@ int varnet_param_count(void);
 /* Byte offsets in ws of the activations the last call left there (for tests and
  * inspection): offsets[0] u = Phi'(K x_t) and offsets[1] v = Phi''(K x_t) K grad_next,
  * bfloat16 [B][H][W][32] (channels 24..31 zero); offsets[2] z = K x_t and
- * offsets[3] K grad_next, float32 [B][H][W][24] (v, z and K grad_next from
- * varnet_stage_backward only). */
+ * offsets[3] K grad_next, float32 [B][H][W][24] (u and z from varnet_stage and a
+ * recomputing varnet_stage_backward; v and K grad_next from varnet_stage_backward). */
 int varnet_workspace_offsets(int B, int H, int W, size_t* offsets);
 int varnet_stage(sense_plan plan, const float* params, const void* AHy, const void* x_t, void* x_next,
                  void* nx_out, void* ws, size_t ws_bytes);
 int varnet_stage_backward(sense_plan plan, const float* params, const void* AHy, const void* x_t,
                           const void* nx_t, const void* grad_next, void* grad_t, float* grad_params,
                           void* ws, size_t ws_bytes);
+/* The same with a choice: recompute != 0 is varnet_stage_backward; recompute == 0 takes z = K x
+ * and u = Phi'(z) from ws as varnet_stage of this stage left them (the caller keeps one varnet
+ * workspace per stage between the forward and reverse passes, parameters unchanged), so only
+ * K g is computed; results are the same. */
+int varnet_stage_backward_ex(sense_plan plan, const float* params, const void* AHy, const void* x_t,
+                             const void* nx_t, const void* grad_next, void* grad_t, float* grad_params,
+                             void* ws, size_t ws_bytes, int recompute);
 
 /* Training loss of the unrolled networks: loss[0] = mean |x - gt|^2 over the
  * plan's B*S*H*W complex elements (float64, fixed-order sum) and

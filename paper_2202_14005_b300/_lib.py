@@ -62,6 +62,7 @@ SIGNATURES = {
     "varnet_workspace_offsets": (_i, [_i, _i, _i, C.POINTER(C.c_size_t)]),
     "varnet_stage": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
     "varnet_stage_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
+    "varnet_stage_backward_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _i]),
     "sense_mse_loss": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "sense_normalize_max": (_i, [_vp, _vp, _vp, _vp]),
     "adam_update_f32": (_i, [_vp, _vp, _vp, _vp, C.c_size_t, _f, _f, _f, _f, _i, _vp]),

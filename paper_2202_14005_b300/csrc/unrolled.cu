@@ -174,8 +174,8 @@ int unrolled_step_backward_ex(sense_plan p, int kind, const float* weights, cons
                               void* grad_t, float* grad_weights, double* grad_lambda, int cg_iters,
                               void* dn_ws, size_t dn_ws_bytes, int recompute) {
   if (kind == SENSE_DENOISER_VARNET)  // d/d lambda_t lands in grad_weights (stage layout)
-    return varnet_stage_backward(p, weights, AHy, x_t, nullptr, grad_next, grad_t, grad_weights, dn_ws,
-                                 dn_ws_bytes);
+    return varnet_stage_backward_ex(p, weights, AHy, x_t, nullptr, grad_next, grad_t, grad_weights, dn_ws,
+                                    dn_ws_bytes, recompute);
   if (int e = check_step(p, kind, weights, lambda, AHy, dn_ws, dn_ws_bytes)) return e;
   if (!x_t || !x_next || !grad_next || !grad_t || !grad_weights || !grad_lambda || !al16(x_t) ||
       !al16(x_next) || !al16(grad_next) || !al16(grad_t) || grad_t == grad_next)

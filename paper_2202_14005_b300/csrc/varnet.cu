@@ -174,9 +174,11 @@ __global__ void k_vn_pack(const float* prm, bf16* wk, bf16* wn) {
 }
 
 // -------------------------------------------------------------- K (2 -> 24)
-// NSRC = 1 (forward stage):  u = Phi'(K x)                          -> u [px][32] bf16
+// NSRC = 1 (forward stage):  z = K x, u = Phi'(z)                   -> u [px][32] bf16, z [px][24] fp32
 // NSRC = 2 (reverse stage):  z = K x, kg = K g;  u = Phi'(z), v = Phi''(z) kg
 //                            -> u, v [px][32] bf16, z, kg [px][24] fp32
+// NSRC = 1, ZIN (reverse stage after a forward that kept z and u): the source is g; kg = K g,
+//                            v = Phi''(z) kg with z read back -> v, kg
 // CTA: 128 pixels x R rows (R = 8 / NSRC), 8 warps x 16 pixels.  Source rows stream through a double-
 // buffered FP32 stage (cp.async) into one im2col tile per source; each source row s feeds every
 // output row h of the CTA with 0 <= s - h + 5 <= 10 (filter row dy = s - h + 5).  The image
@@ -211,8 +213,9 @@ struct KSmem {
   static constexpr int TOTAL = OFF_R + NK * RBF_LD * 4;
 };
 
-template <int NSRC>
+template <int NSRC, bool ZIN = false>
 __global__ void __launch_bounds__(K_THREADS, 2) k_vn_K(const KArgs a) {
+  static_assert(!ZIN || NSRC == 1, "z is read back only by the one-source reverse kernel");
   using S = KSmem<NSRC>;
   constexpr int K_R = K_RMAX / NSRC;
   extern __shared__ __align__(16) uint8_t dsm[];
@@ -349,21 +352,30 @@ __global__ void __launch_bounds__(K_THREADS, 2) k_vn_K(const KArgs a) {
 #pragma unroll
       for (int nt = 0; nt < 3; ++nt) {
         const int i0 = nt * 8 + 2 * tig;
-        const float2 z = make_float2(acc[0][r][nt][half * 2], acc[0][r][nt][half * 2 + 1]);
-        const Rbf2 f = rbf_eval2(z, s_r + i0 * RBF_LD, s_r + (i0 + 1) * RBF_LD);
-        *reinterpret_cast<uint32_t*>(a.u + p * CU + i0) =
-            pack2(__float2bfloat16_rn(f.d1.x), __float2bfloat16_rn(f.d1.y));
-        if (NSRC == 2) {
-          const float2 kg = make_float2(acc[NSRC - 1][r][nt][half * 2], acc[NSRC - 1][r][nt][half * 2 + 1]);
+        const float2 a0 = make_float2(acc[0][r][nt][half * 2], acc[0][r][nt][half * 2 + 1]);
+        if constexpr (ZIN) {  // a0 = K g; z from the forward stage
+          const float2 z = *reinterpret_cast<const float2*>(a.z + p * NK + i0);
+          const Rbf2 f = rbf_eval2(z, s_r + i0 * RBF_LD, s_r + (i0 + 1) * RBF_LD);
           *reinterpret_cast<uint32_t*>(a.v + p * CU + i0) =
-              pack2(__float2bfloat16_rn(f.d2.x * kg.x), __float2bfloat16_rn(f.d2.y * kg.y));
+              pack2(__float2bfloat16_rn(f.d2.x * a0.x), __float2bfloat16_rn(f.d2.y * a0.y));
+          *reinterpret_cast<float2*>(a.kg + p * NK + i0) = a0;
+        } else {
+          const float2 z = a0;
+          const Rbf2 f = rbf_eval2(z, s_r + i0 * RBF_LD, s_r + (i0 + 1) * RBF_LD);
+          *reinterpret_cast<uint32_t*>(a.u + p * CU + i0) =
+              pack2(__float2bfloat16_rn(f.d1.x), __float2bfloat16_rn(f.d1.y));
           *reinterpret_cast<float2*>(a.z + p * NK + i0) = z;
-          *reinterpret_cast<float2*>(a.kg + p * NK + i0) = kg;
+          if (NSRC == 2) {
+            const float2 kg = make_float2(acc[NSRC - 1][r][nt][half * 2], acc[NSRC - 1][r][nt][half * 2 + 1]);
+            *reinterpret_cast<uint32_t*>(a.v + p * CU + i0) =
+                pack2(__float2bfloat16_rn(f.d2.x * kg.x), __float2bfloat16_rn(f.d2.y * kg.y));
+            *reinterpret_cast<float2*>(a.kg + p * NK + i0) = kg;
+          }
         }
       }
       // channels 24..31 of the stored activations are zero
-      *reinterpret_cast<uint32_t*>(a.u + p * CU + NK + 2 * tig) = 0u;
-      if (NSRC == 2) *reinterpret_cast<uint32_t*>(a.v + p * CU + NK + 2 * tig) = 0u;
+      if (!ZIN) *reinterpret_cast<uint32_t*>(a.u + p * CU + NK + 2 * tig) = 0u;
+      if (NSRC == 2 || ZIN) *reinterpret_cast<uint32_t*>(a.v + p * CU + NK + 2 * tig) = 0u;
     }
   }
 }
@@ -681,6 +693,8 @@ int vn_prepare() {
   if (state == 0)
     state = (cudaFuncSetAttribute(k_vn_K<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<1>::TOTAL) ==
                  cudaSuccess &&
+             cudaFuncSetAttribute(k_vn_K<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<1>::TOTAL) ==
+                 cudaSuccess &&
              cudaFuncSetAttribute(k_vn_K<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<2>::TOTAL) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(k_vn_KT, cudaFuncAttributeMaxDynamicSharedMemorySize, KT_SMEM) == cudaSuccess &&
@@ -722,23 +736,27 @@ void vn_pack(const float* prm, uint8_t* ws, const VnLayout& L, cudaStream_t st) 
   prof_mark("vn_misc", st, true);
 }
 
+// nsrc 1: forward (z, u from x); 2: reverse recomputing z (z, u, kg, v from x and g); 3: reverse
+// with z and u kept by the forward stage (kg, v from g alone)
 int launch_K(const Shape& sh, int nsrc, const float* prm, const float2* x, const float2* g, uint8_t* ws,
              const VnLayout& L) {
   KArgs a;
   a.B = sh.B; a.H = sh.H; a.W = sh.W;
-  a.x = x; a.g = g;
+  a.x = nsrc == 3 ? g : x; a.g = g;
   a.wk = reinterpret_cast<const bf16*>(ws + L.wk);
   a.rbf = prm + OFF_RBF;
   a.u = reinterpret_cast<bf16*>(ws + L.u);
   a.v = reinterpret_cast<bf16*>(ws + L.v);
   a.z = reinterpret_cast<float*>(ws + L.z);
   a.kg = reinterpret_cast<float*>(ws + L.kg);
-  const int R = K_RMAX / nsrc;
+  const int R = K_RMAX / (nsrc == 2 ? 2 : 1);
   const dim3 grid((sh.W + TILE - 1) / TILE, (sh.H + R - 1) / R, sh.B);
-  const char* grp = nsrc == 2 ? "vn_Kbwd" : "vn_K";
+  const char* grp = nsrc >= 2 ? "vn_Kbwd" : "vn_K";
   prof_mark(grp, sh.st, false);
   if (nsrc == 2)
     k_vn_K<2><<<grid, K_THREADS, KSmem<2>::TOTAL, sh.st>>>(a);
+  else if (nsrc == 3)
+    k_vn_K<1, true><<<grid, K_THREADS, KSmem<1>::TOTAL, sh.st>>>(a);
   else
     k_vn_K<1><<<grid, K_THREADS, KSmem<1>::TOTAL, sh.st>>>(a);
   prof_mark(grp, sh.st, true);
@@ -825,8 +843,9 @@ int varnet_stage(sense_plan p, const float* prm, const void* AHy, const void* x_
   return SENSE_OK;
 }
 
-int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const void* x_t, const void* nx_t,
-                          const void* grad_next, void* grad_t, float* grad_prm, void* ws, size_t ws_bytes) {
+int varnet_stage_backward_ex(sense_plan p, const float* prm, const void* AHy, const void* x_t, const void* nx_t,
+                             const void* grad_next, void* grad_t, float* grad_prm, void* ws, size_t ws_bytes,
+                             int recompute) {
   if (int e = vn_check(p, prm, AHy, x_t, nx_t, ws, ws_bytes)) return e;
   if (!grad_next || !grad_t || !grad_prm || !al16(grad_next) || !al16(grad_t) || grad_t == grad_next ||
       grad_t == nx_t)
@@ -851,9 +870,9 @@ int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const
   prof_mark("vn_misc", p->stream, false);
   k_vn_addlam<<<1, 1, 0, p->stream>>>(pdot, grad_prm);
   prof_mark("vn_misc", p->stream, true);
-  // z = K x, kg = K g, u = Phi'(z), v = Phi''(z) kg; parameter gradients of -R (read g and x before
-  // grad_t is written)
-  if (int e = launch_K(sh, 2, prm, x, g, w8, L)) return e;
+  // z = K x (recomputed, or kept in ws by this stage's forward together with u = Phi'(z)), kg = K g,
+  // v = Phi''(z) kg; parameter gradients of -R (read g and x before grad_t is written)
+  if (int e = launch_K(sh, recompute ? 2 : 3, prm, x, g, w8, L)) return e;
   launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L);
   // grad_t = g - K^T v - lambda A^H A g
   if (int e = normal0(p, g, n2)) return e;
@@ -862,6 +881,11 @@ int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const
     return e;
   prof_count(8);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
+int varnet_stage_backward(sense_plan p, const float* prm, const void* AHy, const void* x_t, const void* nx_t,
+                          const void* grad_next, void* grad_t, float* grad_prm, void* ws, size_t ws_bytes) {
+  return varnet_stage_backward_ex(p, prm, AHy, x_t, nx_t, grad_next, grad_t, grad_prm, ws, ws_bytes, 1);
 }
 
 }  // extern "C"

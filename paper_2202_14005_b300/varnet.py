@@ -49,8 +49,13 @@ def unpack_params(vec):
 
 
 class VarNetTrainer:
+    """VarNet training on the library.  Each stage keeps z = K x^t and u = Phi'(z) in a workspace
+    of its own (about 0.2 GB per stage for 4 slices of 320 x 368), and its reverse pass reuses them
+    so that only K g is computed; with store_activations=False one workspace serves all stages and
+    the reverse pass recomputes K x^t (the checkpointing of Sec. 2.2.4).  Results are the same."""
+
     def __init__(self, maps: torch.Tensor, mask: torch.Tensor, params: torch.Tensor, lr: float = 1e-4,
-                 normalize: bool = False):
+                 normalize: bool = False, store_activations: bool = True):
         self.plan = SensePlan(maps, mask)
         B, H, W = self.plan.img_shape()
         self.B, self.H, self.W = B, H, W
@@ -65,7 +70,10 @@ class VarNetTrainer:
         self.params = params
         dev = maps.device
         nb = self._lib.varnet_workspace_bytes(B, H, W)
-        self.ws = torch.zeros(int(nb), dtype=torch.uint8, device=dev)
+        self.store = store_activations
+        self.wss = [torch.zeros(int(nb), dtype=torch.uint8, device=dev)
+                    for _ in range(self.T if store_activations else 1)]
+        self.ws = self.wss[0]
         self.gp = torch.zeros_like(params)
         self.m, self.v = torch.zeros_like(params), torch.zeros_like(params)
         self.xs = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(self.T + 1)]
@@ -80,26 +88,35 @@ class VarNetTrainer:
         self.lr = lr
         self.t = 0
 
+    def _ws(self, t: int) -> torch.Tensor:
+        return self.wss[t if self.store else 0]
+
     def stage(self, t: int, x_t: torch.Tensor, x_next: torch.Tensor, nx_out: torch.Tensor | None = None):
+        ws = self._ws(t)
         _lib.check("varnet_stage", self._lib.varnet_stage(
-            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(x_next), _p(nx_out), _p(self.ws),
-            self.ws.numel()))
+            self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(x_next), _p(nx_out), _p(ws),
+            ws.numel()))
 
-    def stage_backward(self, t: int, x_t, grad_next, grad_t, nx_t: torch.Tensor | None = None):
-        _lib.check("varnet_stage_backward", self._lib.varnet_stage_backward(
+    def stage_backward(self, t: int, x_t, grad_next, grad_t, nx_t: torch.Tensor | None = None,
+                       reuse: bool = False):
+        """Reverse pass of stage t; reuse: take z and u from the stage's workspace as stage(t) left
+        them for the same x_t and parameters (else K x_t is recomputed)."""
+        ws = self._ws(t)
+        _lib.check("varnet_stage_backward_ex", self._lib.varnet_stage_backward_ex(
             self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(nx_t), _p(grad_next), _p(grad_t),
-            _p(self.gp[t]), _p(self.ws), self.ws.numel()))
+            _p(self.gp[t]), _p(ws), ws.numel(), 0 if reuse else 1))
 
-    def activations(self):
-        """Views of the workspace activations of the last stage call:
+    def activations(self, t: int = 0):
+        """Views of the workspace activations of the last call on stage t's workspace:
         u, v (bfloat16 [B, H, W, 32]) and z = K x, K g (float32 [B, H, W, 24])."""
+        ws = self._ws(t)
         off = (C.c_size_t * 4)()
         _lib.check("varnet_workspace_offsets", self._lib.varnet_workspace_offsets(self.B, self.H, self.W, off))
         n = self.B * self.H * self.W
-        u = self.ws[off[0]:off[0] + n * 64].view(torch.bfloat16).view(self.B, self.H, self.W, 32)
-        v = self.ws[off[1]:off[1] + n * 64].view(torch.bfloat16).view(self.B, self.H, self.W, 32)
-        z = self.ws[off[2]:off[2] + n * 96].view(torch.float32).view(self.B, self.H, self.W, NK)
-        kg = self.ws[off[3]:off[3] + n * 96].view(torch.float32).view(self.B, self.H, self.W, NK)
+        u = ws[off[0]:off[0] + n * 64].view(torch.bfloat16).view(self.B, self.H, self.W, 32)
+        v = ws[off[1]:off[1] + n * 64].view(torch.bfloat16).view(self.B, self.H, self.W, 32)
+        z = ws[off[2]:off[2] + n * 96].view(torch.float32).view(self.B, self.H, self.W, NK)
+        kg = ws[off[3]:off[3] + n * 96].view(torch.float32).view(self.B, self.H, self.W, NK)
         return u, v, z, kg
 
     def forward(self, y: torch.Tensor, gt: torch.Tensor | None = None) -> torch.Tensor:
@@ -123,7 +140,7 @@ class VarNetTrainer:
             self.plan._h, _p(self.xs[self.T]), _p(self.gtn), _p(self.loss), _p(self.g[0])))
         cur = 0
         for t in range(self.T - 1, -1, -1):
-            self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1], self.nx[t])
+            self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1], self.nx[t], reuse=self.store)
             cur ^= 1
         return self.loss
 
