@@ -48,7 +48,12 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
 NCU_TRAFFIC = {
     "cg_sense": {"normal_lines": 110.3e6},
     "modl_train": {"cg_lines": 26.7e6, "conv64_tc": 30.55e6, "wgrad64": 62.9e6},
-    "varnet_train": {"vn_K": 3.9e6, "vn_Kbwd": 103.4e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
+    "varnet_train": {"vn_K": 3.9e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
+}
+# what the reverse pass reuses from the forward pass of each training workload
+REVERSE_PASS = {
+    "modl_train": "each block's denoiser activations kept from the forward pass (no recompute)",
+    "varnet_train": "each stage's K x and Phi'(K x) kept from the forward pass (K g alone recomputed)",
 }
 # kernel groups the library times with CUDA events when profiling is on
 PROFILE_GROUPS = ("normal_lines", "conv64_tc", "wgrad64", "cg_vec", "fft_generic", "dn_2to64", "dn_64to2",
@@ -530,6 +535,7 @@ def run_ours(args, rank, world, local_rank):
     px = B * Hc * Wc
     conv_flops = 2.0 * px * 64 * 576
     vn_flops = 2.0 * px * 24 * 2 * 121  # one 2<->24 channel 11x11 convolution
+    vn_store = bool(getattr(tr, "store", False)) if args.workload == "varnet_train" else False
     kern = {
         "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks, args.workload),
         "cg_lines": kernel_report("cg_lines", *prof["cg_lines"], ("hbm", cg_bytes), pk, clocks, args.workload)
@@ -537,7 +543,9 @@ def run_ours(args, rank, world, local_rank):
         "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks, args.workload),
         "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("tensor", conv_flops), pk, clocks, args.workload),
         "vn_K": kernel_report("vn_K", *prof["vn_K"], ("tensor", vn_flops), pk, clocks, args.workload),
-        "vn_Kbwd": kernel_report("vn_Kbwd", *prof["vn_Kbwd"], ("tensor", 2 * vn_flops), pk, clocks, args.workload),
+        # reverse K: K g alone when the forward's K x is kept, else K x and K g
+        "vn_Kbwd": kernel_report("vn_Kbwd", *prof["vn_Kbwd"], ("tensor", (1 if vn_store else 2) * vn_flops), pk,
+                                 clocks, args.workload),
         "vn_KT": kernel_report("vn_KT", *prof["vn_KT"], ("tensor", vn_flops), pk, clocks, args.workload),
         "vn_wgrad": kernel_report("vn_wgrad", *prof["vn_wgrad"], ("tensor", 2 * vn_flops), pk, clocks, args.workload),
         "toeplitz": kernel_report("toeplitz", *prof["toeplitz"], ("hbm", normal_bytes), pk, clocks, args.workload),
@@ -583,8 +591,7 @@ def run_ours(args, rank, world, local_rank):
                    "unrolled_blocks": cfg.extra.get("K") if args.workload in ("modl_train", "noncart_modl_infer") else None,
                    "stages": cfg.extra.get("T") if args.workload == "varnet_train" else None,
                    "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps",
-                   "reverse_pass": ("each block's denoiser activations kept from the forward pass (no recompute)"
-                                    if args.workload == "modl_train" else None)},
+                   "reverse_pass": REVERSE_PASS.get(args.workload)},
         "roofline": kern.get(dominant),
         "kernels": kern,
         "time_breakdown": breakdown,

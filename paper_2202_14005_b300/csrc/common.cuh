@@ -132,6 +132,44 @@ SENSE_D double lane_strided_sum(const double* part, int n, int lane) {
   for (; i < n; i += 32) s += __ldcg(part + i);
   return s;
 }
+// Lane part of a strided sum (elements lane, lane + 32, ...) with the loads of each group of
+// eight issued together and each group added as a pairwise tree (FP64 additions take long to
+// complete, so the dependent chain is kept short); groups are added in order.  Deterministic.
+SENSE_D double tree8(const double* v) {
+  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+}
+SENSE_D double lane_tree_sum(const double* p, int n, int lane) {
+  double s = 0.0;
+  int i = lane;
+  for (; i + 7 * 32 < n; i += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + i + 32 * k);
+    s = i == lane ? tree8(v) : s + tree8(v);
+  }
+  for (; i < n; i += 32) s += __ldcg(p + i);
+  return s;
+}
+// Two lane_tree_sum()s over arrays of the same length, loads issued together.
+SENSE_D void lane_tree_sum2(const double* p0, const double* p1, int n, int lane, double& s0, double& s1) {
+  s0 = 0.0;
+  s1 = 0.0;
+  int i = lane;
+  for (; i + 7 * 32 < n; i += 8 * 32) {
+    double v0[8], v1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v0[k] = __ldcg(p0 + i + 32 * k);
+      v1[k] = __ldcg(p1 + i + 32 * k);
+    }
+    s0 = i == lane ? tree8(v0) : s0 + tree8(v0);
+    s1 = i == lane ? tree8(v1) : s1 + tree8(v1);
+  }
+  for (; i < n; i += 32) {
+    s0 += __ldcg(p0 + i);
+    s1 += __ldcg(p1 + i);
+  }
+}
 // Warp sum in a fixed butterfly order (deterministic).
 SENSE_D double warp_sum_d(double v) {
 #pragma unroll

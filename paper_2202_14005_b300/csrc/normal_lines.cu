@@ -185,8 +185,12 @@ int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist) {
     c.pd[i] = w.part2 + i * np;
     c.pg[i] = w.part2 + (2 + i) * np;
   }
-  c.bar = w.counter + 16;  // two words of the zeroed counter block, apart from the last-block counter
-  if (cudaMemsetAsync(c.bar, 0, 2 * sizeof(unsigned), pl->stream) != cudaSuccess) return SENSE_ECUDA;
+  // counter block: last-block counter (bytes 0..127), arrival count (128), release word (256),
+  // scalars (512..895)
+  c.cnt = w.counter + 32;
+  c.rel = w.counter + 64;
+  c.sc = reinterpret_cast<double*>(w.counter + 128);
+  if (cudaMemsetAsync(c.cnt, 0, 256, pl->stream) != cudaSuccess) return SENSE_ECUDA;
   void* args[] = {&a, &c};
   prof_mark("cg_lines", pl->stream, false);
   const cudaError_t e = cudaLaunchCooperativeKernel(T.coop, dim3(T.coop_grid), dim3(T.threads), args,

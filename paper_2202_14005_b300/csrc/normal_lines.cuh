@@ -479,14 +479,18 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
 //   beta_{k-1} = gamma_k / gamma_{k-1},  alpha_k = gamma_k / (delta_k - beta_{k-1} gamma_k / alpha_{k-1})
 // (alpha_0 = gamma_0 / delta_0), using the orthogonality of the residuals.  Pass k (k < iters):
 // staging p, s, x, r of iteration k - 1 (k >= 1), w = S r through the fused operator, row
-// partials of delta and gamma; barrier; every CTA forms beta and alpha per slice from all row
-// partials in fixed order (identical in every CTA).  A last pass makes the update of iteration
+// partials of delta and gamma, grid barrier.  A last pass makes the update of iteration
 // iters - 1 and gamma for the residual history.  Each CTA keeps the same row tiles throughout,
-// so only the row partials cross CTAs.  The grid barrier is a counter and a generation word in
-// global memory; the launch is cooperative (all CTAs resident), and every wait is bounded: a CTA
-// that gives up sets SENSE_STATUS_DEVICE_TIMEOUT and returns.
-constexpr int kCoopMaxB = 16;  // slices per solve on this path (3 x 16 FP64 scalars in static shared
-                               // memory: small enough to keep the CTAs per SM of the operator kernel)
+// so only the row partials and the per-slice scalars cross CTAs.
+//
+// Grid barrier: an arrival count that only grows within the launch (barrier n completes at
+// (n + 1) x gridDim.x arrivals) and a release word.  The CTA that arrives last reduces the row
+// partials of every slice in fixed order, publishes alpha and beta (and its copies of gamma and
+// alpha for the next pass), then releases the others, which read the two scalars of their
+// slices.  One CTA reads the partials instead of every CTA reading all of them at once.  The
+// launch is cooperative (all CTAs resident) and every wait is bounded: a CTA that gives up sets
+// SENSE_STATUS_DEVICE_TIMEOUT and returns.
+constexpr int kCoopMaxB = 16;  // slices per solve on this path
 
 struct CgCoop {
   int iters;
@@ -496,90 +500,110 @@ struct CgCoop {
   float2* s;        // S p
   float2* w;        // S r
   double* hist;     // [iters + 1][B] squared residual norms (row 0 by the caller) or NULL
-  unsigned* bar;    // {arrival count, generation}, count zero between barriers
-  // row partials of delta and gamma, two buffers each used by alternate passes: a CTA may start
-  // writing pass k + 1 while others still read pass k (it cannot get further ahead than that)
+  unsigned* cnt;    // arrival count, zero at launch (a 128-byte line of its own)
+  unsigned* rel;    // barriers released, zero at launch (a line of its own)
+  double* sc;       // published scalars: alpha [kCoopMaxB], beta [kCoopMaxB], gamma [kCoopMaxB]
+  // row partials of delta and gamma, two buffers each, used by alternate passes
   double* pd[2];
   double* pg[2];
 };
 
-__device__ __forceinline__ bool coop_barrier(unsigned* bar) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
-    int ok = 1;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned n = 0;
-      while (*gen == g0) {
-        if (++n > (1u << 22)) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Arrival: release of this CTA's writes (ordered before it by the CTA barrier) and acquire of
+// every earlier arrival's, in one read-modify-write.
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Scalars of pass k from the row partials (delta in part, gamma in part2).  g_prev / a_prev hold
-// gamma_{k-1} / alpha_{k-1} and take gamma_k / alpha_k; beta receives beta_{k-1}.  A slice whose
-// gamma is zero (or whose previous alpha is zero) is frozen: alpha = beta = 0.  With
-// only_gamma the pass made the last update: gamma is recorded, no new alpha.  Block 0 alone
-// records status bits, the history row and the global ||r||^2.
-__device__ __forceinline__ void coop_scalars(const NLArgs& a, int k, bool only_gamma, double* g_prev,
-                                             double* a_prev, double* beta, double* hist) {
+// Scalars of pass k from the row partials (delta in part, gamma in part2), formed by the one CTA
+// that completed barrier k.  gamma_{k-1} and alpha_{k-1} come from the previous publication.
+// A slice whose gamma is zero (or whose previous alpha is zero) is frozen: alpha = beta = 0.
+// With only_gamma the pass made the last update: gamma is recorded, no new alpha.
+__device__ __forceinline__ void coop_scalars(const NLArgs& a, const CgCoop& c, int k, bool only_gamma,
+                                             double* hist) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const bool rec = blockIdx.x == 0;
   for (int b = warp; b < a.B; b += nwarps) {
-    double g = lane_strided_sum(a.part2 + (size_t)b * a.HS, a.HS, lane);
+    const double gp = __ldcg(c.sc + 2 * kCoopMaxB + b), ap = __ldcg(c.sc + b);
+    double g = 0.0, d = 0.0;
+    if (only_gamma) g = lane_tree_sum(a.part2 + (size_t)b * a.HS, a.HS, lane);
+    else lane_tree_sum2(a.part2 + (size_t)b * a.HS, a.part + (size_t)b * a.HS, a.HS, lane, g, d);
     g = warp_sum_d(g);
-    double d = 0.0;
-    if (!only_gamma) {
-      d = lane_strided_sum(a.part + (size_t)b * a.HS, a.HS, lane);
-      d = warp_sum_d(d);
-    }
+    if (!only_gamma) d = warp_sum_d(d);
     if (lane != 0) continue;
     const bool fin = isfinite(g) && isfinite(d);
-    if (!fin && rec) set_status(a.status, SENSE_DEVST_NONFINITE);
-    const double gp = g_prev[b], ap = a_prev[b];
+    if (!fin) set_status(a.status, SENSE_DEVST_NONFINITE);
     double be = 0.0, al = 0.0;
     if (fin && g > 0.0 && (k == 0 || (gp > 0.0 && ap != 0.0))) {
+      // beta g / alpha_prev as (g / gamma_prev)(g / alpha_prev): the two divisions are
+      // independent, so only two FP64 divisions lie on the dependency chain
       be = k == 0 ? 0.0 : g / gp;
       if (!only_gamma) {
-        const double den = k == 0 ? d : d - be * g / ap;
+        const double den = k == 0 ? d : d - be * (g / ap);
         if (den > 0.0) al = g / den;
-        else if (rec) set_status(a.status, SENSE_DEVST_CG_BREAKDOWN);
+        else set_status(a.status, SENSE_DEVST_CG_BREAKDOWN);
       }
     }
-    beta[b] = be;
-    a_prev[b] = al;
-    g_prev[b] = g;
-    if (rec) {
-      a.rr[b] = g;
-      a.alpha[b] = al;
-      if (hist && k > 0) hist[b] = g;
+    c.sc[b] = al;
+    c.sc[kCoopMaxB + b] = be;
+    c.sc[2 * kCoopMaxB + b] = g;
+    a.rr[b] = g;
+    a.alpha[b] = al;
+    if (hist && k > 0) hist[b] = g;
+  }
+}
+
+// Barrier n of the solve with the scalars of pass k formed in between; on return s_alpha and
+// s_beta hold the published values.  False if this CTA's wait timed out.
+__device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsigned n, int k, bool only_gamma,
+                                          double* hist, double* s_alpha, double* s_beta) {
+  __shared__ int s_last, s_ok;
+  __syncthreads();  // this CTA's partials are written
+  if (threadIdx.x == 0) {
+    const unsigned t = atom_add_acq_rel_u32(c.cnt, 1u);
+    s_last = t == (n + 1u) * gridDim.x - 1u;
+    s_ok = 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    coop_scalars(a, c, k, only_gamma, hist);
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_u32(c.rel, n + 1u);
+  } else if (threadIdx.x == 0) {
+    unsigned it = 0;
+    while (ld_acquire_u32(c.rel) < n + 1u) {
+      if (++it > (1u << 22)) {
+        s_ok = 0;
+        break;
+      }
+      __nanosleep(32);
     }
   }
+  __syncthreads();
+  if (!s_ok) return false;
+  for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
+    s_alpha[b] = __ldcg(c.sc + b);
+    s_beta[b] = __ldcg(c.sc + kCoopMaxB + b);
+  }
+  __syncthreads();
+  return true;
 }
 
 template <int Q, int P, int JMAX, int NS>
 __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs a0, const CgCoop c) {
   constexpr int W = Q * P;
-  __shared__ double s_g[kCoopMaxB], s_alpha[kCoopMaxB], s_beta[kCoopMaxB];
+  __shared__ double s_alpha[kCoopMaxB], s_beta[kCoopMaxB];
   const NLSmem S = nl_smem_setup<Q, P, NS>(a0);
-  const int nthreads = blockDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = nthreads >> 5;
-  for (int b = threadIdx.x; b < a0.B; b += nthreads) s_g[b] = s_alpha[b] = s_beta[b] = 0.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int b = threadIdx.x; b < a0.B; b += blockDim.x) s_alpha[b] = s_beta[b] = 0.0;
   __syncthreads();
   NLArgs a = a0;
   a.x = c.r; a.out = c.w; a.pout = c.p; a.sv = c.s; a.xs = c.x; a.beta = s_beta; a.al_s = s_alpha;
@@ -587,19 +611,17 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
   for (int k = 0; k < c.iters; ++k) {
     a.upd = k > 0;
     a.first = k == 1;
-    a.part = c.pd[k & 1];
-    a.part2 = c.pg[k & 1];
+    a.part = (k & 1) ? c.pd[1] : c.pd[0];
+    a.part2 = (k & 1) ? c.pg[1] : c.pg[0];
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);
-    if (!coop_barrier(c.bar)) {
+    if (!coop_step(a, c, (unsigned)k, k, false, c.hist ? c.hist + (size_t)k * a.B : nullptr, s_alpha, s_beta)) {
       if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
       return;
     }
-    coop_scalars(a, k, false, s_g, s_alpha, s_beta, c.hist ? c.hist + (size_t)k * a.B : nullptr);
-    __syncthreads();
   }
   // last update (iteration iters - 1) and gamma of the final residual; one warp per row
   const bool first = c.iters == 1;
-  a.part2 = c.pg[c.iters & 1];
+  a.part2 = (c.iters & 1) ? c.pg[1] : c.pg[0];
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int b = tile / a.tiles_per_slice;
     const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
@@ -633,11 +655,10 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
       if (lane == 0) a.part2[(size_t)b * a.HS + st * a.H + h] = d;
     }
   }
-  if (!coop_barrier(c.bar)) {
+  if (!coop_step(a, c, (unsigned)c.iters, c.iters, true, c.hist ? c.hist + (size_t)c.iters * a.B : nullptr,
+                 s_alpha, s_beta)) {
     if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
-    return;
   }
-  coop_scalars(a, c.iters, true, s_g, s_alpha, s_beta, c.hist ? c.hist + (size_t)c.iters * a.B : nullptr);
 }
 
 typedef void (*CgKernel)(const NLArgs, const CgCoop);
