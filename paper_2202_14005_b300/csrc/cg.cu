@@ -256,6 +256,9 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
       prof_mark("cg_vec", p->stream, true);
       count_launch(p);
     }
+  } else if (p->lines.ok && p->lines.coop && iters > 0) {
+    // x = 0, r = rhs and ||r||^2 in the first pass of the one-launch solve
+    return launch_cg_lines(p, x, iters, rr_hist, rhs);
   } else {
     RowArgs a = base_args(p);
     a.a = rhs; a.o1 = w.r; a.o2 = x; a.fin = FIN_RR0; a.hist = rr_hist;
@@ -265,7 +268,7 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
     count_launch(p);
   }
   // ---- iterations: all of them in one cooperative launch where the fused kernel applies
-  if (p->lines.ok && p->lines.coop && iters > 0) return launch_cg_lines(p, x, iters, rr_hist);
+  if (p->lines.ok && p->lines.coop && iters > 0) return launch_cg_lines(p, x, iters, rr_hist, nullptr);
   for (int it = 0; it < iters; ++it) {
     double* hist = rr_hist ? rr_hist + (size_t)(it + 1) * B : nullptr;
     if (p->lines.ok) {

@@ -163,7 +163,7 @@ void free_lines_tables(sense_plan pl) {
   pl->lines = LinesTables();
 }
 
-int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist) {
+int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const float2* rhs0) {
   const LinesTables& T = pl->lines;
   if (!T.coop) return SENSE_EUNSUPPORTED;
   Workspace& w = pl->w;
@@ -179,7 +179,7 @@ int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist) {
   a.rr = w.rr; a.alpha = w.alpha; a.rr_hist_row = nullptr;
   a.counter = w.counter; a.status = pl->status;
   CgCoop c;
-  c.iters = iters; c.x = x; c.r = w.r; c.p = w.p; c.s = w.sv; c.w = w.wv; c.hist = rr_hist;
+  c.iters = iters; c.x = x; c.r = w.r; c.p = w.p; c.s = w.sv; c.w = w.wv; c.hist = rr_hist; c.rhs0 = rhs0;
   const size_t np = (size_t)pl->B * pl->S * pl->H;
   for (int i = 0; i < 2; ++i) {
     c.pd[i] = w.part2 + i * np;

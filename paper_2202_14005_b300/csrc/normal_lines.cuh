@@ -49,6 +49,7 @@ struct NLArgs {
   double* part2 = nullptr;
   const double* al_s = nullptr;
   int upd = 0, first = 0;
+  const float2* rhs0 = nullptr;  // NM_CG2 without upd: stage r = rhs0 (written to r) and zero x
   const float2* pold;
   float2* pout;
   float2* out;
@@ -220,6 +221,15 @@ __device__ __forceinline__ void nl_tile(const NLArgs& a, const NLSmem& S, int ti
           xv[i] = x;
           rv[i] = r;
           sx4[i] = r;
+        }
+      } else if (a.rhs0) {
+        const float4* r0 = reinterpret_cast<const float4*>(a.rhs0 + img0);
+        float4* xv = reinterpret_cast<float4*>(a.xs + img0);
+        for (int i = threadIdx.x; i < n4; i += nthreads) {
+          const float4 v = r0[i];
+          rv[i] = v;
+          xv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sx4[i] = v;
         }
       } else {
         for (int i = threadIdx.x; i < n4; i += nthreads) sx4[i] = rv[i];
@@ -499,7 +509,8 @@ struct CgCoop {
   float2* p;
   float2* s;        // S p
   float2* w;        // S r
-  double* hist;     // [iters + 1][B] squared residual norms (row 0 by the caller) or NULL
+  double* hist;     // [iters + 1][B] squared residual norms or NULL
+  const float2* rhs0;  // not NULL: start from x = 0, r = rhs0 (first pass)
   unsigned* cnt;    // arrival count, zero at launch (a 128-byte line of its own)
   unsigned* rel;    // barriers released, zero at launch (a line of its own)
   double* sc;       // published scalars: alpha [kCoopMaxB], beta [kCoopMaxB], gamma [kCoopMaxB]
@@ -557,7 +568,7 @@ __device__ __forceinline__ void coop_scalars(const NLArgs& a, const CgCoop& c, i
     c.sc[2 * kCoopMaxB + b] = g;
     a.rr[b] = g;
     a.alpha[b] = al;
-    if (hist && k > 0) hist[b] = g;
+    if (hist) hist[b] = g;
   }
 }
 
@@ -611,6 +622,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
   for (int k = 0; k < c.iters; ++k) {
     a.upd = k > 0;
     a.first = k == 1;
+    a.rhs0 = k == 0 ? c.rhs0 : nullptr;
     a.part = (k & 1) ? c.pd[1] : c.pd[0];
     a.part2 = (k & 1) ? c.pg[1] : c.pg[0];
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);

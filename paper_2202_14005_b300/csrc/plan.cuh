@@ -111,7 +111,8 @@ int launch_normal_lines(sense_plan p, const NormalLaunch& L);
 float2* modl_zout(void* ws, int B, int H, int W);
 // Every CG iteration in one cooperative launch (p->lines.coop): x, w.r, w.p, w.q, w.rr as left by
 // the initial residual; rr_hist rows 1..iters written when non-NULL.
-int launch_cg_lines(sense_plan p, float2* x, int iters, double* rr_hist);
+// rhs0: when not NULL the solve starts from x = 0, r = rhs0 (set in its first pass)
+int launch_cg_lines(sense_plan p, float2* x, int iters, double* rr_hist, const float2* rhs0);
 int build_lines_tables(sense_plan p);
 void free_lines_tables(sense_plan p);
 
