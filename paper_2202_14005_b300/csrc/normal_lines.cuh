@@ -513,6 +513,9 @@ struct CgCoop {
   const float2* rhs0;  // not NULL: start from x = 0, r = rhs0 (first pass)
   unsigned* cnt;    // arrival count, zero at launch (a 128-byte line of its own)
   unsigned* rel;    // barriers released, zero at launch (a line of its own)
+  int per_slice;    // one tile per CTA: a barrier per slice (words cnt_s / rel_s + 32 b)
+  unsigned* cnt_s;
+  unsigned* rel_s;
   double* sc;       // published scalars: alpha [kCoopMaxB], beta [kCoopMaxB], gamma [kCoopMaxB]
   // row partials of delta and gamma, two buffers each, used by alternate passes
   double* pd[2];
@@ -540,9 +543,9 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 // A slice whose gamma is zero (or whose previous alpha is zero) is frozen: alpha = beta = 0.
 // With only_gamma the pass made the last update: gamma is recorded, no new alpha.
 __device__ __forceinline__ void coop_scalars(const NLArgs& a, const CgCoop& c, int k, bool only_gamma,
-                                             double* hist) {
+                                             double* hist, int b0, int b1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int b = warp; b < a.B; b += nwarps) {
+  for (int b = b0 + warp; b < b1; b += nwarps) {
     const double gp = __ldcg(c.sc + 2 * kCoopMaxB + b), ap = __ldcg(c.sc + b);
     double g = 0.0, d = 0.0;
     if (only_gamma) g = lane_tree_sum(a.part2 + (size_t)b * a.HS, a.HS, lane);
@@ -574,23 +577,25 @@ __device__ __forceinline__ void coop_scalars(const NLArgs& a, const CgCoop& c, i
 
 // Barrier n of the solve with the scalars of pass k formed in between; on return s_alpha and
 // s_beta hold the published values.  False if this CTA's wait timed out.
-__device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsigned n, int k, bool only_gamma,
+// cnt / rel / group: the barrier's words and number of CTAs; slices b0..b1-1 get their scalars.
+__device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsigned* cnt, unsigned* rel,
+                                          unsigned group, int b0, int b1, unsigned n, int k, bool only_gamma,
                                           double* hist, double* s_alpha, double* s_beta) {
   __shared__ int s_last, s_ok;
   __syncthreads();  // this CTA's partials are written
   if (threadIdx.x == 0) {
-    const unsigned t = atom_add_acq_rel_u32(c.cnt, 1u);
-    s_last = t == (n + 1u) * gridDim.x - 1u;
+    const unsigned t = atom_add_acq_rel_u32(cnt, 1u);
+    s_last = t == (n + 1u) * group - 1u;
     s_ok = 1;
   }
   __syncthreads();
   if (s_last) {
-    coop_scalars(a, c, k, only_gamma, hist);
+    coop_scalars(a, c, k, only_gamma, hist, b0, b1);
     __syncthreads();
-    if (threadIdx.x == 0) st_release_u32(c.rel, n + 1u);
+    if (threadIdx.x == 0) st_release_u32(rel, n + 1u);
   } else if (threadIdx.x == 0) {
     unsigned it = 0;
-    while (ld_acquire_u32(c.rel) < n + 1u) {
+    while (ld_acquire_u32(rel) < n + 1u) {
       if (++it > (1u << 22)) {
         s_ok = 0;
         break;
@@ -600,7 +605,7 @@ __device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsi
   }
   __syncthreads();
   if (!s_ok) return false;
-  for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
     s_alpha[b] = __ldcg(c.sc + b);
     s_beta[b] = __ldcg(c.sc + kCoopMaxB + b);
   }
@@ -619,6 +624,18 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
   NLArgs a = a0;
   a.x = c.r; a.out = c.w; a.pout = c.p; a.sv = c.s; a.xs = c.x; a.beta = s_beta; a.al_s = s_alpha;
   a.finalize = 0;
+  // per-slice barriers (one tile per CTA): the CTAs of one slice wait only for each other, so
+  // slices drift apart and their phases overlap on the SMs; otherwise one grid barrier
+  unsigned *cnt = c.cnt, *rel = c.rel, group = gridDim.x;
+  int b0 = 0, b1 = a.B;
+  if (c.per_slice) {
+    if ((int)blockIdx.x >= a.ntiles) return;  // no tile: takes part in no barrier
+    b0 = blockIdx.x / a.tiles_per_slice;
+    b1 = b0 + 1;
+    cnt = c.cnt_s + 32 * b0;
+    rel = c.rel_s + 32 * b0;
+    group = a.tiles_per_slice;
+  }
   for (int k = 0; k < c.iters; ++k) {
     a.upd = k > 0;
     a.first = k == 1;
@@ -626,7 +643,8 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
     a.part = (k & 1) ? c.pd[1] : c.pd[0];
     a.part2 = (k & 1) ? c.pg[1] : c.pg[0];
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);
-    if (!coop_step(a, c, (unsigned)k, k, false, c.hist ? c.hist + (size_t)k * a.B : nullptr, s_alpha, s_beta)) {
+    if (!coop_step(a, c, cnt, rel, group, b0, b1, (unsigned)k, k, false, c.hist ? c.hist + (size_t)k * a.B : nullptr,
+                   s_alpha, s_beta)) {
       if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
       return;
     }
@@ -667,8 +685,8 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
       if (lane == 0) a.part2[(size_t)b * a.HS + st * a.H + h] = d;
     }
   }
-  if (!coop_step(a, c, (unsigned)c.iters, c.iters, true, c.hist ? c.hist + (size_t)c.iters * a.B : nullptr,
-                 s_alpha, s_beta)) {
+  if (!coop_step(a, c, cnt, rel, group, b0, b1, (unsigned)c.iters, c.iters, true,
+                 c.hist ? c.hist + (size_t)c.iters * a.B : nullptr, s_alpha, s_beta)) {
     if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
   }
 }
