@@ -1192,13 +1192,51 @@ DnLayout dn_layout(int B, int H, int W) {
   for (int i = 0; i < 2; ++i) { L.g[i] = o; o += act; }
   L.zout = o; o += up256((size_t)B * H * W * 8);  // the block output z of an unrolled step
   L.part_small = o; o += up256((size_t)L.nch_small * kSmallOut * 4);
-  L.part64 = o; o += up256(((size_t)L.nch64 * 9 * CH * CH + (size_t)L.nch64 * CH) * 4);
+  // two sets: the reduction of one layer's partials (side stream) overlaps the next layer's sums
+  L.part64 = o; o += 2 * up256(((size_t)L.nch64 * 9 * CH * CH + (size_t)L.nch64 * CH) * 4);
   L.status = o; o += 256;
   L.total = o;
   return L;
 }
 
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Side stream of the backward pass, one per device: the weight-gradient partial sums of the
+// 2-channel layers and every fixed-order reduction run there, beside the data-gradient chain on
+// the caller's stream (they need other units: CUDA cores and memory against the tensor cores).
+// Events fork and join it, so the call still completes in the caller's stream order.
+constexpr int kSideDevs = 64;
+constexpr int kSideEvents = 8;
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[kSideEvents] = {};
+};
+SideStream g_side[kSideDevs];
+std::mutex g_side_mu;
+
+int side_stream(SideStream** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSideDevs) return SENSE_ECUDA;
+  std::lock_guard<std::mutex> l(g_side_mu);
+  SideStream& ss = g_side[dev];
+  if (!ss.s) {
+    if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess) {
+      ss.s = nullptr;
+      return SENSE_ECUDA;
+    }
+    for (int i = 0; i < kSideEvents; ++i)
+      if (cudaEventCreateWithFlags(&ss.ev[i], cudaEventDisableTiming) != cudaSuccess) return SENSE_ECUDA;
+  }
+  *out = &ss;
+  return SENSE_OK;
+}
+
+// `to` waits for the work issued so far on `from` (event slot i of the side stream's set)
+int stream_after(const SideStream& ss, int i, cudaStream_t from, cudaStream_t to) {
+  if (cudaEventRecord(ss.ev[i], from) != cudaSuccess || cudaStreamWaitEvent(to, ss.ev[i], 0) != cudaSuccess)
+    return SENSE_ECUDA;
+  return SENSE_OK;
+}
 
 int check_common(int kind, const void* weights, const void* x, void* ws, size_t ws_bytes, int B, int H,
                  int W) {
@@ -1318,48 +1356,61 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   float* p64 = reinterpret_cast<float*>(w8 + L.part64);
   int* status = reinterpret_cast<int*>(w8 + L.status);
   // input-gradient weight tables were packed by the forward pass that precedes every backward
-  // last layer: input gradient (masked by a4 > 0) and weight gradient
-  const size_t npx = (size_t)B * H * W;
+  SideStream* ss = nullptr;
+  if (int e = side_stream(&ss)) return e;
+  cudaStream_t sd = ss->s;
+  const size_t p64_set = up256(((size_t)L.nch64 * 9 * CH * CH + (size_t)L.nch64 * CH) * 4) / sizeof(float);
+  // fork: the side stream sees the activations, the output gradient and the zeroed sums
+  if (int e = stream_after(*ss, 0, st, sd)) return e;
+  // last layer: input gradient (masked by a4 > 0) on the caller's stream, weight gradient beside it
   prof_mark("dn_2to64", st, false);
   k_2to64<1><<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(
       B, H, W, go, reinterpret_cast<const uint32_t*>(w8 + L.tf[1]), nullptr, act[3], gbuf[0]);
   prof_mark("dn_2to64", st, true);
-  prof_mark("dn_wgrad_small", st, false);
-  k_wgrad_l5<<<L.nch_small, 256, wl5_smem(W), st>>>(B, H, W, act[3], go, ps);
-  prof_mark("dn_wgrad_small", st, true);
-  prof_mark("dn_reduce", st, false);
-  k_reduce_partials<<<(2 * CH * 9 + 2 + 31) / 32, 256, 0, st>>>(ps, L.nch_small, kSmallOut, 2 * CH * 9,
+  prof_mark("dn_wgrad_small", sd, false);
+  k_wgrad_l5<<<L.nch_small, 256, wl5_smem(W), sd>>>(B, H, W, act[3], go, ps);
+  prof_mark("dn_wgrad_small", sd, true);
+  prof_mark("dn_reduce", sd, false);
+  k_reduce_partials<<<(2 * CH * 9 + 2 + 31) / 32, 256, 0, sd>>>(ps, L.nch_small, kSmallOut, 2 * CH * 9,
                                                                  grad_weights + o.w[4], 2, CH * 18,
                                                                  grad_weights + o.b[4]);
-  prof_mark("dn_reduce", st, true);
-  // 64 -> 64 layers 4, 3, 2 (index l = 2, 1, 0 of the packed set)
+  prof_mark("dn_reduce", sd, true);
+  // 64 -> 64 layers 4, 3, 2 (index l = 2, 1, 0 of the packed set); partial set l & 1
   int cur = 0;
   for (int l = 2; l >= 0; --l) {
     const __nv_bfloat16* ain = act[l];  // input activation of this layer
+    float* pl = p64 + (size_t)(l & 1) * p64_set;
+    // layer 0 reuses layer 2's set: its reduction on the side stream must be done
+    if (l == 0)
+      if (int e = stream_after(*ss, 1, sd, st)) return e;
     int nparts = 0;
-    if (int e = launch_wgrad64(gbuf[cur], ain, p64, L.nch64, B, H, W, status, st, &nparts)) return e;
-    prof_mark("dn_reduce", st, false);
-    k_reduce_wgrad64<<<(CH * CH * 9 + CH + 31) / 32, 256, 0, st>>>(p64, nparts, grad_weights + o.w[l + 1],
+    if (int e = launch_wgrad64(gbuf[cur], ain, pl, L.nch64, B, H, W, status, st, &nparts)) return e;
+    if (int e = stream_after(*ss, 2 + l, st, sd)) return e;
+    prof_mark("dn_reduce", sd, false);
+    k_reduce_wgrad64<<<(CH * CH * 9 + CH + 31) / 32, 256, 0, sd>>>(pl, nparts, grad_weights + o.w[l + 1],
                                                                      grad_weights + o.b[l + 1]);
-    prof_mark("dn_reduce", st, true);
+    prof_mark("dn_reduce", sd, true);
     if (int e = launch_conv64(gbuf[cur], reinterpret_cast<__nv_bfloat16*>(w8 + L.wd[l]), nullptr, ain,
                               gbuf[cur ^ 1], 1, B, H, W, status, st))
       return e;
     cur ^= 1;
   }
-  // first layer: weight gradient and input gradient (+ residual)
-  prof_mark("dn_wgrad_small", st, false);
-  k_wgrad_l1<<<L.nch_small, 256, wl1_smem(W), st>>>(B, H, W, gbuf[cur], xx, ps);
-  prof_mark("dn_wgrad_small", st, true);
-  prof_mark("dn_reduce", st, false);
-  k_reduce_partials<<<(CH * 18 + CH + 31) / 32, 256, 0, st>>>(ps, L.nch_small, kSmallOut, CH * 18,
+  // first layer: weight gradient (side stream) and input gradient (+ residual)
+  if (int e = stream_after(*ss, 5, st, sd)) return e;
+  prof_mark("dn_wgrad_small", sd, false);
+  k_wgrad_l1<<<L.nch_small, 256, wl1_smem(W), sd>>>(B, H, W, gbuf[cur], xx, ps);
+  prof_mark("dn_wgrad_small", sd, true);
+  prof_mark("dn_reduce", sd, false);
+  k_reduce_partials<<<(CH * 18 + CH + 31) / 32, 256, 0, sd>>>(ps, L.nch_small, kSmallOut, CH * 18,
                                                                grad_weights + o.w[0], CH, CH * 18,
                                                                grad_weights + o.b[0]);
-  prof_mark("dn_reduce", st, true);
+  prof_mark("dn_reduce", sd, true);
   // first layer input gradient on the tensor cores: gx = gout + conv^T(g1) (flipped taps)
   if (int e = launch_conv64(gbuf[cur], reinterpret_cast<const __nv_bfloat16*>(w8 + L.ts[1]), nullptr, nullptr,
                             nullptr, 3, B, H, W, status, st, go, static_cast<float2*>(grad_x)))
     return e;
+  // join
+  if (int e = stream_after(*ss, 6, sd, st)) return e;
   prof_count(8);  // every launch of the backward except the tensor-core kernels
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
