@@ -1201,42 +1201,6 @@ DnLayout dn_layout(int B, int H, int W) {
 
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Side stream of the backward pass, one per device: the weight-gradient partial sums of the
-// 2-channel layers and every fixed-order reduction run there, beside the data-gradient chain on
-// the caller's stream (they need other units: CUDA cores and memory against the tensor cores).
-// Events fork and join it, so the call still completes in the caller's stream order.
-constexpr int kSideDevs = 64;
-constexpr int kSideEvents = 8;
-struct SideStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t ev[kSideEvents] = {};
-};
-SideStream g_side[kSideDevs];
-std::mutex g_side_mu;
-
-int side_stream(SideStream** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSideDevs) return SENSE_ECUDA;
-  std::lock_guard<std::mutex> l(g_side_mu);
-  SideStream& ss = g_side[dev];
-  if (!ss.s) {
-    if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess) {
-      ss.s = nullptr;
-      return SENSE_ECUDA;
-    }
-    for (int i = 0; i < kSideEvents; ++i)
-      if (cudaEventCreateWithFlags(&ss.ev[i], cudaEventDisableTiming) != cudaSuccess) return SENSE_ECUDA;
-  }
-  *out = &ss;
-  return SENSE_OK;
-}
-
-// `to` waits for the work issued so far on `from` (event slot i of the side stream's set)
-int stream_after(const SideStream& ss, int i, cudaStream_t from, cudaStream_t to) {
-  if (cudaEventRecord(ss.ev[i], from) != cudaSuccess || cudaStreamWaitEvent(to, ss.ev[i], 0) != cudaSuccess)
-    return SENSE_ECUDA;
-  return SENSE_OK;
-}
 
 int check_common(int kind, const void* weights, const void* x, void* ws, size_t ws_bytes, int B, int H,
                  int W) {
@@ -1355,13 +1319,15 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   float* ps = reinterpret_cast<float*>(w8 + L.part_small);
   float* p64 = reinterpret_cast<float*>(w8 + L.part64);
   int* status = reinterpret_cast<int*>(w8 + L.status);
-  // input-gradient weight tables were packed by the forward pass that precedes every backward
-  SideStream* ss = nullptr;
-  if (int e = side_stream(&ss)) return e;
-  cudaStream_t sd = ss->s;
+  // (the input-gradient weight tables were packed by the forward pass that precedes every backward)
+  // The weight-gradient sums of the 2-channel layers and every fixed-order reduction run on a
+  // side stream beside the data-gradient chain (CUDA cores and memory against tensor cores)
+  SideSet* ss = nullptr;
+  if (int e = side_set(&ss)) return e;
+  cudaStream_t sd = ss->s[0];
   const size_t p64_set = up256(((size_t)L.nch64 * 9 * CH * CH + (size_t)L.nch64 * CH) * 4) / sizeof(float);
   // fork: the side stream sees the activations, the output gradient and the zeroed sums
-  if (int e = stream_after(*ss, 0, st, sd)) return e;
+  if (int e = stream_after(*ss, st, sd)) return e;
   // last layer: input gradient (masked by a4 > 0) on the caller's stream, weight gradient beside it
   prof_mark("dn_2to64", st, false);
   k_2to64<1><<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(
@@ -1382,10 +1348,10 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
     float* pl = p64 + (size_t)(l & 1) * p64_set;
     // layer 0 reuses layer 2's set: its reduction on the side stream must be done
     if (l == 0)
-      if (int e = stream_after(*ss, 1, sd, st)) return e;
+      if (int e = stream_after(*ss, sd, st)) return e;
     int nparts = 0;
     if (int e = launch_wgrad64(gbuf[cur], ain, pl, L.nch64, B, H, W, status, st, &nparts)) return e;
-    if (int e = stream_after(*ss, 2 + l, st, sd)) return e;
+    if (int e = stream_after(*ss, st, sd)) return e;
     prof_mark("dn_reduce", sd, false);
     k_reduce_wgrad64<<<(CH * CH * 9 + CH + 31) / 32, 256, 0, sd>>>(pl, nparts, grad_weights + o.w[l + 1],
                                                                      grad_weights + o.b[l + 1]);
@@ -1396,7 +1362,7 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
     cur ^= 1;
   }
   // first layer: weight gradient (side stream) and input gradient (+ residual)
-  if (int e = stream_after(*ss, 5, st, sd)) return e;
+  if (int e = stream_after(*ss, st, sd)) return e;
   prof_mark("dn_wgrad_small", sd, false);
   k_wgrad_l1<<<L.nch_small, 256, wl1_smem(W), sd>>>(B, H, W, gbuf[cur], xx, ps);
   prof_mark("dn_wgrad_small", sd, true);
@@ -1410,7 +1376,7 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
                             nullptr, 3, B, H, W, status, st, go, static_cast<float2*>(grad_x)))
     return e;
   // join
-  if (int e = stream_after(*ss, 6, sd, st)) return e;
+  if (int e = stream_after(*ss, sd, st)) return e;
   prof_count(8);  // every launch of the backward except the tensor-core kernels
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

@@ -81,6 +81,17 @@ struct sense_plan_s {
 
 // Process-wide launch accounting and per-kernel-class CUDA-event timing (profile.cu).
 void prof_count(int n);
+
+// Library-owned side streams, two per device (created on first use), for work inside one call
+// that can run beside the caller's stream; events fork them from and join them back to it, so a
+// call still completes in the caller's stream order.
+struct SideSet {
+  cudaStream_t s[2];
+  cudaEvent_t ev;
+};
+int side_set(SideSet** out);
+// `to` waits for the work issued so far on `from`
+int stream_after(const SideSet& ss, cudaStream_t from, cudaStream_t to);
 void prof_mark(const char* name, cudaStream_t s, bool stop);
 inline void count_launch(sense_plan, int n = 1) { prof_count(n); }
 

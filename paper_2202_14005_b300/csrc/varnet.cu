@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(256) k_vn_reduce(const float* partial, int nro
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct VnLayout {
-  size_t wk, wn, u, v, z, kg, n1, n2, part, pdot, total;
+  size_t wk, wn, u, v, z, kg, n1, n2, part, part2, pdot, total;
 };
 VnLayout vn_layout(int B, int H, int W) {
   VnLayout L;
@@ -680,7 +680,8 @@ VnLayout vn_layout(int B, int H, int W) {
   L.kg = o; o += up256(px * NK * 4);
   L.n1 = o; o += up256(px * 8);
   L.n2 = o; o += up256(px * 8);
-  L.part = o; o += up256((size_t)B * H * NK * 2 * NT * 4);
+  L.part = o; o += up256((size_t)B * H * NK * 2 * NT * 4);  // filter-gradient rows
+  L.part2 = o; o += up256((size_t)B * H * NK * NW * 4);     // RBF-gradient rows (run beside them)
   L.pdot = o; o += 256;
   L.total = o;
   return L;
@@ -780,24 +781,34 @@ int launch_KT(const Shape& sh, const bf16* src, const float* prm, float sgn, con
 // Parameter gradients of the regulariser sum_i K_i^T Phi_i'(K_i x), scaled by `scale` and added to
 // grad_prm: filters  scale * sum (u (x) g_shift + v (x) x_shift),  RBF weights  scale * sum kg phi_j(z).
 // Needs u, v, z, kg of a two-source K launch in the workspace.
+// The filter gradient runs on stream s_w and the RBF-weight gradient on s_r (the same stream or
+// two side streams: they read the workspace and write disjoint parts of grad_prm).
 void launch_param_grads(const Shape& sh, const float2* x, const float2* g, float scale, float* grad_prm,
-                        uint8_t* ws, const VnLayout& L) {
+                        uint8_t* ws, const VnLayout& L, cudaStream_t s_w, cudaStream_t s_r) {
   const int rows = sh.B * sh.H;
   float* part = reinterpret_cast<float*>(ws + L.part);
-  prof_mark("vn_wgrad", sh.st, false);
-  k_vn_wgrad<<<rows, 128, wg_smem(sh.W), sh.st>>>(sh.B, sh.H, sh.W, reinterpret_cast<const bf16*>(ws + L.u),
-                                                   reinterpret_cast<const bf16*>(ws + L.v), g, x, part);
-  k_vn_reduce<<<(NK * 2 * NT + 31) / 32, 256, 0, sh.st>>>(part, rows, NK * 2 * NT, scale, grad_prm);
-  prof_mark("vn_wgrad", sh.st, true);
-  prof_mark("vn_rbfgrad", sh.st, false);
-  k_vn_rbfgrad<<<rows, 256, 0, sh.st>>>(sh.B, sh.H, sh.W, reinterpret_cast<const float*>(ws + L.z),
-                                         reinterpret_cast<const float*>(ws + L.kg), part);
-  k_vn_reduce<<<(NK * NW + 31) / 32, 256, 0, sh.st>>>(part, rows, NK * NW, scale, grad_prm + OFF_RBF);
-  prof_mark("vn_rbfgrad", sh.st, true);
+  float* part2 = reinterpret_cast<float*>(ws + L.part2);
+  prof_mark("vn_wgrad", s_w, false);
+  k_vn_wgrad<<<rows, 128, wg_smem(sh.W), s_w>>>(sh.B, sh.H, sh.W, reinterpret_cast<const bf16*>(ws + L.u),
+                                                 reinterpret_cast<const bf16*>(ws + L.v), g, x, part);
+  k_vn_reduce<<<(NK * 2 * NT + 31) / 32, 256, 0, s_w>>>(part, rows, NK * 2 * NT, scale, grad_prm);
+  prof_mark("vn_wgrad", s_w, true);
+  prof_mark("vn_rbfgrad", s_r, false);
+  k_vn_rbfgrad<<<rows, 256, 0, s_r>>>(sh.B, sh.H, sh.W, reinterpret_cast<const float*>(ws + L.z),
+                                       reinterpret_cast<const float*>(ws + L.kg), part2);
+  k_vn_reduce<<<(NK * NW + 31) / 32, 256, 0, s_r>>>(part2, rows, NK * NW, scale, grad_prm + OFF_RBF);
+  prof_mark("vn_rbfgrad", s_r, true);
 }
 
-// Normal operator without lambda (A^H A x) through the plan's own path.
-int normal0(sense_plan p, const float2* x, float2* out) { return sense_normal(p, x, out, 0.f); }
+// Normal operator without lambda (A^H A x) through the plan's own path, on stream s (the plan's
+// stream is switched for the call; a plan is used by one host thread at a time).
+int normal0(sense_plan p, const float2* x, float2* out, cudaStream_t s) {
+  const cudaStream_t own = p->stream;
+  p->stream = s;
+  const int e = sense_normal(p, x, out, 0.f);
+  p->stream = own;
+  return e;
+}
 
 // d/dlambda of the stage: -Re<g, n - c>, added to grad[OFF_LAM] (float32).
 __global__ void k_vn_addlam(const double* d, float* g) { g[OFF_LAM] += (float)(-d[0]); }
@@ -833,9 +844,15 @@ int varnet_stage(sense_plan p, const float* prm, const void* AHy, const void* x_
   const Shape sh{p->B, p->H, p->W, p->stream};
   const float2* x = static_cast<const float2*>(x_t);
   float2* n1 = nx_out ? static_cast<float2*>(nx_out) : reinterpret_cast<float2*>(w8 + L.n1);
+  // A^H A x on a side stream beside z = K x and u = Phi'(z); both feed the combine
+  SideSet* ss = nullptr;
+  if (int e = side_set(&ss)) return e;
+  const cudaStream_t sd = ss->s[1];
+  if (int e = stream_after(*ss, p->stream, sd)) return e;
+  if (int e = normal0(p, x, n1, sd)) return e;
   vn_pack(prm, w8, L, p->stream);
-  if (int e = normal0(p, x, n1)) return e;
   if (int e = launch_K(sh, 1, prm, x, nullptr, w8, L)) return e;
+  if (int e = stream_after(*ss, sd, p->stream)) return e;
   if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.u), prm, -1.f, x, n1,
                         static_cast<const float2*>(AHy), static_cast<float2*>(x_next), w8, L))
     return e;
@@ -863,22 +880,32 @@ int varnet_stage_backward_ex(sense_plan p, const float* prm, const void* AHy, co
   const float2* n1 = static_cast<const float2*>(nx_t);
   if (!n1) {
     float2* t = reinterpret_cast<float2*>(w8 + L.n1);
-    if (int e = normal0(p, x, t)) return e;
+    if (int e = normal0(p, x, t, p->stream)) return e;
     n1 = t;
   }
   if (int e = launch_dot_rows(p, g, n1, static_cast<const float2*>(AHy), pdot, 1, 0)) return e;
   prof_mark("vn_misc", p->stream, false);
   k_vn_addlam<<<1, 1, 0, p->stream>>>(pdot, grad_prm);
   prof_mark("vn_misc", p->stream, true);
+  // Side streams: s0 takes the filter gradient, s1 first A^H A g and then the RBF-weight gradient;
+  // the caller's stream runs K g and the combine, and waits for both before returning.
+  SideSet* ss = nullptr;
+  if (int e = side_set(&ss)) return e;
+  const cudaStream_t s0 = ss->s[0], s1 = ss->s[1];
+  if (int e = stream_after(*ss, p->stream, s1)) return e;
+  if (int e = normal0(p, g, n2, s1)) return e;
   // z = K x (recomputed, or kept in ws by this stage's forward together with u = Phi'(z)), kg = K g,
-  // v = Phi''(z) kg; parameter gradients of -R (read g and x before grad_t is written)
+  // v = Phi''(z) kg; parameter gradients of -R beside the combine (they read g, x, u, v, z, kg)
   if (int e = launch_K(sh, recompute ? 2 : 3, prm, x, g, w8, L)) return e;
-  launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L);
-  // grad_t = g - K^T v - lambda A^H A g
-  if (int e = normal0(p, g, n2)) return e;
+  if (int e = stream_after(*ss, p->stream, s0)) return e;
+  if (int e = stream_after(*ss, p->stream, s1)) return e;
+  launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L, s0, s1);
+  // grad_t = g - K^T v - lambda A^H A g (A^H A g was issued on s1 before the RBF gradient)
+  if (int e = stream_after(*ss, s1, p->stream)) return e;
   if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.v), prm, -1.f, g, n2, nullptr,
                         static_cast<float2*>(grad_t), w8, L))
     return e;
+  if (int e = stream_after(*ss, s0, p->stream)) return e;
   prof_count(8);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -930,7 +957,7 @@ int vn_denoiser_backward(const float* prm, const void* x, const void* grad_out, 
   const float2* g = static_cast<const float2*>(grad_out);
   vn_pack(prm, w8, L, st);
   if (int e = launch_K(sh, 2, prm, xx, g, w8, L)) return e;
-  launch_param_grads(sh, xx, g, 1.f, grad_prm, w8, L);
+  launch_param_grads(sh, xx, g, 1.f, grad_prm, w8, L, st, st);
   // dR/dx^H g = K^T (Phi''(K x) K g)  (the Jacobian of R is symmetric)
   if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.v), prm, 1.f, nullptr, nullptr, nullptr,
                         static_cast<float2*>(grad_x), w8, L))
