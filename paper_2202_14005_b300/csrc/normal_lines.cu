@@ -136,9 +136,8 @@ int build_lines_tables(sense_plan pl) {
   T.grid = std::min(tiles, maxb * pl->num_sms);
   T.ok = 1;
   // the whole-solve CG kernel: all of its CTAs must be resident at once (cooperative launch).
-  // It pays off while each CTA holds at most two tiles (the tile's update traffic then sits on
-  // the CTA's own latency chain; with more tiles per CTA separate streaming launches are faster:
-  // measured on B300, 256x232, 12 coils: 4 slices 29.6 vs 36 us, 16 slices 114 vs 98 us per iteration).
+  // Used up to four tiles per CTA (measured on B300, 256x232, 12 coils, 10 iterations: 4 slices
+  // 222 vs 360 us per solve, 16 slices with 3.5 tiles per CTA 0.93 vs 1.06 ms).
   if (pl->B <= kCoopMaxB) {
     CgKernel ck = Q == 8 ? pick_cg_q8(P, JMAX, pl->S) : pick_cg_q16(P, JMAX, pl->S);
     int nb = 0, coop = 0, dev = 0;
@@ -149,7 +148,7 @@ int build_lines_tables(sense_plan pl) {
             cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ck, T.threads, Lo.total) == cudaSuccess && nb >= 1) {
       const int cgrid = std::min(tiles, nb * pl->num_sms);
-      if (tiles <= 2 * cgrid) {
+      if (tiles <= 4 * cgrid) {
         T.coop = reinterpret_cast<const void*>(ck);
         T.coop_grid = cgrid;
       }
