@@ -184,17 +184,12 @@ int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const 
     c.pd[i] = w.part2 + i * np;
     c.pg[i] = w.part2 + (2 + i) * np;
   }
-  // counter block: last-block counter (bytes 0..127), arrival count (128), release word (256),
-  // scalars (512..895), per-slice arrival counts (1024 + 128 b) and release words (3072 + 128 b)
-  c.cnt = w.counter + 32;
-  c.rel = w.counter + 64;
+  // counter block: last-block counter (bytes 0..127), scalars (512..895), per-slice arrival
+  // counts (1024 + 128 b) and release words (3072 + 128 b)
   c.sc = reinterpret_cast<double*>(w.counter + 128);
   c.cnt_s = w.counter + 256;
   c.rel_s = w.counter + 768;
-  c.per_slice = a.ntiles <= T.coop_grid;
-  if (cudaMemsetAsync(c.cnt, 0, 256, pl->stream) != cudaSuccess ||
-      cudaMemsetAsync(c.cnt_s, 0, 4096, pl->stream) != cudaSuccess)
-    return SENSE_ECUDA;
+  if (cudaMemsetAsync(c.cnt_s, 0, 4096, pl->stream) != cudaSuccess) return SENSE_ECUDA;
   void* args[] = {&a, &c};
   prof_mark("cg_lines", pl->stream, false);
   const cudaError_t e = cudaLaunchCooperativeKernel(T.coop, dim3(T.coop_grid), dim3(T.threads), args,

@@ -511,9 +511,8 @@ struct CgCoop {
   float2* w;        // S r
   double* hist;     // [iters + 1][B] squared residual norms or NULL
   const float2* rhs0;  // not NULL: start from x = 0, r = rhs0 (first pass)
-  unsigned* cnt;    // arrival count, zero at launch (a 128-byte line of its own)
-  unsigned* rel;    // barriers released, zero at launch (a line of its own)
-  int per_slice;    // one tile per CTA: a barrier per slice (words cnt_s / rel_s + 32 b)
+  // per slice b: arrival count cnt_s[32 b] and release word rel_s[32 b] (128-byte lines of their
+  // own), zero at launch
   unsigned* cnt_s;
   unsigned* rel_s;
   double* sc;       // published scalars: alpha [kCoopMaxB], beta [kCoopMaxB], gamma [kCoopMaxB]
@@ -624,25 +623,27 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
   NLArgs a = a0;
   a.x = c.r; a.out = c.w; a.pout = c.p; a.sv = c.s; a.xs = c.x; a.beta = s_beta; a.al_s = s_alpha;
   a.finalize = 0;
-  // per-slice barriers (one tile per CTA): the CTAs of one slice wait only for each other, so
-  // slices drift apart and their phases overlap on the SMs; otherwise one grid barrier
-  unsigned *cnt = c.cnt, *rel = c.rel, group = gridDim.x;
-  int b0 = 0, b1 = a.B;
-  if (c.per_slice) {
-    if ((int)blockIdx.x >= a.ntiles) return;  // no tile: takes part in no barrier
-    b0 = blockIdx.x / a.tiles_per_slice;
-    b1 = b0 + 1;
-    cnt = c.cnt_s + 32 * b0;
-    rel = c.rel_s + 32 * b0;
-    group = a.tiles_per_slice;
-  }
+  // One group of CTAs per slice: CTAs (b grid) / B .. ((b + 1) grid) / B - 1 take the row tiles
+  // of slice b round robin, and each group has its own barrier, so the CTAs of a slice wait only
+  // for each other, the slices drift apart and their phases overlap on the SMs.
+  int b0 = 0;
+  while (b0 + 1 < a.B && (int)(((long long)(b0 + 1) * gridDim.x) / a.B) <= (int)blockIdx.x) ++b0;
+  const int g0 = (int)(((long long)b0 * gridDim.x) / a.B), g1 = (int)(((long long)(b0 + 1) * gridDim.x) / a.B);
+  const int li = (int)blockIdx.x - g0;
+  if (li >= a.tiles_per_slice) return;  // more CTAs than tiles in the slice: no tile, no barrier
+  const int gstride = g1 - g0;
+  const unsigned group = (unsigned)min(gstride, a.tiles_per_slice);
+  const int b1 = b0 + 1;
+  const int t0 = b0 * a.tiles_per_slice + li, t1 = b1 * a.tiles_per_slice;
+  unsigned* cnt = c.cnt_s + 32 * b0;
+  unsigned* rel = c.rel_s + 32 * b0;
   for (int k = 0; k < c.iters; ++k) {
     a.upd = k > 0;
     a.first = k == 1;
     a.rhs0 = k == 0 ? c.rhs0 : nullptr;
     a.part = (k & 1) ? c.pd[1] : c.pd[0];
     a.part2 = (k & 1) ? c.pg[1] : c.pg[0];
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);
+    for (int tile = t0; tile < t1; tile += gstride) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);
     if (!coop_step(a, c, cnt, rel, group, b0, b1, (unsigned)k, k, false, c.hist ? c.hist + (size_t)k * a.B : nullptr,
                    s_alpha, s_beta)) {
       if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
   // last update (iteration iters - 1) and gamma of the final residual; one warp per row
   const bool first = c.iters == 1;
   a.part2 = (c.iters & 1) ? c.pg[1] : c.pg[0];
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  for (int tile = t0; tile < t1; tile += gstride) {
     const int b = tile / a.tiles_per_slice;
     const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
     const int nrows = min(a.rows, a.H - h0);

@@ -212,9 +212,9 @@ def _cg_path_counts(fn):
 @pytest.mark.parametrize("B,one_launch", [(4, True), (8, True), (17, False)])
 def test_cg_paths_by_batch(B, one_launch):
     """256x232 line-mask solves: up to 16 slices run every iteration in one cooperative launch
-    (single-reduction recurrence; 4 slices: one row tile per CTA and a barrier per slice, 8
-    slices: up to two tiles per CTA and one grid barrier), 17 per-iteration launches (textbook
-    recurrence); all against the oracle, residual histories included."""
+    (single-reduction recurrence, a group of CTAs and a barrier per slice; 4 slices: one row tile
+    per CTA, 8 slices: up to two), 17 per-iteration launches (textbook recurrence); all against
+    the oracle, residual histories included."""
     cfg, maps, mask, rhs, _ = _cg_inputs(2, B)
     plan = plan_for(maps, mask)
     lam = torch.tensor([cfg.lam], dtype=torch.float64, device="cuda")
