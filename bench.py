@@ -7,7 +7,7 @@ Default step (modl_train): one MoDL training step on 4 slices of 256x232 with
 12 coils (R = 6 variable-density line mask): x^0 = A^H y, five unrolled blocks
 x^{t+1} = (A^H A + lambda I)^{-1}(A^H y + lambda D_W(x^t)) with 10 CG iterations
 each, the MSE loss against the phantoms, the reverse pass through every block
-(second CG solve per block, denoiser backward with recomputed activations) and
+(second CG solve per block, denoiser backward from the activations the forward kept) and
 Adam on the 113,155 parameters — every step in libsense kernels (tensor-core
 convolutions, fused normal operator, CG vector kernels).
 
@@ -42,11 +42,11 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
              "noncart_modl_infer": "modl_infer_radial_b32_c12_256x256_96x512_K10_cg10"}
 # DRAM bytes (read + write) per launch from the committed ncu captures under profiles/, per workload
 # (None where no capture of the current kernel version exists for that workload):
-# normal_lines a 16-slice residual-mode launch (cg_sense); cg_lines one 10-iteration solve, conv64_tc
-# a forward launch and wgrad64 one launch of the 4-slice MoDL step; vn_* one launch each of the
-# 4-slice 320x368 VarNet step.
+# normal_lines a 16-slice residual-mode launch and cg_lines one 16-slice solve (cg_sense); cg_lines
+# one 10-iteration solve, conv64_tc a forward launch and wgrad64 one launch of the 4-slice MoDL step;
+# vn_* one launch each of the 4-slice 320x368 VarNet step.
 NCU_TRAFFIC = {
-    "cg_sense": {"normal_lines": 110.3e6},
+    "cg_sense": {"normal_lines": 110.3e6, "cg_lines": 1.511e9},
     "modl_train": {"cg_lines": None, "conv64_tc": 30.55e6, "wgrad64": 62.9e6},
     "varnet_train": {"vn_K": 23.87e6, "vn_Kbwd": 76.16e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
 }
