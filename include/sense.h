@@ -286,13 +286,26 @@ int varnet_stage(sense_plan plan, const float* params, const void* AHy, const vo
 int varnet_stage_backward(sense_plan plan, const float* params, const void* AHy, const void* x_t,
                           const void* nx_t, const void* grad_next, void* grad_t, float* grad_params,
                           void* ws, size_t ws_bytes);
-/* The same with a choice: recompute != 0 is varnet_stage_backward; recompute == 0 takes z = K x
- * and u = Phi'(z) from ws as varnet_stage of this stage left them (the caller keeps one varnet
- * workspace per stage between the forward and reverse passes, parameters unchanged), so only
- * K g is computed; results are the same. */
+/* The same with choices in `recompute` (bit flags):
+ *   bit 0 (value 1): set = varnet_stage_backward (K x recomputed); clear = take z = K x and
+ *     u = Phi'(z) from ws as varnet_stage of this stage left them (the caller keeps one varnet
+ *     workspace per stage between the forward and reverse passes, parameters unchanged), so only
+ *     K g is computed; results are the same.
+ *   bit 1 (SENSE_VN_DEFER_JOIN): the parameter gradients of the stage (grad_params) may still be
+ *     running on the library's side streams when the call's work on the plan's stream is done;
+ *     grad_t is complete in stream order as always.  Until sense_streams_join(stream) has been
+ *     called on the stream that reads them, the caller must not read grad_params nor change ws,
+ *     x_t, grad_next or params.  A reverse pass over T stages with one workspace and one
+ *     grad_next buffer per stage can so overlap each stage's parameter gradients with the next
+ *     stage's work; the gradients are bitwise the same. */
+#define SENSE_VN_DEFER_JOIN 2
 int varnet_stage_backward_ex(sense_plan plan, const float* params, const void* AHy, const void* x_t,
                              const void* nx_t, const void* grad_next, void* grad_t, float* grad_params,
                              void* ws, size_t ws_bytes, int recompute);
+/* Make `stream` (a cudaStream_t, NULL = the legacy default stream) wait for all work issued so far
+ * on the library's side streams of the current device (see SENSE_VN_DEFER_JOIN).  Asynchronous;
+ * SENSE_ECUDA if the wait cannot be enqueued.  No counterpart in the paper. */
+int sense_streams_join(void* stream);
 
 /* Training loss of the unrolled networks: loss[0] = mean |x - gt|^2 over the
  * plan's B*S*H*W complex elements (float64, fixed-order sum) and

@@ -63,6 +63,7 @@ SIGNATURES = {
     "varnet_stage": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
     "varnet_stage_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t]),
     "varnet_stage_backward_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _i]),
+    "sense_streams_join": (_i, [_vp]),
     "sense_mse_loss": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "sense_normalize_max": (_i, [_vp, _vp, _vp, _vp]),
     "adam_update_f32": (_i, [_vp, _vp, _vp, _vp, C.c_size_t, _f, _f, _f, _f, _i, _vp]),

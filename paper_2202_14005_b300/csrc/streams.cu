@@ -32,3 +32,12 @@ int stream_after(const SideSet& ss, cudaStream_t from, cudaStream_t to) {
     return SENSE_ECUDA;
   return SENSE_OK;
 }
+
+extern "C" int sense_streams_join(void* stream) {
+  SideSet* ss = nullptr;
+  if (int e = side_set(&ss)) return e;
+  const cudaStream_t to = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < 2; ++i)
+    if (int e = stream_after(*ss, ss->s[i], to)) return e;
+  return SENSE_OK;
+}

@@ -887,8 +887,12 @@ int varnet_stage_backward_ex(sense_plan p, const float* prm, const void* AHy, co
   prof_mark("vn_misc", p->stream, false);
   k_vn_addlam<<<1, 1, 0, p->stream>>>(pdot, grad_prm);
   prof_mark("vn_misc", p->stream, true);
-  // Side streams: s0 takes the filter gradient, s1 first A^H A g and then the RBF-weight gradient;
-  // the caller's stream runs K g and the combine, and waits for both before returning.
+  // Side streams: s1 takes A^H A g; the parameter gradients run on s0 (and, when the call joins,
+  // the RBF-weight gradient on s1 after A^H A g); the caller's stream runs K g and the combine.
+  // Deferred: both gradients stay on s0, s1 holds A^H A g only, and s0 is not joined (the next
+  // stage's calls overlap it; sense_streams_join ends it).
+  const bool defer = (recompute & SENSE_VN_DEFER_JOIN) != 0;
+  recompute &= 1;
   SideSet* ss = nullptr;
   if (int e = side_set(&ss)) return e;
   const cudaStream_t s0 = ss->s[0], s1 = ss->s[1];
@@ -897,15 +901,22 @@ int varnet_stage_backward_ex(sense_plan p, const float* prm, const void* AHy, co
   // z = K x (recomputed, or kept in ws by this stage's forward together with u = Phi'(z)), kg = K g,
   // v = Phi''(z) kg; parameter gradients of -R beside the combine (they read g, x, u, v, z, kg)
   if (int e = launch_K(sh, recompute ? 2 : 3, prm, x, g, w8, L)) return e;
-  if (int e = stream_after(*ss, p->stream, s0)) return e;
-  if (int e = stream_after(*ss, p->stream, s1)) return e;
-  launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L, s0, s1);
-  // grad_t = g - K^T v - lambda A^H A g (A^H A g was issued on s1 before the RBF gradient)
-  if (int e = stream_after(*ss, s1, p->stream)) return e;
+  if (defer) {
+    if (int e = stream_after(*ss, s1, p->stream)) return e;  // A^H A g done
+    if (int e = stream_after(*ss, p->stream, s0)) return e;
+    launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L, s0, s0);
+  } else {
+    if (int e = stream_after(*ss, p->stream, s0)) return e;
+    if (int e = stream_after(*ss, p->stream, s1)) return e;
+    launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L, s0, s1);
+    if (int e = stream_after(*ss, s1, p->stream)) return e;  // A^H A g and the RBF gradient done
+  }
+  // grad_t = g - K^T v - lambda A^H A g
   if (int e = launch_KT(sh, reinterpret_cast<const bf16*>(w8 + L.v), prm, -1.f, g, n2, nullptr,
                         static_cast<float2*>(grad_t), w8, L))
     return e;
-  if (int e = stream_after(*ss, s0, p->stream)) return e;
+  if (!defer)
+    if (int e = stream_after(*ss, s0, p->stream)) return e;
   prof_count(8);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }

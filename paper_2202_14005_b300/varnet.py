@@ -52,7 +52,11 @@ class VarNetTrainer:
     """VarNet training on the library.  Each stage keeps z = K x^t and u = Phi'(z) in a workspace
     of its own (about 0.2 GB per stage for 4 slices of 320 x 368), and its reverse pass reuses them
     so that only K g is computed; with store_activations=False one workspace serves all stages and
-    the reverse pass recomputes K x^t (the checkpointing of Sec. 2.2.4).  Results are the same."""
+    the reverse pass recomputes K x^t (the checkpointing of Sec. 2.2.4).  Results are the same.
+
+    With a workspace per stage the reverse pass also keeps one gradient buffer per stage and lets
+    each stage's parameter gradients run on the library's side streams beside the next stages
+    (defer_join, joined once at the end of the pass); the gradients are bitwise the same."""
 
     def __init__(self, maps: torch.Tensor, mask: torch.Tensor, params: torch.Tensor, lr: float = 1e-4,
                  normalize: bool = False, store_activations: bool = True):
@@ -79,7 +83,10 @@ class VarNetTrainer:
         self.xs = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(self.T + 1)]
         # A^H A x^t of every stage, written by the forward pass for the reverse pass
         self.nx = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(self.T)]
-        self.g = [torch.empty((B, H, W), dtype=torch.complex64, device=dev) for _ in range(2)]
+        # gradient w.r.t. x^t for t = T .. 0; one buffer per stage when the joins are deferred
+        self.defer_join = store_activations
+        self.g = [torch.empty((B, H, W), dtype=torch.complex64, device=dev)
+                  for _ in range(self.T + 1 if store_activations else 2)]
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
         # data scaling max|x^0| = 1 per slice (Sec. 2.3.1); gtn holds the equally scaled target
         self.normalize = normalize
@@ -98,13 +105,21 @@ class VarNetTrainer:
             ws.numel()))
 
     def stage_backward(self, t: int, x_t, grad_next, grad_t, nx_t: torch.Tensor | None = None,
-                       reuse: bool = False):
+                       reuse: bool = False, defer: bool = False):
         """Reverse pass of stage t; reuse: take z and u from the stage's workspace as stage(t) left
-        them for the same x_t and parameters (else K x_t is recomputed)."""
+        them for the same x_t and parameters (else K x_t is recomputed); defer: leave the stage's
+        parameter gradients running on the side streams (join() before reading self.gp or reusing
+        the stage's workspace and buffers)."""
         ws = self._ws(t)
+        flags = (0 if reuse else 1) | (2 if defer else 0)
         _lib.check("varnet_stage_backward_ex", self._lib.varnet_stage_backward_ex(
             self.plan._h, _p(self.params[t]), _p(self.xs[0]), _p(x_t), _p(nx_t), _p(grad_next), _p(grad_t),
-            _p(self.gp[t]), _p(ws), ws.numel(), 0 if reuse else 1))
+            _p(self.gp[t]), _p(ws), ws.numel(), flags))
+
+    def join(self):
+        """The plan's stream waits for the library's side streams (deferred parameter gradients)."""
+        _lib.check("sense_streams_join", self._lib.sense_streams_join(
+            C.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
     def activations(self, t: int = 0):
         """Views of the workspace activations of the last call on stage t's workspace:
@@ -138,10 +153,17 @@ class VarNetTrainer:
         self.forward(y, gt)
         _lib.check("sense_mse_loss", self._lib.sense_mse_loss(
             self.plan._h, _p(self.xs[self.T]), _p(self.gtn), _p(self.loss), _p(self.g[0])))
-        cur = 0
-        for t in range(self.T - 1, -1, -1):
-            self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1], self.nx[t], reuse=self.store)
-            cur ^= 1
+        if self.defer_join:
+            # g[T - t] holds the gradient w.r.t. x^t: every stage reads and writes its own buffers
+            for t in range(self.T - 1, -1, -1):
+                self.stage_backward(t, self.xs[t], self.g[self.T - 1 - t], self.g[self.T - t], self.nx[t],
+                                    reuse=True, defer=True)
+            self.join()
+        else:
+            cur = 0
+            for t in range(self.T - 1, -1, -1):
+                self.stage_backward(t, self.xs[t], self.g[cur], self.g[cur ^ 1], self.nx[t], reuse=self.store)
+                cur ^= 1
         return self.loss
 
     def train_step(self, y: torch.Tensor, gt: torch.Tensor):

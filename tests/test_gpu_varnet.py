@@ -273,6 +273,27 @@ def test_stored_stage_state_matches_recompute():
     assert rel(g0, g1) <= 1e-5
 
 
+def test_deferred_parameter_gradients_bitwise_equal():
+    """Reverse pass with each stage's parameter gradients left on the library's side streams
+    (overlapping the next stages, one join at the end) against joining every stage: the same
+    kernels in the same order per gradient, so the gradients are bitwise equal."""
+    maps, mask, y, gt, AHy = problem(2, 4, 20, 136, seed=31)
+    vec, *_ = params(4, seed=32, lam=0.5, perturb=True)
+    from paper_2202_14005_b300.varnet import VarNetTrainer
+    res = []
+    for defer in (True, False):
+        tr = VarNetTrainer(dev(maps), dev(mask), dev(vec))
+        tr.defer_join = defer
+        loss = tr.gradients(dev(y), dev(gt))
+        torch.cuda.synchronize()
+        res.append((loss.item(), tr.gp.cpu().numpy().copy()))
+        assert tr.plan.status() == 0
+    (l0, g0), (l1, g1) = res
+    assert l0 == l1
+    assert np.array_equal(g0, g1)
+    assert np.count_nonzero(g0) > 0
+
+
 def test_train_step_updates_and_clears_gradients():
     maps, mask, y, gt, AHy = problem(1, 3, 16, 64, seed=2)
     vec, *_ = params(2, seed=3)
