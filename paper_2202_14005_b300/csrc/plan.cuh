@@ -82,11 +82,12 @@ struct sense_plan_s {
 // Process-wide launch accounting and per-kernel-class CUDA-event timing (profile.cu).
 void prof_count(int n);
 
-// Library-owned side streams, two per device (created on first use), for work inside one call
+// Library-owned side streams, three per device (created on first use), for work inside one call
 // that can run beside the caller's stream; events fork them from and join them back to it, so a
-// call still completes in the caller's stream order.
+// call still completes in the caller's stream order (except where a call documents otherwise).
+constexpr int kSideStreams = 3;
 struct SideSet {
-  cudaStream_t s[2];
+  cudaStream_t s[kSideStreams];
   cudaEvent_t ev;
 };
 int side_set(SideSet** out);

@@ -1,4 +1,4 @@
-// Side streams of the library (see plan.cuh): two non-blocking streams per device and one event
+// Side streams of the library (see plan.cuh): three non-blocking streams per device and one event
 // used for fork and join (each record is waited on at once, so one event serves every edge).
 #include <mutex>
 
@@ -17,7 +17,7 @@ int side_set(SideSet** out) {
   std::lock_guard<std::mutex> l(g_mu);
   SideSet& ss = g_sets[dev];
   if (!g_ready[dev]) {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < kSideStreams; ++i)
       if (cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking) != cudaSuccess) return SENSE_ECUDA;
     if (cudaEventCreateWithFlags(&ss.ev, cudaEventDisableTiming) != cudaSuccess) return SENSE_ECUDA;
     g_ready[dev] = true;
@@ -37,7 +37,7 @@ extern "C" int sense_streams_join(void* stream) {
   SideSet* ss = nullptr;
   if (int e = side_set(&ss)) return e;
   const cudaStream_t to = static_cast<cudaStream_t>(stream);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < kSideStreams; ++i)
     if (int e = stream_after(*ss, ss->s[i], to)) return e;
   return SENSE_OK;
 }

@@ -887,24 +887,25 @@ int varnet_stage_backward_ex(sense_plan p, const float* prm, const void* AHy, co
   prof_mark("vn_misc", p->stream, false);
   k_vn_addlam<<<1, 1, 0, p->stream>>>(pdot, grad_prm);
   prof_mark("vn_misc", p->stream, true);
-  // Side streams: s1 takes A^H A g; the parameter gradients run on s0 (and, when the call joins,
-  // the RBF-weight gradient on s1 after A^H A g); the caller's stream runs K g and the combine.
-  // Deferred: both gradients stay on s0, s1 holds A^H A g only, and s0 is not joined (the next
-  // stage's calls overlap it; sense_streams_join ends it).
+  // Side streams: the filter gradient runs on s0 and the RBF-weight gradient on s1; A^H A g runs
+  // on s1 before it (joined calls) or alone on s2 (deferred calls, whose gradients are not joined:
+  // the next stage's A^H A g then does not queue behind them; sense_streams_join ends them).
+  // The caller's stream runs K g and the combine.
   const bool defer = (recompute & SENSE_VN_DEFER_JOIN) != 0;
   recompute &= 1;
   SideSet* ss = nullptr;
   if (int e = side_set(&ss)) return e;
-  const cudaStream_t s0 = ss->s[0], s1 = ss->s[1];
-  if (int e = stream_after(*ss, p->stream, s1)) return e;
-  if (int e = normal0(p, g, n2, s1)) return e;
+  const cudaStream_t s0 = ss->s[0], s1 = ss->s[1], sn = defer ? ss->s[2] : ss->s[1];
+  if (int e = stream_after(*ss, p->stream, sn)) return e;
+  if (int e = normal0(p, g, n2, sn)) return e;
   // z = K x (recomputed, or kept in ws by this stage's forward together with u = Phi'(z)), kg = K g,
   // v = Phi''(z) kg; parameter gradients of -R beside the combine (they read g, x, u, v, z, kg)
   if (int e = launch_K(sh, recompute ? 2 : 3, prm, x, g, w8, L)) return e;
   if (defer) {
-    if (int e = stream_after(*ss, s1, p->stream)) return e;  // A^H A g done
+    if (int e = stream_after(*ss, sn, p->stream)) return e;  // A^H A g done
     if (int e = stream_after(*ss, p->stream, s0)) return e;
-    launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L, s0, s0);
+    if (int e = stream_after(*ss, p->stream, s1)) return e;
+    launch_param_grads(sh, x, g, -1.f, grad_prm, w8, L, s0, s1);
   } else {
     if (int e = stream_after(*ss, p->stream, s0)) return e;
     if (int e = stream_after(*ss, p->stream, s1)) return e;
