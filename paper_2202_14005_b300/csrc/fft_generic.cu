@@ -78,28 +78,43 @@ __device__ __forceinline__ void bfly(const float2* in, float2* out, int j, int N
   for (int r = 0; r < R; ++r) out[idxD + r * Ns] = v[r];
 }
 
-// Radix-R stage for the larger primes (R >= 11), one output per work item: item (j, kout) of a
-// stage whose sub-transforms have length Ns evaluates
-//   X_kout = sum_r in[j + r L/R] w^{r D},  D = (j mod Ns) L/(Ns R) + kout L/R,  w = e^{-2 pi i / L},
-// which is the stage twiddle w^{(j mod Ns) r L/(Ns R)} times the R-point kernel w^{(r kout mod R) L/R}
-// folded into one table index (r D mod L).  R times as many work items as butterflies keep all
-// threads busy on short rows, and no R-element register arrays are needed.
+// Radix-R stage for the larger primes with the stage twiddles already applied to the inputs
+// (y_r = in[j + r L/R] w^{r (j mod Ns) L/(Ns R)}): the R-point DFT over r for the output pair
+// (p, R - p) of work item j.  Inputs r and R - r enter as S_r = y_r + y_{R-r} and
+// D_r = y_r - y_{R-r}:  X_p = A -/+ i B,  X_{R-p} = A +/- i B  (forward / inverse) with
+// A = y_0 + sum_r cos(2 pi r p / R) S_r and B = sum_r sin(2 pi r p / R) D_r, r = 1 .. (R - 1)/2,
+// so each pair of outputs costs (R - 1)/2 table loads and 2 (R - 1) multiply-adds.  p = 0 gives
+// X_0 = sum_r y_r.
 template <bool INV>
-__device__ __forceinline__ void bfly_out(const float2* in, float2* out, int j, int kout, int R, int Ns, int L,
-                                         const float2* tw) {
-  const int stride = L / R;
-  const int jm = j % Ns;
-  const int D = jm * (L / (Ns * R)) + kout * stride;  // < L
-  float2 acc = in[j];
-  int idx = 0;
-  for (int r = 1; r < R; ++r) {
-    idx += D;
-    if (idx >= L) idx -= L;
-    const float2 w = __ldg(tw + idx);
-    const float2 v = in[j + r * stride];
-    acc = INV ? cfmac(w, v, acc) : cfma(v, w, acc);
+__device__ __forceinline__ void bfly_pair(const float2* in, float2* out, int j, int p, int R, int Ns, int L,
+                                          const float2* tw) {
+  const int stride = L / R, jm = j % Ns;
+  const int o0 = (j / Ns) * Ns * R + jm;  // output k goes to o0 + k Ns
+  const float2 y0 = in[j];
+  if (p == 0) {
+    float2 sum = y0;
+    for (int r = 1; r < R; ++r) sum = cadd(sum, in[j + r * stride]);
+    out[o0] = sum;
+    return;
   }
-  out[(j / Ns) * Ns * R + jm + kout * Ns] = acc;
+  float2 A = y0, Bs = make_float2(0.f, 0.f);
+  const int step = p * stride;  // angle index of r = 1 in the length-L table
+  int idx = 0;
+  for (int r = 1; r <= (R - 1) / 2; ++r) {
+    idx += step;
+    if (idx >= L) idx -= L;
+    const float2 w = __ldg(tw + idx);  // (cos t, -sin t), t = 2 pi r p / R
+    const float2 u = in[j + r * stride], v = in[j + (R - r) * stride];
+    const float2 S = cadd(u, v), D = csub(u, v);
+    A.x = fmaf(w.x, S.x, A.x);
+    A.y = fmaf(w.x, S.y, A.y);
+    Bs.x = fmaf(-w.y, D.x, Bs.x);
+    Bs.y = fmaf(-w.y, D.y, Bs.y);
+  }
+  const float2 mib = make_float2(Bs.y, -Bs.x);  // -i B
+  const float2 plus = cadd(A, mib), minus = csub(A, mib);
+  out[o0 + p * Ns] = INV ? minus : plus;
+  out[o0 + (R - p) * Ns] = INV ? plus : minus;
 }
 
 // Power-of-two lengths with the stage structure fixed at compile time: the same radix order as
@@ -147,9 +162,10 @@ __device__ __forceinline__ float2* fft_p2(float2* a, float2* b, int ntr, const f
 // passes use ld = L + 1: the transposing loads and stores of neighbouring columns then fall into
 // different shared-memory banks.  Returns the buffer holding the result.  All threads take part.
 // CLS selects the radices compiled into the stage loop: 0 = {2, 4, 8}, 1 = also {3, 5, 7},
-// 2 = also the primes 11 .. 31 (one output per work item, bfly_out).  The radix 3 - 7 butterflies
-// hold R complex values in registers; leaving them out of class 0 keeps power-of-two transforms
-// at the lowest register counts.
+// 2 = also the primes 11 .. 31 (stage twiddles applied in place, then one output pair per work
+// item, bfly_pair; a is overwritten).  The radix 3 - 7 butterflies hold R complex values in
+// registers; leaving them out of class 0 keeps power-of-two transforms at the lowest register
+// counts.
 template <bool INV, int CLS>
 __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, int ld) {
   const int L = f.L;
@@ -168,10 +184,26 @@ __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, in
     const int R = f.radix[s];
     const int nb = L / R;
     if (CLS >= 2 && R >= 11) {
-      for (int w = threadIdx.x; w < ntr * L; w += blockDim.x) {
-        const int tr = w / L, rem = w - tr * L;
-        const int kout = rem / nb, j = rem - kout * nb;
-        bfly_out<INV>(a + tr * ld, b + tr * ld, j, kout, R, Ns, L, f.tw);
+      // stage twiddles in place (element j + r L/R, j mod Ns = jm: w^{r jm L/(Ns R)}), then the
+      // R-point DFTs one output pair per work item
+      if (Ns > 1) {
+        const int tws = L / (Ns * R);
+        for (int w = threadIdx.x; w < ntr * L; w += blockDim.x) {
+          const int tr = w / L, i = w - tr * L;
+          const int r = i / nb, jm = (i - r * nb) % Ns;
+          if (r > 0 && jm > 0) {
+            float2* e = a + tr * ld + i;
+            const float2 t = __ldg(f.tw + r * jm * tws);
+            *e = INV ? cmulc(t, *e) : cmul(*e, t);
+          }
+        }
+        __syncthreads();
+      }
+      const int np = (R + 1) / 2;  // p = 0 .. (R - 1)/2
+      for (int w = threadIdx.x; w < ntr * nb * np; w += blockDim.x) {
+        const int tr = w / (nb * np), rem = w - tr * nb * np;
+        const int pp = rem / nb, j = rem - pp * nb;
+        bfly_pair<INV>(a + tr * ld, b + tr * ld, j, pp, R, Ns, L, f.tw);
       }
       __syncthreads();
       float2* t = a; a = b; b = t;
