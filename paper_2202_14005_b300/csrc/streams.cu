@@ -17,9 +17,14 @@ int side_set(SideSet** out) {
   std::lock_guard<std::mutex> l(g_mu);
   SideSet& ss = g_sets[dev];
   if (!g_ready[dev]) {
-    for (int i = 0; i < kSideStreams; ++i)
-      if (cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking) != cudaSuccess) return SENSE_ECUDA;
-    if (cudaEventCreateWithFlags(&ss.ev, cudaEventDisableTiming) != cudaSuccess) return SENSE_ECUDA;
+    int made = 0;  // streams created so far
+    while (made < kSideStreams && cudaStreamCreateWithFlags(&ss.s[made], cudaStreamNonBlocking) == cudaSuccess)
+      ++made;
+    const bool ok = made == kSideStreams && cudaEventCreateWithFlags(&ss.ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {  // release what was made; the next call tries again
+      for (int i = 0; i < made; ++i) cudaStreamDestroy(ss.s[i]);
+      return SENSE_ECUDA;
+    }
     g_ready[dev] = true;
   }
   *out = &ss;
