@@ -549,6 +549,17 @@ __global__ void __launch_bounds__(k2Threads) k_2to64(int B, int H, int W, const 
   const int ngw = (W + 15) / 16;  // groups per row
   for (int gi = warp; gi < nrows * ngw; gi += k2Threads / 32) {
     const int r = gi / ngw, w0 = (gi - r * ngw) * 16;
+    const size_t prow = ((size_t)b * H + h0 + r) * W;
+    // mode 1: this lane's four 16-byte chunks of the ReLU mask rows, loaded before the MMAs
+    uint4 mk[4];
+    if (MODE == 1) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int idx = q * 32 + lane, px = w0 + (idx >> 3);
+        mk[q] = px < W ? reinterpret_cast<const uint4*>(mask_src + (prow + px) * CH)[idx & 7]
+                       : make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
     float acc[8][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
@@ -608,7 +619,6 @@ __global__ void __launch_bounds__(k2Threads) k_2to64(int B, int H, int W, const 
     }
     __syncwarp();
     // 16 pixels x 8 chunks of 16 bytes: four chunks per lane, whole 128-byte pixel rows per 8 lanes
-    const size_t prow = ((size_t)b * H + h0 + r) * W;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = q * 32 + lane, m = idx >> 3, ch = idx & 7;
@@ -616,8 +626,7 @@ __global__ void __launch_bounds__(k2Threads) k_2to64(int B, int H, int W, const 
       if (px < W) {
         uint4 v = *reinterpret_cast<const uint4*>(so + m * k2Ld + ch * 8);
         if (MODE == 1) {
-          const uint4 mk = reinterpret_cast<const uint4*>(mask_src + (prow + px) * CH)[ch];
-          const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+          const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk[q]);
           __nv_bfloat16* vb = reinterpret_cast<__nv_bfloat16*>(&v);
 #pragma unroll
           for (int e = 0; e < 8; ++e)
