@@ -396,18 +396,20 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
     bool fail = false;
     for (int i = 0; i < n; ++i) {
       const int t = i & 1;
-      if (!fail) {
-        const bool ok_wait = mbar_wait(&tm_full[t], (i >> 1) & 1);
-        if (!ok_wait && lane == 0) atomicExch(s_err, 1);
-        fail = __any_sync(0xffffffffu, !ok_wait);
-      }
-      tc_fence_after();
       int b, h, wt;
       tile_coords(blockIdx.x + i * gridDim.x, a.H, a.ntw, b, h, wt);
       const int p = warp * 32 + lane;
       const int px = wt * CL::TILE_OUT + p;
       const bool valid = p < CL::TILE_OUT && px < a.W;
       const size_t pix = ((size_t)b * a.H + h) * a.W + px;
+      // the residual term of this pixel, loaded before the wait for the tile's accumulators
+      const float2 rv = valid ? a.res[pix] : make_float2(0.f, 0.f);
+      if (!fail) {
+        const bool ok_wait = mbar_wait(&tm_full[t], (i >> 1) & 1);
+        if (!ok_wait && lane == 0) atomicExch(s_err, 1);
+        fail = __any_sync(0xffffffffu, !ok_wait);
+      }
+      tc_fence_after();
       float* xw = xch_base + (size_t)(t * 4 + warp) * 4 * CO;             // this warp's rows
       const float* xn = xch_base + (size_t)(t * 4 + warp + 1) * 4 * CO;   // the next warp's rows
       const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + t * CL::TCOL;
@@ -429,15 +431,11 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
         }
         if (lane >= 30) xw[(2 + lane - 30) * CO + c] = o[c];
       }
-      if (lane < 30 && valid) {
-        const float2 rv = a.res[pix];
-        a.out2[pix] = make_float2(rv.x + s_bias[0] + o[0], rv.y + s_bias[1] + o[1]);
-      }
+      if (lane < 30 && valid) a.out2[pix] = make_float2(rv.x + s_bias[0] + o[0], rv.y + s_bias[1] + o[1]);
       epi_bar();
       if (lane >= 30 && warp < 3 && valid) {
         const float* part = xw + (2 + lane - 30) * CO;
         const float* add = xn + (lane == 31 ? 0 : 1) * CO;
-        const float2 rv = a.res[pix];
         a.out2[pix] = make_float2(rv.x + s_bias[0] + (part[0] + add[0]), rv.y + s_bias[1] + (part[1] + add[1]));
       }
     }
