@@ -350,23 +350,24 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
     // epilogue (NOUT = 64): warp w owns pixels 32w .. 32w + 31 of each tile
     for (int i = 0; i < n; ++i) {
       const int t = i & 1;
-      if (!mbar_wait(&tm_full[t], (i >> 1) & 1)) {
-        atomicExch(s_err, 1);
-        break;
-      }
-      tc_fence_after();
       int b, h, wt;
       tile_coords(blockIdx.x + i * gridDim.x, a.H, a.ntw, b, h, wt);
       const int px = wt * CL::TILE_OUT + warp * 32 + lane;
       const bool valid = px < a.W;
       const size_t pix = ((size_t)b * a.H + h) * a.W + px;
-      // input-gradient mode: the whole 128-byte ReLU-mask row of this pixel in one batch of loads
+      // input-gradient mode: the whole 128-byte ReLU-mask row of this pixel in one batch of loads,
+      // issued before the wait for the tile's accumulators
       uint4 mrow[8];
       if (a.mode == 1 && valid) {
         const uint4* ap = reinterpret_cast<const uint4*>(a.aprev + pix * CH);
 #pragma unroll
         for (int q = 0; q < 8; ++q) mrow[q] = ap[q];
       }
+      if (!mbar_wait(&tm_full[t], (i >> 1) & 1)) {
+        atomicExch(s_err, 1);
+        break;
+      }
+      tc_fence_after();
       float acc[64];
       tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + t * CL::TCOL, acc);
       // the accumulators are in registers: hand the TMEM half back to the producer
