@@ -47,7 +47,7 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
 # vn_* one launch each of the 4-slice 320x368 VarNet step.
 NCU_TRAFFIC = {
     "cg_sense": {"normal_lines": 110.3e6, "cg_lines": 1.511e9},
-    "modl_train": {"cg_lines": 24.8e6, "conv64_tc": 30.55e6, "wgrad64": 62.9e6},
+    "modl_train": {"cg_lines": 24.8e6, "conv64_tc": 30.54e6, "wgrad64": 62.9e6},
     "varnet_train": {"vn_K": 23.87e6, "vn_Kbwd": 76.16e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
 }
 # what the reverse pass reuses from the forward pass of each training workload
