@@ -489,17 +489,18 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
 //   beta_{k-1} = gamma_k / gamma_{k-1},  alpha_k = gamma_k / (delta_k - beta_{k-1} gamma_k / alpha_{k-1})
 // (alpha_0 = gamma_0 / delta_0), using the orthogonality of the residuals.  Pass k (k < iters):
 // staging p, s, x, r of iteration k - 1 (k >= 1), w = S r through the fused operator, row
-// partials of delta and gamma, grid barrier.  A last pass makes the update of iteration
+// partials of delta and gamma, barrier of the slice.  A last pass makes the update of iteration
 // iters - 1 and gamma for the residual history.  Each CTA keeps the same row tiles throughout,
 // so only the row partials and the per-slice scalars cross CTAs.
 //
-// Grid barrier: an arrival count that only grows within the launch (barrier n completes at
-// (n + 1) x gridDim.x arrivals) and a release word.  The CTA that arrives last reduces the row
-// partials of every slice in fixed order, publishes alpha and beta (and its copies of gamma and
-// alpha for the next pass), then releases the others, which read the two scalars of their
-// slices.  One CTA reads the partials instead of every CTA reading all of them at once.  The
-// launch is cooperative (all CTAs resident) and every wait is bounded: a CTA that gives up sets
-// SENSE_STATUS_DEVICE_TIMEOUT and returns.
+// Barriers: the CTAs form one group per slice, and each group has an arrival count that only
+// grows within the launch (barrier n completes at (n + 1) x group-size arrivals) and a release
+// word.  The CTA that arrives last reduces the slice's row partials in fixed order, publishes
+// alpha and beta (and its copies of gamma and alpha for the next pass), then releases the
+// others, which read the two scalars.  One CTA reads the partials instead of every CTA reading
+// them at once, and the slices do not wait for each other.  The launch is cooperative (all CTAs
+// resident) and every wait is bounded: a CTA that gives up sets SENSE_STATUS_DEVICE_TIMEOUT and
+// returns.
 constexpr int kCoopMaxB = 16;  // slices per solve on this path
 
 struct CgCoop {
