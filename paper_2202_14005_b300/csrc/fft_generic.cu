@@ -129,12 +129,22 @@ __device__ __forceinline__ void bfly_p2(const float2* in, float2* out, int j, co
   for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
   const int k = j & (NS - 1);
   if constexpr (NS > 1) {
-    const int step = k * (L / (NS * R));
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      const float2 w = __ldg(tw + step * r);
-      v[r] = INV ? cmulc(w, v[r]) : cmul(v[r], w);
+    // one table load per butterfly: w^r for r >= 2 as products of w (at most three deep), so the
+    // twiddle loads do not saturate the L1 pipe (rounding of w^r stays within a few ulp)
+    float2 w[R];
+    w[1] = __ldg(tw + k * (L / (NS * R)));
+    if constexpr (R >= 4) {
+      w[2] = cmul(w[1], w[1]);
+      w[3] = cmul(w[2], w[1]);
     }
+    if constexpr (R == 8) {
+      w[4] = cmul(w[2], w[2]);
+      w[5] = cmul(w[4], w[1]);
+      w[6] = cmul(w[4], w[2]);
+      w[7] = cmul(w[4], w[3]);
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = INV ? cmulc(w[r], v[r]) : cmul(v[r], w[r]);
   }
   dft_pow2<R, INV>(v);
   const int idxD = (j / NS) * NS * R + k;
