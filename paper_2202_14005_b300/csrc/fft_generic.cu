@@ -65,10 +65,12 @@ __device__ __forceinline__ void bfly(const float2* in, float2* out, int j, int N
   for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
   const int k = j % Ns;
   if (Ns > 1) {
-    const int step = k * (L / (Ns * R));
+    // one table load per butterfly; w^r = w^(r-1) w (rounding stays within a few ulp for R <= 8)
+    const float2 w1 = __ldg(tw + k * (L / (Ns * R)));
+    float2 w = w1;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      const float2 w = __ldg(tw + step * r);
+      if (r > 1) w = cmul(w, w1);
       v[r] = INV ? cmulc(w, v[r]) : cmul(v[r], w);
     }
   }
