@@ -123,12 +123,23 @@ __device__ __forceinline__ void bfly_pair(const float2* in, float2* out, int j, 
 // the generic plan (radix 8 while it divides, then one radix 4 or 2 stage), the same twiddles
 // and butterflies, with every stride, mask and shift a constant (no per-butterfly divisions or
 // radix dispatch).
+// Intermediate results between two stages are stored with the index swizzled inside blocks of
+// 16 (i ^ ((i >> 4) & 7)): the first stage writes each work item's R outputs R elements apart,
+// which in natural order puts 16 lanes on two 8-byte bank slots; swizzled they take 16.  Reads of
+// 16 consecutive elements stay conflict-free.  Input and final output are in natural order.
+template <int L>
+__device__ __forceinline__ int p2_swz(int i) {
+  return L >= 16 ? (i ^ ((i >> 4) & 7)) : i;
+}
+
 template <int R, bool INV, int NS, int L>
 __device__ __forceinline__ void bfly_p2(const float2* in, float2* out, int j, const float2* tw) {
   constexpr int stride = L / R;
+  constexpr bool SWZ_IN = NS > 1;       // written by an earlier stage
+  constexpr bool SWZ_OUT = NS * R < L;  // read by a later stage
   float2 v[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
+  for (int r = 0; r < R; ++r) v[r] = in[SWZ_IN ? p2_swz<L>(j + r * stride) : j + r * stride];
   const int k = j & (NS - 1);
   if constexpr (NS > 1) {
     // one table load per butterfly: w^r for r >= 2 as products of w (at most three deep), so the
@@ -151,7 +162,7 @@ __device__ __forceinline__ void bfly_p2(const float2* in, float2* out, int j, co
   dft_pow2<R, INV>(v);
   const int idxD = (j / NS) * NS * R + k;
 #pragma unroll
-  for (int r = 0; r < R; ++r) out[idxD + r * NS] = v[r];
+  for (int r = 0; r < R; ++r) out[SWZ_OUT ? p2_swz<L>(idxD + r * NS) : idxD + r * NS] = v[r];
 }
 
 template <bool INV, int L, int NS>
