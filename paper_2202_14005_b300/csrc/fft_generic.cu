@@ -527,7 +527,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_tp_cols(int H, int W2, float2* 
 
 // With cpg < C, CTA z sums coils z cpg .. z cpg + cpg - 1 and writes that partial sum over the
 // first W entries of the rows of coil z cpg it has just read; k_coil_groups_sum (row stride 2W)
-// adds the groups in fixed order and + lambda x.
+// adds the groups in fixed order and + lambda x.  The rows of the next coil are copied into a
+// third shared buffer (cp.async) while the current coil is transformed.
+__device__ __forceinline__ void tp_cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void tp_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tp_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+int smem_rows_inv(int W2) { return 3 * kRows * W2 * (int)sizeof(float2); }
 template <int CLS>
 __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W, float2* T,
                                                           const float2* maps, float2* out, Fft1DDev f,
@@ -535,20 +543,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
                                                           const double* lam_dev, int cpg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W2 = f.L;
-  float2* a = reinterpret_cast<float2*>(smem);
-  float2* bb = a + kRows * W2;
+  float2* const base = reinterpret_cast<float2*>(smem);  // three buffers of kRows x W2
+  const int bstride = kRows * W2;
   const int b = blockIdx.y;
   const int h0 = blockIdx.x * kRows;
   const int nr = min(kRows, H - h0);
   const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
+  const int n16 = nr * W2 / 2;  // 16-byte chunks of one coil's rows (W2 even)
+  auto fetch = [&](int c, float2* dst) {
+    const float2* src = T + (((size_t)b * C + c) * H + h0) * W2;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) tp_cp_async16(dst + 2 * i, src + 2 * i);
+    tp_cp_async_commit();
+  };
   float2 acc[kMaxPer];
 #pragma unroll
   for (int e = 0; e < kMaxPer; ++e) acc[e] = make_float2(0.f, 0.f);
+  int ip = 0, is = 1, iq = 2;  // prefetched input, FFT scratch, next prefetch
+  fetch(c0, base + ip * bstride);
   for (int c = c0; c < c1; ++c) {
-    for (int i = threadIdx.x; i < nr * W2; i += blockDim.x)
-      a[i] = T[(((size_t)b * C + c) * H + h0) * W2 + i];
+    tp_cp_async_wait_all();
     __syncthreads();
-    float2* res = fft_smem<true, CLS>(a, bb, nr, f, W2);
+    if (c + 1 < c1) fetch(c + 1, base + iq * bstride);
+    float2* res = fft_smem<true, CLS>(base + ip * bstride, base + is * bstride, nr, f, W2);
 #pragma unroll
     for (int e = 0; e < kMaxPer; ++e) {
       const int i = threadIdx.x + e * blockDim.x;  // output element (row r, column w < W)
@@ -559,6 +575,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
       }
     }
     __syncthreads();
+    const int t = ip;
+    ip = iq;
+    iq = t;
   }
   if (cpg < C) {  // partial sum of this coil group over the rows of coil c0 (already read)
 #pragma unroll
@@ -826,7 +845,7 @@ int toeplitz_prepare(sense_plan p, const float2* psf) {
   if (kRows * W2 > kThreads * kMaxPer || kRows * p->W > kThreads * kMaxPer) return SENSE_EUNSUPPORTED;
   const int sr = smem_rows(W2), sc = smem_cols(H2);
   if (sr > 200 * 1024 || sc > 200 * 1024) return SENSE_EUNSUPPORTED;
-  if (!SENSE_SET_SMEM(k_tp_rows_fwd, sr) || !SENSE_SET_SMEM(k_tp_rows_inv, sr) ||
+  if (!SENSE_SET_SMEM(k_tp_rows_fwd, sr) || !SENSE_SET_SMEM(k_tp_rows_inv, smem_rows_inv(W2)) ||
       !SENSE_SET_SMEM(k_tp_psf_rows, sr) || !SENSE_SET_SMEM(k_tp_cols, sc) || !SENSE_SET_SMEM(k_tp_psf_cols, sc))
     return SENSE_ECUDA;
   SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_psf_rows, (H2 + kRows - 1) / kRows, sr, p->stream, H2, psf,
@@ -853,7 +872,7 @@ int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam
   const int cpg = (p->C + groups - 1) / groups;
   groups = (p->C + cpg - 1) / cpg;
   const dim3 gr2(nrb, p->B, groups);
-  SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows(W2), p->stream, p->C, p->H, p->W, p->w.T,
+  SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows_inv(W2), p->stream, p->C, p->H, p->W, p->w.T,
                    p->maps, out, dev(p->fW2), x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
   if (groups > 1) {
     const long long n = (long long)p->B * p->H * p->W;
