@@ -363,13 +363,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_col(int W, const float2* src, f
   }
 }
 
+// 16-byte asynchronous global -> shared copies: the inverse row passes copy the next coil's rows
+// into a third shared buffer while the current coil is transformed (smem_rows_inv bytes).
+__device__ __forceinline__ void tp_cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void tp_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tp_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+int smem_rows_inv(int W2) { return 3 * kRows * W2 * (int)sizeof(float2); }
+
 // Row pass with coil combination:
 //   out[b,h,:] = sum_c conj(S_c) post(IDFT_W(pre(T[b,c,h,:]))) (+ lambda xin)
 //   mode 1 (adjoint): pre (-1)^{kw}, post (-1)^w (-1)^{W/2}/sqrt(W)
 //   mode 2 (normal):  no modulation, no scale (the scale sits in the mask table)
 // With cpg < C (one map set only), CTA z sums coils z cpg .. z cpg + cpg - 1 and writes that
 // partial sum over the rows of coil z cpg it has just read (no other CTA reads them);
-// k_coil_groups_sum then adds the groups in fixed order.
+// k_coil_groups_sum then adds the groups in fixed order.  The next coil's rows are copied in
+// while the current one is transformed.
 template <int CLS>
 __global__ void __launch_bounds__(kThreads, 2) k_row_combine(int S, int C, int H, float2* T,
                                                           const float2* maps, float2* out,
@@ -378,25 +389,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_combine(int S, int C, int H
                                                           const double* lam_dev, int cpg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = f.L;
-  float2* a = reinterpret_cast<float2*>(smem);
-  float2* bb = a + kRows * W;
+  float2* const base = reinterpret_cast<float2*>(smem);  // three buffers of kRows x W
+  const int bstride = kRows * W;
   const int b = blockIdx.y / S, s = blockIdx.y - b * S;  // output set s of slice b
   const int h0 = blockIdx.x * kRows;
   const int nr = min(kRows, H - h0);
   const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
+  const int n16 = nr * W / 2;  // 16-byte chunks of one coil's rows (W even)
+  auto fetch = [&](int c, float2* dst) {
+    const float2* src = T + (((size_t)b * C + c) * H + h0) * W;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) tp_cp_async16(dst + 2 * i, src + 2 * i);
+    tp_cp_async_commit();
+  };
   float2 acc[kMaxPer];
 #pragma unroll
   for (int e = 0; e < kMaxPer; ++e) acc[e] = make_float2(0.f, 0.f);
   const float sc = pm1(W / 2) * rsqrtf((float)W);
+  int ip = 0, is = 1, iq = 2;  // prefetched input, FFT scratch, next prefetch
+  fetch(c0, base + ip * bstride);
   for (int c = c0; c < c1; ++c) {
-    for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
-      const int r = i / W, k = i - r * W;
-      float2 v = T[(((size_t)b * C + c) * H + h0 + r) * W + k];
-      if (mode == 1) v = cscale(v, pm1(k));
-      a[i] = v;
-    }
+    float2* a = base + ip * bstride;
+    tp_cp_async_wait_all();
     __syncthreads();
-    float2* res = fft_smem<true, CLS>(a, bb, nr, f, W);
+    if (c + 1 < c1) fetch(c + 1, base + iq * bstride);
+    if (mode == 1) {  // (-1)^k on the input (each thread its own copied chunks)
+      for (int i = threadIdx.x; i < n16; i += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int k = (2 * i + q) % W;
+          a[2 * i + q] = cscale(a[2 * i + q], pm1(k));
+        }
+      __syncthreads();
+    }
+    float2* res = fft_smem<true, CLS>(a, base + is * bstride, nr, f, W);
 #pragma unroll
     for (int e = 0; e < kMaxPer; ++e) {
       const int i = threadIdx.x + e * blockDim.x;
@@ -409,6 +434,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_combine(int S, int C, int H
       }
     }
     __syncthreads();
+    const int t = ip;
+    ip = iq;
+    iq = t;
   }
   if (cpg < C) {  // partial sum of this coil group
     float2* dst = T + (((size_t)b * C + c0) * H + h0) * W;
@@ -529,13 +557,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_tp_cols(int H, int W2, float2* 
 // first W entries of the rows of coil z cpg it has just read; k_coil_groups_sum (row stride 2W)
 // adds the groups in fixed order and + lambda x.  The rows of the next coil are copied into a
 // third shared buffer (cp.async) while the current coil is transformed.
-__device__ __forceinline__ void tp_cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void tp_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void tp_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-int smem_rows_inv(int W2) { return 3 * kRows * W2 * (int)sizeof(float2); }
 template <int CLS>
 __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W, float2* T,
                                                           const float2* maps, float2* out, Fft1DDev f,
@@ -751,7 +772,8 @@ int generic_prepare(sense_plan p) {
   if (kRows * p->W > kThreads * kMaxPer) return SENSE_EUNSUPPORTED;
   const int sr = smem_rows(p->W), sc = smem_cols(p->H);
   if (sr > 200 * 1024 || sc > 200 * 1024) return SENSE_EUNSUPPORTED;
-  if (!SENSE_SET_SMEM(k_row_expand, sr) || !SENSE_SET_SMEM(k_row_combine, sr) || !SENSE_SET_SMEM(k_col, sc))
+  if (!SENSE_SET_SMEM(k_row_expand, sr) || !SENSE_SET_SMEM(k_row_combine, smem_rows_inv(p->W)) ||
+      !SENSE_SET_SMEM(k_col, sc))
     return SENSE_ECUDA;
   return SENSE_OK;
 }
@@ -771,7 +793,7 @@ int launch_row_combine(sense_plan p, float2* out, int mode, const float2* xin, f
   groups = (p->C + cpg - 1) / cpg;
   const dim3 gr(nrb, p->B * p->S, groups);
   prof_mark("fft_generic", p->stream, false);
-  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_combine, gr, smem_rows(p->W), p->stream, p->S, p->C, p->H, p->w.T,
+  SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_combine, gr, smem_rows_inv(p->W), p->stream, p->S, p->C, p->H, p->w.T,
                    p->maps, out, dev(p->fW), mode, xin, lam_host, lam_dev, groups > 1 ? cpg : p->C);
   if (groups > 1) {
     const int HW = p->H * p->W;
