@@ -23,7 +23,12 @@
  *     the maps and mask pointers it was created with (no copy): the caller
  *     keeps them alive and unchanged for the plan's lifetime.
  *   - Calls are asynchronous on the plan's CUDA stream; results are ready
- *     when that stream reaches them.  A plan is not thread-safe.
+ *     when that stream reaches them.  A plan is not thread-safe.  Some calls
+ *     (the MoDL denoiser backward, the VarNet stages) also run independent
+ *     parts on three side streams the library creates per device on first
+ *     use, forked from and joined back to the caller's stream with events, so
+ *     their results are still ready in the caller's stream order (except where
+ *     SENSE_VN_DEFER_JOIN says otherwise).
  *   - Return value: SENSE_OK (0) or a negative SENSE_E* code; host-side
  *     argument checks run before any launch, so an error leaves outputs
  *     untouched.  Device-side failures (CG breakdown, non-finite scalars) set
