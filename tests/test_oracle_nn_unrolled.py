@@ -212,3 +212,150 @@ def test_bf16_round_ties_to_even_and_limits():
     r = onn.bf16_round(a)
     assert np.all(np.abs(r - a) <= np.abs(a) * 2.0 ** -8 * (1 + 1e-6))
     assert onn.bf16_round(np.float32(one)) == 1.0
+
+
+# --------------------------------------------------------------------------
+# Independent pins of the unrolled blocks.  The finite-difference tests above
+# compare the oracle's reverse mode with its own forward, so a misreading of
+# Eq. 6 or Eq. 5 made consistently in both would pass them.  The tests below
+# check the forward blocks against the equations themselves, built only from
+# the separately pinned pieces (the normal operator, the forward operator, the
+# CNN and a closed-form RBF potential).
+
+def _dense_normal(maps, mask, lam, H, W):
+    """Explicit matrix of (A^H A + lam I) for one slice, column by column."""
+    from oracle import sense as osense
+    n = H * W
+    M = np.zeros((n, n), dtype=np.complex128)
+    for j in range(n):
+        e = np.zeros((1, H, W), dtype=np.complex128)
+        e.flat[j] = 1.0
+        M[:, j] = osense.normal(e, maps, mask, lam).reshape(-1)
+    return M
+
+
+@pytest.mark.parametrize("H,W", [(8, 8), (12, 10)])
+def test_modl_block_solves_eq6(H, W):
+    """x^{t+1} solves (A^H A + lam I) x = A^H y + lam D_W(x^t) (Eq. 6).
+
+    With converged CG (40 iterations; the condition number is at most
+    (1 + lam) / lam = 6) the block's residual against that system, formed with the
+    pinned normal operator and the pinned CNN, vanishes; a dense direct solve of
+    the same system gives the same point, and T blocks chain from x^0 = A^H y.
+    """
+    from oracle import sense as osense
+    maps, mask, AHy, _ = _small_problem(H=H, W=W, seed=31 + H)
+    ws, bs = synth.modl_cnn_weights(9, chans=(2, 4, 2))
+    bs = [np.full(b.shape, 0.03) for b in bs]
+    lam = 0.2
+    x_t = synth.randn_complex((1, H, W), 77) * 0.5
+    x1, z = ounr.modl_block(x_t, AHy, maps, mask, ws, bs, lam, 40)
+    np.testing.assert_allclose(z, onn.modl_cnn_forward(x_t, ws, bs)[0], rtol=0, atol=1e-14)
+    rhs = AHy + lam * onn.modl_cnn_forward(x_t, ws, bs)[0]
+    res = osense.normal(x1, maps, mask, lam) - rhs
+    assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(rhs)
+    # dense solve of the explicit system, and the two-block chain from A^H y
+    Nl = _dense_normal(maps, mask, lam, H, W)
+    xs_ref = [AHy]
+    for _ in range(2):
+        r = AHy + lam * onn.modl_cnn_forward(xs_ref[-1], ws, bs)[0]
+        xs_ref.append(np.linalg.solve(Nl, r.reshape(-1)).reshape(1, H, W))
+    xT, xs = ounr.modl_forward(AHy, maps, mask, ws, bs, lam, 2, 40)
+    np.testing.assert_allclose(xs[0], AHy, rtol=0, atol=0)
+    for a, b in zip(xs, xs_ref):
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def _rbf_potential(z, wts, Nw=31):
+    """Phi_i(z) = sum_j w_ij * integral of exp(-(s - mu_j)^2 / (2 sigma^2)) ds,
+    i.e. sum_j w_ij sigma sqrt(pi/2) erf((z - mu_j) / (sigma sqrt 2)): the
+    antiderivative of the Gaussian RBF activation, in closed form."""
+    from scipy.special import erf
+    mu = -1.0 + 2.0 * np.arange(Nw) / (Nw - 1)
+    s = 2.0 / (Nw - 1)
+    e = s * np.sqrt(np.pi / 2) * erf((z[..., None] - mu) / (s * np.sqrt(2.0)))
+    return np.einsum("bkhwj,kj->bkhw", e, wts)
+
+
+def _brute_real_conv(xr, wr):
+    """z[b,i,y,x] = sum_{c,dy,dx} wr[i,c,dy,dx] xr[b,c,y+dy-p,x+dx-p], by loops (zero padded)."""
+    B, Ci, H, W = xr.shape
+    Nk, _, k, _ = wr.shape
+    p = k // 2
+    z = np.zeros((B, Nk, H, W))
+    for b in range(B):
+        for i in range(Nk):
+            for yy in range(H):
+                for xx in range(W):
+                    s = 0.0
+                    for c in range(Ci):
+                        for dy in range(k):
+                            for dx in range(k):
+                                sy, sx = yy + dy - p, xx + dx - p
+                                if 0 <= sy < H and 0 <= sx < W:
+                                    s += wr[i, c, dy, dx] * xr[b, c, sy, sx]
+                    z[b, i, yy, xx] = s
+    return z
+
+
+def test_varnet_stage_regulariser_is_gradient_of_rbf_potential():
+    """With lam_t = 0, x^t - x^{t+1} = sum_i K_i^T Phi_i'(K_i x^t) (Eq. 5) is the
+    gradient of R(x) = sum_i sum_pixels Phi_i(Re(k_i * x)), Phi_i the closed-form
+    potential whose derivative is the RBF sum.  The gradient is taken by central
+    differences in the real and imaginary part of single pixels (Sec. 2.2.2)."""
+    maps, mask, AHy, _ = _small_problem(H=7, W=6, seed=41)
+    rng = np.random.default_rng(42)
+    Nk, k = 3, 3
+    filt = (rng.standard_normal((Nk, k, k)) + 1j * rng.standard_normal((Nk, k, k))) * 0.3
+    wts = rng.standard_normal((Nk, 31)) * 0.2
+    x = synth.randn_complex((1, 7, 6), 43) * 0.4
+
+    def R(xx):
+        xr = np.stack([xx.real, xx.imag], axis=1)
+        # Re(k_i * x) = Re k_i * x_re - Im k_i * x_im, by brute-force loops
+        wr = np.stack([filt.real, -filt.imag], axis=1)
+        return float(np.sum(_rbf_potential(_brute_real_conv(xr, wr), wts)))
+
+    x1 = ounr.varnet_stage(x, AHy, maps, mask, filt, wts, 0.0)
+    grad = x - x1
+    eps = 1e-6
+    for idx in [(0, 0, 0), (0, 3, 2), (0, 6, 5), (0, 2, 4)]:
+        for unit, part in ((1.0, np.real), (1j, np.imag)):
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += unit * eps
+            xm[idx] -= unit * eps
+            fd = (R(xp) - R(xm)) / (2 * eps)
+            assert abs(fd - part(grad[idx])) <= 1e-7 * max(1.0, abs(fd)), (idx, fd, grad[idx])
+
+
+def test_varnet_stage_data_term_is_gradient_step():
+    """With all filters zero, a stage is x - lam_t grad(1/2 ||A x - y||^2) (Eq. 5),
+    the gradient taken by central differences of the pinned forward operator."""
+    from oracle import sense as osense
+    H, W = 8, 6
+    maps, mask, _, _ = _small_problem(H=H, W=W, C=3, seed=51)
+    y = osense.forward(synth.randn_complex((1, H, W), 52), maps, mask)
+    AHy = osense.adjoint(y, maps, mask)
+    filt = np.zeros((2, 3, 3), dtype=np.complex128)
+    wts = np.random.default_rng(53).standard_normal((2, 31))
+    x = synth.randn_complex((1, H, W), 54) * 0.7
+    lam_t = 0.37
+    x1 = ounr.varnet_stage(x, AHy, maps, mask, filt, wts, lam_t)
+
+    def f(xx):
+        return 0.5 * float(np.sum(np.abs(osense.forward(xx, maps, mask) - y) ** 2))
+
+    eps = 1e-6
+    for idx in [(0, 0, 0), (0, 4, 3), (0, 7, 5), (0, 1, 2)]:
+        for unit, part in ((1.0, np.real), (1j, np.imag)):
+            xp, xm = x.copy(), x.copy()
+            xp[idx] += unit * eps
+            xm[idx] -= unit * eps
+            fd = (f(xp) - f(xm)) / (2 * eps)
+            want = part(x[idx]) - lam_t * fd
+            assert abs(part(x1[idx]) - want) <= 1e-8, (idx, part(x1[idx]), want)
+    # the chain starts from x^0 = A^H y
+    _, xs = ounr.varnet_forward(AHy, maps, mask, filt[None], wts[None], np.array([lam_t]))
+    np.testing.assert_array_equal(xs[0], AHy)
+    np.testing.assert_allclose(xs[1], ounr.varnet_stage(AHy, AHy, maps, mask, filt, wts, lam_t),
+                               rtol=0, atol=0)
