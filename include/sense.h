@@ -354,10 +354,13 @@ int adam_update_f64(double* param, double* grad, double* m, double* v, size_t n,
  * process exits).  It takes B * H <= SENSE_NOALLOC_MAX_ROWS; larger problems
  * get SENSE_ETOO_LARGE before anything runs.  The first call on each device
  * looks up the array's device address (with that device current), so make
- * that first call before any stream capture.  Every call shares the array:
- * calls that overlap on the GPU (other streams, other host threads) race and
- * give wrong results — serialise them.  Results equal those of the
- * workspace path bit for bit (same order of summation). */
+ * that first call before any stream capture.  Later calls on a stream that is
+ * not being captured look it up again, so an address that moved after
+ * cudaDeviceReset is picked up.  Every call shares the array: calls that
+ * overlap on the GPU (other streams, other host threads) race and give wrong
+ * results — serialise them.  The rows are split and summed exactly as in the
+ * workspace kernel of cg_dc_solve_backward (two warps per row, FP64 warp sums,
+ * fixed-order slice sums), so the results equal that path's bit for bit. */
 #define SENSE_NOALLOC_SCRATCH_BYTES (1u << 20)
 #define SENSE_NOALLOC_MAX_ROWS ((SENSE_NOALLOC_SCRATCH_BYTES - 256u) / 8u)
 int sense_dot_re_noalloc(int B, int H, int W, const void* a, const void* b_, const void* c,
