@@ -162,10 +162,27 @@ int sense_profile_enable(int enable);
 int sense_profile_read(const char* name, double* ms, int* launches);
 /* Kernels launched so far (reset to zero if reset != 0). */
 long long sense_kernel_launches(int reset);
+/* Measurement aid (no counterpart in the paper): a register-only FP32 FMA kernel of `blocks`
+ * blocks of 256 threads, each thread running 8 independent chains of `iters` FMAs
+ * (2 * 8 * 256 * iters FLOP per block), for timing the FP32 pipe's peak with CUDA events on
+ * `stream`.  sink: device float32 [blocks] (written only in a practically unreachable case). */
+int sense_fma_probe(int blocks, int iters, float* sink, void* stream);
 
 /* Synchronises the plan's stream, returns the OR of device status bits set
  * since the last call, and clears them. */
 int sense_get_status(sense_plan plan, int* device_status);
+
+/* Failure detection (no counterpart in the paper): the bounded waits of the
+ * one-launch CG.  Each CTA of that kernel waits at one barrier per CG pass
+ * for the other CTAs of its slice, polling a release word at most `polls`
+ * times (0 restores the default, 2^22 polls of about 32 ns plus the load);
+ * a CTA that gives up sets SENSE_STATUS_DEVICE_TIMEOUT, skips the rest of the
+ * solve and returns, so the kernel always ends and the context stays usable.
+ * unreachable = 1 makes every barrier expect one arrival that never comes, so
+ * every wait runs out (this exists to test the timeout path; the solve's
+ * result is then undefined); 0 is normal operation.  Host-side only; applies
+ * to later calls of this plan.  Errors: SENSE_EINVAL_PTR, SENSE_EINVAL_ARG. */
+int sense_plan_set_wait_limit(sense_plan plan, unsigned polls, int unreachable);
 
 /* ------------------------------------------------------------------------
  * Learned denoisers.  SENSE_DENOISER_MODL: the MoDL residual CNN
@@ -333,6 +350,22 @@ int adam_update_f32(float* param, float* grad, float* m, float* v, size_t n, flo
                     float beta2, float eps, int step, void* stream);
 int adam_update_f64(double* param, double* grad, double* m, double* v, size_t n, double lr,
                     double beta1, double beta2, double eps, int step, double lower, void* stream);
+
+/* iPALM update of VarNet stage parameters (Sec. 2.3.1: the VarNet is trained with iPALM,
+ * the inertial proximal alternating linearised minimisation of Pock and Sabach).  The paper
+ * names neither the constraints nor the inertia; this call takes the variational-network
+ * constraints (each complex filter zero-mean over its taps with Euclidean norm <= 1,
+ * lambda_t >= 0, RBF weights free) and alpha = beta.  Update k of T stages in the layout of
+ * varnet_stage (T * 6,553 float32 values each):
+ *   on entry  params = z^k (the point where grad was taken), x = x^k;
+ *   on exit   x = x^{k+1} = P(z^k - tau grad) blockwise (tau_filters, tau_rbf, tau_lambda),
+ *             params = z^{k+1} = x^{k+1} + alpha_next (x^{k+1} - x^k),
+ *             grad = 0 (ready to accumulate the next step).
+ * Start with x = params (x^0 = z^1); the usual inertia is alpha_next = k / (k + 3).
+ * params, grad and x must not alias.  Asynchronous on stream.  Errors: SENSE_EINVAL_PTR,
+ * SENSE_EINVAL_ARG (T <= 0, negative or non-finite step sizes, alpha_next outside [0, 1)). */
+int ipalm_update_varnet(float* params, float* grad, float* x, int T, float tau_filters,
+                        float tau_rbf, float tau_lambda, float alpha_next, void* stream);
 
 /* Allocation-free variant of the inner product behind the lambda gradient of
  * cg_dc_solve_backward.  The paper has no counterpart; it exists for callers

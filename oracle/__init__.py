@@ -18,6 +18,8 @@ implementation of what the paper defines, each citing the passage it follows
                (MoDL residual CNN D_W; VarNet regulariser K, Phi')
 * ``unrolled`` MoDL (Eq. 6) and VarNet (Eq. 5 "update_vn") blocks, forward and
                reverse mode, with the paper's complex-gradient convention
+* ``ipalm``    the iPALM update of the VarNet parameters with the filter constraints
+               (Sec. 2.3.1, training)
 * ``noncart``  non-Cartesian SENSE: direct non-uniform DFT pair, the PSF and the
                Toeplitz-embedded normal operator (Sec. 2.3.3)
                (Sec. 2.2.2 "Complex numbers": the real part of the gradient is
@@ -28,4 +30,4 @@ Every function here is pinned by a ``-m "not gpu"`` test against something
 other than itself (naive O(N^2) DFT, adjoint identity, closed forms, dense
 direct solves, brute-force loops, finite differences); see ``tests/``.
 """
-from . import fft, sense, cg, nn, unrolled, noncart  # noqa: F401
+from . import fft, sense, cg, nn, unrolled, noncart, ipalm  # noqa: F401

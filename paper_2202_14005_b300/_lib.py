@@ -21,6 +21,7 @@ STATUS_CG_BREAKDOWN = 1
 STATUS_NONFINITE = 2
 STATUS_DEVICE_TIMEOUT = 4
 DENOISER_MODL = 0
+DENOISER_VARNET = 1
 
 _vp = C.c_void_p
 _i = C.c_int
@@ -43,6 +44,9 @@ SIGNATURES = {
     "cg_dc_solve": (_i, [_vp, _vp, _vp, _vp, _dp, _i, _i, _dp]),
     "cg_dc_solve_backward": (_i, [_vp, _vp, _vp, _vp, _dp, _i, _i, _vp, _dp]),
     "sense_get_status": (_i, [_vp, C.POINTER(_i)]),
+    "sense_plan_set_wait_limit": (_i, [_vp, C.c_uint, _i]),
+    "ipalm_update_varnet": (_i, [_vp, _vp, _vp, _i, _f, _f, _f, _f, _vp]),
+    "sense_fma_probe": (_i, [_i, _i, _vp, _vp]),
     "sense_profile_enable": (_i, [_i]),
     "sense_profile_read": (_i, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(_i)]),
     "sense_kernel_launches": (C.c_longlong, [_i]),

@@ -307,6 +307,14 @@ int cg_dc_solve_backward(sense_plan p, const void* grad_x, const void* x, const 
   return SENSE_OK;
 }
 
+int sense_plan_set_wait_limit(sense_plan p, unsigned polls, int unreachable) {
+  if (!p) return SENSE_EINVAL_PTR;
+  if (unreachable != 0 && unreachable != 1) return SENSE_EINVAL_ARG;
+  p->wait_polls = polls ? polls : (1u << 22);
+  p->wait_phantom = (unsigned)unreachable;
+  return SENSE_OK;
+}
+
 int sense_get_status(sense_plan p, int* device_status) {
   if (!p || !device_status) return SENSE_EINVAL_PTR;
   int v = 0;

@@ -179,6 +179,7 @@ int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const 
   a.counter = w.counter; a.status = pl->status;
   CgCoop c;
   c.iters = iters; c.x = x; c.r = w.r; c.p = w.p; c.s = w.sv; c.w = w.wv; c.hist = rr_hist; c.rhs0 = rhs0;
+  c.polls = pl->wait_polls; c.phantom = pl->wait_phantom;
   const size_t np = (size_t)pl->B * pl->S * pl->H;
   for (int i = 0; i < 2; ++i) {
     c.pd[i] = w.part2 + i * np;

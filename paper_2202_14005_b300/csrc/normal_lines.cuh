@@ -520,6 +520,8 @@ struct CgCoop {
   // row partials of delta and gamma, two buffers each, used by alternate passes
   double* pd[2];
   double* pg[2];
+  unsigned polls;    // release-word polls before a waiting CTA gives up
+  unsigned phantom;  // arrivals each barrier expects beyond its CTAs (0; 1 only to test the timeout)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -585,7 +587,7 @@ __device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsi
   __syncthreads();  // this CTA's partials are written
   if (threadIdx.x == 0) {
     const unsigned t = atom_add_acq_rel_u32(cnt, 1u);
-    s_last = t == (n + 1u) * group - 1u;
+    s_last = t == (n + 1u) * (group + c.phantom) - 1u;
     s_ok = 1;
   }
   __syncthreads();
@@ -596,7 +598,7 @@ __device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsi
   } else if (threadIdx.x == 0) {
     unsigned it = 0;
     while (ld_acquire_u32(rel) < n + 1u) {
-      if (++it > (1u << 22)) {
+      if (++it > c.polls) {
         s_ok = 0;
         break;
       }

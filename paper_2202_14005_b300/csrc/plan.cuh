@@ -73,6 +73,10 @@ struct sense_plan_s {
   Fft1D fH2, fW2;
   float2* psf_hat = nullptr;
   int* status = nullptr;        // device status word (plan-owned)
+  // bounded waits of the one-launch CG (sense_plan_set_wait_limit): polls of a per-slice
+  // barrier before a CTA gives up, and arrivals added to every barrier (1 makes it unreachable)
+  unsigned wait_polls = 1u << 22;
+  unsigned wait_phantom = 0;
   void* own = nullptr;          // plan-owned device allocation (tables + status)
   void* ws = nullptr;
   size_t ws_bytes = 0;

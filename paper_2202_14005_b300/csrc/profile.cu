@@ -74,6 +74,32 @@ int sense_profile_read(const char* name, double* ms, int* launches) {
   return SENSE_OK;
 }
 
+// FP32 FMA throughput probe: every thread runs 8 independent FMA chains of `iters` steps in
+// registers (no memory traffic until one store per thread), so the achieved rate is the FP32
+// pipe's peak at the clock the GPU runs.  2 * 8 * iters * 256 FLOP per thread-block.
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, float seed, float* sink) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + 1e-3f * (threadIdx.x + 37 * k);
+  const float m = 0.999999f, c = 1e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], m, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == 12345.678f) sink[blockIdx.x] = s;  // keeps the chains live; practically never taken
+}
+
+int sense_fma_probe(int blocks, int iters, float* sink, void* stream) {
+  if (blocks <= 0 || iters <= 0) return SENSE_EINVAL_ARG;
+  if (!sink) return SENSE_EINVAL_PTR;
+  k_fma_probe<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(iters, 1.0f, sink);
+  prof_count(1);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
 long long sense_kernel_launches(int reset) {
   std::lock_guard<std::mutex> l(g_mu);
   const long long v = g_launches;

@@ -52,6 +52,13 @@ class ModlTrainer:
         self.t = 0
         self._lib = _lib.lib()
 
+    def use_plan(self, plan: SensePlan) -> None:
+        """Run later calls on another plan of the same image shape (another batch of slices:
+        other maps, same mask), keeping the weights, optimizer state and workspaces."""
+        if tuple(plan.img_shape()) != (self.B, self.H, self.W):
+            raise ValueError("plan image shape differs from the trainer's")
+        self.plan = plan
+
     def _step_args(self):
         return (self.plan._h, _lib.DENOISER_MODL, _p(self.weights), _p(self.lam))
 

@@ -59,8 +59,10 @@ class VarNetTrainer:
     (defer_join, joined once at the end of the pass); the gradients are bitwise the same."""
 
     def __init__(self, maps: torch.Tensor, mask: torch.Tensor, params: torch.Tensor, lr: float = 1e-4,
-                 normalize: bool = False, store_activations: bool = True):
-        self.plan = SensePlan(maps, mask)
+                 normalize: bool = False, store_activations: bool = True, plan: SensePlan | None = None,
+                 optimizer: str = "adam", ipalm_tau=(1e-2, 1e-2, 1e-2)):
+        # plan: an existing plan of the maps and mask instead of a new one
+        self.plan = plan if plan is not None else SensePlan(maps, mask)
         B, H, W = self.plan.img_shape()
         self.B, self.H, self.W = B, H, W
         if params.dim() != 2 or params.shape[1] != N_PARAM or params.dtype != torch.float32:
@@ -94,9 +96,23 @@ class VarNetTrainer:
         self.gtn = torch.empty((B, H, W), dtype=torch.complex64, device=dev)
         self.lr = lr
         self.t = 0
+        # optimizer "adam", or "ipalm" (Sec. 2.3.1): params then hold the inertial point z^k and
+        # self.x the iterate x^k; the filter constraints are applied by every update
+        if optimizer not in ("adam", "ipalm"):
+            raise ValueError("optimizer must be 'adam' or 'ipalm'")
+        self.optimizer = optimizer
+        self.ipalm_tau = tuple(float(v) for v in ipalm_tau)
+        self.x = params.clone() if optimizer == "ipalm" else None
 
     def _ws(self, t: int) -> torch.Tensor:
         return self.wss[t if self.store else 0]
+
+    def use_plan(self, plan: SensePlan) -> None:
+        """Run later calls on another plan of the same image shape (another batch of slices),
+        keeping the parameters, optimizer state and workspaces."""
+        if tuple(plan.img_shape()) != (self.B, self.H, self.W):
+            raise ValueError("plan image shape differs from the trainer's")
+        self.plan = plan
 
     def stage(self, t: int, x_t: torch.Tensor, x_next: torch.Tensor, nx_out: torch.Tensor | None = None):
         ws = self._ws(t)
@@ -170,7 +186,17 @@ class VarNetTrainer:
         loss = self.gradients(y, gt)
         self.t += 1
         st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        if self.optimizer == "ipalm":
+            # update k = self.t: gradient taken at z^k; next inertia alpha_{k+1} = k / (k + 3)
+            tf, tr_, tl = self.ipalm_tau
+            _lib.check("ipalm_update_varnet", self._lib.ipalm_update_varnet(
+                _p(self.params), _p(self.gp), _p(self.x), self.T, tf, tr_, tl, self.t / (self.t + 3.0), st))
+            return loss
         _lib.check("adam_update_f32", self._lib.adam_update_f32(
             _p(self.params), _p(self.gp), _p(self.m), _p(self.v), self.params.numel(), self.lr, 0.9,
             0.999, 1e-8, self.t, st))
         return loss
+
+    def iterate(self) -> torch.Tensor:
+        """The current parameters: x^k under iPALM (params holds the inertial point), else params."""
+        return self.x if self.optimizer == "ipalm" else self.params

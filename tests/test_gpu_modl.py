@@ -14,7 +14,13 @@ second unrolled block on, such flips in the denoiser input add up to a few
   per-layer bound, 1e-2 relative;
 * block outputs and the loss of the two-block chain: 1e-2;
 * gradients of the whole two-block chain (two BF16 reverse chains in series,
-  each input differing by the flips above): 5e-2 relative L2.
+  each input differing by the flips above): 5e-2 relative L2;
+* the same kind of chain taken block by block, each block's reverse mode
+  given the GPU's own intermediates (x^t, x^{t+1} and the incoming gradient
+  the GPU produced for that block) and the oracle using the activations the
+  GPU stored for that block: 1e-2 for every block and for the chain's sums;
+* the forward against the exact oracle (FP32 master weights, FP64 arithmetic,
+  no rounding hooks): 2e-2, the accumulated BF16 storage error of K blocks.
 """
 import numpy as np
 import pytest
@@ -146,3 +152,210 @@ def test_modl_train_step_updates_and_clears_gradients():
     assert torch.count_nonzero(tr.gw).item() == 0 and tr.gl.item() == 0.0
     assert all(np.isfinite(losses))
     assert tr.lam.item() >= 1e-6
+
+
+def _block_reverse(tr, t, g_in, recompute=0):
+    """unrolled_step_backward_ex of block t alone, into fresh gradient buffers."""
+    import ctypes as C
+    from paper_2202_14005_b300 import _lib
+    p = lambda a: C.c_void_p(a.data_ptr())
+    g_out = torch.empty_like(g_in)
+    gw = torch.zeros_like(tr.weights)
+    gl = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = tr._ws(t)
+    _lib.check("unrolled_step_backward_ex", _lib.lib().unrolled_step_backward_ex(
+        tr.plan._h, _lib.DENOISER_MODL, p(tr.weights), p(tr.lam), p(tr.xs[0]), p(tr.xs[t]),
+        p(tr.xs[t + 1]), p(g_in), p(g_out), p(gw), p(gl), tr.iters, p(ws), ws.numel(), recompute))
+    return g_out, gw, gl
+
+
+def _oracle_block_reverse(dn, x_t, x_next, g_next, wo, bs, lam, solve):
+    """The oracle's block derivative given the GPU's stored activations of D(x^t)
+    (ReLU masks and layer inputs as the GPU took them); solve(g) applies S^{-1}."""
+    acts, _ = dn.activations()
+    A = [a.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2) for a in acts]
+    xr = bf16_round(onn.c2r(x_t))
+    z = x_t.astype(np.complex128) + onn.r2c(onn.conv2d(A[3], wo[4], bs[4]))
+    v = solve(g_next)
+    glam = float(np.sum(np.real(np.conj(v) * (z - x_next))))
+    cache = {"acts": [xr] + A, "pre": A + [None]}
+    rg, rws, rbs = onn.modl_cnn_backward(x_t, wo, bs, lam * v, cache=cache, grad_round=bf16_round)
+    return rg, rws, rbs, glam
+
+
+def _check_block(tag, g_out, gw, gl, ref, tol=1e-2):
+    rg, rws, rbs, rgl = ref
+    errs = {"grad_x": rel(g_out.cpu().numpy(), rg)}
+    gws, gbs = unflat(gw.cpu().numpy().astype(np.float64))
+    for l in range(5):
+        errs[f"w{l + 1}"] = rel(gws[l], rws[l])
+        errs[f"b{l + 1}"] = rel(gbs[l], rbs[l])
+    if gl is not None:
+        errs["lambda"] = abs(gl.item() - rgl) / abs(rgl)
+    print(tag, {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v <= tol, f"{tag} {k}: {v:.3e}"
+
+
+def test_denoiser_reverse_mode_at_workload_shape():
+    """denoiser_backward on the 4 x 256 x 232 workload (about 14 row segments per CTA in the
+    64-channel weight-gradient kernel, the halo ring wrapping across tiles) against the
+    oracle fed the GPU's recomputed activations: every layer's weight, bias and input
+    gradient within 1e-2."""
+    from paper_2202_14005_b300.denoiser import ModlDenoiser
+    from test_gpu_denoiser import make_x
+    cfg = synth.CONFIGS[3]
+    B, H, W = cfg.B, cfg.H, cfg.W
+    ws, bs, flat = make_weights(41)
+    x = make_x(B, H, W, 43)
+    g = (synth.randn_complex((B, H, W), 44) * 0.1).astype(np.complex64)
+    dn = ModlDenoiser(B, H, W)
+    wt = dev(flat)
+    gw = torch.zeros_like(wt)
+    gx = dn.backward(wt, dev(x), dev(g), gw, recompute=True)
+    torch.cuda.synchronize()
+    wo = oracle_weights(ws)
+    acts, _ = dn.activations()
+    A = [a.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2) for a in acts]
+    cache = {"acts": [bf16_round(onn.c2r(x))] + A, "pre": A + [None]}
+    rg, rws, rbs = onn.modl_cnn_backward(x, wo, bs, g, cache=cache, grad_round=bf16_round)
+    _check_block("denoiser 4x256x232", gx, gw, None, (rg, rws, rbs, None))
+    assert dn.status() == 0
+
+
+def test_unrolled_step_reverse_mode_at_workload_shape():
+    """One MoDL block of the training workload (4 slices, 12 coils, 256 x 232, 10 CG
+    iterations) in reverse mode from its stored activations, against the oracle block
+    derivative on identical inputs (1e-2)."""
+    from paper_2202_14005_b300.modl import ModlTrainer
+    cfg = synth.CONFIGS[3]
+    d = synth.make_slices(cfg)
+    maps, mask = d["maps"].astype(np.complex64), d["mask"]
+    y = (osense.forward(d["x_gt"], maps, mask) + mask * d["noise"]).astype(np.complex64)
+    ws, bs, flat = make_weights(47)
+    lam, iters = cfg.lam, cfg.cg_iters
+    tr = ModlTrainer(dev(maps), dev(mask), dev(flat), lam, 1, iters)
+    tr.forward(dev(y))
+    torch.cuda.synchronize()
+    x0, x1 = tr.xs[0].cpu().numpy(), tr.xs[1].cpu().numpy()
+    g1 = (synth.randn_complex(x0.shape, 48) * 1e-3).astype(np.complex64)
+    g0, gw, gl = _block_reverse(tr, 0, dev(g1), recompute=0)
+    torch.cuda.synchronize()
+    ref = _oracle_block_reverse(tr.dns[0], x0, x1, g1, oracle_weights(ws), bs, lam,
+                                lambda g: ocg.cg_solve(maps, mask, lam, g, None, iters)[0])
+    _check_block("block 4x12x256x232", g0, gw, gl, ref)
+    assert tr.plan.status() == 0 and tr.denoiser_status() == 0
+
+
+def test_modl_chain_gradients_block_by_block():
+    """A three-block chain in reverse mode, one block at a time on the GPU's own
+    intermediates: each block's gradients, and their sums over the chain, within 1e-2 of
+    the oracle's block derivatives; the sums agree with the trainer's whole-chain
+    gradients up to FP32 accumulation order."""
+    from paper_2202_14005_b300.modl import ModlTrainer
+    maps, mask, y, gt = problem(B=2, C=4, H=32, W=232, seed=23)
+    ws, bs, flat = make_weights(25)
+    K, iters, lam = 3, 10, 0.05
+    wo = oracle_weights(ws)
+    tr = ModlTrainer(dev(maps), dev(mask), dev(flat), lam, K, iters)
+    tr.gradients(dev(y), dev(gt))              # whole chain, for the sums
+    torch.cuda.synchronize()
+    gw_chain, gl_chain = tr.gw.clone(), tr.gl.clone()
+    import ctypes as C
+    from paper_2202_14005_b300 import _lib
+    tr.forward(dev(y))                          # the same forward again (bitwise)
+    g = torch.empty_like(tr.xs[K])              # the loss gradient, as the whole-chain pass formed it
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p = lambda a: C.c_void_p(a.data_ptr())
+    _lib.check("sense_mse_loss", _lib.lib().sense_mse_loss(tr.plan._h, p(tr.xs[K]), p(dev(gt)),
+                                                           p(loss), p(g)))
+    gw_sum = torch.zeros_like(tr.weights)
+    gl_sum = 0.0
+    rw_sum = [np.zeros_like(w) for w in wo]
+    rb_sum = [np.zeros_like(b) for b in bs]
+    rl_sum = 0.0
+    solve = lambda gg: ocg.cg_solve(maps, mask, lam, gg, None, iters)[0]
+    for t in range(K - 1, -1, -1):
+        g_out, gw, gl = _block_reverse(tr, t, g, recompute=0)
+        torch.cuda.synchronize()
+        ref = _oracle_block_reverse(tr.dns[t], tr.xs[t].cpu().numpy(), tr.xs[t + 1].cpu().numpy(),
+                                    g.cpu().numpy(), wo, bs, lam, solve)
+        _check_block(f"block {t}", g_out, gw, gl, ref)
+        gw_sum += gw
+        gl_sum += gl.item()
+        for l in range(5):
+            rw_sum[l] += ref[1][l]
+            rb_sum[l] += ref[2][l]
+        rl_sum += ref[3]
+        g = g_out
+    gws, gbs = unflat(gw_sum.cpu().numpy().astype(np.float64))
+    for l in range(5):
+        assert rel(gws[l], rw_sum[l]) <= 1e-2, f"chain w{l + 1}"
+        assert rel(gbs[l], rb_sum[l]) <= 1e-2, f"chain b{l + 1}"
+    assert abs(gl_sum - rl_sum) <= 1e-2 * abs(rl_sum)
+    # the whole-chain call adds the same block contributions (in another FP32 order)
+    assert rel(gw_chain.cpu().numpy(), gw_sum.cpu().numpy()) <= 1e-5
+    assert abs(gl_chain.item() - gl_sum) <= 1e-9 * abs(gl_sum)
+    assert tr.plan.status() == 0 and tr.denoiser_status() == 0
+
+
+def test_modl_forward_against_exact_oracle():
+    """The GPU forward (BF16 weights and activations, FP32 CG) against the exact FP64
+    oracle with the FP32 master weights and no rounding hooks: every block output within
+    2e-2."""
+    from paper_2202_14005_b300.modl import ModlTrainer
+    maps, mask, y, gt = problem(B=2, C=6, H=48, W=232, seed=29)
+    ws, bs, flat = make_weights(27)
+    K, iters, lam = 3, 10, 0.05
+    tr = ModlTrainer(dev(maps), dev(mask), dev(flat), lam, K, iters)
+    tr.forward(dev(y))
+    torch.cuda.synchronize()
+    AHy = osense.adjoint(y, maps, mask)
+    _, rxs = ounr.modl_forward(AHy, maps, mask, ws, bs, lam, K, iters)
+    errs = [rel(tr.xs[t].cpu().numpy(), rxs[t]) for t in range(K + 1)]
+    print("MoDL forward vs exact oracle, per block:", [f"{e:.2e}" for e in errs])
+    for t, e in enumerate(errs):
+        assert e <= 2e-2, f"x^{t}: {e:.3e}"
+    assert tr.plan.status() == 0
+
+
+def test_modl_block_on_toeplitz_plan():
+    """unrolled_step and its reverse mode on a non-Cartesian (Toeplitz) plan, against the
+    oracle block with the Toeplitz normal operator inside its CG (Sec. 2.3.3, Eq. 6)."""
+    from oracle import noncart as onc
+    from paper_2202_14005_b300.modl import ModlTrainer
+    from paper_2202_14005_b300.sense import SensePlan, toeplitz_psf
+    B, Cc, N = 2, 3, 40
+    rng = np.random.default_rng(61)
+    maps = np.stack([synth.coil_maps(Cc, N, N, rng) for _ in range(B)]).astype(np.complex64)
+    traj = synth.radial_trajectory(24, 80, N).reshape(-1, 2).astype(np.float32)
+    psf = toeplitz_psf(dev(traj), N, N)
+    torch.cuda.synchronize()
+    rpsf = psf.cpu().numpy().astype(np.complex128)
+    plan = SensePlan.toeplitz(dev(maps), psf)
+    ws, bs, flat = make_weights(63)
+    # Without density compensation this trajectory's normal operator has its largest eigenvalue
+    # near 35 (1 for a Cartesian mask), so lambda = 2 gives S_lambda the condition number
+    # (35 + 2) / 2 < 21 of the Cartesian workloads, for which the tolerances are set.
+    lam, iters = 2.0, 10
+    tr = ModlTrainer(dev(maps), None, dev(flat), lam, 1, iters, plan=plan)
+    gt = np.stack([synth.phantom(N, N, rng, 6) for _ in range(B)]).astype(np.complex64)
+    AHy = onc.toeplitz_normal(gt, maps, rpsf, 0.0).astype(np.complex64)
+    tr.forward_from_adjoint(dev(AHy))
+    torch.cuda.synchronize()
+    x0, x1 = tr.xs[0].cpu().numpy(), tr.xs[1].cpu().numpy()
+    wo = oracle_weights(ws)
+    # forward: the block output from the GPU's own denoiser output D(x^0)
+    acts, _ = tr.dns[0].activations()
+    A3 = acts[3].float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2)
+    z = x0.astype(np.complex128) + onn.r2c(onn.conv2d(A3, wo[4], bs[4]))
+    Sl = lambda p_: onc.toeplitz_normal(p_, maps, rpsf, lam)
+    rx1, _ = ocg.cg(Sl, AHy.astype(np.complex128) + lam * z, None, iters)
+    assert rel(x1, rx1) <= 1e-4
+    g1 = (synth.randn_complex(x0.shape, 64) * 1e-3).astype(np.complex64)
+    g0, gw, gl = _block_reverse(tr, 0, dev(g1), recompute=0)
+    torch.cuda.synchronize()
+    ref = _oracle_block_reverse(tr.dns[0], x0, x1, g1, wo, bs, lam,
+                                lambda g: ocg.cg(Sl, g, None, iters)[0])
+    _check_block("toeplitz block", g0, gw, gl, ref)
+    assert tr.plan.status() == 0 and tr.denoiser_status() == 0

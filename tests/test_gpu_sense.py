@@ -316,6 +316,28 @@ def test_cg_breakdown_and_nonfinite_status():
     assert plan.status() == 0  # cleared by the read
 
 
+def test_cg_barrier_wait_runs_out_and_context_stays_usable():
+    """Failure detection without a fault: with every per-slice barrier of the one-launch CG
+    made unreachable (one arrival expected that never comes) and a limit of 64 polls, every
+    waiting CTA gives up, the kernel returns, SENSE_STATUS_DEVICE_TIMEOUT is reported, and
+    the next solve on the same plan (default limits) is correct."""
+    from paper_2202_14005_b300 import _lib
+    cfg, maps, mask, rhs, _ = _cg_inputs(2, 4)
+    plan = plan_for(maps, mask)
+    L = _lib.lib()
+    lam = torch.tensor([cfg.lam], dtype=torch.float64, device="cuda")
+    assert L.sense_plan_set_wait_limit(plan._h, 64, 2) == -7  # unreachable must be 0 or 1
+    assert L.sense_plan_set_wait_limit(plan._h, 64, 1) == 0
+    x, n = _cg_path_counts(lambda: plan.cg_solve(dev(rhs), lam, cfg.cg_iters))
+    assert n["cg_lines"] == 1, n
+    assert plan.status() & 4  # SENSE_STATUS_DEVICE_TIMEOUT
+    assert L.sense_plan_set_wait_limit(plan._h, 0, 0) == 0
+    x = plan.cg_solve(dev(rhs), lam, cfg.cg_iters)
+    xref, _ = ocg.cg_solve(maps, mask, cfg.lam, rhs, None, cfg.cg_iters)
+    assert rel(host(x), xref) <= TOL_CG
+    assert plan.status() == 0
+
+
 def test_workspace_required_errors():
     from paper_2202_14005_b300 import _lib
     import ctypes as C
