@@ -12,7 +12,9 @@ Adam on the 113,155 parameters — every step in libsense kernels (tensor-core
 convolutions, fused normal operator, CG vector kernels).
 
 Also measured: plain CG-SENSE on the 16-slice batch (slices/s, NRMSE) and the
-standalone normal operator (GB/s).  Inputs are seeded synthetic phantoms, coil
+standalone normal operator (GB/s).  After the timed region (untimed), MoDL is
+trained on operator-simulated slices and evaluated on 16 held-out slices against
+plain CG-SENSE on the same slices (nrmse_learned, nrmse_cg_sense).  Inputs are seeded synthetic phantoms, coil
 maps and k-space simulated with the library's own forward operator.
 
 Printed (rank 0, one JSON line): slices/s with inputs resident in HBM (value),
@@ -37,6 +39,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "unrolled-recon slices/s (fwd+bwd) & normal-op HBM GB/s vs plain CG-SENSE @NRMSE"
+# Training of the learned reconstruction reported beside the timed step (network, Adam steps,
+# learning rate): operator-simulated training slices, evaluated on 16 held-out slices against
+# plain CG-SENSE on the same slices (paper_2202_14005_b300.train).
+LEARNED = {"modl_train": ("modl", 3000, 1e-3)}
+
 WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it",
              "varnet_train": "varnet_train_b4_c15_320x368_R4_T10",
              "noncart_modl_infer": "modl_infer_radial_b32_c12_256x256_96x512_K10_cg10"}
@@ -185,8 +192,36 @@ def fp32_peak_tflops(sm_mhz):
     return 148 * 128 * 2 * (sm_mhz or 2032.0) * 1e6 / 1e12
 
 
-def kernel_report(name, ms, n, alg, peaks_d, clocks, workload):
-    """Achieved vs peak for one kernel group; alg = (kind, amount per launch)."""
+def measure_fp32_peak(dev, reps=5):
+    """FP32 FMA peak of this GPU, measured: the library's register-only FMA probe (8 blocks of
+    256 threads per SM, 8 independent chains per thread) timed with CUDA events; best of reps.
+    Returns (TFLOP/s, median SM MHz sampled while it ran)."""
+    import torch
+    from paper_2202_14005_b300 import _lib
+    import ctypes as C
+    blocks, iters = 148 * 8, 20000
+    flops = 2.0 * 8 * 256 * iters * blocks
+    sink = torch.zeros(blocks, dtype=torch.float32, device=dev)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = _lib.lib()
+    _lib.check("sense_fma_probe", L.sense_fma_probe(blocks, 100, C.c_void_p(sink.data_ptr()), st))
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _lib.check("sense_fma_probe", L.sense_fma_probe(blocks, iters, C.c_void_p(sink.data_ptr()), st))
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    c = clk.stop()
+    return flops / (best * 1e-3) / 1e12, c.get("sm_mhz")
+
+
+def kernel_report(name, ms, n, alg, peaks_d, clocks, workload, alu_flops=None):
+    """Achieved vs peak for one kernel group; alg = (kind, amount per launch).  alu_flops: FP32
+    FLOPs per launch of the kernel's arithmetic, reported against the measured FP32 peak."""
     if n == 0 or ms <= 0:
         return None
     kind, per = alg
@@ -200,9 +235,15 @@ def kernel_report(name, ms, n, alg, peaks_d, clocks, workload):
     else:  # alu (FP32 FMA)
         ach = per / t / 1e12
         peak, unit = fp32_peak_tflops(clocks.get("sm_max_mhz")), "TFLOP/s"
-    return {"kernel": name, "bound": kind, "achieved": round(ach, 2), "peak": round(peak, 1),
-            "unit": unit, "frac": round(ach / peak, 4), "traffic": NCU_TRAFFIC.get(workload, {}).get(name),
-            "launches": n, "avg_launch_us": round(1e3 * ms / n, 3), "alg_per_launch": per}
+    rep = {"kernel": name, "bound": kind, "achieved": round(ach, 2), "peak": round(peak, 1),
+           "unit": unit, "frac": round(ach / peak, 4), "traffic": NCU_TRAFFIC.get(workload, {}).get(name),
+           "launches": n, "avg_launch_us": round(1e3 * ms / n, 3), "alg_per_launch": per}
+    if alu_flops and peaks_d.get("fp32_tflops"):
+        a = alu_flops / t / 1e12
+        rep["alu"] = {"achieved": round(a, 2), "peak": round(peaks_d["fp32_tflops"], 1), "unit": "TFLOP/s",
+                      "frac": round(a / peaks_d["fp32_tflops"], 4), "flop_per_launch": alu_flops,
+                      "peak_source": "measured FP32 FMA probe"}
+    return rep
 
 
 def load_peaks():
@@ -251,6 +292,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     dist = torch.distributed if world > 1 else None
     pk = load_peaks()
+    pk["fp32_tflops"], pk["fp32_probe_sm_mhz"] = measure_fp32_peak(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
     clk = ClockSampler(local_rank)
     res = {}
@@ -301,7 +343,11 @@ def run_ours(args, rank, world, local_rank):
     nbytes = 8 * N * c2.B * (c2.C + 2)
     res["normal_op"] = {"workload": "256x232, 12 coils, 16 slices, lambda I", "GB/s": round(nbytes / (tn_med * 1e-3) / 1e9, 1),
                         "frac": round(nbytes / (tn_med * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
-                        "median_us": round(tn_med * 1e3, 2), "alg_bytes": nbytes}
+                        "median_us": round(tn_med * 1e3, 2), "alg_bytes": nbytes,
+                        "alu": {"flop": 154.0 * N * c2.B * c2.C,
+                                "TFLOP/s": round(154.0 * N * c2.B * c2.C / (tn_med * 1e-3) / 1e12, 2),
+                                "frac": round(154.0 * N * c2.B * c2.C / (tn_med * 1e-3) / 1e12 / pk["fp32_tflops"], 4),
+                                "peak_tflops": round(pk["fp32_tflops"], 1)}}
     # soft-SENSE normal operator (two map sets, Sec. 2.3.3) on the same batch: fused line kernel
     maps_s = torch.stack([maps2, 0.6 * torch.roll(maps2, 1, dims=1)], dim=1).contiguous()
     plan_s = SensePlan(maps_s, mask2)
@@ -536,9 +582,17 @@ def run_ours(args, rank, world, local_rank):
     conv_flops = 2.0 * px * 64 * 576
     vn_flops = 2.0 * px * 24 * 2 * 121  # one 2<->24 channel 11x11 convolution
     vn_store = bool(getattr(tr, "store", False)) if args.workload == "varnet_train" else False
+    # FP32 arithmetic per application: the line path's ~154 FLOP per pixel and coil (two pruned
+    # row transforms, coil expand and combine); the Toeplitz path's two 2H x 2W FFTs per coil
+    # (5 n log2 n FLOP each)
+    line_flops = 154.0 * px * cfg.C
+    n4 = 4 * Hc * Wc
+    tp_flops = 2 * 5.0 * n4 * math.log2(n4) * B * cfg.C
     kern = {
-        "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks, args.workload),
-        "cg_lines": kernel_report("cg_lines", *prof["cg_lines"], ("hbm", cg_bytes), pk, clocks, args.workload)
+        "normal_lines": kernel_report("normal_lines", *prof["normal_lines"], ("hbm", normal_bytes), pk, clocks,
+                                      args.workload, alu_flops=line_flops),
+        "cg_lines": kernel_report("cg_lines", *prof["cg_lines"], ("hbm", cg_bytes), pk, clocks, args.workload,
+                                  alu_flops=line_flops * cfg.cg_iters)
         if cg_bytes else None,
         "conv64_tc": kernel_report("conv64_tc", *prof["conv64_tc"], ("tensor", conv_flops), pk, clocks, args.workload),
         "wgrad64": kernel_report("wgrad64", *prof["wgrad64"], ("tensor", conv_flops), pk, clocks, args.workload),
@@ -548,7 +602,8 @@ def run_ours(args, rank, world, local_rank):
                                  clocks, args.workload),
         "vn_KT": kernel_report("vn_KT", *prof["vn_KT"], ("tensor", vn_flops), pk, clocks, args.workload),
         "vn_wgrad": kernel_report("vn_wgrad", *prof["vn_wgrad"], ("tensor", 2 * vn_flops), pk, clocks, args.workload),
-        "toeplitz": kernel_report("toeplitz", *prof["toeplitz"], ("hbm", normal_bytes), pk, clocks, args.workload),
+        "toeplitz": kernel_report("toeplitz", *prof["toeplitz"], ("hbm", normal_bytes), pk, clocks, args.workload,
+                                  alu_flops=tp_flops),
     }
     kern = {k: v for k, v in kern.items() if v}
     total_kernel_ms = {k: prof[k][0] for k in prof}
@@ -602,6 +657,14 @@ def run_ours(args, rank, world, local_rank):
         "peaks": pk,
     }
     out.update(res)
+    if args.workload in LEARNED and not args.no_train:
+        # the learned reconstruction against CG-SENSE on the same held-out slices (untimed)
+        from paper_2202_14005_b300 import train as _train
+        net, steps_tr, lr_tr = LEARNED[args.workload]
+        lr_res = _train.run(net, steps_tr, 256, 16, lr_tr, seed=3, log_every=250)
+        out["nrmse_learned"] = round(lr_res["nrmse_learned"], 5)
+        out["nrmse_cg_sense"] = round(lr_res["nrmse_cg_sense"], 5)
+        out["learned_recon"] = lr_res
     return out
 
 
@@ -704,26 +767,103 @@ def cpu_baseline(workload):
                       f"{est:.1f} s per step"}
 
 
+def _oracle_full_step(args):
+    """One slice's share of a whole step of a workload on the FP64 oracle, run in full (no
+    extrapolation); returns its CPU seconds."""
+    import numpy as np
+    import synth
+    from oracle import cg as ocg
+    from oracle import sense as osense
+    from oracle import unrolled as ounr
+    workload, s = args
+    if workload == "cg_sense":
+        return _oracle_slice(args)
+    cfg = synth.CONFIGS[{"modl_train": 3, "varnet_train": 4, "noncart_modl_infer": 5}[workload]]
+    d = synth.make_slices(cfg, [s])
+    maps = d["maps"].astype(np.complex64)
+    mask = d["mask"]
+    gt = d["x_gt"].astype(np.complex64)
+    if workload == "noncart_modl_infer":
+        from oracle import nn as onn
+        from oracle import noncart as onc
+        traj = synth.radial_trajectory(cfg.extra["spokes"], cfg.extra["samples"], cfg.H).reshape(-1, 2)
+        psf = onc.toeplitz_psf(traj, cfg.H, cfg.W)
+        x = onc.toeplitz_normal(gt, maps, psf, 0.0)  # x^0 (setup, not timed)
+        ws, bs = synth.modl_cnn_weights(5000)
+        t0 = time.perf_counter()
+        x0 = x
+        for _ in range(cfg.extra["K"]):
+            z, _ = onn.modl_cnn_forward(x, ws, bs)
+            x, _ = ocg.cg(lambda p: onc.toeplitz_normal(p, maps, psf, cfg.lam), x0 + cfg.lam * z, None,
+                          cfg.cg_iters)
+        return time.perf_counter() - t0
+    y = (osense.forward(gt, maps, mask) + mask * d["noise"]).astype(np.complex64)
+    t0 = time.perf_counter()
+    rhs = osense.adjoint(y, maps, mask)
+    if workload == "varnet_train":
+        filt, rbfw, lam = synth.varnet_weights(4000, cfg.extra["T"])
+        ounr.varnet_train_grads(rhs, maps, mask, gt, filt, rbfw, lam)
+    else:
+        ws, bs = synth.modl_cnn_weights(3000)
+        ounr.modl_train_grads(rhs, maps, mask, gt, ws, bs, cfg.lam, cfg.extra["K"], cfg.cg_iters)
+    return time.perf_counter() - t0
+
+
+REFERENCE_BUDGET_S = 150.0  # wall time the reference arm's timed and warm-up steps may take
+
+
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores, whole steps timed in full.
+
+    A step is every slice of the sample (16 slices for CG-SENSE, one per core, at most the
+    workload's batch, otherwise) going through the whole step of the workload, one spawn process
+    per slice.  The first step is a warm-up; further warm-ups and the timed steps are as many of
+    the requested ones as fit in REFERENCE_BUDGET_S (at least one timed step), and the line
+    reports the counts actually run."""
     if rank != 0:
         return None
-    n = 16 if args.workload == "cg_sense" else 4
-    reps = args.warmup + args.steps
-    if args.workload != "cg_sense":
-        reps = max(1, min(reps, 2))  # each rep is ~1 min of CPU work per slice
-    walls, used, per = oracle_pool_run(args.workload, n, reps)
-    vals = walls[min(args.warmup, reps - 1):]
-    wall = sum(vals)
-    value = n * len(vals) / wall
-    if args.workload != "cg_sense":
-        value = n / max(per)
+    import synth
+    cores = os.cpu_count() or 1
+    B = {"cg_sense": 16, "modl_train": synth.CONFIGS[3].B, "varnet_train": synth.CONFIGS[4].B,
+         "noncart_modl_infer": synth.CONFIGS[5].B}[args.workload]
+    n = 16 if args.workload == "cg_sense" else max(1, min(cores, B))
+    ctx = mp.get_context("spawn")
+    work = [(args.workload, s) for s in range(n)]
+    with ctx.Pool(processes=min(n, cores), initializer=_worker_init) as pool:
+        pool.map(_oracle_slice, [("cg_sense", 0)])  # imports and FFT plans (untimed)
+        t0 = time.perf_counter()
+        pool.map(_oracle_full_step, work)
+        probe = time.perf_counter() - t0
+        left = REFERENCE_BUDGET_S - probe
+        warm = 1 + max(0, min(args.warmup - 1, int(left / probe) - args.steps))
+        for _ in range(warm - 1):
+            pool.map(_oracle_full_step, work)
+        left = REFERENCE_BUDGET_S - warm * probe
+        steps = max(1, min(args.steps, int(left / probe)))
+        walls = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_full_step, work)
+            walls.append(time.perf_counter() - t0)
+    wall = sum(walls)
+    value = n * steps / wall
+    what = {"cg_sense": "A^H y + 10 CG iterations (x0 = A^H y)",
+            "modl_train": "A^H y, 5 MoDL blocks forward (CNN + 10-iteration CG) and reverse (second CG, "
+                          "CNN backward), loss and gradients",
+            "varnet_train": "A^H y, 10 VarNet stages forward and reverse, loss and gradients",
+            "noncart_modl_infer": "10 MoDL blocks (CNN + 10 CG iterations with the Toeplitz normal operator "
+                                  "on the 512x512 embedding; PSF and x^0 precomputed)"}[args.workload]
+    sample = (f"{n} slices per step, each the whole step: {what} (FP64 NumPy oracle, one spawn process "
+              f"per slice, {min(n, cores)} of {cores} host cores); {warm} warm-up and {steps} timed steps "
+              f"run in full (of {args.warmup} and {args.steps} requested; the arm's wall-time budget is "
+              f"{REFERENCE_BUDGET_S:.0f} s)")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "slices/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1e3 * wall / len(vals), 2), "higher_is_better": True,
+            "n_gpus": world, "steps": steps, "warmup": warm,
+            "ms_per_step": round(1e3 * wall / steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "slices_per_step": n},
-            "cpu_baseline": {"value": round(value, 5), "unit": "slices/s", "cores": used, "kind": "oracle",
-                             "sample": f"{n} slices per step (FP64 NumPy oracle, spawn pool)"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "slices/s", "cores": min(n, cores),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 5), "unit": "slices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -736,6 +876,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="modl_train", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true",
+                    help="skip the (untimed) training and held-out NRMSE evaluation")
     args = ap.parse_args()
     if args.impl == "ours":
         args.warmup = max(args.warmup, 3)

@@ -75,7 +75,15 @@ CONFIGS = {
 }
 
 
-def slice_rng(config: int, slice_index: int) -> np.random.Generator:
+def slice_rng(config: int, slice_index: int, split: str = "eval") -> np.random.Generator:
+    """Generator of one slice.  The "eval" split (the workloads, the tests and the held-out
+    evaluation) is seeded 1000 config + slice; the "train" split draws from the seed sequence
+    (7, config, slice), a stream disjoint from every integer seed, so training slices never
+    repeat an evaluation slice."""
+    if split == "train":
+        return np.random.default_rng([7, config, slice_index])
+    if split != "eval":
+        raise ValueError("split must be 'eval' or 'train'")
     return np.random.default_rng(1000 * config + slice_index)
 
 
@@ -174,18 +182,18 @@ def he_normal(shape, fan_in: int, rng: np.random.Generator) -> np.ndarray:
     return rng.standard_normal(shape) * math.sqrt(2.0 / fan_in)
 
 
-def make_slices(cfg: Config, slices=None, noise_sigma: float = 1e-3) -> dict:
+def make_slices(cfg: Config, slices=None, noise_sigma: float = 1e-3, split: str = "eval") -> dict:
     """Per-slice inputs of one workload (complex128 / float32 numpy arrays).
 
-    Returns x_gt [B,H,W], maps [B,C,H,W], mask [W] (shared by the batch, drawn
-    from the slice-0 generator stream of this config) and noise [B,C,H,W].
+    Returns x_gt [B,H,W], maps [B,C,H,W], mask [W] (shared by the batch and by
+    both splits, drawn from its own stream of this config) and noise [B,C,H,W].
     """
     idx = list(range(cfg.B)) if slices is None else list(slices)
     xs, Ss, ns = [], [], []
     mask = line_mask(cfg.W, cfg.R, cfg.n_centre, cfg.density,
                      np.random.default_rng(1000 * cfg.index + 999))
     for s in idx:
-        rng = slice_rng(cfg.index, s)
+        rng = slice_rng(cfg.index, s, split)
         xs.append(phantom(cfg.H, cfg.W, rng, cfg.n_ellipses, cfg.texture))
         Ss.append(coil_maps(cfg.C, cfg.H, cfg.W, rng))
         ns.append(complex_noise((cfg.C, cfg.H, cfg.W), noise_sigma, rng))
