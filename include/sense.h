@@ -102,6 +102,20 @@ int sense_plan_create_toeplitz(sense_plan* plan, int B, int C, int H, int W, con
  * centred (index - H/2, index - W/2), so on-grid samples give the centred
  * unitary DFT of sense_forward.  psf: device complex64 [2H][2W]. */
 int sense_toeplitz_psf(const float* traj, int M, int H, int W, void* psf, void* stream);
+/* Non-uniform DFT pair of non-Cartesian SENSE by direct summation (Sec. 2.3.3: the adjoint of
+ * the measured non-Cartesian samples initialises the networks, x^0 = A^H y):
+ *   forward  y[b][c][m] = (H W)^{-1/2} sum_n S_c(n) x(n) exp(-2 pi i (ky_m n'_y / H + kx_m n'_x / W))
+ *   adjoint  x[b][n]    = (H W)^{-1/2} sum_c conj(S_c(n)) sum_m y[b][c][m] exp(+2 pi i (...))
+ * n' = n - (H/2, W/2) (centred image coordinates), traj as for sense_toeplitz_psf, so on-grid
+ * samples give the centred unitary DFT of sense_forward and A^H A equals the Toeplitz-embedded
+ * normal operator of the PSF.  maps complex64 [B][C][H][W], x [B][H][W], y [B][C][M] (device,
+ * 8-byte aligned; x and y must not alias).  Cost O(M H W C) per slice (set-up calls, like the
+ * PSF).  Asynchronous on stream.  Errors: SENSE_EINVAL_SHAPE, SENSE_EINVAL_PTR,
+ * SENSE_EUNSUPPORTED (H or W > 4096). */
+int sense_nudft_forward(const float* traj, int M, int B, int C, int H, int W, const void* maps,
+                        const void* x, void* y, void* stream);
+int sense_nudft_adjoint(const float* traj, int M, int B, int C, int H, int W, const void* maps,
+                        const void* y, void* x, void* stream);
 int sense_plan_destroy(sense_plan plan);
 /* Change the stream later calls launch on. */
 int sense_plan_set_stream(sense_plan plan, void* stream);

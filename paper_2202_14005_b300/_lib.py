@@ -47,6 +47,8 @@ SIGNATURES = {
     "sense_plan_set_wait_limit": (_i, [_vp, C.c_uint, _i]),
     "ipalm_update_varnet": (_i, [_vp, _vp, _vp, _i, _f, _f, _f, _f, _vp]),
     "sense_fma_probe": (_i, [_i, _i, _vp, _vp]),
+    "sense_nudft_forward": (_i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    "sense_nudft_adjoint": (_i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "sense_profile_enable": (_i, [_i]),
     "sense_profile_read": (_i, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(_i)]),
     "sense_kernel_launches": (C.c_longlong, [_i]),

@@ -181,3 +181,34 @@ def toeplitz_psf(traj: torch.Tensor, H: int, W: int) -> torch.Tensor:
     _lib.check("sense_toeplitz_psf", _lib.lib().sense_toeplitz_psf(_ptr(traj), traj.shape[0], H, W, _ptr(psf),
                                                                   _stream()))
     return psf
+
+
+def _nudft_args(traj, maps):
+    if traj.device.type != "cuda" or traj.dtype != torch.float32 or traj.dim() != 2 or traj.shape[1] != 2:
+        raise ValueError("traj must be a CUDA float32 [M, 2] tensor")
+    _req(maps, "maps", torch.complex64, tuple(maps.shape))
+    if maps.dim() != 4:
+        raise ValueError("maps must be complex64 [B, C, H, W]")
+    return traj.contiguous()
+
+
+def nudft_forward(traj: torch.Tensor, maps: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    """Non-Cartesian samples y [B, C, M] of images x [B, H, W] (direct non-uniform DFT, Sec. 2.3.3)."""
+    traj = _nudft_args(traj, maps)
+    B, Cc, H, W = maps.shape
+    _req(x, "x", torch.complex64, (B, H, W))
+    y = torch.empty((B, Cc, traj.shape[0]), dtype=torch.complex64, device=x.device)
+    _lib.check("sense_nudft_forward", _lib.lib().sense_nudft_forward(
+        _ptr(traj), traj.shape[0], B, Cc, H, W, _ptr(maps), _ptr(x), _ptr(y), _stream()))
+    return y
+
+
+def nudft_adjoint(traj: torch.Tensor, maps: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """A^H y [B, H, W] of non-Cartesian samples y [B, C, M] (direct non-uniform DFT, Sec. 2.3.3)."""
+    traj = _nudft_args(traj, maps)
+    B, Cc, H, W = maps.shape
+    _req(y, "y", torch.complex64, (B, Cc, traj.shape[0]))
+    x = torch.empty((B, H, W), dtype=torch.complex64, device=y.device)
+    _lib.check("sense_nudft_adjoint", _lib.lib().sense_nudft_adjoint(
+        _ptr(traj), traj.shape[0], B, Cc, H, W, _ptr(maps), _ptr(y), _ptr(x), _stream()))
+    return x

@@ -89,3 +89,51 @@ def test_full_size_radial_workload_sampled():
     ref_rows[rows.index(256)] = 0
     assert rel(g[rows], ref_rows) <= 1e-6
     assert rel(out, onc.toeplitz_normal(x, maps, g, 0.0)) <= 1e-5
+
+
+@pytest.mark.parametrize("B,C,N,spokes,samples", [(2, 3, 32, 16, 64), (1, 13, 40, 21, 48)])
+def test_nudft_pair_against_direct_sums(B, C, N, spokes, samples):
+    """The GPU non-uniform DFT pair against the oracle's direct FP64 sums (1e-5; 13 coils
+    exercise a partial coil pass), the adjoint identity <A x, y> = <x, A^H y>, and A^H A of the
+    pair equal to the Toeplitz normal operator of the PSF."""
+    from paper_2202_14005_b300.sense import SensePlan, nudft_adjoint, nudft_forward, toeplitz_psf
+    maps, traj = case(B, C, N, spokes, samples, seed=N + C)
+    t64 = traj.astype(np.float64)
+    x = synth.randn_complex((B, N, N), 11).astype(np.complex64)
+    y = synth.randn_complex((B, C, traj.shape[0]), 12).astype(np.complex64)
+    yg = nudft_forward(dev(traj), dev(maps), dev(x)).cpu().numpy()
+    xg = nudft_adjoint(dev(traj), dev(maps), dev(y)).cpu().numpy()
+    assert rel(yg, onc.nudft_forward(x, maps, t64)) <= 1e-5
+    assert rel(xg, onc.nudft_adjoint(y, maps, t64)) <= 1e-5
+    lhs = np.vdot(yg.astype(np.complex128), y)          # <A x, y>
+    rhs = np.vdot(x.astype(np.complex128), xg)          # <x, A^H y>
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    psf = toeplitz_psf(dev(traj), N, N)
+    plan = SensePlan.toeplitz(dev(maps), psf)
+    n_op = plan.normal(dev(x), 0.0).cpu().numpy()
+    pair = nudft_adjoint(dev(traj), dev(maps), nudft_forward(dev(traj), dev(maps), dev(x))).cpu().numpy()
+    assert rel(pair, n_op) <= 1e-5
+
+
+def test_nudft_full_size_sampled():
+    """256 x 256, 12 coils, 96 golden-angle spokes x 512 samples: sampled outputs of both
+    directions against direct FP64 sums for those entries alone."""
+    from paper_2202_14005_b300.sense import nudft_adjoint, nudft_forward
+    N, C = 256, 12
+    maps, traj = case(1, C, N, 96, 512, seed=21)
+    t64 = traj.astype(np.float64)
+    x = synth.randn_complex((1, N, N), 13).astype(np.complex64)
+    y = synth.randn_complex((1, C, traj.shape[0]), 14).astype(np.complex64)
+    yg = nudft_forward(dev(traj), dev(maps), dev(x)).cpu().numpy()
+    xg = nudft_adjoint(dev(traj), dev(maps), dev(y)).cpu().numpy()
+    ny = np.arange(N) - N // 2
+    u = maps[0].astype(np.complex128) * x[0].astype(np.complex128)          # [C, N, N]
+    for m in (0, 1, 255, 256, 10000, traj.shape[0] - 1):
+        e = np.exp(-2j * np.pi * (t64[m, 0] * ny[:, None] / N + t64[m, 1] * ny[None, :] / N))
+        ref = (u * e).sum(axis=(1, 2)) / N
+        assert np.linalg.norm(yg[0, :, m] - ref) <= 1e-5 * np.linalg.norm(ref)
+    for (r, c) in ((0, 0), (128, 128), (17, 250), (255, 3)):
+        ph = np.exp(2j * np.pi * (t64[:, 0] * (r - N // 2) / N + t64[:, 1] * (c - N // 2) / N))
+        v = (y[0].astype(np.complex128) * ph[None]).sum(axis=1) / N          # [C]
+        ref = np.sum(np.conj(maps[0, :, r, c].astype(np.complex128)) * v)
+        assert abs(xg[0, r, c] - ref) <= 1e-5 * max(abs(ref), np.abs(v).max())
