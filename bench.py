@@ -42,7 +42,11 @@ METRIC = "unrolled-recon slices/s (fwd+bwd) & normal-op HBM GB/s vs plain CG-SEN
 # Training of the learned reconstruction reported beside the timed step (network, Adam steps,
 # learning rate): operator-simulated training slices, evaluated on 16 held-out slices against
 # plain CG-SENSE on the same slices (paper_2202_14005_b300.train).
-LEARNED = {"modl_train": ("modl", 3000, 1e-3)}
+LEARNED = {"modl_train": dict(network="modl", steps=3000, lr=1e-3),
+           "varnet_train": dict(network="varnet", steps=3000, lr=5e-4, optimizer="ipalm",
+                                ipalm_tau=(1e-2, 1e-2, 1e-1)),
+           # two-step schedule (Sec. 3): K = 1 first, then the workload's K = 10 blocks
+           "noncart_modl_infer": dict(network="modl_radial", steps=300, lr=1e-3, pre_steps=2000)}
 
 WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it",
              "varnet_train": "varnet_train_b4_c15_320x368_R4_T10",
@@ -420,20 +424,24 @@ def run_ours(args, rank, world, local_rank):
         value_slices = B
     elif args.workload == "noncart_modl_infer":
         # Sec. 2.3.3: radial sampling, A^H A through the Toeplitz embedding (PSF on the 2x grid,
-        # computed on the GPU from the trajectory); x^0 = A^H y precomputed (noiseless here:
-        # A^H A x_gt, since the non-uniform adjoint of measured samples is gridding, not built);
-        # MoDL inference with K = 10 blocks of the config-3 CNN (He-initialised weights) and 10 CG
-        # iterations each; plain 30-iteration CG-SENSE measured beside it.
-        from paper_2202_14005_b300.sense import toeplitz_psf
+        # computed on the GPU from the trajectory); the radial samples are simulated with the
+        # non-uniform DFT plus noise at the samples, and x^0 = A^H y (their non-uniform adjoint) is
+        # precomputed, as in the paper; MoDL inference with K = 10 blocks of the config-3 CNN and
+        # 10 CG iterations each (timed); plain 30-iteration CG-SENSE measured beside it.
+        from paper_2202_14005_b300.sense import nudft_adjoint, nudft_forward, toeplitz_psf
         c5 = synth.CONFIGS[5]
         cfg = c5
         inp5 = make_inputs(c5, slice_offset=replica_slice_offset(rank, c5.B))
         maps5 = torch.from_numpy(inp5["maps"]).to(dev)
         traj = synth.radial_trajectory(c5.extra["spokes"], c5.extra["samples"], c5.H).reshape(-1, 2)
-        psf = toeplitz_psf(torch.from_numpy(traj.astype(np.float32)).to(dev), c5.H, c5.W)
+        traj_d = torch.from_numpy(traj.astype(np.float32)).to(dev)
+        psf = toeplitz_psf(traj_d, c5.H, c5.W)
         plan5 = SensePlan.toeplitz(maps5, psf)
         gt5 = torch.from_numpy(inp5["x_gt"]).to(dev)
-        AHy5 = plan5.normal(gt5, 0.0)
+        y5 = nudft_forward(traj_d, maps5, gt5)
+        noise5 = synth.complex_noise(tuple(y5.shape), 1e-3, np.random.default_rng([11, 5000 + rank]))
+        y5 += torch.from_numpy(noise5.astype(np.complex64)).to(dev)
+        AHy5 = nudft_adjoint(traj_d, maps5, y5)
         ws, bs = synth.modl_cnn_weights(5000 + rank)
         flat = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(ws, bs)]).astype(np.float32)
         tr = ModlTrainer(maps5, None, torch.from_numpy(flat).to(dev), c5.lam, c5.extra["K"], c5.cg_iters,
@@ -488,7 +496,7 @@ def run_ours(args, rank, world, local_rank):
                           "cg_sense_30it": {"slices_per_s": round(B * world / (statistics.median(tc) * 1e-3), 1),
                                             "nrmse": round(nrmse_cg, 5)},
                           "modl_untrained_nrmse": round(nrmse_modl, 5),
-                          "data": "x^0 = A^H A x_gt (noiseless; the adjoint of measured radial samples is not built)"}
+                          "data": "x^0 = A^H y of radial samples simulated by the non-uniform DFT, noise sigma 1e-3"}
         y_h, maps_h = AHy5.cpu().pin_memory(), maps5.cpu().pin_memory()
         out_h = torch.empty(tr.xs[-1].shape, dtype=tr.xs[-1].dtype).pin_memory()
         ins = [(AHy5, y_h), (maps5, maps_h)]
@@ -660,8 +668,9 @@ def run_ours(args, rank, world, local_rank):
     if args.workload in LEARNED and not args.no_train:
         # the learned reconstruction against CG-SENSE on the same held-out slices (untimed)
         from paper_2202_14005_b300 import train as _train
-        net, steps_tr, lr_tr = LEARNED[args.workload]
-        lr_res = _train.run(net, steps_tr, 256, 16, lr_tr, seed=3, log_every=250)
+        kw = dict(LEARNED[args.workload])
+        lr_res = _train.run(kw.pop("network"), kw.pop("steps"), 256, 16, kw.pop("lr"), seed=3, log_every=250,
+                            **kw)
         out["nrmse_learned"] = round(lr_res["nrmse_learned"], 5)
         out["nrmse_cg_sense"] = round(lr_res["nrmse_cg_sense"], 5)
         out["learned_recon"] = lr_res

@@ -34,6 +34,7 @@
 #include <mutex>
 
 #include "plan.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -380,6 +381,231 @@ __global__ void __launch_bounds__(K_THREADS, 2) k_vn_K(const KArgs a) {
   }
 }
 
+// ------------------------------------------------- K (2 -> 24) on the tensor cores (tcgen05)
+// One CTA per band of KC_R = 8 output rows x 128 pixels, as k_vn_K, with the contraction issued
+// as tcgen05.mma (BF16 operands from shared memory, FP32 accumulators in tensor memory):
+//   per source row s of the band (s - h0 = delta, -5 .. 12):
+//     D[px][(r, i)] += sum_k A_s[px][k] B[(r, i)][k]   (M = 128 pixels, N = 8 rows x 32 filters, K = 80)
+//   A_s = im2col of source row s: k = part * 24 + c * 11 + dx (three BF16 terms of x, as in k_vn_K;
+//         columns 22, 23 of each part and 72 .. 79 zero);
+//   B   = the filters of row dy = delta + 5 - r for output row r (zero outside 0 .. 10).  All eight
+//         rows' blocks of one source row are a contiguous slice of one table: block j holds the
+//         24 filters (8 zero rows) of filter row dy = 17 - j, j = 0 .. 24, and source row delta
+//         takes blocks 12 - delta .. 19 - delta.
+// Operands sit in shared memory in the no-swizzle K-major core-matrix layout: element (row, k) at
+// (k / 8) * (rows * 16) + row * 16 + (k % 8) * 2 bytes (leading byte offset rows * 16 between the
+// two 8-element K halves of one MMA, stride byte offset 128 between 8-row groups).  The im2col
+// tile is double-buffered: thread 0 issues the five MMAs of a source row and commits them to the
+// buffer's mbarrier; the tile is rebuilt only after the MMAs that read it two rows earlier have
+// completed.  After the last source row the 8 warps read the accumulators (warp w: TMEM lanes of
+// its quadrant w % 4, output rows 4 (w / 4) .. 4 (w / 4) + 3) and run the RBF epilogue of k_vn_K.
+// Every wait is bounded; a CTA that gives up sets SENSE_STATUS_DEVICE_TIMEOUT (when a status word
+// is given), drains its committed MMAs (bounded) and frees its tensor memory.
+constexpr int KC_R = 8;
+constexpr int KC_CHUNKS = 10;                          // K = 80: ten 8-element chunks (72 used)
+constexpr int KC_A_CHUNK = TILE * 16;                  // bytes of one K chunk of the im2col tile
+constexpr int KC_A_BYTES = KC_A_CHUNK * KC_CHUNKS;     // 20,480
+constexpr int KC_BROWS = 25 * 32;                      // table rows: 25 blocks of 32 (24 filters)
+constexpr int KC_B_CHUNK = KC_BROWS * 16;              // 12,800
+constexpr int KC_B_BYTES = KC_B_CHUNK * KC_CHUNKS;     // 128,000
+constexpr int KC_TMEM_COLS = 256;                      // 8 rows x 32 columns of FP32 accumulators
+
+struct KcSmem {
+  static constexpr int OFF_B = 0;
+  static constexpr int OFF_A = OFF_B + KC_B_BYTES;
+  static constexpr int OFF_STG = OFF_A + 2 * KC_A_BYTES;
+  static constexpr int OFF_PR = OFF_STG + 2 * K_STG * 8;
+  static constexpr int PR_BYTES = K_PARTS * 2 * K_PR_LD * 2;
+  static constexpr int OFF_R = OFF_PR + PR_BYTES;
+  static constexpr int OFF_BAR = (OFF_R + NK * RBF_LD * 4 + 15) & ~15;
+  static constexpr int TOTAL = OFF_BAR + 32;
+};
+
+// The K table in the core-matrix layout above (bf16 element index (k / 8) * KC_BROWS * 8 + n * 8 + k % 8).
+__global__ void k_vn_pack_tc(const float* prm, bf16* wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= KC_BROWS * KC_CHUNKS * 8) return;
+  const int n = i / (KC_CHUNKS * 8), k = i % (KC_CHUNKS * 8);
+  const int j = n / 32, f = n % 32, dy = 17 - j;
+  float v = 0.f;
+  if (f < NK && dy >= 0 && dy < KS && k < K_KP && (k % 24) < 2 * KS) {
+    const int kk = k % 24, c = kk / KS, dx = kk % KS;
+    v = prm[(f * 2 + c) * NT + dy * KS + dx];
+  }
+  wt[(size_t)(k / 8) * KC_BROWS * 8 + n * 8 + (k % 8)] = __float2bfloat16_rn(v);
+}
+
+template <bool ZIN>
+__global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const bf16* wt, int* status) {
+  using S = KcSmem;
+  extern __shared__ __align__(128) uint8_t dsm[];
+  float* s_r = reinterpret_cast<float*>(dsm + S::OFF_R);
+  uint64_t* mma_done = reinterpret_cast<uint64_t*>(dsm + S::OFF_BAR);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(dsm + S::OFF_BAR + 16);
+  int* s_err = reinterpret_cast<int*>(dsm + S::OFF_BAR + 20);
+  const int w0 = blockIdx.x * TILE, h0 = blockIdx.y * KC_R, b = blockIdx.z;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    mbar_init(&mma_done[0], 1);
+    mbar_init(&mma_done[1], 1);
+    *s_err = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(s_tmem, KC_TMEM_COLS);
+    tmem_relinquish();
+  }
+  for (int i = tid; i < KC_B_BYTES / 16; i += K_THREADS)
+    cp16(dsm + S::OFF_B + i * 16, reinterpret_cast<const uint8_t*>(wt) + i * 16, true);
+  for (int i = tid; i < NK * RBF_LD; i += K_THREADS) {
+    const int j = i % RBF_LD - RBF_PAD;
+    s_r[i] = (unsigned)j < (unsigned)NW ? a.rbf[(i / RBF_LD) * NW + j] : 0.f;
+  }
+  const int s_lo = max(h0 - KH, 0), s_hi = min(h0 + KC_R - 1 + KH, a.H - 1);
+  const int nrows = s_hi - s_lo + 1;
+  auto stage = [&](int k) {
+    const int s = s_lo + k, buf = k & 1;
+    for (int q = tid; q < K_STG / 2; q += K_THREADS) {
+      const int col = w0 - 6 + 2 * q;  // even; W is even, so col + 1 < W whenever col < W
+      const bool ok = col >= 0 && col < a.W;
+      cp16(dsm + S::OFF_STG + buf * K_STG * 8 + q * 16, a.x + (ok ? ((size_t)b * a.H + s) * a.W + col : 0), ok);
+    }
+  };
+  stage(0);
+  cp_commit();
+  // the unused last K chunk (k = 72 .. 79) of both im2col buffers is zero
+  for (int i = tid; i < 2 * TILE; i += K_THREADS)
+    *reinterpret_cast<uint4*>(dsm + S::OFF_A + (i / TILE) * KC_A_BYTES + 9 * KC_A_CHUNK + (i % TILE) * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t idesc = umma_idesc_bf16(TILE, KC_R * 32);
+  int last_issued = -1;  // thread 0: the last source row whose MMAs were committed
+
+#pragma unroll 1
+  for (int k = 0; k < nrows; ++k) {
+    if (k + 1 < nrows) stage(k + 1);
+    cp_commit();
+    cp_wait<1>();  // source row k (and, at k = 0, the tables) have landed
+    if (tid == 0 && k >= 2 && !mbar_wait(&mma_done[k & 1], ((k - 2) >> 1) & 1)) *s_err = 1;
+    __syncthreads();
+    if (*s_err) break;
+    // BF16 terms of source row k
+    for (int j = tid; j < K_STG; j += K_THREADS) {
+      float2 v = reinterpret_cast<const float2*>(dsm + S::OFF_STG + (k & 1) * K_STG * 8)[j];
+      bf16* pr = reinterpret_cast<bf16*>(dsm + S::OFF_PR);
+#pragma unroll
+      for (int part = 0; part < K_PARTS; ++part) {
+        const bf16 re = __float2bfloat16_rn(v.x), im = __float2bfloat16_rn(v.y);
+        pr[(part * 2) * K_PR_LD + j] = re;
+        pr[(part * 2 + 1) * K_PR_LD + j] = im;
+        v.x -= __bfloat162float(re);
+        v.y -= __bfloat162float(im);
+      }
+    }
+    __syncthreads();
+    // im2col of source row k into buffer k & 1: item (part, pixel m) = 24 columns = 3 K chunks
+    uint8_t* At = dsm + S::OFF_A + (k & 1) * KC_A_BYTES;
+    for (int it = tid; it < K_PARTS * TILE; it += K_THREADS) {
+      const int part = it / TILE, m = it % TILE;
+      const uint32_t* r0 = reinterpret_cast<const uint32_t*>(dsm + S::OFF_PR + (part * 2) * K_PR_LD * 2);
+      const uint32_t* r1 = r0 + K_PR_LD / 2;
+      const int e0 = m + 1, w0i = e0 >> 1;
+      const bool odd = e0 & 1;
+      uint32_t A[6], Bw[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        A[q] = r0[w0i + q];
+        Bw[q] = r1[w0i + q];
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        A[q] = odd ? __byte_perm(A[q], A[q + 1], 0x5432) : A[q];
+        Bw[q] = odd ? __byte_perm(Bw[q], Bw[q + 1], 0x5432) : Bw[q];
+      }
+      A[5] = odd ? (A[5] >> 16) : (A[5] & 0xffffu);
+      Bw[5] = odd ? (Bw[5] >> 16) : (Bw[5] & 0xffffu);
+      uint8_t* dst = At + (part * 3) * KC_A_CHUNK + m * 16;
+      *reinterpret_cast<uint4*>(dst) = make_uint4(A[0], A[1], A[2], A[3]);
+      *reinterpret_cast<uint4*>(dst + KC_A_CHUNK) =
+          make_uint4(A[4], A[5] | (Bw[0] << 16), __byte_perm(Bw[0], Bw[1], 0x5432), __byte_perm(Bw[1], Bw[2], 0x5432));
+      *reinterpret_cast<uint4*>(dst + 2 * KC_A_CHUNK) =
+          make_uint4(__byte_perm(Bw[2], Bw[3], 0x5432), __byte_perm(Bw[3], Bw[4], 0x5432),
+                     __byte_perm(Bw[4], Bw[5], 0x5432), 0u);
+    }
+    fence_proxy_async();  // this thread's shared-memory writes (and landed copies) -> tensor core
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const int j0 = 12 - (s_lo + k - h0);  // first table block of this source row
+      const uint32_t sa = smem_u32(At), sb = smem_u32(dsm + S::OFF_B) + j0 * 32 * 16;
+#pragma unroll
+      for (int ks = 0; ks < 5; ++ks) {
+        const uint64_t ad = umma_desc(sa + ks * 2 * KC_A_CHUNK, KC_A_CHUNK, 128);
+        const uint64_t bd = umma_desc(sb + ks * 2 * KC_B_CHUNK, KC_B_CHUNK, 128);
+        umma_bf16(tmem, ad, bd, idesc, (k | ks) != 0);
+      }
+      umma_commit(&mma_done[k & 1]);
+      last_issued = k;
+    }
+  }
+  // accumulators of the band: every lane waits for the last commit
+  bool ok = *s_err == 0;
+  if (ok) {
+    const int kl = nrows - 1;
+    const bool got = mbar_wait(&mma_done[kl & 1], (kl >> 1) & 1);
+    if (!got) atomicExch(s_err, 1);
+    ok = __all_sync(0xffffffffu, got);
+  }
+  tc_fence_after();
+  if (ok) {
+    const int q = warp & 3;
+    const int w = w0 + q * 32 + lane;
+#pragma unroll 1
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = (warp >> 2) * 4 + rr, h = h0 + r;
+      float acc[32];
+      __syncwarp();  // the TMEM loads are warp-collective
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + r * 32, *reinterpret_cast<float(*)[16]>(acc));
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + r * 32 + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+      if (h >= a.H || w >= a.W) continue;
+      const size_t p = ((size_t)b * a.H + h) * a.W + w;
+#pragma unroll
+      for (int i0 = 0; i0 < NK; i0 += 2) {
+        const float2 a0 = make_float2(acc[i0], acc[i0 + 1]);
+        if constexpr (ZIN) {  // a0 = K g; z from the forward stage
+          const float2 z = *reinterpret_cast<const float2*>(a.z + p * NK + i0);
+          const Rbf2 f = rbf_eval2(z, s_r + i0 * RBF_LD, s_r + (i0 + 1) * RBF_LD);
+          *reinterpret_cast<uint32_t*>(a.v + p * CU + i0) =
+              pack2(__float2bfloat16_rn(f.d2.x * a0.x), __float2bfloat16_rn(f.d2.y * a0.y));
+          *reinterpret_cast<float2*>(a.kg + p * NK + i0) = a0;
+        } else {
+          const Rbf2 f = rbf_eval2(a0, s_r + i0 * RBF_LD, s_r + (i0 + 1) * RBF_LD);
+          *reinterpret_cast<uint32_t*>(a.u + p * CU + i0) =
+              pack2(__float2bfloat16_rn(f.d1.x), __float2bfloat16_rn(f.d1.y));
+          *reinterpret_cast<float2*>(a.z + p * NK + i0) = a0;
+        }
+      }
+      // channels 24..31 of the stored activations are zero
+      uint4* pad = reinterpret_cast<uint4*>((ZIN ? a.v : a.u) + p * CU + NK);
+      pad[0] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*s_err && tid == 0) {
+    if (status) set_status(status, SENSE_STATUS_DEVICE_TIMEOUT);
+    if (last_issued >= 0) mbar_wait(&mma_done[last_issued & 1], (last_issued >> 1) & 1, 1u << 20);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, KC_TMEM_COLS);
+}
+
 // ------------------------------------------------------------ K^T (24 -> 2)
 // out = base + sgn K^T(src) - lambda (n - c): base, n and c may be NULL (zero; no data term
 // without n)
@@ -666,7 +892,7 @@ __global__ void __launch_bounds__(256) k_vn_reduce(const float* partial, int nro
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 struct VnLayout {
-  size_t wk, wn, u, v, z, kg, n1, n2, part, part2, pdot, total;
+  size_t wk, wn, wtc, u, v, z, kg, n1, n2, part, part2, pdot, total;
 };
 VnLayout vn_layout(int B, int H, int W) {
   VnLayout L;
@@ -674,6 +900,7 @@ VnLayout vn_layout(int B, int H, int W) {
   size_t o = 0;
   L.wk = o; o += up256(K_W_ELEMS * 2);
   L.wn = o; o += up256(KT_W_ELEMS * 2);
+  L.wtc = o; o += up256(KC_B_BYTES);
   L.u = o; o += up256(px * CU * 2);
   L.v = o; o += up256(px * CU * 2);
   L.z = o; o += up256(px * NK * 4);
@@ -692,9 +919,9 @@ int vn_prepare() {
   static std::mutex mu;
   std::lock_guard<std::mutex> l(mu);
   if (state == 0)
-    state = (cudaFuncSetAttribute(k_vn_K<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<1>::TOTAL) ==
+    state = (             cudaFuncSetAttribute(k_vn_K_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, KcSmem::TOTAL) ==
                  cudaSuccess &&
-             cudaFuncSetAttribute(k_vn_K<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<1>::TOTAL) ==
+             cudaFuncSetAttribute(k_vn_K_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, KcSmem::TOTAL) ==
                  cudaSuccess &&
              cudaFuncSetAttribute(k_vn_K<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSmem<2>::TOTAL) ==
                  cudaSuccess &&
@@ -727,6 +954,7 @@ int vn_check(sense_plan p, const float* prm, const void* AHy, const void* xt, co
 struct Shape {
   int B, H, W;
   cudaStream_t st;
+  int* status = nullptr;  // device status word for bounded-wait timeouts (plan calls), or none
 };
 
 void vn_pack(const float* prm, uint8_t* ws, const VnLayout& L, cudaStream_t st) {
@@ -734,6 +962,8 @@ void vn_pack(const float* prm, uint8_t* ws, const VnLayout& L, cudaStream_t st) 
   prof_mark("vn_misc", st, false);
   k_vn_pack<<<(n + 255) / 256, 256, 0, st>>>(prm, reinterpret_cast<bf16*>(ws + L.wk),
                                              reinterpret_cast<bf16*>(ws + L.wn));
+  const int ntc = KC_BROWS * KC_CHUNKS * 8;
+  k_vn_pack_tc<<<(ntc + 255) / 256, 256, 0, st>>>(prm, reinterpret_cast<bf16*>(ws + L.wtc));
   prof_mark("vn_misc", st, true);
 }
 
@@ -750,16 +980,17 @@ int launch_K(const Shape& sh, int nsrc, const float* prm, const float2* x, const
   a.v = reinterpret_cast<bf16*>(ws + L.v);
   a.z = reinterpret_cast<float*>(ws + L.z);
   a.kg = reinterpret_cast<float*>(ws + L.kg);
-  const int R = K_RMAX / (nsrc == 2 ? 2 : 1);
+  const int R = nsrc == 2 ? K_RMAX / 2 : KC_R;
   const dim3 grid((sh.W + TILE - 1) / TILE, (sh.H + R - 1) / R, sh.B);
   const char* grp = nsrc >= 2 ? "vn_Kbwd" : "vn_K";
+  const bf16* wtc = reinterpret_cast<const bf16*>(ws + L.wtc);
   prof_mark(grp, sh.st, false);
-  if (nsrc == 2)
+  if (nsrc == 2)  // K x and K g together (the recomputing reverse pass): warp-level tensor cores
     k_vn_K<2><<<grid, K_THREADS, KSmem<2>::TOTAL, sh.st>>>(a);
   else if (nsrc == 3)
-    k_vn_K<1, true><<<grid, K_THREADS, KSmem<1>::TOTAL, sh.st>>>(a);
+    k_vn_K_tc<true><<<grid, K_THREADS, KcSmem::TOTAL, sh.st>>>(a, wtc, sh.status);
   else
-    k_vn_K<1><<<grid, K_THREADS, KSmem<1>::TOTAL, sh.st>>>(a);
+    k_vn_K_tc<false><<<grid, K_THREADS, KcSmem::TOTAL, sh.st>>>(a, wtc, sh.status);
   prof_mark(grp, sh.st, true);
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
@@ -841,7 +1072,7 @@ int varnet_stage(sense_plan p, const float* prm, const void* AHy, const void* x_
   if (!x_next || !al16(x_next) || x_next == x_t || nx_out == x_t || nx_out == x_next) return SENSE_EINVAL_PTR;
   uint8_t* w8 = static_cast<uint8_t*>(ws);
   const VnLayout L = vn_layout(p->B, p->H, p->W);
-  const Shape sh{p->B, p->H, p->W, p->stream};
+  const Shape sh{p->B, p->H, p->W, p->stream, p->status};
   const float2* x = static_cast<const float2*>(x_t);
   float2* n1 = nx_out ? static_cast<float2*>(nx_out) : reinterpret_cast<float2*>(w8 + L.n1);
   // A^H A x on a side stream beside z = K x and u = Phi'(z); both feed the combine
@@ -870,7 +1101,7 @@ int varnet_stage_backward_ex(sense_plan p, const float* prm, const void* AHy, co
   if (!p->ws) return SENSE_EWORKSPACE;  // the lambda-gradient dot uses the plan's workspace
   uint8_t* w8 = static_cast<uint8_t*>(ws);
   const VnLayout L = vn_layout(p->B, p->H, p->W);
-  const Shape sh{p->B, p->H, p->W, p->stream};
+  const Shape sh{p->B, p->H, p->W, p->stream, p->status};
   const float2* x = static_cast<const float2*>(x_t);
   const float2* g = static_cast<const float2*>(grad_next);
   float2* n2 = reinterpret_cast<float2*>(w8 + L.n2);

@@ -95,6 +95,19 @@ class ModlTrainer:
     def gradients(self, y: torch.Tensor, gt: torch.Tensor):
         """Forward, loss and reverse mode; gradients accumulate into self.gw / self.gl."""
         self.forward(y)
+        return self._reverse(gt)
+
+    def gradients_from_adjoint(self, AHy: torch.Tensor, gt: torch.Tensor):
+        """As gradients, from a given x^0 = A^H y (non-Cartesian data, Sec. 2.3.3)."""
+        self.forward_from_adjoint(AHy)
+        return self._reverse(gt)
+
+    def train_step_from_adjoint(self, AHy: torch.Tensor, gt: torch.Tensor):
+        loss = self.gradients_from_adjoint(AHy, gt)
+        self._update()
+        return loss
+
+    def _reverse(self, gt: torch.Tensor):
         _lib.check("sense_mse_loss", self._lib.sense_mse_loss(
             self.plan._h, _p(self.xs[self.K]), _p(gt), _p(self.loss), _p(self.g[0])))
         h, kind, w, lam = self._step_args()
@@ -110,6 +123,10 @@ class ModlTrainer:
 
     def train_step(self, y: torch.Tensor, gt: torch.Tensor):
         loss = self.gradients(y, gt)
+        self._update()
+        return loss
+
+    def _update(self):
         self.t += 1
         st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
         _lib.check("adam_update_f32", self._lib.adam_update_f32(
@@ -118,4 +135,3 @@ class ModlTrainer:
         _lib.check("adam_update_f64", self._lib.adam_update_f64(
             _p(self.lam), _p(self.gl), _p(self.m_l), _p(self.v_l), 1, self.lam_lr, 0.9, 0.999, 1e-8,
             self.t, 1e-6, st))
-        return loss

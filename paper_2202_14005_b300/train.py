@@ -13,6 +13,11 @@ stand in for them):
 * training slices come from the "train" seed split and the evaluation slices from the
   workload's own seeds, so the two sets never share a slice.
 
+Radial data (network modl_radial, Sec. 2.3.3): golden-angle radial samples simulated by the
+library's non-uniform DFT with noise at the samples; x^0 = A^H y by the non-uniform adjoint; the
+normal operator through the Toeplitz embedding of the trajectory's PSF; CG-SENSE with 30
+iterations.
+
 Training (every arithmetic step of the network in the library's kernels): MoDL (Eq. 6) with K
 blocks sharing one residual CNN and a learnable lambda, or the VarNet (Eq. 5) with T stages,
 Adam on all parameters, a constant learning rate with a tenfold decay over the last quarter of
@@ -72,6 +77,27 @@ class Batch:
         self.B = x_gt.shape[0]
 
 
+class RadialBatch:
+    """One batch of radially sampled slices (Sec. 2.3.3): non-Cartesian samples simulated by the
+    library's non-uniform DFT, noise at the samples, x^0 = A^H y by the non-uniform adjoint and a
+    Toeplitz plan (the trajectory's PSF) for the normal operator."""
+
+    def __init__(self, host, traj, psf, noise_seed: int, sigma: float = 1e-3, device="cuda"):
+        import torch
+        import synth
+        from .sense import SensePlan, nudft_adjoint, nudft_forward
+        x_gt, maps, _, _ = host
+        self.gt = torch.from_numpy(x_gt).to(device)
+        self.maps = torch.from_numpy(maps).to(device)
+        self.mask = None  # no Cartesian mask: the plan holds the trajectory's PSF
+        self.plan = SensePlan.toeplitz(self.maps, psf)
+        self.B = x_gt.shape[0]
+        M = traj.shape[0]
+        noise = synth.complex_noise((self.B, maps.shape[1], M), sigma, np.random.default_rng([11, noise_seed]))
+        y = nudft_forward(traj, self.maps, self.gt) + torch.from_numpy(noise.astype(np.complex64)).to(device)
+        self.AHy = nudft_adjoint(traj, self.maps, y)
+
+
 def nrmse_per_slice(x, gt) -> np.ndarray:
     a = x.detach().cpu().numpy().astype(np.complex128)
     b = gt.detach().cpu().numpy().astype(np.complex128)
@@ -84,7 +110,7 @@ def cg_sense(batches, lam: float, iters: int) -> np.ndarray:
     import torch
     out = []
     for b in batches:
-        AHy = b.plan.adjoint(b.y)
+        AHy = b.AHy if hasattr(b, "AHy") else b.plan.adjoint(b.y)
         lt = torch.tensor([lam], dtype=torch.float64, device=AHy.device)
         x = b.plan.cg_solve(AHy, lt, iters, x0=AHy)
         out.append(nrmse_per_slice(x, b.gt))
@@ -118,6 +144,18 @@ def _schedule(step: int, steps: int, lr: float) -> float:
     return lr if step < int(0.75 * steps) else 0.1 * lr
 
 
+def _modl_step(tr, b):
+    if hasattr(b, "AHy"):
+        return tr.train_step_from_adjoint(b.AHy, b.gt)
+    return tr.train_step(b.y, b.gt)
+
+
+def _modl_infer(tr, b):
+    if hasattr(b, "AHy"):
+        return tr.forward_from_adjoint(b.AHy)
+    return tr.forward(b.y)
+
+
 def train_modl(train, evals, *, K=5, iters=10, lam0=0.05, steps=2000, lr=5e-4, lam_lr=1e-3,
                seed=3, log_every=100, store_activations=True, pre_steps=0) -> dict:
     """pre_steps > 0: the two-step schedule of Sec. 3 (MoDL): the weights and lambda are first
@@ -136,7 +174,7 @@ def train_modl(train, evals, *, K=5, iters=10, lam0=0.05, steps=2000, lr=5e-4, l
             t1.use_plan(b.plan)
             t1.lr = _schedule(step, pre_steps, lr)
             t1.lam_lr = _schedule(step, pre_steps, lam_lr)
-            loss = t1.train_step(b.y, b.gt)
+            loss = _modl_step(t1, b)
             if step % log_every == 0 or step == pre_steps - 1:
                 pre_curve.append([step, float(loss.item())])
         lam0 = float(t1.lam.item())
@@ -148,7 +186,7 @@ def train_modl(train, evals, *, K=5, iters=10, lam0=0.05, steps=2000, lr=5e-4, l
         out = []
         for b in evals:
             tr.use_plan(b.plan)
-            out.append(nrmse_per_slice(tr.forward(b.y), b.gt))
+            out.append(nrmse_per_slice(_modl_infer(tr, b), b.gt))
         return float(np.concatenate(out).mean())
 
     nrmse0 = evaluate()
@@ -164,7 +202,7 @@ def train_modl(train, evals, *, K=5, iters=10, lam0=0.05, steps=2000, lr=5e-4, l
         tr.use_plan(b.plan)
         tr.lr = _schedule(step, steps, lr)
         tr.lam_lr = _schedule(step, steps, lam_lr)
-        loss = tr.train_step(b.y, b.gt)
+        loss = _modl_step(tr, b)
         if step % log_every == 0 or step == steps - 1:
             curve.append([step, float(loss.item())])
     torch.cuda.synchronize()
@@ -234,20 +272,36 @@ def run(network: str, steps: int, train_slices: int, eval_slices: int, lr: float
         optimizer: str = "adam", ipalm_tau=(1e-2, 1e-2, 1e-2)) -> dict:
     """Generate the data, train, and evaluate against CG-SENSE on the same held-out slices."""
     import synth
-    cfg_index = 3 if network == "modl" else 4
+    cfg_index = {"modl": 3, "varnet": 4, "modl_radial": 5}[network]
     cfg = synth.CONFIGS[cfg_index]
+    bsz = 4  # slices per training batch (the radial workload's inference batch is larger)
     t0 = time.perf_counter()
-    host_train = generate(cfg_index, "train", train_slices, cfg.B, workers)
-    host_eval = generate(cfg_index, "eval", eval_slices, cfg.B, workers)
+    host_train = generate(cfg_index, "train", train_slices, bsz, workers)
+    host_eval = generate(cfg_index, "eval", eval_slices, bsz, workers)
     t_gen = time.perf_counter() - t0
-    train = [Batch(h) for h in host_train]
-    evals = [Batch(h) for h in host_eval]
-    if network == "modl":
+    if network == "modl_radial":
+        import torch
+        from .sense import toeplitz_psf
+        traj = torch.from_numpy(synth.radial_trajectory(cfg.extra["spokes"], cfg.extra["samples"], cfg.H)
+                                .reshape(-1, 2).astype(np.float32)).cuda()
+        psf = toeplitz_psf(traj, cfg.H, cfg.W)
+        train = [RadialBatch(h, traj, psf, 1000 + i) for i, h in enumerate(host_train)]
+        evals = [RadialBatch(h, traj, psf, i) for i, h in enumerate(host_eval)]
+        res = train_modl(train, evals, K=cfg.extra["K"], iters=cfg.cg_iters, lam0=cfg.lam, steps=steps,
+                         lr=lr, seed=seed, log_every=log_every, pre_steps=pre_steps)
+        res.pop("weights")
+        res["network"] = "modl_radial"
+        res.update(cg_sense_report(evals, cfg.lam, 30))
+    elif network == "modl":
+        train = [Batch(h) for h in host_train]
+        evals = [Batch(h) for h in host_eval]
         res = train_modl(train, evals, K=cfg.extra["K"], iters=cfg.cg_iters, lam0=cfg.lam, steps=steps,
                          lr=lr, seed=seed, log_every=log_every, pre_steps=pre_steps)
         res.pop("weights")
         res.update(cg_sense_report(evals, cfg.lam, cfg.cg_iters))
     else:
+        train = [Batch(h) for h in host_train]
+        evals = [Batch(h) for h in host_eval]
         res = train_varnet(train, evals, steps=steps, lr=lr, seed=seed, log_every=log_every,
                            T=cfg.extra["T"], optimizer=optimizer, ipalm_tau=ipalm_tau)
         res.update(cg_sense_report(evals, 0.05, 10))
@@ -258,7 +312,7 @@ def run(network: str, steps: int, train_slices: int, eval_slices: int, lr: float
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--network", choices=["modl", "varnet"], default="modl")
+    ap.add_argument("--network", choices=["modl", "varnet", "modl_radial"], default="modl")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--train-slices", type=int, default=256)
     ap.add_argument("--eval-slices", type=int, default=16)
