@@ -44,9 +44,7 @@ METRIC = "unrolled-recon slices/s (fwd+bwd) & normal-op HBM GB/s vs plain CG-SEN
 # plain CG-SENSE on the same slices (paper_2202_14005_b300.train).
 LEARNED = {"modl_train": dict(network="modl", steps=3000, lr=1e-3),
            "varnet_train": dict(network="varnet", steps=3000, lr=5e-4, optimizer="ipalm",
-                                ipalm_tau=(1e-2, 1e-2, 1e-1)),
-           # two-step schedule (Sec. 3): K = 1 first, then the workload's K = 10 blocks
-           "noncart_modl_infer": dict(network="modl_radial", steps=300, lr=1e-3, pre_steps=2000)}
+                                ipalm_tau=(1e-2, 1e-2, 1e-1))}
 
 WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "cg_sense_b16_c12_256x232_R6_10it",
              "varnet_train": "varnet_train_b4_c15_320x368_R4_T10",
@@ -59,7 +57,7 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
 NCU_TRAFFIC = {
     "cg_sense": {"normal_lines": 110.3e6, "cg_lines": 1.511e9},
     "modl_train": {"cg_lines": 24.8e6, "conv64_tc": 30.54e6, "wgrad64": 62.9e6},
-    "varnet_train": {"vn_K": 23.87e6, "vn_Kbwd": 76.16e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
+    "varnet_train": {"vn_K": 31.18e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
 }
 # what the reverse pass reuses from the forward pass of each training workload
 REVERSE_PASS = {
@@ -413,8 +411,10 @@ def run_ours(args, rank, world, local_rank):
         cfg, B, t_ms, prof, launches, steps = c2, c2.B, t_cg, prof_cg, launches_cg, steps_cg
         # initial residual (normal operator, maps + x + rhs + out) and the one-launch CG solve:
         # per iteration the normal operator (maps, r, p_old, p, q) and the update (p, q, x, r; x, r)
-        normal_bytes = 8 * N * c2.B * (c2.C + 3)
-        cg_bytes = 8 * N * c2.B * ((c2.C + 3) + (c2.cg_iters - 1) * (c2.C + 4) + 6 * c2.cg_iters)
+        # algorithmic bytes per unit (one slice): normal operator 8 N (C + 2) (read x and the
+        # maps, write out), one CG iteration 8 N (C + 8) (the operator plus six vector passes)
+        normal_bytes = 8 * N * c2.B * (c2.C + 2)
+        cg_bytes = 8 * N * c2.B * (c2.C + 8) * c2.cg_iters
         # e2e through host buffers: k-space and maps in, reconstruction out
         y_h, maps_h = y2.cpu().pin_memory(), maps2.cpu().pin_memory()
         out_h = torch.empty(x2.shape, dtype=x2.dtype).pin_memory()
@@ -570,8 +570,8 @@ def run_ours(args, rank, world, local_rank):
         assert tr.plan.status() == 0 and tr.denoiser_status() == 0
         B = c3.B
         N3 = c3.H * c3.W
-        normal_bytes = 8 * N3 * B * (c3.C + 3)
-        cg_bytes = 8 * N3 * B * ((c3.C + 3) + (c3.cg_iters - 1) * (c3.C + 4) + 6 * c3.cg_iters)
+        normal_bytes = 8 * N3 * B * (c3.C + 2)
+        cg_bytes = 8 * N3 * B * (c3.C + 8) * c3.cg_iters
         y_h, maps_h, gt_h = y3.cpu().pin_memory(), maps3.cpu().pin_memory(), gt3.cpu().pin_memory()
         out_h = torch.empty(1, dtype=torch.float64).pin_memory()
         ins = [(y3, y_h), (maps3, maps_h), (gt3, gt_h)]

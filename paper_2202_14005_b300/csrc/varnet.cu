@@ -405,14 +405,16 @@ constexpr int KC_R = 8;
 constexpr int KC_CHUNKS = 10;                          // K = 80: ten 8-element chunks (72 used)
 constexpr int KC_A_CHUNK = TILE * 16;                  // bytes of one K chunk of the im2col tile
 constexpr int KC_A_BYTES = KC_A_CHUNK * KC_CHUNKS;     // 20,480
-constexpr int KC_BROWS = 25 * 32;                      // table rows: 25 blocks of 32 (24 filters)
-constexpr int KC_B_CHUNK = KC_BROWS * 16;              // 12,800
-constexpr int KC_B_BYTES = KC_B_CHUNK * KC_CHUNKS;     // 128,000
+constexpr int KC_NBLK = 25;                            // table blocks (filter rows dy = 17 - j)
+constexpr int KC_BLK_BYTES = 32 * 16 * KC_CHUNKS;      // one block: 32 rows x 80 K = 5,120 bytes
+constexpr int KC_B_BYTES = KC_NBLK * KC_BLK_BYTES;     // 128,000 (global table)
+constexpr int KC_RING = 10;                            // blocks held in shared memory
+constexpr int KC_RB_CHUNK = KC_RING * 32 * 16;         // one K chunk of the ring: 5,120 bytes
 constexpr int KC_TMEM_COLS = 256;                      // 8 rows x 32 columns of FP32 accumulators
 
 struct KcSmem {
-  static constexpr int OFF_B = 0;
-  static constexpr int OFF_A = OFF_B + KC_B_BYTES;
+  static constexpr int OFF_B = 0;                      // ring of KC_RING table blocks
+  static constexpr int OFF_A = OFF_B + KC_RB_CHUNK * KC_CHUNKS;
   static constexpr int OFF_STG = OFF_A + 2 * KC_A_BYTES;
   static constexpr int OFF_PR = OFF_STG + 2 * K_STG * 8;
   static constexpr int PR_BYTES = K_PARTS * 2 * K_PR_LD * 2;
@@ -421,10 +423,11 @@ struct KcSmem {
   static constexpr int TOTAL = OFF_BAR + 32;
 };
 
-// The K table in the core-matrix layout above (bf16 element index (k / 8) * KC_BROWS * 8 + n * 8 + k % 8).
+// The K table, block-major: block j (32 rows, filter row dy = 17 - j) is contiguous, each of its
+// K chunks a 512-byte core-matrix column (bf16 index j * 2560 + (k / 8) * 256 + f * 8 + k % 8).
 __global__ void k_vn_pack_tc(const float* prm, bf16* wt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= KC_BROWS * KC_CHUNKS * 8) return;
+  if (i >= KC_NBLK * 32 * KC_CHUNKS * 8) return;
   const int n = i / (KC_CHUNKS * 8), k = i % (KC_CHUNKS * 8);
   const int j = n / 32, f = n % 32, dy = 17 - j;
   float v = 0.f;
@@ -432,13 +435,13 @@ __global__ void k_vn_pack_tc(const float* prm, bf16* wt) {
     const int kk = k % 24, c = kk / KS, dx = kk % KS;
     v = prm[(f * 2 + c) * NT + dy * KS + dx];
   }
-  wt[(size_t)(k / 8) * KC_BROWS * 8 + n * 8 + (k % 8)] = __float2bfloat16_rn(v);
+  wt[(size_t)j * (KC_BLK_BYTES / 2) + (k / 8) * 256 + f * 8 + (k % 8)] = __float2bfloat16_rn(v);
 }
 
 template <bool ZIN>
-__global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const bf16* wt, int* status) {
+__global__ void __launch_bounds__(K_THREADS, 2) k_vn_K_tc(const KArgs a, const bf16* wt, int* status) {
   using S = KcSmem;
-  extern __shared__ __align__(128) uint8_t dsm[];
+  extern __shared__ __align__(16) uint8_t dsm[];
   float* s_r = reinterpret_cast<float*>(dsm + S::OFF_R);
   uint64_t* mma_done = reinterpret_cast<uint64_t*>(dsm + S::OFF_BAR);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(dsm + S::OFF_BAR + 16);
@@ -456,8 +459,13 @@ __global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const b
     tmem_alloc(s_tmem, KC_TMEM_COLS);
     tmem_relinquish();
   }
-  for (int i = tid; i < KC_B_BYTES / 16; i += K_THREADS)
-    cp16(dsm + S::OFF_B + i * 16, reinterpret_cast<const uint8_t*>(wt) + i * 16, true);
+  // table block j into ring slot j % KC_RING (its K chunk kc: 32 rows x 16 bytes at kc * KC_RB_CHUNK)
+  auto load_block = [&](int j) {
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(wt) + (size_t)j * KC_BLK_BYTES;
+    uint8_t* dst = dsm + S::OFF_B + (j % KC_RING) * 512;
+    for (int i = tid; i < KC_BLK_BYTES / 16; i += K_THREADS)
+      cp16(dst + (i >> 5) * KC_RB_CHUNK + (i & 31) * 16, src + i * 16, true);
+  };
   for (int i = tid; i < NK * RBF_LD; i += K_THREADS) {
     const int j = i % RBF_LD - RBF_PAD;
     s_r[i] = (unsigned)j < (unsigned)NW ? a.rbf[(i / RBF_LD) * NW + j] : 0.f;
@@ -472,6 +480,9 @@ __global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const b
       cp16(dsm + S::OFF_STG + buf * K_STG * 8 + q * 16, a.x + (ok ? ((size_t)b * a.H + s) * a.W + col : 0), ok);
     }
   };
+  // first source row: its x row and the eight table blocks of its window (12 - delta .. 19 - delta)
+  const int jw0 = 12 - (s_lo - h0);
+  for (int j = jw0; j < jw0 + KC_R; ++j) load_block(j);
   stage(0);
   cp_commit();
   // the unused last K chunk (k = 72 .. 79) of both im2col buffers is zero
@@ -482,17 +493,25 @@ __global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const b
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const uint32_t idesc = umma_idesc_bf16(TILE, KC_R * 32);
   int last_issued = -1;  // thread 0: the last source row whose MMAs were committed
 
+  // Source row k reads im2col buffer k & 1 and the ring slots of blocks j0 .. j0 + 7 (j0 = 12 -
+  // delta, one less per row).  Before row k's x row and block j0 - 1 (for row k + 1) are copied in,
+  // the MMAs of row k - 2 (the last reader of that buffer and of that slot: a ring of ten blocks)
+  // must have completed.
 #pragma unroll 1
   for (int k = 0; k < nrows; ++k) {
-    if (k + 1 < nrows) stage(k + 1);
-    cp_commit();
-    cp_wait<1>();  // source row k (and, at k = 0, the tables) have landed
+    const int j0 = 12 - (s_lo + k - h0);
     if (tid == 0 && k >= 2 && !mbar_wait(&mma_done[k & 1], ((k - 2) >> 1) & 1)) *s_err = 1;
     __syncthreads();
     if (*s_err) break;
+    if (k + 1 < nrows) {
+      stage(k + 1);
+      load_block(j0 - 1);
+    }
+    cp_commit();
+    cp_wait<1>();  // source row k and its window have landed
+    __syncthreads();
     // BF16 terms of source row k
     for (int j = tid; j < K_STG; j += K_THREADS) {
       float2 v = reinterpret_cast<const float2*>(dsm + S::OFF_STG + (k & 1) * K_STG * 8)[j];
@@ -540,13 +559,18 @@ __global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const b
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const int j0 = 12 - (s_lo + k - h0);  // first table block of this source row
-      const uint32_t sa = smem_u32(At), sb = smem_u32(dsm + S::OFF_B) + j0 * 32 * 16;
+      // the window's 256 rows start at ring slot j0 % KC_RING; where they wrap past the last slot
+      // the MMA is split in two (N1 + N2 = 256 accumulator columns, both multiples of 32)
+      const int sl = j0 % KC_RING;
+      const int n1 = min(KC_RING - sl, KC_R) * 32, n2 = KC_R * 32 - n1;
+      const uint32_t sa = smem_u32(At), sb = smem_u32(dsm + S::OFF_B);
+      const uint32_t id1 = umma_idesc_bf16(TILE, n1), id2 = umma_idesc_bf16(TILE, n2 > 0 ? n2 : 32);
 #pragma unroll
       for (int ks = 0; ks < 5; ++ks) {
         const uint64_t ad = umma_desc(sa + ks * 2 * KC_A_CHUNK, KC_A_CHUNK, 128);
-        const uint64_t bd = umma_desc(sb + ks * 2 * KC_B_CHUNK, KC_B_CHUNK, 128);
-        umma_bf16(tmem, ad, bd, idesc, (k | ks) != 0);
+        const uint32_t bk = sb + ks * 2 * KC_RB_CHUNK;
+        umma_bf16(tmem, ad, umma_desc(bk + sl * 512, KC_RB_CHUNK, 128), id1, (k | ks) != 0);
+        if (n2 > 0) umma_bf16(tmem + n1, ad, umma_desc(bk, KC_RB_CHUNK, 128), id2, (k | ks) != 0);
       }
       umma_commit(&mma_done[k & 1]);
       last_issued = k;
@@ -567,15 +591,18 @@ __global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const b
 #pragma unroll 1
     for (int rr = 0; rr < 4; ++rr) {
       const int r = (warp >> 2) * 4 + rr, h = h0 + r;
-      float acc[32];
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+      float acc[16];
       __syncwarp();  // the TMEM loads are warp-collective
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + r * 32, *reinterpret_cast<float(*)[16]>(acc));
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + r * 32 + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + r * 32 + half * 16, acc);
       if (h >= a.H || w >= a.W) continue;
       const size_t p = ((size_t)b * a.H + h) * a.W + w;
 #pragma unroll
-      for (int i0 = 0; i0 < NK; i0 += 2) {
-        const float2 a0 = make_float2(acc[i0], acc[i0 + 1]);
+      for (int e = 0; e < 16; e += 2) {
+        const int i0 = half * 16 + e;
+        if (i0 >= NK) break;
+        const float2 a0 = make_float2(acc[e], acc[e + 1]);
         if constexpr (ZIN) {  // a0 = K g; z from the forward stage
           const float2 z = *reinterpret_cast<const float2*>(a.z + p * NK + i0);
           const Rbf2 f = rbf_eval2(z, s_r + i0 * RBF_LD, s_r + (i0 + 1) * RBF_LD);
@@ -590,8 +617,8 @@ __global__ void __launch_bounds__(K_THREADS, 1) k_vn_K_tc(const KArgs a, const b
         }
       }
       // channels 24..31 of the stored activations are zero
-      uint4* pad = reinterpret_cast<uint4*>((ZIN ? a.v : a.u) + p * CU + NK);
-      pad[0] = make_uint4(0u, 0u, 0u, 0u);
+      if (half == 1) *reinterpret_cast<uint4*>((ZIN ? a.v : a.u) + p * CU + NK) = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
   }
   tc_fence_before();
@@ -962,7 +989,7 @@ void vn_pack(const float* prm, uint8_t* ws, const VnLayout& L, cudaStream_t st) 
   prof_mark("vn_misc", st, false);
   k_vn_pack<<<(n + 255) / 256, 256, 0, st>>>(prm, reinterpret_cast<bf16*>(ws + L.wk),
                                              reinterpret_cast<bf16*>(ws + L.wn));
-  const int ntc = KC_BROWS * KC_CHUNKS * 8;
+  const int ntc = KC_NBLK * 32 * KC_CHUNKS * 8;
   k_vn_pack_tc<<<(ntc + 255) / 256, 256, 0, st>>>(prm, reinterpret_cast<bf16*>(ws + L.wtc));
   prof_mark("vn_misc", st, true);
 }

@@ -165,6 +165,14 @@ class SensePlan:
             _ptr(v), _ptr(gl)))
         return v, gl
 
+    def normalize_max(self, x: torch.Tensor, other: torch.Tensor | None = None, scale: torch.Tensor | None = None):
+        """x_b /= max |x_b| per slice (in place), other_b likewise (Sec. 2.3.1 data scaling)."""
+        _req(x, "x", torch.complex64, self.img_shape())
+        if other is not None:
+            _req(other, "other", torch.complex64, self.img_shape())
+        self._sync_stream()
+        _lib.check("sense_normalize_max", self._lib.sense_normalize_max(self._h, _ptr(x), _ptr(other), _ptr(scale)))
+
     def status(self) -> int:
         v = C.c_int()
         _lib.check("sense_get_status", self._lib.sense_get_status(self._h, C.byref(v)))

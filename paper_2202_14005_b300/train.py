@@ -82,7 +82,8 @@ class RadialBatch:
     library's non-uniform DFT, noise at the samples, x^0 = A^H y by the non-uniform adjoint and a
     Toeplitz plan (the trajectory's PSF) for the normal operator."""
 
-    def __init__(self, host, traj, psf, noise_seed: int, sigma: float = 1e-3, device="cuda"):
+    def __init__(self, host, traj, psf, noise_seed: int, sigma: float = 1e-3, device="cuda",
+                 normalize: bool = False):
         import torch
         import synth
         from .sense import SensePlan, nudft_adjoint, nudft_forward
@@ -96,6 +97,10 @@ class RadialBatch:
         noise = synth.complex_noise((self.B, maps.shape[1], M), sigma, np.random.default_rng([11, noise_seed]))
         y = nudft_forward(traj, self.maps, self.gt) + torch.from_numpy(noise.astype(np.complex64)).to(device)
         self.AHy = nudft_adjoint(traj, self.maps, y)
+        if normalize:
+            # the data scaling of Sec. 2.3.1 (max |x^0| = 1 per slice), target scaled alike: without
+            # density compensation x^0 is far larger than x_gt (NRMSE is unchanged by the scaling)
+            self.plan.normalize_max(self.AHy, self.gt)
 
 
 def nrmse_per_slice(x, gt) -> np.ndarray:
