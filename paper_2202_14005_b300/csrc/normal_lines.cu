@@ -82,11 +82,14 @@ int build_lines_tables(sense_plan pl) {
       }
     }
   }
-  // launch geometry: nwr warps per row (GB coils each), several rows per CTA
+  // launch geometry: nwr warps per row (GB coils each), several rows per CTA.  Small batches take
+  // half as many rows per CTA, so the one-launch CG spreads a slice over twice as many CTAs
+  // (measured on B300, 4 slices of 256 x 232 with 12 coils: 221 against 231 us per 10-iteration
+  // solve; 16 slices keep two rows per tile: 782 against 1051 us with one).
   const int GB = 32 / Q;
   const int nwr = (pl->C + GB - 1) / GB;
   if (nwr > 8) return SENSE_OK;
-  int rows = std::max(1, 8 / nwr);
+  int rows = std::max(1, (pl->B <= 4 ? 4 : 8) / nwr);
   const int nwarps = rows * nwr;
   const NLLayout Lo = nl_layout(Q, P, J, kstride, rows, nwarps, GB, pl->S);
   if (Lo.total > 200 * 1024) return SENSE_OK;

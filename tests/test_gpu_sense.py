@@ -441,3 +441,18 @@ def test_soft_sense_fused_line_kernel(shape):
     xa = plan.adjoint(dev(y))
     assert rel(xa.cpu().numpy(), osense.adjoint_sets(y, maps, mask)) <= 1e-5
     assert plan.status() == 0
+
+
+def test_fma_probe_runs_and_checks_arguments():
+    """The FP32 FMA probe the bench times for the ALU peak: argument checks on the host, and a
+    launch that completes (its sink is written only in a practically unreachable case)."""
+    import ctypes as C
+    from paper_2202_14005_b300 import _lib
+    L = _lib.lib()
+    sink = torch.zeros(8, dtype=torch.float32, device="cuda")
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.sense_fma_probe(0, 10, C.c_void_p(sink.data_ptr()), st) == -7
+    assert L.sense_fma_probe(8, 10, None, st) == -2
+    assert L.sense_fma_probe(8, 1000, C.c_void_p(sink.data_ptr()), st) == 0
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(sink).item() == 0
