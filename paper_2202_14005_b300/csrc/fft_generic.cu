@@ -132,14 +132,21 @@ __device__ __forceinline__ int p2_swz(int i) {
   return L >= 16 ? (i ^ ((i >> 4) & 7)) : i;
 }
 
-template <int R, bool INV, int NS, int L>
+// ZHI: the upper half of the transform's input is zero (a zero-padded sequence): in the first
+// stage (NS = 1) input j + r L/R lies in the upper half exactly when r >= R/2, so those loads are
+// skipped.  HOUT: only the lower half of the output is used: in the last stage (NS R = L) output
+// k + r NS lies in the lower half exactly when r < R/2, so the other stores are skipped.
+template <int R, bool INV, int NS, int L, bool ZHI = false, bool HOUT = false>
 __device__ __forceinline__ void bfly_p2(const float2* in, float2* out, int j, const float2* tw) {
   constexpr int stride = L / R;
   constexpr bool SWZ_IN = NS > 1;       // written by an earlier stage
   constexpr bool SWZ_OUT = NS * R < L;  // read by a later stage
+  constexpr bool ZERO_HI = ZHI && NS == 1;
+  constexpr bool STORE_LO = HOUT && NS * R == L;
   float2 v[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = in[SWZ_IN ? p2_swz<L>(j + r * stride) : j + r * stride];
+  for (int r = 0; r < R; ++r)
+    v[r] = (ZERO_HI && 2 * r >= R) ? make_float2(0.f, 0.f) : in[SWZ_IN ? p2_swz<L>(j + r * stride) : j + r * stride];
   const int k = j & (NS - 1);
   if constexpr (NS > 1) {
     // one table load per butterfly: w^r for r >= 2 as products of w (at most three deep), so the
@@ -162,10 +169,11 @@ __device__ __forceinline__ void bfly_p2(const float2* in, float2* out, int j, co
   dft_pow2<R, INV>(v);
   const int idxD = (j / NS) * NS * R + k;
 #pragma unroll
-  for (int r = 0; r < R; ++r) out[SWZ_OUT ? p2_swz<L>(idxD + r * NS) : idxD + r * NS] = v[r];
+  for (int r = 0; r < R; ++r)
+    if (!STORE_LO || 2 * r < R) out[SWZ_OUT ? p2_swz<L>(idxD + r * NS) : idxD + r * NS] = v[r];
 }
 
-template <bool INV, int L, int NS>
+template <bool INV, int L, int NS, bool ZHI = false, bool HOUT = false>
 __device__ __forceinline__ float2* fft_p2(float2* a, float2* b, int ntr, const float2* tw, int ld) {
   if constexpr (NS >= L) {
     return a;
@@ -174,12 +182,25 @@ __device__ __forceinline__ float2* fft_p2(float2* a, float2* b, int ntr, const f
     constexpr int NB = L / R;
     for (int w = threadIdx.x; w < ntr * NB; w += blockDim.x) {
       const int tr = w / NB, j = w - tr * NB;
-      bfly_p2<R, INV, NS, L>(a + tr * ld, b + tr * ld, j, tw);
+      bfly_p2<R, INV, NS, L, ZHI, HOUT>(a + tr * ld, b + tr * ld, j, tw);
     }
     __syncthreads();
-    return fft_p2<INV, L, NS * R>(b, a, ntr, tw, ld);
+    return fft_p2<INV, L, NS * R, ZHI, HOUT>(b, a, ntr, tw, ld);
   }
 }
+
+// True where fft_smem_half takes a compile-time power-of-two plan (and so honours ZHI / HOUT).
+template <int CLS>
+__device__ __forceinline__ bool p2_plan(int L) {
+  return CLS == 0 && (L == 64 || L == 128 || L == 256 || L == 512 || L == 1024);
+}
+
+// fft_smem for a zero-padded input (ZHI: the upper half of every sequence is zero and need not
+// be stored) and/or a half-length result (HOUT: only the lower half is valid on return).  Lengths
+// without a compile-time plan fall back to the full transform: the caller then stores the zeros
+// and reads only the lower half.
+template <bool INV, int CLS, bool ZHI, bool HOUT>
+__device__ float2* fft_smem_half(float2* a, float2* b, int ntr, const Fft1DDev& f, int ld);
 
 // Transform ntr sequences of length L held in a at stride ld (>= L; ping-pong with b).  Column
 // passes use ld = L + 1: the transposing loads and stores of neighbouring columns then fall into
@@ -257,6 +278,21 @@ __device__ float2* fft_smem(float2* a, float2* b, int ntr, const Fft1DDev& f, in
     Ns *= R;
   }
   return a;
+}
+
+template <bool INV, int CLS, bool ZHI, bool HOUT>
+__device__ float2* fft_smem_half(float2* a, float2* b, int ntr, const Fft1DDev& f, int ld) {
+  if constexpr (CLS == 0) {
+    switch (f.L) {
+      case 64: return fft_p2<INV, 64, 1, ZHI, HOUT>(a, b, ntr, f.tw, ld);
+      case 128: return fft_p2<INV, 128, 1, ZHI, HOUT>(a, b, ntr, f.tw, ld);
+      case 256: return fft_p2<INV, 256, 1, ZHI, HOUT>(a, b, ntr, f.tw, ld);
+      case 512: return fft_p2<INV, 512, 1, ZHI, HOUT>(a, b, ntr, f.tw, ld);
+      case 1024: return fft_p2<INV, 1024, 1, ZHI, HOUT>(a, b, ntr, f.tw, ld);
+      default: break;
+    }
+  }
+  return fft_smem<INV, CLS>(a, b, ntr, f, ld);
 }
 
 __device__ __forceinline__ float pm1(int n) { return (n & 1) ? -1.f : 1.f; }
@@ -508,14 +544,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_fwd(int C, int H, int W
   const int bc = blockIdx.y, b = bc / C;
   const int h0 = blockIdx.x * kRows;
   const int nr = min(kRows, H - h0);
-  for (int i = threadIdx.x; i < nr * W2; i += blockDim.x) {
-    const int r = i / W2, w = i - r * W2, h = h0 + r;
+  // the zero half of each padded row is stored only for a transform without the pruned plan
+  const int wst = p2_plan<CLS>(W2) ? W : W2;
+  for (int i = threadIdx.x; i < nr * wst; i += blockDim.x) {
+    const int r = i / wst, w = i - r * wst, h = h0 + r;
     float2 v = make_float2(0.f, 0.f);
     if (w < W) v = cmul(maps[((size_t)bc * H + h) * W + w], x[((size_t)b * H + h) * W + w]);
-    a[i] = v;
+    a[r * W2 + w] = v;
   }
   __syncthreads();
-  float2* res = fft_smem<false, CLS>(a, bb, nr, f, W2);
+  float2* res = fft_smem_half<false, CLS, true, false>(a, bb, nr, f, W2);
   for (int i = threadIdx.x; i < nr * W2; i += blockDim.x)
     T[((size_t)bc * H + h0) * W2 + i] = res[i];
 }
@@ -531,14 +569,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_tp_cols(int H, int W2, float2* 
   const int w0 = blockIdx.x * kCols;
   const int nc = min(kCols, W2 - w0);
   const size_t base = (size_t)bc * H * W2;
-  for (int i = threadIdx.x; i < H2 * kCols; i += blockDim.x) {
+  const int hst = p2_plan<CLS>(H2) ? H : H2;  // rows H .. 2H - 1 are zero (stored only without the pruned plan)
+  for (int i = threadIdx.x; i < hst * kCols; i += blockDim.x) {
     const int h = i / kCols, cc = i - h * kCols;
     float2 v = make_float2(0.f, 0.f);
     if (cc < nc && h < H) v = T[base + (size_t)h * W2 + w0 + cc];
     a[cc * ld + h] = v;
   }
   __syncthreads();
-  float2* res = fft_smem<false, CLS>(a, bb, kCols, f, ld);
+  float2* res = fft_smem_half<false, CLS, true, false>(a, bb, kCols, f, ld);
   float2* other = (res == a) ? bb : a;
   for (int i = threadIdx.x; i < H2 * kCols; i += blockDim.x) {
     const int h = i / kCols, cc = i - h * kCols;  // psf_hat read along its rows
@@ -546,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tp_cols(int H, int W2, float2* 
     res[cc * ld + h] = cmul(res[cc * ld + h], ph);
   }
   __syncthreads();
-  res = fft_smem<true, CLS>(res, other, kCols, f, ld);
+  res = fft_smem_half<true, CLS, false, true>(res, other, kCols, f, ld);  // rows < H only
   for (int i = threadIdx.x; i < H * kCols; i += blockDim.x) {
     const int h = i / kCols, cc = i - h * kCols;
     if (cc < nc) T[base + (size_t)h * W2 + w0 + cc] = res[cc * ld + h];
@@ -585,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
     tp_cp_async_wait_all();
     __syncthreads();
     if (c + 1 < c1) fetch(c + 1, base + iq * bstride);
-    float2* res = fft_smem<true, CLS>(base + ip * bstride, base + is * bstride, nr, f, W2);
+    float2* res = fft_smem_half<true, CLS, false, true>(base + ip * bstride, base + is * bstride, nr, f, W2);
 #pragma unroll
     for (int e = 0; e < kMaxPer; ++e) {
       const int i = threadIdx.x + e * blockDim.x;  // output element (row r, column w < W)
