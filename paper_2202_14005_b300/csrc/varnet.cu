@@ -862,17 +862,19 @@ __global__ void __launch_bounds__(128) k_vn_wgrad(int B, int H, int W, const __n
 // shared-memory row of 31 accumulators (13-centre window by the product recurrence of
 // rbf_eval2); the ten rows of each filter are then added in order.
 constexpr int RG_Q = 10;
-constexpr int RG_LD = NW + 2;  // 33: distinct banks for the 32 lanes at equal j
 __global__ void __launch_bounds__(256) k_vn_rbfgrad(int B, int H, int W, const float* z, const float* kg,
                                                     float* partial) {
-  __shared__ float acc[NK * RG_Q * RG_LD];
+  // accumulator j of thread t at acc[j * 256 + t]: every thread keeps to its own bank whatever
+  // window its pixel's z selects (a thread-major layout put the lanes of a warp on banks that
+  // depend on z, and the read-modify-writes conflicted)
+  __shared__ float acc[NW * 256];
   const int t = threadIdx.x;
-  for (int k = t; k < NK * RG_Q * RG_LD; k += blockDim.x) acc[k] = 0.f;
+  for (int k = t; k < NW * 256; k += blockDim.x) acc[k] = 0.f;
   __syncthreads();
   const int b = blockIdx.x / H, h = blockIdx.x % H;
   if (t < NK * RG_Q) {
     const int i = t % NK, q = t / NK;
-    float* my = acc + t * RG_LD;
+    float* my = acc + t;
     for (int w = q; w < W; w += RG_Q) {
       const size_t p = ((size_t)b * H + h) * W + w;
       const float zz = z[p * NK + i], g = kg[p * NK + i];
@@ -882,7 +884,7 @@ __global__ void __launch_bounds__(256) k_vn_rbfgrad(int B, int H, int W, const f
       float rho = expf(d - 0.5f);
 #pragma unroll
       for (int k = 0; k < RBF_WIN; ++k) {
-        if ((unsigned)(j0 + k) < (unsigned)NW) my[j0 + k] += phi;
+        if ((unsigned)(j0 + k) < (unsigned)NW) my[(j0 + k) * 256] += phi;
         phi *= rho;
         rho *= kEinv;
       }
@@ -893,7 +895,7 @@ __global__ void __launch_bounds__(256) k_vn_rbfgrad(int B, int H, int W, const f
   for (int k = t; k < NK * NW; k += blockDim.x) {
     const int i = k / NW, j = k % NW;
     float s = 0.f;
-    for (int q = 0; q < RG_Q; ++q) s += acc[(q * NK + i) * RG_LD + j];
+    for (int q = 0; q < RG_Q; ++q) s += acc[j * 256 + q * NK + i];
     out[k] = s;
   }
 }
