@@ -28,7 +28,11 @@
  *     parts on three side streams the library creates per device on first
  *     use, forked from and joined back to the caller's stream with events, so
  *     their results are still ready in the caller's stream order (except where
- *     SENSE_VN_DEFER_JOIN says otherwise).
+ *     SENSE_VN_DEFER_JOIN says otherwise).  The side streams are shared by every
+ *     plan and call on the device: calls made at the same time from different
+ *     caller streams queue behind each other's side-stream work, and a stream
+ *     capture of such a call must not overlap library calls from other threads
+ *     on that device (their side-stream work would join the capture).
  *   - Return value: SENSE_OK (0) or a negative SENSE_E* code; host-side
  *     argument checks run before any launch, so an error leaves outputs
  *     untouched.  Device-side failures (CG breakdown, non-finite scalars) set
