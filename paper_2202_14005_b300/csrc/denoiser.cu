@@ -3,18 +3,24 @@
 // biases and ReLU between them; the complex image enters as two real channels.
 //
 // Activations are BF16, channels-last [B][H][W][64]; accumulation is FP32.
-// * 64 -> 64 layers (forward and input-gradient): implicit GEMM on the 5th-gen
-//   tensor cores.  One MMA tile is 128 consecutive output pixels of one image
-//   row (M = 128) by 64 channels (N = 64), K = 9 taps x 64 channels.  A TMA
-//   tensor copy brings the 3 x 130-pixel halo into shared memory grouped by
-//   8-channel chunks, so each tap is the same K-major operand at a shifted
+// * Layers with a 64-channel input (the 64 -> 64 layers, forward and input
+//   gradient; the 64 -> 2 last layer and the first layer's input gradient):
+//   implicit GEMM on the 5th-gen tensor cores (k_conv64).  One MMA tile is 128
+//   consecutive pixels of one image row (M = 128); K = 9 taps x 64 channels.  A
+//   TMA tensor copy brings the 3 x 130-pixel halo into shared memory with the
+//   128-byte swizzle, so each tap is the same K-major operand at a shifted
 //   start address; weights sit in shared memory K-major; the FP32 accumulator
 //   lives in tensor memory (two buffers, so the epilogue of one tile overlaps
-//   the MMAs of the next).  Epilogue: bias + ReLU (forward) or the ReLU mask of
-//   the layer input (input gradient), rounded to BF16.
-// * 2 -> 64 and 64 -> 2 layers and all weight gradients run on CUDA cores with
-//   FP32 accumulation; weight gradients are per-chunk partials reduced in a
-//   fixed order (deterministic) and added to the caller's FP32 buffer.
+//   the MMAs of the next).  N = 64 for the 64 -> 64 layers (epilogue: bias +
+//   ReLU, or the ReLU mask of the layer input, rounded to BF16); N = 16 with the
+//   three horizontal taps on the output side for the 64 -> 2 layers.
+// * Weight gradients of the 64 -> 64 layers: a contraction over pixels on the
+//   tensor cores (k_wgrad64, accumulators in tensor memory).
+// * The 2 -> 64 first layer and the last layer's input gradient: warp-level
+//   tensor cores (mma.sync, k_2to64); the weight gradients of the two
+//   2-channel layers: CUDA cores (k_wgrad_l1, k_wgrad_l5).  Every weight
+//   gradient is a set of per-chunk FP32 partials reduced in a fixed order
+//   (deterministic) and added to the caller's FP32 buffer.
 #include <cuda_bf16.h>
 
 #include <algorithm>
