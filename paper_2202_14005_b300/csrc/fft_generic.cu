@@ -592,6 +592,264 @@ __global__ void __launch_bounds__(kThreads, 3) k_tp_cols(int H, int W2, float2* 
   }
 }
 
+// ---------------------------------------- 512-point transforms held in registers
+// The Toeplitz passes along a length-512 axis (2H = 512 for the column pass, 2W = 512 for the
+// row passes) keep each sequence in the registers of 64 threads, 8 points each: 512 = 8 x 8 x 8,
+// three radix-8 stages with two exchanges through shared memory per transform (the generic
+// passes move every element through shared memory once per stage and twice more for the
+// transposing load and store).  Index digits, base 8, of one sequence (all sums over one digit
+// are 8-point DFTs in registers; w = e^{-2 pi i / 512}; thread t = lo + 8 hi of the sequence):
+//   forward, input n = 64 n1 + n2 (n1 < 4: the upper half is the zero padding):
+//     s1  t = n2:            Y[n2][k1]  = w^{n2 k1} sum_{n1} x[64 n1 + n2] w^{64 n1 k1}
+//     s2  t = m2 + 8 k1:     V[k1][m2][j1] = w^{8 m2 j1} sum_{m1} Y[8 m1 + m2][k1] w^{64 m1 j1}
+//     s3  t = j1 + 8 k1:     X[k1 + 8 j1 + 64 j2] = sum_{m2} V[k1][m2][j1] w^{64 m2 j2}
+//   inverse, in decimation-in-frequency order from the layout s3 leaves (k = d0 + 8 d1 + 64 d2,
+//   output n = e0 + 8 e1 + 64 e2; only e2 < 4, the first half, is formed):
+//     A   t = d1 + 8 d0:     U[d0][d1][e0] = w^{-8 d1 e0} sum_{d2} P[k] w^{-64 d2 e0}
+//     B   t = e0 + 8 d0:     Z[d0][e0][e1] = w^{-d0 (e0 + 8 e1)} sum_{d1} U[d0][d1][e0] w^{-64 d1 e1}
+//     C   t = e0 + 8 e1:     y[e0 + 8 e1 + 64 e2] = sum_{d0} Z[d0][e0][e1] w^{-64 d0 e2}
+// Shared layouts of Y, V (and U), Z per sequence: with the column pass's lanes (8 columns x 4
+// threads per warp, sequence stride 514 = 2 mod 16 float2) Y at 64 k1 + n2, V at
+// 64 a + 8 b + ((c + b) & 7) for [a][b][c], Z at e0 + 8 e1 + 64 d0; with the row passes' lanes
+// (32 threads of one row) the same with the rotations and flips that put the two values of hi
+// in a half-warp on different bank halves.  Either way the 16 lanes of every half-warp access 16
+// different bank pairs on every exchange.
+template <bool ROW>
+struct Lay512 {
+  static __device__ __forceinline__ int y(int n2, int k1) { return 64 * k1 + (ROW ? ((n2 + 8 * k1) & 63) : n2); }
+  static __device__ __forceinline__ int v(int a, int b, int c) {
+    return 64 * a + 8 * (ROW ? (b ^ (a & 1)) : b) + ((c + b) & 7);
+  }
+  static __device__ __forceinline__ int z(int d0, int e0, int e1) {
+    return e0 + 8 * (ROW ? (e1 ^ (d0 & 1)) : e1) + 64 * d0;
+  }
+};
+
+// 8-point DFT of (x0, x1, x2, x3, 0, 0, 0, 0): even outputs the 4-point DFT of x, odd outputs
+// the 4-point DFT of x_n e^{-/+ 2 pi i n / 8}.
+template <bool INV>
+__device__ __forceinline__ void dft8_lowhalf(float2 (&v)[8]) {
+  float2 e[4] = {v[0], v[1], v[2], v[3]};
+  float2 o[4] = {v[0], cmul_tw<INV>(v[1], 1, 8), cmul_tw<INV>(v[2], 2, 8), cmul_tw<INV>(v[3], 3, 8)};
+  dft_pow2<4, INV>(e);
+  dft_pow2<4, INV>(o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = e[k];
+    v[2 * k + 1] = o[k];
+  }
+}
+
+// Twiddles of the thread with index t = lo + 8 hi of its sequence, the same for every sequence:
+// slots 1 .. 7 w^{t j} (s1), 9 .. 15 w^{8 lo j} (s2 and, conjugated, A), 16 .. 23
+// w^{hi (lo + 8 e1)} (B); slots 0 and 8 hold 1.  A CTA fills the kTw512 x 64 table in shared
+// memory once (tw512_fill, all threads, then a barrier), slot-major: lanes with consecutive t
+// read consecutive entries, and the threads of sequences that share t the same entry.
+constexpr int kTw512 = 24;
+constexpr int kTwTab = 64 * kTw512;  // float2 per table
+__device__ __forceinline__ void tw512_fill(float2* tab, const float2* __restrict__ tw) {
+  for (int i = threadIdx.x; i < kTwTab; i += blockDim.x) {
+    const int s = i >> 6, t = i & 63, lo = t & 7, hi = t >> 3;
+    const int e = s < 8 ? t * s : (s < 16 ? 8 * lo * (s - 8) : hi * (lo + 8 * (s - 16)));
+    tab[i] = __ldg(tw + (e & 511));
+  }
+}
+// dst[addr(j)] = v[j] * w_j (CONJ: conj(w_j) * v[j]) with w_j table slot o + j of the thread
+// (tabt = tab + t), j = 0 .. 7, slot o skipped where it holds 1 (ONE0).
+template <bool CONJ, bool ONE0, typename Addr>
+__device__ __forceinline__ void tw512_apply(float2 (&v)[8], const float2* tabt, int o, float2* dst, Addr addr) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (ONE0 && j == 0) {
+      dst[addr(0)] = v[0];
+    } else {
+      const float2 w = tabt[64 * (o + j)];
+      dst[addr(j)] = CONJ ? cmulc(w, v[j]) : cmul(v[j], w);
+    }
+  }
+}
+
+// Forward transform of one zero-padded sequence.  Entry: v[n1] = x[64 n1 + t] for n1 < 4.
+// Exit: v[j2] = X[hi + 8 lo + 64 j2].  s0, s1: the sequence's two exchange buffers; tabt: the
+// thread's twiddle row.  Contains two __syncthreads.
+template <bool ROW>
+__device__ __forceinline__ void fwd512_zhi(float2 (&v)[8], float2* s0, float2* s1, int t, const float2* tabt) {
+  using L = Lay512<ROW>;
+  const int lo = t & 7, hi = t >> 3;
+  dft8_lowhalf<false>(v);
+  tw512_apply<false, true>(v, tabt, 0, s0, [&](int k1) { return L::y(t, k1); });
+  __syncthreads();
+#pragma unroll
+  for (int m1 = 0; m1 < 8; ++m1) v[m1] = s0[L::y(8 * m1 + lo, hi)];
+  dft_pow2<8, false>(v);
+  tw512_apply<false, true>(v, tabt, 8, s1, [&](int j1) { return L::v(hi, lo, j1); });
+  __syncthreads();
+#pragma unroll
+  for (int m2 = 0; m2 < 8; ++m2) v[m2] = s1[L::v(hi, m2, lo)];
+  dft_pow2<8, false>(v);
+}
+
+// Inverse transform, first half of the output.  Entry: v[d2] = P[hi + 8 lo + 64 d2].
+// Exit: v[e2] = y[t + 64 e2] for e2 < 4 (v[4..7] are not formed).  Contains two __syncthreads.
+template <bool ROW>
+__device__ __forceinline__ void inv512_hout(float2 (&v)[8], float2* s0, float2* s1, int t, const float2* tabt) {
+  using L = Lay512<ROW>;
+  const int lo = t & 7, hi = t >> 3;
+  dft_pow2<8, true>(v);
+  tw512_apply<true, true>(v, tabt, 8, s0, [&](int e0) { return L::v(hi, lo, e0); });
+  __syncthreads();
+#pragma unroll
+  for (int d1 = 0; d1 < 8; ++d1) v[d1] = s0[L::v(hi, d1, lo)];
+  dft_pow2<8, true>(v);
+  tw512_apply<true, false>(v, tabt, 16, s1, [&](int e1) { return L::z(hi, lo, e1); });  // w^{d0 (e0 + 8 e1)}
+  __syncthreads();
+#pragma unroll
+  for (int d0 = 0; d0 < 8; ++d0) v[d0] = s1[L::z(d0, lo, hi)];
+  dft_pow2<8, true>(v);
+}
+
+// Column pass for 2H = 512: T[:, kw] (rows < 256) = rows < 256 of IFFT(psf_hat[:, kw] FFT(T[:, kw]
+// padded)).  CTA (g, y) transforms columns 8 g .. 8 g + 7 of the coil images y kTpImages ..
+// (y + 1) kTpImages - 1 in turn; lanes run over the 8 columns first (row segments of 64 bytes),
+// and blockIdx.x fastest keeps the CTAs in flight on whole rows of a few images.  The group's
+// PSF columns (the same for every coil image) are read into shared memory once per CTA.
+constexpr int kC5 = 8;          // columns per CTA
+constexpr int kS5 = 514;        // exchange stride of one column (float2)
+constexpr int kTpImages = 8;    // coil images per CTA
+// exchange buffers, per-thread PSF slots (8 values), twiddle table
+int smem_cols512() { return (2 * kC5 * kS5 + 8 * 64 * kC5 + kTwTab) * (int)sizeof(float2); }
+
+__global__ void __launch_bounds__(64 * kC5, 2) k_tp_cols512(int BC, int W2, float2* __restrict__ T,
+                                                           const float2* __restrict__ tw,
+                                                           const float2* __restrict__ psf_hat) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int kT = 64 * kC5;
+  const int c = threadIdx.x & (kC5 - 1), t = threadIdx.x / kC5;
+  const int lo = t & 7, hi = t >> 3;
+  float2* const base = reinterpret_cast<float2*>(smem);
+  float2* tab = base + 2 * kC5 * kS5 + 8 * kT;
+  float2* s0 = base + c * kS5;
+  float2* s1 = s0 + kC5 * kS5;
+  float2* ps = base + 2 * kC5 * kS5 + threadIdx.x;  // PSF slot j at ps[kT j]
+  const float2* tabt = tab + t;
+  const int col = blockIdx.x * kC5 + c;
+  const bool live = col < W2;
+  const int bc0 = blockIdx.y * kTpImages, bc1 = min(BC, bc0 + kTpImages);
+  tw512_fill(tab, tw);
+#pragma unroll
+  for (int j2 = 0; j2 < 8; ++j2)  // this thread's PSF values: k = hi + 8 lo + 64 j2
+    ps[kT * j2] = live ? psf_hat[(size_t)(hi + 8 * lo + 64 * j2) * W2 + col] : make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int bc = bc0; bc < bc1; ++bc) {
+    float2* Tc = T + (size_t)bc * 256 * W2 + col;  // column col of image bc, rows < 256
+    float2 v[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) v[n1] = live ? Tc[(size_t)(t + 64 * n1) * W2] : make_float2(0.f, 0.f);
+    fwd512_zhi<false>(v, s0, s1, t, tabt);
+#pragma unroll
+    for (int j2 = 0; j2 < 8; ++j2) v[j2] = cmul(v[j2], ps[kT * j2]);
+    inv512_hout<false>(v, s0, s1, t, tabt);
+    if (live) {
+#pragma unroll
+      for (int e2 = 0; e2 < 4; ++e2) Tc[(size_t)(t + 64 * e2) * W2] = v[e2];
+    }
+  }
+}
+
+// Row passes for 2W = 512, 8 rows per CTA (64 threads each, lanes along the row).
+constexpr int kR5 = 8;
+int smem_rows512() { return (2 * kR5 * 512 + kTwTab) * (int)sizeof(float2); }
+
+// T[b,c,h,:] = FFT_512(S_c x [b,h,0..255], zero-padded).
+__global__ void __launch_bounds__(64 * kR5, 2) k_tp_rows_fwd512(int C, int H, const float2* __restrict__ x,
+                                                               const float2* __restrict__ maps,
+                                                               float2* __restrict__ T,
+                                                               const float2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int bc = blockIdx.y, b = bc / C;
+  const int h = blockIdx.x * kR5 + r;
+  const bool live = h < H;
+  float2* const base = reinterpret_cast<float2*>(smem);
+  float2* tab = base + 2 * kR5 * 512;
+  float2* s0 = base + r * 512;
+  float2* s1 = s0 + kR5 * 512;
+  const size_t mrow = ((size_t)bc * H + h) * 256, xrow = ((size_t)b * H + h) * 256;
+  tw512_fill(tab, tw);
+  float2 v[8];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1)
+    v[n1] = live ? cmul(maps[mrow + t + 64 * n1], x[xrow + t + 64 * n1]) : make_float2(0.f, 0.f);
+  __syncthreads();
+  fwd512_zhi<true>(v, s0, s1, t, tab + t);
+  if (live) {
+    float2* Tr = T + ((size_t)bc * H + h) * 512 + (t >> 3) + 8 * (t & 7);
+#pragma unroll
+    for (int j2 = 0; j2 < 8; ++j2) Tr[64 * j2] = v[j2];
+  }
+}
+
+// out[b,h,:] = sum_c conj(S_c) IFFT_512(T[b,c,h,:])[0..255] + lambda x, the coils of group
+// blockIdx.z (cpg < C: the partial sum goes to the first 256 entries of the rows of the group's
+// first coil, as in k_tp_rows_inv).  The next coil's row is loaded into registers while the
+// current one is transformed.
+__global__ void __launch_bounds__(64 * kR5, 2) k_tp_rows_inv512(int C, int H, float2* __restrict__ T,
+                                                               const float2* __restrict__ maps,
+                                                               float2* __restrict__ out,
+                                                               const float2* __restrict__ tw,
+                                                               const float2* __restrict__ xin, float lam_host,
+                                                               const double* __restrict__ lam_dev, int cpg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int b = blockIdx.y;
+  const int h = blockIdx.x * kR5 + r;
+  const bool live = h < H;
+  float2* const base = reinterpret_cast<float2*>(smem);
+  float2* tab = base + 2 * kR5 * 512;
+  float2* s0 = base + r * 512;
+  float2* s1 = s0 + kR5 * 512;
+  const float2* tabt = tab + t;
+  const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
+  tw512_fill(tab, tw);
+  const int kin = (t >> 3) + 8 * (t & 7);  // this thread's input index k = hi + 8 lo (+ 64 d2)
+  float2 nx[8], acc[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc[e] = make_float2(0.f, 0.f);
+  auto fetch = [&](int c) {
+    const float2* src = T + (((size_t)b * C + c) * H + h) * 512 + kin;
+#pragma unroll
+    for (int d2 = 0; d2 < 8; ++d2) nx[d2] = live ? src[64 * d2] : make_float2(0.f, 0.f);
+  };
+  fetch(c0);
+  __syncthreads();  // twiddle table
+  for (int c = c0; c < c1; ++c) {
+    float2 v[8];
+#pragma unroll
+    for (int d2 = 0; d2 < 8; ++d2) v[d2] = nx[d2];
+    if (c + 1 < c1) fetch(c + 1);
+    inv512_hout<true>(v, s0, s1, t, tabt);
+    if (live) {
+      const float2* sm = maps + (((size_t)b * C + c) * H + h) * 256 + t;
+#pragma unroll
+      for (int e2 = 0; e2 < 4; ++e2) acc[e2] = cfmac(sm[64 * e2], v[e2], acc[e2]);
+    }
+  }
+  if (!live) return;
+  if (cpg < C) {
+    float2* dst = T + (((size_t)b * C + c0) * H + h) * 512 + t;
+#pragma unroll
+    for (int e2 = 0; e2 < 4; ++e2) dst[64 * e2] = acc[e2];
+    return;
+  }
+  const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
+  const size_t o = ((size_t)b * H + h) * 256 + t;
+#pragma unroll
+  for (int e2 = 0; e2 < 4; ++e2) {
+    const float2 xv = xin[o + 64 * e2];
+    out[o + 64 * e2] = make_float2(fmaf(lam, xv.x, acc[e2].x), fmaf(lam, xv.y, acc[e2].y));
+  }
+}
+
 // With cpg < C, CTA z sums coils z cpg .. z cpg + cpg - 1 and writes that partial sum over the
 // first W entries of the rows of coil z cpg it has just read; k_coil_groups_sum (row stride 2W)
 // adds the groups in fixed order and + lambda x.  The rows of the next coil are copied into a
@@ -901,6 +1159,11 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
   return launch_row_combine(p, out, 2, x, lam_host, lam_dev);
 }
 
+// The register-resident passes serve a length-512 axis (their index digits are fixed): the
+// column pass 2H = 512, the row passes 2W = 512.
+bool use_cols512(sense_plan p) { return p->H == 256; }
+bool use_rows512(sense_plan p) { return p->W == 256; }
+
 int toeplitz_prepare(sense_plan p, const float2* psf) {
   const int H2 = 2 * p->H, W2 = 2 * p->W;
   if (kRows * W2 > kThreads * kMaxPer || kRows * p->W > kThreads * kMaxPer) return SENSE_EUNSUPPORTED;
@@ -908,6 +1171,14 @@ int toeplitz_prepare(sense_plan p, const float2* psf) {
   if (sr > 200 * 1024 || sc > 200 * 1024) return SENSE_EUNSUPPORTED;
   if (!SENSE_SET_SMEM(k_tp_rows_fwd, sr) || !SENSE_SET_SMEM(k_tp_rows_inv, smem_rows_inv(W2)) ||
       !SENSE_SET_SMEM(k_tp_psf_rows, sr) || !SENSE_SET_SMEM(k_tp_cols, sc) || !SENSE_SET_SMEM(k_tp_psf_cols, sc))
+    return SENSE_ECUDA;
+  if (use_cols512(p) && cudaFuncSetAttribute(k_tp_cols512, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_cols512()) != cudaSuccess)
+    return SENSE_ECUDA;
+  if (use_rows512(p) && (cudaFuncSetAttribute(k_tp_rows_fwd512, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem_rows512()) != cudaSuccess ||
+                         cudaFuncSetAttribute(k_tp_rows_inv512, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem_rows512()) != cudaSuccess))
     return SENSE_ECUDA;
   SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_psf_rows, (H2 + kRows - 1) / kRows, sr, p->stream, H2, psf,
                    p->psf_hat, dev(p->fW2));
@@ -919,22 +1190,40 @@ int toeplitz_prepare(sense_plan p, const float2* psf) {
 
 int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam_host, const double* lam_dev) {
   const int W2 = 2 * p->W;
-  const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
+  const bool rows512 = use_rows512(p);
   prof_mark("toeplitz", p->stream, false);
-  SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_fwd, gr, smem_rows(W2), p->stream, p->C, p->H, p->W, x, p->maps,
-                   p->w.T, dev(p->fW2));
-  const dim3 gc((W2 + kCols - 1) / kCols, p->B * p->C);
-  SENSE_LAUNCH_CLS(fft_class(p->fH2), k_tp_cols, gc, smem_cols(2 * p->H), p->stream, p->H, W2, p->w.T,
-                   dev(p->fH2), p->psf_hat);
-  // inverse rows and coil combine, the coils split into groups across grid.z (about 2048 CTAs)
-  const int nrb = (p->H + kRows - 1) / kRows;
-  int groups = (2048 + nrb * p->B - 1) / (nrb * p->B);
+  if (rows512) {
+    const dim3 gr((p->H + kR5 - 1) / kR5, p->B * p->C);
+    k_tp_rows_fwd512<<<gr, 64 * kR5, smem_rows512(), p->stream>>>(p->C, p->H, x, p->maps, p->w.T, p->fW2.tw);
+  } else {
+    const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
+    SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_fwd, gr, smem_rows(W2), p->stream, p->C, p->H, p->W, x, p->maps,
+                     p->w.T, dev(p->fW2));
+  }
+  if (use_cols512(p)) {
+    const dim3 gc((W2 + kC5 - 1) / kC5, (p->B * p->C + kTpImages - 1) / kTpImages);
+    k_tp_cols512<<<gc, 64 * kC5, smem_cols512(), p->stream>>>(p->B * p->C, W2, p->w.T, p->fH2.tw, p->psf_hat);
+  } else {
+    const dim3 gc((W2 + kCols - 1) / kCols, p->B * p->C);
+    SENSE_LAUNCH_CLS(fft_class(p->fH2), k_tp_cols, gc, smem_cols(2 * p->H), p->stream, p->H, W2, p->w.T,
+                     dev(p->fH2), p->psf_hat);
+  }
+  // inverse rows and coil combine, the coils split into groups across grid.z (about 2048 CTAs
+  // of 256 threads, or 1024 of 512 with the register-resident pass)
+  const int nrb = rows512 ? (p->H + kR5 - 1) / kR5 : (p->H + kRows - 1) / kRows;
+  const int target = rows512 ? 1024 : 2048;
+  int groups = (target + nrb * p->B - 1) / (nrb * p->B);
   groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
   const int cpg = (p->C + groups - 1) / groups;
   groups = (p->C + cpg - 1) / cpg;
   const dim3 gr2(nrb, p->B, groups);
-  SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows_inv(W2), p->stream, p->C, p->H, p->W, p->w.T,
-                   p->maps, out, dev(p->fW2), x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
+  if (rows512) {
+    k_tp_rows_inv512<<<gr2, 64 * kR5, smem_rows512(), p->stream>>>(p->C, p->H, p->w.T, p->maps, out, p->fW2.tw, x,
+                                                                    lam_host, lam_dev, groups > 1 ? cpg : p->C);
+  } else {
+    SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows_inv(W2), p->stream, p->C, p->H, p->W, p->w.T,
+                     p->maps, out, dev(p->fW2), x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
+  }
   if (groups > 1) {
     const long long n = (long long)p->B * p->H * p->W;
     const int grid = (int)std::min<long long>((n + 255) / 256, 2048LL);

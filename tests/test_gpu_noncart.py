@@ -91,6 +91,46 @@ def test_full_size_radial_workload_sampled():
     assert rel(out, onc.toeplitz_normal(x, maps, g, 0.0)) <= 1e-5
 
 
+def test_toeplitz_256_rows_ragged_columns():
+    """H = 256 takes the register-resident 512-point column pass; W = 250 leaves a last group of
+    4 of its 8 columns (2W = 500), and two slices with their own maps."""
+    from paper_2202_14005_b300.sense import SensePlan, toeplitz_psf
+    B, C, H, W = 2, 3, 256, 250
+    rng = np.random.default_rng(11)
+    maps = np.stack([synth.coil_maps(C, H, W, rng) for _ in range(B)]).astype(np.complex64)
+    traj = synth.radial_trajectory(40, 300, W).reshape(-1, 2).astype(np.float32)
+    psf = toeplitz_psf(dev(traj), H, W)
+    plan = SensePlan.toeplitz(dev(maps), psf)
+    x = synth.randn_complex((B, H, W), 4).astype(np.complex64)
+    out = plan.normal(dev(x), 0.3).cpu().numpy()
+    g = psf.cpu().numpy().astype(np.complex128)
+    ref = onc.toeplitz_normal(x, maps, g, 0.3)
+    for b in range(B):
+        assert rel(out[b], ref[b]) <= 1e-5
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("B,C,H,lam", [(2, 3, 100, 0.2), (32, 2, 256, 0.0)])
+def test_toeplitz_256_columns_row_passes(B, C, H, lam):
+    """W = 256 takes the register-resident 512-point row passes.  H = 100 leaves a last CTA with
+    4 of its 8 rows and splits the coils into groups (partial sums and the group sum); 32 slices
+    of 256 rows put all coils in one group (the combine and + lambda x in the row pass)."""
+    from paper_2202_14005_b300.sense import SensePlan, toeplitz_psf
+    W = 256
+    rng = np.random.default_rng(B + H)
+    maps = np.stack([synth.coil_maps(C, H, W, rng) for _ in range(B)]).astype(np.complex64)
+    traj = synth.radial_trajectory(32, 256, H).reshape(-1, 2).astype(np.float32)
+    psf = toeplitz_psf(dev(traj), H, W)
+    plan = SensePlan.toeplitz(dev(maps), psf)
+    x = synth.randn_complex((B, H, W), 5).astype(np.complex64)
+    out = plan.normal(dev(x), lam).cpu().numpy()
+    g = psf.cpu().numpy().astype(np.complex128)
+    ref = onc.toeplitz_normal(x, maps, g, lam)
+    for b in range(B):
+        assert rel(out[b], ref[b]) <= 1e-5
+    assert plan.status() == 0
+
+
 @pytest.mark.parametrize("B,C,N,spokes,samples", [(2, 3, 32, 16, 64), (1, 13, 40, 21, 48)])
 def test_nudft_pair_against_direct_sums(B, C, N, spokes, samples):
     """The GPU non-uniform DFT pair against the oracle's direct FP64 sums (1e-5; 13 coils
