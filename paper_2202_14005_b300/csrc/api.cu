@@ -202,6 +202,7 @@ int sense_plan_destroy(sense_plan p) {
   if (!p) return SENSE_EINVAL_PTR;
   free_lines_tables(p);
   if (p->own) cudaFree(p->own);
+  if (p->blue) cudaFree(p->blue);
   delete p;
   return SENSE_OK;
 }

@@ -920,6 +920,254 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
   }
 }
 
+// ------------------------------------ Bluestein row passes of the normal operator
+// A W-point DFT of a row (128 < W <= 256) as a 512-point circular convolution (Bluestein):
+// with the chirp c_n = e^{s pi i n^2 / W} (s = -1 forward, +1 inverse; n^2 reduced mod 2W in
+// integers on the host),
+//   X_k = c_k sum_n (x_n c_n) conj(c_{k-n}) = c_k IFFT_512(FFT_512(a) . Bh)_k,   k < W,
+// a = x c zero-padded to 512, Bh = FFT_512(b) / 512, b_m = conj(c_m) for |m| < W wrapped modulo
+// 512 (2W - 1 <= 512: the circular convolution does not alias into k < W).  Both transforms
+// are the register-resident ones above (input below 256, output below 256).  The plan's table
+// block (sense_plan_s::blue) holds the 512 roots, the two chirps [256] and the two spectra [512].
+constexpr int kBlueTw = 0, kBlueCf = 512, kBlueCi = 768, kBlueBf = 1024, kBlueBi = 1536, kBlueN = 2048;
+// exchange buffers, twiddle table, the pass's spectrum [512] and chirp [256]
+int smem_blue() { return (2 * kR5 * 512 + kTwTab + 512 + 256) * (int)sizeof(float2); }
+
+__device__ __forceinline__ void blue_tables(float2* bh, float2* ch, const float2* __restrict__ Bh,
+                                            const float2* __restrict__ chirp) {
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) bh[i] = __ldg(Bh + i);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) ch[i] = __ldg(chirp + i);
+}
+
+// T[b,c,h,k] = sum_n S_c x [b,h,n] e^{-2 pi i n k / W}  (the plain row DFT of the normal operator)
+__global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_fwd(int C, int H, int W, const float2* __restrict__ x,
+                                                              const float2* __restrict__ maps,
+                                                              float2* __restrict__ T,
+                                                              const float2* __restrict__ blue) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int bc = blockIdx.y, b = bc / C;
+  const int h = blockIdx.x * kR5 + r;
+  const bool live = h < H;
+  float2* const base = reinterpret_cast<float2*>(smem);
+  float2* s0 = base + r * 512;
+  float2* s1 = s0 + kR5 * 512;
+  float2* tab = base + 2 * kR5 * 512;
+  float2* bh = tab + kTwTab;
+  float2* ch = bh + 512;
+  tw512_fill(tab, blue + kBlueTw);
+  blue_tables(bh, ch, blue + kBlueBf, blue + kBlueCf);
+  const size_t row = ((size_t)bc * H + h) * W, xrow = ((size_t)b * H + h) * W;
+  float2 v[8];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    const int n = t + 64 * n1;
+    v[n1] = (live && n < W) ? cmul(maps[row + n], x[xrow + n]) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) v[n1] = cmul(v[n1], ch[t + 64 * n1]);
+  fwd512_zhi<true>(v, s0, s1, t, tab + t);
+  const int k0 = (t >> 3) + 8 * (t & 7);
+#pragma unroll
+  for (int j2 = 0; j2 < 8; ++j2) v[j2] = cmul(v[j2], bh[k0 + 64 * j2]);
+  inv512_hout<true>(v, s0, s1, t, tab + t);
+  if (live) {
+#pragma unroll
+    for (int e2 = 0; e2 < 4; ++e2) {
+      const int k = t + 64 * e2;
+      if (k < W) T[row + k] = cmul(v[e2], ch[k]);
+    }
+  }
+}
+
+// out[b,h,n] = sum_c conj(S_c) sum_k T[b,c,h,k] e^{+2 pi i n k / W} + lambda x over the coils of
+// group blockIdx.z (cpg < C: the partial sum goes to the row of the group's first coil in T, for
+// k_coil_groups_sum).  The next coil's row is loaded into registers while the current one is
+// transformed.
+__global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_inv(int C, int H, int W, float2* __restrict__ T,
+                                                              const float2* __restrict__ maps,
+                                                              float2* __restrict__ out,
+                                                              const float2* __restrict__ blue,
+                                                              const float2* __restrict__ xin, float lam_host,
+                                                              const double* __restrict__ lam_dev, int cpg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int b = blockIdx.y;
+  const int h = blockIdx.x * kR5 + r;
+  const bool live = h < H;
+  float2* const base = reinterpret_cast<float2*>(smem);
+  float2* s0 = base + r * 512;
+  float2* s1 = s0 + kR5 * 512;
+  float2* tab = base + 2 * kR5 * 512;
+  float2* bh = tab + kTwTab;
+  float2* ch = bh + 512;
+  const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
+  tw512_fill(tab, blue + kBlueTw);
+  blue_tables(bh, ch, blue + kBlueBi, blue + kBlueCi);
+  const int k0 = (t >> 3) + 8 * (t & 7);
+  float2 nx[4], acc[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc[e] = make_float2(0.f, 0.f);
+  auto fetch = [&](int c) {
+    const float2* src = T + (((size_t)b * C + c) * H + h) * W;
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      const int k = t + 64 * n1;
+      nx[n1] = (live && k < W) ? src[k] : make_float2(0.f, 0.f);
+    }
+  };
+  fetch(c0);
+  __syncthreads();  // tables
+  for (int c = c0; c < c1; ++c) {
+    float2 v[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) v[n1] = cmul(nx[n1], ch[t + 64 * n1]);
+    if (c + 1 < c1) fetch(c + 1);
+    fwd512_zhi<true>(v, s0, s1, t, tab + t);
+#pragma unroll
+    for (int j2 = 0; j2 < 8; ++j2) v[j2] = cmul(v[j2], bh[k0 + 64 * j2]);
+    inv512_hout<true>(v, s0, s1, t, tab + t);
+    if (live) {
+      const float2* sm = maps + (((size_t)b * C + c) * H + h) * W;
+#pragma unroll
+      for (int e2 = 0; e2 < 4; ++e2) {
+        const int n = t + 64 * e2;
+        if (n < W) acc[e2] = cfmac(sm[n], cmul(v[e2], ch[n]), acc[e2]);
+      }
+    }
+  }
+  if (!live) return;
+  if (cpg < C) {
+    float2* dst = T + (((size_t)b * C + c0) * H + h) * W;
+#pragma unroll
+    for (int e2 = 0; e2 < 4; ++e2) {
+      const int n = t + 64 * e2;
+      if (n < W) dst[n] = acc[e2];
+    }
+    return;
+  }
+  const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
+  const size_t o = ((size_t)b * H + h) * W;
+#pragma unroll
+  for (int e2 = 0; e2 < 4; ++e2) {
+    const int n = t + 64 * e2;
+    if (n < W) {
+      const float2 xv = xin[o + n];
+      out[o + n] = make_float2(fmaf(lam, xv.x, acc[e2].x), fmaf(lam, xv.y, acc[e2].y));
+    }
+  }
+}
+
+// ------------------------------------ column pass of the normal operator for H = 256
+// dst = IDFT_256(m2s . DFT_256(T[:, kw])) in place, the transforms held in registers: 32 threads
+// per column, 8 points each, 256 = 8 x 8 x 4, two shared exchanges per transform.  Digits
+// (w = e^{-2 pi i / 256}; thread t = lo + 4 hi of its column, lo < 4, hi < 8):
+//   forward, n = 32 n1 + n2:
+//     s1  t = n2:              Y[n2][k1] = w^{n2 k1} sum_{n1} x[32 n1 + n2] w^{32 n1 k1}
+//     s2  t = m2 + 4 k1:       V[k1][m2][j1] = w^{8 m2 j1} sum_{m1} Y[4 m1 + m2][k1] w^{32 m1 j1}
+//     s3  t = a + 4 k1, j1 in {a, a + 4}:  X[k1 + 8 j1 + 64 j2] = sum_{m2} V[k1][m2][j1] w^{64 m2 j2}
+//   the mask product where s3 leaves X; the inverse in decimation-in-frequency order from there
+//   (k = d0 + 8 d1 + 64 d2, n = e0 + 4 e1 + 32 e2):
+//     A   t = a + 4 d0, d1 in {a, a + 4}:  U[d0][d1][e0] = w^{-8 e0 d1} sum_{d2} P[k] w^{-64 d2 e0}
+//     B   t = e0 + 4 d0:       Z[d0][e0][e1] = w^{-d0 (e0 + 4 e1)} sum_{d1} U[d0][d1][e0] w^{-32 d1 e1}
+//     C   t = e0 + 4 e1:       y[e0 + 4 e1 + 32 e2] = sum_{d0} Z[d0][e0][e1] w^{-32 d0 e2}
+// Lanes run over 8 columns first; with the column stride 258 (2 mod 16) and the layouts of Y,
+// V, U, Z below, the 16 lanes of every half-warp access 16 different bank pairs.
+constexpr int kC6 = 8;           // columns per CTA
+constexpr int kS6 = 258;         // exchange stride of one column (float2)
+constexpr int kCol256Images = 4; // coil images per CTA
+constexpr int kTw256 = 32;       // twiddle slots per thread index
+// exchange buffers, twiddle table, per-thread mask slots (8 floats)
+int smem_col256() { return (2 * kC6 * kS6 + kTw256 * 32 + 4 * 32 * kC6) * (int)sizeof(float2); }
+
+__device__ __forceinline__ int l256_y(int n2, int k1) { return 32 * k1 + n2; }
+__device__ __forceinline__ int l256_v(int k1, int m2, int j1) { return 32 * k1 + 8 * m2 + ((j1 + m2) & 7); }
+__device__ __forceinline__ int l256_u(int d0, int d1, int e0) { return 32 * d0 + 4 * d1 + ((e0 + d1) & 3); }
+
+// slots: 0..7 w^{t k1}; 8..15 w^{8 lo j1}; 16 + 4 q + e0: w^{8 e0 (lo + 4 q)}; 24 + e1: w^{hi (lo + 4 e1)}
+__device__ __forceinline__ void tw256_fill(float2* tab, const float2* __restrict__ tw) {
+  for (int i = threadIdx.x; i < kTw256 * 32; i += blockDim.x) {
+    const int s = i >> 5, t = i & 31, lo = t & 3, hi = t >> 2;
+    int e;
+    if (s < 8) e = t * s;
+    else if (s < 16) e = 8 * lo * (s - 8);
+    else if (s < 24) e = 8 * ((s - 16) & 3) * (lo + 4 * ((s - 16) >> 2));
+    else e = hi * (lo + 4 * (s - 24));
+    tab[i] = __ldg(tw + (e & 255));
+  }
+}
+
+__global__ void __launch_bounds__(32 * kC6, 4) k_col256(int BC, int W, float2* __restrict__ T,
+                                                       const float2* __restrict__ tw,
+                                                       const float* __restrict__ m2s, int lines) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int c = threadIdx.x & (kC6 - 1), t = threadIdx.x / kC6;
+  const int lo = t & 3, hi = t >> 2;
+  float2* const base = reinterpret_cast<float2*>(smem);
+  float2* s0 = base + c * kS6;
+  float2* s1 = s0 + kC6 * kS6;
+  float2* tab = base + 2 * kC6 * kS6;
+  const float2* tt = tab + t;  // slot s at tt[32 s]
+  const int col = blockIdx.x * kC6 + c;
+  const bool live = col < W;
+  float* mk = reinterpret_cast<float*>(tab + kTw256 * 32) + threadIdx.x;  // slot 4 q + j2 at mk[32 kC6 (4 q + j2)]
+  tw256_fill(tab, tw);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)  // mask^2/(HW) at k = hi + 8 (lo + 4 q) + 64 j2
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2)
+      mk[32 * kC6 * (4 * q + j2)] =
+          live ? __ldg(m2s + (lines ? col : (size_t)(hi + 8 * (lo + 4 * q) + 64 * j2) * W + col)) : 0.f;
+  __syncthreads();
+  const int bc0 = blockIdx.y * kCol256Images, bc1 = min(BC, bc0 + kCol256Images);
+  for (int bc = bc0; bc < bc1; ++bc) {
+    float2* Tc = T + (size_t)bc * 256 * W + col;
+    float2 v[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = live ? Tc[(size_t)(t + 32 * n1) * W] : make_float2(0.f, 0.f);
+    dft_pow2<8, false>(v);
+    s0[l256_y(t, 0)] = v[0];
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) s0[l256_y(t, k1)] = cmul(v[k1], tt[32 * k1]);
+    __syncthreads();
+#pragma unroll
+    for (int m1 = 0; m1 < 8; ++m1) v[m1] = s0[l256_y(4 * m1 + lo, hi)];
+    dft_pow2<8, false>(v);
+    s1[l256_v(hi, lo, 0)] = v[0];
+#pragma unroll
+    for (int j1 = 1; j1 < 8; ++j1) s1[l256_v(hi, lo, j1)] = cmul(v[j1], tt[32 * (8 + j1)]);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float2 u[4];
+#pragma unroll
+      for (int m2 = 0; m2 < 4; ++m2) u[m2] = s1[l256_v(hi, m2, lo + 4 * q)];
+      dft_pow2<4, false>(u);
+#pragma unroll
+      for (int j2 = 0; j2 < 4; ++j2) u[j2] = cscale(u[j2], mk[32 * kC6 * (4 * q + j2)]);
+      dft_pow2<4, true>(u);
+      s0[l256_u(hi, lo + 4 * q, 0)] = u[0];
+#pragma unroll
+      for (int e0 = 1; e0 < 4; ++e0) s0[l256_u(hi, lo + 4 * q, e0)] = cmulc(tt[32 * (16 + 4 * q + e0)], u[e0]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d1 = 0; d1 < 8; ++d1) v[d1] = s0[l256_u(hi, d1, lo)];
+    dft_pow2<8, true>(v);
+#pragma unroll
+    for (int e1 = 0; e1 < 8; ++e1) s1[lo + 4 * e1 + 32 * hi] = cmulc(tt[32 * (24 + e1)], v[e1]);
+    __syncthreads();
+#pragma unroll
+    for (int d0 = 0; d0 < 8; ++d0) v[d0] = s1[t + 32 * d0];
+    dft_pow2<8, true>(v);
+    if (live) {
+#pragma unroll
+      for (int e2 = 0; e2 < 8; ++e2) Tc[(size_t)(t + 32 * e2) * W] = v[e2];
+    }
+  }
+}
+
 // psf_hat = FFT2(psf) / (4 H W): rows along 2W, then columns along 2H (in place, one array).
 template <int CLS>
 __global__ void __launch_bounds__(kThreads, 2) k_tp_psf_rows(int H2, const float2* psf, float2* out, Fft1DDev f) {
@@ -1065,6 +1313,58 @@ int build_fft1d(Fft1D& f, int L, std::vector<float2>& host_tw) {
   return SENSE_OK;
 }
 
+// Column pass of the normal operator over p->w.T [B][C][H][W]: IDFT_H(m2s . DFT_H), in place
+// (register-resident for H = 256, else the generic k_col; the map sets are already summed in T).
+bool use_col256(sense_plan p) { return p->H == 256 && !p->toep; }
+
+// The normal operator's row passes go through Bluestein's 512-point convolution where the
+// generic transform would need a radix above 7 (class 2) and 2W - 1 <= 512.
+bool use_blue(sense_plan p) { return p->S == 1 && !p->toep && p->W > 128 && p->W <= 256 && fft_class(p->fW) == 2; }
+
+// Bluestein tables (layout kBlue*), FP64 on the host with the phases reduced in integers.
+int blue_prepare(sense_plan p) {
+  const int W = p->W, L = 512;
+  std::vector<float2> h(kBlueN, make_float2(0.f, 0.f));
+  std::vector<double> rc(L), rs(L);
+  for (int m = 0; m < L; ++m) {
+    rc[m] = cos(2.0 * M_PI * m / L);
+    rs[m] = -sin(2.0 * M_PI * m / L);  // e^{-2 pi i m / L}
+  }
+  for (int m = 0; m < L; ++m) h[kBlueTw + m] = make_float2((float)rc[m], (float)rs[m]);
+  for (int si = 0; si < 2; ++si) {
+    const double sg = si == 0 ? -1.0 : 1.0;  // forward, inverse
+    std::vector<double> br(L, 0.0), bi(L, 0.0);
+    for (int n = 0; n < W; ++n) {
+      const double ang = M_PI * (double)(((long long)n * n) % (2 * W)) / W;  // pi n^2 / W
+      h[(si == 0 ? kBlueCf : kBlueCi) + n] = make_float2((float)cos(ang), (float)(sg * sin(ang)));
+      br[n] = cos(ang);        // b_n = conj(c_n)
+      bi[n] = -sg * sin(ang);
+      if (n > 0) {
+        br[L - n] = br[n];
+        bi[L - n] = bi[n];
+      }
+    }
+    for (int k = 0; k < L; ++k) {  // Bh_k = sum_m b_m e^{-2 pi i m k / L} / L
+      double xr = 0.0, xi = 0.0;
+      for (int m = 0; m < L; ++m) {
+        const int e = (int)(((long long)m * k) % L);
+        xr += br[m] * rc[e] - bi[m] * rs[e];
+        xi += br[m] * rs[e] + bi[m] * rc[e];
+      }
+      h[(si == 0 ? kBlueBf : kBlueBi) + k] = make_float2((float)(xr / L), (float)(xi / L));
+    }
+  }
+  if (cudaMalloc(&p->blue, kBlueN * sizeof(float2)) != cudaSuccess) {
+    p->blue = nullptr;
+    return SENSE_ECUDA;
+  }
+  if (cudaMemcpy(p->blue, h.data(), kBlueN * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaFuncSetAttribute(k_blue_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_blue()) != cudaSuccess ||
+      cudaFuncSetAttribute(k_blue_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_blue()) != cudaSuccess)
+    return SENSE_ECUDA;
+  return SENSE_OK;
+}
+
 int generic_prepare(sense_plan p) {
   if (kRows * p->W > kThreads * kMaxPer) return SENSE_EUNSUPPORTED;
   const int sr = smem_rows(p->W), sc = smem_cols(p->H);
@@ -1072,6 +1372,10 @@ int generic_prepare(sense_plan p) {
   if (!SENSE_SET_SMEM(k_row_expand, sr) || !SENSE_SET_SMEM(k_row_combine, smem_rows_inv(p->W)) ||
       !SENSE_SET_SMEM(k_col, sc))
     return SENSE_ECUDA;
+  if (use_col256(p) && cudaFuncSetAttribute(k_col256, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            smem_col256()) != cudaSuccess)
+    return SENSE_ECUDA;
+  if (use_blue(p)) return blue_prepare(p);
   return SENSE_OK;
 }
 
@@ -1142,18 +1446,55 @@ int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
   return launch_row_combine(p, x, 1, nullptr, 0.f, nullptr);
 }
 
+void launch_col_normal(sense_plan p) {
+  if (use_col256(p)) {
+    const dim3 gc((p->W + kC6 - 1) / kC6, (p->B * p->C + kCol256Images - 1) / kCol256Images);
+    k_col256<<<gc, 32 * kC6, smem_col256(), p->stream>>>(p->B * p->C, p->W, p->w.T, p->fH.tw, p->mask2s,
+                                                         p->mask_is_lines);
+    return;
+  }
+  const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
+  SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, p->w.T, p->w.T, dev(p->fH),
+                   p->mask2s, p->mask_is_lines, 2, nullptr, 0);
+}
+
+// Normal operator with the Bluestein row passes (use_blue): forward rows, the column
+// pass, inverse rows with the coil sum in groups across grid.z (about 1024 CTAs).
+int launch_normal_blue(sense_plan p, const float2* x, float2* out, float lam_host, const double* lam_dev) {
+  const int nrb = (p->H + kR5 - 1) / kR5;
+  prof_mark("fft_generic", p->stream, false);
+  k_blue_rows_fwd<<<dim3(nrb, p->B * p->C), 64 * kR5, smem_blue(), p->stream>>>(p->C, p->H, p->W, x, p->maps,
+                                                                                 p->w.T, p->blue);
+  launch_col_normal(p);
+  int groups = (1024 + nrb * p->B - 1) / (nrb * p->B);
+  groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
+  const int cpg = (p->C + groups - 1) / groups;
+  groups = (p->C + cpg - 1) / cpg;
+  k_blue_rows_inv<<<dim3(nrb, p->B, groups), 64 * kR5, smem_blue(), p->stream>>>(
+      p->C, p->H, p->W, p->w.T, p->maps, out, p->blue, x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
+  if (groups > 1) {
+    const long long n = (long long)p->B * p->H * p->W;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 2048LL);
+    k_coil_groups_sum<<<grid, 256, 0, p->stream>>>(p->B, p->C, p->H, p->W, p->W, cpg, p->w.T, x, lam_host,
+                                                    lam_dev, out);
+    count_launch(p, 1);
+  }
+  prof_mark("fft_generic", p->stream, true);
+  count_launch(p, 3);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
 int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
                           const double* lam_dev) {
   if (p->toep) return launch_normal_toeplitz(p, x, out, lam_host, lam_dev);
+  if (p->blue) return launch_normal_blue(p, x, out, lam_host, lam_dev);
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
   SENSE_LAUNCH_CLS(fft_class(p->fW), k_row_expand, gr, smem_rows(p->W), p->stream, p->B, p->S, p->C, p->H, x,
                    p->maps, p->w.T, dev(p->fW), 1);
   prof_mark("fft_generic", p->stream, true);
-  const dim3 gc((p->W + kCols - 1) / kCols, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);
-  SENSE_LAUNCH_CLS(fft_class(p->fH), k_col, gc, smem_cols(p->H), p->stream, p->W, p->w.T, p->w.T, dev(p->fH),
-                   p->mask2s, p->mask_is_lines, 2, nullptr, 0);
+  launch_col_normal(p);
   prof_mark("fft_generic", p->stream, true);
   count_launch(p, 2);
   return launch_row_combine(p, out, 2, x, lam_host, lam_dev);

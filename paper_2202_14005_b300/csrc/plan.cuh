@@ -72,6 +72,10 @@ struct sense_plan_s {
   int toep = 0;
   Fft1D fH2, fW2;
   float2* psf_hat = nullptr;
+  // Bluestein tables of the generic normal operator's row passes (128 < W <= 256 with a radix
+  // above 7, one map set; plan-owned, null otherwise): roots of the 512-point transforms | chirp
+  // e^{-pi i n^2/W} [256] | chirp e^{+pi i n^2/W} [256] | the two convolution spectra [512]
+  float2* blue = nullptr;
   int* status = nullptr;        // device status word (plan-owned)
   // bounded waits of the one-launch CG (sense_plan_set_wait_limit): polls of a per-slice
   // barrier before a CTA gives up, and arrivals added to every barrier (1 makes it unreachable)

@@ -65,6 +65,7 @@ NORMAL_CASES = [
     (2, 3, 6, 64, 2.0, 4),
     (1, 7, 12, 368, 4.0, 24),
     (2, 4, 16, 256, 4.0, 8),       # W = 16 * 16
+    (2, 3, 256, 174, 4.0, 8),      # no fused kernel for W = 174: Bluestein rows, 256-point columns
 ]
 
 
@@ -120,7 +121,11 @@ def test_normal_generic_paths(case):
     assert rel(host(out), osense.normal(x, maps, mask, 0.2)) <= TOL_OP
 
 
-@pytest.mark.parametrize("case", [(1, 4, 16, 20), (2, 3, 64, 64), (1, 5, 24, 232)])
+# W = 232 and 174 (radix 29) take the Bluestein row passes: one coil per group (B = 1), two
+# groups (16 slices of 256 rows, the bench shape), all coils in one group (32 slices), and a
+# last CTA with 4 of its 8 rows (H = 100)
+@pytest.mark.parametrize("case", [(1, 4, 16, 20), (2, 3, 64, 64), (1, 5, 24, 232), (16, 12, 256, 232),
+                                  (2, 3, 100, 174), (32, 2, 256, 174)])
 def test_normal_2d_mask(case):
     B, Cc, H, W = case
     maps, mask, x = make_problem(B, Cc, H, W, 3.0, 4, seed=5, lines=False)
@@ -257,9 +262,10 @@ def test_cg_solve_full_workload_256x232_b16():
     assert rel(host(x), xref) <= TOL_CG
 
 
-def test_cg_per_slice_lambda_zero_start_and_2d_mask():
-    maps, mask, _ = make_problem(3, 4, 16, 20, 3.0, 4, seed=21, lines=False)
-    rhs = c64(synth.randn_complex((3, 16, 20), 22))
+@pytest.mark.parametrize("H,W", [(16, 20), (40, 232)])
+def test_cg_per_slice_lambda_zero_start_and_2d_mask(H, W):
+    maps, mask, _ = make_problem(3, 4, H, W, 3.0, 4, seed=21, lines=False)
+    rhs = c64(synth.randn_complex((3, H, W), 22))
     lamv = np.array([0.01, 0.1, 1.0])
     plan = plan_for(maps, mask)
     x = plan.cg_solve(dev(rhs), torch.tensor(lamv, device="cuda"), 10)
