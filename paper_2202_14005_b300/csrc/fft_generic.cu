@@ -928,7 +928,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
 // a = x c zero-padded to 512, Bh = FFT_512(b) / 512, b_m = conj(c_m) for |m| < W wrapped modulo
 // 512 (2W - 1 <= 512: the circular convolution does not alias into k < W).  Both transforms
 // are the register-resident ones above (input below 256, output below 256).  The plan's table
-// block (sense_plan_s::blue) holds the 512 roots, the two chirps [256] and the two spectra [512].
+// block (sense_plan_s::blue) holds the 512 roots, the two chirps [256] and the two spectra [512],
+// each spectrum permuted so that the thread t holding k = hi + 8 lo + 64 j2 reads slot t + 64 j2.
 constexpr int kBlueTw = 0, kBlueCf = 512, kBlueCi = 768, kBlueBf = 1024, kBlueBi = 1536, kBlueN = 2048;
 // exchange buffers, twiddle table, the pass's spectrum [512] and chirp [256]
 int smem_blue() { return (2 * kR5 * 512 + kTwTab + 512 + 256) * (int)sizeof(float2); }
@@ -968,9 +969,8 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_fwd(int C, int H, int
 #pragma unroll
   for (int n1 = 0; n1 < 4; ++n1) v[n1] = cmul(v[n1], ch[t + 64 * n1]);
   fwd512_zhi<true>(v, s0, s1, t, tab + t);
-  const int k0 = (t >> 3) + 8 * (t & 7);
 #pragma unroll
-  for (int j2 = 0; j2 < 8; ++j2) v[j2] = cmul(v[j2], bh[k0 + 64 * j2]);
+  for (int j2 = 0; j2 < 8; ++j2) v[j2] = cmul(v[j2], bh[t + 64 * j2]);
   inv512_hout<true>(v, s0, s1, t, tab + t);
   if (live) {
 #pragma unroll
@@ -983,8 +983,7 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_fwd(int C, int H, int
 
 // out[b,h,n] = sum_c conj(S_c) sum_k T[b,c,h,k] e^{+2 pi i n k / W} + lambda x over the coils of
 // group blockIdx.z (cpg < C: the partial sum goes to the row of the group's first coil in T, for
-// k_coil_groups_sum).  The next coil's row is loaded into registers while the current one is
-// transformed.
+// k_coil_groups_sum).
 __global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_inv(int C, int H, int W, float2* __restrict__ T,
                                                               const float2* __restrict__ maps,
                                                               float2* __restrict__ out,
@@ -1005,7 +1004,6 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_inv(int C, int H, int
   const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
   tw512_fill(tab, blue + kBlueTw);
   blue_tables(bh, ch, blue + kBlueBi, blue + kBlueCi);
-  const int k0 = (t >> 3) + 8 * (t & 7);
   float2 nx[4], acc[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) acc[e] = make_float2(0.f, 0.f);
@@ -1017,16 +1015,15 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_inv(int C, int H, int
       nx[n1] = (live && k < W) ? src[k] : make_float2(0.f, 0.f);
     }
   };
-  fetch(c0);
   __syncthreads();  // tables
   for (int c = c0; c < c1; ++c) {
     float2 v[8];
+    fetch(c);
 #pragma unroll
     for (int n1 = 0; n1 < 4; ++n1) v[n1] = cmul(nx[n1], ch[t + 64 * n1]);
-    if (c + 1 < c1) fetch(c + 1);
     fwd512_zhi<true>(v, s0, s1, t, tab + t);
 #pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) v[j2] = cmul(v[j2], bh[k0 + 64 * j2]);
+    for (int j2 = 0; j2 < 8; ++j2) v[j2] = cmul(v[j2], bh[t + 64 * j2]);
     inv512_hout<true>(v, s0, s1, t, tab + t);
     if (live) {
       const float2* sm = maps + (((size_t)b * C + c) * H + h) * W;
@@ -1351,7 +1348,10 @@ int blue_prepare(sense_plan p) {
         xr += br[m] * rc[e] - bi[m] * rs[e];
         xi += br[m] * rs[e] + bi[m] * rc[e];
       }
-      h[(si == 0 ? kBlueBf : kBlueBi) + k] = make_float2((float)(xr / L), (float)(xi / L));
+      // stored at the index of the thread that reads it: thread t = lo + 8 hi holds
+      // k = hi + 8 lo + 64 j2 after the forward transform and reads slot t + 64 j2
+      const int j2 = k >> 6, hi = k & 7, lo = (k >> 3) & 7;
+      h[(si == 0 ? kBlueBf : kBlueBi) + lo + 8 * hi + 64 * j2] = make_float2((float)(xr / L), (float)(xi / L));
     }
   }
   if (cudaMalloc(&p->blue, kBlueN * sizeof(float2)) != cudaSuccess) {
