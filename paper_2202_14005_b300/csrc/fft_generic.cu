@@ -930,9 +930,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
 // are the register-resident ones above (input below 256, output below 256).  The plan's table
 // block (sense_plan_s::blue) holds the 512 roots, the two chirps [256] and the two spectra [512],
 // each spectrum permuted so that the thread t holding k = hi + 8 lo + 64 j2 reads slot t + 64 j2.
+constexpr int kRB = 4;  // rows per CTA (four 256-thread CTAs per SM)
 constexpr int kBlueTw = 0, kBlueCf = 512, kBlueCi = 768, kBlueBf = 1024, kBlueBi = 1536, kBlueN = 2048;
 // exchange buffers, twiddle table, the pass's spectrum [512] and chirp [256]
-int smem_blue() { return (2 * kR5 * 512 + kTwTab + 512 + 256) * (int)sizeof(float2); }
+int smem_blue() { return (2 * kRB * 512 + kTwTab + 512 + 256) * (int)sizeof(float2); }
 
 __device__ __forceinline__ void blue_tables(float2* bh, float2* ch, const float2* __restrict__ Bh,
                                             const float2* __restrict__ chirp) {
@@ -941,19 +942,19 @@ __device__ __forceinline__ void blue_tables(float2* bh, float2* ch, const float2
 }
 
 // T[b,c,h,k] = sum_n S_c x [b,h,n] e^{-2 pi i n k / W}  (the plain row DFT of the normal operator)
-__global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_fwd(int C, int H, int W, const float2* __restrict__ x,
+__global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_fwd(int C, int H, int W, const float2* __restrict__ x,
                                                               const float2* __restrict__ maps,
                                                               float2* __restrict__ T,
                                                               const float2* __restrict__ blue) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
   const int bc = blockIdx.y, b = bc / C;
-  const int h = blockIdx.x * kR5 + r;
+  const int h = blockIdx.x * kRB + r;
   const bool live = h < H;
   float2* const base = reinterpret_cast<float2*>(smem);
   float2* s0 = base + r * 512;
-  float2* s1 = s0 + kR5 * 512;
-  float2* tab = base + 2 * kR5 * 512;
+  float2* s1 = s0 + kRB * 512;
+  float2* tab = base + 2 * kRB * 512;
   float2* bh = tab + kTwTab;
   float2* ch = bh + 512;
   tw512_fill(tab, blue + kBlueTw);
@@ -984,7 +985,7 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_fwd(int C, int H, int
 // out[b,h,n] = sum_c conj(S_c) sum_k T[b,c,h,k] e^{+2 pi i n k / W} + lambda x over the coils of
 // group blockIdx.z (cpg < C: the partial sum goes to the row of the group's first coil in T, for
 // k_coil_groups_sum).
-__global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_inv(int C, int H, int W, float2* __restrict__ T,
+__global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_inv(int C, int H, int W, float2* __restrict__ T,
                                                               const float2* __restrict__ maps,
                                                               float2* __restrict__ out,
                                                               const float2* __restrict__ blue,
@@ -993,12 +994,12 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_blue_rows_inv(int C, int H, int
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
   const int b = blockIdx.y;
-  const int h = blockIdx.x * kR5 + r;
+  const int h = blockIdx.x * kRB + r;
   const bool live = h < H;
   float2* const base = reinterpret_cast<float2*>(smem);
   float2* s0 = base + r * 512;
-  float2* s1 = s0 + kR5 * 512;
-  float2* tab = base + 2 * kR5 * 512;
+  float2* s1 = s0 + kRB * 512;
+  float2* tab = base + 2 * kRB * 512;
   float2* bh = tab + kTwTab;
   float2* ch = bh + 512;
   const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
@@ -1461,16 +1462,16 @@ void launch_col_normal(sense_plan p) {
 // Normal operator with the Bluestein row passes (use_blue): forward rows, the column
 // pass, inverse rows with the coil sum in groups across grid.z (about 1024 CTAs).
 int launch_normal_blue(sense_plan p, const float2* x, float2* out, float lam_host, const double* lam_dev) {
-  const int nrb = (p->H + kR5 - 1) / kR5;
+  const int nrb = (p->H + kRB - 1) / kRB;
   prof_mark("fft_generic", p->stream, false);
-  k_blue_rows_fwd<<<dim3(nrb, p->B * p->C), 64 * kR5, smem_blue(), p->stream>>>(p->C, p->H, p->W, x, p->maps,
+  k_blue_rows_fwd<<<dim3(nrb, p->B * p->C), 64 * kRB, smem_blue(), p->stream>>>(p->C, p->H, p->W, x, p->maps,
                                                                                  p->w.T, p->blue);
   launch_col_normal(p);
   int groups = (1024 + nrb * p->B - 1) / (nrb * p->B);
   groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
   const int cpg = (p->C + groups - 1) / groups;
   groups = (p->C + cpg - 1) / cpg;
-  k_blue_rows_inv<<<dim3(nrb, p->B, groups), 64 * kR5, smem_blue(), p->stream>>>(
+  k_blue_rows_inv<<<dim3(nrb, p->B, groups), 64 * kRB, smem_blue(), p->stream>>>(
       p->C, p->H, p->W, p->w.T, p->maps, out, p->blue, x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
   if (groups > 1) {
     const long long n = (long long)p->B * p->H * p->W;
