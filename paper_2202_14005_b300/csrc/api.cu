@@ -203,6 +203,7 @@ int sense_plan_destroy(sense_plan p) {
   free_lines_tables(p);
   if (p->own) cudaFree(p->own);
   if (p->blue) cudaFree(p->blue);
+  if (p->twtab) cudaFree(p->twtab);
   delete p;
   return SENSE_OK;
 }

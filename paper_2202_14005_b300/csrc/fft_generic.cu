@@ -642,17 +642,21 @@ __device__ __forceinline__ void dft8_lowhalf(float2 (&v)[8]) {
 
 // Twiddles of the thread with index t = lo + 8 hi of its sequence, the same for every sequence:
 // slots 1 .. 7 w^{t j} (s1), 9 .. 15 w^{8 lo j} (s2 and, conjugated, A), 16 .. 23
-// w^{hi (lo + 8 e1)} (B); slots 0 and 8 hold 1.  A CTA fills the kTw512 x 64 table in shared
-// memory once (tw512_fill, all threads, then a barrier), slot-major: lanes with consecutive t
-// read consecutive entries, and the threads of sequences that share t the same entry.
+// w^{hi (lo + 8 e1)} (B); slots 0 and 8 hold 1.  The plan holds the kTw512 x 64 table,
+// slot-major (lanes with consecutive t read consecutive entries, the threads of sequences that
+// share t the same entry); a CTA copies it into shared memory once (tw_copy, then a barrier).
 constexpr int kTw512 = 24;
 constexpr int kTwTab = 64 * kTw512;  // float2 per table
-__device__ __forceinline__ void tw512_fill(float2* tab, const float2* __restrict__ tw) {
-  for (int i = threadIdx.x; i < kTwTab; i += blockDim.x) {
-    const int s = i >> 6, t = i & 63, lo = t & 7, hi = t >> 3;
-    const int e = s < 8 ? t * s : (s < 16 ? 8 * lo * (s - 8) : hi * (lo + 8 * (s - 16)));
-    tab[i] = __ldg(tw + (e & 511));
-  }
+// exponent of slot s of thread t, in units of 2 pi / 512
+SENSE_HD int tw512_exp(int s, int t) {
+  const int lo = t & 7, hi = t >> 3;
+  return (s < 8 ? t * s : (s < 16 ? 8 * lo * (s - 8) : hi * (lo + 8 * (s - 16)))) & 511;
+}
+// n float2 (n even, both addresses 16-byte aligned), all threads of the CTA
+__device__ __forceinline__ void tw_copy(float2* tab, const float2* __restrict__ g, int n) {
+  const float4* src = reinterpret_cast<const float4*>(g);
+  float4* dst = reinterpret_cast<float4*>(tab);
+  for (int i = threadIdx.x; i < n / 2; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 // dst[addr(j)] = v[j] * w_j (CONJ: conj(w_j) * v[j]) with w_j table slot o + j of the thread
 // (tabt = tab + t), j = 0 .. 7, slot o skipped where it holds 1 (ONE0).
@@ -735,7 +739,7 @@ __global__ void __launch_bounds__(64 * kC5, 2) k_tp_cols512(int BC, int W2, floa
   const int col = blockIdx.x * kC5 + c;
   const bool live = col < W2;
   const int bc0 = blockIdx.y * kTpImages, bc1 = min(BC, bc0 + kTpImages);
-  tw512_fill(tab, tw);
+  tw_copy(tab, tw, kTwTab);
 #pragma unroll
   for (int j2 = 0; j2 < 8; ++j2)  // this thread's PSF values: k = hi + 8 lo + 64 j2
     ps[kT * j2] = live ? psf_hat[(size_t)(hi + 8 * lo + 64 * j2) * W2 + col] : make_float2(0.f, 0.f);
@@ -775,7 +779,7 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_tp_rows_fwd512(int C, int H, co
   float2* s0 = base + r * 512;
   float2* s1 = s0 + kR5 * 512;
   const size_t mrow = ((size_t)bc * H + h) * 256, xrow = ((size_t)b * H + h) * 256;
-  tw512_fill(tab, tw);
+  tw_copy(tab, tw, kTwTab);
   float2 v[8];
 #pragma unroll
   for (int n1 = 0; n1 < 4; ++n1)
@@ -810,7 +814,7 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_tp_rows_inv512(int C, int H, fl
   float2* s1 = s0 + kR5 * 512;
   const float2* tabt = tab + t;
   const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
-  tw512_fill(tab, tw);
+  tw_copy(tab, tw, kTwTab);
   const int kin = (t >> 3) + 8 * (t & 7);  // this thread's input index k = hi + 8 lo (+ 64 d2)
   float2 nx[8], acc[4];
 #pragma unroll
@@ -928,10 +932,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_tp_rows_inv(int C, int H, int W
 // a = x c zero-padded to 512, Bh = FFT_512(b) / 512, b_m = conj(c_m) for |m| < W wrapped modulo
 // 512 (2W - 1 <= 512: the circular convolution does not alias into k < W).  Both transforms
 // are the register-resident ones above (input below 256, output below 256).  The plan's table
-// block (sense_plan_s::blue) holds the 512 roots, the two chirps [256] and the two spectra [512],
+// block (sense_plan_s::blue) holds the two chirps [256] and the two spectra [512],
 // each spectrum permuted so that the thread t holding k = hi + 8 lo + 64 j2 reads slot t + 64 j2.
 constexpr int kRB = 4;  // rows per CTA (four 256-thread CTAs per SM)
-constexpr int kBlueTw = 0, kBlueCf = 512, kBlueCi = 768, kBlueBf = 1024, kBlueBi = 1536, kBlueN = 2048;
+constexpr int kBlueCf = 0, kBlueCi = 256, kBlueBf = 512, kBlueBi = 1024, kBlueN = 1536;
 // exchange buffers, twiddle table, the pass's spectrum [512] and chirp [256]
 int smem_blue() { return (2 * kRB * 512 + kTwTab + 512 + 256) * (int)sizeof(float2); }
 
@@ -945,6 +949,7 @@ __device__ __forceinline__ void blue_tables(float2* bh, float2* ch, const float2
 __global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_fwd(int C, int H, int W, const float2* __restrict__ x,
                                                               const float2* __restrict__ maps,
                                                               float2* __restrict__ T,
+                                                              const float2* __restrict__ tw,
                                                               const float2* __restrict__ blue) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -957,7 +962,7 @@ __global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_fwd(int C, int H, int
   float2* tab = base + 2 * kRB * 512;
   float2* bh = tab + kTwTab;
   float2* ch = bh + 512;
-  tw512_fill(tab, blue + kBlueTw);
+  tw_copy(tab, tw, kTwTab);
   blue_tables(bh, ch, blue + kBlueBf, blue + kBlueCf);
   const size_t row = ((size_t)bc * H + h) * W, xrow = ((size_t)b * H + h) * W;
   float2 v[8];
@@ -988,6 +993,7 @@ __global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_fwd(int C, int H, int
 __global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_inv(int C, int H, int W, float2* __restrict__ T,
                                                               const float2* __restrict__ maps,
                                                               float2* __restrict__ out,
+                                                              const float2* __restrict__ tw,
                                                               const float2* __restrict__ blue,
                                                               const float2* __restrict__ xin, float lam_host,
                                                               const double* __restrict__ lam_dev, int cpg) {
@@ -1003,7 +1009,7 @@ __global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_inv(int C, int H, int
   float2* bh = tab + kTwTab;
   float2* ch = bh + 512;
   const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
-  tw512_fill(tab, blue + kBlueTw);
+  tw_copy(tab, tw, kTwTab);
   blue_tables(bh, ch, blue + kBlueBi, blue + kBlueCi);
   float2 nx[4], acc[4];
 #pragma unroll
@@ -1083,17 +1089,17 @@ __device__ __forceinline__ int l256_y(int n2, int k1) { return 32 * k1 + n2; }
 __device__ __forceinline__ int l256_v(int k1, int m2, int j1) { return 32 * k1 + 8 * m2 + ((j1 + m2) & 7); }
 __device__ __forceinline__ int l256_u(int d0, int d1, int e0) { return 32 * d0 + 4 * d1 + ((e0 + d1) & 3); }
 
-// slots: 0..7 w^{t k1}; 8..15 w^{8 lo j1}; 16 + 4 q + e0: w^{8 e0 (lo + 4 q)}; 24 + e1: w^{hi (lo + 4 e1)}
-__device__ __forceinline__ void tw256_fill(float2* tab, const float2* __restrict__ tw) {
-  for (int i = threadIdx.x; i < kTw256 * 32; i += blockDim.x) {
-    const int s = i >> 5, t = i & 31, lo = t & 3, hi = t >> 2;
-    int e;
-    if (s < 8) e = t * s;
-    else if (s < 16) e = 8 * lo * (s - 8);
-    else if (s < 24) e = 8 * ((s - 16) & 3) * (lo + 4 * ((s - 16) >> 2));
-    else e = hi * (lo + 4 * (s - 24));
-    tab[i] = __ldg(tw + (e & 255));
-  }
+// slots: 0..7 w^{t k1}; 8..15 w^{8 lo j1}; 16 + 4 q + e0: w^{8 e0 (lo + 4 q)}; 24 + e1:
+// w^{hi (lo + 4 e1)}; exponent of slot s of thread t in units of 2 pi / 256 (the plan holds the
+// table at sense_plan_s::twtab + kTwTab, slot-major)
+SENSE_HD int tw256_exp(int s, int t) {
+  const int lo = t & 3, hi = t >> 2;
+  int e;
+  if (s < 8) e = t * s;
+  else if (s < 16) e = 8 * lo * (s - 8);
+  else if (s < 24) e = 8 * ((s - 16) & 3) * (lo + 4 * ((s - 16) >> 2));
+  else e = hi * (lo + 4 * (s - 24));
+  return e & 255;
 }
 
 __global__ void __launch_bounds__(32 * kC6, 4) k_col256(int BC, int W, float2* __restrict__ T,
@@ -1110,7 +1116,7 @@ __global__ void __launch_bounds__(32 * kC6, 4) k_col256(int BC, int W, float2* _
   const int col = blockIdx.x * kC6 + c;
   const bool live = col < W;
   float* mk = reinterpret_cast<float*>(tab + kTw256 * 32) + threadIdx.x;  // slot 4 q + j2 at mk[32 kC6 (4 q + j2)]
-  tw256_fill(tab, tw);
+  tw_copy(tab, tw, kTw256 * 32);
 #pragma unroll
   for (int q = 0; q < 2; ++q)  // mask^2/(HW) at k = hi + 8 (lo + 4 q) + 64 j2
 #pragma unroll
@@ -1315,6 +1321,28 @@ int build_fft1d(Fft1D& f, int L, std::vector<float2>& host_tw) {
 // (register-resident for H = 256, else the generic k_col; the map sets are already summed in T).
 bool use_col256(sense_plan p) { return p->H == 256 && !p->toep; }
 
+// Per-thread-index twiddle tables of the register-resident transforms (slot-major, FP64 on the
+// host): the 512-point table at twtab, the 256-point one at twtab + kTwTab.
+int twtab_prepare(sense_plan p) {
+  if (p->twtab) return SENSE_OK;
+  std::vector<float2> h(kTwTab + kTw256 * 32);
+  for (int i = 0; i < kTwTab; ++i) {
+    const double a = -2.0 * M_PI * tw512_exp(i >> 6, i & 63) / 512.0;
+    h[i] = make_float2((float)cos(a), (float)sin(a));
+  }
+  for (int i = 0; i < kTw256 * 32; ++i) {
+    const double a = -2.0 * M_PI * tw256_exp(i >> 5, i & 31) / 256.0;
+    h[kTwTab + i] = make_float2((float)cos(a), (float)sin(a));
+  }
+  if (cudaMalloc(&p->twtab, h.size() * sizeof(float2)) != cudaSuccess) {
+    p->twtab = nullptr;
+    return SENSE_ECUDA;
+  }
+  return cudaMemcpy(p->twtab, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess
+             ? SENSE_OK
+             : SENSE_ECUDA;
+}
+
 // The normal operator's row passes go through Bluestein's 512-point convolution where the
 // generic transform would need a radix above 7 (class 2) and 2W - 1 <= 512.
 bool use_blue(sense_plan p) { return p->S == 1 && !p->toep && p->W > 128 && p->W <= 256 && fft_class(p->fW) == 2; }
@@ -1328,7 +1356,6 @@ int blue_prepare(sense_plan p) {
     rc[m] = cos(2.0 * M_PI * m / L);
     rs[m] = -sin(2.0 * M_PI * m / L);  // e^{-2 pi i m / L}
   }
-  for (int m = 0; m < L; ++m) h[kBlueTw + m] = make_float2((float)rc[m], (float)rs[m]);
   for (int si = 0; si < 2; ++si) {
     const double sg = si == 0 ? -1.0 : 1.0;  // forward, inverse
     std::vector<double> br(L, 0.0), bi(L, 0.0);
@@ -1376,6 +1403,8 @@ int generic_prepare(sense_plan p) {
   if (use_col256(p) && cudaFuncSetAttribute(k_col256, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             smem_col256()) != cudaSuccess)
     return SENSE_ECUDA;
+  if (use_col256(p) || use_blue(p))
+    if (int e = twtab_prepare(p)) return e;
   if (use_blue(p)) return blue_prepare(p);
   return SENSE_OK;
 }
@@ -1450,7 +1479,7 @@ int launch_adjoint_generic(sense_plan p, const float2* y, float2* x) {
 void launch_col_normal(sense_plan p) {
   if (use_col256(p)) {
     const dim3 gc((p->W + kC6 - 1) / kC6, (p->B * p->C + kCol256Images - 1) / kCol256Images);
-    k_col256<<<gc, 32 * kC6, smem_col256(), p->stream>>>(p->B * p->C, p->W, p->w.T, p->fH.tw, p->mask2s,
+    k_col256<<<gc, 32 * kC6, smem_col256(), p->stream>>>(p->B * p->C, p->W, p->w.T, p->twtab + kTwTab, p->mask2s,
                                                          p->mask_is_lines);
     return;
   }
@@ -1465,14 +1494,14 @@ int launch_normal_blue(sense_plan p, const float2* x, float2* out, float lam_hos
   const int nrb = (p->H + kRB - 1) / kRB;
   prof_mark("fft_generic", p->stream, false);
   k_blue_rows_fwd<<<dim3(nrb, p->B * p->C), 64 * kRB, smem_blue(), p->stream>>>(p->C, p->H, p->W, x, p->maps,
-                                                                                 p->w.T, p->blue);
+                                                                                 p->w.T, p->twtab, p->blue);
   launch_col_normal(p);
   int groups = (1024 + nrb * p->B - 1) / (nrb * p->B);
   groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
   const int cpg = (p->C + groups - 1) / groups;
   groups = (p->C + cpg - 1) / cpg;
   k_blue_rows_inv<<<dim3(nrb, p->B, groups), 64 * kRB, smem_blue(), p->stream>>>(
-      p->C, p->H, p->W, p->w.T, p->maps, out, p->blue, x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
+      p->C, p->H, p->W, p->w.T, p->maps, out, p->twtab, p->blue, x, lam_host, lam_dev, groups > 1 ? cpg : p->C);
   if (groups > 1) {
     const long long n = (long long)p->B * p->H * p->W;
     const int grid = (int)std::min<long long>((n + 255) / 256, 2048LL);
@@ -1517,6 +1546,8 @@ int toeplitz_prepare(sense_plan p, const float2* psf) {
   if (use_cols512(p) && cudaFuncSetAttribute(k_tp_cols512, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem_cols512()) != cudaSuccess)
     return SENSE_ECUDA;
+  if (use_cols512(p) || use_rows512(p))
+    if (int e = twtab_prepare(p)) return e;
   if (use_rows512(p) && (cudaFuncSetAttribute(k_tp_rows_fwd512, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               smem_rows512()) != cudaSuccess ||
                          cudaFuncSetAttribute(k_tp_rows_inv512, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1536,7 +1567,7 @@ int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam
   prof_mark("toeplitz", p->stream, false);
   if (rows512) {
     const dim3 gr((p->H + kR5 - 1) / kR5, p->B * p->C);
-    k_tp_rows_fwd512<<<gr, 64 * kR5, smem_rows512(), p->stream>>>(p->C, p->H, x, p->maps, p->w.T, p->fW2.tw);
+    k_tp_rows_fwd512<<<gr, 64 * kR5, smem_rows512(), p->stream>>>(p->C, p->H, x, p->maps, p->w.T, p->twtab);
   } else {
     const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
     SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_fwd, gr, smem_rows(W2), p->stream, p->C, p->H, p->W, x, p->maps,
@@ -1544,7 +1575,7 @@ int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam
   }
   if (use_cols512(p)) {
     const dim3 gc((W2 + kC5 - 1) / kC5, (p->B * p->C + kTpImages - 1) / kTpImages);
-    k_tp_cols512<<<gc, 64 * kC5, smem_cols512(), p->stream>>>(p->B * p->C, W2, p->w.T, p->fH2.tw, p->psf_hat);
+    k_tp_cols512<<<gc, 64 * kC5, smem_cols512(), p->stream>>>(p->B * p->C, W2, p->w.T, p->twtab, p->psf_hat);
   } else {
     const dim3 gc((W2 + kCols - 1) / kCols, p->B * p->C);
     SENSE_LAUNCH_CLS(fft_class(p->fH2), k_tp_cols, gc, smem_cols(2 * p->H), p->stream, p->H, W2, p->w.T,
@@ -1560,7 +1591,7 @@ int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam
   groups = (p->C + cpg - 1) / cpg;
   const dim3 gr2(nrb, p->B, groups);
   if (rows512) {
-    k_tp_rows_inv512<<<gr2, 64 * kR5, smem_rows512(), p->stream>>>(p->C, p->H, p->w.T, p->maps, out, p->fW2.tw, x,
+    k_tp_rows_inv512<<<gr2, 64 * kR5, smem_rows512(), p->stream>>>(p->C, p->H, p->w.T, p->maps, out, p->twtab, x,
                                                                     lam_host, lam_dev, groups > 1 ? cpg : p->C);
   } else {
     SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows_inv(W2), p->stream, p->C, p->H, p->W, p->w.T,

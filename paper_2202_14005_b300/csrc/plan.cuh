@@ -76,6 +76,9 @@ struct sense_plan_s {
   // above 7, one map set; plan-owned, null otherwise): roots of the 512-point transforms | chirp
   // e^{-pi i n^2/W} [256] | chirp e^{+pi i n^2/W} [256] | the two convolution spectra [512]
   float2* blue = nullptr;
+  // per-thread-index twiddle tables of the register-resident 512- and 256-point transforms
+  // (plan-owned, null where no such transform is used)
+  float2* twtab = nullptr;
   int* status = nullptr;        // device status word (plan-owned)
   // bounded waits of the one-launch CG (sense_plan_set_wait_limit): polls of a per-slice
   // barrier before a CTA gives up, and arrivals added to every barrier (1 makes it unreachable)
