@@ -1063,6 +1063,171 @@ __global__ void __launch_bounds__(64 * kRB, 4) k_blue_rows_inv(int C, int H, int
   }
 }
 
+// ------------------------------------ direct row passes for W = 8 P (P prime, 17 <= P <= 31)
+// A row of W = 8 P points per warp.  With n = t + P n1 and k = k1 + 8 k2 (w = e^{-2 pi i / W}):
+//   forward   X[k1 + 8 k2] = sum_t w_P^{t k2} Y[k1][t],  Y[k1][t] = w^{t k1} sum_{n1} x[t + P n1] w_8^{n1 k1}
+//   inverse   x[t + P n1] = sum_{k1} w_8^{-n1 k1} Z[k1][t],  Z[k1][t] = w^{-t k1} sum_{k2} X[k1 + 8 k2] w_P^{-t k2}
+// The 8-point DFTs run in registers (lane t < P); the P-point DFTs are direct sums over the
+// conjugate pairs (t, P - t), S = a_t + a_{P-t}, D = a_t - a_{P-t}:
+//   sum_t a_t w_P^{+-t k} = a_0 + sum_{t <= (P-1)/2} (S cos(2 pi t k / P) -+ i D sin(2 pi t k / P))
+// so one cosine and sine give the outputs k and P - k.  Lane (k1 = lane & 7, g = lane >> 3)
+// takes the output pairs g, g + 4, g + 8, ... <= (P-1)/2 of residue k1 (pair 0 is the single
+// output 0).  Each lane keeps t k mod P incrementally and reads cos, sin from a P-entry table.
+constexpr int kR8Rows = 8;  // rows (warps) per CTA
+template <int P>
+int smem_r8p() { return (32 + kR8Rows * 16 * P) * (int)sizeof(float2); }
+
+// (cos, sin)(2 pi m / P) from the plan's W-point roots e^{-2 pi i m / W} at m 8.
+template <int P>
+__device__ __forceinline__ void r8p_cs(float2* cs, const float2* __restrict__ tw) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const float2 w = __ldg(tw + 8 * i);
+    cs[i] = make_float2(w.x, -w.y);
+  }
+}
+
+// P-point sums of one residue k1 over the pairs of this lane: za[q] = sum_t S_t cos - s D_t sin
+// (SIGN = -1: forward; +1: inverse, i D s with the opposite sign), zb[q] the partner output P - k.
+// get(t) returns a_t of the residue.
+template <int P, int SIGN, typename Get>
+__device__ __forceinline__ void r8p_pairs(int g, const float2* cs, Get get, float2 (&za)[4], float2 (&zb)[4]) {
+  constexpr int HP = (P - 1) / 2;
+  int m[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    za[q] = zb[q] = make_float2(0.f, 0.f);
+    m[q] = 0;
+  }
+#pragma unroll 2
+  for (int t = 1; t <= HP; ++t) {
+    const float2 a = get(t), b = get(P - t);
+    const float2 S = cadd(a, b), D = csub(a, b);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int it = g + 4 * q;  // pair index; t it mod P kept in m[q]
+      m[q] += it;
+      if (m[q] >= P) m[q] -= P;
+      const float2 w = cs[it <= HP ? m[q] : 0];
+      // forward: S c - i D s = (S.x c + D.y s, S.y c - D.x s); inverse: S c + i D s
+      const float sy = SIGN < 0 ? D.y * w.y : -D.y * w.y, sx = SIGN < 0 ? -D.x * w.y : D.x * w.y;
+      za[q].x = fmaf(S.x, w.x, za[q].x + sy);
+      za[q].y = fmaf(S.y, w.x, za[q].y + sx);
+      zb[q].x = fmaf(S.x, w.x, zb[q].x - sy);
+      zb[q].y = fmaf(S.y, w.x, zb[q].y - sx);
+    }
+  }
+}
+
+// T[b,c,h,k] = sum_n S_c x [b,h,n] e^{-2 pi i n k / W}  (the plain row DFT of the normal operator)
+template <int P>
+__global__ void __launch_bounds__(32 * kR8Rows, 4) k_r8p_fwd(int C, int H, const float2* __restrict__ x,
+                                                            const float2* __restrict__ maps,
+                                                            float2* __restrict__ T,
+                                                            const float2* __restrict__ tw) {
+  constexpr int W = 8 * P, HP = (P - 1) / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* cs = reinterpret_cast<float2*>(smem);
+  float2* Y = cs + 32 + warp * 16 * P;  // [8][P]
+  r8p_cs<P>(cs, tw);
+  __syncthreads();
+  const int bc = blockIdx.y, b = bc / C, h = blockIdx.x * kR8Rows + warp;
+  if (h >= H) return;  // whole warp, after the only CTA barrier
+  const size_t row = ((size_t)bc * H + h) * W, xrow = ((size_t)b * H + h) * W;
+  if (lane < P) {
+    float2 v[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = cmul(maps[row + lane + P * n1], x[xrow + lane + P * n1]);
+    dft_pow2<8, false>(v);
+    Y[lane] = v[0];
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) Y[k1 * P + lane] = cmul(v[k1], __ldg(tw + lane * k1));
+  }
+  __syncwarp();
+  const int k1 = lane & 7, g = lane >> 3;
+  const float2* Yk = Y + k1 * P;
+  float2 za[4], zb[4];
+  r8p_pairs<P, -1>(g, cs, [&](int t) { return Yk[t]; }, za, zb);
+  const float2 y0 = Yk[0];
+  float2* Tr = T + row + k1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int it = g + 4 * q;
+    if (it <= HP) {
+      Tr[8 * it] = cadd(y0, za[q]);
+      if (it > 0) Tr[8 * (P - it)] = cadd(y0, zb[q]);
+    }
+  }
+}
+
+// out[b,h,n] = sum_c conj(S_c) sum_k T[b,c,h,k] e^{+2 pi i n k / W} + lambda x over the coils of
+// group blockIdx.z (cpg < C: the partial sum goes to the row of the group's first coil in T, for
+// k_coil_groups_sum).
+template <int P>
+__global__ void __launch_bounds__(32 * kR8Rows, 4) k_r8p_inv(int C, int H, float2* __restrict__ T,
+                                                            const float2* __restrict__ maps,
+                                                            float2* __restrict__ out,
+                                                            const float2* __restrict__ tw,
+                                                            const float2* __restrict__ xin, float lam_host,
+                                                            const double* __restrict__ lam_dev, int cpg) {
+  constexpr int W = 8 * P, HP = (P - 1) / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* cs = reinterpret_cast<float2*>(smem);
+  float2* R = cs + 32 + warp * 16 * P;  // the coil's row [W]
+  float2* Z = R + W;                    // [8][P]
+  r8p_cs<P>(cs, tw);
+  __syncthreads();
+  const int b = blockIdx.y, h = blockIdx.x * kR8Rows + warp;
+  if (h >= H) return;  // whole warp, after the only CTA barrier
+  const int c0 = blockIdx.z * cpg, c1 = min(C, c0 + cpg);
+  const int k1 = lane & 7, g = lane >> 3;
+  float2 acc[8];
+#pragma unroll
+  for (int n1 = 0; n1 < 8; ++n1) acc[n1] = make_float2(0.f, 0.f);
+  for (int c = c0; c < c1; ++c) {
+    const size_t row = (((size_t)b * C + c) * H + h) * W;
+    for (int i = lane; i < W; i += 32) R[i] = T[row + i];
+    __syncwarp();
+    float2 za[4], zb[4];
+    r8p_pairs<P, 1>(g, cs, [&](int k2) { return R[k1 + 8 * k2]; }, za, zb);
+    const float2 x0 = R[k1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int it = g + 4 * q;
+      if (it <= HP) {
+        Z[k1 * P + it] = cmulc(__ldg(tw + it * k1), cadd(x0, za[q]));
+        if (it > 0) Z[k1 * P + P - it] = cmulc(__ldg(tw + (P - it) * k1), cadd(x0, zb[q]));
+      }
+    }
+    __syncwarp();
+    if (lane < P) {
+      float2 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = Z[j * P + lane];
+      dft_pow2<8, true>(v);
+      const float2* sm = maps + row + lane;
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) acc[n1] = cfmac(sm[P * n1], v[n1], acc[n1]);
+    }
+    __syncwarp();
+  }
+  if (lane >= P) return;
+  if (cpg < C) {
+    float2* dst = T + (((size_t)b * C + c0) * H + h) * W + lane;
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) dst[P * n1] = acc[n1];
+    return;
+  }
+  const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
+  const size_t o = ((size_t)b * H + h) * W + lane;
+#pragma unroll
+  for (int n1 = 0; n1 < 8; ++n1) {
+    const float2 xv = xin[o + P * n1];
+    out[o + P * n1] = make_float2(fmaf(lam, xv.x, acc[n1].x), fmaf(lam, xv.y, acc[n1].y));
+  }
+}
+
 // ------------------------------------ column pass of the normal operator for H = 256
 // dst = IDFT_256(m2s . DFT_256(T[:, kw])) in place, the transforms held in registers: 32 threads
 // per column, 8 points each, 256 = 8 x 8 x 4, two shared exchanges per transform.  Digits
@@ -1343,9 +1508,39 @@ int twtab_prepare(sense_plan p) {
              : SENSE_ECUDA;
 }
 
-// The normal operator's row passes go through Bluestein's 512-point convolution where the
-// generic transform would need a radix above 7 (class 2) and 2W - 1 <= 512.
-bool use_blue(sense_plan p) { return p->S == 1 && !p->toep && p->W > 128 && p->W <= 256 && fft_class(p->fW) == 2; }
+// The normal operator's row passes are direct for W = 8 P (P prime, 17 .. 31); else they go
+// through Bluestein's 512-point convolution where the generic transform would need a radix
+// above 7 (class 2) and 2W - 1 <= 512.
+int r8p_of(sense_plan p) {
+  if (p->S != 1 || p->toep || p->W % 8) return 0;
+  const int P = p->W / 8;
+  return (P == 17 || P == 19 || P == 23 || P == 29 || P == 31) ? P : 0;
+}
+bool use_blue(sense_plan p) {
+  return !r8p_of(p) && p->S == 1 && !p->toep && p->W > 128 && p->W <= 256 && fft_class(p->fW) == 2;
+}
+
+#define SENSE_R8P_SWITCH(P, ...)                              \
+  switch (P) {                                                 \
+    case 17: { constexpr int kP = 17; __VA_ARGS__; } break;    \
+    case 19: { constexpr int kP = 19; __VA_ARGS__; } break;    \
+    case 23: { constexpr int kP = 23; __VA_ARGS__; } break;    \
+    case 29: { constexpr int kP = 29; __VA_ARGS__; } break;    \
+    case 31: { constexpr int kP = 31; __VA_ARGS__; } break;    \
+    default: break;                                            \
+  }
+
+int r8p_prepare(sense_plan p) {
+  const int P = r8p_of(p);
+  bool ok = true;
+  SENSE_R8P_SWITCH(P, ok = cudaFuncSetAttribute(k_r8p_fwd<kP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                smem_r8p<kP>()) == cudaSuccess &&
+                           cudaFuncSetAttribute(k_r8p_inv<kP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                smem_r8p<kP>()) == cudaSuccess)
+  if (!ok) return SENSE_ECUDA;
+  p->r8p = P;
+  return SENSE_OK;
+}
 
 // Bluestein tables (layout kBlue*), FP64 on the host with the phases reduced in integers.
 int blue_prepare(sense_plan p) {
@@ -1405,6 +1600,7 @@ int generic_prepare(sense_plan p) {
     return SENSE_ECUDA;
   if (use_col256(p) || use_blue(p))
     if (int e = twtab_prepare(p)) return e;
+  if (r8p_of(p)) return r8p_prepare(p);
   if (use_blue(p)) return blue_prepare(p);
   return SENSE_OK;
 }
@@ -1514,9 +1710,38 @@ int launch_normal_blue(sense_plan p, const float2* x, float2* out, float lam_hos
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
+// Normal operator with the direct W = 8 P row passes: forward rows, the column pass, inverse rows
+// with the coil sum in groups across grid.z (about 1024 CTAs).
+int launch_normal_r8p(sense_plan p, const float2* x, float2* out, float lam_host, const double* lam_dev) {
+  const int nrb = (p->H + kR8Rows - 1) / kR8Rows;
+  int groups = (1024 + nrb * p->B - 1) / (nrb * p->B);
+  groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
+  const int cpg = (p->C + groups - 1) / groups;
+  groups = (p->C + cpg - 1) / cpg;
+  prof_mark("fft_generic", p->stream, false);
+  SENSE_R8P_SWITCH(p->r8p,
+    k_r8p_fwd<kP><<<dim3(nrb, p->B * p->C), 32 * kR8Rows, smem_r8p<kP>(), p->stream>>>(p->C, p->H, x, p->maps,
+                                                                                       p->w.T, p->fW.tw))
+  launch_col_normal(p);
+  SENSE_R8P_SWITCH(p->r8p,
+    k_r8p_inv<kP><<<dim3(nrb, p->B, groups), 32 * kR8Rows, smem_r8p<kP>(), p->stream>>>(
+        p->C, p->H, p->w.T, p->maps, out, p->fW.tw, x, lam_host, lam_dev, groups > 1 ? cpg : p->C))
+  if (groups > 1) {
+    const long long n = (long long)p->B * p->H * p->W;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 2048LL);
+    k_coil_groups_sum<<<grid, 256, 0, p->stream>>>(p->B, p->C, p->H, p->W, p->W, cpg, p->w.T, x, lam_host,
+                                                    lam_dev, out);
+    count_launch(p, 1);
+  }
+  prof_mark("fft_generic", p->stream, true);
+  count_launch(p, 3);
+  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+}
+
 int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
                           const double* lam_dev) {
   if (p->toep) return launch_normal_toeplitz(p, x, out, lam_host, lam_dev);
+  if (p->r8p) return launch_normal_r8p(p, x, out, lam_host, lam_dev);
   if (p->blue) return launch_normal_blue(p, x, out, lam_host, lam_dev);
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
   prof_mark("fft_generic", p->stream, false);

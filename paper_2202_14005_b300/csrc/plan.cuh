@@ -79,6 +79,9 @@ struct sense_plan_s {
   // per-thread-index twiddle tables of the register-resident 512- and 256-point transforms
   // (plan-owned, null where no such transform is used)
   float2* twtab = nullptr;
+  // P of the direct row passes of the generic normal operator (W = 8 P, P prime 17 .. 31, one map
+  // set); 0 where they are not used
+  int r8p = 0;
   int* status = nullptr;        // device status word (plan-owned)
   // bounded waits of the one-launch CG (sense_plan_set_wait_limit): polls of a per-slice
   // barrier before a CTA gives up, and arrivals added to every barrier (1 makes it unreachable)

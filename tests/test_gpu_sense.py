@@ -121,11 +121,13 @@ def test_normal_generic_paths(case):
     assert rel(host(out), osense.normal(x, maps, mask, 0.2)) <= TOL_OP
 
 
-# W = 232 and 174 (radix 29) take the Bluestein row passes (4 rows per CTA): one coil per group
-# (B = 1), two groups of 6 coils (8 slices of 256 rows), all coils in one group (16 slices, the
-# bench shape; 32 slices), and a last CTA with 2 of its 4 rows (H = 102)
+# W = 8 P (P = 17, 19, 23, 29, 31) takes the direct row passes (8 rows per CTA), W = 174 (2 3 29)
+# the Bluestein ones (4 rows per CTA): one coil per group (B = 1), two groups of 6 coils (8
+# slices of 256 rows), all coils in one group (16 slices, the bench shape; 32 slices), and last
+# CTAs with part of their rows (H = 10, 18, 102)
 @pytest.mark.parametrize("case", [(1, 4, 16, 20), (2, 3, 64, 64), (1, 5, 24, 232), (16, 12, 256, 232),
-                                  (8, 12, 256, 232), (2, 3, 102, 174), (32, 2, 256, 174)])
+                                  (8, 12, 256, 232), (2, 3, 102, 174), (32, 2, 256, 174),
+                                  (2, 3, 24, 136), (1, 4, 10, 152), (2, 2, 18, 184), (1, 3, 12, 248)])
 def test_normal_2d_mask(case):
     B, Cc, H, W = case
     maps, mask, x = make_problem(B, Cc, H, W, 3.0, 4, seed=5, lines=False)
