@@ -275,6 +275,19 @@ def test_cg_per_slice_lambda_zero_start_and_2d_mask(H, W):
     assert rel(host(x), xref) <= TOL_CG
 
 
+def test_cg_2d_mask_many_rows():
+    """12 slices of 256 rows through the generic CG: more row groups than CTAs, so the vector
+    kernels' CTAs take several groups each."""
+    maps, mask, _ = make_problem(12, 2, 256, 232, 4.0, 8, seed=23, lines=False)
+    rhs = c64(synth.randn_complex((12, 256, 232), 24))
+    lamv = np.linspace(0.01, 0.2, 12)
+    plan = plan_for(maps, mask)
+    x = plan.cg_solve(dev(rhs), torch.tensor(lamv, device="cuda"), 10)
+    xref, _ = ocg.cg_solve(maps, mask, lamv, rhs, None, 10)
+    assert rel(host(x), xref) <= TOL_CG
+    assert plan.status() == 0
+
+
 @pytest.mark.parametrize("cfg_index,B", [(1, None), (3, 2)])
 def test_cg_backward_parity(cfg_index, B):
     cfg, maps, mask, rhs, gt = _cg_inputs(cfg_index, B)
