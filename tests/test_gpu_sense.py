@@ -391,8 +391,11 @@ def _sets_problem(B, NS, C, H, W, seed, line=True):
     return maps, mask
 
 
+# H = 256: the generic row passes with the register-resident 256-point column pass (2-D mask;
+# line mask at W = 174, which has no fused kernel)
 @pytest.mark.parametrize("shape,line", [((2, 2, 4, 24, 40), True), ((1, 2, 3, 32, 64), False),
-                                        ((3, 3, 2, 16, 30), True)])
+                                        ((3, 3, 2, 16, 30), True), ((2, 2, 3, 256, 232), False),
+                                        ((1, 2, 3, 256, 174), True)])
 def test_soft_sense_operators(shape, line):
     """Forward, adjoint and normal operator with several map sets against the oracle."""
     from paper_2202_14005_b300.sense import SensePlan
