@@ -60,6 +60,8 @@ NCU_TRAFFIC = {
     "cg_sense": {"normal_lines": 110.3e6, "cg_lines": 1.511e9},
     "modl_train": {"cg_lines": 24.8e6, "conv64_tc": 30.54e6, "wgrad64": 62.9e6},
     "varnet_train": {"vn_K": 31.18e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
+    # one Toeplitz application: its three passes (rows 568 MB, columns 754 MB, inverse rows 642 MB)
+    "noncart_modl_infer": {"toeplitz": 1.964e9},
 }
 # what the reverse pass reuses from the forward pass of each training workload
 REVERSE_PASS = {
