@@ -124,10 +124,12 @@ def test_normal_generic_paths(case):
 # W = 8 P (P = 17, 19, 23, 29, 31) takes the direct row passes (8 rows per CTA), W = 174 (2 3 29)
 # the Bluestein ones (4 rows per CTA): one coil per group (B = 1), two groups of 6 coils (8
 # slices of 256 rows), all coils in one group (16 slices, the bench shape; 32 slices), and last
-# CTAs with part of their rows (H = 10, 18, 102)
+# CTAs with part of their rows (H = 10, 18, 102); the smallest Bluestein width (130 = 2 5 13) and
+# a 256-point column pass over two columns
 @pytest.mark.parametrize("case", [(1, 4, 16, 20), (2, 3, 64, 64), (1, 5, 24, 232), (16, 12, 256, 232),
                                   (8, 12, 256, 232), (2, 3, 102, 174), (32, 2, 256, 174),
-                                  (2, 3, 24, 136), (1, 4, 10, 152), (2, 2, 18, 184), (1, 3, 12, 248)])
+                                  (2, 3, 24, 136), (1, 4, 10, 152), (2, 2, 18, 184), (1, 3, 12, 248),
+                                  (1, 2, 6, 130), (2, 3, 256, 2)])
 def test_normal_2d_mask(case):
     B, Cc, H, W = case
     maps, mask, x = make_problem(B, Cc, H, W, 3.0, 4, seed=5, lines=False)
