@@ -434,7 +434,7 @@ def run_ours(args, rank, world, local_rank):
                        "ms_per_step": round(t_cg / steps_cg, 4), "nrmse": round(nrmse_cg, 5)}
 
     cg_bytes = None  # algorithmic bytes of one whole-solve CG launch (line-mask workloads)
-    pipe = None      # training workloads: (device buffer sets, host inputs, step(k), loss) for e2e
+    pipe = None      # (device buffer sets, host inputs, step(k), result read back) for the pipelined e2e
     if args.workload == "cg_sense":
         cfg, B, t_ms, prof, launches, steps, t_prof = c2, c2.B, t_cg, prof_cg, launches_cg, steps_cg, t_cg_prof
         # initial residual (normal operator, maps + x + rhs + out) and the one-launch CG solve:
@@ -530,6 +530,15 @@ def run_ours(args, rank, world, local_rank):
         ins = [(AHy5, y_h), (maps5, maps_h)]
         outs = [(out_h, tr.xs[-1])]
         step_fn = step_nc
+        # a second device buffer set (and Toeplitz plan, same PSF) for the pipelined end-to-end
+        # loop: the next batch's x^0 and maps are copied in while this one is reconstructed
+        bufs = [(AHy5, maps5), (torch.empty_like(AHy5), torch.empty_like(maps5))]
+        plans = [plan5, SensePlan.toeplitz(bufs[1][1], psf)]
+
+        def step_buf_nc(k):
+            tr.use_plan(plans[k])
+            tr.forward_from_adjoint(bufs[k][0])
+        pipe = (bufs, (y_h, maps_h), step_buf_nc, lambda: tr.xs[-1])
         value_slices = B
     elif args.workload == "varnet_train":
         from paper_2202_14005_b300.varnet import VarNetTrainer, pack_params
@@ -689,8 +698,9 @@ def run_ours(args, rank, world, local_rank):
         if ms_p < e2e_ms:
             e2e_ms = ms_p
             e2e_mode = ("pipelined: each step's inputs copied from pinned host memory on a second stream "
-                        "while the previous step runs (two device buffer sets), loss read back every step; "
-                        "an L2 flush (512 MB write) before every step, counted in the time")
+                        "while the previous step runs (two device buffer sets), the step's result (loss, or "
+                        "the reconstruction of an inference step) read back every step; an L2 flush (512 MB "
+                        "write) before every step, counted in the time")
     _l.profile_enable(False)
     for k in PROFILE_GROUPS:
         _l.profile_read(k)  # discard the e2e loops' event times
@@ -938,18 +948,21 @@ def run_reference(args, rank, world):
 
 
 def e2e_pipelined(bufs, host, step, loss_fn, n, flush):
-    """End-to-end time per step (ms) of n training steps fed from pinned host memory: the copies
-    of step i + 1's inputs into device buffer set (i + 1) % 2 run on a second stream while step i
-    runs on the current stream; every step's loss is read back to the host.  Before every step
-    the L2 cache is flushed (a write larger than L2), as between the device-resident timed steps,
-    and the flush's time counts.  The timed region runs from before the first copy to the
-    completion of the last read-back."""
+    """End-to-end time per step (ms) of n steps fed from pinned host memory: the copies of step
+    i + 1's inputs into device buffer set (i + 1) % 2 run on a second stream while step i runs on
+    the current stream; every step's result (the loss of a training step, the reconstruction of
+    an inference step) is read back to the host.  Before every step the L2 cache is flushed (a
+    write larger than L2), as between the device-resident timed steps, and the flush's time
+    counts.  The timed region runs from before the first copy to the completion of the last
+    read-back."""
     import torch
     main = torch.cuda.current_stream()
     cs = torch.cuda.Stream()
     ev = lambda: torch.cuda.Event(enable_timing=False)
     copied, used = [ev(), ev()], [ev(), ev()]
-    loss_h = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(n)]
+    res = loss_fn()
+    hb = [torch.empty(res.shape, dtype=res.dtype).pin_memory() for _ in range(2)]
+    loss_h = [hb[i % 2] for i in range(n)]
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(main)
