@@ -56,6 +56,9 @@ WORKLOADS = {"modl_train": "modl_train_b4_c12_256x232_R6_K5_cg10", "cg_sense": "
 # normal_lines a 16-slice residual-mode launch and cg_lines one 16-slice solve (cg_sense); cg_lines
 # one 10-iteration solve, conv64_tc a forward launch and wgrad64 one launch of the 4-slice MoDL step;
 # vn_* one launch each of the 4-slice 320x368 VarNet step.
+# steps of the pipelined end-to-end loop (at least): the first step's input copy overlaps nothing,
+# and a training or inference loop runs many steps
+E2E_PIPELINED_STEPS = 30
 # the HBM denominator the project statement quotes for the operator's roofline fraction
 NOMINAL_HBM_GBS = 8000.0
 NCU_TRAFFIC = {
@@ -701,13 +704,15 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = statistics.mean(e2e)
     e2e_mode = "serial: copy in, step, read back"
     if pipe is not None:
-        ms_p = e2e_pipelined(*pipe, max(args.steps, 4), flush)
+        n_pipe = max(args.steps, E2E_PIPELINED_STEPS)
+        ms_p = e2e_pipelined(*pipe, n_pipe, flush)
         if ms_p < e2e_ms:
             e2e_ms = ms_p
-            e2e_mode = ("pipelined: each step's inputs copied from pinned host memory on a second stream "
-                        "while the previous step runs (two device buffer sets), the step's result (loss, or "
-                        "the reconstruction of an inference step) read back every step; an L2 flush (512 MB "
-                        "write) before every step, counted in the time")
+            e2e_mode = (f"pipelined over {n_pipe} steps: each step's inputs copied from pinned host memory on a "
+                        "second stream while the previous step runs (two device buffer sets; the first step's "
+                        "copy, which nothing overlaps, counted), the step's result (loss, or the reconstruction "
+                        "of an inference step) read back every step; an L2 flush (512 MB write) before every "
+                        "step, counted in the time")
     _l.profile_enable(False)
     for k in PROFILE_GROUPS:
         _l.profile_read(k)  # discard the e2e loops' event times
