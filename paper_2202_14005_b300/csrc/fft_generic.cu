@@ -9,6 +9,15 @@
 // i.e. a plain DFT between two (-1)^n modulations.  For the normal operator the
 // modulations cancel against each other (F^H diag(m) F is circulant), so that
 // path uses a plain DFT pair and the mask shifted to plain frequency order.
+//
+// Passes that hold their transforms in registers (threads own a few points each; exchanges
+// through shared memory between radix stages):
+//   - 512 points (8 x 8 x 8, 64 threads per sequence): the Toeplitz operator's row and column
+//     passes for 2H = 512 or 2W = 512 (non-Cartesian SENSE, Sec. 2.3.3), and Bluestein's
+//     512-point convolution for the normal operator's row DFTs of other widths up to 256;
+//   - 256 points (8 x 8 x 4, 32 threads per column): the normal operator's column pass, H = 256;
+//   - W = 8 P points (P prime 17 .. 31, one warp per row): the normal operator's row DFTs, the
+//     P-point DFTs as direct sums over conjugate pairs.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
