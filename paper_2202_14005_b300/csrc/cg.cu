@@ -44,12 +44,37 @@ struct RowArgs {
   int* status;
 };
 
+// Per slice: the fixed-order sum of its row partials (a warp per slice, warp, warp + nwarps, ...),
+// then, one thread per slice, the scalar update: the FP64 divisions of all slices run side by
+// side instead of one after another in each warp's lane 0.  kFinChunk slices per round (their
+// sums are held in shared memory between the two steps).
+constexpr int kFinChunk = 256;
+__device__ void finalize_slice(const RowArgs& a, int b, double s);
+
 __device__ void finalize(const RowArgs& a) {
+  __shared__ double s_sum[kFinChunk];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int b = warp; b < a.B; b += nwarps) {
-    double s = lane_strided_sum(a.part + (size_t)b * a.H, a.H, lane);
-    s = warp_sum_d(s);
-    if (lane != 0) continue;
+  for (int b0 = 0; b0 < a.B; b0 += kFinChunk) {
+    const int nb = min(kFinChunk, a.B - b0);
+    for (int i = warp; i < nb; i += nwarps) {
+      const double s = warp_sum_d(lane_strided_sum(a.part + (size_t)(b0 + i) * a.H, a.H, lane));
+      if (lane == 0) s_sum[i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) finalize_slice(a, b0 + i, s_sum[i]);
+    __syncthreads();
+  }
+  if (a.fin == FIN_GLAM && a.gcount != a.B) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int b = 0; b < a.B; ++b) t += a.alpha[b];
+      a.gout[0] = a.gacc ? a.gout[0] + t : t;
+    }
+  }
+}
+
+__device__ void finalize_slice(const RowArgs& a, int b, double s) {
+  {
     if (a.fin == FIN_RR0) {
       if (!isfinite(s)) set_status(a.status, SENSE_DEVST_NONFINITE);
       a.rr[b] = s;
@@ -71,15 +96,7 @@ __device__ void finalize(const RowArgs& a) {
       if (a.hist) a.hist[b] = s;
     } else if (a.fin == FIN_GLAM) {
       if (a.gcount == a.B) a.gout[b] = a.gacc ? a.gout[b] + s : s;
-      else a.alpha[b] = s;  // per-slice scratch, summed below in slice order
-    }
-  }
-  if (a.fin == FIN_GLAM && a.gcount != a.B) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int b = 0; b < a.B; ++b) t += a.alpha[b];
-      a.gout[0] = a.gacc ? a.gout[0] + t : t;
+      else a.alpha[b] = s;  // per-slice scratch, summed in slice order by finalize
     }
   }
 }
