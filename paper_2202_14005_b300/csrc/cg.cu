@@ -118,22 +118,29 @@ __device__ void last_block(const RowArgs& a) {
   }
 }
 
-// Two warps per image row (four rows per 256-thread CTA); elements are taken
-// two at a time (float4 = 2 complex).  Each warp reduces its FP32 lane sums in
-// FP64; the two warp sums of a row are added in warp order.
+// Two warps per image row (four rows per 256-thread CTA and pass); elements are
+// taken two at a time (float4 = 2 complex).  Each warp reduces its FP32 lane
+// sums in FP64; the two warp sums of a row are added in warp order.  A CTA
+// takes the groups of four rows blockIdx.x, blockIdx.x + gridDim.x, ... (a
+// grid of kCtasPerSm CTAs per SM): fewer CTAs, and so fewer fences and
+// counter increments of the last-CTA reduction.
 constexpr int kRowsPerCta = kWarps / 2;
+constexpr int kCtasPerSm = 4;
 
 __device__ __forceinline__ void row_partial(const RowArgs& a, int row, bool rv, float part) {
   __shared__ double s_w[kWarps];
   const double d = warp_sum_d((double)part);
   const int warp = threadIdx.x >> 5;
+  __syncthreads();  // the previous group's sums have been read
   if ((threadIdx.x & 31) == 0) s_w[warp] = d;
   __syncthreads();
   if (rv && a.part && (threadIdx.x & 63) == 0) a.part[row] = s_w[warp] + s_w[warp + 1];
 }
 
 #define ROW_LOOP_BEGIN                                                    \
-  const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 6);          \
+  for (int rbase = blockIdx.x * kRowsPerCta; rbase < a.B * a.H;           \
+       rbase += gridDim.x * kRowsPerCta) {                                \
+  const int row = rbase + (threadIdx.x >> 6);                             \
   const int lt = threadIdx.x & 63;                                        \
   const bool rv = row < a.B * a.H;                                        \
   float part = 0.f;                                                       \
@@ -145,7 +152,8 @@ __device__ __forceinline__ void row_partial(const RowArgs& a, int row, bool rv, 
 #define ROW_LOOP_END                                                      \
     }                                                                     \
   }                                                                       \
-  row_partial(a, row, rv, part);
+  row_partial(a, row, rv, part);                                          \
+  }
 
 __device__ __forceinline__ float nrm2(float4 v) {
   return fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
@@ -240,7 +248,10 @@ RowArgs base_args(sense_plan p) {
   return a;
 }
 
-int grid_rows(sense_plan p) { return (p->B * p->S * p->H + kRowsPerCta - 1) / kRowsPerCta; }
+int grid_rows(sense_plan p) {
+  const int groups = (p->B * p->S * p->H + kRowsPerCta - 1) / kRowsPerCta;
+  return groups < kCtasPerSm * p->num_sms ? groups : kCtasPerSm * p->num_sms;
+}
 
 }  // namespace
 
