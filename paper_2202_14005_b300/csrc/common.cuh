@@ -181,3 +181,50 @@ SENSE_D float warp_sum_f(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// ------------------------------------------------ compensated FP32 sums (float-float)
+// A value carried as the unevaluated sum hi + lo of two floats.  Addition: Knuth's TwoSum
+// recovers the rounding error of hi_a + hi_b exactly, the low parts are added to it, and
+// Dekker's fast two-sum renormalises (|lo| <= ulp(hi) / 2): about 44 significant bits, on the
+// FP32 pipes.  This GPU's FP64 units take tens of cycles per warp instruction, so sums that
+// need more than FP32 accuracy are carried this way and converted to FP64 once.  The operation
+// is symmetric in its operands (the TwoSum error is exact), so butterfly partners agree bitwise.
+// Only additions and subtractions: nothing for the compiler to contract into an FMA.
+SENSE_HD float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  float e = (a.x - (s - bb)) + (b.x - bb);
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+SENSE_HD double ff_to_d(float2 a) { return (double)a.x + (double)a.y; }
+// Warp sum in a fixed butterfly order (deterministic, every lane gets the same value).
+SENSE_D float2 warp_sum_ff(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float2 w;
+    w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+    w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+    v = ff_add(v, w);
+  }
+  return v;
+}
+SENSE_D float2 warp_sum_ff(float v) { return warp_sum_ff(make_float2(v, 0.f)); }
+// Lane part of a strided float-float sum (elements lane, lane + 32, ...): groups of eight loaded
+// together and added as a pairwise tree, groups added in order (as lane_tree_sum).
+SENSE_D float2 ff_tree8(const float2* v) {
+  return ff_add(ff_add(ff_add(v[0], v[1]), ff_add(v[2], v[3])), ff_add(ff_add(v[4], v[5]), ff_add(v[6], v[7])));
+}
+SENSE_D float2 lane_tree_sum_ff(const float2* p, int n, int lane) {
+  float2 s = make_float2(0.f, 0.f);
+  int i = lane;
+  for (; i + 7 * 32 < n; i += 8 * 32) {
+    float2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + i + 32 * k);
+    s = i == lane ? ff_tree8(v) : ff_add(s, ff_tree8(v));
+  }
+  for (; i < n; i += 32) s = ff_add(s, __ldcg(p + i));
+  return s;
+}

@@ -47,7 +47,7 @@ struct NLArgs {
   float2* sv = nullptr;
   float2* xs = nullptr;
   double* part2 = nullptr;
-  const double* al_s = nullptr;
+  const float* ab_f = nullptr;  // NM_CG2: alpha, beta of the tile's slice
   int upd = 0, first = 0;
   const float2* rhs0 = nullptr;  // NM_CG2 without upd: stage r = rhs0 (written to r) and zero x
   const float2* pold;
@@ -200,8 +200,9 @@ __device__ __forceinline__ void nl_tile(const NLArgs& a, const NLSmem& S, int ti
     if (MODE == NM_CG2) {
       float4* rv = reinterpret_cast<float4*>(const_cast<float2*>(a.x) + img0);
       if (a.upd) {
-        const float be = a.first ? 0.f : (float)a.beta[b];
-        const float al = (float)a.al_s[b];
+        // the solve kernel's CTA holds the scalars of its one slice (FP32)
+        const float be = a.first ? 0.f : a.ab_f[1];
+        const float al = a.ab_f[0];
         float4* pv = reinterpret_cast<float4*>(a.pout + img0);
         float4* sv = reinterpret_cast<float4*>(a.sv + img0);
         float4* xv = reinterpret_cast<float4*>(a.xs + img0);
@@ -428,47 +429,71 @@ __device__ __forceinline__ void nl_tile(const NLArgs& a, const NLSmem& S, int ti
   }
   __syncthreads();
 
-  // ---- epilogue: sum coil groups in fixed order, + lambda x, row partial (per set and row)
-  for (int it = warp; it < NS * nrows; it += nwarps) {
-    const int st = it / nrows, rr = it - st * nrows;
-    const int h = h0 + rr;
-    const size_t orow0 = (((size_t)b * NS + st) * a.H + h) * W;
-    float part = 0.f, part_rr = 0.f;
-    const float2* xr = s_x + (st * a.rows + rr) * W;
-    const float2* rh = (MODE == NM_RESID) ? a.rhs + orow0 : nullptr;
-    float2* orow = a.out + orow0;
-    for (int n = lane; n < W; n += 32) {
-      float2 s = make_float2(0.f, 0.f);
-      for (int g = 0; g < a.nwr; ++g) {
-        const float2* yb = s_y + (rr * a.nwr + g) * (GB * W) + st * GA * W;
+  // ---- epilogue, per set: sum coil groups in fixed order, + lambda x, row partial.  The nwr
+  // warps of a row split its columns (warp cgp: columns cgp * 32 + lane, stride 32 nwr); each
+  // warp's share of the row partial (compensated float-float warp sum of its FP32 lane sums)
+  // goes to shared memory and the shares of a row are added in warp order after the barrier.
+  // The one-launch CG (NM_CG2) keeps its row partials as float-float pairs (stored in the
+  // 8-byte slots of its partial arrays); the other modes store them as FP64.
+  // nwarps = rows x nwr <= 8.
+  __shared__ float2 s_rp[2][NS][8];
+  if (wrow < nrows) {
+    const int rr = wrow, h = h0 + rr;
 #pragma unroll
-        for (int ga = 0; ga < GA; ++ga) s = cadd(s, yb[ga * W + n]);
+    for (int st = 0; st < NS; ++st) {
+      const size_t orow0 = (((size_t)b * NS + st) * a.H + h) * W;
+      float part = 0.f, part_rr = 0.f;
+      const float2* xr = s_x + (st * a.rows + rr) * W;
+      const float2* rh = (MODE == NM_RESID) ? a.rhs + orow0 : nullptr;
+      float2* orow = a.out + orow0;
+      for (int n = cgp * 32 + lane; n < W; n += 32 * a.nwr) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int g = 0; g < a.nwr; ++g) {
+          const float2* yb = s_y + (rr * a.nwr + g) * (GB * W) + st * GA * W;
+#pragma unroll
+          for (int ga = 0; ga < GA; ++ga) s = cadd(s, yb[ga * W + n]);
+        }
+        if (MODE == NM_ADJ) {
+          orow[n] = s;
+          continue;
+        }
+        const float2 xv = xr[n];
+        float2 o = make_float2(fmaf(lam, xv.x, s.x), fmaf(lam, xv.y, s.y));
+        if (MODE == NM_RESID) {
+          o = csub(rh[n], o);
+          part = fmaf(o.x, o.x, fmaf(o.y, o.y, part));
+        } else {
+          part = fmaf(xv.x, o.x, fmaf(xv.y, o.y, part));
+          if (MODE == NM_CG2) part_rr = fmaf(xv.x, xv.x, fmaf(xv.y, xv.y, part_rr));
+        }
+        orow[n] = o;
       }
-      if (MODE == NM_ADJ) {
-        orow[n] = s;
-        continue;
+      if (MODE != NM_ADJ) {
+        const float2 d = warp_sum_ff(part);
+        if (lane == 0) s_rp[0][st][warp] = d;
       }
-      const float2 xv = xr[n];
-      float2 o = make_float2(fmaf(lam, xv.x, s.x), fmaf(lam, xv.y, s.y));
-      if (MODE == NM_RESID) {
-        o = csub(rh[n], o);
-        part = fmaf(o.x, o.x, fmaf(o.y, o.y, part));
-      } else {
-        part = fmaf(xv.x, o.x, fmaf(xv.y, o.y, part));
-        if (MODE == NM_CG2) part_rr = fmaf(xv.x, xv.x, fmaf(xv.y, xv.y, part_rr));
+      if (MODE == NM_CG2) {
+        const float2 d = warp_sum_ff(part_rr);
+        if (lane == 0) s_rp[1][st][warp] = d;
       }
-      orow[n] = o;
-    }
-    if (MODE != NM_ADJ && a.part) {
-      const double d = warp_sum_d((double)part);
-      if (lane == 0) a.part[(size_t)b * a.HS + st * a.H + h] = d;
-    }
-    if (MODE == NM_CG2) {
-      const double d = warp_sum_d((double)part_rr);
-      if (lane == 0) a.part2[(size_t)b * a.HS + st * a.H + h] = d;
     }
   }
   __syncthreads();
+  if (MODE != NM_ADJ && a.part && (int)threadIdx.x < NS * nrows) {
+    const int st = threadIdx.x / nrows, rr = threadIdx.x - st * nrows;
+    const size_t prow = (size_t)b * a.HS + st * a.H + h0 + rr;
+    float2 d = s_rp[0][st][rr * a.nwr], d2 = s_rp[1][st][rr * a.nwr];
+    for (int g = 1; g < a.nwr; ++g) {
+      d = ff_add(d, s_rp[0][st][rr * a.nwr + g]);
+      if (MODE == NM_CG2) d2 = ff_add(d2, s_rp[1][st][rr * a.nwr + g]);
+    }
+    if (MODE == NM_CG2) {
+      reinterpret_cast<float2*>(a.part)[prow] = d;
+      reinterpret_cast<float2*>(a.part2)[prow] = d2;
+    } else {
+      a.part[prow] = ff_to_d(d);
+    }
+  }
 }
 
 // NS = map sets (soft-SENSE): x, out [B][NS][H][W], maps [B][NS][C][H][W]; coil image
@@ -494,10 +519,10 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_normal_lines(const NLA
 // so only the row partials and the per-slice scalars cross CTAs.
 //
 // Barriers: the CTAs form one group per slice, and each group has an arrival count that only
-// grows within the launch (barrier n completes at (n + 1) x group-size arrivals) and a release
-// word.  The CTA that arrives last reduces the slice's row partials in fixed order, publishes
-// alpha and beta (and its copies of gamma and alpha for the next pass), then releases the
-// others, which read the two scalars.  One CTA reads the partials instead of every CTA reading
+// grows within the launch (barrier n completes at (n + 1) x group-size arrivals) and two release
+// words.  The CTA that arrives last reduces the slice's row partials in fixed order, keeps gamma
+// and alpha (FP64) for the next pass, and releases the others with the two words, which carry
+// the generation and the FP32 alpha and beta the vector updates use.  One CTA reads the partials instead of every CTA reading
 // them at once, and the slices do not wait for each other.  The launch is cooperative (all CTAs
 // resident) and every wait is bounded: a CTA that gives up sets SENSE_STATUS_DEVICE_TIMEOUT and
 // returns.
@@ -512,11 +537,11 @@ struct CgCoop {
   float2* w;        // S r
   double* hist;     // [iters + 1][B] squared residual norms or NULL
   const float2* rhs0;  // not NULL: start from x = 0, r = rhs0 (first pass)
-  // per slice b: arrival count cnt_s[32 b] and release word rel_s[32 b] (128-byte lines of their
-  // own), zero at launch
+  // per slice b: arrival count cnt_s[32 b] and two 64-bit release words at rel_s + 32 b
+  // (128-byte lines of their own), zero at launch
   unsigned* cnt_s;
   unsigned* rel_s;
-  double* sc;       // published scalars: alpha [kCoopMaxB], beta [kCoopMaxB], gamma [kCoopMaxB]
+  double* sc;       // FP64 scalars kept for the next pass: alpha [kCoopMaxB], gamma alpha [kCoopMaxB], gamma [kCoopMaxB]
   // row partials of delta and gamma, two buffers each, used by alternate passes
   double* pd[2];
   double* pg[2];
@@ -540,50 +565,94 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Scalars of pass k from the row partials (delta in part, gamma in part2), formed by the one CTA
-// that completed barrier k.  gamma_{k-1} and alpha_{k-1} come from the previous publication.
-// A slice whose gamma is zero (or whose previous alpha is zero) is frozen: alpha = beta = 0.
-// With only_gamma the pass made the last update: gamma is recorded, no new alpha.
+// Scalars of pass k from the row partials (delta in part, gamma in part2) of slice b, formed by
+// the one CTA that completed barrier k.  gamma_{k-1} and alpha_{k-1} come from the previous
+// publication.  A slice whose gamma is zero (or whose previous alpha is zero) is frozen:
+// alpha = beta = 0.  With only_gamma the pass made the last update: gamma is recorded, no new
+// alpha.  The row partials are float-float pairs; the sums over the rows run in float-float
+// arithmetic (gamma on warp 0, delta on warp 1, side by side) and are converted to FP64 once.
+// With c = gamma_{k-1} alpha_{k-1},
+//   alpha_k = g / (d - beta_{k-1} g / alpha_{k-1}) = g c / (d c - g^2),  beta_{k-1} = g / gamma_{k-1},
+// so one FP64 division lies on the path to alpha (warp 0) and beta's runs beside it (warp 1).
+// On return (thread 0) ab[0], ab[1] hold alpha and beta in FP32 for the vector updates.
 __device__ __forceinline__ void coop_scalars(const NLArgs& a, const CgCoop& c, int k, bool only_gamma,
-                                             double* hist, int b0, int b1) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int b = b0 + warp; b < b1; b += nwarps) {
-    const double gp = __ldcg(c.sc + 2 * kCoopMaxB + b), ap = __ldcg(c.sc + b);
-    double g = 0.0, d = 0.0;
-    if (only_gamma) g = lane_tree_sum(a.part2 + (size_t)b * a.HS, a.HS, lane);
-    else lane_tree_sum2(a.part2 + (size_t)b * a.HS, a.part + (size_t)b * a.HS, a.HS, lane, g, d);
-    g = warp_sum_d(g);
-    if (!only_gamma) d = warp_sum_d(d);
-    if (lane != 0) continue;
-    const bool fin = isfinite(g) && isfinite(d);
-    if (!fin) set_status(a.status, SENSE_DEVST_NONFINITE);
-    double be = 0.0, al = 0.0;
-    if (fin && g > 0.0 && (k == 0 || (gp > 0.0 && ap != 0.0))) {
-      // beta g / alpha_prev as (g / gamma_prev)(g / alpha_prev): the two divisions are
-      // independent, so only two FP64 divisions lie on the dependency chain
-      be = k == 0 ? 0.0 : g / gp;
-      if (!only_gamma) {
-        const double den = k == 0 ? d : d - be * (g / ap);
-        if (den > 0.0) al = g / den;
-        else set_status(a.status, SENSE_DEVST_CG_BREAKDOWN);
-      }
-    }
-    c.sc[b] = al;
-    c.sc[kCoopMaxB + b] = be;
-    c.sc[2 * kCoopMaxB + b] = g;
-    a.rr[b] = g;
-    a.alpha[b] = al;
-    if (hist) hist[b] = g;
+                                             int b, float* ab, double* s_gd) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wd = (blockDim.x >> 5) > 1 ? 1 : 0;  // the warp that sums delta and divides for beta
+  // gamma_{k-1}, alpha_{k-1} and their product, loaded beside the partials
+  const double gp = __ldcg(c.sc + 2 * kCoopMaxB + b), ap = __ldcg(c.sc + b), gap = __ldcg(c.sc + kCoopMaxB + b);
+  if (warp == 0) {
+    const float2 g = warp_sum_ff(lane_tree_sum_ff(reinterpret_cast<const float2*>(a.part2) + (size_t)b * a.HS, a.HS, lane));
+    if (lane == 0) s_gd[0] = ff_to_d(g);
   }
+  if (warp == wd) {
+    const float2 d = only_gamma ? make_float2(0.f, 0.f)
+                                : warp_sum_ff(lane_tree_sum_ff(reinterpret_cast<const float2*>(a.part) + (size_t)b * a.HS, a.HS, lane));
+    if (lane == 0) s_gd[1] = ff_to_d(d);
+  }
+  __syncthreads();
+  const double g = s_gd[0], d = s_gd[1];
+  const bool fin = isfinite(g) && isfinite(d);
+  const bool live = fin && g > 0.0 && (k == 0 || (gp > 0.0 && ap != 0.0));
+  if (lane == 0 && warp == wd && live && k > 0) s_gd[2] = g / gp;
+  double al = 0.0;
+  bool brk = false;
+  if (threadIdx.x == 0 && live && !only_gamma) {
+    const double cp = k == 0 ? 1.0 : gap;
+    const double den = k == 0 ? d : d * cp - g * g;
+    if (den > 0.0) al = k == 0 ? g / den : (g * cp) / den;
+    else brk = true;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double be = (live && k > 0) ? s_gd[2] : 0.0;
+  ab[0] = (float)al;
+  ab[1] = (float)be;
+  s_gd[0] = g;  // for coop_keep, after the release
+  s_gd[1] = al;
+  if (!fin) set_status(a.status, SENSE_DEVST_NONFINITE);
+  if (brk) set_status(a.status, SENSE_DEVST_CG_BREAKDOWN);
+}
+// The FP64 gamma, alpha and their product of slice b for the next pass, gamma and alpha for the host (thread 0 of the CTA that
+// formed them, after the release: the next pass's last CTA reads them after its arrival, which
+// the arrival chain orders after these stores).
+__device__ __forceinline__ void coop_keep(const NLArgs& a, const CgCoop& c, double* hist, int b, const double* gd) {
+  const double g = gd[0], al = gd[1];
+  c.sc[b] = al;
+  c.sc[kCoopMaxB + b] = g * al;
+  c.sc[2 * kCoopMaxB + b] = g;
+  a.rr[b] = g;
+  a.alpha[b] = al;
+  if (hist) hist[b] = g;
 }
 
-// Barrier n of the solve with the scalars of pass k formed in between; on return s_alpha and
-// s_beta hold the published values.  False if this CTA's wait timed out.
-// cnt / rel / group: the barrier's words and number of CTAs; slices b0..b1-1 get their scalars.
-__device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsigned* cnt, unsigned* rel,
-                                          unsigned group, int b0, int b1, unsigned n, int k, bool only_gamma,
-                                          double* hist, double* s_alpha, double* s_beta) {
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// A release word: the barrier generation in the high half, an FP32 scalar in the low half.
+__device__ __forceinline__ unsigned long long rel_word(unsigned gen, float v) {
+  return ((unsigned long long)gen << 32) | (unsigned long long)__float_as_uint(v);
+}
+
+// Barrier n of the solve with the scalars of pass k formed in between; on return ab[0], ab[1]
+// (shared memory) hold the published FP32 alpha and beta of slice b0.  False if this CTA's wait
+// timed out.  cnt / group: the barrier's arrival count and number of CTAs; rel: the slice's two
+// 64-bit release words, each carrying generation n + 1 and one of the scalars, so a waiting CTA
+// has the scalars when it sees the release.  The words are written and read with relaxed 64-bit
+// accesses (no fence on the path): each word is read whole, so its scalar is that of the
+// generation it carries, and no other data crosses CTAs here.  The vectors are per CTA; the row
+// partials a pass writes go to the buffer of two passes back, whose reads by that pass's last
+// CTA precede its next arrival, and each arrival is a release, the last one an acquire.
+__device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsigned* cnt,
+                                          unsigned long long* rel, unsigned group, int b0, unsigned n, int k,
+                                          bool only_gamma, double* hist, float* ab) {
   __shared__ int s_last, s_ok;
+  __shared__ double s_gd[3];
   __syncthreads();  // this CTA's partials are written
   if (threadIdx.x == 0) {
     const unsigned t = atom_add_acq_rel_u32(cnt, 1u);
@@ -592,12 +661,21 @@ __device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsi
   }
   __syncthreads();
   if (s_last) {
-    coop_scalars(a, c, k, only_gamma, hist, b0, b1);
-    __syncthreads();
-    if (threadIdx.x == 0) st_release_u32(rel, n + 1u);
+    coop_scalars(a, c, k, only_gamma, b0, ab, s_gd);
+    if (threadIdx.x == 0) {
+      st_relaxed_u64(rel, rel_word(n + 1u, ab[0]));
+      st_relaxed_u64(rel + 1, rel_word(n + 1u, ab[1]));
+      coop_keep(a, c, hist, b0, s_gd);
+    }
   } else if (threadIdx.x == 0) {
     unsigned it = 0;
-    while (ld_acquire_u32(rel) < n + 1u) {
+    for (;;) {
+      const unsigned long long w0 = ld_relaxed_u64(rel), w1 = ld_relaxed_u64(rel + 1);
+      if ((unsigned)(w0 >> 32) >= n + 1u && (unsigned)(w1 >> 32) >= n + 1u) {
+        ab[0] = __uint_as_float((unsigned)w0);
+        ab[1] = __uint_as_float((unsigned)w1);
+        break;
+      }
       if (++it > c.polls) {
         s_ok = 0;
         break;
@@ -606,25 +684,19 @@ __device__ __forceinline__ bool coop_step(const NLArgs& a, const CgCoop& c, unsi
     }
   }
   __syncthreads();
-  if (!s_ok) return false;
-  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
-    s_alpha[b] = __ldcg(c.sc + b);
-    s_beta[b] = __ldcg(c.sc + kCoopMaxB + b);
-  }
-  __syncthreads();
-  return true;
+  return s_ok != 0;
 }
 
 template <int Q, int P, int JMAX, int NS>
 __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs a0, const CgCoop c) {
   constexpr int W = Q * P;
-  __shared__ double s_alpha[kCoopMaxB], s_beta[kCoopMaxB];
+  __shared__ float s_ab[2];  // alpha and beta of this CTA's slice (FP32, as the vector updates use them)
   const NLSmem S = nl_smem_setup<Q, P, NS>(a0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int b = threadIdx.x; b < a0.B; b += blockDim.x) s_alpha[b] = s_beta[b] = 0.0;
+  if (threadIdx.x == 0) s_ab[0] = s_ab[1] = 0.f;
   __syncthreads();
   NLArgs a = a0;
-  a.x = c.r; a.out = c.w; a.pout = c.p; a.sv = c.s; a.xs = c.x; a.beta = s_beta; a.al_s = s_alpha;
+  a.x = c.r; a.out = c.w; a.pout = c.p; a.sv = c.s; a.xs = c.x; a.ab_f = s_ab;
   a.finalize = 0;
   // One group of CTAs per slice: CTAs (b grid) / B .. ((b + 1) grid) / B - 1 take the row tiles
   // of slice b round robin, and each group has its own barrier, so the CTAs of a slice wait only
@@ -639,7 +711,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
   const int b1 = b0 + 1;
   const int t0 = b0 * a.tiles_per_slice + li, t1 = b1 * a.tiles_per_slice;
   unsigned* cnt = c.cnt_s + 32 * b0;
-  unsigned* rel = c.rel_s + 32 * b0;
+  unsigned long long* rel = reinterpret_cast<unsigned long long*>(c.rel_s + 32 * b0);
   for (int k = 0; k < c.iters; ++k) {
     a.upd = k > 0;
     a.first = k == 1;
@@ -647,8 +719,8 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
     a.part = (k & 1) ? c.pd[1] : c.pd[0];
     a.part2 = (k & 1) ? c.pg[1] : c.pg[0];
     for (int tile = t0; tile < t1; tile += gstride) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);
-    if (!coop_step(a, c, cnt, rel, group, b0, b1, (unsigned)k, k, false, c.hist ? c.hist + (size_t)k * a.B : nullptr,
-                   s_alpha, s_beta)) {
+    if (!coop_step(a, c, cnt, rel, group, b0, (unsigned)k, k, false, c.hist ? c.hist + (size_t)k * a.B : nullptr,
+                   s_ab)) {
       if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
       return;
     }
@@ -660,7 +732,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
     const int b = tile / a.tiles_per_slice;
     const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
     const int nrows = min(a.rows, a.H - h0);
-    const float al = (float)s_alpha[b], be = first ? 0.f : (float)s_beta[b];
+    const float al = s_ab[0], be = first ? 0.f : s_ab[1];
     for (int rw = warp; rw < NS * nrows; rw += nwarps) {
       const int st = rw / nrows, h = h0 + (rw - st * nrows);
       const size_t off = ((((size_t)b * NS + st) * a.H + h) * W) / 2;
@@ -685,12 +757,12 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
         rv[i] = r;
         part = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, part))));
       }
-      const double d = warp_sum_d((double)part);
-      if (lane == 0) a.part2[(size_t)b * a.HS + st * a.H + h] = d;
+      const float2 d = warp_sum_ff(part);
+      if (lane == 0) reinterpret_cast<float2*>(a.part2)[(size_t)b * a.HS + st * a.H + h] = d;
     }
   }
-  if (!coop_step(a, c, cnt, rel, group, b0, b1, (unsigned)c.iters, c.iters, true,
-                 c.hist ? c.hist + (size_t)c.iters * a.B : nullptr, s_alpha, s_beta)) {
+  if (!coop_step(a, c, cnt, rel, group, b0, (unsigned)c.iters, c.iters, true,
+                 c.hist ? c.hist + (size_t)c.iters * a.B : nullptr, s_ab)) {
     if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
   }
 }
