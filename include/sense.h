@@ -152,7 +152,9 @@ int sense_normal(sense_plan plan, const void* x, void* out, float lambda);
  *   lambda device float64, lambda_count = 1 (shared) or B (per slice), > 0
  *          (not checked on the host: lambda <= 0 shows up as a breakdown bit)
  *   rr_hist NULL or device float64 [iters + 1][B]: ||r_i||^2 per iteration.
- * Vectors are FP32 complex; inner products, alpha and beta are FP64.
+ * Vectors are FP32 complex; alpha and beta are FP64.  Inner products take FP32
+ * products and lane sums, summed across lanes and rows in FP64 or (the one-launch
+ * solve on line masks) as compensated float-float pairs converted to FP64 once.
  * A slice whose residual is exactly zero is frozen.  Needs the workspace. */
 int cg_dc_solve(sense_plan plan, const void* rhs, const void* x0, void* x,
                 const double* lambda, int lambda_count, int iters, double* rr_hist);

@@ -19,8 +19,9 @@
 //   phase C  inverse twiddle, inverse Q-point DFT in registers, accumulate
 //            conj(S_c) * v over the coils of the warp.
 // Warps of one row sum their coil groups through shared memory in a fixed
-// order; per-row FP64 partials of the CG inner products are written, and the
-// last CTA to finish reduces them per slice (fixed order, deterministic).
+// order; per-row partials of the CG inner products are written (FP32 lane sums
+// carried across lanes and warps as float-float pairs), and the last CTA to
+// finish reduces them per slice (fixed order, deterministic).
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -613,9 +614,9 @@ __device__ __forceinline__ void coop_scalars(const NLArgs& a, const CgCoop& c, i
   if (!fin) set_status(a.status, SENSE_DEVST_NONFINITE);
   if (brk) set_status(a.status, SENSE_DEVST_CG_BREAKDOWN);
 }
-// The FP64 gamma, alpha and their product of slice b for the next pass, gamma and alpha for the host (thread 0 of the CTA that
-// formed them, after the release: the next pass's last CTA reads them after its arrival, which
-// the arrival chain orders after these stores).
+// The FP64 gamma, alpha and their product of slice b for the next pass, and gamma and alpha for
+// the host (thread 0 of the CTA that formed them, after the release: the next pass's last CTA
+// reads them after its arrival, which the arrival chain orders after these stores).
 __device__ __forceinline__ void coop_keep(const NLArgs& a, const CgCoop& c, double* hist, int b, const double* gd) {
   const double g = gd[0], al = gd[1];
   c.sc[b] = al;
