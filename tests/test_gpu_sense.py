@@ -239,6 +239,33 @@ def test_cg_paths_by_batch(B, one_launch):
     assert plan.status() == 0
 
 
+@pytest.mark.parametrize("B,C,H,sets", [(6, 12, 38, 1), (5, 7, 22, 1), (3, 4, 30, 1), (2, 4, 18, 2)])
+def test_cg_one_launch_ragged_row_tiles(B, C, H, sets):
+    """One-launch solves with the row epilogue split over a row's warps: 6 slices of 38 rows in
+    2-row tiles with three warps per row; partial last tiles (H even, as the plan requires, so
+    4-row tiles): 7 coils in two warps per row and 22 rows, 4 coils in one warp and 30 rows, two
+    map sets and 18 rows.  Against the oracle with residual histories."""
+    W, lam_v, iters = 232, 0.05, 10
+    lam = torch.tensor([lam_v], dtype=torch.float64, device="cuda")
+    if sets == 1:
+        maps, mask, _ = make_problem(B, C, H, W, 6.0, 24, seed=B + H)
+        rhs = c64(synth.randn_complex((B, H, W), H))
+    else:
+        maps, mask = _sets_problem(B, sets, C, H, W, seed=B + H)
+        rhs = c64(synth.randn_complex((B, sets, H, W), H))
+    plan = plan_for(maps, mask)
+    hist = torch.zeros((iters + 1, B), dtype=torch.float64, device="cuda")
+    x, n = _cg_path_counts(lambda: plan.cg_solve(dev(rhs), lam, iters, rr_hist=hist))
+    assert n["cg_lines"] == 1, n
+    if sets == 1:
+        xref, rr = ocg.cg_solve(maps, mask, lam_v, rhs, None, iters)
+    else:
+        xref, rr = ocg.cg_solve_sets(maps, mask, lam_v, rhs, None, iters)
+    assert rel(host(x), xref) <= TOL_CG
+    np.testing.assert_allclose(hist.cpu().numpy(), rr, rtol=1e-3, atol=1e-12 * rr[0].max())
+    assert plan.status() == 0
+
+
 def test_cg_one_launch_long_solve_and_frozen_slice():
     """40 iterations of the one-launch solve against the oracle (the single-reduction recurrence
     over many steps), with one slice whose right-hand side is zero (frozen: stays zero, no
