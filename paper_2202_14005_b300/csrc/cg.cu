@@ -260,10 +260,14 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
   Workspace& w = p->w;
   const int gr = grid_rows(p);
   const int B = p->B;
-  prof_mark("cg_vec", p->stream, false);
-  k_lam_expand<<<(B + 127) / 128, 128, 0, p->stream>>>(B, lam, lam_count, w.lam);
-  prof_mark("cg_vec", p->stream, true);
-  count_launch(p);
+  // the one-launch solve reads lambda in place; the other paths take one value per slice
+  const bool coop = p->lines.ok && p->lines.coop && iters > 0;
+  if (!coop || x0) {
+    prof_mark("cg_vec", p->stream, false);
+    k_lam_expand<<<(B + 127) / 128, 128, 0, p->stream>>>(B, lam, lam_count, w.lam);
+    prof_mark("cg_vec", p->stream, true);
+    count_launch(p);
+  }
   // ---- initial residual
   if (x0) {
     if (x0 != x &&
@@ -284,9 +288,9 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
       prof_mark("cg_vec", p->stream, true);
       count_launch(p);
     }
-  } else if (p->lines.ok && p->lines.coop && iters > 0) {
+  } else if (coop) {
     // x = 0, r = rhs and ||r||^2 in the first pass of the one-launch solve
-    return launch_cg_lines(p, x, iters, rr_hist, rhs);
+    return launch_cg_lines(p, x, iters, rr_hist, rhs, lam, lam_count);
   } else {
     RowArgs a = base_args(p);
     a.a = rhs; a.o1 = w.r; a.o2 = x; a.fin = FIN_RR0; a.hist = rr_hist;
@@ -296,7 +300,7 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
     count_launch(p);
   }
   // ---- iterations: all of them in one cooperative launch where the fused kernel applies
-  if (p->lines.ok && p->lines.coop && iters > 0) return launch_cg_lines(p, x, iters, rr_hist, nullptr);
+  if (coop) return launch_cg_lines(p, x, iters, rr_hist, nullptr, lam, lam_count);
   for (int it = 0; it < iters; ++it) {
     double* hist = rr_hist ? rr_hist + (size_t)(it + 1) * B : nullptr;
     if (p->lines.ok) {

@@ -165,7 +165,8 @@ void free_lines_tables(sense_plan pl) {
   pl->lines = LinesTables();
 }
 
-int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const float2* rhs0) {
+int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const float2* rhs0, const double* lam,
+                    int lam_count) {
   const LinesTables& T = pl->lines;
   if (!T.coop) return SENSE_EUNSUPPORTED;
   Workspace& w = pl->w;
@@ -176,7 +177,7 @@ int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const 
   a.ntiles = pl->B * a.tiles_per_slice;
   a.maps = pl->maps; a.coef = T.coef; a.tw = T.tw; a.wt = T.wt; a.sgn = T.sgn; a.akx = T.akx; a.af = T.af;
   a.x = w.r; a.pold = nullptr; a.pout = w.p; a.out = w.q; a.rhs = nullptr;
-  a.lam_host = 0.f; a.lam_dev = w.lam;
+  a.lam_host = 0.f; a.lam_dev = lam; a.lam_shared = lam_count == 1;
   a.beta = nullptr; a.part = w.part; a.finalize = 0;
   a.rr = w.rr; a.alpha = w.alpha; a.rr_hist_row = nullptr;
   a.counter = w.counter; a.status = pl->status;

@@ -57,6 +57,7 @@ struct NLArgs {
   const float2* rhs;
   float lam_host;
   const double* lam_dev;
+  int lam_shared = 0;  // lam_dev holds one value for every slice (else one per slice)
   const double* beta;
   double* part;
   int finalize;
@@ -189,7 +190,7 @@ __device__ __forceinline__ void nl_tile(const NLArgs& a, const NLSmem& S, int ti
   const int b = tile / a.tiles_per_slice;
   const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
   const int nrows = min(a.rows, a.H - h0);
-  const float lam = a.lam_dev ? (float)a.lam_dev[b] : a.lam_host;
+  const float lam = a.lam_dev ? (float)a.lam_dev[a.lam_shared ? 0 : b] : a.lam_host;
 
   // ---- stage the input rows of every set (CG: p = r + beta p_old, written back)
 #pragma unroll

@@ -138,7 +138,9 @@ float2* modl_zout(void* ws, int B, int H, int W);
 // Every CG iteration in one cooperative launch (p->lines.coop): x, w.r, w.p, w.q, w.rr as left by
 // the initial residual; rr_hist rows 1..iters written when non-NULL.
 // rhs0: when not NULL the solve starts from x = 0, r = rhs0 (set in its first pass)
-int launch_cg_lines(sense_plan p, float2* x, int iters, double* rr_hist, const float2* rhs0);
+// lam: device FP64, lam_count = 1 (shared by the slices) or B (one per slice), read in place.
+int launch_cg_lines(sense_plan p, float2* x, int iters, double* rr_hist, const float2* rhs0, const double* lam,
+                    int lam_count);
 int build_lines_tables(sense_plan p);
 void free_lines_tables(sense_plan p);
 
