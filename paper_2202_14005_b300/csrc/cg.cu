@@ -255,6 +255,14 @@ int grid_rows(sense_plan p) {
 
 }  // namespace
 
+bool cg_one_launch(sense_plan p, int iters) { return p->lines.ok && p->lines.coop && iters > 0; }
+
+int cg_run_one_launch(sense_plan p, const float2* rhs, const float2* rhs_b, float2* x, const double* lam,
+                      int lam_count, int iters, double* rr_hist, float2* xlam) {
+  if (!cg_one_launch(p, iters)) return SENSE_EUNSUPPORTED;
+  return launch_cg_lines(p, x, iters, rr_hist, rhs, lam, lam_count, rhs_b, xlam);
+}
+
 int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const double* lam,
            int lam_count, int iters, double* rr_hist) {
   Workspace& w = p->w;
@@ -290,7 +298,7 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
     }
   } else if (coop) {
     // x = 0, r = rhs and ||r||^2 in the first pass of the one-launch solve
-    return launch_cg_lines(p, x, iters, rr_hist, rhs, lam, lam_count);
+    return launch_cg_lines(p, x, iters, rr_hist, rhs, lam, lam_count, nullptr, nullptr);
   } else {
     RowArgs a = base_args(p);
     a.a = rhs; a.o1 = w.r; a.o2 = x; a.fin = FIN_RR0; a.hist = rr_hist;
@@ -300,7 +308,7 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
     count_launch(p);
   }
   // ---- iterations: all of them in one cooperative launch where the fused kernel applies
-  if (coop) return launch_cg_lines(p, x, iters, rr_hist, nullptr, lam, lam_count);
+  if (coop) return launch_cg_lines(p, x, iters, rr_hist, nullptr, lam, lam_count, nullptr, nullptr);
   for (int it = 0; it < iters; ++it) {
     double* hist = rr_hist ? rr_hist + (size_t)(it + 1) * B : nullptr;
     if (p->lines.ok) {

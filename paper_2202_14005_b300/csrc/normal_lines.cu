@@ -166,7 +166,7 @@ void free_lines_tables(sense_plan pl) {
 }
 
 int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const float2* rhs0, const double* lam,
-                    int lam_count) {
+                    int lam_count, const float2* rhs0b, float2* xlam) {
   const LinesTables& T = pl->lines;
   if (!T.coop) return SENSE_EUNSUPPORTED;
   Workspace& w = pl->w;
@@ -183,6 +183,7 @@ int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const 
   a.counter = w.counter; a.status = pl->status;
   CgCoop c;
   c.iters = iters; c.x = x; c.r = w.r; c.p = w.p; c.s = w.sv; c.w = w.wv; c.hist = rr_hist; c.rhs0 = rhs0;
+  c.rhs0b = rhs0 ? rhs0b : nullptr; c.xlam = xlam;
   c.polls = pl->wait_polls; c.phantom = pl->wait_phantom;
   const size_t np = (size_t)pl->B * pl->S * pl->H;
   for (int i = 0; i < 2; ++i) {

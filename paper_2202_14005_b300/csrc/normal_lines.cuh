@@ -51,6 +51,7 @@ struct NLArgs {
   const float* ab_f = nullptr;  // NM_CG2: alpha, beta of the tile's slice
   int upd = 0, first = 0;
   const float2* rhs0 = nullptr;  // NM_CG2 without upd: stage r = rhs0 (written to r) and zero x
+  const float2* rhs0b = nullptr;  // with rhs0: r = rhs0 + lambda rhs0b (the MoDL right-hand side)
   const float2* pold;
   float2* pout;
   float2* out;
@@ -227,9 +228,14 @@ __device__ __forceinline__ void nl_tile(const NLArgs& a, const NLSmem& S, int ti
         }
       } else if (a.rhs0) {
         const float4* r0 = reinterpret_cast<const float4*>(a.rhs0 + img0);
+        const float4* r0b = a.rhs0b ? reinterpret_cast<const float4*>(a.rhs0b + img0) : nullptr;
         float4* xv = reinterpret_cast<float4*>(a.xs + img0);
         for (int i = threadIdx.x; i < n4; i += nthreads) {
-          const float4 v = r0[i];
+          float4 v = r0[i];
+          if (r0b) {
+            const float4 z = r0b[i];
+            v = make_float4(fmaf(lam, z.x, v.x), fmaf(lam, z.y, v.y), fmaf(lam, z.z, v.z), fmaf(lam, z.w, v.w));
+          }
           rv[i] = v;
           xv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
           sx4[i] = v;
@@ -539,6 +545,8 @@ struct CgCoop {
   float2* w;        // S r
   double* hist;     // [iters + 1][B] squared residual norms or NULL
   const float2* rhs0;  // not NULL: start from x = 0, r = rhs0 (first pass)
+  const float2* rhs0b;  // with rhs0, not NULL: r = rhs0 + lambda rhs0b
+  float2* xlam;         // not NULL: the last pass also writes lambda x here
   // per slice b: arrival count cnt_s[32 b] and two 64-bit release words at rel_s + 32 b
   // (128-byte lines of their own), zero at launch
   unsigned* cnt_s;
@@ -718,6 +726,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
     a.upd = k > 0;
     a.first = k == 1;
     a.rhs0 = k == 0 ? c.rhs0 : nullptr;
+    a.rhs0b = k == 0 ? c.rhs0b : nullptr;
     a.part = (k & 1) ? c.pd[1] : c.pd[0];
     a.part2 = (k & 1) ? c.pg[1] : c.pg[0];
     for (int tile = t0; tile < t1; tile += gstride) nl_tile<Q, P, JMAX, NM_CG2, NS>(a, S, tile);
@@ -735,9 +744,11 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
     const int h0 = (tile - b * a.tiles_per_slice) * a.rows;
     const int nrows = min(a.rows, a.H - h0);
     const float al = s_ab[0], be = first ? 0.f : s_ab[1];
+    const float lamx = a.lam_dev ? (float)a.lam_dev[a.lam_shared ? 0 : b] : a.lam_host;
     for (int rw = warp; rw < NS * nrows; rw += nwarps) {
       const int st = rw / nrows, h = h0 + (rw - st * nrows);
       const size_t off = ((((size_t)b * NS + st) * a.H + h) * W) / 2;
+      float4* xl = c.xlam ? reinterpret_cast<float4*>(c.xlam) + off : nullptr;
       const float4* pv = reinterpret_cast<const float4*>(c.p) + off;
       const float4* sv = reinterpret_cast<const float4*>(c.s) + off;
       const float4* wv = reinterpret_cast<const float4*>(c.w) + off;
@@ -757,6 +768,7 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
         r.x = fmaf(-al, ss.x, r.x); r.y = fmaf(-al, ss.y, r.y); r.z = fmaf(-al, ss.z, r.z); r.w = fmaf(-al, ss.w, r.w);
         xv[i] = x;
         rv[i] = r;
+        if (xl) xl[i] = make_float4(lamx * x.x, lamx * x.y, lamx * x.z, lamx * x.w);
         part = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, part))));
       }
       const float2 d = warp_sum_ff(part);

@@ -139,8 +139,10 @@ float2* modl_zout(void* ws, int B, int H, int W);
 // the initial residual; rr_hist rows 1..iters written when non-NULL.
 // rhs0: when not NULL the solve starts from x = 0, r = rhs0 (set in its first pass)
 // lam: device FP64, lam_count = 1 (shared by the slices) or B (one per slice), read in place.
+// rhs0b (with rhs0): the first pass stages r = rhs0 + lambda rhs0b; xlam: the last pass also
+// writes lambda x there (both NULL when not wanted).
 int launch_cg_lines(sense_plan p, float2* x, int iters, double* rr_hist, const float2* rhs0, const double* lam,
-                    int lam_count);
+                    int lam_count, const float2* rhs0b, float2* xlam);
 int build_lines_tables(sense_plan p);
 void free_lines_tables(sense_plan p);
 
@@ -156,6 +158,13 @@ int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam
 
 int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const double* lam,
            int lam_count, int iters, double* rr_hist);
+// True when cg_run with x0 == NULL runs as one cooperative launch (the line-mask fused kernel).
+bool cg_one_launch(sense_plan p, int iters);
+// The one-launch solve from x0 = 0 of (A^H A + lambda I) x = rhs + lambda rhs_b, with lambda x also
+// written to xlam when it is not NULL (the MoDL block's right-hand side and its reverse-mode
+// scaling, fused into the first and last passes).  Only where cg_one_launch(p, iters).
+int cg_run_one_launch(sense_plan p, const float2* rhs, const float2* rhs_b, float2* x, const double* lam,
+                      int lam_count, int iters, double* rr_hist, float2* xlam);
 int launch_dot_rows(sense_plan p, const float2* a, const float2* b, const float2* c,
                     double* out, int out_count, int accumulate);
 

@@ -160,6 +160,10 @@ int unrolled_step(sense_plan p, int kind, const float* weights, const double* la
   float2* z = modl_zout(dn_ws, p->B, p->H, p->W);
   if (int e = denoiser_forward(kind, weights, x_t, z, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
     return e;
+  // rhs = A^H y + lambda z: formed by the one-launch solve's first pass where it applies
+  if (cg_one_launch(p, cg_iters))
+    return cg_run_one_launch(p, static_cast<const float2*>(AHy), z, static_cast<float2*>(x_next), lambda, 1,
+                             cg_iters, nullptr, nullptr);
   prof_mark("unrolled_misc", p->stream, false);
   k_rhs<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, static_cast<const float4*>(AHy),
                                                              reinterpret_cast<const float4*>(z), lambda,
@@ -189,17 +193,22 @@ int unrolled_step_backward_ex(sense_plan p, int kind, const float* weights, cons
   if (recompute)
     if (int e = denoiser_forward(kind, weights, x_t, z, dn_ws, dn_ws_bytes, p->B, p->H, p->W, p->stream))
       return e;
-  // v = S^{-1} g  and  grad_lambda += Re<v, z - x_next>
-  if (int e = cg_run(p, static_cast<const float2*>(grad_next), nullptr, w.t1, lambda, 1, cg_iters, nullptr))
+  // v = S^{-1} g  and  grad_lambda += Re<v, z - x_next>;  grad_z = lambda v, written by the
+  // one-launch solve's last pass where it applies
+  const bool one = cg_one_launch(p, cg_iters);
+  if (int e = one ? cg_run_one_launch(p, static_cast<const float2*>(grad_next), nullptr, w.t1, lambda, 1, cg_iters,
+                                      nullptr, w.t0)
+                  : cg_run(p, static_cast<const float2*>(grad_next), nullptr, w.t1, lambda, 1, cg_iters, nullptr))
     return e;
   if (int e = launch_dot_rows(p, w.t1, z, static_cast<const float2*>(x_next), grad_lambda, 1, 1))
     return e;
-  // grad_z = lambda v  (z is no longer needed)
-  prof_mark("unrolled_misc", p->stream, false);
-  k_scale<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, reinterpret_cast<const float4*>(w.t1),
-                                                               lambda, reinterpret_cast<float4*>(w.t0));
-  prof_mark("unrolled_misc", p->stream, true);
-  count_launch(p);
+  if (!one) {
+    prof_mark("unrolled_misc", p->stream, false);
+    k_scale<<<(unsigned)((n2 + 255) / 256), 256, 0, p->stream>>>(n2, reinterpret_cast<const float4*>(w.t1),
+                                                                 lambda, reinterpret_cast<float4*>(w.t0));
+    prof_mark("unrolled_misc", p->stream, true);
+    count_launch(p);
+  }
   return denoiser_backward(kind, weights, x_t, w.t0, grad_t, grad_weights, dn_ws, dn_ws_bytes, p->B, p->H,
                            p->W, 0, p->stream);
 }
