@@ -736,8 +736,11 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
       return;
     }
   }
-  // last update (iteration iters - 1) and gamma of the final residual; one warp per row
+  // last update (iteration iters - 1), and the final residual with its gamma only when the
+  // residual history is kept (nothing else reads them; without it the pass updates x alone and
+  // ends without a barrier); one warp per row
   const bool first = c.iters == 1;
+  const bool keep_r = c.hist != nullptr;
   a.part2 = (c.iters & 1) ? c.pg[1] : c.pg[0];
   for (int tile = t0; tile < t1; tile += gstride) {
     const int b = tile / a.tiles_per_slice;
@@ -757,26 +760,34 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
       float part = 0.f;
       for (int i = lane; i < W / 2; i += 32) {
         float4 r = rv[i], x = xv[i];
-        const float4 w = wv[i];
-        float4 pp = r, ss = w;
+        float4 pp = r;
         if (!first) {
-          const float4 po = pv[i], so = sv[i];
+          const float4 po = pv[i];
           pp.x = fmaf(be, po.x, r.x); pp.y = fmaf(be, po.y, r.y); pp.z = fmaf(be, po.z, r.z); pp.w = fmaf(be, po.w, r.w);
-          ss.x = fmaf(be, so.x, w.x); ss.y = fmaf(be, so.y, w.y); ss.z = fmaf(be, so.z, w.z); ss.w = fmaf(be, so.w, w.w);
         }
         x.x = fmaf(al, pp.x, x.x); x.y = fmaf(al, pp.y, x.y); x.z = fmaf(al, pp.z, x.z); x.w = fmaf(al, pp.w, x.w);
-        r.x = fmaf(-al, ss.x, r.x); r.y = fmaf(-al, ss.y, r.y); r.z = fmaf(-al, ss.z, r.z); r.w = fmaf(-al, ss.w, r.w);
         xv[i] = x;
-        rv[i] = r;
         if (xl) xl[i] = make_float4(lamx * x.x, lamx * x.y, lamx * x.z, lamx * x.w);
-        part = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, part))));
+        if (keep_r) {
+          const float4 w = wv[i];
+          float4 ss = w;
+          if (!first) {
+            const float4 so = sv[i];
+            ss.x = fmaf(be, so.x, w.x); ss.y = fmaf(be, so.y, w.y); ss.z = fmaf(be, so.z, w.z); ss.w = fmaf(be, so.w, w.w);
+          }
+          r.x = fmaf(-al, ss.x, r.x); r.y = fmaf(-al, ss.y, r.y); r.z = fmaf(-al, ss.z, r.z); r.w = fmaf(-al, ss.w, r.w);
+          rv[i] = r;
+          part = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, part))));
+        }
       }
-      const float2 d = warp_sum_ff(part);
-      if (lane == 0) reinterpret_cast<float2*>(a.part2)[(size_t)b * a.HS + st * a.H + h] = d;
+      if (keep_r) {
+        const float2 d = warp_sum_ff(part);
+        if (lane == 0) reinterpret_cast<float2*>(a.part2)[(size_t)b * a.HS + st * a.H + h] = d;
+      }
     }
   }
-  if (!coop_step(a, c, cnt, rel, group, b0, (unsigned)c.iters, c.iters, true,
-                 c.hist ? c.hist + (size_t)c.iters * a.B : nullptr, s_ab)) {
+  if (keep_r && !coop_step(a, c, cnt, rel, group, b0, (unsigned)c.iters, c.iters, true,
+                           c.hist + (size_t)c.iters * a.B, s_ab)) {
     if (threadIdx.x == 0) set_status(a.status, SENSE_STATUS_DEVICE_TIMEOUT);
   }
 }

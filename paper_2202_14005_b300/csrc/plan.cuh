@@ -136,7 +136,8 @@ int launch_normal_lines(sense_plan p, const NormalLaunch& L);
 // The region of a MoDL denoiser workspace that keeps an unrolled step's z = D(x_t).
 float2* modl_zout(void* ws, int B, int H, int W);
 // Every CG iteration in one cooperative launch (p->lines.coop): x, w.r, w.p, w.q, w.rr as left by
-// the initial residual; rr_hist rows 1..iters written when non-NULL.
+// the initial residual; rr_hist rows 1..iters written when non-NULL (without it the final
+// residual and its norm are not formed: w.r and w.rr then hold those of the last iteration but one).
 // rhs0: when not NULL the solve starts from x = 0, r = rhs0 (set in its first pass)
 // lam: device FP64, lam_count = 1 (shared by the slices) or B (one per slice), read in place.
 // rhs0b (with rhs0): the first pass stages r = rhs0 + lambda rhs0b; xlam: the last pass also
