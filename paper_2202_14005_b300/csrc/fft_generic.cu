@@ -682,40 +682,51 @@ __device__ __forceinline__ void tw512_apply(float2 (&v)[8], const float2* tabt, 
   }
 }
 
+// Exchange barrier of one sequence.  Row mapping: the sequence's 64 threads are the two warps
+// 2r, 2r + 1 (r = threadIdx.x / 64, at most 8 rows per CTA), which sync alone on named barrier
+// 1 + r, so the rows of a CTA do not wait for each other.  Column mapping: every warp holds lanes
+// of every column, so the whole CTA syncs.
+template <bool ROW>
+__device__ __forceinline__ void seq512_bar() {
+  if constexpr (ROW) asm volatile("bar.sync %0, 64;" ::"r"(1 + (int)(threadIdx.x >> 6)) : "memory");
+  else __syncthreads();
+}
+
 // Forward transform of one zero-padded sequence.  Entry: v[n1] = x[64 n1 + t] for n1 < 4.
 // Exit: v[j2] = X[hi + 8 lo + 64 j2].  s0, s1: the sequence's two exchange buffers; tabt: the
-// thread's twiddle row.  Contains two __syncthreads.
+// thread's twiddle row.  Contains two exchange barriers (seq512_bar).
 template <bool ROW>
 __device__ __forceinline__ void fwd512_zhi(float2 (&v)[8], float2* s0, float2* s1, int t, const float2* tabt) {
   using L = Lay512<ROW>;
   const int lo = t & 7, hi = t >> 3;
   dft8_lowhalf<false>(v);
   tw512_apply<false, true>(v, tabt, 0, s0, [&](int k1) { return L::y(t, k1); });
-  __syncthreads();
+  seq512_bar<ROW>();
 #pragma unroll
   for (int m1 = 0; m1 < 8; ++m1) v[m1] = s0[L::y(8 * m1 + lo, hi)];
   dft_pow2<8, false>(v);
   tw512_apply<false, true>(v, tabt, 8, s1, [&](int j1) { return L::v(hi, lo, j1); });
-  __syncthreads();
+  seq512_bar<ROW>();
 #pragma unroll
   for (int m2 = 0; m2 < 8; ++m2) v[m2] = s1[L::v(hi, m2, lo)];
   dft_pow2<8, false>(v);
 }
 
 // Inverse transform, first half of the output.  Entry: v[d2] = P[hi + 8 lo + 64 d2].
-// Exit: v[e2] = y[t + 64 e2] for e2 < 4 (v[4..7] are not formed).  Contains two __syncthreads.
+// Exit: v[e2] = y[t + 64 e2] for e2 < 4 (v[4..7] are not formed).  Contains two exchange
+// barriers (seq512_bar).
 template <bool ROW>
 __device__ __forceinline__ void inv512_hout(float2 (&v)[8], float2* s0, float2* s1, int t, const float2* tabt) {
   using L = Lay512<ROW>;
   const int lo = t & 7, hi = t >> 3;
   dft_pow2<8, true>(v);
   tw512_apply<true, true>(v, tabt, 8, s0, [&](int e0) { return L::v(hi, lo, e0); });
-  __syncthreads();
+  seq512_bar<ROW>();
 #pragma unroll
   for (int d1 = 0; d1 < 8; ++d1) v[d1] = s0[L::v(hi, d1, lo)];
   dft_pow2<8, true>(v);
   tw512_apply<true, false>(v, tabt, 16, s1, [&](int e1) { return L::z(hi, lo, e1); });  // w^{d0 (e0 + 8 e1)}
-  __syncthreads();
+  seq512_bar<ROW>();
 #pragma unroll
   for (int d0 = 0; d0 < 8; ++d0) v[d0] = s1[L::z(d0, lo, hi)];
   dft_pow2<8, true>(v);
