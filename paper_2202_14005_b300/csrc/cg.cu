@@ -230,6 +230,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_resid(const RowArgs a) {
   if (a.fin) last_block(a);
 }
 
+// The per-slice reductions alone, over row partials another kernel wrote (one CTA).
+__global__ void __launch_bounds__(256) k_cg_fin(const RowArgs a) { finalize(a); }
+
 __global__ void k_lam_expand(int B, const double* lam, int count, double* out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < B) out[b] = lam[count == 1 ? 0 : b];
@@ -323,12 +326,22 @@ int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const d
       k_cg_p<<<gr, kWarps * 32, 0, p->stream>>>(a);
       prof_mark("cg_vec", p->stream, true);
       count_launch(p);
-      if (int e = launch_normal_generic(p, w.p, w.q, 0.f, w.lam)) return e;
       RowArgs d = base_args(p);
       d.a = w.p; d.b = w.q; d.fin = FIN_ALPHA;
-      prof_mark("cg_vec", p->stream, false);
-      k_dot<<<gr, kWarps * 32, 0, p->stream>>>(d);
-      prof_mark("cg_vec", p->stream, true);
+      if (toeplitz_fused_dot(p)) {
+        // the operator's inverse row pass writes the rows of Re<p, q> (two slots per row)
+        if (int e = launch_normal_toeplitz(p, w.p, w.q, 0.f, w.lam, w.part2)) return e;
+        d.part = w.part2;
+        d.H = 2 * p->S * p->H;
+        prof_mark("cg_vec", p->stream, false);
+        k_cg_fin<<<1, 256, 0, p->stream>>>(d);
+        prof_mark("cg_vec", p->stream, true);
+      } else {
+        if (int e = launch_normal_generic(p, w.p, w.q, 0.f, w.lam)) return e;
+        prof_mark("cg_vec", p->stream, false);
+        k_dot<<<gr, kWarps * 32, 0, p->stream>>>(d);
+        prof_mark("cg_vec", p->stream, true);
+      }
       count_launch(p);
     }
     RowArgs u = base_args(p);

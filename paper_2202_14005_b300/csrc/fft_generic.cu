@@ -822,7 +822,8 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_tp_rows_inv512(int C, int H, fl
                                                                float2* __restrict__ out,
                                                                const float2* __restrict__ tw,
                                                                const float2* __restrict__ xin, float lam_host,
-                                                               const double* __restrict__ lam_dev, int cpg) {
+                                                               const double* __restrict__ lam_dev, int cpg,
+                                                               double* __restrict__ dpart) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = threadIdx.x >> 6, t = threadIdx.x & 63;
   const int b = blockIdx.y;
@@ -867,10 +868,17 @@ __global__ void __launch_bounds__(64 * kR5, 2) k_tp_rows_inv512(int C, int H, fl
   }
   const float lam = lam_dev ? (float)lam_dev[b] : lam_host;
   const size_t o = ((size_t)b * H + h) * 256 + t;
+  float dot = 0.f;
 #pragma unroll
   for (int e2 = 0; e2 < 4; ++e2) {
     const float2 xv = xin[o + 64 * e2];
-    out[o + 64 * e2] = make_float2(fmaf(lam, xv.x, acc[e2].x), fmaf(lam, xv.y, acc[e2].y));
+    const float2 q = make_float2(fmaf(lam, xv.x, acc[e2].x), fmaf(lam, xv.y, acc[e2].y));
+    out[o + 64 * e2] = q;
+    dot = fmaf(xv.x, q.x, fmaf(xv.y, q.y, dot));
+  }
+  if (dpart) {  // Re<x, out> of this row, one slot per warp of the row (float-float warp sum, FP64 once)
+    const float2 d = warp_sum_ff(dot);
+    if ((threadIdx.x & 31) == 0) dpart[((size_t)b * H + h) * 2 + ((threadIdx.x >> 5) & 1)] = ff_to_d(d);
   }
 }
 
@@ -1760,7 +1768,7 @@ int launch_normal_r8p(sense_plan p, const float2* x, float2* out, float lam_host
 
 int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_host,
                           const double* lam_dev) {
-  if (p->toep) return launch_normal_toeplitz(p, x, out, lam_host, lam_dev);
+  if (p->toep) return launch_normal_toeplitz(p, x, out, lam_host, lam_dev, nullptr);
   if (p->r8p) return launch_normal_r8p(p, x, out, lam_host, lam_dev);
   if (p->blue) return launch_normal_blue(p, x, out, lam_host, lam_dev);
   const dim3 gr((p->H + kRows - 1) / kRows, p->B * p->C);
@@ -1806,7 +1814,23 @@ int toeplitz_prepare(sense_plan p, const float2* psf) {
   return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
-int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam_host, const double* lam_dev) {
+// The Toeplitz operator's inverse row pass can also form the rows of Re<x, out> (one coil
+// group: the register-resident row passes with every coil of a row in one CTA).
+static int toeplitz_groups(sense_plan p, bool rows512) {
+  const int nrb = rows512 ? (p->H + kR5 - 1) / kR5 : (p->H + kRows - 1) / kRows;
+  const int target = rows512 ? 1024 : 2048;
+  int groups = (target + nrb * p->B - 1) / (nrb * p->B);
+  groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
+  const int cpg = (p->C + groups - 1) / groups;
+  return (p->C + cpg - 1) / cpg;
+}
+bool toeplitz_fused_dot(sense_plan p) {
+  return p->toep && use_rows512(p) && toeplitz_groups(p, true) == 1;
+}
+
+int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam_host, const double* lam_dev,
+                           double* dpart) {
+  if (dpart && !toeplitz_fused_dot(p)) return SENSE_EUNSUPPORTED;
   const int W2 = 2 * p->W;
   const bool rows512 = use_rows512(p);
   prof_mark("toeplitz", p->stream, false);
@@ -1829,15 +1853,13 @@ int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam
   // inverse rows and coil combine, the coils split into groups across grid.z (about 2048 CTAs
   // of 256 threads, or 1024 of 512 with the register-resident pass)
   const int nrb = rows512 ? (p->H + kR5 - 1) / kR5 : (p->H + kRows - 1) / kRows;
-  const int target = rows512 ? 1024 : 2048;
-  int groups = (target + nrb * p->B - 1) / (nrb * p->B);
-  groups = groups < 1 ? 1 : (groups > p->C ? p->C : groups);
+  const int groups = toeplitz_groups(p, rows512);
   const int cpg = (p->C + groups - 1) / groups;
-  groups = (p->C + cpg - 1) / cpg;
   const dim3 gr2(nrb, p->B, groups);
   if (rows512) {
     k_tp_rows_inv512<<<gr2, 64 * kR5, smem_rows512(), p->stream>>>(p->C, p->H, p->w.T, p->maps, out, p->twtab, x,
-                                                                    lam_host, lam_dev, groups > 1 ? cpg : p->C);
+                                                                    lam_host, lam_dev, groups > 1 ? cpg : p->C,
+                                                                    groups > 1 ? nullptr : dpart);
   } else {
     SENSE_LAUNCH_CLS(fft_class(p->fW2), k_tp_rows_inv, gr2, smem_rows_inv(W2), p->stream, p->C, p->H, p->W, p->w.T,
                      p->maps, out, dev(p->fW2), x, lam_host, lam_dev, groups > 1 ? cpg : p->C);

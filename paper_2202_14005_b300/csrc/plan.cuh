@@ -155,7 +155,10 @@ int launch_normal_generic(sense_plan p, const float2* x, float2* out, float lam_
                           const double* lam_dev);
 int toeplitz_prepare(sense_plan p, const float2* psf);  // psf_hat from the PSF, kernel attributes
 int launch_normal_toeplitz(sense_plan p, const float2* x, float2* out, float lam_host,
-                           const double* lam_dev);
+                           const double* lam_dev, double* dpart);
+// True when launch_normal_toeplitz can also write the rows of Re<x, out> into dpart ([B][H][2]
+// FP64: one slot per warp of a row, summed in slot order by the CG finalize).
+bool toeplitz_fused_dot(sense_plan p);
 
 int cg_run(sense_plan p, const float2* rhs, const float2* x0, float2* x, const double* lam,
            int lam_count, int iters, double* rr_hist);

@@ -177,3 +177,24 @@ def test_nudft_full_size_sampled():
         v = (y[0].astype(np.complex128) * ph[None]).sum(axis=1) / N          # [C]
         ref = np.sum(np.conj(maps[0, :, r, c].astype(np.complex128)) * v)
         assert abs(xg[0, r, c] - ref) <= 1e-5 * max(abs(ref), np.abs(v).max())
+
+
+def test_cg_toeplitz_fused_dot_32_slices():
+    """32 slices of 256 x 256 put every coil of a row in one CTA of the register-resident inverse
+    row pass, which then also forms the rows of Re<p, S p> for the CG step (no separate dot
+    pass): 5 iterations against the oracle's CG on the Toeplitz operator of the GPU's PSF, with
+    residual histories."""
+    from paper_2202_14005_b300.sense import SensePlan, toeplitz_psf
+    B, C, N, lam_v, iters = 32, 2, 256, 0.5, 5
+    maps, traj = case(B, C, N, 32, 256, seed=9)
+    psf = toeplitz_psf(dev(traj), N, N)
+    plan = SensePlan.toeplitz(dev(maps), psf)
+    rhs = synth.randn_complex((B, N, N), 6).astype(np.complex64)
+    lam = torch.tensor([lam_v], dtype=torch.float64, device="cuda")
+    hist = torch.zeros((iters + 1, B), dtype=torch.float64, device="cuda")
+    x = plan.cg_solve(dev(rhs), lam, iters, rr_hist=hist).cpu().numpy()
+    g = psf.cpu().numpy().astype(np.complex128)
+    ref, rr = ocg.cg(lambda p: onc.toeplitz_normal(p, maps, g, lam_v), rhs, None, iters)
+    assert rel(x, ref) <= 1e-4
+    np.testing.assert_allclose(hist.cpu().numpy(), rr, rtol=1e-3, atol=1e-12 * rr[0].max())
+    assert plan.status() == 0
