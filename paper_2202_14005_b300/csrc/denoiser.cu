@@ -315,6 +315,15 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  // The packed weights (and the bias above) come from launches at least two kernels back, so they
+  // load before the wait for the previous kernel; the halos, masks and residuals it may have
+  // written, and every store, come after.
+  if (warp == 4 && lane == 0 && n > 0) {
+    mbar_expect_tx(w_full, CL::WP);
+    bulk_load(smem + CL::OFF_W, a.wpack, CL::WP, w_full);
+  }
+  griddep_wait();
+  griddep_release();
 
   // producer bookkeeping (lane 0 of warp 4): what it issued and what it has seen complete
   int tma_issued = 0, mma_issued = 0;
@@ -322,8 +331,6 @@ k_conv64(const __grid_constant__ CUtensorMap tmap, const ConvArgs a) {
     if (lane == 0 && n > 0) {
       const uint32_t sw = smem_u32(smem + CL::OFF_W);
       bool ok = true;
-      mbar_expect_tx(w_full, CL::WP);
-      bulk_load(smem + CL::OFF_W, a.wpack, CL::WP, w_full);
       const int pre = n < 2 ? n : 2;
       for (int j = 0; j < pre; ++j) {
         issue_halo<NOUT>(&tmap, s_halo + j * CL::HALO_SLOT, &halo_full[j], blockIdx.x + j * gridDim.x, a.H, a.ntw);
@@ -941,6 +948,8 @@ k_wgrad64(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUte
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  griddep_wait();  // the activations and gradient rows, and the partial sums written below
+  griddep_release();
 
   int tma_issued = 0, mma_issued = 0;
   if (warp == 4) {
@@ -1152,17 +1161,19 @@ int launch_conv64(const __nv_bfloat16* in, const __nv_bfloat16* wpack, const flo
   a.res = res; a.out2 = out2;
   const int ntiles = B * H * a.ntw;
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  // programmatic stream serialisation: the prologue overlaps the previous kernel's tail
+  cudaError_t e;
   if (mode >= 2) {  // 64 -> 2 layers
     prof_mark("dn_64to2", st, false);
-    k_conv64<16><<<grid, CONV_THREADS, ConvLayout<16>::SMEM, st>>>(map, a);
+    e = launch_pdl(k_conv64<16>, dim3(grid), dim3(CONV_THREADS), ConvLayout<16>::SMEM, st, map, a);
     prof_mark("dn_64to2", st, true);
   } else {
     prof_mark("conv64_tc", st, false);
-    k_conv64<64><<<grid, CONV_THREADS, ConvLayout<64>::SMEM, st>>>(map, a);
+    e = launch_pdl(k_conv64<64>, dim3(grid), dim3(CONV_THREADS), ConvLayout<64>::SMEM, st, map, a);
     prof_mark("conv64_tc", st, true);
   }
   prof_count(1);
-  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
 size_t up256(size_t n) { return (n + 255) & ~(size_t)255; }
@@ -1181,10 +1192,10 @@ int launch_wgrad64(const __nv_bfloat16* g, const __nv_bfloat16* act, float* part
   if (grid > max_parts) grid = max_parts;
   *nparts = grid;
   prof_mark("wgrad64", st, false);
-  k_wgrad64<<<grid, WG_THREADS, WG_SMEM, st>>>(amap, gmap, a);
+  const cudaError_t e = launch_pdl(k_wgrad64, dim3(grid), dim3(WG_THREADS), WG_SMEM, st, amap, gmap, a);
   prof_mark("wgrad64", st, true);
   prof_count(1);
-  return cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
 struct DnLayout {
