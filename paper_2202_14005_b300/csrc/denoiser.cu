@@ -128,6 +128,8 @@ __device__ __forceinline__ float w2to64(const float* w, int mode, int k, int j) 
   return mode == 0 ? w[(j * 2 + c) * 9 + tap] : w[(c * CH + j) * 9 + tap];
 }
 __global__ void k_pack64(const PackArgs a) {
+  griddep_wait();  // launched with programmatic serialisation: nothing is read before this
+  griddep_release();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9*8*64*8
   if (blockIdx.y >= 8) {  // B fragments of the 2 -> 64 layers, in the order a lane loads them
     const int mode = blockIdx.y - 8, ks_n = mode == 0 ? 2 : 4;
@@ -513,6 +515,8 @@ __global__ void __launch_bounds__(k2Threads) k_2to64(int B, int H, int W, const 
                                                      __nv_bfloat16* out) {
   constexpr int KS = MODE == 0 ? 2 : 4;  // k-steps of 16
   constexpr int KV = MODE == 0 ? 18 : 54;
+  griddep_wait();  // launched with programmatic serialisation: the fragments and the input come
+  griddep_release();  // from the kernels before it
   extern __shared__ __align__(16) uint8_t dsm[];
   float2* s_n = reinterpret_cast<float2*>(dsm);  // [k2Rows + 2][W + 2]
   const int ld = W + 2;
@@ -1258,12 +1262,12 @@ int forward_impl(const float* wts, const float2* x, float2* out, uint8_t* ws, in
     pa.t1 = reinterpret_cast<__nv_bfloat16*>(ws + L.ts[1]);
     pa.f1 = reinterpret_cast<uint32_t*>(ws + L.tf[0]);
     pa.f5 = reinterpret_cast<uint32_t*>(ws + L.tf[1]);
-    k_pack64<<<dim3((9 * 8 * CH * 8 + 255) / 256, 10), 256, 0, st>>>(pa);
+    launch_pdl(k_pack64, dim3((9 * 8 * CH * 8 + 255) / 256, 10), dim3(256), 0, st, pa);
     prof_mark("dn_pack", st, true);
   }
   const size_t npx = (size_t)B * H * W;
   prof_mark("dn_2to64", st, false);
-  k_2to64<0><<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(
+  launch_pdl(k_2to64<0>, dim3((unsigned)(B * ((H + k2Rows - 1) / k2Rows))), dim3(k2Threads), k2_smem(W), st,
       B, H, W, x, reinterpret_cast<const uint32_t*>(ws + L.tf[0]), wts + o.b[0], nullptr, act[0]);
   prof_mark("dn_2to64", st, true);
   for (int l = 0; l < 3; ++l)
@@ -1355,7 +1359,7 @@ int denoiser_backward(int kind, const float* weights, const void* x, const void*
   if (int e = stream_after(*ss, st, sd)) return e;
   // last layer: input gradient (masked by a4 > 0) on the caller's stream, weight gradient beside it
   prof_mark("dn_2to64", st, false);
-  k_2to64<1><<<(unsigned)(B * ((H + k2Rows - 1) / k2Rows)), k2Threads, k2_smem(W), st>>>(
+  launch_pdl(k_2to64<1>, dim3((unsigned)(B * ((H + k2Rows - 1) / k2Rows))), dim3(k2Threads), k2_smem(W), st,
       B, H, W, go, reinterpret_cast<const uint32_t*>(w8 + L.tf[1]), nullptr, act[3], gbuf[0]);
   prof_mark("dn_2to64", st, true);
   prof_mark("dn_wgrad_small", sd, false);
