@@ -74,32 +74,6 @@ SENSE_D void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // whole warp
 SENSE_D void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 SENSE_D void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Programmatic dependent launch (a kernel launched with programmatic stream serialisation may
-// start while the kernel before it in the stream is still running): griddep_wait returns once
-// that kernel has completed and its memory is visible (at once for a kernel launched without
-// the attribute); griddep_release lets the next such kernel start its own prologue.  A kernel
-// calls griddep_release only after griddep_wait, so whenever a prologue runs, every kernel
-// before its predecessor has completed.
-SENSE_D void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-SENSE_D void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// Launch with programmatic stream serialisation (for the kernels that call griddep_wait before
-// reading what the previous kernel wrote and before writing anything).
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
-}
 
 // Shared-memory matrix descriptor, no swizzle: start address, leading-dimension
 // byte offset (between core matrices along K for K-major operands), stride
