@@ -35,7 +35,7 @@ WsLayout ws_layout(const sense_plan p) {
   L.alpha = o; o += up256(p->B * sizeof(double));
   L.beta = o; o += up256(p->B * sizeof(double));
   L.lam = o; o += up256(p->B * sizeof(double));
-  L.counter = o; o += 8192;  // counters, the one-launch CG scalars and barrier words
+  L.counter = o; o += 12288;  // counters, the one-launch CG scalars and two sets of barrier words
   L.total = o;
   return L;
 }
@@ -243,7 +243,7 @@ int sense_plan_set_workspace(sense_plan p, void* ws, size_t bytes) {
   w.beta = reinterpret_cast<double*>(b + L.beta);
   w.lam = reinterpret_cast<double*>(b + L.lam);
   w.counter = reinterpret_cast<unsigned*>(b + L.counter);
-  return cudaMemsetAsync(w.counter, 0, 8192, p->stream) == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
+  return cudaMemsetAsync(w.counter, 0, 12288, p->stream) == cudaSuccess ? SENSE_OK : SENSE_ECUDA;
 }
 
 int sense_forward(sense_plan p, const void* x, void* y) {

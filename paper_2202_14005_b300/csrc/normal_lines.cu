@@ -190,16 +190,38 @@ int launch_cg_lines(sense_plan pl, float2* x, int iters, double* rr_hist, const 
     c.pd[i] = w.part2 + i * np;
     c.pg[i] = w.part2 + (2 + i) * np;
   }
-  // counter block: last-block counter (bytes 0..127), scalars (512..895), per-slice arrival
-  // counts (1024 + 128 b) and release words (3072 + 128 b)
+  // counter block: last-block counter (bytes 0..127), scalars (512..895), and two sets of
+  // per-slice arrival counts (set base + 128 b) and release words (set base + 2048 + 128 b) at
+  // bytes 1024 and 5120.  Solves alternate between the sets; each zeroes the other set (the
+  // previous solve's) after its wait for the previous kernel, so no reset sits in the stream
+  // between the solve and the kernel before it (both sets are zero when the workspace is set up).
   c.sc = reinterpret_cast<double*>(w.counter + 128);
-  c.cnt_s = w.counter + 256;
-  c.rel_s = w.counter + 768;
-  if (cudaMemsetAsync(c.cnt_s, 0, 4096, pl->stream) != cudaSuccess) return SENSE_ECUDA;
+  const int set = pl->coop_set;
+  pl->coop_set = 1 - set;
+  c.cnt_s = w.counter + 256 + 1024 * set;
+  c.rel_s = c.cnt_s + 512;
+  c.cnt_o = w.counter + 256 + 1024 * (1 - set);
   void* args[] = {&a, &c};
   prof_mark("cg_lines", pl->stream, false);
-  const cudaError_t e = cudaLaunchCooperativeKernel(T.coop, dim3(T.coop_grid), dim3(T.threads), args,
-                                                    (size_t)T.smem, pl->stream);
+  // cooperative launch with programmatic stream serialisation (the prologue overlaps the previous
+  // kernel's tail); where the driver refuses the pair, the plain cooperative launch
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(T.coop_grid);
+  cfg.blockDim = dim3(T.threads);
+  cfg.dynamicSmemBytes = (size_t)T.smem;
+  cfg.stream = pl->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, T.coop, args);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    e = cudaLaunchCooperativeKernel(T.coop, dim3(T.coop_grid), dim3(T.threads), args, (size_t)T.smem, pl->stream);
+  }
   prof_mark("cg_lines", pl->stream, true);
   count_launch(pl);
   return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? SENSE_OK : SENSE_ECUDA;

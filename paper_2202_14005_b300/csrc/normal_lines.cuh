@@ -551,6 +551,9 @@ struct CgCoop {
   // (128-byte lines of their own), zero at launch
   unsigned* cnt_s;
   unsigned* rel_s;
+  // the other set of barrier words (4 KB from cnt_o), used by the previous solve: zeroed by this
+  // solve after its wait for the previous kernel, for the next solve
+  unsigned* cnt_o;
   double* sc;       // FP64 scalars kept for the next pass: alpha [kCoopMaxB], gamma alpha [kCoopMaxB], gamma [kCoopMaxB]
   // row partials of delta and gamma, two buffers each, used by alternate passes
   double* pd[2];
@@ -704,6 +707,11 @@ __global__ void __launch_bounds__(256, NS == 1 ? 3 : 2) k_cg_lines(const NLArgs 
   const NLSmem S = nl_smem_setup<Q, P, NS>(a0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   if (threadIdx.x == 0) s_ab[0] = s_ab[1] = 0.f;
+  // Launched with programmatic serialisation where the driver allows it: the tables above are
+  // plan constants; the vectors, partials and barrier words come after the wait.
+  griddep_wait();
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) c.cnt_o[i] = 0u;
   __syncthreads();
   NLArgs a = a0;
   a.x = c.r; a.out = c.w; a.pout = c.p; a.sv = c.s; a.xs = c.x; a.ab_f = s_ab;

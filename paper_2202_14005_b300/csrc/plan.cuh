@@ -87,6 +87,7 @@ struct sense_plan_s {
   // barrier before a CTA gives up, and arrivals added to every barrier (1 makes it unreachable)
   unsigned wait_polls = 1u << 22;
   unsigned wait_phantom = 0;
+  int coop_set = 0;  // barrier-word set of the next one-launch CG solve (0 or 1, alternating)
   void* own = nullptr;          // plan-owned device allocation (tables + status)
   void* ws = nullptr;
   size_t ws_bytes = 0;
