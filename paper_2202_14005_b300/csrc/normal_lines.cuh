@@ -548,7 +548,8 @@ struct CgCoop {
   const float2* rhs0b;  // with rhs0, not NULL: r = rhs0 + lambda rhs0b
   float2* xlam;         // not NULL: the last pass also writes lambda x here
   // per slice b: arrival count cnt_s[32 b] and two 64-bit release words at rel_s + 32 b
-  // (128-byte lines of their own), zero at launch
+  // (128-byte lines of their own), zero at launch (zeroed by the previous solve, or at workspace
+  // setup)
   unsigned* cnt_s;
   unsigned* rel_s;
   // the other set of barrier words (4 KB from cnt_o), used by the previous solve: zeroed by this
