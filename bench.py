@@ -65,8 +65,8 @@ NCU_TRAFFIC = {
     "cg_sense": {"normal_lines": 102.8e6, "cg_lines": 1.527e9},
     "modl_train": {"cg_lines": 26.7e6, "conv64_tc": 30.52e6, "wgrad64": 61.3e6},
     "varnet_train": {"vn_K": 31.18e6, "vn_KT": 41.5e6, "vn_wgrad": 70.9e6},
-    # one Toeplitz application: its three passes (rows 568 MB, columns 754 MB, inverse rows 642 MB)
-    "noncart_modl_infer": {"toeplitz": 1.964e9},
+    # one Toeplitz application: its three passes (rows 567 MB, columns 754 MB, inverse rows 633 MB)
+    "noncart_modl_infer": {"toeplitz": 1.955e9},
 }
 # what the reverse pass reuses from the forward pass of each training workload
 REVERSE_PASS = {
